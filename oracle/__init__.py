@@ -1,0 +1,213 @@
+"""CPU oracle of the TU-fRG hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product path (``paper_1710_08830_gb300``) never imports it and never falls
+back to it.
+
+``oracle/tufrg_oracle.c`` is a plain FP64 C implementation written from the
+paper's equations; this module compiles it with gcc (``build()``) and wraps it
+with ctypes.  ``oracle/bruteforce.py`` is a second, independent numpy
+implementation of the full-momentum RGE used to pin the oracle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tufrg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (OpenMP, -O2, no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(C.Structure):
+    _fields_ = [("ns", C.c_int), ("nhop", C.c_int), ("hopR", C.c_void_p), ("hopt", C.c_void_p),
+                ("V0", C.c_void_p), ("nff", C.c_int), ("ffR", C.c_void_p),
+                ("Lq", C.c_int), ("nc", C.c_int), ("mu", C.c_double)]
+
+
+class FlowOpts(C.Structure):
+    _fields_ = [("T0", C.c_double), ("T_end", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("h0", C.c_double), ("stop", C.c_double), ("chmask", C.c_int), ("max_steps", C.c_int),
+                ("fixed_n", C.c_int)]
+
+
+class FlowResult(C.Structure):
+    _fields_ = [("Tc", C.c_double), ("crossed", C.c_int), ("n_steps", C.c_int), ("n_reject", C.c_int),
+                ("n_rhs", C.c_int), ("amax", C.c_double), ("T_last", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            vp, d, i = C.c_void_p, C.c_double, C.c_int
+            L.or_eigh.argtypes = [i, vp, vp, vp]
+            L.or_bands.argtypes = [vp, vp, vp]
+            L.or_density.argtypes = [vp, vp, d, d]
+            L.or_density.restype = d
+            L.or_find_mu.argtypes = [vp, vp, d, d]
+            L.or_find_mu.restype = d
+            L.or_fermi.argtypes = [d, d, vp, vp, vp]
+            for fn in ("or_wm", "or_wp", "or_Fm", "or_Fp"):
+                getattr(L, fn).argtypes = [d, d, d]
+                getattr(L, fn).restype = d
+            L.or_delta_list.argtypes = [vp, vp]
+            L.or_delta_list.restype = i
+            L.or_loops.argtypes = [vp, vp, vp, d, i, i, vp]
+            L.or_project.argtypes = [vp, vp, i, vp]
+            L.or_project.restype = d
+            L.or_vlv.argtypes = [vp, vp, vp, vp, i, vp]
+            L.or_rhs.argtypes = [vp, vp, vp, d, vp, i, vp, vp]
+            L.or_rhs.restype = d
+            L.or_flow.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.or_flow.restype = i
+            L.or_num_threads.restype = i
+            L.or_set_threads.argtypes = [i]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def eigh(H: np.ndarray):
+    """Eigen-decomposition of one Hermitian matrix by the oracle's Jacobi solver."""
+    H = np.ascontiguousarray(H, np.complex128)
+    n = H.shape[0]
+    E = np.zeros(n)
+    U = np.zeros((n, n), np.complex128)
+    lib().or_eigh(n, _ptr(H), _ptr(E), _ptr(U))
+    return E, U
+
+
+def fermi(e: float, T: float):
+    f, g, gp = C.c_double(), C.c_double(), C.c_double()
+    lib().or_fermi(e, T, C.byref(f), C.byref(g), C.byref(gp))
+    return f.value, g.value, gp.value
+
+
+def wm(e1, e2, T):
+    return lib().or_wm(e1, e2, T)
+
+
+def wp(e1, e2, T):
+    return lib().or_wp(e1, e2, T)
+
+
+def Fm(e1, e2, T):
+    return lib().or_Fm(e1, e2, T)
+
+
+def Fp(e1, e2, T):
+    return lib().or_Fp(e1, e2, T)
+
+
+class Oracle:
+    """The oracle bound to one model descriptor (``inputs.ModelSpec``)."""
+
+    def __init__(self, spec, mu: float | None = None):
+        self.spec = spec
+        self._hopR = np.ascontiguousarray(spec.hop_R, np.int32)
+        self._hopt = np.ascontiguousarray(spec.hop_t, np.complex128)
+        self._V0 = np.ascontiguousarray(spec.V0, np.complex128)
+        self._ffR = np.ascontiguousarray(spec.ff_R, np.int32)
+        self.m = _Model(spec.n_s, self._hopR.shape[0], _ptr(self._hopR), _ptr(self._hopt),
+                        _ptr(self._V0), self._ffR.shape[0], _ptr(self._ffR), spec.Lq, spec.nc, 0.0)
+        self.E, self.U = self.bands()
+        if mu is not None:
+            self.mu = float(mu)
+        elif spec.filling > 0:
+            self.mu = self.find_mu(spec.filling, spec.T_mu)
+        else:
+            self.mu = float(spec.mu)
+        self.m.mu = self.mu
+        dl = np.zeros((4096, 2), np.int32)
+        nd = lib().or_delta_list(C.byref(self.m), _ptr(dl))
+        self.deltas = dl[:nd].copy()
+
+    @property
+    def nd(self) -> int:
+        return int(self.deltas.shape[0])
+
+    def bands(self):
+        s = self.spec
+        E = np.zeros((s.Nk, s.n_s))
+        U = np.zeros((s.Nk, s.n_s, s.n_s), np.complex128)
+        lib().or_bands(C.byref(self.m), _ptr(E), _ptr(U))
+        return E, U
+
+    def density(self, mu: float, T: float) -> float:
+        return lib().or_density(C.byref(self.m), _ptr(self.E), mu, T)
+
+    def find_mu(self, filling: float, T: float) -> float:
+        return lib().or_find_mu(C.byref(self.m), _ptr(self.E), filling, T)
+
+    def loops(self, T: float, which: int, kind: int = 0) -> np.ndarray:
+        """Compact loops [Nq][nd][ns^2][ns^2]; which 0 = P (L^-), 1 = C (L^+); kind 1 = bubble F."""
+        s = self.spec
+        out = np.zeros((s.Nq, self.nd, s.n_s ** 2, s.n_s ** 2), np.complex128)
+        lib().or_loops(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, which, kind, _ptr(out))
+        return out
+
+    def project(self, state: np.ndarray, chmask: int = 3):
+        s = self.spec
+        state = np.ascontiguousarray(state, np.complex128)
+        A = np.zeros_like(state)
+        amax = lib().or_project(C.byref(self.m), _ptr(state), chmask, _ptr(A))
+        return A, amax
+
+    def vlv(self, A: np.ndarray, LcP: np.ndarray, LcC: np.ndarray, chmask: int = 3) -> np.ndarray:
+        A = np.ascontiguousarray(A, np.complex128)
+        LcP = np.ascontiguousarray(LcP, np.complex128)
+        LcC = np.ascontiguousarray(LcC, np.complex128)
+        out = np.zeros_like(A)
+        lib().or_vlv(C.byref(self.m), _ptr(A), _ptr(LcP), _ptr(LcC), chmask, _ptr(out))
+        return out
+
+    def rhs(self, T: float, state: np.ndarray, chmask: int = 3, want_A: bool = False):
+        """dX/dT at temperature T; returns (dX, max|A|[, A])."""
+        state = np.ascontiguousarray(state, np.complex128)
+        d = np.zeros_like(state)
+        A = np.zeros_like(state) if want_A else None
+        amax = lib().or_rhs(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, _ptr(state), chmask,
+                            _ptr(d), _ptr(A) if want_A else None)
+        return (d, amax, A) if want_A else (d, amax)
+
+    def flow(self, T0=10.0, T_end=0.02, rtol=1e-6, atol=1e-8, h0=-0.05, stop=50.0, chmask=3,
+             max_steps=100000, fixed_n=0):
+        s = self.spec
+        state = np.zeros((2, s.Nq, s.M, s.M), np.complex128)
+        o = FlowOpts(T0, T_end, rtol, atol, h0, stop, chmask, max_steps, fixed_n)
+        r = FlowResult()
+        st = lib().or_flow(C.byref(self.m), _ptr(self.E), _ptr(self.U), C.byref(o), _ptr(state), C.byref(r))
+        res = {f: getattr(r, f) for f, _ in FlowResult._fields_}
+        res["status"] = st
+        return state, res

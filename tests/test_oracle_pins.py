@@ -1,0 +1,347 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test names the passage of the paper it follows and the class of mistake
+it would catch.  The pins are:
+  * library routines on special cases (numpy eigh, mpmath derivatives);
+  * an independent full-momentum brute-force fRG (oracle/bruteforce.py), exact
+    for the complete form-factor set on a 4x4 torus;
+  * the paper's closed-form particle-particle solution (Sec. 4, Eq. sol_spin);
+  * second-order perturbation theory (the bubble itself, not its derivative);
+  * the q -> 0 compressibility of the single-band particle-hole loop;
+  * hermiticity, SU(2) and bookkeeping invariants.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bruteforce
+from paper_1710_08830_gb300 import inputs
+
+
+# ---------------------------------------------------------------- eigensolver (step 1)
+
+@pytest.mark.parametrize("n", [2, 3, 6])
+def test_eigh_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    for _ in range(20):
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        A = A + A.conj().T
+        E, U = oracle.eigh(A)
+        assert np.allclose(E, np.linalg.eigvalsh(A), atol=1e-13, rtol=0)
+        assert np.abs(A @ U - U * E).max() < 1e-13 * max(1.0, np.abs(A).max())
+        assert np.abs(U.conj().T @ U - np.eye(n)).max() < 1e-13
+
+
+def test_eigh_degenerate_is_identity():
+    """Spin-degenerate bands (no SOC): H = eps * 1 must give U = 1 exactly."""
+    E, U = oracle.eigh(np.eye(2) * -1.3)
+    assert np.array_equal(U, np.eye(2))
+    assert np.array_equal(E, [-1.3, -1.3])
+
+
+def test_bands_match_numpy():
+    spec = inputs.t2g_soc(seed=3, Lq=4, nc=1)
+    o = oracle.Oracle(spec, mu=0.0)
+    L = spec.Lf
+    kx, ky = np.divmod(np.arange(spec.Nk), L)
+    H = np.zeros((spec.Nk, 6, 6), complex)
+    for R, t in zip(spec.hop_R, spec.hop_t):
+        H += np.exp(2j * np.pi * (kx * R[0] + ky * R[1]) / L)[:, None, None] * t
+    assert np.allclose(o.E, np.linalg.eigvalsh(H), atol=1e-12)
+    res = np.einsum("kij,kjl->kil", H, o.U) - o.U * o.E[:, None, :]
+    assert np.abs(res).max() < 1e-12
+
+
+# ---------------------------------------------------------------- Fermi weights (Eqs. disc_2a/2b)
+
+mp = pytest.importorskip("mpmath")
+
+
+def _mp_f(e, T):
+    return 1 / (mp.exp(e / T) + 1)
+
+
+@pytest.mark.parametrize("e,T", [(-0.3, 0.1), (0.05, 0.1), (0.2, 0.1), (1.0, 0.1), (0.01, 0.02), (-3.0, 0.05)])
+def test_fermi_derivatives_vs_mpmath(e, T):
+    mp.mp.dps = 40
+    f, g, gp = oracle.fermi(e, T)
+    ef, Tf = mp.mpf(e), mp.mpf(T)
+    assert abs(f - float(_mp_f(ef, Tf))) < 1e-15
+    g_ref = float(mp.diff(lambda t: _mp_f(ef, t), Tf))
+    gp_ref = float(mp.diff(lambda x: mp.diff(lambda t: _mp_f(x, t), Tf), ef))
+    assert abs(g - g_ref) <= 1e-12 * max(1.0, abs(g_ref))
+    assert abs(gp - gp_ref) <= 1e-11 * max(1.0, abs(gp_ref))
+
+
+@pytest.mark.parametrize("e1,e2,T", [(0.3, -0.1, 0.1), (0.05, 0.05 + 3e-7, 0.1), (0.05, 0.05 + 2e-6, 0.1),
+                                     (-0.2, 0.2 + 1e-9, 0.05), (0.12, -0.12 + 4e-6, 0.05), (1.5, 1.5, 0.3)])
+def test_pair_weights_vs_mpmath(e1, e2, T):
+    """dF^-/dT and dF^+/dT, including the degenerate switch, against 40-digit arithmetic."""
+    mp.mp.dps = 40
+    a, b, t = mp.mpf(e1), mp.mpf(e2), mp.mpf(T)
+
+    def Fm(tt):
+        return (1 - _mp_f(a, tt) - _mp_f(b, tt)) / (a + b) if a + b != 0 else -mp.diff(lambda x: _mp_f(x, tt), a)
+
+    def Fp(tt):
+        return (_mp_f(a, tt) - _mp_f(b, tt)) / (a - b) if a != b else mp.diff(lambda x: _mp_f(x, tt), a)
+
+    wm_ref = float(mp.diff(Fm, t))
+    wp_ref = float(mp.diff(Fp, t))
+    assert abs(oracle.wm(e1, e2, T) - wm_ref) <= 1e-9 * abs(wm_ref) + 1e-12
+    assert abs(oracle.wp(e1, e2, T) - wp_ref) <= 1e-9 * abs(wp_ref) + 1e-12
+    assert abs(oracle.Fm(e1, e2, T) - float(Fm(t))) <= 1e-10 * abs(float(Fm(t))) + 1e-13
+    assert abs(oracle.Fp(e1, e2, T) - float(Fp(t))) <= 1e-10 * abs(float(Fp(t))) + 1e-13
+
+
+# ---------------------------------------------------------------- bookkeeping (Sec. 2)
+
+@pytest.mark.parametrize("nff,nd", [(5, 13), (9, 25), (13, 41)])
+def test_delta_list_counts(nff, nd):
+    spec = inputs.rashba_hubbard(Lq=16, nc=1, n_ff=nff)
+    o = oracle.Oracle(spec)
+    ff = spec.ff_R
+    ref = sorted({(int(a[0] - b[0]), int(a[1] - b[1])) for a in ff for b in ff})
+    assert o.nd == nd
+    assert [tuple(d) for d in o.deltas] == ref
+
+
+@pytest.mark.parametrize("L,nff", [(8, 5), (24, 9), (16, 13)])
+def test_form_factor_orthonormality(L, nff):
+    """(1/N) sum_k f_R(k) f*_R'(k) = delta_RR' on the meshes used (Sec. 2)."""
+    ff = inputs.ff_set(nff)
+    kx, ky = np.divmod(np.arange(L * L), L)
+    f = np.exp(-2j * np.pi * (np.outer(kx, ff[:, 0]) + np.outer(ky, ff[:, 1])) / L)
+    G = f.T @ f.conj() / (L * L)
+    assert np.abs(G - np.eye(nff)).max() < 1e-13
+
+
+def test_mu_bisection_hits_filling():
+    spec = inputs.hubbard_square(Lq=4, nc=4, filling=0.9, T_mu=0.05)
+    o = oracle.Oracle(spec)
+    assert abs(o.density(o.mu, 0.05) - 0.9) < 1e-13
+
+
+# ---------------------------------------------------------------- brute-force exactness (Secs. 3.1-3.3)
+
+def _complete_spec(model="rashba"):
+    if model == "rashba":
+        spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.4, U=2.0, mu=-0.7, Lq=4, nc=1)
+    else:
+        spec = inputs.hubbard_square(tp=-0.25, U=2.0, Lq=4, nc=1, filling=0.0, mu=-0.5)
+    return spec.with_(ff_R=inputs.ff_complete(4))
+
+
+@pytest.mark.parametrize("model,T", [("rashba", 0.5), ("rashba", 0.07), ("hubbard", 0.2)])
+def test_rhs_equals_full_momentum_rge(model, T):
+    """Complete form factors on a 4x4 torus: the channel-decomposed RHS (loops, all four
+    projection formulas, V.L.V with c_P = 1, c_C = 2) equals the projections of the
+    unprojected one-loop terms Phi^pp and Phi^{ph,c} (Eqs. eq_phipp, eq_phiphd)."""
+    spec = _complete_spec(model)
+    o = oracle.Oracle(spec)
+    bf = bruteforce.Torus(spec, o.mu)
+    P, C, _, _ = bf.random_consistent_state(np.random.default_rng(7))
+    V = bf.vertex_from_channels(spec.V0, P, C)
+    dP, dC = bf.channel_rhs(V, T)
+    d, _ = o.rhs(T, np.stack([P, C]), 3)
+    scale = max(np.abs(dP).max(), np.abs(dC).max())
+    assert np.abs(d[0] - dP).max() < 1e-12 * scale
+    assert np.abs(d[1] - dC).max() < 1e-12 * scale
+
+
+def test_flow_equals_full_momentum_flow():
+    """Same exactness for a whole flow: fixed-step RK4 of the full vertex vs the
+    (P, C) flow, compared on the reconstructed vertex V0 + V^P + V^C + V^D."""
+    spec = _complete_spec("rashba")
+    o = oracle.Oracle(spec)
+    bf = bruteforce.Torus(spec, o.mu)
+    state, res = o.flow(T0=2.0, T_end=0.5, chmask=3, fixed_n=3)
+    V_tu = bf.vertex_from_channels(spec.V0, state[0], state[1])
+    V_bf = bf.flow_rk4(spec.V0, 2.0, 0.5, 3)
+    assert np.abs(V_tu - V_bf).max() < 1e-12 * np.abs(V_bf).max()
+    assert np.abs(V_bf - spec.V0[None, None, None]).max() > 1e-2   # the flow did something
+
+
+@pytest.mark.parametrize("nff", [5, 9])
+def test_truncated_projections_vs_double_k_sums(nff):
+    """Eq. proj_PD and the D->P, P->C, D->C gathers against the defining double
+    k-sums (Eq. def_P and analogues) for exchange propagators supported on a
+    truncated bond set (8x8 coarse mesh)."""
+    spec = inputs.rashba_hubbard(Lq=8, nc=1, n_ff=nff, mu=-0.8)
+    o = oracle.Oracle(spec)
+    bf = bruteforce.Torus(spec, o.mu)
+    st = inputs.random_state(spec, seed=11, hermitian=False)
+    A, _ = o.project(st, 3)
+    V0 = spec.V0
+    zero = np.zeros_like(st[0])
+    # P-channel: A_P - P = P^[V0] + P^[V^C + V^D]
+    VCD = bf.vertex_from_channels(V0, zero, st[1], which="C") + bf.vertex_from_channels(V0, zero, st[1], which="CD")
+    ref_P = bf.project_P(VCD + V0[None, None, None])
+    assert np.abs(A[0] - st[0] - ref_P).max() < 1e-12
+    # C-channel: A_C - C = C^[V0] + C^[V^P] + C^[V^D]
+    VP = bf.vertex_from_channels(V0, st[0], zero, which="P")
+    VD = bf.vertex_from_channels(V0, zero, st[1], which="CD")
+    ref_C = bf.project_C(VP + VD + V0[None, None, None])
+    assert np.abs(A[1] - st[1] - ref_C).max() < 1e-12
+
+
+# ---------------------------------------------------------------- closed forms (Sec. 4)
+
+def _pair_structure(ns):
+    A = np.zeros((ns,) * 4)
+    for a in range(ns):
+        for b in range(ns):
+            for c in range(ns):
+                for d in range(ns):
+                    A[a, b, c, d] = (a == c) * (b == d) - (a == d) * (b == c)
+    return A
+
+
+@pytest.mark.parametrize("alpha,tp", [(0.3, -0.2), (0.0, -0.25)])
+def test_particle_particle_closed_form(alpha, tp):
+    """Eq. sol_spin: two-band TRS model, onsite U, P-only flow.  P stays local,
+    P = -(g+U)/2 (d13 d24 - d14 d23) with g = -U/(1 + U [B(T) - B(T0)]), B from the
+    bubble F^- itself (not its T-derivative), so the integrator is pinned too."""
+    U = 2.5
+    spec = inputs.rashba_hubbard(tp=tp, alpha=alpha, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5)
+    o = oracle.Oracle(spec)
+    T0, T1 = 10.0, 0.3
+    state, res = o.flow(T0=T0, T_end=T1, rtol=1e-10, atol=1e-12, chmask=1, stop=1e9)
+    assert res["T_last"] == pytest.approx(T1)
+    ns = 2
+    d0 = [i for i, (x, y) in enumerate(o.deltas) if x == 0 and y == 0][0]
+
+    def Bbar(T):
+        L = o.loops(T, 0, kind=1)[:, d0].reshape(spec.Nq, ns, ns, ns, ns)   # [s][t2][t1][t4][t3]
+        B = np.zeros(spec.Nq, complex)
+        for t1 in range(ns):
+            for t2 in range(ns):
+                B += 0.5 * (L[:, t2, t1, t2, t1] - L[:, t2, t1, t1, t2])
+        return B
+
+    g = -U / (1 + U * (Bbar(T1) - Bbar(T0)))
+    A = _pair_structure(ns)
+    expect = np.zeros((spec.Nq, spec.M, spec.M), complex)
+    for s1 in range(ns):
+        for s2 in range(ns):
+            for s3 in range(ns):
+                for s4 in range(ns):
+                    expect[:, s1 * ns + s2, s4 * ns + s3] = -0.5 * (g + U) * A[s1, s2, s3, s4]
+    assert np.abs(state[0] - expect).max() < 1e-9
+    assert np.abs(state[1]).max() == 0.0
+
+
+def test_second_order_perturbation_theory():
+    """At O(U^2): P(T) = V0 [B^-(T) - B^-(T0)] V0 and C(T) = 2 V0 [B^+(T) - B^+(T0)] V0 with
+    the bubble matrices built from F^-, F^+ directly; the remainder is O(U^3)."""
+    base = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, mu=-0.8, Lq=4, nc=2, n_ff=5)
+    T0, T1 = 10.0, 0.4
+    res = []
+    for U in (0.2, 0.1):
+        spec = base.with_(V0=inputs.onsite_hubbard_vertex(U))
+        o = oracle.Oracle(spec)
+        st, _ = o.flow(T0=T0, T_end=T1, rtol=1e-11, atol=1e-14, chmask=3, stop=1e9)
+        ns, nff, M = spec.n_s, spec.n_ff, spec.M
+        d_of = {tuple(d): i for i, d in enumerate(o.deltas)}
+        V0P = np.zeros((M, M), complex)
+        V0C = np.zeros((M, M), complex)
+        for a in range(ns):
+            for b in range(ns):
+                for c in range(ns):
+                    for d in range(ns):
+                        V0P[a * ns + b, d * ns + c] = spec.V0[a, b, c, d]
+                        V0C[a * ns + c, d * ns + b] = spec.V0[a, b, c, d]
+
+        def expand(Lc):
+            out = np.zeros((spec.Nq, M, M), complex)
+            for i1 in range(nff):
+                for i2 in range(nff):
+                    di = d_of[tuple(spec.ff_R[i1] - spec.ff_R[i2])]
+                    out[:, i1 * ns * ns:(i1 + 1) * ns * ns, i2 * ns * ns:(i2 + 1) * ns * ns] = Lc[:, di]
+            return out
+
+        BP = expand(o.loops(T1, 0, 1) - o.loops(T0, 0, 1))
+        BC = expand(o.loops(T1, 1, 1) - o.loops(T0, 1, 1))
+        P2 = V0P @ BP @ V0P
+        C2 = 2 * V0C @ BC @ V0C
+        res.append((np.abs(st[0] - P2).max(), np.abs(st[1] - C2).max(), np.abs(P2).max()))
+    (p1, c1, s1), (p2, c2, s2) = res
+    assert s1 / s2 == pytest.approx(4.0, rel=1e-6)        # the O(U^2) part itself
+    assert 6.0 < p1 / p2 < 10.0 and 6.0 < c1 / c2 < 10.0  # the remainder is cubic
+    assert p1 < 0.05 * s1
+
+
+def test_compressibility_limit():
+    """Single band: [L^+_{up up up up}(u=0)]_{R1=R2} = (1/Nk) sum_k d/dT F^+(e,e) = -d/dT d/dmu n_up(mu,T);
+    pins the degenerate branch of the particle-hole weight."""
+    spec = inputs.hubbard_square(tp=-0.25, Lq=4, nc=8, filling=0.0, mu=-0.6)
+    o = oracle.Oracle(spec)
+    T = 0.15
+    Lc = o.loops(T, 1)
+    d0 = [i for i, (x, y) in enumerate(o.deltas) if x == 0 and y == 0][0]
+    lhs = Lc[0, d0, 0, 0].real
+    L = spec.Lf
+    kx, ky = np.divmod(np.arange(spec.Nk), L)
+    kx, ky = 2 * np.pi * kx / L, 2 * np.pi * ky / L
+    eps = -2 * (np.cos(kx) + np.cos(ky)) + 1.0 * np.cos(kx) * np.cos(ky)   # t=1, t'=-0.25
+
+    def n(mu, T):
+        return np.mean(1.0 / (np.exp((eps - mu) / T) + 1.0))
+
+    h = 2e-3
+    w = [1, -8, 8, -1]
+    off = [-2, -1, 1, 2]
+    dd = 0.0
+    for wi, oi in zip(w, off):
+        for wj, oj in zip(w, off):
+            dd += wi * wj * n(-0.6 + oi * h, T + oj * h)
+    dd /= (12 * h) ** 2
+    assert lhs == pytest.approx(-dd, rel=1e-6)
+    assert abs(Lc[0, d0, 0, 0].imag) < 1e-14
+
+
+# ---------------------------------------------------------------- symmetries
+
+def _expand_all(spec, o, Lc):
+    ns2 = spec.n_s ** 2
+    d_of = {tuple(d): i for i, d in enumerate(o.deltas)}
+    out = np.zeros((spec.Nq, spec.M, spec.M), complex)
+    for i1 in range(spec.n_ff):
+        for i2 in range(spec.n_ff):
+            out[:, i1 * ns2:(i1 + 1) * ns2, i2 * ns2:(i2 + 1) * ns2] = Lc[:, d_of[tuple(spec.ff_R[i1] - spec.ff_R[i2])]]
+    return out
+
+
+def test_hermiticity_of_loops_and_flow():
+    """Sec. 2 (hermiticity of the projections): loop matrices, A and the flowing P, C are Hermitian."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=4, nc=2, n_ff=9)
+    o = oracle.Oracle(spec)
+    for which in (0, 1):
+        Lm = _expand_all(spec, o, o.loops(0.2, which))
+        assert np.abs(Lm - np.conj(np.swapaxes(Lm, 1, 2))).max() < 1e-14 * np.abs(Lm).max()
+    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
+    A, _ = o.project(st, 3)
+    for X in (st[0], st[1], A[0], A[1]):
+        assert np.abs(X - np.conj(np.swapaxes(X, 1, 2))).max() < 1e-12 * np.abs(X).max()
+
+
+def test_su2_relations_without_soc():
+    """Zero SOC: X_{uuuu} = X_{udud} + X_{uddu}, spin conservation and up/down symmetry."""
+    spec = inputs.hubbard_square(tp=-0.25, U=3.0, Lq=4, nc=2, filling=0.0, mu=-0.7)
+    o = oracle.Oracle(spec)
+    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
+    nff = spec.n_ff
+    P = st[0].reshape(spec.Nq, nff, 2, 2, nff, 2, 2)   # [q][R][s1][s2][R'][s4][s3]
+    C = st[1].reshape(spec.Nq, nff, 2, 2, nff, 2, 2)   # [q][R][s1][s3][R'][s4][s2]
+    Pt = lambda a, b, c, d: P[:, :, a, b, :, d, c]
+    Ct = lambda a, b, c, d: C[:, :, a, c, :, d, b]
+    for X in (Pt, Ct):
+        assert np.abs(X(0, 0, 0, 0) - X(0, 1, 0, 1) - X(0, 1, 1, 0)).max() < 1e-12
+        assert np.abs(X(0, 0, 0, 0) - X(1, 1, 1, 1)).max() < 1e-12
+        for a in range(2):
+            for b in range(2):
+                for c in range(2):
+                    for d in range(2):
+                        if a + b != c + d:
+                            assert np.abs(X(a, b, c, d)).max() < 1e-13
+    assert np.abs(Pt(0, 1, 0, 1)).max() > 1e-3 and np.abs(Ct(0, 1, 0, 1)).max() > 1e-3
