@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: TU-fRG right-hand-side evaluations per second on the 24x24 / 8x8-per-cell
+Rashba-Hubbard workload (N_s = 2, N_ff = 9, M = 36), split precision, plus the plain
+FP64 GPU path, time-to-Lambda_c of both, the end-to-end host-buffer rate, the loop
+kernel's roofline and the CPU oracle as a reported baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-flow]
+
+One step = one full right-hand side (Fermi tables, P and C loop k-sums, Fourier
+transform, projections, V.L.V) at T = 0.1 on a mid-flow state.  Inputs are resident
+in HBM; the L2 is flushed (a 256 MB write) between timed steps.  N > 1 runs one
+independent model instance per rank (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rashba_hubbard_q24x24_k8x8_ff9"
+METRIC = "TU-fRG RHS evals/s (split precision, <=1e-4 vertex err) on Rashba-Hubbard 24x24 q / 8x8 k per cell"
+T_BENCH = 0.1
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = sorted(sm)
+        med = load[len(load) // 2]
+        return {"sm_mhz": med, "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def loop_traffic_record():
+    """DRAM bytes per loop-kernel launch from the committed ncu summary, if it matches the current source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "loops_traffic.json")
+    src = os.path.join(ROOT, "paper_1710_08830_gb300", "csrc", "k_loops.cu")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("k_loops_sha256_16") != h:
+        return None, rec
+    return rec, rec
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on bounded samples of the same workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_1710_08830_gb300 import inputs
+    spec = inputs.rashba_q24_k8_ff9(0)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=1, scale=0.2)
+    rng = np.random.default_rng(0)
+    # size a step so that W + K steps take about two minutes in total
+    probe = [int(x) for x in rng.choice(spec.Nq, 4, replace=False)]
+    t = time.perf_counter()
+    o.rhs_at(T_BENCH, st, probe, 3)
+    per_q = (time.perf_counter() - t) / 4
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    b = int(max(1, min(spec.Nq, budget / per_q)))
+    units = 0.0
+    for i in range(args.warmup):
+        o.rhs_at(T_BENCH, st, [int(x) for x in rng.choice(spec.Nq, b, replace=False)], 3)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        o.rhs_at(T_BENCH, st, [int(x) for x in rng.choice(spec.Nq, b, replace=False)], 3)
+        units += b / spec.Nq
+    dt = time.perf_counter() - t
+    value = units / dt
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "Nq": spec.Nq, "Nk": spec.Nk, "M": spec.M, "T": T_BENCH,
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: the right-hand side restricted to {b} of {spec.Nq} random transfer "
+                                   f"momenta (loops, Fourier transform, projections, V.L.V); counted as {b}/{spec.Nq} RHS"},
+        "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-flow", action="store_true", help="skip the time-to-Lambda_c measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300 import inputs
+    from paper_1710_08830_gb300.api import FP64, SPLIT32, Model
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    spec = inputs.rashba_q24_k8_ff9(seed=rank)     # one independent instance per rank
+    stream = torch.cuda.current_stream()
+    m32 = Model(spec, SPLIT32, stream=stream)
+    m64 = Model(spec, FP64, stream=stream)
+    # a mid-flow state: the split flow from T0 = 10 down to the benchmark temperature
+    state, _ = m32.flow(T_end=T_BENCH, stop=1e9)
+    out = torch.empty_like(state)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.warmup):
+        m32.rhs(T_BENCH, state, out=out)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K split-precision right-hand sides
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    m32.timing_begin()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        m32.rhs(T_BENCH, state, out=out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    phase_ms, launches, loop_launches = m32.timing_end()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms_max = allmax(dev_ms)
+    value = world * args.steps / (dev_ms_max * 1e-3)
+    ms_per_step = dev_ms_max / args.steps
+
+    # ---------------- accuracy of the split path against the FP64 GPU path (same state)
+    d32 = m32.rhs(T_BENCH, state).cpu().numpy()
+    d64 = m64.rhs(T_BENCH, state).cpu().numpy()
+    err_split = float(np.abs(d32 - d64).max() / np.abs(d64).max())
+
+    # ---------------- plain FP64 GPU right-hand sides
+    k64 = max(3, min(args.steps, 30))
+    for _ in range(2):
+        m64.rhs(T_BENCH, state, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k64):
+        m64.rhs(T_BENCH, state, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = k64 / (e0.elapsed_time(e1) * 1e-3)
+
+    # ---------------- end to end through the C ABI with host buffers (pinned)
+    hs = state.cpu().pin_memory()
+    ho = torch.empty_like(hs).pin_memory()
+    for _ in range(3):
+        m32.rhs_host(T_BENCH, hs, ho)
+    ke = max(3, min(args.steps, 100))
+    t = time.perf_counter()
+    for _ in range(ke):
+        m32.rhs_host(T_BENCH, hs, ho)
+    e2e_rate = ke / (time.perf_counter() - t)
+    e2e_rate = world * ke / (allmax(ke / e2e_rate))
+    state_bytes = int(hs.numel() * hs.element_size())
+
+    # ---------------- time-to-Lambda_c (full flows from T0 = 10)
+    flows = None
+    if not args.no_flow:
+        _, r32 = m32.flow()
+        _, r64 = m64.flow()
+        flows = {"split": {"wall_s": r32["wall_s"], "Tc": r32["Tc"], "crossed": r32["crossed"],
+                           "n_rhs": r32["n_rhs"], "n_steps": r32["n_steps"], "lead_channel": "PC"[r32["lead_channel"]],
+                           "amax": r32["amax"]},
+                 "fp64": {"wall_s": r64["wall_s"], "Tc": r64["Tc"], "crossed": r64["crossed"],
+                          "n_rhs": r64["n_rhs"], "n_steps": r64["n_steps"], "lead_channel": "PC"[r64["lead_channel"]],
+                          "amax": r64["amax"]},
+                 "note": "Tc is the crossing of max|A| = 50 when crossed == 1, else the end temperature 0.02"}
+    clocks = sampler.stop()
+
+    # ---------------- roofline of the dominant kernel (the loop k-sum)
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    ns = spec.n_s
+    ndy_half = int(sum(1 for d in np.unique(spec.ff_R[:, 1][:, None] - spec.ff_R[:, 1][None, :]) if d >= 0))
+    unit_cfma = ns ** 4 + ns ** 5 + ndy_half * ns ** 4
+    flops_per_launch = 8.0 * spec.Nq * spec.Nk * unit_cfma
+    loop_ms_avg = phase_ms["loops"] / max(1, loop_launches)
+    achieved = flops_per_launch / (loop_ms_avg * 1e-3) / 1e12
+    trec, _ = loop_traffic_record()
+    roofline = {"bound": "alu", "kernel": "loops_ns2_kernel<float> (split-precision loop k-sum)",
+                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": (trec["dram_bytes_per_launch"] if trec else None),
+                "peak_source": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
+                "algorithmic_flops_per_launch": flops_per_launch,
+                "unit_work": f"(N_s^4 + N_s^5 + {ndy_half} N_s^4) = {unit_cfma} complex FMA per (q, k) pair",
+                "avg_launch_ms": loop_ms_avg}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        o = oracle.Oracle(spec)
+        st_np = state.cpu().numpy()
+        o.rhs(T_BENCH, st_np, 3)   # warm
+        t = time.perf_counter()
+        n_cpu = 2
+        for _ in range(n_cpu):
+            o.rhs(T_BENCH, st_np, 3)
+        cpu_rate = n_cpu / (time.perf_counter() - t)
+        cpu = {"value": cpu_rate, "unit": "RHS/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{n_cpu} full right-hand sides of the same workload (after one warm-up)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "Lq": spec.Lq, "nc": spec.nc, "Nq": spec.Nq, "Nk": spec.Nk,
+                       "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH, "precision": "split (FP32 loop sums, FP64 state)",
+                       "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},
+            "split_vs_fp64_maxrel": err_split,
+            "fp64_gpu": {"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate},
+            "time_to_lambda_c": flows,
+            "phase_ms_per_rhs": {k: v / args.steps for k, v in phase_ms.items()},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_rate, "unit": "RHS/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "peaks_source": peak_src,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

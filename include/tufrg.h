@@ -1,0 +1,180 @@
+/*
+ * tufrg.h -- C ABI of the GB300 (sm_103a) truncated-unity fRG right-hand side.
+ *
+ * Method: Schober, Ehrlich, Reckling, Honerkamp, "Truncated-unity functional
+ * renormalization group for multiband systems with spin-orbit coupling".
+ * The library evaluates the channel-decomposed flow of the exchange
+ * propagators P(s) and C(u) in the orbital (spin) basis:
+ *
+ *   dP/dT(s) = A_P(s) L^-(s) A_P(s)        (Sec. 4.2, Eq. RGE_spin)
+ *   dC/dT(u) = 2 A_C(u) L^+(u) A_C(u)      (orbital form of Sec. 3.1, Eq. rge_Dmat)
+ *
+ * with A_X the projected vertex of Sec. 3.3 (Eq. sum_P and the four gathers
+ * Eq. proj_PD ... Eq. proj_DC) and L^- / L^+ the loop matrices of Eqs.
+ * loopminus / loopplus dressed into the orbital basis (Eq. loop_orbital).
+ * The flow parameter is the temperature: Lambda = T, the regulator chi = 1,
+ * so the single-scale loops of Eq. def_lmp are d/dT of the bubbles F^-/F^+
+ * (Eqs. disc_2a, disc_2b).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) doubles (C99 double complex).
+ * - Square lattice; Bloch Hamiltonian H(k)[t][t'] = sum_R t_R[t][t'] e^{i k.R}.
+ * - Coarse (transfer) mesh Lq x Lq, index q = qx*Lq + qy, q = 2 pi (qx,qy)/Lq.
+ *   Fine (loop) mesh Lf = Lq*nc, index k = kx*Lf + ky.
+ * - Bonds (form factors f_R(k) = e^{-i k.R}, Sec. 2): n_ff vectors, ff_R[0] = (0,0),
+ *   pairwise distinct modulo Lq.  M = n_ff * n_s^2.
+ * - State / derivative / projected vertex: X[2][Nq][M][M], channel 0 = P,
+ *   channel 1 = C, row-major M x M per transfer momentum:
+ *     P row (R,(s1,s2)), column (R',(s4,s3)) holds P^{RR'}_{s1 s2 s3 s4}(s)
+ *     C row (R,(s1,s3)), column (R',(s4,s2)) holds C^{RR'}_{s1 s2 s3 s4}(u)
+ *   where (a,b) = a*n_s + b and the R index is the position in ff_R.  In these
+ *   layouts the flow equations above are plain matrix products and
+ *   hermiticity (Sec. 2, item 3) is matrix hermiticity.
+ * - Compact loops: Lc[Nq][n_delta][n_s^2][n_s^2], delta indexing the sorted
+ *   (by dx, then dy) list of distinct bond differences R1 - R2 (tufrg_deltas),
+ *     P: Lc[q][d][(t2,t1)][(t4,t3)] = [L^-_{t1t2t3t4}(q)]_{R1R2}, R1-R2 = delta_d
+ *     C: Lc[q][d][(t1,t2)][(t3,t4)] = [L^+_{t1t2t3t4}(q)]_{R1R2}
+ *   so the M x M loop matrix is L[(R1,a),(R2,b)] = Lc[q][d(R1-R2)][a][b].
+ * - Every call is stream-ordered on the stream given to tufrg_init_model and
+ *   returns a status; no call throws, aborts or exits.  On error the outputs
+ *   are unspecified and tufrg_last_error() describes the cause.
+ * - Device pointers (prefix d_) must be device memory of the current device
+ *   with the documented size, owned by the caller; host pointers (h_) are
+ *   host memory owned by the caller.  Descriptors are copied at init.
+ */
+#ifndef TUFRG_H
+#define TUFRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TUFRG_OK = 0,
+    TUFRG_EINVAL = 1,      /* invalid argument or descriptor */
+    TUFRG_ENOMEM = 2,      /* device or host allocation failed */
+    TUFRG_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    TUFRG_ENONFINITE = 4,  /* a right-hand side or error norm was not finite */
+    TUFRG_ENOTCONV = 5,    /* step size underflow or step limit in the flow */
+    TUFRG_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    TUFRG_EFALLBACK = 7,   /* surrogate rejected, direct loops used (informational) */
+    TUFRG_ENOTSUP = 8      /* configuration not supported by this build */
+} tufrg_status;
+
+enum { TUFRG_FP64 = 0, TUFRG_SPLIT32 = 1 };
+enum { TUFRG_CH_P = 1, TUFRG_CH_C = 2 };
+
+typedef struct tufrg_model tufrg_model;   /* opaque; owns all of its device memory */
+
+/* Model descriptor (host memory, copied by tufrg_init_model). */
+typedef struct {
+    int n_s;               /* spin-orbitals N_s (1..8) */
+    int n_hop;             /* number of hopping matrices */
+    const int *hop_R;      /* [n_hop][2] lattice vectors R */
+    const double *hop_t;   /* [n_hop][n_s][n_s] complex t_R; H(k) must be Hermitian */
+    double mu;             /* chemical potential, used when filling <= 0 */
+    double filling;        /* > 0: electrons per site; mu is bisected at T_mu and held fixed */
+    double T_mu;           /* temperature of the mu bisection */
+    const double *V0;      /* [n_s]^4 complex onsite antisymmetric initial vertex V0[s1][s2][s3][s4] */
+    int n_ff;              /* bonds (form factors) */
+    const int *ff_R;       /* [n_ff][2], ff_R[0] must be (0,0), distinct modulo Lq */
+    int Lq;                /* coarse transfer mesh Lq x Lq (>= 2) */
+    int nc;                /* fine points per coarse cell per direction (>= 1) */
+    int precision;         /* TUFRG_FP64 or TUFRG_SPLIT32 (FP32 loop sums, FP32/TF32 products) */
+} tufrg_model_desc;
+
+/* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
+typedef struct {
+    double T0, T_end;      /* start and end temperature, T0 > T_end > 0 */
+    double rtol, atol;     /* error norm max_i |err_i| / (atol + rtol max(|y_i|, |y'_i|)) <= 1 */
+    double h0;             /* first step in ln T (negative) */
+    double stop;           /* stop when max |A_X(q)| over channels, q, entries exceeds this */
+    int channel_mask;      /* TUFRG_CH_P | TUFRG_CH_C */
+    int max_steps;         /* accepted + rejected step limit */
+} tufrg_flow_opts;
+
+typedef struct {
+    double Tc;             /* critical scale (linear interpolation in ln T), or T_last if not crossed */
+    int crossed;           /* 1 if max|A| exceeded opts.stop */
+    int n_steps, n_reject, n_rhs;
+    double amax;           /* max |A| at the last accepted state */
+    double T_last;         /* temperature of the last accepted state */
+    int lead_channel;      /* 0 = P, 1 = C: channel holding max |A| at the last state */
+    int lead_q;            /* transfer momentum index of that maximum */
+    double wall_s;         /* host wall time of the flow call */
+} tufrg_flow_result;
+
+/* Build the model: copies the descriptor, computes the eigensystem of H(k) on
+ * the fine mesh (Sec. 3.1; FP64), bisects mu if requested, builds the bond
+ * and projection gather tables (Sec. 3.3) and allocates all work memory.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: TUFRG_EINVAL (bad descriptor, non-Hermitian H), TUFRG_ENOMEM, TUFRG_ECUDA. */
+tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, tufrg_model **out);
+
+/* Release every resource of the model (NULL is ignored). */
+void tufrg_free(tufrg_model *m);
+
+/* Human-readable description of the last error on this model ("" if none). */
+const char *tufrg_last_error(const tufrg_model *m);
+
+/* Sizes: Nq, M, n_delta (loop bond differences), Nk and the chemical potential in use. */
+tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int *Nk, double *mu);
+
+/* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */
+tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out);
+
+/* Projection gather table of one output channel (0 = P, 1 = C), Sec. 3.3.
+ * Each term is 9 int32: iR, iR', kind, R''x, R''y, i1, i2, phase_x, phase_y, where
+ * kind 0 = P<-C (Eq. proj_PD), 1 = P<-D, 2 = C<-P, 3 = C<-D (Eq. proj_DC);
+ * R'' and the phase vector are reduced modulo Lq into [0, Lq).  The term adds
+ * sign * e^{i q.phase} * X_src(R'')[(i1, pair),(i2, pair')] with sign -1 for the
+ * D kinds.  Writes at most cap terms, returns the total count in *n_terms. */
+tufrg_status tufrg_gather_table(const tufrg_model *m, int channel, int *h_out, int cap, int *n_terms);
+
+/* Eigensystem on the fine mesh: d_E [Nk][n_s] doubles (ascending E, not shifted
+ * by mu), d_U [Nk][n_s][n_s] complex, column l the eigenvector of E_l. */
+tufrg_status tufrg_bands(tufrg_model *m, double *d_E, double *d_U);
+
+/* Compact loops d/dT F at temperature T (Eqs. loopminus, loopplus, loop_orbital,
+ * fine-mesh direct k-sum).  d_loops: [2][Nq][n_delta][n_s^2][n_s^2] complex; the
+ * channels not in channel_mask are left untouched. */
+tufrg_status tufrg_loops(tufrg_model *m, double T, int channel_mask, void *d_loops);
+
+/* Projected vertices A_P(s), A_C(u) of a state (Eq. sum_P, Eq. proj_PD, the
+ * D->P gather, the P->C gather, Eq. proj_DC).  d_state, d_Ahat: [2][Nq][M][M]
+ * complex.  A channel outside channel_mask is treated as zero and its A is
+ * zero-filled.  *h_amax (may be NULL) receives max |A| (synchronises). */
+tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask, void *d_Ahat,
+                           double *h_amax);
+
+/* Right-hand side dX/dT of the flow at temperature T (device buffers, no host sync):
+ * loops, Fourier transform to bonds, projections, dP/dT = A L^- A, dC/dT = 2 A L^+ A.
+ * d_state, d_dstate: [2][Nq][M][M] complex; channels outside the mask get zero. */
+tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate);
+
+/* Same right-hand side with host buffers: copies h_state to the device, evaluates,
+ * copies dX/dT back into h_dstate and synchronises the stream. */
+tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate);
+
+/* Adaptive flow from X(T0) = 0 (Eqs. def_VP... at Lambda_0) down to T_end or to
+ * max|A| > opts->stop.  d_state_out (may be NULL): [2][Nq][M][M] complex, the
+ * last accepted state.  Errors: TUFRG_ENONFINITE, TUFRG_ENOTCONV, ... */
+tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_state_out, tufrg_flow_result *res);
+
+/* Optional CUDA-event timing on the model's stream (used by the benchmark).
+ * tufrg_timing_begin resets the counters and starts recording; every later
+ * kernel phase is bracketed by two events.  tufrg_timing_end synchronises the
+ * stream, stops recording and returns:
+ *   h_ms[i], i < n_ms: summed device milliseconds per phase, in the order
+ *     0 Fermi tables, 1 loop k-sum kernels, 2 loop partial reduction,
+ *     3 Fourier transform, 4 projections, 5 V.L.V products, 6 Runge-Kutta kernels;
+ *   *h_launches: kernels this library launched while recording;
+ *   *h_loop_launches: launches of the loop k-sum kernel (phase 1) alone. */
+tufrg_status tufrg_timing_begin(tufrg_model *m);
+tufrg_status tufrg_timing_end(tufrg_model *m, double *h_ms, int n_ms, long long *h_launches, long long *h_loop_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUFRG_H */

@@ -73,11 +73,13 @@ def lib():
             L.or_delta_list.argtypes = [vp, vp]
             L.or_delta_list.restype = i
             L.or_loops.argtypes = [vp, vp, vp, d, i, i, vp]
+            L.or_loops_at.argtypes = [vp, vp, vp, d, i, i, i, vp, vp]
             L.or_project.argtypes = [vp, vp, i, vp]
             L.or_project.restype = d
             L.or_vlv.argtypes = [vp, vp, vp, vp, i, vp]
             L.or_rhs.argtypes = [vp, vp, vp, d, vp, i, vp, vp]
             L.or_rhs.restype = d
+            L.or_rhs_at.argtypes = [vp, vp, vp, d, vp, i, i, vp, vp]
             L.or_flow.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_flow.restype = i
             L.or_num_threads.restype = i
@@ -177,6 +179,15 @@ class Oracle:
         lib().or_loops(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, which, kind, _ptr(out))
         return out
 
+    def loops_at(self, T: float, which: int, s_list, kind: int = 0) -> np.ndarray:
+        """Compact loops for the listed transfer momenta only: [len(s_list)][nd][ns^2][ns^2]."""
+        s = self.spec
+        sl = np.ascontiguousarray(s_list, np.int32)
+        out = np.zeros((sl.shape[0], self.nd, s.n_s ** 2, s.n_s ** 2), np.complex128)
+        lib().or_loops_at(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, which, kind, sl.shape[0], _ptr(sl),
+                          _ptr(out))
+        return out
+
     def project(self, state: np.ndarray, chmask: int = 3):
         s = self.spec
         state = np.ascontiguousarray(state, np.complex128)
@@ -200,6 +211,16 @@ class Oracle:
         amax = lib().or_rhs(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, _ptr(state), chmask,
                             _ptr(d), _ptr(A) if want_A else None)
         return (d, amax, A) if want_A else (d, amax)
+
+    def rhs_at(self, T: float, state: np.ndarray, s_list, chmask: int = 3) -> np.ndarray:
+        """dX/dT restricted to the listed transfer momenta: [2][len(s_list)][M][M]."""
+        s = self.spec
+        state = np.ascontiguousarray(state, np.complex128)
+        sl = np.ascontiguousarray(s_list, np.int32)
+        out = np.zeros((2, sl.shape[0], s.M, s.M), np.complex128)
+        lib().or_rhs_at(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, _ptr(state), chmask, sl.shape[0], _ptr(sl),
+                        _ptr(out))
+        return out
 
     def flow(self, T0=10.0, T_end=0.02, rtol=1e-6, atol=1e-8, h0=-0.05, stop=50.0, chmask=3,
              max_steps=100000, fixed_n=0):

@@ -349,68 +349,104 @@ static int ff_index_mod(const or_model *m, int x, int y)
  * kind = 1: w = F itself (the bubble, used only by the closed-form pins).
  * Output Lc[q][d][a][b] in the matrix pair order given in the file header.
  */
-void or_loops(const or_model *m, const double *E, const double *Uin, double T, int which, int kind,
-              double *Lc_out)
+/* the k-sum for one transfer momentum s (coarse index), accumulated into acc[nd][ns^4] */
+static void loops_one(const or_model *m, const double *E, const cplx *U, double T, int which, int kind, int s,
+                      int nd, const cplx *ph_tab, cplx *acc)
 {
     int ns = m->ns, ns2 = ns * ns, ns4 = ns2 * ns2;
-    int Lq = m->Lq, nc = m->nc, Lf = Lq * nc, Nk = Lf * Lf, Nq = Lq * Lq;
-    int dl[2 * 4096];
-    int nd = or_delta_list(m, dl);
-    const cplx *U = (const cplx *)Uin;
-    cplx *Lc = (cplx *)Lc_out;
-    memset(Lc, 0, sizeof(cplx) * (size_t)Nq * nd * ns4);
-    /* e^{-i q.(R1-R2)} for every fine q and bond difference (depends on q only) */
-    cplx *ph_tab = malloc(sizeof(cplx) * (size_t)Nk * nd);
+    int Lq = m->Lq, nc = m->nc, Lf = Lq * nc, Nk = Lf * Lf;
+    int sx = (s / Lq) * nc, sy = (s % Lq) * nc;   /* transfer momentum on the fine mesh */
+    cplx *Y = malloc(sizeof(cplx) * ns4);
+    double *w = malloc(sizeof(double) * ns2);
+    for (size_t i = 0; i < (size_t)nd * ns4; i++) acc[i] = 0.0;
+    for (int qx = 0; qx < Lf; qx++)
+        for (int qy = 0; qy < Lf; qy++) {
+            int k1, k2;
+            if (which == 0) { k1 = imod(sx - qx, Lf) * Lf + imod(sy - qy, Lf); k2 = qx * Lf + qy; }
+            else            { k1 = qx * Lf + qy; k2 = imod(qx - sx, Lf) * Lf + imod(qy - sy, Lf); }
+            const double *e1 = E + (size_t)k1 * ns, *e2 = E + (size_t)k2 * ns;
+            const cplx *U1 = U + (size_t)k1 * ns2, *U2 = U + (size_t)k2 * ns2;
+            for (int l1 = 0; l1 < ns; l1++)
+                for (int l2 = 0; l2 < ns; l2++) {
+                    double a = e1[l1] - m->mu, b = e2[l2] - m->mu;
+                    if (which == 0) w[l1 * ns + l2] = kind ? or_Fm(a, b, T) : or_wm(a, b, T);
+                    else            w[l1 * ns + l2] = kind ? or_Fp(a, b, T) : or_wp(a, b, T);
+                }
+            /* Y[t1 t2 t3 t4] = sum_{l1 l2} (...) */
+            for (int t1 = 0; t1 < ns; t1++)
+                for (int t2 = 0; t2 < ns; t2++)
+                    for (int t3 = 0; t3 < ns; t3++)
+                        for (int t4 = 0; t4 < ns; t4++) {
+                            cplx y = 0.0;
+                            for (int l1 = 0; l1 < ns; l1++)
+                                for (int l2 = 0; l2 < ns; l2++) {
+                                    cplx left = U1[t1 * ns + l1] * conj(U1[t3 * ns + l1]);
+                                    cplx right = (which == 0) ? U2[t2 * ns + l2] * conj(U2[t4 * ns + l2])
+                                                              : conj(U2[t2 * ns + l2]) * U2[t4 * ns + l2];
+                                    y += left * w[l1 * ns + l2] * right;
+                                }
+                            int a, b;
+                            if (which == 0) { a = t2 * ns + t1; b = t4 * ns + t3; }
+                            else            { a = t1 * ns + t2; b = t3 * ns + t4; }
+                            Y[a * ns2 + b] = y;
+                        }
+            for (int d = 0; d < nd; d++) {
+                cplx ph = ph_tab[((size_t)qx * Lf + qy) * nd + d];
+                cplx *o = acc + (size_t)d * ns4;
+                for (int i = 0; i < ns4; i++) o[i] += ph * Y[i];
+            }
+        }
+    for (size_t i = 0; i < (size_t)nd * ns4; i++) acc[i] /= (double)Nk;
+    free(Y); free(w);
+}
+
+/* e^{-i q.(R1-R2)} for every fine q and bond difference (depends on q only) */
+static cplx *loop_phase_table(const or_model *m, const int *dl, int nd)
+{
+    int Lf = m->Lq * m->nc;
+    cplx *ph_tab = malloc(sizeof(cplx) * (size_t)Lf * Lf * nd);
     for (int qx = 0; qx < Lf; qx++)
         for (int qy = 0; qy < Lf; qy++)
             for (int d = 0; d < nd; d++)
                 ph_tab[((size_t)qx * Lf + qy) * nd + d] = conj(lattice_phase((long)qx * dl[2 * d] + (long)qy * dl[2 * d + 1], Lf));
+    return ph_tab;
+}
+
+/*
+ * which = 0 (particle-particle, s on the coarse mesh):
+ *   [L^-_{t1t2t3t4}(s)]_{R1R2} = (1/Nk) sum_q e^{-iq.(R1-R2)}
+ *        sum_{l1 l2} U_{t1 l1}(s-q) U*_{t3 l1}(s-q) w^-_{l1 l2}(s-q, q) U_{t2 l2}(q) U*_{t4 l2}(q)
+ * which = 1 (crossed particle-hole, u on the coarse mesh):
+ *   [L^+_{t1t2t3t4}(u)]_{R1R2} = (1/Nk) sum_q e^{-iq.(R1-R2)}
+ *        sum_{l1 l2} U_{t1 l1}(q) U*_{t3 l1}(q) w^+_{l1 l2}(q, q-u) U*_{t2 l2}(q-u) U_{t4 l2}(q-u)
+ * kind = 0: w = d/dT F (the flowing loop, Eq. def_lmp with chi = 1 and Lambda = T)
+ * kind = 1: w = F itself (the bubble, used only by the closed-form pins).
+ * Output Lc[q][d][a][b] in the matrix pair order given in the file header.
+ */
+void or_loops(const or_model *m, const double *E, const double *Uin, double T, int which, int kind,
+              double *Lc_out)
+{
+    int ns2 = m->ns * m->ns, ns4 = ns2 * ns2, Nq = m->Lq * m->Lq;
+    int dl[2 * 4096];
+    int nd = or_delta_list(m, dl);
+    cplx *ph_tab = loop_phase_table(m, dl, nd);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int s = 0; s < Nq; s++) {
-        int sx = (s / Lq) * nc, sy = (s % Lq) * nc;   /* transfer momentum on the fine mesh */
-        cplx *Y = malloc(sizeof(cplx) * ns4);
-        double *w = malloc(sizeof(double) * ns2);
-        cplx *acc = Lc + (size_t)s * nd * ns4;
-        for (int qx = 0; qx < Lf; qx++)
-            for (int qy = 0; qy < Lf; qy++) {
-                int k1, k2;
-                if (which == 0) { k1 = imod(sx - qx, Lf) * Lf + imod(sy - qy, Lf); k2 = qx * Lf + qy; }
-                else            { k1 = qx * Lf + qy; k2 = imod(qx - sx, Lf) * Lf + imod(qy - sy, Lf); }
-                const double *e1 = E + (size_t)k1 * ns, *e2 = E + (size_t)k2 * ns;
-                const cplx *U1 = U + (size_t)k1 * ns2, *U2 = U + (size_t)k2 * ns2;
-                for (int l1 = 0; l1 < ns; l1++)
-                    for (int l2 = 0; l2 < ns; l2++) {
-                        double a = e1[l1] - m->mu, b = e2[l2] - m->mu;
-                        if (which == 0) w[l1 * ns + l2] = kind ? or_Fm(a, b, T) : or_wm(a, b, T);
-                        else            w[l1 * ns + l2] = kind ? or_Fp(a, b, T) : or_wp(a, b, T);
-                    }
-                /* Y[t1 t2 t3 t4] = sum_{l1 l2} (...) */
-                for (int t1 = 0; t1 < ns; t1++)
-                    for (int t2 = 0; t2 < ns; t2++)
-                        for (int t3 = 0; t3 < ns; t3++)
-                            for (int t4 = 0; t4 < ns; t4++) {
-                                cplx y = 0.0;
-                                for (int l1 = 0; l1 < ns; l1++)
-                                    for (int l2 = 0; l2 < ns; l2++) {
-                                        cplx left = U1[t1 * ns + l1] * conj(U1[t3 * ns + l1]);
-                                        cplx right = (which == 0) ? U2[t2 * ns + l2] * conj(U2[t4 * ns + l2])
-                                                                  : conj(U2[t2 * ns + l2]) * U2[t4 * ns + l2];
-                                        y += left * w[l1 * ns + l2] * right;
-                                    }
-                                int a, b;
-                                if (which == 0) { a = t2 * ns + t1; b = t4 * ns + t3; }
-                                else            { a = t1 * ns + t2; b = t3 * ns + t4; }
-                                Y[a * ns2 + b] = y;
-                            }
-                for (int d = 0; d < nd; d++) {
-                    cplx ph = ph_tab[((size_t)qx * Lf + qy) * nd + d];
-                    cplx *o = acc + (size_t)d * ns4;
-                    for (int i = 0; i < ns4; i++) o[i] += ph * Y[i];
-                }
-            }
-        for (size_t i = 0; i < (size_t)nd * ns4; i++) acc[i] /= (double)Nk;
-        free(Y); free(w);
-    }
+    for (int s = 0; s < Nq; s++)
+        loops_one(m, E, (const cplx *)Uin, T, which, kind, s, nd, ph_tab, (cplx *)Lc_out + (size_t)s * nd * ns4);
+    free(ph_tab);
+}
+
+/* Same loops for a list of n transfer momenta only: out[n][nd][ns^2][ns^2]. */
+void or_loops_at(const or_model *m, const double *E, const double *Uin, double T, int which, int kind, int n,
+                 const int *s_list, double *out)
+{
+    int ns2 = m->ns * m->ns, ns4 = ns2 * ns2;
+    int dl[2 * 4096];
+    int nd = or_delta_list(m, dl);
+    cplx *ph_tab = loop_phase_table(m, dl, nd);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; i++)
+        loops_one(m, E, (const cplx *)Uin, T, which, kind, s_list[i], nd, ph_tab, (cplx *)out + (size_t)i * nd * ns4);
     free(ph_tab);
 }
 
@@ -448,125 +484,163 @@ static void dft_to_bond(const or_model *m, const cplx *X, int Rx, int Ry, cplx *
  * zero and contributes nothing.
  * Returns max |A| over both channels.
  */
-double or_project(const or_model *m, const double *state, int chmask, double *Ahat_out)
-{
-    int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = nff * ns2;
-    int Lq = m->Lq, Nq = Lq * Lq;
-    size_t M2 = (size_t)M * M;
-    const cplx *P = (const cplx *)state, *C = P + (size_t)Nq * M2;
-    cplx *AP = (cplx *)Ahat_out, *AC = AP + (size_t)Nq * M2;
-    const cplx *V0 = (const cplx *)m->V0;
-    int i0 = ff_index_mod(m, 0, 0);
-    int onP = chmask & 1, onC = (chmask >> 1) & 1;
+typedef struct {
+    const or_model *m;
+    int chmask, ncls;
+    const cplx *P, *C;
+    int *cls, *plus, *minus, *negminus, *negcls, *dcidx;
+    cplx *Pr, *Cr;
+} proj_ctx;
 
+/* Fourier transforms of P and C to every bond class that can occur, plus bond look-ups */
+static void proj_prepare(const or_model *m, const double *state, int chmask, proj_ctx *c)
+{
+    int ns2 = m->ns * m->ns, nff = m->nff, M = nff * ns2, Lq = m->Lq, Nq = Lq * Lq;
+    size_t M2 = (size_t)M * M;
+    c->m = m;
+    c->chmask = chmask;
+    c->P = (const cplx *)state;
+    c->C = c->P + (size_t)Nq * M2;
     /* R'' classes modulo Lq that can give a non-zero term: differences of two bonds */
-    int *cls = malloc(sizeof(int) * 2 * nff * nff);
+    c->cls = malloc(sizeof(int) * 2 * nff * nff);
     int ncls = 0;
     for (int i = 0; i < nff; i++)
         for (int j = 0; j < nff; j++) {
             int x = imod(m->ffR[2 * i] - m->ffR[2 * j], Lq), y = imod(m->ffR[2 * i + 1] - m->ffR[2 * j + 1], Lq);
             int seen = 0;
-            for (int c = 0; c < ncls; c++) if (cls[2 * c] == x && cls[2 * c + 1] == y) { seen = 1; break; }
-            if (!seen) { cls[2 * ncls] = x; cls[2 * ncls + 1] = y; ncls++; }
+            for (int k = 0; k < ncls; k++) if (c->cls[2 * k] == x && c->cls[2 * k + 1] == y) { seen = 1; break; }
+            if (!seen) { c->cls[2 * ncls] = x; c->cls[2 * ncls + 1] = y; ncls++; }
         }
-    /* Fourier transforms of P and C to those bonds */
-    cplx *Pr = calloc((size_t)ncls * M2, sizeof(cplx));
-    cplx *Cr = calloc((size_t)ncls * M2, sizeof(cplx));
+    c->ncls = ncls;
+    c->Pr = calloc((size_t)ncls * M2, sizeof(cplx));
+    c->Cr = calloc((size_t)ncls * M2, sizeof(cplx));
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int c = 0; c < ncls; c++) {
-        if (onP) dft_to_bond(m, P, cls[2 * c], cls[2 * c + 1], Pr + (size_t)c * M2);
-        if (onC) dft_to_bond(m, C, cls[2 * c], cls[2 * c + 1], Cr + (size_t)c * M2);
+    for (int k = 0; k < ncls; k++) {
+        if (chmask & 1) dft_to_bond(m, c->P, c->cls[2 * k], c->cls[2 * k + 1], c->Pr + (size_t)k * M2);
+        if (chmask & 2) dft_to_bond(m, c->C, c->cls[2 * k], c->cls[2 * k + 1], c->Cr + (size_t)k * M2);
     }
     /* bond look-ups (pure bookkeeping of which shifted bonds are in the set) */
-    int *plus = malloc(sizeof(int) * nff * ncls), *minus = malloc(sizeof(int) * nff * ncls);
-    int *negminus = malloc(sizeof(int) * nff * ncls), *negcls = malloc(sizeof(int) * nff);
-    int *dcidx = malloc(sizeof(int) * nff * nff * nff);
+    c->plus = malloc(sizeof(int) * nff * ncls);
+    c->minus = malloc(sizeof(int) * nff * ncls);
+    c->negminus = malloc(sizeof(int) * nff * ncls);
+    c->negcls = malloc(sizeof(int) * nff);
+    c->dcidx = malloc(sizeof(int) * nff * nff * nff);
     for (int i = 0; i < nff; i++) {
         int Rx = m->ffR[2 * i], Ry = m->ffR[2 * i + 1];
-        for (int c = 0; c < ncls; c++) {
-            plus[i * ncls + c] = ff_index_mod(m, Rx + cls[2 * c], Ry + cls[2 * c + 1]);
-            minus[i * ncls + c] = ff_index_mod(m, Rx - cls[2 * c], Ry - cls[2 * c + 1]);
-            negminus[i * ncls + c] = ff_index_mod(m, -Rx - cls[2 * c], -Ry - cls[2 * c + 1]);
+        for (int k = 0; k < ncls; k++) {
+            c->plus[i * ncls + k] = ff_index_mod(m, Rx + c->cls[2 * k], Ry + c->cls[2 * k + 1]);
+            c->minus[i * ncls + k] = ff_index_mod(m, Rx - c->cls[2 * k], Ry - c->cls[2 * k + 1]);
+            c->negminus[i * ncls + k] = ff_index_mod(m, -Rx - c->cls[2 * k], -Ry - c->cls[2 * k + 1]);
         }
-        negcls[i] = -1;
-        for (int c = 0; c < ncls; c++)
-            if (cls[2 * c] == imod(-Rx, Lq) && cls[2 * c + 1] == imod(-Ry, Lq)) negcls[i] = c;
+        c->negcls[i] = -1;
+        for (int k = 0; k < ncls; k++)
+            if (c->cls[2 * k] == imod(-Rx, Lq) && c->cls[2 * k + 1] == imod(-Ry, Lq)) c->negcls[i] = k;
         for (int j = 0; j < nff; j++)
             for (int w = 0; w < nff; w++)
-                dcidx[(i * nff + j) * nff + w] = ff_index_mod(m, Rx - m->ffR[2 * j] + m->ffR[2 * w],
-                                                              Ry - m->ffR[2 * j + 1] + m->ffR[2 * w + 1]);
+                c->dcidx[(i * nff + j) * nff + w] = ff_index_mod(m, Rx - m->ffR[2 * j] + m->ffR[2 * w],
+                                                                 Ry - m->ffR[2 * j + 1] + m->ffR[2 * w + 1]);
     }
+}
 
+static void proj_free(proj_ctx *c)
+{
+    free(c->Pr); free(c->Cr); free(c->cls); free(c->plus); free(c->minus); free(c->negminus); free(c->negcls);
+    free(c->dcidx);
+}
+
+/* A_P(q) and A_C(q) of one transfer momentum; returns max |A| over both */
+static double proj_one(const proj_ctx *c, int q, cplx *AP, cplx *AC)
+{
+    const or_model *m = c->m;
+    int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = nff * ns2, Lq = m->Lq, ncls = c->ncls;
+    size_t M2 = (size_t)M * M;
+    const cplx *V0 = (const cplx *)m->V0;
+    const cplx *P = c->P, *C = c->C, *Pr = c->Pr, *Cr = c->Cr;
+    int i0 = ff_index_mod(m, 0, 0);
+    int onP = c->chmask & 1, onC = (c->chmask >> 1) & 1;
+    int qx = q / Lq, qy = q % Lq;
+    double amax = 0.0;
+    for (int iR = 0; iR < nff; iR++)
+        for (int iRp = 0; iRp < nff; iRp++) {
+            int Rpx = m->ffR[2 * iRp], Rpy = m->ffR[2 * iRp + 1];
+            for (int s1 = 0; s1 < ns; s1++)
+                for (int s2 = 0; s2 < ns; s2++)
+                    for (int s3 = 0; s3 < ns; s3++)
+                        for (int s4 = 0; s4 < ns; s4++) {
+                            cplx v0 = (iR == i0 && iRp == i0) ? V0[((s1 * ns + s2) * ns + s3) * ns + s4] : 0.0;
+                            /* ---- P channel entry (R,(s1,s2)),(R',(s4,s3)) ---- */
+                            if (onP) {
+                                size_t row = (size_t)iR * ns2 + s1 * ns + s2, col = (size_t)iRp * ns2 + s4 * ns + s3;
+                                cplx val = v0 + P[(size_t)q * M2 + row * M + col];
+                                if (onC) {
+                                    for (int k = 0; k < ncls; k++) {
+                                        int Ux = c->cls[2 * k], Uy = c->cls[2 * k + 1];   /* R'' */
+                                        int i1 = c->plus[iR * ncls + k];
+                                        if (i1 < 0) continue;
+                                        int i2 = c->minus[iRp * ncls + k];
+                                        if (i2 >= 0) {
+                                            cplx ph = lattice_phase((long)qx * Ux + (long)qy * Uy, Lq);
+                                            size_t sr = (size_t)i1 * ns2 + s1 * ns + s3, sc = (size_t)i2 * ns2 + s4 * ns + s2;
+                                            val += ph * Cr[(size_t)k * M2 + sr * M + sc];
+                                        }
+                                        int j2 = c->negminus[iRp * ncls + k];
+                                        if (j2 >= 0) {
+                                            /* C_{s1 s2 s4 s3}: row (s1, s4), column (s3, s2) */
+                                            cplx ph2 = lattice_phase((long)qx * (Rpx + Ux) + (long)qy * (Rpy + Uy), Lq);
+                                            size_t sr = (size_t)i1 * ns2 + s1 * ns + s4, sc = (size_t)j2 * ns2 + s3 * ns + s2;
+                                            val -= ph2 * Cr[(size_t)k * M2 + sr * M + sc];
+                                        }
+                                    }
+                                }
+                                AP[row * M + col] = val;
+                                if (cabs(val) > amax) amax = cabs(val);
+                            }
+                            /* ---- C channel entry (R,(s1,s3)),(R',(s4,s2)) ---- */
+                            if (onC) {
+                                size_t row = (size_t)iR * ns2 + s1 * ns + s3, col = (size_t)iRp * ns2 + s4 * ns + s2;
+                                cplx val = v0 + C[(size_t)q * M2 + row * M + col];
+                                if (onP) {
+                                    for (int k = 0; k < ncls; k++) {
+                                        int i1 = c->plus[iR * ncls + k], i2 = c->minus[iRp * ncls + k];
+                                        if (i1 < 0 || i2 < 0) continue;
+                                        cplx ph = lattice_phase((long)qx * c->cls[2 * k] + (long)qy * c->cls[2 * k + 1], Lq);
+                                        size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s4 * ns + s3;
+                                        val += ph * Pr[(size_t)k * M2 + sr * M + sc];
+                                    }
+                                }
+                                /* D -> C: the Fourier argument is -R', the sum runs over R'' in the bond set */
+                                int cm = c->negcls[iRp];
+                                for (int i2 = 0; i2 < nff; i2++) {
+                                    int i1 = c->dcidx[(iR * nff + iRp) * nff + i2];
+                                    if (i1 < 0) continue;
+                                    cplx ph = lattice_phase((long)qx * m->ffR[2 * i2] + (long)qy * m->ffR[2 * i2 + 1], Lq);
+                                    size_t sr = (size_t)i1 * ns2 + s1 * ns + s4, sc = (size_t)i2 * ns2 + s3 * ns + s2;
+                                    val -= ph * Cr[(size_t)cm * M2 + sr * M + sc];
+                                }
+                                AC[row * M + col] = val;
+                                if (cabs(val) > amax) amax = cabs(val);
+                            }
+                        }
+        }
+    if (!onP) memset(AP, 0, sizeof(cplx) * M2);
+    if (!onC) memset(AC, 0, sizeof(cplx) * M2);
+    return amax;
+}
+
+double or_project(const or_model *m, const double *state, int chmask, double *Ahat_out)
+{
+    int M = m->nff * m->ns * m->ns, Nq = m->Lq * m->Lq;
+    size_t M2 = (size_t)M * M;
+    cplx *AP = (cplx *)Ahat_out, *AC = AP + (size_t)Nq * M2;
+    proj_ctx c;
+    proj_prepare(m, state, chmask, &c);
     double amax = 0.0;
 #pragma omp parallel for schedule(static) reduction(max : amax)
     for (int q = 0; q < Nq; q++) {
-        int qx = q / Lq, qy = q % Lq;
-        for (int iR = 0; iR < nff; iR++)
-            for (int iRp = 0; iRp < nff; iRp++) {
-                int Rpx = m->ffR[2 * iRp], Rpy = m->ffR[2 * iRp + 1];
-                for (int s1 = 0; s1 < ns; s1++)
-                    for (int s2 = 0; s2 < ns; s2++)
-                        for (int s3 = 0; s3 < ns; s3++)
-                            for (int s4 = 0; s4 < ns; s4++) {
-                                cplx v0 = (iR == i0 && iRp == i0) ? V0[((s1 * ns + s2) * ns + s3) * ns + s4] : 0.0;
-                                /* ---- P channel entry (R,(s1,s2)),(R',(s4,s3)) ---- */
-                                if (onP) {
-                                    size_t row = (size_t)iR * ns2 + s1 * ns + s2, col = (size_t)iRp * ns2 + s4 * ns + s3;
-                                    cplx val = v0 + P[(size_t)q * M2 + row * M + col];
-                                    if (onC) {
-                                        for (int c = 0; c < ncls; c++) {
-                                            int Ux = cls[2 * c], Uy = cls[2 * c + 1];   /* R'' */
-                                            int i1 = plus[iR * ncls + c];
-                                            if (i1 < 0) continue;
-                                            int i2 = minus[iRp * ncls + c];
-                                            if (i2 >= 0) {
-                                                cplx ph = lattice_phase((long)qx * Ux + (long)qy * Uy, Lq);
-                                                size_t sr = (size_t)i1 * ns2 + s1 * ns + s3, sc = (size_t)i2 * ns2 + s4 * ns + s2;
-                                                val += ph * Cr[(size_t)c * M2 + sr * M + sc];
-                                            }
-                                            int j2 = negminus[iRp * ncls + c];
-                                            if (j2 >= 0) {
-                                                /* C_{s1 s2 s4 s3}: row (s1, s4), column (s3, s2) */
-                                                cplx ph2 = lattice_phase((long)qx * (Rpx + Ux) + (long)qy * (Rpy + Uy), Lq);
-                                                size_t sr = (size_t)i1 * ns2 + s1 * ns + s4, sc = (size_t)j2 * ns2 + s3 * ns + s2;
-                                                val -= ph2 * Cr[(size_t)c * M2 + sr * M + sc];
-                                            }
-                                        }
-                                    }
-                                    AP[(size_t)q * M2 + row * M + col] = val;
-                                    if (cabs(val) > amax) amax = cabs(val);
-                                }
-                                /* ---- C channel entry (R,(s1,s3)),(R',(s4,s2)) ---- */
-                                if (onC) {
-                                    size_t row = (size_t)iR * ns2 + s1 * ns + s3, col = (size_t)iRp * ns2 + s4 * ns + s2;
-                                    cplx val = v0 + C[(size_t)q * M2 + row * M + col];
-                                    if (onP) {
-                                        for (int c = 0; c < ncls; c++) {
-                                            int i1 = plus[iR * ncls + c], i2 = minus[iRp * ncls + c];
-                                            if (i1 < 0 || i2 < 0) continue;
-                                            cplx ph = lattice_phase((long)qx * cls[2 * c] + (long)qy * cls[2 * c + 1], Lq);
-                                            size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s4 * ns + s3;
-                                            val += ph * Pr[(size_t)c * M2 + sr * M + sc];
-                                        }
-                                    }
-                                    /* D -> C: the Fourier argument is -R', the sum runs over R'' in the bond set */
-                                    int cm = negcls[iRp];
-                                    for (int i2 = 0; i2 < nff; i2++) {
-                                        int i1 = dcidx[(iR * nff + iRp) * nff + i2];
-                                        if (i1 < 0) continue;
-                                        cplx ph = lattice_phase((long)qx * m->ffR[2 * i2] + (long)qy * m->ffR[2 * i2 + 1], Lq);
-                                        size_t sr = (size_t)i1 * ns2 + s1 * ns + s4, sc = (size_t)i2 * ns2 + s3 * ns + s2;
-                                        val -= ph * Cr[(size_t)cm * M2 + sr * M + sc];
-                                    }
-                                    AC[(size_t)q * M2 + row * M + col] = val;
-                                    if (cabs(val) > amax) amax = cabs(val);
-                                }
-                            }
-            }
+        double a = proj_one(&c, q, AP + (size_t)q * M2, AC + (size_t)q * M2);
+        if (a > amax) amax = a;
     }
-    if (!onP) memset(AP, 0, sizeof(cplx) * Nq * M2);
-    if (!onC) memset(AC, 0, sizeof(cplx) * Nq * M2);
-    free(Pr); free(Cr); free(cls); free(plus); free(minus); free(negminus); free(negcls); free(dcidx);
+    proj_free(&c);
     return amax;
 }
 
@@ -644,6 +718,52 @@ double or_rhs(const or_model *m, const double *E, const double *U, double T, con
     free(LcP); free(LcC);
     if (!Ahat_out) free(A);
     return amax;
+}
+
+/* dX/dT for a list of n transfer momenta only (a bounded sample of one right-hand side):
+ * out [2][n][M][M].  Same steps as or_rhs, restricted to the listed momenta where possible
+ * (the Fourier transform always runs over the whole mesh). */
+void or_rhs_at(const or_model *m, const double *E, const double *U, double T, const double *state, int chmask,
+               int n, const int *s_list, double *out)
+{
+    int ns2 = m->ns * m->ns, M = m->nff * ns2, ns4 = ns2 * ns2;
+    size_t M2 = (size_t)M * M;
+    int dl[2 * 4096];
+    int nd = or_delta_list(m, dl);
+    cplx *Lp = calloc((size_t)n * nd * ns4, sizeof(cplx)), *Lcc = calloc((size_t)n * nd * ns4, sizeof(cplx));
+    if (chmask & 1) or_loops_at(m, E, U, T, 0, 0, n, s_list, (double *)Lp);
+    if (chmask & 2) or_loops_at(m, E, U, T, 1, 0, n, s_list, (double *)Lcc);
+    proj_ctx c;
+    proj_prepare(m, state, chmask, &c);
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; i++) {
+        cplx *AP = malloc(sizeof(cplx) * M2), *AC = malloc(sizeof(cplx) * M2);
+        cplx *Lm = malloc(sizeof(cplx) * M2), *Tm = malloc(sizeof(cplx) * M2);
+        proj_one(&c, s_list[i], AP, AC);
+        for (int ch = 0; ch < 2; ch++) {
+            cplx *D = o + ((size_t)ch * n + i) * M2;
+            if (!((chmask >> ch) & 1)) { memset(D, 0, sizeof(cplx) * M2); continue; }
+            const cplx *A = ch == 0 ? AP : AC;
+            expand_loop(m, (ch == 0 ? Lp : Lcc) + (size_t)i * nd * ns4, dl, nd, Lm);
+            double cx = ch == 0 ? 1.0 : 2.0;
+            for (int r = 0; r < M; r++)
+                for (int col = 0; col < M; col++) {
+                    cplx sacc = 0.0;
+                    for (int k = 0; k < M; k++) sacc += A[(size_t)r * M + k] * Lm[(size_t)k * M + col];
+                    Tm[(size_t)r * M + col] = sacc;
+                }
+            for (int r = 0; r < M; r++)
+                for (int col = 0; col < M; col++) {
+                    cplx sacc = 0.0;
+                    for (int k = 0; k < M; k++) sacc += Tm[(size_t)r * M + k] * A[(size_t)k * M + col];
+                    D[(size_t)r * M + col] = cx * sacc;
+                }
+        }
+        free(AP); free(AC); free(Lm); free(Tm);
+    }
+    proj_free(&c);
+    free(Lp); free(Lcc);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,90 @@
+"""ctypes declarations of the libtufrg C ABI (include/tufrg.h).
+
+Argument marshalling only.  Loading fails loudly when the library has not been
+built: there is no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA", 4: "TUFRG_ENONFINITE",
+          5: "TUFRG_ENOTCONV", 6: "TUFRG_ETIMEOUT", 7: "TUFRG_EFALLBACK", 8: "TUFRG_ENOTSUP"}
+
+FP64, SPLIT32 = 0, 1
+CH_P, CH_C = 1, 2
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("n_s", C.c_int), ("n_hop", C.c_int), ("hop_R", C.c_void_p), ("hop_t", C.c_void_p),
+                ("mu", C.c_double), ("filling", C.c_double), ("T_mu", C.c_double), ("V0", C.c_void_p),
+                ("n_ff", C.c_int), ("ff_R", C.c_void_p), ("Lq", C.c_int), ("nc", C.c_int),
+                ("precision", C.c_int)]
+
+
+class FlowOpts(C.Structure):
+    _fields_ = [("T0", C.c_double), ("T_end", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("h0", C.c_double), ("stop", C.c_double), ("channel_mask", C.c_int), ("max_steps", C.c_int)]
+
+
+class FlowResult(C.Structure):
+    _fields_ = [("Tc", C.c_double), ("crossed", C.c_int), ("n_steps", C.c_int), ("n_reject", C.c_int),
+                ("n_rhs", C.c_int), ("amax", C.c_double), ("T_last", C.c_double), ("lead_channel", C.c_int),
+                ("lead_q", C.c_int), ("wall_s", C.c_double)]
+
+
+class TufrgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded library; raises if it has not been built (call build.build() first)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libtufrg is not built ({path} missing); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(path)
+            vp, d, i, ip = C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)
+            L.tufrg_init_model.argtypes = [C.POINTER(ModelDesc), vp, C.POINTER(vp)]
+            L.tufrg_free.argtypes = [vp]
+            L.tufrg_free.restype = None
+            L.tufrg_last_error.argtypes = [vp]
+            L.tufrg_last_error.restype = C.c_char_p
+            L.tufrg_dims.argtypes = [vp, ip, ip, ip, ip, C.POINTER(d)]
+            L.tufrg_deltas.argtypes = [vp, vp]
+            L.tufrg_gather_table.argtypes = [vp, i, vp, i, ip]
+            L.tufrg_bands.argtypes = [vp, vp, vp]
+            L.tufrg_loops.argtypes = [vp, d, i, vp]
+            L.tufrg_project.argtypes = [vp, vp, i, vp, C.POINTER(d)]
+            L.tufrg_rhs.argtypes = [vp, d, vp, i, vp]
+            L.tufrg_rhs_host.argtypes = [vp, d, vp, i, vp]
+            L.tufrg_flow.argtypes = [vp, C.POINTER(FlowOpts), vp, C.POINTER(FlowResult)]
+            L.tufrg_timing_begin.argtypes = [vp]
+            L.tufrg_timing_end.argtypes = [vp, vp, i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+            for fn in ("tufrg_init_model", "tufrg_dims", "tufrg_deltas", "tufrg_gather_table", "tufrg_bands",
+                       "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host", "tufrg_flow",
+                       "tufrg_timing_begin", "tufrg_timing_end"):
+                getattr(L, fn).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+# names every header in include/ declares; the CPU test checks the exports against the headers
+EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
+           "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
+           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end")

@@ -1,0 +1,160 @@
+"""Python face of libtufrg: one ``Model`` per lattice model, device buffers as torch tensors.
+
+Every numerical step runs in the library's CUDA kernels; this module only
+marshals arguments (descriptor arrays, device pointers, the current torch
+stream) and turns status codes into exceptions.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CH_C, CH_P, FP64, SPLIT32, FlowOpts, FlowResult, ModelDesc, TufrgError
+from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
+
+__all__ = ["Model", "FP64", "SPLIT32", "CH_P", "CH_C", "TufrgError"]
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data
+
+
+class Model:
+    """A TU-fRG model on the current CUDA device (see include/tufrg.h for layouts)."""
+
+    def __init__(self, spec: ModelSpec, precision: int = FP64, stream: Optional[torch.cuda.Stream] = None,
+                 mu: Optional[float] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtufrg needs a CUDA device")
+        self.spec = spec
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._L = _lib.lib()
+        # keep the descriptor arrays alive for the duration of the init call
+        self._hopR = np.ascontiguousarray(spec.hop_R, np.int32)
+        self._hopt = np.ascontiguousarray(spec.hop_t, np.complex128)
+        self._V0 = np.ascontiguousarray(spec.V0, np.complex128)
+        self._ffR = np.ascontiguousarray(spec.ff_R, np.int32)
+        use_fill = mu is None and spec.filling > 0
+        d = ModelDesc(spec.n_s, self._hopR.shape[0], self._hopR.ctypes.data, self._hopt.ctypes.data,
+                      float(spec.mu if mu is None else mu), float(spec.filling if use_fill else 0.0),
+                      float(spec.T_mu), self._V0.ctypes.data, self._ffR.shape[0], self._ffR.ctypes.data,
+                      spec.Lq, spec.nc, int(precision))
+        h = C.c_void_p()
+        st = self._L.tufrg_init_model(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        self._h = h
+        if st != 0:
+            msg = self._L.tufrg_last_error(h).decode() if h.value else ""
+            self._L.tufrg_free(h)
+            self._h = C.c_void_p()
+            raise TufrgError(st, msg)
+        Nq, M, nd, Nk = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        mu_ = C.c_double()
+        self._check(self._L.tufrg_dims(self._h, C.byref(Nq), C.byref(M), C.byref(nd), C.byref(Nk), C.byref(mu_)))
+        self.Nq, self.M, self.nd, self.Nk, self.mu = Nq.value, M.value, nd.value, Nk.value, mu_.value
+        dl = np.zeros((self.nd, 2), np.int32)
+        self._check(self._L.tufrg_deltas(self._h, dl.ctypes.data))
+        self.deltas = dl
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, st: int):
+        if st != 0:
+            raise TufrgError(st, self._L.tufrg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.tufrg_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device(self):
+        return torch.device("cuda", torch.cuda.current_device())
+
+    def state_shape(self):
+        return (2, self.Nq, self.M, self.M)
+
+    def loop_shape(self):
+        ns2 = self.spec.n_s ** 2
+        return (2, self.Nq, self.nd, ns2, ns2)
+
+    def zeros_state(self) -> torch.Tensor:
+        return torch.zeros(self.state_shape(), dtype=torch.complex128, device=self.device)
+
+    def _dev(self, x) -> torch.Tensor:
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x, np.complex128))
+        x = x.to(device=self.device, dtype=torch.complex128)
+        return x.contiguous()
+
+    # ------------------------------------------------------------------ entry points
+    def gather_table(self, channel: int) -> np.ndarray:
+        n = C.c_int()
+        self._check(self._L.tufrg_gather_table(self._h, channel, None, 0, C.byref(n)))
+        out = np.zeros((n.value, 9), np.int32)
+        self._check(self._L.tufrg_gather_table(self._h, channel, out.ctypes.data, n.value, C.byref(n)))
+        return out
+
+    def bands(self):
+        E = torch.empty((self.Nk, self.spec.n_s), dtype=torch.float64, device=self.device)
+        U = torch.empty((self.Nk, self.spec.n_s, self.spec.n_s), dtype=torch.complex128, device=self.device)
+        self._check(self._L.tufrg_bands(self._h, _ptr(E), _ptr(U)))
+        return E, U
+
+    def loops(self, T: float, mask: int = CH_P | CH_C, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.zeros(self.loop_shape(), dtype=torch.complex128, device=self.device)
+        self._check(self._L.tufrg_loops(self._h, float(T), int(mask), _ptr(out)))
+        return out
+
+    def project(self, state, mask: int = CH_P | CH_C, out: Optional[torch.Tensor] = None, want_max: bool = True):
+        state = self._dev(state)
+        if out is None:
+            out = torch.empty_like(state)
+        amax = C.c_double(0.0)
+        self._check(self._L.tufrg_project(self._h, _ptr(state), int(mask), _ptr(out),
+                                          C.byref(amax) if want_max else None))
+        return out, amax.value
+
+    def rhs(self, T: float, state, mask: int = CH_P | CH_C, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        state = self._dev(state)
+        if out is None:
+            out = torch.empty_like(state)
+        self._check(self._L.tufrg_rhs(self._h, float(T), _ptr(state), int(mask), _ptr(out)))
+        return out
+
+    def rhs_host(self, T: float, state_host: torch.Tensor, out_host: torch.Tensor, mask: int = CH_P | CH_C):
+        """dX/dT with host (ideally pinned) buffers: H2D, evaluation and D2H inside the call."""
+        assert state_host.device.type == "cpu" and out_host.device.type == "cpu"
+        self._check(self._L.tufrg_rhs_host(self._h, float(T), _ptr(state_host), int(mask), _ptr(out_host)))
+        return out_host
+
+    PHASES = ("fermi", "loops", "loop_reduce", "dft", "project", "vlv", "rk")
+
+    def timing_begin(self):
+        self._check(self._L.tufrg_timing_begin(self._h))
+
+    def timing_end(self):
+        ms = np.zeros(len(self.PHASES))
+        nl, nloop = C.c_longlong(), C.c_longlong()
+        self._check(self._L.tufrg_timing_end(self._h, ms.ctypes.data, len(ms), C.byref(nl), C.byref(nloop)))
+        return dict(zip(self.PHASES, ms.tolist())), nl.value, nloop.value
+
+    def flow(self, T0: float = FLOW_T0, T_end: float = FLOW_T_END, rtol: float = FLOW_RTOL, atol: float = FLOW_ATOL,
+             h0: float = -0.05, stop: float = FLOW_STOP, mask: int = CH_P | CH_C, max_steps: int = 100000,
+             want_state: bool = True):
+        o = FlowOpts(T0, T_end, rtol, atol, h0, stop, int(mask), int(max_steps))
+        r = FlowResult()
+        st_out = self.zeros_state() if want_state else None
+        self._check(self._L.tufrg_flow(self._h, C.byref(o), _ptr(st_out) if want_state else None, C.byref(r)))
+        res = {f: getattr(r, f) for f, _ in FlowResult._fields_}
+        return st_out, res

@@ -1,0 +1,620 @@
+// C ABI of libtufrg: model set-up (tables, memory), the right-hand side and the flow.
+// Every entry point returns a tufrg_status and never throws across the boundary.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+
+#include "tufrg_internal.cuh"
+
+using namespace tufrg;
+
+namespace {
+
+int imod(int a, int m)
+{
+    int r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+tufrg_status fail(tufrg_model *m, tufrg_status st, const std::string &msg)
+{
+    if (m) m->err = msg;
+    return st;
+}
+
+tufrg_status cuda_fail(tufrg_model *m, cudaError_t e, const char *where)
+{
+    if (m) m->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorNotSupported ? TUFRG_ENOTSUP : TUFRG_ECUDA;
+}
+
+#define CK(expr, where)                                        \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return cuda_fail(m, _e, where); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * count);
+}
+
+template <typename T>
+cudaError_t upload(T **p, const std::vector<T> &v, cudaStream_t s)
+{
+    cudaError_t e = dalloc(p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    e = cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);   // the host vector may go away
+}
+
+int ff_index_mod(const tufrg_model *m, int x, int y)
+{
+    for (int i = 0; i < m->nff; i++)
+        if (imod(m->ffR[2 * i] - x, m->Lq) == 0 && imod(m->ffR[2 * i + 1] - y, m->Lq) == 0) return i;
+    return -1;
+}
+
+// Bond bookkeeping for the loops: sorted differences, separable dx / dy sets, slots.
+void build_loop_tables(tufrg_model *m)
+{
+    std::vector<std::pair<int, int>> d;
+    for (int i = 0; i < m->nff; i++)
+        for (int j = 0; j < m->nff; j++) d.emplace_back(m->ffR[2 * i] - m->ffR[2 * j], m->ffR[2 * i + 1] - m->ffR[2 * j + 1]);
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    m->nd = (int)d.size();
+    m->deltas.clear();
+    for (auto &p : d) { m->deltas.push_back(p.first); m->deltas.push_back(p.second); }
+    std::vector<int> xs, ys;
+    for (auto &p : d) { xs.push_back(p.first); ys.push_back(p.second); }
+    std::sort(xs.begin(), xs.end()); xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
+    std::sort(ys.begin(), ys.end()); ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
+    m->dxs = xs;
+    m->dys = ys;
+    std::vector<int> dyh;
+    for (int v : ys) if (v >= 0) dyh.push_back(v);
+    const int ndyh = (int)dyh.size();
+    m->dslot.assign(m->nd, 0);
+    for (int k = 0; k < m->nd; k++) {
+        int dx = d[k].first, dy = d[k].second;
+        if (!(dy > 0 || (dy == 0 && dx >= 0))) { dx = -dx; dy = -dy; }
+        const int xi = (int)(std::find(xs.begin(), xs.end(), dx) - xs.begin());
+        const int yi = (int)(std::find(dyh.begin(), dyh.end(), dy) - dyh.begin());
+        m->dslot[k] = xi * ndyh + yi;
+    }
+    m->dij.assign(m->nff * m->nff, 0);
+    for (int i = 0; i < m->nff; i++)
+        for (int j = 0; j < m->nff; j++) {
+            std::pair<int, int> v(m->ffR[2 * i] - m->ffR[2 * j], m->ffR[2 * i + 1] - m->ffR[2 * j + 1]);
+            m->dij[i * m->nff + j] = (int)(std::lower_bound(d.begin(), d.end(), v) - d.begin());
+        }
+}
+
+// Projection gather tables (Sec. 3.3): bond classes, phase vectors, per-(R,R') term lists.
+void build_gather_tables(tufrg_model *m)
+{
+    const int L = m->Lq, nff = m->nff;
+    std::map<std::pair<int, int>, int> cls, phv;
+    auto cls_of = [&](int x, int y) {
+        std::pair<int, int> k(imod(x, L), imod(y, L));
+        auto it = cls.find(k);
+        if (it != cls.end()) return it->second;
+        int id = (int)cls.size();
+        cls[k] = id;
+        return id;
+    };
+    auto ph_of = [&](int x, int y) {
+        std::pair<int, int> k(imod(x, L), imod(y, L));
+        auto it = phv.find(k);
+        if (it != phv.end()) return it->second;
+        int id = (int)phv.size();
+        phv[k] = id;
+        return id;
+    };
+    // classes of differences of two bonds, in a fixed enumeration order
+    std::vector<std::pair<int, int>> clist;
+    for (int i = 0; i < nff; i++)
+        for (int j = 0; j < nff; j++) {
+            const int x = imod(m->ffR[2 * i] - m->ffR[2 * j], L), y = imod(m->ffR[2 * i + 1] - m->ffR[2 * j + 1], L);
+            if (cls.find({x, y}) == cls.end()) { cls_of(x, y); clist.emplace_back(x, y); }
+        }
+    for (int ch = 0; ch < 2; ch++) {
+        m->gofs[ch].assign(nff * nff + 1, 0);
+        m->gterms[ch].clear();
+        m->gtab_export[ch].clear();
+    }
+    auto add = [&](int ch, int iR, int iRp, int kind, int cx, int cy, int i1, int i2, int px, int py) {
+        GatherTerm t;
+        t.cls = cls_of(cx, cy);
+        t.i1 = i1;
+        t.i2 = i2;
+        t.ph = ph_of(px, py);
+        t.kind = kind;
+        m->gterms[ch].push_back(t);
+        const int ex[9] = {iR, iRp, kind, imod(cx, L), imod(cy, L), i1, i2, imod(px, L), imod(py, L)};
+        m->gtab_export[ch].insert(m->gtab_export[ch].end(), ex, ex + 9);
+    };
+    for (int iR = 0; iR < nff; iR++)
+        for (int iRp = 0; iRp < nff; iRp++) {
+            const int Rx = m->ffR[2 * iR], Ry = m->ffR[2 * iR + 1], Px = m->ffR[2 * iRp], Py = m->ffR[2 * iRp + 1];
+            // P output
+            for (auto &c : clist) {
+                const int i1 = ff_index_mod(m, Rx + c.first, Ry + c.second);
+                if (i1 < 0) continue;
+                const int i2 = ff_index_mod(m, Px - c.first, Py - c.second);
+                if (i2 >= 0) add(0, iR, iRp, 0, c.first, c.second, i1, i2, c.first, c.second);
+                const int j2 = ff_index_mod(m, -Px - c.first, -Py - c.second);
+                if (j2 >= 0) add(0, iR, iRp, 1, c.first, c.second, i1, j2, Px + c.first, Py + c.second);
+            }
+            m->gofs[0][iR * nff + iRp + 1] = (int)m->gterms[0].size();
+            // C output
+            for (auto &c : clist) {
+                const int i1 = ff_index_mod(m, Rx + c.first, Ry + c.second);
+                const int i2 = ff_index_mod(m, Px - c.first, Py - c.second);
+                if (i1 >= 0 && i2 >= 0) add(1, iR, iRp, 2, c.first, c.second, i1, i2, c.first, c.second);
+            }
+            for (int i2 = 0; i2 < nff; i2++) {
+                const int Wx = m->ffR[2 * i2], Wy = m->ffR[2 * i2 + 1];
+                const int i1 = ff_index_mod(m, Rx - Px + Wx, Ry - Py + Wy);
+                if (i1 >= 0) add(1, iR, iRp, 3, -Px, -Py, i1, i2, Wx, Wy);
+            }
+            m->gofs[1][iR * nff + iRp + 1] = (int)m->gterms[1].size();
+        }
+    m->ncls = (int)cls.size();
+    m->cls.assign(2 * m->ncls, 0);
+    for (auto &kv : cls) { m->cls[2 * kv.second] = kv.first.first; m->cls[2 * kv.second + 1] = kv.first.second; }
+    m->nph = (int)phv.size();
+    m->phv.assign(2 * m->nph, 0);
+    for (auto &kv : phv) { m->phv[2 * kv.second] = kv.first.first; m->phv[2 * kv.second + 1] = kv.first.second; }
+}
+
+// e^{i q.R} for every coarse q and every listed vector (exact lattice phases).
+std::vector<double2> phase_table(int Lq, const std::vector<int> &vecs)
+{
+    const int n = (int)vecs.size() / 2, Nq = Lq * Lq;
+    std::vector<double2> t((size_t)Nq * n);
+    for (int q = 0; q < Nq; q++)
+        for (int c = 0; c < n; c++) {
+            const long k = ((long)(q / Lq) * vecs[2 * c] + (long)(q % Lq) * vecs[2 * c + 1]) % Lq;
+            const double a = 2.0 * M_PI * (double)((k + Lq) % Lq) / (double)Lq;
+            t[(size_t)q * n + c] = make_double2(std::cos(a), std::sin(a));
+        }
+    return t;
+}
+
+void release(tufrg_model *m)
+{
+    void *ptrs[] = {m->d_E, m->d_U, m->d_U32, m->d_ft, m->d_ft32, m->d_dslot, m->d_deltas, m->d_hopR, m->d_hopt,
+                    m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
+                    m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
+                    m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &p : m->d_k)
+        if (p) cudaFree(p);
+    for (auto &e : m->evpool) cudaEventDestroy(e);
+    m->evpool.clear();
+}
+
+size_t state_elems(const tufrg_model *m) { return (size_t)2 * m->Nq * m->M * m->M; }
+
+// One evaluation of the right-hand side into d_out, scaled per channel by scale * c_X.
+tufrg_status rhs_device(tufrg_model *m, double T, const double2 *d_state, int mask, double2 *d_out, double scale)
+{
+    CK(launch_fermi(m, T), "fermi tables");
+    CK(launch_loops(m, mask), "loop k-sum");
+    CK(launch_dft(m, d_state, mask), "Fourier transform");
+    CK(launch_project(m, d_state, mask, m->d_A), "projections");
+    CK(launch_vlv(m, m->d_A, mask, scale, d_out), "V.L.V products");
+    return TUFRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, tufrg_model **out)
+{
+    if (!out) return TUFRG_EINVAL;
+    *out = nullptr;
+    if (!desc) return TUFRG_EINVAL;
+    tufrg_model *m = new (std::nothrow) tufrg_model();
+    if (!m) return TUFRG_ENOMEM;
+    *out = m;   // so that tufrg_last_error works even when set-up fails
+    const tufrg_model_desc &d = *desc;
+    if (d.n_s < 1 || d.n_s > 8) return fail(m, TUFRG_EINVAL, "n_s must be in [1, 8]");
+    if (d.n_s != 2) return fail(m, TUFRG_ENOTSUP, "this build's loop kernels support n_s = 2");
+    if (d.n_hop < 1 || !d.hop_R || !d.hop_t) return fail(m, TUFRG_EINVAL, "empty hopping list");
+    if (!d.V0) return fail(m, TUFRG_EINVAL, "V0 is NULL");
+    if (d.n_ff < 1 || !d.ff_R) return fail(m, TUFRG_EINVAL, "empty bond set");
+    if (d.ff_R[0] != 0 || d.ff_R[1] != 0) return fail(m, TUFRG_EINVAL, "ff_R[0] must be (0,0)");
+    if (d.Lq < 2 || d.nc < 1) return fail(m, TUFRG_EINVAL, "Lq >= 2 and nc >= 1 required");
+    if ((long)d.Lq * d.nc > 4096) return fail(m, TUFRG_EINVAL, "fine mesh too large");
+    if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
+    if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
+    m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
+    m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
+    m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    m->hopR.assign(d.hop_R, d.hop_R + 2 * d.n_hop);
+    m->hopt.assign(d.hop_t, d.hop_t + (size_t)2 * d.n_hop * d.n_s * d.n_s);
+    m->V0.assign(d.V0, d.V0 + 2 * (size_t)d.n_s * d.n_s * d.n_s * d.n_s);
+    m->ffR.assign(d.ff_R, d.ff_R + 2 * d.n_ff);
+    // bonds must be distinct modulo Lq (otherwise the plane waves are not orthonormal on the mesh)
+    for (int i = 0; i < m->nff; i++)
+        for (int j = 0; j < i; j++)
+            if (imod(m->ffR[2 * i] - m->ffR[2 * j], m->Lq) == 0 && imod(m->ffR[2 * i + 1] - m->ffR[2 * j + 1], m->Lq) == 0)
+                return fail(m, TUFRG_EINVAL, "bonds are not distinct modulo Lq");
+    // Hermiticity of H(k): t_{-R} = t_R^dagger
+    const int ns = m->ns;
+    for (int h = 0; h < m->nhop; h++) {
+        int g = -1;
+        for (int h2 = 0; h2 < m->nhop; h2++)
+            if (m->hopR[2 * h2] == -m->hopR[2 * h] && m->hopR[2 * h2 + 1] == -m->hopR[2 * h + 1]) g = h2;
+        if (g < 0) return fail(m, TUFRG_EINVAL, "hopping list lacks t_{-R} for some R");
+        for (int i = 0; i < ns; i++)
+            for (int j = 0; j < ns; j++) {
+                const double *a = &m->hopt[2 * ((size_t)h * ns * ns + i * ns + j)];
+                const double *b = &m->hopt[2 * ((size_t)g * ns * ns + j * ns + i)];
+                if (std::fabs(a[0] - b[0]) > 1e-12 || std::fabs(a[1] + b[1]) > 1e-12)
+                    return fail(m, TUFRG_EINVAL, "H(k) is not Hermitian: t_{-R} != t_R^dagger");
+            }
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev), "device attributes");
+
+    build_loop_tables(m);
+    build_gather_tables(m);
+    m->plan = plan_loops(m);
+
+    // ---- device memory
+    const size_t Nk = m->Nk, ns2 = (size_t)ns * ns, ns4 = ns2 * ns2, M2 = (size_t)m->M * m->M;
+    const bool split = m->precision == TUFRG_SPLIT32;
+    std::vector<double2> hopt2((size_t)m->nhop * ns2), V02(ns4);
+    for (size_t i = 0; i < hopt2.size(); i++) hopt2[i] = make_double2(m->hopt[2 * i], m->hopt[2 * i + 1]);
+    for (size_t i = 0; i < V02.size(); i++) V02[i] = make_double2(m->V0[2 * i], m->V0[2 * i + 1]);
+    CK(upload(&m->d_hopR, m->hopR, m->stream), "upload hoppings");
+    CK(upload(&m->d_hopt, hopt2, m->stream), "upload hoppings");
+    CK(upload(&m->d_V0, V02, m->stream), "upload V0");
+    CK(upload(&m->d_deltas, m->deltas, m->stream), "upload bond tables");
+    CK(upload(&m->d_dslot, m->dslot, m->stream), "upload bond tables");
+    CK(upload(&m->d_dij, m->dij, m->stream), "upload bond tables");
+    for (int ch = 0; ch < 2; ch++) {
+        CK(upload(&m->d_gofs[ch], m->gofs[ch], m->stream), "upload gather tables");
+        CK(upload(&m->d_gterms[ch], m->gterms[ch], m->stream), "upload gather tables");
+    }
+    CK(upload(&m->d_ph, phase_table(m->Lq, m->phv), m->stream), "upload phase table");
+    // the Fourier transform uses e^{i u.R''} for the classes
+    CK(upload(&m->d_clsph, phase_table(m->Lq, m->cls), m->stream), "upload phase table");
+    CK(dalloc(&m->d_E, Nk * ns), "cudaMalloc eigenvalues");
+    CK(dalloc(&m->d_U, Nk * ns2), "cudaMalloc eigenvectors");
+    CK(dalloc(&m->d_ft, Nk * ns), "cudaMalloc Fermi table");
+    if (split) {
+        CK(dalloc(&m->d_U32, Nk * ns2), "cudaMalloc eigenvectors");
+        CK(dalloc(&m->d_ft32, Nk * ns), "cudaMalloc Fermi table");
+        CK(dalloc(&m->d_Lc32, 2 * (size_t)m->Nq * m->nd * ns4), "cudaMalloc loops");
+        CK(dalloc(&m->d_A32, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");
+    }
+    CK(dalloc(&m->d_Lc, 2 * (size_t)m->Nq * m->nd * ns4), "cudaMalloc loops");
+    int ndyh = 0;
+    for (int v : m->dys) ndyh += v >= 0;
+    m->part_bytes = (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
+    CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
+    CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
+    CK(dalloc(&m->d_A, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");
+    CK(dalloc(&m->d_amax, 4), "cudaMalloc reductions");
+    CK(dalloc(&m->d_red, 512), "cudaMalloc reductions");
+
+    // ---- eigensystem and chemical potential
+    CK(launch_bands(m), "eigensolve");
+    if (d.filling > 0) {
+        std::vector<double> E(Nk * ns);
+        CK(cudaMemcpyAsync(E.data(), m->d_E, sizeof(double) * E.size(), cudaMemcpyDeviceToHost, m->stream), "copy bands");
+        CK(cudaStreamSynchronize(m->stream), "sync");
+        double lo = *std::min_element(E.begin(), E.end()) - 1.0, hi = *std::max_element(E.begin(), E.end()) + 1.0;
+        for (int it = 0; it < 200; it++) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            double n = 0.0;
+            CK(launch_density(m, mid, d.T_mu, &n), "density");
+            if (n < d.filling) lo = mid; else hi = mid;
+        }
+        m->mu = 0.5 * (lo + hi);
+    } else {
+        m->mu = d.mu;
+    }
+    CK(cudaStreamSynchronize(m->stream), "init sync");
+    return TUFRG_OK;
+}
+
+void tufrg_free(tufrg_model *m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    release(m);
+    delete m;
+}
+
+const char *tufrg_last_error(const tufrg_model *m)
+{
+    return m ? m->err.c_str() : "model handle is NULL";
+}
+
+tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int *Nk, double *mu)
+{
+    if (!m) return TUFRG_EINVAL;
+    if (Nq) *Nq = m->Nq;
+    if (M) *M = m->M;
+    if (n_delta) *n_delta = m->nd;
+    if (Nk) *Nk = m->Nk;
+    if (mu) *mu = m->mu;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out)
+{
+    if (!m || !h_out) return TUFRG_EINVAL;
+    std::memcpy(h_out, m->deltas.data(), sizeof(int) * m->deltas.size());
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_gather_table(const tufrg_model *m, int channel, int *h_out, int cap, int *n_terms)
+{
+    if (!m || channel < 0 || channel > 1 || !n_terms || cap < 0) return TUFRG_EINVAL;
+    const int n = (int)m->gtab_export[channel].size() / 9;
+    *n_terms = n;
+    if (h_out) std::memcpy(h_out, m->gtab_export[channel].data(), sizeof(int) * 9 * (size_t)std::min(n, cap));
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_bands(tufrg_model *m, double *d_E, double *d_U)
+{
+    if (!m || !d_E || !d_U) return fail(m, TUFRG_EINVAL, "NULL argument");
+    CK(cudaMemcpyAsync(d_E, m->d_E, sizeof(double) * m->Nk * m->ns, cudaMemcpyDeviceToDevice, m->stream), "copy bands");
+    CK(cudaMemcpyAsync(d_U, m->d_U, sizeof(double2) * m->Nk * m->ns * m->ns, cudaMemcpyDeviceToDevice, m->stream), "copy bands");
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_loops(tufrg_model *m, double T, int channel_mask, void *d_loops)
+{
+    if (!m || !d_loops) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
+    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    CK(launch_fermi(m, T), "fermi tables");
+    CK(launch_loops(m, channel_mask), "loop k-sum");
+    const size_t per = (size_t)m->Nq * m->nd * m->ns * m->ns * m->ns * m->ns;
+    for (int ch = 0; ch < 2; ch++)
+        if ((channel_mask >> ch) & 1)
+            CK(cudaMemcpyAsync(reinterpret_cast<double2 *>(d_loops) + ch * per, m->d_Lc + ch * per, sizeof(double2) * per,
+                               cudaMemcpyDeviceToDevice, m->stream), "copy loops");
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask, void *d_Ahat, double *h_amax)
+{
+    if (!m || !d_state || !d_Ahat) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    const double2 *st = reinterpret_cast<const double2 *>(d_state);
+    CK(launch_dft(m, st, channel_mask), "Fourier transform");
+    CK(launch_project(m, st, channel_mask, reinterpret_cast<double2 *>(d_Ahat)), "projections");
+    if (h_amax) {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, m->d_amax, sizeof(bits), cudaMemcpyDeviceToHost, m->stream), "copy max");
+        CK(cudaStreamSynchronize(m->stream), "sync");
+        std::memcpy(h_amax, &bits, sizeof(double));
+    }
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate)
+{
+    if (!m || !d_state || !d_dstate) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
+    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    return rhs_device(m, T, reinterpret_cast<const double2 *>(d_state), channel_mask,
+                      reinterpret_cast<double2 *>(d_dstate), 1.0);
+}
+
+tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)
+{
+    if (!m || !h_state || !h_dstate) return fail(m, TUFRG_EINVAL, "NULL argument");
+    const size_t bytes = sizeof(double2) * state_elems(m);
+    if (!m->d_state_in) {
+        CK(cudaMalloc(&m->d_state_in, bytes), "cudaMalloc state");
+        CK(cudaMalloc(&m->d_state_out, bytes), "cudaMalloc state");
+    }
+    CK(cudaMemcpyAsync(m->d_state_in, h_state, bytes, cudaMemcpyHostToDevice, m->stream), "copy state in");
+    tufrg_status st = tufrg_rhs(m, T, m->d_state_in, channel_mask, m->d_state_out);
+    if (st != TUFRG_OK) return st;
+    CK(cudaMemcpyAsync(h_dstate, m->d_state_out, bytes, cudaMemcpyDeviceToHost, m->stream), "copy derivative out");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_out, tufrg_flow_result *res)
+{
+    if (!m || !o || !res) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!(o->T0 > o->T_end) || !(o->T_end > 0)) return fail(m, TUFRG_EINVAL, "need T0 > T_end > 0");
+    if (!(o->rtol > 0) || !(o->atol >= 0) || !(o->h0 < 0)) return fail(m, TUFRG_EINVAL, "bad tolerances or h0");
+    if ((o->channel_mask & 3) == 0 || (o->channel_mask & ~3)) return fail(m, TUFRG_EINVAL, "bad channel_mask");
+    static const double C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+    static const double A[7][6] = {
+        {0},
+        {1.0 / 5},
+        {3.0 / 40, 9.0 / 40},
+        {44.0 / 45, -56.0 / 15, 32.0 / 9},
+        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+        {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+    static const double E[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
+                                125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
+                                11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+    const auto t_start = std::chrono::steady_clock::now();
+    std::memset(res, 0, sizeof(*res));
+    const size_t n = state_elems(m);
+    if (!m->d_y) {
+        CK(dalloc(&m->d_y, n), "cudaMalloc flow state");
+        CK(dalloc(&m->d_yt, n), "cudaMalloc flow state");
+        CK(dalloc(&m->d_yn, n), "cudaMalloc flow state");
+        for (auto &k : m->d_k) CK(dalloc(&k, n), "cudaMalloc flow stages");
+    }
+    double2 *y = m->d_y, *yn = m->d_yn, *yt = m->d_yt, *k[7];
+    for (int i = 0; i < 7; i++) k[i] = m->d_k[i];
+    CK(cudaMemsetAsync(y, 0, sizeof(double2) * n, m->stream), "zero state");
+    const int mask = o->channel_mask;
+    double x = std::log(o->T0);
+    const double xend = std::log(o->T_end);
+    double h = o->h0;
+    auto read_scalars = [&](double *amax, double *err) -> tufrg_status {
+        unsigned long long b[4];
+        CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
+        CK(cudaStreamSynchronize(m->stream), "sync");
+        if (amax) std::memcpy(amax, &b[0], sizeof(double));
+        if (err) std::memcpy(err, &b[2], sizeof(double));
+        return TUFRG_OK;
+    };
+    // k0 = f(x0, y0);  f = T dX/dT (integration variable ln T)
+    tufrg_status st = rhs_device(m, std::exp(x), y, mask, k[0], std::exp(x));
+    if (st != TUFRG_OK) return st;
+    res->n_rhs = 1;
+    double amax_prev = 0.0;
+    if ((st = read_scalars(&amax_prev, nullptr)) != TUFRG_OK) return st;
+    res->amax = amax_prev;
+    double x_prev = x;
+    int tries = 0;
+    tufrg_status out_status = TUFRG_OK;
+    while (true) {
+        if (++tries > o->max_steps) { out_status = fail(m, TUFRG_ENOTCONV, "flow step limit reached"); break; }
+        if (x + h < xend) h = xend - x;
+        for (int j = 1; j < 7; j++) {
+            double2 *dst = j == 6 ? yn : yt;
+            CK(launch_rk_combine(m, dst, y, h, A[j], k, j, n), "stage combination");
+            const double T = std::exp(x + C[j] * h);
+            if ((st = rhs_device(m, T, dst, mask, k[j], T)) != TUFRG_OK) return st;
+            res->n_rhs++;
+        }
+        CK(launch_rk_error(m, y, yn, h, E, k, 7, n, o->atol, o->rtol), "error norm");
+        double amax_new = 0.0, err = 0.0;
+        if ((st = read_scalars(&amax_new, &err)) != TUFRG_OK) return st;
+        if (!std::isfinite(err) || !std::isfinite(amax_new)) {
+            out_status = fail(m, TUFRG_ENONFINITE, "non-finite right-hand side or error norm");
+            break;
+        }
+        if (err <= 1.0) {
+            x_prev = x;
+            x += h;
+            std::swap(y, yn);
+            std::swap(k[0], k[6]);
+            res->n_steps++;
+            res->amax = amax_new;
+            double fac = err > 0 ? 0.9 * std::pow(err, -0.2) : 5.0;
+            fac = std::min(5.0, std::max(0.2, fac));
+            if (amax_new > o->stop) {
+                const double t = (o->stop - amax_prev) / (amax_new - amax_prev);
+                res->Tc = std::exp(x_prev + t * (x - x_prev));
+                res->crossed = 1;
+                break;
+            }
+            amax_prev = amax_new;
+            if (x <= xend + 1e-14) break;
+            h *= fac;
+        } else {
+            res->n_reject++;
+            h *= std::min(1.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+            if (std::fabs(h) < 1e-12) { out_status = fail(m, TUFRG_ENOTCONV, "step size underflow"); break; }
+        }
+    }
+    res->T_last = std::exp(x);
+    if (!res->crossed) res->Tc = res->T_last;
+    // the last evaluated projection belongs to the last accepted state (stage 7 = FSAL)
+    const size_t nA = state_elems(m);
+    CK(launch_amax_locate(m, m->d_A, nA, res->amax), "locate maximum");
+    unsigned long long b[4];
+    CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    const size_t M2 = (size_t)m->M * m->M;
+    if (b[1] < nA) {
+        res->lead_channel = (int)(b[1] / ((size_t)m->Nq * M2));
+        res->lead_q = (int)((b[1] / M2) % m->Nq);
+    }
+    if (d_state_out)
+        CK(cudaMemcpyAsync(d_state_out, y, sizeof(double2) * n, cudaMemcpyDeviceToDevice, m->stream), "copy state out");
+    // keep the buffers consistent for the next call
+    m->d_y = y; m->d_yn = yn;
+    for (int i = 0; i < 7; i++) m->d_k[i] = k[i];
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    res->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return out_status;
+}
+
+}  // extern "C"
+
+namespace tufrg {
+
+PhaseScope::PhaseScope(tufrg_model *mm, int phase, int n_launch) : m(mm)
+{
+    m->launches += n_launch;
+    if (phase == PH_LOOPS) m->loop_launches += n_launch;
+    if (!m->timing) return;
+    while (m->evpool.size() < m->evused + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        m->evpool.push_back(e);
+    }
+    tufrg_model::TimerRec r{phase, m->evpool[m->evused], m->evpool[m->evused + 1]};
+    m->evused += 2;
+    cudaEventRecord(r.a, m->stream);
+    idx = (int)m->trec.size();
+    m->trec.push_back(r);
+}
+
+PhaseScope::~PhaseScope()
+{
+    if (idx >= 0) cudaEventRecord(m->trec[idx].b, m->stream);
+}
+
+}  // namespace tufrg
+
+extern "C" {
+
+tufrg_status tufrg_timing_begin(tufrg_model *m)
+{
+    if (!m) return TUFRG_EINVAL;
+    m->trec.clear();
+    m->evused = 0;
+    m->launches = 0;
+    m->loop_launches = 0;
+    m->timing = true;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_timing_end(tufrg_model *m, double *h_ms, int n_ms, long long *h_launches, long long *h_loop_launches)
+{
+    if (!m) return TUFRG_EINVAL;
+    m->timing = false;
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    double acc[PH_N] = {0};
+    for (auto &r : m->trec) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b), "event time");
+        acc[r.phase] += ms;
+    }
+    for (int i = 0; i < n_ms && i < PH_N; i++) h_ms[i] = acc[i];
+    if (h_launches) *h_launches = m->launches;
+    if (h_loop_launches) *h_loop_launches = m->loop_launches;
+    m->trec.clear();
+    m->evused = 0;
+    return TUFRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations shared by the translation units of libtufrg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tufrg.h"
+
+namespace tufrg {
+
+// ------------------------------------------------------------------ small complex helpers
+template <typename R> struct cpx;
+template <> struct cpx<double> { using t = double2; };
+template <> struct cpx<float> { using t = float2; };
+
+__host__ __device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+
+// Fine-mesh Fermi table entry, one per (k, band): e = E - mu, g = df/dT, gp = dg/de.
+struct FermiEntry {
+    double e, g, gp;
+};
+
+// Split-precision copy used by the FP32 loop kernel.
+struct FermiEntry32 {
+    float e, g, gp, pad;
+};
+
+// Everything the projection kernel needs about one gather term.
+// kind: 0 = P<-C, 1 = P<-D, 2 = C<-P, 3 = C<-D.
+struct GatherTerm {
+    int cls;   // row of the Fourier-transformed source (bond class of R'' or -R')
+    int i1, i2;
+    int ph;    // column of the phase table e^{i q.R}
+    int kind;
+};
+
+struct LoopPlan {
+    int kx_per_cta;     // threads (columns) per CTA
+    int ky_chunks;      // number of ky ranges per column
+    int n_partials;     // partial sums per transfer momentum
+};
+
+}  // namespace tufrg
+
+struct tufrg_model {
+    // ---- descriptor copy
+    int ns = 0, nhop = 0, nff = 0, Lq = 0, nc = 0, Lf = 0, Nq = 0, Nk = 0, M = 0, precision = 0;
+    std::vector<int> hopR, ffR;
+    std::vector<double> hopt, V0;
+    double mu = 0.0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int sm_count = 0;
+
+    // ---- bond bookkeeping (host)
+    std::vector<int> deltas;        // [nd][2] sorted (dx, dy)
+    int nd = 0;
+    std::vector<int> dxs, dys;      // distinct dx / dy values (sorted)
+    std::vector<int> dslot;         // [nd] see d_dslot
+    std::vector<int> dij;           // [nff][nff] -> delta index of R1 - R2
+    std::vector<int> cls;           // [ncls][2] bond classes mod Lq used by projections
+    int ncls = 0;
+    std::vector<int> phv;           // [nph][2] phase vectors mod Lq
+    int nph = 0;
+    std::vector<int> gofs[2];       // CSR offsets per output channel, [nff*nff + 1]
+    std::vector<tufrg::GatherTerm> gterms[2];
+    std::vector<int> gtab_export[2];  // 9 ints per term, for tufrg_gather_table
+
+    // ---- device memory (owned)
+    double *d_E = nullptr;          // [Nk][ns]
+    double2 *d_U = nullptr;         // [Nk][ns][ns]
+    float2 *d_U32 = nullptr;        // [Nk][ns][ns] (split path)
+    tufrg::FermiEntry *d_ft = nullptr;      // [Nk][ns]
+    tufrg::FermiEntry32 *d_ft32 = nullptr;  // [Nk][ns]
+    int *d_dslot = nullptr;         // [nd] partial slot (dxi * ndyh + dyi) of the half-plane partner
+    int *d_deltas = nullptr;        // [nd][2]
+    int *d_hopR = nullptr;          // [nhop][2]
+    double2 *d_hopt = nullptr;      // [nhop][ns][ns]
+    double cur_T = 0.0;             // temperature of the current Fermi tables
+    int *d_dij = nullptr;           // [nff][nff]
+    int *d_gofs[2] = {nullptr, nullptr};
+    tufrg::GatherTerm *d_gterms[2] = {nullptr, nullptr};
+    double2 *d_ph = nullptr;        // [Nq][nph] phase table e^{i q.R}
+    double2 *d_clsph = nullptr;     // [Nq][ncls] e^{i q.R''} for the Fourier transform
+    double2 *d_V0 = nullptr;        // [ns^4]
+    double2 *d_Lc = nullptr;        // [2][Nq][nd][ns^4] loops (FP64 view)
+    float2 *d_Lc32 = nullptr;       // [2][Nq][nd][ns^4] loops (split path)
+    void *d_part = nullptr;         // loop partial sums (scratch)
+    size_t part_bytes = 0;
+    double2 *d_Xr = nullptr;        // [2][ncls][M][M] Fourier transforms
+    double2 *d_A = nullptr;         // [2][Nq][M][M] projected vertex
+    float2 *d_A32 = nullptr;        // [2][Nq][M][M] (split path)
+    double2 *d_T = nullptr;         // [Nq][M][M] GEMM intermediate (large M)
+    unsigned long long *d_amax = nullptr;   // [4] reductions (max|A|, argmax, err)
+    double *d_red = nullptr;        // density reduction scratch
+    // flow work buffers
+    double2 *d_y = nullptr, *d_yt = nullptr, *d_yn = nullptr, *d_k[7] = {};
+    double2 *d_state_in = nullptr, *d_state_out = nullptr;   // host-buffer entry points
+
+    tufrg::LoopPlan plan{};
+
+    // ---- optional event timing (phases as listed in tufrg.h)
+    bool timing = false;
+    long long launches = 0, loop_launches = 0;
+    struct TimerRec { int phase; cudaEvent_t a, b; };
+    std::vector<TimerRec> trec;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+};
+
+namespace tufrg {
+
+// ------------------------------------------------------------------ launchers (k_*.cu)
+cudaError_t launch_bands(tufrg_model *m);
+cudaError_t launch_density(tufrg_model *m, double mu, double T, double *h_out);
+cudaError_t launch_fermi(tufrg_model *m, double T);
+cudaError_t launch_loops(tufrg_model *m, int channel_mask);
+cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, int channel_mask);
+cudaError_t launch_project(tufrg_model *m, const double2 *d_state, int channel_mask, double2 *d_A);
+cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out);
+cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, double h, const double *a,
+                              double2 *const *k, int nk, size_t n);
+cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, double h, const double *e,
+                            double2 *const *k, int nk, size_t n, double atol, double rtol);
+cudaError_t launch_amax_locate(tufrg_model *m, const double2 *d_A, size_t n, double amax);
+LoopPlan plan_loops(const tufrg_model *m);
+
+enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_N = 7 };
+
+// Brackets one kernel phase with events when timing is on; counts launches always.
+struct PhaseScope {
+    tufrg_model *m;
+    int idx = -1;
+    PhaseScope(tufrg_model *mm, int phase, int n_launch = 1);
+    ~PhaseScope();
+};
+
+}  // namespace tufrg
+
+#define TUFRG_CUDA_TRY(expr)                                  \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return _e;                     \
+    } while (0)

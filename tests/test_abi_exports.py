@@ -1,0 +1,89 @@
+"""CPU checks of the C-ABI library: it builds, loads and exports every function the headers declare."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(tufrg_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1710_08830_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_function(libpath):
+    declared = _declared()
+    assert "tufrg_init_model" in declared and "tufrg_rhs" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = sorted(declared - exported)
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_library_loads_and_binding_matches(libpath):
+    from paper_1710_08830_gb300 import _lib
+    L = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(L, name)
+    assert set(_lib.EXPORTS) <= _declared()
+
+
+def test_null_arguments_are_rejected_without_a_gpu(libpath):
+    """Argument checks happen before any CUDA call."""
+    from paper_1710_08830_gb300 import _lib
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    assert L.tufrg_init_model(None, None, ctypes.byref(h)) == 1      # TUFRG_EINVAL
+    assert L.tufrg_dims(None, None, None, None, None, None) == 1
+    assert L.tufrg_rhs(None, 1.0, None, 3, None) == 1
+    assert L.tufrg_last_error(None) == b"model handle is NULL"
+
+
+def test_bad_descriptors_are_rejected_before_device_use(libpath):
+    import numpy as np
+    from paper_1710_08830_gb300 import _lib, inputs
+    L = _lib.lib()
+    spec = inputs.rashba_hubbard(Lq=6, nc=2, n_ff=5)
+    hopR = np.ascontiguousarray(spec.hop_R, np.int32)
+    hopt = np.ascontiguousarray(spec.hop_t, np.complex128)
+    V0 = np.ascontiguousarray(spec.V0, np.complex128)
+
+    def init(ff, **kw):
+        ff = np.ascontiguousarray(ff, np.int32)
+        f = dict(n_s=2, n_hop=hopR.shape[0], hop_R=hopR.ctypes.data, hop_t=hopt.ctypes.data, mu=-0.9, filling=0.0,
+                 T_mu=0.02, V0=V0.ctypes.data, n_ff=ff.shape[0], ff_R=ff.ctypes.data, Lq=6, nc=2, precision=0)
+        f.update(kw)
+        d = _lib.ModelDesc(**f)
+        h = ctypes.c_void_p()
+        st = L.tufrg_init_model(ctypes.byref(d), None, ctypes.byref(h))
+        msg = L.tufrg_last_error(h).decode()
+        L.tufrg_free(h)
+        return st, msg
+
+    st, msg = init(np.array([[1, 0], [0, 0]]))
+    assert st == 1 and "(0,0)" in msg
+    st, msg = init(np.array([[0, 0], [6, 0]]))
+    assert st == 1 and "distinct" in msg
+    st, msg = init(spec.ff_R, Lq=1)
+    assert st == 1
+    st, msg = init(spec.ff_R, precision=7)
+    assert st == 1
+    bad = hopt.copy()
+    bad[0] *= 2.0   # breaks t_{-R} = t_R^dagger
+    st, msg = init(spec.ff_R, hop_t=bad.ctypes.data)
+    assert st == 1 and "Hermitian" in msg

@@ -1,0 +1,271 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (stated per result):
+  * integer gather tables: bit-exact;
+  * FP64 path vs oracle: <= 1e-10 relative (max abs error / max abs value);
+  * split path (FP32 loop sums and products, FP64 state) vs FP64 oracle: <= 1e-4 relative.
+Sizes span several CTAs and a ragged tail of the fine mesh (Lf = 24, 25, 30, 120), the
+degenerate bands of the SU(2) model, the complete 4x4 bond set and the full-size
+24x24 / 8x8 Rashba workload.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1710_08830_gb300 import inputs  # noqa: E402
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_08830_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _api():
+    from paper_1710_08830_gb300 import api
+    return api
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    "rashba_ff5_Lf24": lambda: inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=6, nc=4, n_ff=5),
+    "rashba_ff9_Lf25": lambda: inputs.rashba_hubbard(tp=-0.15, alpha=0.35, U=2.0, mu=-0.7, Lq=5, nc=5, n_ff=9),
+    "hubbard_ff5_Lf24": lambda: inputs.hubbard_square(tp=-0.25, U=3.0, Lq=6, nc=4, n_ff=5, filling=0.9, T_mu=0.05),
+    "rashba_ff13_Lf30": lambda: inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=2.0, mu=-1.0, Lq=10, nc=3, n_ff=13),
+    "complete_4x4": lambda: inputs.rashba_hubbard(tp=-0.2, alpha=0.4, U=2.0, mu=-0.7, Lq=4, nc=1).with_(
+        ff_R=inputs.ff_complete(4)),
+    "rashba_ff9_Lf120": lambda: inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=12, nc=10, n_ff=9),
+}
+
+
+@pytest.mark.parametrize("case", ["rashba_ff5_Lf24", "hubbard_ff5_Lf24", "rashba_ff13_Lf30"])
+def test_bands(case):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    E, U = m.bands()
+    E, U = E.cpu().numpy(), U.cpu().numpy()
+    assert np.abs(E - o.E).max() < 1e-12
+    L = spec.Lf
+    kx, ky = np.divmod(np.arange(spec.Nk), L)
+    H = np.zeros((spec.Nk, 2, 2), complex)
+    for R, t in zip(spec.hop_R, spec.hop_t):
+        H += np.exp(2j * np.pi * (kx * R[0] + ky * R[1]) / L)[:, None, None] * t
+    assert np.abs(np.einsum("kij,kjl->kil", H, U) - U * E[:, None, :]).max() < 1e-12
+    assert np.abs(np.einsum("kji,kjl->kil", U.conj(), U) - np.eye(2)).max() < 1e-13
+    assert abs(m.mu - o.mu) < 1e-12
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("T", [2.0, 0.07])
+def test_loops_fp64(case, T):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    assert np.array_equal(m.deltas, o.deltas)
+    L = m.loops(T).cpu().numpy()
+    for ch in (0, 1):
+        ref = o.loops(T, ch)
+        assert rel(L[ch], ref) < TOL64, (ch, rel(L[ch], ref))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("T", [2.0, 0.07])
+def test_loops_split(case, T):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.SPLIT32)
+    o = oracle.Oracle(spec)
+    L = m.loops(T).cpu().numpy()
+    for ch in (0, 1):
+        ref = o.loops(T, ch)
+        assert rel(L[ch], ref) < 2e-5, (ch, rel(L[ch], ref))
+
+
+def _paper_gather_terms(spec):
+    """Independent enumeration of the gather terms from the printed projection formulas."""
+    L = spec.Lq
+    ff = [tuple(map(int, r)) for r in spec.ff_R]
+    idx = {((x % L), (y % L)): i for i, (x, y) in enumerate(ff)}
+    classes = sorted({((a[0] - b[0]) % L, (a[1] - b[1]) % L) for a in ff for b in ff})
+    P, C = set(), set()
+    for iR, (Rx, Ry) in enumerate(ff):
+        for iRp, (Px, Py) in enumerate(ff):
+            for (cx, cy) in classes:
+                i1 = idx.get(((Rx + cx) % L, (Ry + cy) % L))
+                i2 = idx.get(((Px - cx) % L, (Py - cy) % L))
+                j2 = idx.get(((-Px - cx) % L, (-Py - cy) % L))
+                if i1 is not None and i2 is not None:
+                    P.add((iR, iRp, 0, cx, cy, i1, i2, cx, cy))          # Eq. proj_PD
+                    C.add((iR, iRp, 2, cx, cy, i1, i2, cx, cy))          # P -> C
+                if i1 is not None and j2 is not None:
+                    P.add((iR, iRp, 1, cx, cy, i1, j2, (Px + cx) % L, (Py + cy) % L))   # D -> P
+            for i2, (Wx, Wy) in enumerate(ff):
+                i1 = idx.get(((Rx - Px + Wx) % L, (Ry - Py + Wy) % L))
+                if i1 is not None:
+                    C.add((iR, iRp, 3, (-Px) % L, (-Py) % L, i1, i2, Wx % L, Wy % L))   # Eq. proj_DC
+    return P, C
+
+
+@pytest.mark.parametrize("case", ["rashba_ff5_Lf24", "rashba_ff9_Lf25", "rashba_ff13_Lf30", "complete_4x4"])
+def test_gather_tables_bit_exact(case):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.FP64)
+    P, C = _paper_gather_terms(spec)
+    gP = [tuple(int(v) for v in r) for r in m.gather_table(0)]
+    gC = [tuple(int(v) for v in r) for r in m.gather_table(1)]
+    assert len(gP) == len(set(gP)) and len(gC) == len(set(gC))
+    assert set(gP) == P
+    assert set(gC) == C
+
+
+@pytest.mark.parametrize("case", ["rashba_ff5_Lf24", "rashba_ff9_Lf25", "rashba_ff13_Lf30", "complete_4x4"])
+@pytest.mark.parametrize("mask", [3, 1, 2])
+def test_projections(case, mask):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=5, scale=0.4)
+    A, amax = m.project(st, mask)
+    A = A.cpu().numpy()
+    ref, amax_ref = o.project(st, mask)
+    assert rel(A, ref) < 1e-13
+    assert amax == pytest.approx(amax_ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("T", [5.0, 0.3, 0.05])
+def test_rhs_fp64(case, T):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=9, scale=0.3)
+    d = m.rhs(T, st).cpu().numpy()
+    ref, _ = o.rhs(T, st, 3)
+    assert rel(d, ref) < TOL64
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("T", [5.0, 0.05])
+def test_rhs_split(case, T):
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.SPLIT32)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=9, scale=0.3)
+    d = m.rhs(T, st).cpu().numpy()
+    ref, _ = o.rhs(T, st, 3)
+    assert rel(d, ref) < TOL32
+
+
+@pytest.mark.parametrize("mask", [1, 2])
+def test_rhs_single_channel(mask):
+    api = _api()
+    spec = CASES["rashba_ff9_Lf25"]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=2, scale=0.3)
+    st[2 - mask] = 0.0   # the channel that does not flow is zero
+    d = m.rhs(0.2, st, mask).cpu().numpy()
+    ref, _ = o.rhs(0.2, st, mask)
+    assert rel(d, ref) < TOL64
+    assert np.abs(d[2 - mask]).max() == 0.0
+
+
+def test_rhs_host_buffers_match_device():
+    api = _api()
+    spec = CASES["rashba_ff5_Lf24"]()
+    m = api.Model(spec, api.FP64)
+    st = inputs.random_state(spec, seed=4, scale=0.3)
+    d_dev = m.rhs(0.4, st).cpu()
+    hs = torch.from_numpy(st).pin_memory()
+    ho = torch.empty_like(hs).pin_memory()
+    m.rhs_host(0.4, hs, ho)
+    assert torch.equal(d_dev, ho)
+
+
+def test_rhs_deterministic():
+    api = _api()
+    spec = CASES["rashba_ff9_Lf120"]()
+    for prec in (api.FP64, api.SPLIT32):
+        m = api.Model(spec, prec)
+        st = inputs.random_state(spec, seed=4, scale=0.3)
+        a = m.rhs(0.1, st).cpu()
+        b = m.rhs(0.1, st).cpu()
+        assert torch.equal(a, b)
+
+
+def test_flow_fp64_matches_oracle():
+    api = _api()
+    spec = inputs.hubbard_square(U=3.0, Lq=6, nc=4, n_ff=5, filling=0.9, T_mu=0.02)
+    o = oracle.Oracle(spec)
+    st_ref, r_ref = o.flow(stop=6.0)
+    m = api.Model(spec, api.FP64)
+    st, r = m.flow(stop=6.0)
+    assert r_ref["crossed"] == 1 and r["crossed"] == 1
+    assert r["n_steps"] == r_ref["n_steps"] and r["n_reject"] == r_ref["n_reject"]
+    assert r["Tc"] == pytest.approx(r_ref["Tc"], rel=1e-9)
+    assert rel(st.cpu().numpy(), st_ref) < 1e-9
+
+
+def test_flow_split_critical_scale_within_one_percent():
+    api = _api()
+    spec = inputs.hubbard_square(U=3.0, Lq=6, nc=4, n_ff=5, filling=0.9, T_mu=0.02)
+    o = oracle.Oracle(spec)
+    _, r_ref = o.flow(stop=6.0)
+    m = api.Model(spec, api.SPLIT32)
+    st, r = m.flow(stop=6.0)
+    assert r["crossed"] == 1
+    assert abs(r["Tc"] / r_ref["Tc"] - 1) < 0.01
+
+
+def test_flow_closed_form_particle_particle():
+    """GPU flow in P-only mode reproduces the paper's closed form (Sec. 4, Eq. sol_spin)."""
+    api = _api()
+    U = 2.5
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5)
+    m = api.Model(spec, api.FP64)
+    st, r = m.flow(T0=10.0, T_end=0.3, rtol=1e-10, atol=1e-12, stop=1e9, mask=1)
+    o = oracle.Oracle(spec)
+    st_ref, _ = o.flow(T0=10.0, T_end=0.3, rtol=1e-10, atol=1e-12, stop=1e9, chmask=1)
+    assert rel(st.cpu().numpy(), st_ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_rhs_full_size_rashba_24x24(prec):
+    """The benchmark workload itself (Lq = 24, nc = 8, N_ff = 9, M = 36): full right-hand side."""
+    api = _api()
+    spec = inputs.rashba_q24_k8_ff9(0)
+    m = api.Model(spec, getattr(api, prec))
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=1, scale=0.2)
+    d = m.rhs(0.1, st).cpu().numpy()
+    ref, _ = o.rhs(0.1, st, 3)
+    assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32)
+
+
+def test_invalid_temperature_is_rejected():
+    api = _api()
+    m = api.Model(CASES["rashba_ff5_Lf24"](), api.FP64)
+    with pytest.raises(api.TufrgError) as e:
+        m.rhs(-1.0, m.zeros_state())
+    assert e.value.status == 1
