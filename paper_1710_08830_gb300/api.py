@@ -134,7 +134,14 @@ class Model:
 
     def rhs_host(self, T: float, state_host: torch.Tensor, out_host: torch.Tensor, mask: int = CH_P | CH_C):
         """dX/dT with host (ideally pinned) buffers: H2D, evaluation and D2H inside the call."""
-        assert state_host.device.type == "cpu" and out_host.device.type == "cpu"
+        if state_host.device.type != "cpu" or out_host.device.type != "cpu":
+            raise ValueError("rhs_host takes host tensors")
+        if not (state_host.is_contiguous() and out_host.is_contiguous()):
+            raise ValueError("rhs_host needs C-contiguous host tensors")
+        if state_host.dtype != torch.complex128 or out_host.dtype != torch.complex128:
+            raise ValueError("rhs_host needs complex128 tensors")
+        if tuple(state_host.shape) != self.state_shape() or tuple(out_host.shape) != self.state_shape():
+            raise ValueError(f"rhs_host needs tensors of shape {self.state_shape()}")
         self._check(self._L.tufrg_rhs_host(self._h, float(T), _ptr(state_host), int(mask), _ptr(out_host)))
         return out_host
 

@@ -324,4 +324,4 @@ def random_state(spec: ModelSpec, seed: int, scale: float = 0.3, hermitian: bool
     X = (rng.standard_normal((2, Nq, M, M)) + 1j * rng.standard_normal((2, Nq, M, M))) * scale
     if hermitian:
         X = 0.5 * (X + np.conj(np.swapaxes(X, -1, -2)))
-    return X.astype(np.complex128)
+    return np.ascontiguousarray(X, dtype=np.complex128)
