@@ -197,7 +197,8 @@ void release(tufrg_model *m)
     void *ptrs[] = {m->d_E, m->d_U, m->d_U32, m->d_ft, m->d_ft32, m->d_dslot, m->d_deltas, m->d_hopR, m->d_hopt,
                     m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
-                    m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out};
+                    m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
+                    m->d_ph32, m->d_dftpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -293,7 +294,20 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(upload(&m->d_gofs[ch], m->gofs[ch], m->stream), "upload gather tables");
         CK(upload(&m->d_gterms[ch], m->gterms[ch], m->stream), "upload gather tables");
     }
-    CK(upload(&m->d_ph, phase_table(m->Lq, m->phv), m->stream), "upload phase table");
+    {
+        std::vector<double2> ph = phase_table(m->Lq, m->phv);
+        CK(upload(&m->d_ph, ph, m->stream), "upload phase table");
+        if (split) {
+            std::vector<float2> ph32(ph.size());
+            for (size_t i = 0; i < ph.size(); i++) ph32[i] = make_float2((float)ph[i].x, (float)ph[i].y);
+            CK(upload(&m->d_ph32, ph32, m->stream), "upload phase table");
+        }
+    }
+    m->max_terms = 0;
+    for (int ch = 0; ch < 2; ch++)
+        for (int p = 0; p < m->nff * m->nff; p++)
+            m->max_terms = std::max(m->max_terms, m->gofs[ch][p + 1] - m->gofs[ch][p]);
+    m->dft_nsplit = dft_plan_nsplit(m);
     // the Fourier transform uses e^{i u.R''} for the classes
     CK(upload(&m->d_clsph, phase_table(m->Lq, m->cls), m->stream), "upload phase table");
     CK(dalloc(&m->d_E, Nk * ns), "cudaMalloc eigenvalues");
@@ -311,6 +325,10 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     m->part_bytes = (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
     CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
     CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
+    CK(cudaMalloc(&m->d_dftpart, (size_t)m->dft_nsplit * 2 * m->ncls * M2 * (split ? sizeof(float2) : sizeof(double2))),
+       "cudaMalloc Fourier partials");
+    if (split) CK(dalloc(&m->d_Xr32, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
+    if (loops2_supported(m)) CK(dalloc(&m->d_rec, Nk * 3), "cudaMalloc loop records");
     CK(dalloc(&m->d_A, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");
     CK(dalloc(&m->d_amax, 4), "cudaMalloc reductions");
     CK(dalloc(&m->d_red, 512), "cudaMalloc reductions");

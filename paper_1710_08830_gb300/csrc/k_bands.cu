@@ -215,6 +215,10 @@ cudaError_t launch_bands(tufrg_model *m)
 
 cudaError_t launch_fermi(tufrg_model *m, double T)
 {
+    if (loops2_supported(m)) {   // the split two-band kernel reads its own per-k records
+        m->cur_T = T;
+        return launch_loop_records(m, T);
+    }
     const int n = m->Nk * m->ns;
     FermiEntry32 *ft32 = m->precision == TUFRG_FP64 ? nullptr : m->d_ft32;
     PhaseScope ps(m, PH_FERMI);

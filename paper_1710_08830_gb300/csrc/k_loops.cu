@@ -286,7 +286,7 @@ LoopPlan plan_loops(const tufrg_model *m)
     LoopPlan p{};
     p.kx_per_cta = 32 * WARPS;
     const int ctas_x = (m->Lf + p.kx_per_cta - 1) / p.kx_per_cta;
-    const int per_sm = m->precision == TUFRG_FP64 ? 4 : 6;     // resident CTAs per SM (register bound)
+    const int per_sm = loops2_supported(m) ? loops2_blocks_per_sm(m) : (m->precision == TUFRG_FP64 ? 4 : 6);
     const double slots = (double)m->sm_count * per_sm;
     double best = 1e300;
     int best_c = 1;
@@ -315,7 +315,15 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
     for (int ch = 0; ch < 2; ch++) {
         if (!((channel_mask >> ch) & 1)) continue;
         const double inv_nk = 1.0 / (double)m->Nk;
-        if (m->precision == TUFRG_FP64) {
+        if (loops2_supported(m)) {
+            TUFRG_CUDA_TRY(launch_loops2(m, ch));
+            const size_t total = (size_t)m->Nq * m->nd * NS4;
+            PhaseScope ps(m, PH_LOOPRED);
+            loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+                reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq,
+                inv_nk, m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4);
+            TUFRG_CUDA_TRY(cudaGetLastError());
+        } else if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};
             a.U = m->d_U; a.ft = m->d_ft; a.part = reinterpret_cast<double2 *>(m->d_part);
             a.Lq = m->Lq; a.nc = m->nc; a.Lf = m->Lf; a.ndx = ndx; a.ndyh = ndyh;

@@ -1,0 +1,339 @@
+// Split-precision (FP32) loop k-sum for N_s = 2, the dominant kernel of the right-hand side.
+//
+// Same sums as k_loops.cu (Eqs. loopminus / loopplus dressed by Eq. trafo), organised
+// around the structure of the two-band problem:
+//   * the band projectors are complete and rank one: rho^1 = 1 - rho^0 and
+//     rho^0_00 + rho^0_11 = 1, so one 48-byte record per fine k holds
+//     (rho^0_00, Re rho^0_01, Im rho^0_01) and the Fermi data (e_l, g_l = df/dT,
+//     gp_l = dg/de), rewritten once per temperature;
+//   * with D = T^0 - T^1, Y = 1 (x) T^1 + rho1^0 (x) D, where
+//     T^{l1} = w_{l1 1} 1 + (w_{l1 0} - w_{l1 1}) rho2^0;  Y is Hermitian in the sense
+//     Y[(t3 t1),(t4 t2)] = conj(Y[(t1 t3),(t2 t4)]), so only 4 real and 6 complex
+//     entries are formed;
+//   * the row sums W[dy] = sum_ky e^{-i ky dy} Y keep, for each complex pair
+//     (Z, conj Z), the real sums of c Re Z, s Im Z, c Im Z, s Re Z, which give both
+//     members; dy = 0 needs no phase;
+//   * the records are stored as three float4 planes transposed to [ky][kx], so the
+//     32 columns of a warp read 512 contiguous bytes per plane (coalesced), and each
+//     thread loads the next row while it computes the current one; rows advance
+//     without integer division.
+// One thread per fine-mesh column, one CTA per (transfer momentum, 64 columns, row range).
+// The flush and the partial layout are the ones of k_loops.cu, so the same
+// deterministic reduction kernel finishes the sum.
+#include "tufrg_internal.cuh"
+
+namespace tufrg {
+namespace {
+
+constexpr int MAXD = 9;
+constexpr int WARPS = 2;
+
+constexpr int RECF4 = 3;         // float4 planes per record
+
+struct Args2 {
+    const float4 *rec;       // [3][Lf][Lf] planes, index [j][ky][kx]:
+                             //   (rho00, Re rho01, Im rho01, e0), (e1, g0, g1, gp0), (gp1, -, -, -)
+    float2 *part;            // [Nq][n_part][ndx][ndyh][16]
+    int Lq, nc, Lf, ndx, ndyh;
+    int dxs[MAXD], dys[MAXD];
+    unsigned needed[MAXD];
+    int ky_chunks, ky_len;
+    float thr;
+};
+
+// (t1,t3,t2,t4) -> ab index of the compact loop (P: a=(t2,t1), b=(t4,t3); C: a=(t1,t2), b=(t3,t4))
+template <int WHICH>
+__host__ __device__ constexpr int abx(int t1, int t3, int t2, int t4)
+{
+    return WHICH == 0 ? ((t2 * 2 + t1) * 4 + t4 * 2 + t3) : ((t1 * 2 + t2) * 4 + t3 * 2 + t4);
+}
+
+template <int WHICH>
+__device__ __forceinline__ float pw(float e1, float g1, float gp1, float e2, float g2, float gp2, float thr)
+{
+    if (WHICH == 0) {
+        const float s = e1 + e2;
+        return fabsf(s) > thr ? -__fdividef(g1 + g2, s) : -0.5f * (gp1 + gp2);
+    } else {
+        const float d = e1 - e2;
+        return fabsf(d) > thr ? __fdividef(g1 - g2, d) : 0.5f * (gp1 + gp2);
+    }
+}
+
+template <int NDYH, int WHICH>
+__global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *ptab = reinterpret_cast<float2 *>(smem_raw);
+    float *red = reinterpret_cast<float *>(smem_raw + ((sizeof(float2) * a.Lf + 15) & ~size_t(15)));
+    const int Lf = a.Lf;
+    for (int n = threadIdx.x; n < Lf; n += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)n / (double)Lf, &sn, &cs);
+        ptab[n] = make_float2((float)cs, (float)-sn);   // e^{-2 pi i n / Lf}
+    }
+    __syncthreads();
+
+    constexpr int NT = 32 * WARPS;
+    const int s = blockIdx.x;
+    const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kx = blockIdx.y * NT + threadIdx.x;
+    const bool valid = kx < Lf;
+    const int kyc = blockIdx.z;
+    const int ky0 = kyc * a.ky_len;
+    const int ky1 = min(Lf, ky0 + a.ky_len);
+
+    float R0[4], P0y[6], P0z[6];
+    float Rc[NDYH > 1 ? NDYH - 1 : 1][4], Rs[NDYH > 1 ? NDYH - 1 : 1][4];
+    float Pcy[NDYH > 1 ? NDYH - 1 : 1][6], Psz[NDYH > 1 ? NDYH - 1 : 1][6];
+    float Pcz[NDYH > 1 ? NDYH - 1 : 1][6], Psy[NDYH > 1 ? NDYH - 1 : 1][6];
+#pragma unroll
+    for (int j = 0; j < 4; j++) R0[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; j++) { P0y[j] = 0.f; P0z[j] = 0.f; }
+#pragma unroll
+    for (int i = 0; i < NDYH - 1; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) { Rc[i][j] = 0.f; Rs[i][j] = 0.f; }
+#pragma unroll
+        for (int j = 0; j < 6; j++) { Pcy[i][j] = 0.f; Psz[i][j] = 0.f; Pcz[i][j] = 0.f; Psy[i][j] = 0.f; }
+    }
+
+    if (valid && ky0 < ky1) {
+        // columns of k1 and k2; rows step by +1 on the q side and by -1 on the s - q side
+        const int k1x = WHICH == 0 ? (sx - kx + Lf) % Lf : kx;
+        const int k2x = WHICH == 0 ? kx : (kx - sx + Lf) % Lf;
+        int k1y = WHICH == 0 ? ((sy - ky0) % Lf + Lf) % Lf : ky0;
+        int k2y = WHICH == 0 ? ky0 : ((ky0 - sy) % Lf + Lf) % Lf;
+        const size_t plane = (size_t)Lf * Lf;
+        const float4 *P0 = a.rec, *P1 = a.rec + plane, *P2 = a.rec + 2 * plane;
+        int o1 = k1y * Lf + k1x, o2 = k2y * Lf + k2x;        // offsets of the row being loaded
+        float4 n0 = __ldg(P0 + o1), n1 = __ldg(P1 + o1), n2 = __ldg(P2 + o1);
+        float4 m0 = __ldg(P0 + o2), m1 = __ldg(P1 + o2), m2 = __ldg(P2 + o2);
+        int pn[MAXD];
+#pragma unroll
+        for (int i = 1; i < NDYH; i++) pn[i] = (int)(((long)ky0 * a.dys[i]) % Lf);
+        const float sgn = WHICH == 0 ? 1.f : -1.f;
+        const int wrap = (Lf - 1) * Lf;
+        for (int ky = ky0; ky < ky1; ky++) {
+            const float4 a0 = n0, a1 = n1, a2 = n2, b0 = m0, b1 = m1, b2 = m2;
+            // next row: the q side moves by +Lf, the s - q side by -Lf (P), both +Lf (C), with wrap
+            if (WHICH == 0) { o1 = o1 >= Lf ? o1 - Lf : o1 + wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
+            else            { o1 = o1 < wrap ? o1 + Lf : o1 - wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
+            if (ky + 1 < ky1) {
+                n0 = __ldg(P0 + o1); n1 = __ldg(P1 + o1); n2 = __ldg(P2 + o1);
+                m0 = __ldg(P0 + o2); m1 = __ldg(P1 + o2); m2 = __ldg(P2 + o2);
+            }
+            // pair weights w[l1][l2]: l1 on k1, l2 on k2
+            const float e1[2] = {a0.w, a1.x}, g1[2] = {a1.y, a1.z}, gp1[2] = {a1.w, a2.x};
+            const float e2[2] = {b0.w, b1.x}, g2[2] = {b1.y, b1.z}, gp2[2] = {b1.w, b2.x};
+            float w[2][2];
+#pragma unroll
+            for (int l1 = 0; l1 < 2; l1++)
+#pragma unroll
+                for (int l2 = 0; l2 < 2; l2++) w[l1][l2] = pw<WHICH>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], a.thr);
+            // T^{l1} = w_{l1 1} 1 + (w_{l1 0} - w_{l1 1}) rho2'^0 ;  D = T^0 - T^1
+            const float A2 = b0.x, C2r = b0.y, C2i = sgn * b0.z;    // rho2' = rho2 (P) or conj(rho2) (C)
+            const float dw0 = w[0][0] - w[0][1], dw1 = w[1][0] - w[1][1];
+            const float T1_00 = fmaf(dw1, A2, w[1][1]), T1_11 = fmaf(dw1, 1.f - A2, w[1][1]);
+            const float T1r = dw1 * C2r, T1i = dw1 * C2i;
+            const float dd = dw0 - dw1, dd0 = w[0][1] - w[1][1];
+            const float D00 = fmaf(dd, A2, dd0), D11 = fmaf(dd, 1.f - A2, dd0);
+            const float Dr = dd * C2r, Di = dd * C2i;
+            // Y = 1 (x) T^1 + rho1^0 (x) D: 4 real and 6 complex independent entries
+            const float A1 = a0.x, B1 = 1.f - a0.x, C1r = a0.y, C1i = a0.z;
+            float X[4], Zy[6], Zz[6];
+            X[0] = fmaf(A1, D00, T1_00);    // Y[00][00]
+            X[1] = fmaf(A1, D11, T1_11);    // Y[00][11]
+            X[2] = fmaf(B1, D00, T1_00);    // Y[11][00]
+            X[3] = fmaf(B1, D11, T1_11);    // Y[11][11]
+            Zy[0] = fmaf(A1, Dr, T1r); Zz[0] = fmaf(A1, Di, T1i);   // Y[00][01]
+            Zy[1] = fmaf(B1, Dr, T1r); Zz[1] = fmaf(B1, Di, T1i);   // Y[11][01]
+            Zy[2] = C1r * D00; Zz[2] = C1i * D00;                   // Y[01][00]
+            Zy[3] = C1r * D11; Zz[3] = C1i * D11;                   // Y[01][11]
+            Zy[4] = C1r * Dr - C1i * Di; Zz[4] = C1r * Di + C1i * Dr;   // Y[01][01] = rho01 D01
+            Zy[5] = C1r * Dr + C1i * Di; Zz[5] = C1i * Dr - C1r * Di;   // Y[01][10] = rho01 conj(D01)
+            // row sums
+#pragma unroll
+            for (int j = 0; j < 4; j++) R0[j] += X[j];
+#pragma unroll
+            for (int j = 0; j < 6; j++) { P0y[j] += Zy[j]; P0z[j] += Zz[j]; }
+#pragma unroll
+            for (int i = 1; i < NDYH; i++) {
+                const float2 ph = ptab[pn[i]];
+                pn[i] += a.dys[i];
+                if (pn[i] >= Lf) pn[i] -= Lf;
+#pragma unroll
+                for (int j = 0; j < 4; j++) { Rc[i - 1][j] = fmaf(ph.x, X[j], Rc[i - 1][j]); Rs[i - 1][j] = fmaf(ph.y, X[j], Rs[i - 1][j]); }
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    Pcy[i - 1][j] = fmaf(ph.x, Zy[j], Pcy[i - 1][j]);
+                    Psz[i - 1][j] = fmaf(ph.y, Zz[j], Psz[i - 1][j]);
+                    Pcz[i - 1][j] = fmaf(ph.x, Zz[j], Pcz[i - 1][j]);
+                    Psy[i - 1][j] = fmaf(ph.y, Zy[j], Psy[i - 1][j]);
+                }
+            }
+        }
+    }
+
+    // ---- rebuild W[dy][ab] from the paired sums
+    constexpr int XR[4] = {abx<WHICH>(0, 0, 0, 0), abx<WHICH>(0, 0, 1, 1), abx<WHICH>(1, 1, 0, 0), abx<WHICH>(1, 1, 1, 1)};
+    constexpr int ZA[6] = {abx<WHICH>(0, 0, 0, 1), abx<WHICH>(1, 1, 0, 1), abx<WHICH>(0, 1, 0, 0),
+                           abx<WHICH>(0, 1, 1, 1), abx<WHICH>(0, 1, 0, 1), abx<WHICH>(0, 1, 1, 0)};
+    constexpr int ZB[6] = {abx<WHICH>(0, 0, 1, 0), abx<WHICH>(1, 1, 1, 0), abx<WHICH>(1, 0, 0, 0),
+                           abx<WHICH>(1, 0, 1, 1), abx<WHICH>(1, 0, 1, 0), abx<WHICH>(1, 0, 0, 1)};
+    float2 W[NDYH][16];
+#pragma unroll
+    for (int j = 0; j < 4; j++) W[0][XR[j]] = make_float2(R0[j], 0.f);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        W[0][ZA[j]] = make_float2(P0y[j], P0z[j]);
+        W[0][ZB[j]] = make_float2(P0y[j], -P0z[j]);
+    }
+#pragma unroll
+    for (int i = 1; i < NDYH; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) W[i][XR[j]] = make_float2(Rc[i - 1][j], Rs[i - 1][j]);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            W[i][ZA[j]] = make_float2(Pcy[i - 1][j] - Psz[i - 1][j], Pcz[i - 1][j] + Psy[i - 1][j]);
+            W[i][ZB[j]] = make_float2(Pcy[i - 1][j] + Psz[i - 1][j], Psy[i - 1][j] - Pcz[i - 1][j]);
+        }
+    }
+
+    // ---- flush: per distinct dx, multiply by e^{-i kx dx}, sum the warp through smem
+    constexpr int NV = 2 * NDYH * 16;
+    constexpr int PITCH = NV + 1;
+    float *buf = red + warp * 32 * PITCH;
+    const int n_part = gridDim.y * WARPS * gridDim.z;
+    const int p = (blockIdx.y * WARPS + warp) * gridDim.z + kyc;
+    for (int dxi = 0; dxi < a.ndx; dxi++) {
+        if (a.needed[dxi] == 0) continue;
+        const int n = (int)((((long)kx * a.dxs[dxi]) % Lf + Lf) % Lf);
+        const float2 phx = valid ? ptab[n] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NDYH; i++)
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                buf[lane * PITCH + 2 * (i * 16 + j)] = phx.x * W[i][j].x - phx.y * W[i][j].y;
+                buf[lane * PITCH + 2 * (i * 16 + j) + 1] = phx.x * W[i][j].y + phx.y * W[i][j].x;
+            }
+        __syncwarp();
+        for (int v = lane; v < NV; v += 32) {
+            float acc = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < 32; r++) acc += buf[r * PITCH + v];
+            const int i = v / 32, j = (v / 2) % 16, re = v & 1;
+            if ((a.needed[dxi] >> i) & 1u) {
+                const size_t o = ((((size_t)s * n_part + p) * a.ndx + dxi) * a.ndyh + i) * 16 + j;
+                reinterpret_cast<float *>(a.part)[2 * o + re] = acc;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Per-temperature record of one fine k: band-0 projector and the Fermi data of both bands, FP32.
+__global__ void rec_kernel(const double *E, const double2 *U, int Nk, int Lf, double mu, double T, float4 *rec)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nk) return;
+    float e[2], g[2], gp[2];
+#pragma unroll
+    for (int l = 0; l < 2; l++) {
+        const double x = (E[2 * k + l] - mu) / T, ax = fabs(x);
+        const double z = exp(-ax);
+        const double h = z / ((1.0 + z) * (1.0 + z));
+        e[l] = (float)(E[2 * k + l] - mu);
+        g[l] = (float)(x / T * h);
+        gp[l] = (float)(h / (T * T) * (1.0 - ax * (1.0 - z) / (1.0 + z)));
+    }
+    // rho^0 = U_{.0} U*_{.0}: rho00 = |U_00|^2, rho01 = U_00 conj(U_10)
+    const double2 u0 = U[(size_t)k * 4 + 0], u1 = U[(size_t)k * 4 + 2];
+    const int kx = k / Lf, ky = k % Lf;
+    const size_t t = (size_t)ky * Lf + kx, plane = (size_t)Lf * Lf;
+    rec[t] = make_float4((float)(u0.x * u0.x + u0.y * u0.y), (float)(u0.x * u1.x + u0.y * u1.y),
+                         (float)(u0.y * u1.x - u0.x * u1.y), e[0]);
+    rec[plane + t] = make_float4(e[1], g[0], g[1], gp[0]);
+    rec[2 * plane + t] = make_float4(gp[1], 0.f, 0.f, 0.f);
+}
+
+template <int NDYH, int WHICH>
+cudaError_t launch2(tufrg_model *m, const Args2 &a)
+{
+    dim3 grid(m->Nq, (m->Lf + 32 * WARPS - 1) / (32 * WARPS), a.ky_chunks);
+    const size_t flush = sizeof(float) * WARPS * 32 * (2 * NDYH * 16 + 1);
+    const size_t smem = ((sizeof(float2) * m->Lf + 15) & ~size_t(15)) + flush;
+    auto kern = loops2_kernel<NDYH, WHICH>;
+    if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PhaseScope ps(m, PH_LOOPS);
+    kern<<<grid, 32 * WARPS, smem, m->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Resident CTAs per SM of the instantiation this model launches (occupancy API).
+int loops2_blocks_per_sm(const tufrg_model *m)
+{
+    int ndyh = 0;
+    for (int v : m->dys) ndyh += v >= 0;
+    const size_t smem = ((sizeof(float2) * m->Lf + 15) & ~size_t(15)) + sizeof(float) * WARPS * 32 * (2 * ndyh * 16 + 1);
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ndyh == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<1, 0>, 32 * WARPS, smem);
+    if (ndyh == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<2, 0>, 32 * WARPS, smem);
+    if (ndyh == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<3, 0>, 32 * WARPS, smem);
+    return (e == cudaSuccess && n > 0) ? n : 4;
+}
+
+bool loops2_supported(const tufrg_model *m)
+{
+    int ndyh = 0;
+    for (int v : m->dys) ndyh += v >= 0;
+    return m->ns == 2 && m->precision == TUFRG_SPLIT32 && ndyh <= 3 && (int)m->dxs.size() <= MAXD;
+}
+
+cudaError_t launch_loop_records(tufrg_model *m, double T)
+{
+    PhaseScope ps(m, PH_FERMI);
+    rec_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->d_U, m->Nk, m->Lf, m->mu, T, m->d_rec);
+    return cudaGetLastError();
+}
+
+// Loop sums of the channels in channel_mask into the partial buffer (no reduction).
+cudaError_t launch_loops2(tufrg_model *m, int ch)
+{
+    const LoopPlan &pl = m->plan;
+    Args2 a{};
+    a.rec = m->d_rec;
+    a.part = reinterpret_cast<float2 *>(m->d_part);
+    a.Lq = m->Lq; a.nc = m->nc; a.Lf = m->Lf;
+    a.ndx = (int)m->dxs.size();
+    int ndyh = 0;
+    for (int v : m->dys)
+        if (v >= 0) a.dys[ndyh++] = v;
+    a.ndyh = ndyh;
+    for (int i = 0; i < a.ndx; i++) {
+        a.dxs[i] = m->dxs[i];
+        a.needed[i] = 0;
+        for (int j = 0; j < ndyh; j++) {
+            const int dx = m->dxs[i], dy = a.dys[j];
+            bool in = false;
+            for (int d = 0; d < m->nd; d++) in |= (m->deltas[2 * d] == dx && m->deltas[2 * d + 1] == dy);
+            if (in && (dy > 0 || dx >= 0)) a.needed[i] |= 1u << j;
+        }
+    }
+    a.ky_chunks = pl.ky_chunks;
+    a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
+    a.thr = (float)(1e-2 * m->cur_T);
+    switch (ndyh) {
+    case 1: return ch == 0 ? launch2<1, 0>(m, a) : launch2<1, 1>(m, a);
+    case 2: return ch == 0 ? launch2<2, 0>(m, a) : launch2<2, 1>(m, a);
+    case 3: return ch == 0 ? launch2<3, 0>(m, a) : launch2<3, 1>(m, a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace tufrg

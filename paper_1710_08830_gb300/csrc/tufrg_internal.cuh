@@ -94,6 +94,12 @@ struct tufrg_model {
     double2 *d_A = nullptr;         // [2][Nq][M][M] projected vertex
     float2 *d_A32 = nullptr;        // [2][Nq][M][M] (split path)
     double2 *d_T = nullptr;         // [Nq][M][M] GEMM intermediate (large M)
+    float4 *d_rec = nullptr;        // [Nk][4] split-path loop records (projectors + Fermi data)
+    float2 *d_Xr32 = nullptr;       // [2][ncls][M][M] Fourier transforms (split path)
+    float2 *d_ph32 = nullptr;       // [Nq][nph] phase table (split path)
+    void *d_dftpart = nullptr;      // Fourier-transform partial sums (scratch)
+    int dft_nsplit = 1;             // transfer-mesh slices of the Fourier transform
+    int max_terms = 0;              // largest gather-term list of one (R, R') pair
     unsigned long long *d_amax = nullptr;   // [4] reductions (max|A|, argmax, err)
     double *d_red = nullptr;        // density reduction scratch
     // flow work buffers
@@ -127,6 +133,11 @@ cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn,
                             double2 *const *k, int nk, size_t n, double atol, double rtol);
 cudaError_t launch_amax_locate(tufrg_model *m, const double2 *d_A, size_t n, double amax);
 LoopPlan plan_loops(const tufrg_model *m);
+int dft_plan_nsplit(const tufrg_model *m);
+bool loops2_supported(const tufrg_model *m);
+int loops2_blocks_per_sm(const tufrg_model *m);
+cudaError_t launch_loop_records(tufrg_model *m, double T);
+cudaError_t launch_loops2(tufrg_model *m, int ch);
 
 enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_N = 7 };
 
