@@ -59,7 +59,8 @@ typedef enum {
     TUFRG_ENOTCONV = 5,    /* step size underflow or step limit in the flow */
     TUFRG_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
     TUFRG_EFALLBACK = 7,   /* surrogate rejected, direct loops used (informational) */
-    TUFRG_ENOTSUP = 8      /* configuration not supported by this build */
+    TUFRG_ENOTSUP = 8,     /* configuration not supported by this build */
+    TUFRG_ETOOBIG = 9      /* problem larger than the fixed scratch of tufrg_loops_noalloc */
 } tufrg_status;
 
 enum { TUFRG_FP64 = 0, TUFRG_SPLIT32 = 1 };
@@ -161,6 +162,44 @@ tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int c
  * max|A| > opts->stop.  d_state_out (may be NULL): [2][Nq][M][M] complex, the
  * last accepted state.  Errors: TUFRG_ENONFINITE, TUFRG_ENOTCONV, ... */
 tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_state_out, tufrg_flow_result *res);
+
+/* Loop k-sum that allocates nothing (no counterpart in the paper; an interface addition).
+ *
+ * For callers that cannot call cudaMalloc: code that runs where device allocation
+ * is forbidden or must go through a host framework's own allocator, and code that
+ * must not change the device's memory footprint while it runs.  It computes the
+ * same compact loops as tufrg_loops on a TUFRG_SPLIT32 model (N_s = 2, FP32 sums,
+ * bond sets whose non-negative bond-difference y components number at most 3, e.g.
+ * 5 or 9 bonds), but takes every input from the caller and keeps its scratch (the
+ * per-k records and the partial sums) in one file-scope device array of
+ * TUFRG_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ *   Lq, nc          coarse mesh Lq x Lq, nc fine points per cell (Lf = Lq*nc)
+ *   d_E             device [Lf*Lf][2] band energies E_l(k), ascending, k = kx*Lf + ky
+ *   d_U             device [Lf*Lf][2][2] complex eigenvectors (row orbital, column band),
+ *                   e.g. as returned by tufrg_bands
+ *   mu, T           chemical potential and temperature (T > 0)
+ *   n_ff, h_ffR     host [n_ff][2] bonds, ff_R[0] = (0,0), as in tufrg_model_desc
+ *   channel_mask    TUFRG_CH_P | TUFRG_CH_C
+ *   d_loops         device [2][Lq*Lq][n_delta][4][4] complex output, layout of tufrg_loops;
+ *                   channels outside the mask are left untouched
+ *   cuda_stream     stream for all work (NULL = legacy default stream)
+ *
+ * The scratch must hold Lf*Lf*48 bytes of records plus the partial sums of one
+ * channel, Lq*Lq * 2*ceil(Lf/64) * n_dx * n_dy * 128 bytes (n_dx distinct x and n_dy
+ * non-negative y components of the bond differences); a larger problem returns
+ * TUFRG_ETOOBIG before any work.  The first call on each device looks up the
+ * device address of the scratch with cudaGetSymbolAddress (the device must be
+ * current); make that first call before any stream capture.  Calls share the
+ * scratch: calls that overlap on the GPU (other streams, other threads) race and
+ * give wrong results.  Nothing in the scratch needs to start at zero: every record
+ * and every partial that is read is first written by the same call.
+ * Errors: TUFRG_EINVAL (bad arguments), TUFRG_ENOTSUP (configuration), TUFRG_ETOOBIG,
+ * TUFRG_ECUDA (a launch or the symbol look-up failed). */
+#define TUFRG_NOALLOC_SCRATCH_BYTES (16u << 20)
+tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, const double *d_U, double mu, double T, int n_ff,
+                                 const int *h_ffR, int channel_mask, void *d_loops, void *cuda_stream);
 
 /* Optional CUDA-event timing on the model's stream (used by the benchmark).
  * tufrg_timing_begin resets the counters and starts recording; every later

@@ -15,7 +15,7 @@ _lock = threading.Lock()
 _lib = None
 
 STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA", 4: "TUFRG_ENONFINITE",
-          5: "TUFRG_ENOTCONV", 6: "TUFRG_ETIMEOUT", 7: "TUFRG_EFALLBACK", 8: "TUFRG_ENOTSUP"}
+          5: "TUFRG_ENOTCONV", 6: "TUFRG_ETIMEOUT", 7: "TUFRG_EFALLBACK", 8: "TUFRG_ENOTSUP", 9: "TUFRG_ETOOBIG"}
 
 FP64, SPLIT32 = 0, 1
 CH_P, CH_C = 1, 2
@@ -74,6 +74,8 @@ def lib():
             L.tufrg_rhs.argtypes = [vp, d, vp, i, vp]
             L.tufrg_rhs_host.argtypes = [vp, d, vp, i, vp]
             L.tufrg_flow.argtypes = [vp, C.POINTER(FlowOpts), vp, C.POINTER(FlowResult)]
+            L.tufrg_loops_noalloc.argtypes = [i, i, vp, vp, d, d, i, vp, i, vp, vp]
+            L.tufrg_loops_noalloc.restype = C.c_int
             L.tufrg_timing_begin.argtypes = [vp]
             L.tufrg_timing_end.argtypes = [vp, vp, i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for fn in ("tufrg_init_model", "tufrg_dims", "tufrg_deltas", "tufrg_gather_table", "tufrg_bands",
@@ -87,4 +89,4 @@ def lib():
 # names every header in include/ declares; the CPU test checks the exports against the headers
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
-           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end")
+           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc")

@@ -20,6 +20,8 @@
 // One thread per fine-mesh column, one CTA per (transfer momentum, 64 columns, row range).
 // The flush and the partial layout are the ones of k_loops.cu, so the same
 // deterministic reduction kernel finishes the sum.
+#include <cmath>
+
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -337,3 +339,153 @@ cudaError_t launch_loops2(tufrg_model *m, int ch)
 }
 
 }  // namespace tufrg
+
+// ---------------------------------------------------------------------------------
+// Loop k-sum without allocation: the same kernels with their scratch in a static array.
+// ---------------------------------------------------------------------------------
+#include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+namespace tufrg {
+namespace {
+
+// Records of one fine mesh plus the partial sums of one channel; see tufrg.h.
+__device__ __align__(256) unsigned char g_noalloc_scratch[TUFRG_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAXND = 64;
+constexpr int NOALLOC_MAXDEV = 64;
+
+struct NoallocTables {
+    int nd;
+    int d[2 * NOALLOC_MAXND];      // sorted bond differences (dx, dy)
+    int slot[NOALLOC_MAXND];       // dxi * ndyh + dyi of the half-plane representative
+};
+
+// Fixed-order sum of the partials, scaled by 1/Nk; writes both Hermitian halves (FP64).
+__global__ void noalloc_reduce_kernel(const float2 *part, int n_part, int ndx, int ndyh, NoallocTables t, int Nq,
+                                      double inv_nk, double2 *out)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)Nq * t.nd * 16) return;
+    const int ab = idx % 16;
+    const int d = (idx / 16) % t.nd;
+    const int s = (int)(idx / (16 * (size_t)t.nd));
+    const int dx = t.d[2 * d], dy = t.d[2 * d + 1];
+    const bool half = dy > 0 || (dy == 0 && dx >= 0);
+    const int src_ab = half ? ab : (ab % 4) * 4 + ab / 4;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < n_part; p++) {
+        const float2 v = part[(((size_t)s * n_part + p) * ndx * ndyh + t.slot[d]) * 16 + src_ab];
+        re += (double)v.x;
+        im += (double)v.y;
+    }
+    out[idx] = make_double2(re * inv_nk, (half ? im : -im) * inv_nk);
+}
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAXDEV] = {};
+
+}  // namespace
+}  // namespace tufrg
+
+extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, const double *d_U, double mu, double T,
+                                            int n_ff, const int *h_ffR, int channel_mask, void *d_loops,
+                                            void *cuda_stream)
+{
+    using namespace tufrg;
+    if (Lq < 2 || nc < 1 || (long)Lq * nc > 4096 || !d_E || !d_U || !h_ffR || !d_loops || n_ff < 1)
+        return TUFRG_EINVAL;
+    if (!(T > 0) || !std::isfinite(T) || !std::isfinite(mu) || (channel_mask & ~3)) return TUFRG_EINVAL;
+    if (h_ffR[0] != 0 || h_ffR[1] != 0) return TUFRG_EINVAL;
+    const int Lf = Lq * nc;
+    const size_t Nk = (size_t)Lf * Lf;
+    const int Nq = Lq * Lq;
+    // bond differences (sorted) and their separable parts, as the model builds them
+    std::vector<std::pair<int, int>> dl;
+    for (int i = 0; i < n_ff; i++)
+        for (int j = 0; j < n_ff; j++) dl.emplace_back(h_ffR[2 * i] - h_ffR[2 * j], h_ffR[2 * i + 1] - h_ffR[2 * j + 1]);
+    std::sort(dl.begin(), dl.end());
+    dl.erase(std::unique(dl.begin(), dl.end()), dl.end());
+    std::vector<int> xs, ys;
+    for (auto &p : dl) { xs.push_back(p.first); ys.push_back(p.second); }
+    std::sort(xs.begin(), xs.end()); xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
+    std::sort(ys.begin(), ys.end()); ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
+    std::vector<int> dyh;
+    for (int v : ys) if (v >= 0) dyh.push_back(v);
+    const int ndx = (int)xs.size(), ndyh = (int)dyh.size(), nd = (int)dl.size();
+    if (ndyh < 1 || ndyh > 3 || ndx > MAXD || nd > NOALLOC_MAXND) return TUFRG_ENOTSUP;
+    // scratch budget: records, then the partials of one channel (one row range per column)
+    const int ctas_x = (Lf + 32 * WARPS - 1) / (32 * WARPS);
+    const int n_part = ctas_x * WARPS;
+    const size_t rec_bytes = ((Nk * RECF4 * sizeof(float4)) + 255) & ~size_t(255);
+    const size_t part_bytes = (size_t)Nq * n_part * ndx * ndyh * 16 * sizeof(float2);
+    if (rec_bytes + part_bytes > (size_t)TUFRG_NOALLOC_SCRATCH_BYTES) return TUFRG_ETOOBIG;
+    // device address of the static scratch, looked up once per device (the device must be current)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAXDEV) return TUFRG_ECUDA;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TUFRG_ECUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    float4 *rec = reinterpret_cast<float4 *>(base);
+    float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(base) + rec_bytes);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+    rec_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d_E, reinterpret_cast<const double2 *>(d_U), (int)Nk, Lf,
+                                                               mu, T, rec);
+    if (cudaGetLastError() != cudaSuccess) return TUFRG_ECUDA;
+    Args2 a{};
+    a.rec = rec;
+    a.part = part;
+    a.Lq = Lq; a.nc = nc; a.Lf = Lf; a.ndx = ndx; a.ndyh = ndyh;
+    for (int j = 0; j < ndyh; j++) a.dys[j] = dyh[j];
+    for (int i = 0; i < ndx; i++) {
+        a.dxs[i] = xs[i];
+        a.needed[i] = 0;
+        for (int j = 0; j < ndyh; j++) {
+            const bool in = std::binary_search(dl.begin(), dl.end(), std::make_pair(xs[i], dyh[j]));
+            if (in && (dyh[j] > 0 || xs[i] >= 0)) a.needed[i] |= 1u << j;
+        }
+    }
+    a.ky_chunks = 1;
+    a.ky_len = Lf;
+    a.thr = (float)(1e-2 * T);
+    NoallocTables t{};
+    t.nd = nd;
+    for (int k = 0; k < nd; k++) {
+        int dx = dl[k].first, dy = dl[k].second;
+        t.d[2 * k] = dx;
+        t.d[2 * k + 1] = dy;
+        if (!(dy > 0 || (dy == 0 && dx >= 0))) { dx = -dx; dy = -dy; }
+        const int xi = (int)(std::find(xs.begin(), xs.end(), dx) - xs.begin());
+        const int yi = (int)(std::find(dyh.begin(), dyh.end(), dy) - dyh.begin());
+        t.slot[k] = xi * ndyh + yi;
+    }
+    const size_t flush = sizeof(float) * WARPS * 32 * (2 * ndyh * 16 + 1);
+    const size_t smem = ((sizeof(float2) * Lf + 15) & ~size_t(15)) + flush;
+    const dim3 grid(Nq, ctas_x, 1);
+    const size_t per = (size_t)Nq * nd * 16;
+    for (int ch = 0; ch < 2; ch++) {
+        if (!((channel_mask >> ch) & 1)) continue;
+        void (*kern)(Args2) = nullptr;
+        if (ndyh == 1) kern = ch == 0 ? loops2_kernel<1, 0> : loops2_kernel<1, 1>;
+        if (ndyh == 2) kern = ch == 0 ? loops2_kernel<2, 0> : loops2_kernel<2, 1>;
+        if (ndyh == 3) kern = ch == 0 ? loops2_kernel<3, 0> : loops2_kernel<3, 1>;
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return TUFRG_ECUDA;
+        kern<<<grid, 32 * WARPS, smem, st>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return TUFRG_ECUDA;
+        noalloc_reduce_kernel<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(
+            part, n_part, ndx, ndyh, t, Nq, 1.0 / (double)Nk, reinterpret_cast<double2 *>(d_loops) + ch * per);
+        if (cudaGetLastError() != cudaSuccess) return TUFRG_ECUDA;
+    }
+    return TUFRG_OK;
+}
