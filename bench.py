@@ -106,13 +106,13 @@ def loop_traffic_record():
     """DRAM bytes per loop-kernel launch from the committed ncu summary, if it matches the current source."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "loops_traffic.json")
-    src = os.path.join(ROOT, "paper_1710_08830_gb300", "csrc", "k_loops.cu")
+    src = os.path.join(ROOT, "paper_1710_08830_gb300", "csrc", "k_loops2.cu")
     if not os.path.exists(p):
         return None, None
     with open(p) as f:
         rec = json.load(f)
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("k_loops_sha256_16") != h:
+    if rec.get("k_loops2_sha256_16") != h:
         return None, rec
     return rec, rec
 
@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-flow", action="store_true", help="skip the time-to-Lambda_c measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-rhs", type=int, default=0,
+                    help="only evaluate this many split-precision right-hand sides on a seeded state (for ncu)")
+    ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
@@ -181,6 +184,16 @@ def main():
     from paper_1710_08830_gb300.api import FP64, SPLIT32, Model
 
     torch.cuda.set_device(local)
+    if args.profile_rhs > 0:
+        # a short, fixed launch sequence for profilers: model set-up, then N right-hand sides
+        spec = inputs.rashba_q24_k8_ff9(0)
+        m = Model(spec, SPLIT32 if args.profile_precision == "split" else FP64)
+        st = torch.from_numpy(inputs.random_state(spec, seed=1, scale=0.2)).cuda()
+        for _ in range(args.profile_rhs):
+            m.rhs(T_BENCH, st)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_rhs": args.profile_rhs, "workload": WORKLOAD}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -290,7 +303,7 @@ def main():
     loop_ms_avg = phase_ms["loops"] / max(1, loop_launches)
     achieved = flops_per_launch / (loop_ms_avg * 1e-3) / 1e12
     trec, _ = loop_traffic_record()
-    roofline = {"bound": "alu", "kernel": "loops_ns2_kernel<float> (split-precision loop k-sum)",
+    roofline = {"bound": "alu", "kernel": "loops2_kernel (split-precision two-band loop k-sum)",
                 "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": (trec["dram_bytes_per_launch"] if trec else None),
                 "peak_source": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
