@@ -92,6 +92,11 @@ void build_loop_tables(tufrg_model *m)
         const int yi = (int)(std::find(dyh.begin(), dyh.end(), dy) - dyh.begin());
         m->dslot[k] = xi * ndyh + yi;
     }
+    m->dpartner.assign(m->nd, -1);
+    for (int k = 0; k < m->nd; k++) {
+        std::pair<int, int> v(-d[k].first, -d[k].second);
+        m->dpartner[k] = (int)(std::lower_bound(d.begin(), d.end(), v) - d.begin());
+    }
     m->dij.assign(m->nff * m->nff, 0);
     for (int i = 0; i < m->nff; i++)
         for (int j = 0; j < m->nff; j++) {
@@ -198,7 +203,7 @@ void release(tufrg_model *m)
                     m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
-                    m->d_ph32, m->d_dftpart};
+                    m->d_ph32, m->d_dftpart, m->d_dpartner};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -234,7 +239,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     *out = m;   // so that tufrg_last_error works even when set-up fails
     const tufrg_model_desc &d = *desc;
     if (d.n_s < 1 || d.n_s > 8) return fail(m, TUFRG_EINVAL, "n_s must be in [1, 8]");
-    if (d.n_s != 2) return fail(m, TUFRG_ENOTSUP, "this build's loop kernels support n_s = 2");
+    if (d.n_s != 2 && d.n_s != 4 && d.n_s != 6) return fail(m, TUFRG_ENOTSUP, "this build supports n_s = 2, 4, 6");
     if (d.n_hop < 1 || !d.hop_R || !d.hop_t) return fail(m, TUFRG_EINVAL, "empty hopping list");
     if (!d.V0) return fail(m, TUFRG_EINVAL, "V0 is NULL");
     if (d.n_ff < 1 || !d.ff_R) return fail(m, TUFRG_EINVAL, "empty bond set");
@@ -289,6 +294,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     CK(upload(&m->d_V0, V02, m->stream), "upload V0");
     CK(upload(&m->d_deltas, m->deltas, m->stream), "upload bond tables");
     CK(upload(&m->d_dslot, m->dslot, m->stream), "upload bond tables");
+    CK(upload(&m->d_dpartner, m->dpartner, m->stream), "upload bond tables");
     CK(upload(&m->d_dij, m->dij, m->stream), "upload bond tables");
     for (int ch = 0; ch < 2; ch++) {
         CK(upload(&m->d_gofs[ch], m->gofs[ch], m->stream), "upload gather tables");
@@ -323,6 +329,13 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
     m->part_bytes = (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
+    if (ns != 2) {
+        if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
+        m->part_bytes = (size_t)m->Nq * m->nd * ns4 * sizeof(double2);   // FP64 accumulators of one channel
+    }
+    if (m->M > 64)
+        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_T), (size_t)m->Nq * M2 * (split ? sizeof(float2) : sizeof(double2))),
+           "cudaMalloc product scratch");
     CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
     CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
     CK(cudaMalloc(&m->d_dftpart, (size_t)m->dft_nsplit * 2 * m->ncls * M2 * (split ? sizeof(float2) : sizeof(double2))),

@@ -305,7 +305,7 @@ LoopPlan plan_loops(const tufrg_model *m)
 
 cudaError_t launch_loops(tufrg_model *m, int channel_mask)
 {
-    if (m->ns != NS) return cudaErrorNotSupported;
+    if (m->ns != NS) return loops_gen_supported(m) ? launch_loops_gen(m, channel_mask) : cudaErrorNotSupported;
     const LoopPlan &pl = m->plan;
     const int ndx = (int)m->dxs.size();
     int ndyh = 0;

@@ -65,7 +65,7 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out)
 {
     const int M = m->M;
-    if (M > 64) return cudaErrorNotSupported;
+    if (M > 64) return launch_vlv_large(m, d_A, channel_mask, scale, d_out);
     const int ns2 = m->ns * m->ns;
     dim3 grid(m->Nq, 2);
     const int threads = 256;

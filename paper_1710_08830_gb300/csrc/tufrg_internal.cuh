@@ -60,6 +60,7 @@ struct tufrg_model {
     int nd = 0;
     std::vector<int> dxs, dys;      // distinct dx / dy values (sorted)
     std::vector<int> dslot;         // [nd] see d_dslot
+    std::vector<int> dpartner;      // [nd] index of -delta
     std::vector<int> dij;           // [nff][nff] -> delta index of R1 - R2
     std::vector<int> cls;           // [ncls][2] bond classes mod Lq used by projections
     int ncls = 0;
@@ -77,6 +78,7 @@ struct tufrg_model {
     tufrg::FermiEntry32 *d_ft32 = nullptr;  // [Nk][ns]
     int *d_dslot = nullptr;         // [nd] partial slot (dxi * ndyh + dyi) of the half-plane partner
     int *d_deltas = nullptr;        // [nd][2]
+    int *d_dpartner = nullptr;      // [nd] index of -delta
     int *d_hopR = nullptr;          // [nhop][2]
     double2 *d_hopt = nullptr;      // [nhop][ns][ns]
     double cur_T = 0.0;             // temperature of the current Fermi tables
@@ -136,6 +138,9 @@ LoopPlan plan_loops(const tufrg_model *m);
 int dft_plan_nsplit(const tufrg_model *m);
 bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
+bool loops_gen_supported(const tufrg_model *m);
+cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
+cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out);
 cudaError_t launch_loop_records(tufrg_model *m, double T);
 cudaError_t launch_loops2(tufrg_model *m, int ch);
 

@@ -269,3 +269,65 @@ def test_invalid_temperature_is_rejected():
     with pytest.raises(api.TufrgError) as e:
         m.rhs(-1.0, m.zeros_state())
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ N_s = 6: three orbitals with atomic SOC
+
+T2G = {
+    "t2g_ff1_Lf8": lambda: inputs.t2g_soc(seed=1, Lq=4, nc=2, n_ff=1, filling=4.0, T_mu=0.05),          # M = 36
+    "t2g_ff5_Lf8": lambda: inputs.t2g_soc(seed=2, Lq=4, nc=2, n_ff=5, filling=4.0, T_mu=0.05),          # M = 180
+    "t2g_ff9_Lf10": lambda: inputs.t2g_soc(seed=3, Lq=5, nc=2, n_ff=9, filling=4.0, T_mu=0.05),         # M = 324
+}
+
+
+@pytest.mark.parametrize("case", list(T2G))
+def test_t2g_bands_and_mu(case):
+    api = _api()
+    spec = T2G[case]()
+    m = api.Model(spec, api.FP64)
+    o = oracle.Oracle(spec)
+    E, U = m.bands()
+    E, U = E.cpu().numpy(), U.cpu().numpy()
+    assert np.abs(E - o.E).max() < 1e-12
+    assert np.abs(np.einsum("kji,kjl->kil", U.conj(), U) - np.eye(6)).max() < 1e-12
+    assert abs(m.mu - o.mu) < 1e-11
+
+
+@pytest.mark.parametrize("case", list(T2G))
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_t2g_loops(case, prec):
+    api = _api()
+    spec = T2G[case]()
+    m = api.Model(spec, getattr(api, prec))
+    o = oracle.Oracle(spec)
+    L = m.loops(0.15).cpu().numpy()
+    for ch in (0, 1):
+        ref = o.loops(0.15, ch)
+        assert rel(L[ch], ref) < (TOL64 if prec == "FP64" else 2e-5), (ch, rel(L[ch], ref))
+
+
+@pytest.mark.parametrize("case", list(T2G))
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_t2g_rhs(case, prec):
+    api = _api()
+    spec = T2G[case]()
+    m = api.Model(spec, getattr(api, prec))
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=13, scale=0.15)
+    d = m.rhs(0.2, st).cpu().numpy()
+    ref, _ = o.rhs(0.2, st, 3)
+    assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_t2g_full_size_sampled_loops(prec):
+    """The 32x32 / 6x6-per-cell t2g workload (N_s = 6, M = 324): loops at sampled transfer momenta."""
+    api = _api()
+    spec = inputs.t2g_q32_k6_ff9(0)
+    m = api.Model(spec, getattr(api, prec))
+    o = oracle.Oracle(spec, mu=m.mu)
+    L = m.loops(0.1).cpu().numpy()
+    qs = [0, 33, 517]
+    for ch in (0, 1):
+        ref = o.loops_at(0.1, ch, qs)
+        assert rel(L[ch][qs], ref) < (TOL64 if prec == "FP64" else 2e-5)
