@@ -332,6 +332,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "Lq": spec.Lq, "nc": spec.nc, "Nq": spec.Nq, "Nk": spec.Nk,
                        "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH, "precision": "split (FP32 loop sums, FP64 state)",
+                       "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},
             "split_vs_fp64_maxrel": err_split,
             "fp64_gpu": {"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate},

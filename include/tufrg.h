@@ -63,7 +63,12 @@ typedef enum {
     TUFRG_ETOOBIG = 9      /* problem larger than the fixed scratch of tufrg_loops_noalloc */
 } tufrg_status;
 
+/* TUFRG_FP64: every step in FP64.  TUFRG_SPLIT32: FP32 loop sums, FP32 Fourier transform and gathers,
+ * FP32-accurate products; the state and its update stay FP64. */
 enum { TUFRG_FP64 = 0, TUFRG_SPLIT32 = 1 };
+/* Backend of the V.L.V products on the split path: tensor cores (tcgen05, 3xTF32, FP32 accumulation in
+ * tensor memory) or FP32 CUDA cores; AUTO times both on the model's sizes at init and keeps the faster. */
+enum { TUFRG_PRODUCTS_AUTO = 0, TUFRG_PRODUCTS_TC = 1, TUFRG_PRODUCTS_SIMT = 2 };
 enum { TUFRG_CH_P = 1, TUFRG_CH_C = 2 };
 
 typedef struct tufrg_model tufrg_model;   /* opaque; owns all of its device memory */
@@ -82,7 +87,8 @@ typedef struct {
     const int *ff_R;       /* [n_ff][2], ff_R[0] must be (0,0), distinct modulo Lq */
     int Lq;                /* coarse transfer mesh Lq x Lq (>= 2) */
     int nc;                /* fine points per coarse cell per direction (>= 1) */
-    int precision;         /* TUFRG_FP64 or TUFRG_SPLIT32 (FP32 loop sums, FP32/TF32 products) */
+    int precision;         /* TUFRG_FP64 or TUFRG_SPLIT32 (see above) */
+    int products;          /* TUFRG_PRODUCTS_AUTO / _TC / _SIMT (split path only) */
 } tufrg_model_desc;
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
@@ -120,7 +126,12 @@ void tufrg_free(tufrg_model *m);
 const char *tufrg_last_error(const tufrg_model *m);
 
 /* Sizes: Nq, M, n_delta (loop bond differences), Nk and the chemical potential in use. */
+/* (tufrg_model_info below also reports the products backend chosen at init.) */
 tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int *Nk, double *mu);
+
+/* Products backend in use on the split path (TUFRG_PRODUCTS_TC or _SIMT; _SIMT for FP64 models)
+ * and, when AUTO chose it, the two measured times in milliseconds (else -1). */
+tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt);
 
 /* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */
 tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out);

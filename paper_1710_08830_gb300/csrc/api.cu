@@ -203,7 +203,7 @@ void release(tufrg_model *m)
                     m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
-                    m->d_ph32, m->d_dftpart, m->d_dpartner};
+                    m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -247,6 +247,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if (d.Lq < 2 || d.nc < 1) return fail(m, TUFRG_EINVAL, "Lq >= 2 and nc >= 1 required");
     if ((long)d.Lq * d.nc > 4096) return fail(m, TUFRG_EINVAL, "fine mesh too large");
     if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
+    if (d.products < TUFRG_PRODUCTS_AUTO || d.products > TUFRG_PRODUCTS_SIMT) return fail(m, TUFRG_EINVAL, "unknown products backend");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
@@ -285,7 +286,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
 
     // ---- device memory
     const size_t Nk = m->Nk, ns2 = (size_t)ns * ns, ns4 = ns2 * ns2, M2 = (size_t)m->M * m->M;
-    const bool split = m->precision == TUFRG_SPLIT32;
+    const bool split = m->precision != TUFRG_FP64;
     std::vector<double2> hopt2((size_t)m->nhop * ns2), V02(ns4);
     for (size_t i = 0; i < hopt2.size(); i++) hopt2[i] = make_double2(m->hopt[2 * i], m->hopt[2 * i + 1]);
     for (size_t i = 0; i < V02.size(); i++) V02[i] = make_double2(m->V0[2 * i], m->V0[2 * i + 1]);
@@ -333,9 +334,12 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
         m->part_bytes = (size_t)m->Nq * m->nd * ns4 * sizeof(double2);   // FP64 accumulators of one channel
     }
-    if (m->M > 64)
+    m->products = split ? (d.products == TUFRG_PRODUCTS_AUTO ? TUFRG_PRODUCTS_TC : d.products) : TUFRG_PRODUCTS_SIMT;
+    if (m->M > 64 || split)
         CK(cudaMalloc(reinterpret_cast<void **>(&m->d_T), (size_t)m->Nq * M2 * (split ? sizeof(float2) : sizeof(double2))),
            "cudaMalloc product scratch");
+    CK(dalloc(&m->d_err, 1), "cudaMalloc error flag");
+    CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "zero error flag");
     CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
     CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
     CK(cudaMalloc(&m->d_dftpart, (size_t)m->dft_nsplit * 2 * m->ncls * M2 * (split ? sizeof(float2) : sizeof(double2))),
@@ -365,6 +369,48 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         m->mu = d.mu;
     }
     CK(cudaStreamSynchronize(m->stream), "init sync");
+    if (split && d.products == TUFRG_PRODUCTS_AUTO) {
+        // autotune the products backend on this model's sizes (the cost does not depend on the values)
+        const size_t nA = 2 * (size_t)m->Nq * M2;
+        double2 *tmp = nullptr;
+        CK(dalloc(&tmp, nA), "cudaMalloc autotune output");
+        CK(cudaMemsetAsync(m->d_A32, 0, sizeof(float2) * nA, m->stream), "zero");
+        CK(cudaMemsetAsync(m->d_Lc32, 0, sizeof(float2) * 2 * (size_t)m->Nq * m->nd * ns4, m->stream), "zero");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        const int cand[2] = {TUFRG_PRODUCTS_TC, TUFRG_PRODUCTS_SIMT};
+        for (int c = 0; c < 2; c++) {
+            m->products = cand[c];
+            CK(launch_vlv(m, m->d_A, 3, 1.0, tmp), "autotune warm-up");
+            CK(cudaEventRecord(e0, m->stream), "event");
+            const int reps = 3;
+            for (int r = 0; r < reps; r++) CK(launch_vlv(m, m->d_A, 3, 1.0, tmp), "autotune");
+            CK(cudaEventRecord(e1, m->stream), "event");
+            CK(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+            m->tune_ms[c] = ms / reps;
+        }
+        m->products = m->tune_ms[0] <= m->tune_ms[1] ? TUFRG_PRODUCTS_TC : TUFRG_PRODUCTS_SIMT;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(tmp);
+        m->launches = 0;
+        m->loop_launches = 0;
+        int dev_err = 0;
+        CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
+        if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
+    }
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt)
+{
+    if (!m) return TUFRG_EINVAL;
+    if (products) *products = m->products;
+    if (ms_tc) *ms_tc = m->tune_ms[0];
+    if (ms_simt) *ms_simt = m->tune_ms[1];
     return TUFRG_OK;
 }
 
@@ -468,7 +514,10 @@ tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int c
     tufrg_status st = tufrg_rhs(m, T, m->d_state_in, channel_mask, m->d_state_out);
     if (st != TUFRG_OK) return st;
     CK(cudaMemcpyAsync(h_dstate, m->d_state_out, bytes, cudaMemcpyDeviceToHost, m->stream), "copy derivative out");
+    int dev_err = 0;
+    CK(cudaMemcpyAsync(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream), "copy error flag");
     CK(cudaStreamSynchronize(m->stream), "sync");
+    if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up");
     return TUFRG_OK;
 }
 
@@ -508,8 +557,11 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_
     double h = o->h0;
     auto read_scalars = [&](double *amax, double *err) -> tufrg_status {
         unsigned long long b[4];
+        int dev_err = 0;
         CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
+        CK(cudaMemcpyAsync(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream), "copy error flag");
         CK(cudaStreamSynchronize(m->stream), "sync");
+        if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up");
         if (amax) std::memcpy(amax, &b[0], sizeof(double));
         if (err) std::memcpy(err, &b[2], sizeof(double));
         return TUFRG_OK;

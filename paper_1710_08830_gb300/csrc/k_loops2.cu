@@ -294,7 +294,7 @@ bool loops2_supported(const tufrg_model *m)
 {
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
-    return m->ns == 2 && m->precision == TUFRG_SPLIT32 && ndyh <= 3 && (int)m->dxs.size() <= MAXD;
+    return m->ns == 2 && m->precision != TUFRG_FP64 && ndyh <= 3 && (int)m->dxs.size() <= MAXD;
 }
 
 cudaError_t launch_loop_records(tufrg_model *m, double T)

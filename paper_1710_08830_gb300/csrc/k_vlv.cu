@@ -65,6 +65,7 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out)
 {
     const int M = m->M;
+    if (tc_supported(m)) return launch_vlv_tc(m, channel_mask, scale, d_out);
     if (M > 64) return launch_vlv_large(m, d_A, channel_mask, scale, d_out);
     const int ns2 = m->ns * m->ns;
     dim3 grid(m->Nq, 2);

@@ -103,6 +103,9 @@ struct tufrg_model {
     int dft_nsplit = 1;             // transfer-mesh slices of the Fourier transform
     int max_terms = 0;              // largest gather-term list of one (R, R') pair
     unsigned long long *d_amax = nullptr;   // [4] reductions (max|A|, argmax, err)
+    int *d_err = nullptr;           // device-side error flag (bounded waits)
+    int products = TUFRG_PRODUCTS_SIMT;     // backend of the split-path products
+    double tune_ms[2] = {-1.0, -1.0};       // autotuner timings (tensor cores, CUDA cores)
     double *d_red = nullptr;        // density reduction scratch
     // flow work buffers
     double2 *d_y = nullptr, *d_yt = nullptr, *d_yn = nullptr, *d_k[7] = {};
@@ -141,6 +144,8 @@ int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
 cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out);
+bool tc_supported(const tufrg_model *m);
+cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double scale, double2 *d_out);
 cudaError_t launch_loop_records(tufrg_model *m, double T);
 cudaError_t launch_loops2(tufrg_model *m, int ch);
 

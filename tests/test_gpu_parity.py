@@ -166,10 +166,12 @@ def test_rhs_fp64(case, T):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("T", [5.0, 0.05])
-def test_rhs_split(case, T):
+@pytest.mark.parametrize("products", ["PRODUCTS_TC", "PRODUCTS_SIMT"])
+def test_rhs_split(case, T, products):
+    """Split path with tensor-core (tcgen05, 3xTF32) or CUDA-core FP32 products."""
     api = _api()
     spec = CASES[case]()
-    m = api.Model(spec, api.SPLIT32)
+    m = api.Model(spec, api.SPLIT32, products=getattr(api, products))
     o = oracle.Oracle(spec)
     st = inputs.random_state(spec, seed=9, scale=0.3)
     d = m.rhs(T, st).cpu().numpy()
@@ -307,11 +309,16 @@ def test_t2g_loops(case, prec):
 
 
 @pytest.mark.parametrize("case", list(T2G))
-@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32", "SPLIT32_SIMT"])
 def test_t2g_rhs(case, prec):
     api = _api()
     spec = T2G[case]()
-    m = api.Model(spec, getattr(api, prec))
+    if prec == "SPLIT32_SIMT":
+        m = api.Model(spec, api.SPLIT32, products=api.PRODUCTS_SIMT)
+    elif prec == "SPLIT32":
+        m = api.Model(spec, api.SPLIT32, products=api.PRODUCTS_TC)
+    else:
+        m = api.Model(spec, api.FP64)
     o = oracle.Oracle(spec)
     st = inputs.random_state(spec, seed=13, scale=0.15)
     d = m.rhs(0.2, st).cpu().numpy()
