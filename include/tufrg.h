@@ -170,8 +170,11 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate);
 
 /* Adaptive flow from X(T0) = 0 (Eqs. def_VP... at Lambda_0) down to T_end or to
- * max|A| > opts->stop.  d_state_out (may be NULL): [2][Nq][M][M] complex, the
- * last accepted state.  Errors: TUFRG_ENONFINITE, TUFRG_ENOTCONV, ... */
+ * max|A| > opts->stop.  The Dormand-Prince controller runs on the device: one attempt
+ * (six stage right-hand sides, error norm, accept/reject, FSAL commit) is captured once as
+ * a CUDA graph and replayed; the host only polls the controller state between attempts.
+ * d_state_out (may be NULL): [2][Nq][M][M] complex, the last accepted state.
+ * Errors: TUFRG_ENONFINITE, TUFRG_ENOTCONV, TUFRG_ETIMEOUT, ... */
 tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_state_out, tufrg_flow_result *res);
 
 /* Loop k-sum that allocates nothing (no counterpart in the paper; an interface addition).
@@ -211,6 +214,13 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_sta
 #define TUFRG_NOALLOC_SCRATCH_BYTES (16u << 20)
 tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, const double *d_U, double mu, double T, int n_ff,
                                  const int *h_ffR, int channel_mask, void *d_loops, void *cuda_stream);
+
+/* Many independent adaptive flows at once (uneven sizes allowed).  Each model must have been created
+ * on its own stream; every flow runs exactly as tufrg_flow would (same device controller, one captured
+ * CUDA graph per model per Dormand-Prince attempt), and the attempts of all running flows are launched
+ * round by round on their streams so that they overlap on the GPU.  results[i] receives flow i; wall_s
+ * is the wall time of the whole batch.  Returns the first error status (all results are filled). */
+tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *opts, tufrg_flow_result *results);
 
 /* Optional CUDA-event timing on the model's stream (used by the benchmark).
  * tufrg_timing_begin resets the counters and starts recording; every later

@@ -79,6 +79,8 @@ def lib():
             L.tufrg_flow.argtypes = [vp, C.POINTER(FlowOpts), vp, C.POINTER(FlowResult)]
             L.tufrg_loops_noalloc.argtypes = [i, i, vp, vp, d, d, i, vp, i, vp, vp]
             L.tufrg_loops_noalloc.restype = C.c_int
+            L.tufrg_flow_batch.argtypes = [vp, i, C.POINTER(FlowOpts), vp]
+            L.tufrg_flow_batch.restype = C.c_int
             L.tufrg_timing_begin.argtypes = [vp]
             L.tufrg_timing_end.argtypes = [vp, vp, i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for fn in ("tufrg_init_model", "tufrg_dims", "tufrg_deltas", "tufrg_gather_table", "tufrg_bands",
@@ -92,4 +94,5 @@ def lib():
 # names every header in include/ declares; the CPU test checks the exports against the headers
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
-           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info")
+           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info",
+           "tufrg_flow_batch")

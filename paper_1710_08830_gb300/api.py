@@ -17,7 +17,8 @@ from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, 
                    ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
-__all__ = ["Model", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "CH_P", "CH_C", "TufrgError"]
+__all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "CH_P", "CH_C",
+           "TufrgError"]
 
 
 def _ptr(t) -> int:
@@ -170,3 +171,23 @@ class Model:
         self._check(self._L.tufrg_flow(self._h, C.byref(o), _ptr(st_out) if want_state else None, C.byref(r)))
         res = {f: getattr(r, f) for f, _ in FlowResult._fields_}
         return st_out, res
+
+
+def flow_batch(models, T0: float = FLOW_T0, T_end: float = FLOW_T_END, rtol: float = FLOW_RTOL,
+               atol: float = FLOW_ATOL, h0: float = -0.05, stop: float = FLOW_STOP, mask: int = CH_P | CH_C,
+               max_steps: int = 100000):
+    """Run the adaptive flows of several models together (tufrg_flow_batch).
+
+    Each model should have been created on its own torch stream so that the flows overlap.
+    Returns one result dict per model."""
+    if not models:
+        return []
+    L = models[0]._L
+    arr = (C.c_void_p * len(models))(*[m._h.value for m in models])
+    res = (FlowResult * len(models))()
+    o = FlowOpts(T0, T_end, rtol, atol, h0, stop, int(mask), int(max_steps))
+    st = L.tufrg_flow_batch(arr, len(models), C.byref(o), res)
+    if st != 0:
+        msgs = "; ".join(m._L.tufrg_last_error(m._h).decode() for m in models if m._L.tufrg_last_error(m._h))
+        raise TufrgError(st, msgs)
+    return [{f: getattr(r, f) for f, _ in FlowResult._fields_} for r in res]

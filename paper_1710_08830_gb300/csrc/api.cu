@@ -203,25 +203,195 @@ void release(tufrg_model *m)
                     m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
-                    m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err};
+                    m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
         if (p) cudaFree(p);
     for (auto &e : m->evpool) cudaEventDestroy(e);
     m->evpool.clear();
+    if (m->h_flow) cudaFreeHost(m->h_flow);
+    if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
+    if (m->flow_ev) cudaEventDestroy(m->flow_ev);
+    if (m->flow_stream) cudaStreamDestroy(m->flow_stream);
 }
 
 size_t state_elems(const tufrg_model *m) { return (size_t)2 * m->Nq * m->M * m->M; }
 
-// One evaluation of the right-hand side into d_out, scaled per channel by scale * c_X.
-tufrg_status rhs_device(tufrg_model *m, double T, const double2 *d_state, int mask, double2 *d_out, double scale)
+// One evaluation of the right-hand side into d_out at the temperature held in m->d_scal[0],
+// each channel scaled by c_X * m->d_scal[1] (1 for dX/dT, T for the flow variable ln T).
+tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double2 *d_out)
 {
-    CK(launch_fermi(m, T), "fermi tables");
+    CK(launch_fermi(m), "fermi tables");
     CK(launch_loops(m, mask), "loop k-sum");
     CK(launch_dft(m, d_state, mask), "Fourier transform");
     CK(launch_project(m, d_state, mask, m->d_A), "projections");
-    CK(launch_vlv(m, m->d_A, mask, scale, d_out), "V.L.V products");
+    CK(launch_vlv(m, m->d_A, mask, d_out), "V.L.V products");
+    return TUFRG_OK;
+}
+
+// Dormand-Prince 5(4) tableau (stage nodes c, coefficients a, error weights b - b*)
+const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+const double DP_A[7][6] = {
+    {0},
+    {1.0 / 5},
+    {3.0 / 40, 9.0 / 40},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+    {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+const double DP_E[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640,
+                        -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+
+// Enqueue one Dormand-Prince attempt on the model's stream: six stage right-hand sides, the error
+// norm, the accept/reject decision and the FSAL commit, all driven by the device flow state.
+tufrg_status enqueue_attempt(tufrg_model *m, int mask)
+{
+    const size_t n = state_elems(m);
+    double2 *k[7];
+    for (int i = 0; i < 7; i++) k[i] = m->d_k[i];
+    for (int j = 1; j < 7; j++) {
+        double2 *dst = j == 6 ? m->d_yn : m->d_yt;
+        CK(launch_rk_combine(m, dst, m->d_y, m->d_flow, DP_A[j], k, j, n), "stage combination");
+        CK(launch_stage_scalars(m, m->d_flow, DP_C[j]), "stage temperature");
+        tufrg_status st = rhs_device(m, dst, mask, k[j]);
+        if (st != TUFRG_OK) return st;
+    }
+    CK(launch_rk_error(m, m->d_y, m->d_yn, m->d_flow, DP_E, k, 7, n), "error norm");
+    CK(launch_flow_decide(m, m->d_flow), "step decision");
+    CK(launch_flow_commit(m, m->d_flow, m->d_y, m->d_yn, k[0], k[6], n), "step commit");
+    return TUFRG_OK;
+}
+
+// Allocate the flow buffers, zero the state, evaluate k1 = f(y0) and capture one attempt as a graph.
+tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
+{
+    const size_t n = state_elems(m);
+    if (!m->d_y) {
+        CK(dalloc(&m->d_y, n), "cudaMalloc flow state");
+        CK(dalloc(&m->d_yt, n), "cudaMalloc flow state");
+        CK(dalloc(&m->d_yn, n), "cudaMalloc flow state");
+        for (auto &k : m->d_k) CK(dalloc(&k, n), "cudaMalloc flow stages");
+        CK(dalloc(&m->d_flow, 1), "cudaMalloc flow state");
+        CK(cudaMallocHost(reinterpret_cast<void **>(&m->h_flow), sizeof(FlowDev)), "cudaMallocHost flow state");
+    }
+    FlowDev f{};
+    f.x = std::log(o->T0);
+    f.xend = std::log(o->T_end);
+    f.h = o->h0;
+    if (f.x + f.h < f.xend) f.h = f.xend - f.x;
+    f.x_prev = f.x;
+    f.atol = o->atol;
+    f.rtol = o->rtol;
+    f.stop = o->stop;
+    f.max_tries = o->max_steps;
+    f.Tc = o->T_end;
+    *m->h_flow = f;
+    CK(cudaMemcpyAsync(m->d_flow, m->h_flow, sizeof(FlowDev), cudaMemcpyHostToDevice, m->stream), "copy flow state");
+    CK(cudaMemsetAsync(m->d_y, 0, sizeof(double2) * n, m->stream), "zero state");
+    // k1 = f(x0, y0) and max|A| of the initial state
+    CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
+    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0]);
+    if (st != TUFRG_OK) return st;
+    CK(launch_flow_init(m, m->d_flow), "flow init");
+    if (!m->step_graph || m->step_graph_mask != o->channel_mask) {
+        if (m->step_graph) {
+            cudaGraphExecDestroy(m->step_graph);
+            m->step_graph = nullptr;
+        }
+        const bool timing = m->timing;
+        m->timing = false;   // no event records inside the captured graph
+        const long long l0 = m->launches, ll0 = m->loop_launches;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        st = enqueue_attempt(m, o->channel_mask);
+        cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+        m->timing = timing;
+        m->launches = l0;
+        m->loop_launches = ll0;
+        if (st != TUFRG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(m, ce, "end capture");
+        ce = cudaGraphInstantiate(&m->step_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(m, ce, "graph instantiate");
+        m->step_graph_mask = o->channel_mask;
+    }
+    return TUFRG_OK;
+}
+
+// Flows run on a private non-blocking stream (the legacy default stream cannot be captured);
+// it is ordered after the user's stream on entry and the user's stream after it on exit.
+tufrg_status flow_enter(tufrg_model *m, cudaStream_t *user)
+{
+    *user = m->stream;
+    if (!m->flow_stream) {
+        CK(cudaStreamCreateWithFlags(&m->flow_stream, cudaStreamNonBlocking), "create flow stream");
+        CK(cudaEventCreateWithFlags(&m->flow_ev, cudaEventDisableTiming), "create flow event");
+    }
+    CK(cudaEventRecord(m->flow_ev, m->stream), "record");
+    CK(cudaStreamWaitEvent(m->flow_stream, m->flow_ev, 0), "wait");
+    m->stream = m->flow_stream;
+    return TUFRG_OK;
+}
+
+tufrg_status flow_leave(tufrg_model *m, cudaStream_t user)
+{
+    m->stream = user;
+    CK(cudaEventRecord(m->flow_ev, m->flow_stream), "record");
+    CK(cudaStreamWaitEvent(user, m->flow_ev, 0), "wait");
+    return TUFRG_OK;
+}
+
+tufrg_status flow_check_args(tufrg_model *m, const tufrg_flow_opts *o, tufrg_flow_result *res)
+{
+    if (!m || !o || !res) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!(o->T0 > o->T_end) || !(o->T_end > 0)) return fail(m, TUFRG_EINVAL, "need T0 > T_end > 0");
+    if (!(o->rtol > 0) || !(o->atol >= 0) || !(o->h0 < 0)) return fail(m, TUFRG_EINVAL, "bad tolerances or h0");
+    if ((o->channel_mask & 3) == 0 || (o->channel_mask & ~3)) return fail(m, TUFRG_EINVAL, "bad channel_mask");
+    if (o->max_steps < 1) return fail(m, TUFRG_EINVAL, "max_steps must be positive");
+    return TUFRG_OK;
+}
+
+// Result of a finished flow: read the device state, locate the maximum of the last projection.
+tufrg_status flow_finish(tufrg_model *m, void *d_state_out, tufrg_flow_result *res)
+{
+    const FlowDev &f = *m->h_flow;
+    res->n_steps = f.n_steps;
+    res->n_reject = f.n_reject;
+    res->n_rhs = 1 + 6 * f.tries;
+    res->amax = f.amax;
+    res->T_last = std::exp(f.x);
+    res->crossed = f.status == 1;
+    res->Tc = res->crossed ? f.Tc : res->T_last;
+    // the last stage-7 projection belongs to the last accepted state when the flow stopped on an accepted step
+    const size_t nA = state_elems(m), M2 = (size_t)m->M * m->M;
+    CK(launch_amax_locate(m, m->d_A, nA, res->amax), "locate maximum");
+    unsigned long long b[4];
+    CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    if (b[1] < nA) {
+        res->lead_channel = (int)(b[1] / ((size_t)m->Nq * M2));
+        res->lead_q = (int)((b[1] / M2) % m->Nq);
+    }
+    if (d_state_out)
+        CK(cudaMemcpyAsync(d_state_out, m->d_y, sizeof(double2) * nA, cudaMemcpyDeviceToDevice, m->stream), "copy state out");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    switch (f.status) {
+    case 3: return fail(m, TUFRG_ENOTCONV, "flow step limit reached");
+    case 4: return fail(m, TUFRG_ENONFINITE, "non-finite right-hand side or error norm");
+    case 5: return fail(m, TUFRG_ENOTCONV, "step size underflow");
+    default: return TUFRG_OK;
+    }
+}
+
+tufrg_status read_device_error(tufrg_model *m)
+{
+    int dev_err = 0;
+    CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
+    if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up");
     return TUFRG_OK;
 }
 
@@ -339,6 +509,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaMalloc(reinterpret_cast<void **>(&m->d_T), (size_t)m->Nq * M2 * (split ? sizeof(float2) : sizeof(double2))),
            "cudaMalloc product scratch");
     CK(dalloc(&m->d_err, 1), "cudaMalloc error flag");
+    CK(dalloc(&m->d_scal, 2), "cudaMalloc scalars");
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "zero error flag");
     CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
     CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
@@ -380,12 +551,13 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
         const int cand[2] = {TUFRG_PRODUCTS_TC, TUFRG_PRODUCTS_SIMT};
+        CK(launch_set_scalars(m, 1.0, 1.0), "set scalars");
         for (int c = 0; c < 2; c++) {
             m->products = cand[c];
-            CK(launch_vlv(m, m->d_A, 3, 1.0, tmp), "autotune warm-up");
+            CK(launch_vlv(m, m->d_A, 3, tmp), "autotune warm-up");
             CK(cudaEventRecord(e0, m->stream), "event");
             const int reps = 3;
-            for (int r = 0; r < reps; r++) CK(launch_vlv(m, m->d_A, 3, 1.0, tmp), "autotune");
+            for (int r = 0; r < reps; r++) CK(launch_vlv(m, m->d_A, 3, tmp), "autotune");
             CK(cudaEventRecord(e1, m->stream), "event");
             CK(cudaEventSynchronize(e1), "event");
             float ms = 0.f;
@@ -467,7 +639,8 @@ tufrg_status tufrg_loops(tufrg_model *m, double T, int channel_mask, void *d_loo
     if (!m || !d_loops) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
-    CK(launch_fermi(m, T), "fermi tables");
+    CK(launch_set_scalars(m, T, 1.0), "set temperature");
+    CK(launch_fermi(m), "fermi tables");
     CK(launch_loops(m, channel_mask), "loop k-sum");
     const size_t per = (size_t)m->Nq * m->nd * m->ns * m->ns * m->ns * m->ns;
     for (int ch = 0; ch < 2; ch++)
@@ -498,8 +671,8 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
     if (!m || !d_state || !d_dstate) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
-    return rhs_device(m, T, reinterpret_cast<const double2 *>(d_state), channel_mask,
-                      reinterpret_cast<double2 *>(d_dstate), 1.0);
+    CK(launch_set_scalars(m, T, 1.0), "set temperature");
+    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask, reinterpret_cast<double2 *>(d_dstate));
 }
 
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)
@@ -523,121 +696,92 @@ tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int c
 
 tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_out, tufrg_flow_result *res)
 {
-    if (!m || !o || !res) return fail(m, TUFRG_EINVAL, "NULL argument");
-    if (!(o->T0 > o->T_end) || !(o->T_end > 0)) return fail(m, TUFRG_EINVAL, "need T0 > T_end > 0");
-    if (!(o->rtol > 0) || !(o->atol >= 0) || !(o->h0 < 0)) return fail(m, TUFRG_EINVAL, "bad tolerances or h0");
-    if ((o->channel_mask & 3) == 0 || (o->channel_mask & ~3)) return fail(m, TUFRG_EINVAL, "bad channel_mask");
-    static const double C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
-    static const double A[7][6] = {
-        {0},
-        {1.0 / 5},
-        {3.0 / 40, 9.0 / 40},
-        {44.0 / 45, -56.0 / 15, 32.0 / 9},
-        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
-        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
-        {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
-    static const double E[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
-                                125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
-                                11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+    tufrg_status st = flow_check_args(m, o, res);
+    if (st != TUFRG_OK) return st;
     const auto t_start = std::chrono::steady_clock::now();
     std::memset(res, 0, sizeof(*res));
-    const size_t n = state_elems(m);
-    if (!m->d_y) {
-        CK(dalloc(&m->d_y, n), "cudaMalloc flow state");
-        CK(dalloc(&m->d_yt, n), "cudaMalloc flow state");
-        CK(dalloc(&m->d_yn, n), "cudaMalloc flow state");
-        for (auto &k : m->d_k) CK(dalloc(&k, n), "cudaMalloc flow stages");
+    cudaStream_t user;
+    if ((st = flow_enter(m, &user)) != TUFRG_OK) return st;
+    st = flow_prepare(m, o);
+    // replay the captured attempt until the device controller stops the flow
+    while (st == TUFRG_OK) {
+        cudaError_t e = cudaGraphLaunch(m->step_graph, m->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) st = cuda_fail(m, e, "flow graph");
+        else if (m->h_flow->status != 0) break;
     }
-    double2 *y = m->d_y, *yn = m->d_yn, *yt = m->d_yt, *k[7];
-    for (int i = 0; i < 7; i++) k[i] = m->d_k[i];
-    CK(cudaMemsetAsync(y, 0, sizeof(double2) * n, m->stream), "zero state");
-    const int mask = o->channel_mask;
-    double x = std::log(o->T0);
-    const double xend = std::log(o->T_end);
-    double h = o->h0;
-    auto read_scalars = [&](double *amax, double *err) -> tufrg_status {
-        unsigned long long b[4];
-        int dev_err = 0;
-        CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
-        CK(cudaMemcpyAsync(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream), "copy error flag");
-        CK(cudaStreamSynchronize(m->stream), "sync");
-        if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up");
-        if (amax) std::memcpy(amax, &b[0], sizeof(double));
-        if (err) std::memcpy(err, &b[2], sizeof(double));
-        return TUFRG_OK;
-    };
-    // k0 = f(x0, y0);  f = T dX/dT (integration variable ln T)
-    tufrg_status st = rhs_device(m, std::exp(x), y, mask, k[0], std::exp(x));
-    if (st != TUFRG_OK) return st;
-    res->n_rhs = 1;
-    double amax_prev = 0.0;
-    if ((st = read_scalars(&amax_prev, nullptr)) != TUFRG_OK) return st;
-    res->amax = amax_prev;
-    double x_prev = x;
-    int tries = 0;
-    tufrg_status out_status = TUFRG_OK;
-    while (true) {
-        if (++tries > o->max_steps) { out_status = fail(m, TUFRG_ENOTCONV, "flow step limit reached"); break; }
-        if (x + h < xend) h = xend - x;
-        for (int j = 1; j < 7; j++) {
-            double2 *dst = j == 6 ? yn : yt;
-            CK(launch_rk_combine(m, dst, y, h, A[j], k, j, n), "stage combination");
-            const double T = std::exp(x + C[j] * h);
-            if ((st = rhs_device(m, T, dst, mask, k[j], T)) != TUFRG_OK) return st;
-            res->n_rhs++;
-        }
-        CK(launch_rk_error(m, y, yn, h, E, k, 7, n, o->atol, o->rtol), "error norm");
-        double amax_new = 0.0, err = 0.0;
-        if ((st = read_scalars(&amax_new, &err)) != TUFRG_OK) return st;
-        if (!std::isfinite(err) || !std::isfinite(amax_new)) {
-            out_status = fail(m, TUFRG_ENONFINITE, "non-finite right-hand side or error norm");
-            break;
-        }
-        if (err <= 1.0) {
-            x_prev = x;
-            x += h;
-            std::swap(y, yn);
-            std::swap(k[0], k[6]);
-            res->n_steps++;
-            res->amax = amax_new;
-            double fac = err > 0 ? 0.9 * std::pow(err, -0.2) : 5.0;
-            fac = std::min(5.0, std::max(0.2, fac));
-            if (amax_new > o->stop) {
-                const double t = (o->stop - amax_prev) / (amax_new - amax_prev);
-                res->Tc = std::exp(x_prev + t * (x - x_prev));
-                res->crossed = 1;
-                break;
-            }
-            amax_prev = amax_new;
-            if (x <= xend + 1e-14) break;
-            h *= fac;
-        } else {
-            res->n_reject++;
-            h *= std::min(1.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
-            if (std::fabs(h) < 1e-12) { out_status = fail(m, TUFRG_ENOTCONV, "step size underflow"); break; }
-        }
-    }
-    res->T_last = std::exp(x);
-    if (!res->crossed) res->Tc = res->T_last;
-    // the last evaluated projection belongs to the last accepted state (stage 7 = FSAL)
-    const size_t nA = state_elems(m);
-    CK(launch_amax_locate(m, m->d_A, nA, res->amax), "locate maximum");
-    unsigned long long b[4];
-    CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
-    CK(cudaStreamSynchronize(m->stream), "sync");
-    const size_t M2 = (size_t)m->M * m->M;
-    if (b[1] < nA) {
-        res->lead_channel = (int)(b[1] / ((size_t)m->Nq * M2));
-        res->lead_q = (int)((b[1] / M2) % m->Nq);
-    }
-    if (d_state_out)
-        CK(cudaMemcpyAsync(d_state_out, y, sizeof(double2) * n, cudaMemcpyDeviceToDevice, m->stream), "copy state out");
-    // keep the buffers consistent for the next call
-    m->d_y = y; m->d_yn = yn;
-    for (int i = 0; i < 7; i++) m->d_k[i] = k[i];
-    CK(cudaStreamSynchronize(m->stream), "sync");
+    if (st == TUFRG_OK) st = read_device_error(m);
+    if (st == TUFRG_OK) st = flow_finish(m, d_state_out, res);
+    const tufrg_status st2 = flow_leave(m, user);
     res->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    return out_status;
+    return st != TUFRG_OK ? st : st2;
+}
+
+tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *o, tufrg_flow_result *res)
+{
+    if (!models || n < 1 || !o || !res) return TUFRG_EINVAL;
+    for (int i = 0; i < n; i++) {
+        if (!models[i]) return TUFRG_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (models[j] == models[i]) return fail(models[i], TUFRG_EINVAL, "a model appears twice in the batch");
+        tufrg_status st = flow_check_args(models[i], o, &res[i]);
+        if (st != TUFRG_OK) return st;
+    }
+    const auto t_start = std::chrono::steady_clock::now();
+    std::vector<char> active(n, 1);
+    std::vector<cudaStream_t> user(n, nullptr);
+    std::vector<char> entered(n, 0);
+    tufrg_status first = TUFRG_OK;
+    for (int i = 0; i < n; i++) {
+        std::memset(&res[i], 0, sizeof(res[i]));
+        tufrg_status st = flow_enter(models[i], &user[i]);
+        if (st == TUFRG_OK) {
+            entered[i] = 1;
+            st = flow_prepare(models[i], o);
+        }
+        if (st != TUFRG_OK) {
+            active[i] = 0;
+            if (first == TUFRG_OK) first = st;
+        }
+    }
+    // lock-step rounds: every running flow replays one attempt on its own stream, then all are polled
+    int running = 0;
+    for (int i = 0; i < n; i++) running += active[i];
+    while (running > 0) {
+        for (int i = 0; i < n; i++) {
+            if (!active[i]) continue;
+            tufrg_model *m = models[i];
+            cudaError_t e = cudaGraphLaunch(m->step_graph, m->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream);
+            if (e != cudaSuccess) {
+                active[i] = 0;
+                running--;
+                if (first == TUFRG_OK) first = cuda_fail(m, e, "batched graph launch");
+            }
+        }
+        for (int i = 0; i < n; i++) {
+            if (!active[i]) continue;
+            tufrg_model *m = models[i];
+            cudaError_t e = cudaStreamSynchronize(m->stream);
+            if (e != cudaSuccess || m->h_flow->status != 0) {
+                active[i] = 0;
+                running--;
+                tufrg_status st = e != cudaSuccess ? cuda_fail(m, e, "sync") : read_device_error(m);
+                if (st == TUFRG_OK) st = flow_finish(m, nullptr, &res[i]);
+                if (st != TUFRG_OK && first == TUFRG_OK) first = st;
+            }
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        if (!entered[i]) continue;
+        tufrg_status st = flow_leave(models[i], user[i]);
+        if (st != TUFRG_OK && first == TUFRG_OK) first = st;
+    }
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    for (int i = 0; i < n; i++) res[i].wall_s = wall;
+    return first;
 }
 
 }  // extern "C"

@@ -156,10 +156,11 @@ __device__ __forceinline__ void fermi_g(double e, double T, double &f, double &g
     gp = h / (T * T) * (1.0 - ax * (1.0 - z) / (1.0 + z));
 }
 
-__global__ void fermi_kernel(const double *E, int n, double mu, double T, FermiEntry *ft, FermiEntry32 *ft32)
+__global__ void fermi_kernel(const double *E, int n, double mu, const double *scal, FermiEntry *ft, FermiEntry32 *ft32)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double T = scal[0];
     const double e = E[i] - mu;
     double f, g, gp;
     fermi_g(e, T, f, g, gp);
@@ -213,17 +214,26 @@ cudaError_t launch_bands(tufrg_model *m)
     return cudaGetLastError();
 }
 
-cudaError_t launch_fermi(tufrg_model *m, double T)
+__global__ void set_scalars_kernel(double *scal, double T, double scale)
 {
-    if (loops2_supported(m)) {   // the split two-band kernel reads its own per-k records
-        m->cur_T = T;
-        return launch_loop_records(m, T);
-    }
+    scal[0] = T;
+    scal[1] = scale;
+}
+
+cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale)
+{
+    m->launches++;
+    set_scalars_kernel<<<1, 1, 0, m->stream>>>(m->d_scal, T, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fermi(tufrg_model *m)
+{
+    if (loops2_supported(m)) return launch_loop_records(m);   // the split two-band kernel reads its own per-k records
     const int n = m->Nk * m->ns;
     FermiEntry32 *ft32 = m->precision == TUFRG_FP64 ? nullptr : m->d_ft32;
     PhaseScope ps(m, PH_FERMI);
-    fermi_kernel<<<(n + 255) / 256, 256, 0, m->stream>>>(m->d_E, n, m->mu, T, m->d_ft, ft32);
-    m->cur_T = T;
+    fermi_kernel<<<(n + 255) / 256, 256, 0, m->stream>>>(m->d_E, n, m->mu, m->d_scal, m->d_ft, ft32);
     return cudaGetLastError();
 }
 

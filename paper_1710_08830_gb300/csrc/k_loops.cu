@@ -42,7 +42,8 @@ struct LoopArgs {
     int dys[MAXD];                      // non-negative dy values (half plane)
     unsigned needed[MAXD];              // bit dyi set if (dx, dy) is a needed half-plane difference
     int ky_chunks, ky_len;
-    R thr;                              // degenerate-pair switch
+    R thr_factor;                       // degenerate-pair switch = thr_factor * T
+    const double *Tp;                   // device temperature
     int which;                          // 0 = P, 1 = C (uniform, also a template arg below)
 };
 
@@ -95,6 +96,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs<R> &a, const typename c
     const int kx = blockIdx.y * (32 * WARPS) + threadIdx.x;
     const bool valid = kx < Lf;
     const int kyc = blockIdx.z % a.ky_chunks;   // the ab group is blockIdx.z / ky_chunks
+    const R thr = a.thr_factor * (R)(*a.Tp);
     const int ky0 = kyc * a.ky_len;
     const int ky1 = min(Lf, ky0 + a.ky_len);
 
@@ -144,7 +146,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs<R> &a, const typename c
                 R w[NS];
 #pragma unroll
                 for (int l2 = 0; l2 < NS; l2++)
-                    w[l2] = pair_weight<WHICH, R>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], a.thr);
+                    w[l2] = pair_weight<WHICH, R>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr);
 #pragma unroll
                 for (int t2 = 0; t2 < NS; t2++)
 #pragma unroll
@@ -339,7 +341,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
                 }
             }
             a.ky_chunks = pl.ky_chunks; a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
-            a.thr = 1e-5 * m->cur_T; a.which = ch;
+            a.thr_factor = 1e-5; a.Tp = m->d_scal; a.which = ch;
             cudaError_t e;
             if (ndyh <= 3) e = ch == 0 ? launch_one<double, 3, 8, 0>(m, a, 2) : launch_one<double, 3, 8, 1>(m, a, 2);
             else           e = ch == 0 ? launch_one<double, 5, 4, 0>(m, a, 4) : launch_one<double, 5, 4, 1>(m, a, 4);
@@ -366,7 +368,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
                 }
             }
             a.ky_chunks = pl.ky_chunks; a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
-            a.thr = (float)(1e-2 * m->cur_T); a.which = ch;
+            a.thr_factor = 1e-2f; a.Tp = m->d_scal; a.which = ch;
             cudaError_t e;
             if (ndyh <= 3) e = ch == 0 ? launch_one<float, 3, 16, 0>(m, a, 1) : launch_one<float, 3, 16, 1>(m, a, 1);
             else           e = ch == 0 ? launch_one<float, 5, 8, 0>(m, a, 2) : launch_one<float, 5, 8, 1>(m, a, 2);

@@ -40,7 +40,8 @@ struct Args2 {
     int dxs[MAXD], dys[MAXD];
     unsigned needed[MAXD];
     int ky_chunks, ky_len;
-    float thr;
+    float thr;               // degenerate-pair switch, used when Tp is null
+    const double *Tp;        // device temperature: switch = 1e-2 * (*Tp)
 };
 
 // (t1,t3,t2,t4) -> ab index of the compact loop (P: a=(t2,t1), b=(t4,t3); C: a=(t1,t2), b=(t3,t4))
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int kx = blockIdx.y * NT + threadIdx.x;
+    const float thr = a.Tp ? (float)(1e-2 * *a.Tp) : a.thr;
     const bool valid = kx < Lf;
     const int kyc = blockIdx.z;
     const int ky0 = kyc * a.ky_len;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
 #pragma unroll
             for (int l1 = 0; l1 < 2; l1++)
 #pragma unroll
-                for (int l2 = 0; l2 < 2; l2++) w[l1][l2] = pw<WHICH>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], a.thr);
+                for (int l2 = 0; l2 < 2; l2++) w[l1][l2] = pw<WHICH>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr);
             // T^{l1} = w_{l1 1} 1 + (w_{l1 0} - w_{l1 1}) rho2'^0 ;  D = T^0 - T^1
             const float A2 = b0.x, C2r = b0.y, C2i = sgn * b0.z;    // rho2' = rho2 (P) or conj(rho2) (C)
             const float dw0 = w[0][0] - w[0][1], dw1 = w[1][0] - w[1][1];
@@ -237,10 +239,12 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
 }
 
 // Per-temperature record of one fine k: band-0 projector and the Fermi data of both bands, FP32.
-__global__ void rec_kernel(const double *E, const double2 *U, int Nk, int Lf, double mu, double T, float4 *rec)
+__global__ void rec_kernel(const double *E, const double2 *U, int Nk, int Lf, double mu, double T_value,
+                           const double *Tp, float4 *rec)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nk) return;
+    const double T = Tp ? *Tp : T_value;   // device-resident temperature when given
     float e[2], g[2], gp[2];
 #pragma unroll
     for (int l = 0; l < 2; l++) {
@@ -297,10 +301,10 @@ bool loops2_supported(const tufrg_model *m)
     return m->ns == 2 && m->precision != TUFRG_FP64 && ndyh <= 3 && (int)m->dxs.size() <= MAXD;
 }
 
-cudaError_t launch_loop_records(tufrg_model *m, double T)
+cudaError_t launch_loop_records(tufrg_model *m)
 {
     PhaseScope ps(m, PH_FERMI);
-    rec_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->d_U, m->Nk, m->Lf, m->mu, T, m->d_rec);
+    rec_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->d_U, m->Nk, m->Lf, m->mu, 0.0, m->d_scal, m->d_rec);
     return cudaGetLastError();
 }
 
@@ -329,7 +333,8 @@ cudaError_t launch_loops2(tufrg_model *m, int ch)
     }
     a.ky_chunks = pl.ky_chunks;
     a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
-    a.thr = (float)(1e-2 * m->cur_T);
+    a.thr = 0.f;
+    a.Tp = m->d_scal;
     switch (ndyh) {
     case 1: return ch == 0 ? launch2<1, 0>(m, a) : launch2<1, 1>(m, a);
     case 2: return ch == 0 ? launch2<2, 0>(m, a) : launch2<2, 1>(m, a);
@@ -440,7 +445,7 @@ extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, c
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
     rec_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d_E, reinterpret_cast<const double2 *>(d_U), (int)Nk, Lf,
-                                                               mu, T, rec);
+                                                               mu, T, nullptr, rec);
     if (cudaGetLastError() != cudaSuccess) return TUFRG_ECUDA;
     Args2 a{};
     a.rec = rec;
@@ -458,6 +463,7 @@ extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, c
     a.ky_chunks = 1;
     a.ky_len = Lf;
     a.thr = (float)(1e-2 * T);
+    a.Tp = nullptr;
     NoallocTables t{};
     t.nd = nd;
     for (int k = 0; k < nd; k++) {

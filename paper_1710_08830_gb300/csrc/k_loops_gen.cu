@@ -35,7 +35,8 @@ struct GenArgs {
     int Lq, nc, Lf, nd, ndx, ndyh;
     int dxs[GMAXD], dys[GMAXD];
     int dslot[GMAXD][GMAXD];            // [dxi][dyi] -> delta index (half plane), or -1
-    R thr;
+    R thr_factor;                       // degenerate-pair switch = thr_factor * T
+    const double *Tp;                   // device temperature
 };
 
 template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
@@ -83,6 +84,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     const int s = blockIdx.x;
     const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
     const int ta = threadIdx.x / GB, tb = threadIdx.x % GB;
+    const R thr = a.thr_factor * (R)(*a.Tp);
     const bool active = threadIdx.x < NT;
     double2 *acc = a.acc + (size_t)s * a.nd * NS2 * NS2;
 
@@ -118,7 +120,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
                 R e1, g1, gp1, e2, g2, gp2;
                 ldft(&a.ft[(size_t)k1 * NS + l1], e1, g1, gp1);
                 ldft(&a.ft[(size_t)k2 * NS + l2], e2, g2, gp2);
-                sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, a.thr);
+                sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr);
             }
             __syncthreads();
             // T^{l1}_{p} = sum_l2 w_{l1 l2} rho2'^{l2}_p
@@ -285,12 +287,12 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask)
         cudaError_t e;
         if (m->precision == TUFRG_FP64) {
             GenArgs<double> a{};
-            a.U = m->d_U; a.ft = m->d_ft; a.acc = acc; a.thr = 1e-5 * m->cur_T;
+            a.U = m->d_U; a.ft = m->d_ft; a.acc = acc; a.thr_factor = 1e-5; a.Tp = m->d_scal;
             fill_args(m, a);
             e = m->ns == 6 ? dispatch_gen<double, 6, 2, 3>(m, a, ch) : dispatch_gen<double, 4, 2, 2>(m, a, ch);
         } else {
             GenArgs<float> a{};
-            a.U = m->d_U32; a.ft = m->d_ft32; a.acc = acc; a.thr = (float)(1e-2 * m->cur_T);
+            a.U = m->d_U32; a.ft = m->d_ft32; a.acc = acc; a.thr_factor = 1e-2f; a.Tp = m->d_scal;
             fill_args(m, a);
             e = m->ns == 6 ? dispatch_gen<float, 6, 4, 3>(m, a, ch) : dispatch_gen<float, 4, 2, 2>(m, a, ch);
         }

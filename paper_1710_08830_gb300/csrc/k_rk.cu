@@ -11,9 +11,10 @@ struct StageArgs {
     int nk;
 };
 
-// out = y + h * sum_j a_j k_j  (element-wise over doubles)
-__global__ void rk_combine_kernel(double *out, const double *y, double h, StageArgs s, size_t n)
+// out = y + h * sum_j a_j k_j  (element-wise over doubles), h read from the device flow state
+__global__ void rk_combine_kernel(double *out, const double *y, const FlowDev *fs, StageArgs s, size_t n)
 {
+    const double h = fs->h;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int j = 0; j < s.nk; j++) acc = fma(s.a[j], s.k[j][i], acc);
@@ -22,9 +23,10 @@ __global__ void rk_combine_kernel(double *out, const double *y, double h, StageA
 }
 
 // max over complex entries of |h sum_j e_j k_j| / (atol + rtol max(|y|, |yn|)); non-finite -> +inf
-__global__ void rk_error_kernel(const double2 *y, const double2 *yn, double h, StageArgs s, size_t n, double atol,
-                                double rtol, unsigned long long *out)
+__global__ void rk_error_kernel(const double2 *y, const double2 *yn, const FlowDev *fs, StageArgs s, size_t n,
+                                unsigned long long *out)
 {
+    const double h = fs->h, atol = fs->atol, rtol = fs->rtol;
     double mx = 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double er = 0.0, ei = 0.0;
@@ -44,6 +46,77 @@ __global__ void rk_error_kernel(const double2 *y, const double2 *yn, double h, S
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
+// temperature of stage j: T = exp(x + c_j h); the products are scaled by T (f = T dX/dT)
+__global__ void stage_scalars_kernel(const FlowDev *fs, double cj, double *scal)
+{
+    const double T = exp(fs->x + cj * fs->h);
+    scal[0] = T;
+    scal[1] = T;
+}
+
+__global__ void flow_init_kernel(FlowDev *fs, const unsigned long long *red)
+{
+    const double amax = __longlong_as_double((long long)red[0]);
+    fs->amax = amax;
+    fs->amax_prev = amax;
+    if (!isfinite(amax)) fs->status = 4;
+}
+
+// Accept or reject the attempt just computed (error norm in red[2], max|A| at the candidate in red[0]).
+__global__ void flow_decide_kernel(FlowDev *fs, const unsigned long long *red)
+{
+    fs->accepted = 0;
+    if (fs->status != 0) return;
+    const double err = __longlong_as_double((long long)red[2]);
+    const double amax_new = __longlong_as_double((long long)red[0]);
+    fs->tries++;
+    fs->err = err;
+    if (!isfinite(err) || !isfinite(amax_new)) {
+        fs->status = 4;
+        return;
+    }
+    if (err <= 1.0) {
+        fs->x_prev = fs->x;
+        fs->x += fs->h;
+        fs->n_steps++;
+        fs->amax = amax_new;
+        fs->accepted = 1;
+        double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+        fac = fmin(5.0, fmax(0.2, fac));
+        if (amax_new > fs->stop) {
+            const double t = (fs->stop - fs->amax_prev) / (amax_new - fs->amax_prev);
+            fs->Tc = exp(fs->x_prev + t * (fs->x - fs->x_prev));
+            fs->status = 1;
+            return;
+        }
+        fs->amax_prev = amax_new;
+        if (fs->x <= fs->xend + 1e-14) {
+            fs->status = 2;
+            return;
+        }
+        fs->h *= fac;
+    } else {
+        fs->n_reject++;
+        fs->h *= fmin(1.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+        if (fabs(fs->h) < 1e-12) {
+            fs->status = 5;
+            return;
+        }
+    }
+    if (fs->x + fs->h < fs->xend) fs->h = fs->xend - fs->x;
+    if (fs->tries >= fs->max_tries) fs->status = 3;
+}
+
+// FSAL commit of an accepted attempt: y <- y_n, k_1 <- k_7
+__global__ void flow_commit_kernel(const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0, const double2 *k6, size_t n)
+{
+    if (!fs->accepted) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        y[i] = yn[i];
+        k0[i] = k6[i];
+    }
+}
+
 int grid_for(const tufrg_model *m, size_t n)
 {
     const size_t want = (n + 255) / 256;
@@ -53,7 +126,7 @@ int grid_for(const tufrg_model *m, size_t n)
 
 }  // namespace
 
-cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, double h, const double *a,
+cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, const FlowDev *fs, const double *a,
                               double2 *const *k, int nk, size_t n)
 {
     StageArgs s{};
@@ -67,12 +140,12 @@ cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, do
     const size_t nd = 2 * n;
     PhaseScope ps(m, PH_RK);
     rk_combine_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
-                                                              reinterpret_cast<const double *>(y), h, s, nd);
+                                                              reinterpret_cast<const double *>(y), fs, s, nd);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, double h, const double *e,
-                            double2 *const *k, int nk, size_t n, double atol, double rtol)
+cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, const FlowDev *fs, const double *e,
+                            double2 *const *k, int nk, size_t n)
 {
     StageArgs s{};
     s.nk = 0;
@@ -84,7 +157,36 @@ cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn,
     }
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax + 2, 0, sizeof(unsigned long long), m->stream));
     PhaseScope ps(m, PH_RK);
-    rk_error_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(y, yn, h, s, n, atol, rtol, m->d_amax + 2);
+    rk_error_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(y, yn, fs, s, n, m->d_amax + 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_scalars(tufrg_model *m, const FlowDev *fs, double cj)
+{
+    m->launches++;
+    stage_scalars_kernel<<<1, 1, 0, m->stream>>>(fs, cj, m->d_scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_init(tufrg_model *m, FlowDev *fs)
+{
+    m->launches++;
+    flow_init_kernel<<<1, 1, 0, m->stream>>>(fs, m->d_amax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_decide(tufrg_model *m, FlowDev *fs)
+{
+    m->launches++;
+    flow_decide_kernel<<<1, 1, 0, m->stream>>>(fs, m->d_amax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0,
+                               const double2 *k6, size_t n)
+{
+    PhaseScope ps(m, PH_RK);
+    flow_commit_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(fs, y, yn, k0, k6, n);
     return cudaGetLastError();
 }
 

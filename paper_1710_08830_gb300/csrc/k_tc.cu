@@ -74,6 +74,7 @@ struct TcArgs {
     int *err;               // error flag (set to 1 on a wait time-out)
     int M, nff, ns2, nd, nt, tmem_cols;
     double scale;
+    const double *scal;     // optional device scale factor (scal[1])
 };
 
 __global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
     const int M = a.M, K2 = 2 * M;
     const size_t M2 = (size_t)M * M;
     const float *Aq = reinterpret_cast<const float *>(a.A + (size_t)q * M2);
+    const double scale = a.scal ? a.scale * a.scal[1] : a.scale;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
                     if (n >= M) continue;
                     const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
                     const size_t o = (size_t)q * M2 + (size_t)row * M + n;
-                    if (a.out64) a.out64[o] = make_double2(a.scale * (double)re, a.scale * (double)im);
-                    else a.out32[o] = make_float2((float)(a.scale * re), (float)(a.scale * im));
+                    if (a.out64) a.out64[o] = make_double2(scale * (double)re, scale * (double)im);
+                    else a.out32[o] = make_float2((float)(scale * re), (float)(scale * im));
                 }
             }
         }
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
 
 bool tc_supported(const tufrg_model *m) { return m->precision == TUFRG_SPLIT32 && m->products == TUFRG_PRODUCTS_TC; }
 
-cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double scale, double2 *d_out)
+cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
 {
     const int M = m->M, ns2 = m->ns * m->ns;
     const size_t M2 = (size_t)M * M, lper = (size_t)m->Nq * m->nd * ns2 * ns2;
@@ -238,6 +240,7 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double scale, double
         a.err = m->d_err;
         a.M = M; a.nff = m->nff; a.ns2 = ns2; a.nd = m->nd; a.nt = nt; a.tmem_cols = cols;
         a.scale = 1.0;
+        a.scal = nullptr;
         tc_cgemm_kernel<<<grid, TC_THREADS, smem, m->stream>>>(a);           // T = A L
         TUFRG_CUDA_TRY(cudaGetLastError());
         TcArgs b = a;
@@ -246,7 +249,8 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double scale, double
         b.Lc = nullptr;
         b.out32 = nullptr;
         b.out64 = o;
-        b.scale = scale * (ch == 0 ? 1.0 : 2.0);
+        b.scale = ch == 0 ? 1.0 : 2.0;
+        b.scal = m->d_scal;
         tc_cgemm_kernel<<<grid, TC_THREADS, smem, m->stream>>>(b);           // dX = c T A
         TUFRG_CUDA_TRY(cudaGetLastError());
     }

@@ -20,8 +20,7 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
 
 template <typename R>
 __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Lc, const int *dij, int Nq,
-                                 int M, int nff, int ns2, int nd, int chmask, double scaleP, double scaleC,
-                                 double2 *out)
+                                 int M, int nff, int ns2, int nd, int chmask, const double *scal, double2 *out)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,7 +50,7 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
         sT[i] = acc;
     }
     __syncthreads();
-    const double sc = ch == 0 ? scaleP : scaleC;
+    const double sc = (ch == 0 ? 1.0 : 2.0) * scal[1];   // c_P = 1, c_C = 2, times the output scale
     for (int i = threadIdx.x; i < (int)M2; i += blockDim.x) {
         const int r = i / M, c = i % M;
         C2 acc = mk(R(0), R(0));
@@ -62,11 +61,11 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 
 }  // namespace
 
-cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out)
+cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out)
 {
     const int M = m->M;
-    if (tc_supported(m)) return launch_vlv_tc(m, channel_mask, scale, d_out);
-    if (M > 64) return launch_vlv_large(m, d_A, channel_mask, scale, d_out);
+    if (tc_supported(m)) return launch_vlv_tc(m, channel_mask, d_out);
+    if (M > 64) return launch_vlv_large(m, d_A, channel_mask, d_out);
     const int ns2 = m->ns * m->ns;
     dim3 grid(m->Nq, 2);
     const int threads = 256;
@@ -76,13 +75,13 @@ cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, dou
         auto k = vlv_small_kernel<double>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, threads, smem, m->stream>>>(d_A, m->d_Lc, m->d_dij, m->Nq, M, m->nff, ns2, m->nd, channel_mask,
-                                              scale * 1.0, scale * 2.0, d_out);
+                                              m->d_scal, d_out);
     } else {
         const size_t smem = 3 * sizeof(float2) * M * M;
         auto k = vlv_small_kernel<float>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, threads, smem, m->stream>>>(m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, ns2, m->nd,
-                                              channel_mask, scale * 1.0, scale * 2.0, d_out);
+                                              channel_mask, m->d_scal, d_out);
     }
     return cudaGetLastError();
 }

@@ -37,6 +37,16 @@ struct GatherTerm {
     int kind;
 };
 
+// Device-resident state of one adaptive flow (Dormand-Prince 5(4) in x = ln T).
+struct FlowDev {
+    double x, h, xend, x_prev;
+    double amax_prev, amax, Tc, err;
+    double atol, rtol, stop;
+    int n_steps, n_reject, tries, max_tries;
+    int status;       // 0 running, 1 crossed the stop value, 2 reached T_end, 3 step limit, 4 non-finite, 5 step underflow
+    int accepted;     // 1 if the last attempt was accepted
+};
+
 struct LoopPlan {
     int kx_per_cta;     // threads (columns) per CTA
     int ky_chunks;      // number of ky ranges per column
@@ -81,7 +91,7 @@ struct tufrg_model {
     int *d_dpartner = nullptr;      // [nd] index of -delta
     int *d_hopR = nullptr;          // [nhop][2]
     double2 *d_hopt = nullptr;      // [nhop][ns][ns]
-    double cur_T = 0.0;             // temperature of the current Fermi tables
+    double *d_scal = nullptr;       // device scalars: [0] temperature of the current evaluation, [1] product scale
     int *d_dij = nullptr;           // [nff][nff]
     int *d_gofs[2] = {nullptr, nullptr};
     tufrg::GatherTerm *d_gterms[2] = {nullptr, nullptr};
@@ -110,6 +120,12 @@ struct tufrg_model {
     // flow work buffers
     double2 *d_y = nullptr, *d_yt = nullptr, *d_yn = nullptr, *d_k[7] = {};
     double2 *d_state_in = nullptr, *d_state_out = nullptr;   // host-buffer entry points
+    tufrg::FlowDev *d_flow = nullptr;        // device controller state
+    tufrg::FlowDev *h_flow = nullptr;        // pinned host mirror
+    cudaGraphExec_t step_graph = nullptr;    // one captured Dormand-Prince attempt
+    cudaStream_t flow_stream = nullptr;      // private capturable stream of the flow (joined to `stream` by events)
+    cudaEvent_t flow_ev = nullptr;
+    int step_graph_mask = 0;
 
     tufrg::LoopPlan plan{};
 
@@ -127,15 +143,21 @@ namespace tufrg {
 // ------------------------------------------------------------------ launchers (k_*.cu)
 cudaError_t launch_bands(tufrg_model *m);
 cudaError_t launch_density(tufrg_model *m, double mu, double T, double *h_out);
-cudaError_t launch_fermi(tufrg_model *m, double T);
+cudaError_t launch_fermi(tufrg_model *m);
+cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
 cudaError_t launch_loops(tufrg_model *m, int channel_mask);
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, int channel_mask);
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, int channel_mask, double2 *d_A);
-cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out);
-cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, double h, const double *a,
+cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
+cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, const FlowDev *fs, const double *a,
                               double2 *const *k, int nk, size_t n);
-cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, double h, const double *e,
-                            double2 *const *k, int nk, size_t n, double atol, double rtol);
+cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, const FlowDev *fs, const double *e,
+                            double2 *const *k, int nk, size_t n);
+cudaError_t launch_stage_scalars(tufrg_model *m, const FlowDev *fs, double cj);
+cudaError_t launch_flow_init(tufrg_model *m, FlowDev *fs);
+cudaError_t launch_flow_decide(tufrg_model *m, FlowDev *fs);
+cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0,
+                               const double2 *k6, size_t n);
 cudaError_t launch_amax_locate(tufrg_model *m, const double2 *d_A, size_t n, double amax);
 LoopPlan plan_loops(const tufrg_model *m);
 int dft_plan_nsplit(const tufrg_model *m);
@@ -143,10 +165,10 @@ bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
-cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double scale, double2 *d_out);
+cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
 bool tc_supported(const tufrg_model *m);
-cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double scale, double2 *d_out);
-cudaError_t launch_loop_records(tufrg_model *m, double T);
+cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out);
+cudaError_t launch_loop_records(tufrg_model *m);
 cudaError_t launch_loops2(tufrg_model *m, int ch);
 
 enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_N = 7 };

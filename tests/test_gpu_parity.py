@@ -338,3 +338,41 @@ def test_t2g_full_size_sampled_loops(prec):
     for ch in (0, 1):
         ref = o.loops_at(0.1, ch, qs)
         assert rel(L[ch][qs], ref) < (TOL64 if prec == "FP64" else 2e-5)
+
+
+# ------------------------------------------------------------------ batched uneven flows
+
+def test_flow_batch_matches_single_flows():
+    """Uneven Rashba/Hubbard instances (different meshes and bond sets) run together through
+    tufrg_flow_batch give exactly the flows tufrg_flow gives one at a time."""
+    api = _api()
+    specs = [inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=6, nc=4, n_ff=5),
+             inputs.rashba_hubbard(tp=-0.25, alpha=0.35, U=3.4, mu=-1.0, Lq=8, nc=3, n_ff=9),
+             inputs.hubbard_square(U=3.0, Lq=6, nc=4, n_ff=5, filling=0.9, T_mu=0.02),
+             inputs.rashba_hubbard(tp=-0.05, alpha=0.1, U=2.8, mu=-0.7, Lq=10, nc=2, n_ff=13)]
+    for prec in (api.FP64, api.SPLIT32):
+        single = []
+        for sp in specs:
+            m = api.Model(sp, prec)
+            _, r = m.flow(stop=6.0)
+            single.append(r)
+        streams = [torch.cuda.Stream() for _ in specs]
+        models = [api.Model(sp, prec, stream=s) for sp, s in zip(specs, streams)]
+        batch = api.flow_batch(models, stop=6.0)
+        for r1, r2 in zip(single, batch):
+            assert r1["n_steps"] == r2["n_steps"] and r1["n_reject"] == r2["n_reject"]
+            assert r1["crossed"] == r2["crossed"]
+            assert r1["Tc"] == r2["Tc"]
+
+
+def test_flow_batch_matches_oracle():
+    api = _api()
+    specs = [inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=6, nc=2, n_ff=5),
+             inputs.hubbard_square(U=3.0, Lq=4, nc=4, n_ff=5, filling=0.9, T_mu=0.02)]
+    streams = [torch.cuda.Stream() for _ in specs]
+    models = [api.Model(sp, api.FP64, stream=s) for sp, s in zip(specs, streams)]
+    batch = api.flow_batch(models, stop=4.0)
+    for sp, r in zip(specs, batch):
+        _, ref = oracle.Oracle(sp).flow(stop=4.0)
+        assert r["n_steps"] == ref["n_steps"]
+        assert r["Tc"] == pytest.approx(ref["Tc"], rel=1e-9)
