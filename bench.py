@@ -170,6 +170,8 @@ def main():
     ap.add_argument("--profile-rhs", type=int, default=0,
                     help="only evaluate this many split-precision right-hand sides on a seeded state (for ncu)")
     ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--batch-flows", type=int, default=0,
+                    help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
@@ -181,7 +183,7 @@ def main():
     import numpy as np
     import torch
     from paper_1710_08830_gb300 import inputs
-    from paper_1710_08830_gb300.api import FP64, SPLIT32, Model
+    from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, Model
 
     torch.cuda.set_device(local)
     if args.profile_rhs > 0:
@@ -288,6 +290,31 @@ def main():
                           "n_rhs": r64["n_rhs"], "n_steps": r64["n_steps"], "lead_channel": "PC"[r64["lead_channel"]],
                           "amax": r64["amax"]},
                  "note": "Tc is the crossing of max|A| = 50 when crossed == 1, else the end temperature 0.02"}
+    batch = None
+    if args.batch_flows > 0:
+        from paper_1710_08830_gb300.api import flow_batch
+        specs = inputs.rashba_batch(seed=rank, n=args.batch_flows)
+        streams = [torch.cuda.Stream() for _ in specs]
+        models = [Model(sp, SPLIT32, stream=st, products=PRODUCTS_SIMT) for sp, st in zip(specs, streams)]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rb = flow_batch(models)
+        t_batch = time.perf_counter() - t
+        del models
+        seq = []
+        t = time.perf_counter()
+        for sp in specs:
+            m = Model(sp, SPLIT32, products=PRODUCTS_SIMT)
+            _, r = m.flow()
+            seq.append(r)
+            del m
+        t_seq = time.perf_counter() - t
+        same = all(a["Tc"] == b["Tc"] and a["n_steps"] == b["n_steps"] for a, b in zip(rb, seq))
+        batch = {"instances": len(specs), "wall_s_batch": t_batch, "wall_s_one_by_one": t_seq,
+                 "flows_per_s": len(specs) / t_batch, "speedup": t_seq / t_batch,
+                 "rhs_total": int(sum(r["n_rhs"] for r in rb)), "crossed": int(sum(r["crossed"] for r in rb)),
+                 "identical_to_single_flows": same,
+                 "mix": {"Lq": sorted(set(sp.Lq for sp in specs)), "n_ff": sorted(set(sp.n_ff for sp in specs))}}
     clocks = sampler.stop()
 
     # ---------------- roofline of the dominant kernel (the loop k-sum)
@@ -343,6 +370,7 @@ def main():
                     "d2h_bytes_per_step": state_bytes},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "batch_flows": batch,
             "clocks": clocks,
             "peaks_source": peak_src,
             "wall_s_timed": t_wall,

@@ -291,6 +291,8 @@ int loops2_blocks_per_sm(const tufrg_model *m)
     if (ndyh == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<1, 0>, 32 * WARPS, smem);
     if (ndyh == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<2, 0>, 32 * WARPS, smem);
     if (ndyh == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<3, 0>, 32 * WARPS, smem);
+    if (ndyh == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<4, 0>, 32 * WARPS, smem);
+    if (ndyh == 5) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<5, 0>, 32 * WARPS, smem);
     return (e == cudaSuccess && n > 0) ? n : 4;
 }
 
@@ -298,7 +300,7 @@ bool loops2_supported(const tufrg_model *m)
 {
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
-    return m->ns == 2 && m->precision != TUFRG_FP64 && ndyh <= 3 && (int)m->dxs.size() <= MAXD;
+    return m->ns == 2 && m->precision != TUFRG_FP64 && ndyh <= 5 && (int)m->dxs.size() <= MAXD;
 }
 
 cudaError_t launch_loop_records(tufrg_model *m)
@@ -339,6 +341,8 @@ cudaError_t launch_loops2(tufrg_model *m, int ch)
     case 1: return ch == 0 ? launch2<1, 0>(m, a) : launch2<1, 1>(m, a);
     case 2: return ch == 0 ? launch2<2, 0>(m, a) : launch2<2, 1>(m, a);
     case 3: return ch == 0 ? launch2<3, 0>(m, a) : launch2<3, 1>(m, a);
+    case 4: return ch == 0 ? launch2<4, 0>(m, a) : launch2<4, 1>(m, a);
+    case 5: return ch == 0 ? launch2<5, 0>(m, a) : launch2<5, 1>(m, a);
     default: return cudaErrorNotSupported;
     }
 }
