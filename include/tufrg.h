@@ -222,6 +222,46 @@ tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, const double
  * is the wall time of the whole batch.  Returns the first error status (all results are filled). */
 tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *opts, tufrg_flow_result *results);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned loop surrogate (an addition with no counterpart in the paper).
+ * A multilayer perceptron n_in -> [width, GELU] x depth -> n_out with BF16 weights, FP32
+ * accumulation and FP32 master weights (Adam, mean-squared-error loss).  Training passes round the
+ * activations to BF16; inference (tufrg_mlp_forward, the surrogate) keeps them in FP32.
+ * Parameters are one flat FP32 vector: for each linear layer l, W_l [din][dout] row-major then
+ * b_l [dout].  All device buffers are FP32, row-major [batch][features].
+ * ------------------------------------------------------------------------------------------ */
+typedef struct tufrg_mlp tufrg_mlp;
+tufrg_status tufrg_mlp_create(int n_in, int width, int depth, int n_out, unsigned long long seed, void *cuda_stream,
+                              tufrg_mlp **out);
+void tufrg_mlp_free(tufrg_mlp *net);
+const char *tufrg_mlp_last_error(const tufrg_mlp *net);
+long long tufrg_mlp_num_params(const tufrg_mlp *net);
+tufrg_status tufrg_mlp_get_params(tufrg_mlp *net, float *h_params);
+tufrg_status tufrg_mlp_set_params(tufrg_mlp *net, const float *h_params);   /* also resets the Adam state */
+tufrg_status tufrg_mlp_forward(tufrg_mlp *net, const float *d_X, int batch, float *d_Y);
+/* gradient of the mean squared error mean((Y - T)^2) w.r.t. the flat parameters into d_grad */
+tufrg_status tufrg_mlp_gradients(tufrg_mlp *net, const float *d_X, const float *d_T, int batch, float *d_grad, float *h_loss);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; h_loss (may be NULL) receives the loss */
+tufrg_status tufrg_mlp_train_step(tufrg_mlp *net, const float *d_X, const float *d_T, int batch, float lr, float *h_loss);
+
+/* Attach a trained network as the loop surrogate of a split-precision two-band model (net = NULL
+ * detaches).  Features per transfer momentum q = 2 pi (qx, qy)/Lq: sin(n qx), cos(n qx), sin(n qy),
+ * cos(n qy) for n = 1..4, then (log T + 0.8)/3.1, (alpha - 0.2)/0.2, (t' + 0.15)/0.15, (mu + 0.9)/0.3 with
+ * h_feature_params = {alpha, t', mu}.  Output j = ((ch*n_delta + d)*16 + ab)*2 + (0 re, 1 im) is
+ * un-standardised as L = (y_j * h_std[j] + h_mean[j]) / T.  Every evaluation of the loops then checks
+ * the surrogate against the direct k-sum at the n_check listed transfer momenta (relative Frobenius
+ * norm over both channels) and falls back to the direct k-sum when the residual exceeds resid_tol.
+ * A failed check switches the surrogate off (direct k-sum, network skipped) until it is re-armed:
+ * tufrg_loops, tufrg_rhs, tufrg_rhs_host and every flow start re-arm it, so within a flow it serves
+ * an unbroken first stretch.  All decisions are taken on the device.  The network must outlive its use
+ * by the model. */
+tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_mean, const float *h_std,
+                                 const double *h_feature_params, double resid_tol, int n_check, const int *h_check_q);
+/* Evaluations since the surrogate was attached that kept it, that fell back after a failed check, and
+ * that skipped it because it was off (synchronises; any pointer may be NULL). */
+tufrg_status tufrg_surrogate_stats(tufrg_model *m, long long *accepted, long long *rejected, long long *skipped);
+
+
 /* Optional CUDA-event timing on the model's stream (used by the benchmark).
  * tufrg_timing_begin resets the counters and starts recording; every later
  * kernel phase is bracketed by two events.  tufrg_timing_end synchronises the

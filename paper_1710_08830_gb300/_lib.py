@@ -81,6 +81,25 @@ def lib():
             L.tufrg_loops_noalloc.restype = C.c_int
             L.tufrg_flow_batch.argtypes = [vp, i, C.POINTER(FlowOpts), vp]
             L.tufrg_flow_batch.restype = C.c_int
+            L.tufrg_mlp_create.argtypes = [i, i, i, i, C.c_ulonglong, vp, C.POINTER(vp)]
+            L.tufrg_mlp_free.argtypes = [vp]
+            L.tufrg_mlp_free.restype = None
+            L.tufrg_mlp_last_error.argtypes = [vp]
+            L.tufrg_mlp_last_error.restype = C.c_char_p
+            L.tufrg_mlp_num_params.argtypes = [vp]
+            L.tufrg_mlp_num_params.restype = C.c_longlong
+            L.tufrg_mlp_get_params.argtypes = [vp, vp]
+            L.tufrg_mlp_set_params.argtypes = [vp, vp]
+            L.tufrg_mlp_forward.argtypes = [vp, vp, i, vp]
+            L.tufrg_mlp_gradients.argtypes = [vp, vp, vp, i, vp, C.POINTER(C.c_float)]
+            L.tufrg_mlp_train_step.argtypes = [vp, vp, vp, i, C.c_float, C.POINTER(C.c_float)]
+            for fn in ("tufrg_mlp_create", "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward",
+                       "tufrg_mlp_gradients", "tufrg_mlp_train_step"):
+                getattr(L, fn).restype = C.c_int
+            L.tufrg_set_surrogate.argtypes = [vp, vp, vp, vp, vp, d, i, vp]
+            L.tufrg_set_surrogate.restype = C.c_int
+            L.tufrg_surrogate_stats.argtypes = [vp] + [C.POINTER(C.c_longlong)] * 3
+            L.tufrg_surrogate_stats.restype = C.c_int
             L.tufrg_timing_begin.argtypes = [vp]
             L.tufrg_timing_end.argtypes = [vp, vp, i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for fn in ("tufrg_init_model", "tufrg_dims", "tufrg_deltas", "tufrg_gather_table", "tufrg_bands",
@@ -95,4 +114,6 @@ def lib():
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
            "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info",
-           "tufrg_flow_batch")
+           "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
+           "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
+           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")

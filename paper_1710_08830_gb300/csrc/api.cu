@@ -210,6 +210,7 @@ void release(tufrg_model *m)
         if (p) cudaFree(p);
     for (auto &e : m->evpool) cudaEventDestroy(e);
     m->evpool.clear();
+    tufrg_set_surrogate(m, nullptr, nullptr, nullptr, nullptr, 0.0, 0, nullptr);
     if (m->h_flow) cudaFreeHost(m->h_flow);
     if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
     if (m->flow_ev) cudaEventDestroy(m->flow_ev);
@@ -289,6 +290,7 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
     *m->h_flow = f;
     CK(cudaMemcpyAsync(m->d_flow, m->h_flow, sizeof(FlowDev), cudaMemcpyHostToDevice, m->stream), "copy flow state");
     CK(cudaMemsetAsync(m->d_y, 0, sizeof(double2) * n, m->stream), "zero state");
+    CK(surrogate_rearm(m), "re-arm surrogate");
     // k1 = f(x0, y0) and max|A| of the initial state
     CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
     tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0]);
@@ -640,6 +642,7 @@ tufrg_status tufrg_loops(tufrg_model *m, double T, int channel_mask, void *d_loo
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     CK(launch_set_scalars(m, T, 1.0), "set temperature");
+    CK(surrogate_rearm(m), "re-arm surrogate");
     CK(launch_fermi(m), "fermi tables");
     CK(launch_loops(m, channel_mask), "loop k-sum");
     const size_t per = (size_t)m->Nq * m->nd * m->ns * m->ns * m->ns * m->ns;
@@ -672,6 +675,7 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     CK(launch_set_scalars(m, T, 1.0), "set temperature");
+    CK(surrogate_rearm(m), "re-arm surrogate");
     return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask, reinterpret_cast<double2 *>(d_dstate));
 }
 

@@ -240,8 +240,9 @@ __global__ void __launch_bounds__(32 * WARPS) loops_ns2_kernel(LoopArgs<R> a)
 template <typename R>
 __global__ void loops_reduce_kernel(const typename cpx<R>::t *part, int n_part, int ndx, int ndyh,
                                     const int *dslot, const int *deltas, int nd, int Nq, double inv_nk,
-                                    double2 *out64, typename cpx<R>::t *out32)
+                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
 {
+    if (skip && *skip) return;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)Nq * nd * NS4;
     if (idx >= total) return;
@@ -305,8 +306,22 @@ LoopPlan plan_loops(const tufrg_model *m)
     return p;
 }
 
+cudaError_t launch_loops_reduce_f32(tufrg_model *m, const float2 *part, int n_s, double2 *out64, float2 *out32,
+                                    const int *skip)
+{
+    int ndyh = 0;
+    for (int v : m->dys) ndyh += v >= 0;
+    const size_t total = (size_t)n_s * m->nd * NS4;
+    PhaseScope ps(m, PH_LOOPRED);
+    loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+        part, m->plan.n_partials, (int)m->dxs.size(), ndyh, m->d_dslot, m->d_deltas, m->nd, n_s, 1.0 / (double)m->Nk,
+        out64, out32, skip);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_loops(tufrg_model *m, int channel_mask)
 {
+    if (m->sur) TUFRG_CUDA_TRY(launch_surrogate(m, channel_mask));
     if (m->ns != NS) return loops_gen_supported(m) ? launch_loops_gen(m, channel_mask) : cudaErrorNotSupported;
     const LoopPlan &pl = m->plan;
     const int ndx = (int)m->dxs.size();
@@ -323,7 +338,8 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
                 reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq,
-                inv_nk, m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4);
+                inv_nk, m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4,
+                m->sur ? m->d_sur_flag : nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};
@@ -350,7 +366,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<double><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
                 a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq, inv_nk,
-                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr);
+                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else {
             LoopArgs<float> a{};
@@ -377,7 +393,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
                 a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq, inv_nk,
-                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4);
+                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         }
     }

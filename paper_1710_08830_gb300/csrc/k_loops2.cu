@@ -42,6 +42,8 @@ struct Args2 {
     int ky_chunks, ky_len;
     float thr;               // degenerate-pair switch, used when Tp is null
     const double *Tp;        // device temperature: switch = 1e-2 * (*Tp)
+    const int *s_list;       // optional: CTA x evaluates transfer momentum s_list[x] (partials indexed by x)
+    const int *skip;         // optional: the whole launch returns at once when *skip != 0
 };
 
 // (t1,t3,t2,t4) -> ab index of the compact loop (P: a=(t2,t1), b=(t4,t3); C: a=(t1,t2), b=(t3,t4))
@@ -67,6 +69,7 @@ template <int NDYH, int WHICH>
 __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.skip && *a.skip) return;   // uniform over the grid
     float2 *ptab = reinterpret_cast<float2 *>(smem_raw);
     float *red = reinterpret_cast<float *>(smem_raw + ((sizeof(float2) * a.Lf + 15) & ~size_t(15)));
     const int Lf = a.Lf;
@@ -78,8 +81,9 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     __syncthreads();
 
     constexpr int NT = 32 * WARPS;
-    const int s = blockIdx.x;
-    const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
+    const int s = blockIdx.x;                                    // slot of the partial sums
+    const int sq = a.s_list ? a.s_list[blockIdx.x] : blockIdx.x;  // transfer momentum
+    const int sx = (sq / a.Lq) * a.nc, sy = (sq % a.Lq) * a.nc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int kx = blockIdx.y * NT + threadIdx.x;
     const float thr = a.Tp ? (float)(1e-2 * *a.Tp) : a.thr;
@@ -266,9 +270,9 @@ __global__ void rec_kernel(const double *E, const double2 *U, int Nk, int Lf, do
 }
 
 template <int NDYH, int WHICH>
-cudaError_t launch2(tufrg_model *m, const Args2 &a)
+cudaError_t launch2(tufrg_model *m, const Args2 &a, int n_s)
 {
-    dim3 grid(m->Nq, (m->Lf + 32 * WARPS - 1) / (32 * WARPS), a.ky_chunks);
+    dim3 grid(n_s, (m->Lf + 32 * WARPS - 1) / (32 * WARPS), a.ky_chunks);
     const size_t flush = sizeof(float) * WARPS * 32 * (2 * NDYH * 16 + 1);
     const size_t smem = ((sizeof(float2) * m->Lf + 15) & ~size_t(15)) + flush;
     auto kern = loops2_kernel<NDYH, WHICH>;
@@ -310,13 +314,16 @@ cudaError_t launch_loop_records(tufrg_model *m)
     return cudaGetLastError();
 }
 
-// Loop sums of the channels in channel_mask into the partial buffer (no reduction).
-cudaError_t launch_loops2(tufrg_model *m, int ch)
+// Loop sums of channel ch into the partial buffer (no reduction).  With s_list, only the
+// listed transfer momenta (n_list of them) are evaluated, into partial slots 0..n_list-1 of part.
+cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_list, float2 *part, const int *skip)
 {
     const LoopPlan &pl = m->plan;
     Args2 a{};
     a.rec = m->d_rec;
-    a.part = reinterpret_cast<float2 *>(m->d_part);
+    a.part = part;
+    a.s_list = s_list;
+    a.skip = skip;
     a.Lq = m->Lq; a.nc = m->nc; a.Lf = m->Lf;
     a.ndx = (int)m->dxs.size();
     int ndyh = 0;
@@ -337,14 +344,20 @@ cudaError_t launch_loops2(tufrg_model *m, int ch)
     a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
     a.thr = 0.f;
     a.Tp = m->d_scal;
+    const int n_s = s_list ? n_list : m->Nq;
     switch (ndyh) {
-    case 1: return ch == 0 ? launch2<1, 0>(m, a) : launch2<1, 1>(m, a);
-    case 2: return ch == 0 ? launch2<2, 0>(m, a) : launch2<2, 1>(m, a);
-    case 3: return ch == 0 ? launch2<3, 0>(m, a) : launch2<3, 1>(m, a);
-    case 4: return ch == 0 ? launch2<4, 0>(m, a) : launch2<4, 1>(m, a);
-    case 5: return ch == 0 ? launch2<5, 0>(m, a) : launch2<5, 1>(m, a);
+    case 1: return ch == 0 ? launch2<1, 0>(m, a, n_s) : launch2<1, 1>(m, a, n_s);
+    case 2: return ch == 0 ? launch2<2, 0>(m, a, n_s) : launch2<2, 1>(m, a, n_s);
+    case 3: return ch == 0 ? launch2<3, 0>(m, a, n_s) : launch2<3, 1>(m, a, n_s);
+    case 4: return ch == 0 ? launch2<4, 0>(m, a, n_s) : launch2<4, 1>(m, a, n_s);
+    case 5: return ch == 0 ? launch2<5, 0>(m, a, n_s) : launch2<5, 1>(m, a, n_s);
     default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t launch_loops2(tufrg_model *m, int ch)
+{
+    return launch_loops2_ex(m, ch, nullptr, 0, reinterpret_cast<float2 *>(m->d_part), m->sur ? m->d_sur_flag : nullptr);
 }
 
 }  // namespace tufrg

@@ -55,6 +55,8 @@ struct LoopPlan {
 
 }  // namespace tufrg
 
+struct tufrg_mlp;
+
 struct tufrg_model {
     // ---- descriptor copy
     int ns = 0, nhop = 0, nff = 0, Lq = 0, nc = 0, Lf = 0, Nq = 0, Nk = 0, M = 0, precision = 0;
@@ -129,6 +131,21 @@ struct tufrg_model {
 
     tufrg::LoopPlan plan{};
 
+    // ---- learned loop surrogate (optional)
+    tufrg_mlp *sur = nullptr;       // network (not owned)
+    double sur_tol = 1e-3;          // relative Frobenius residual accepted at the check momenta
+    double sur_params[3] = {0, 0, 0};   // alpha, t', mu features of this model
+    int n_check = 0;
+    int *d_check_q = nullptr;       // [n_check] transfer momenta of the residual check
+    float *d_sur_X = nullptr;       // [Nq][20] features
+    float *d_sur_Y = nullptr;       // [Nq][n_out] network output (standardised)
+    float *d_sur_mean = nullptr, *d_sur_std = nullptr;   // [n_out]
+    float2 *d_chk_part = nullptr;   // partial sums of the check momenta
+    double2 *d_chk = nullptr;       // [2][n_check][nd][16] direct loops at the check momenta
+    int *d_sur_flag = nullptr;      // [0] 1: surrogate accepted for this evaluation (direct k-sum skipped)
+                                    // [1] 1: a check failed since the last re-arm; surrogate off until then
+    unsigned long long *d_sur_count = nullptr;   // [3] accepted, rejected, skipped
+
     // ---- optional event timing (phases as listed in tufrg.h)
     bool timing = false;
     long long launches = 0, loop_launches = 0;
@@ -170,6 +187,11 @@ bool tc_supported(const tufrg_model *m);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out);
 cudaError_t launch_loop_records(tufrg_model *m);
 cudaError_t launch_loops2(tufrg_model *m, int ch);
+cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_list, float2 *part, const int *skip);
+cudaError_t launch_surrogate(tufrg_model *m, int channel_mask);
+cudaError_t mlp_forward_on(tufrg_mlp *n, cudaStream_t s, const float *X, int batch, float *Y, const int *skip);
+cudaError_t surrogate_rearm(tufrg_model *m);
+void mlp_dims(const tufrg_mlp *n, int *n_in, int *n_out);
 
 enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_N = 7 };
 
