@@ -1,6 +1,7 @@
 // C ABI of libtufrg: model set-up (tables, memory), the right-hand side and the flow.
 // Every entry point returns a tufrg_status and never throws across the boundary.
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -183,6 +184,49 @@ void build_gather_tables(tufrg_model *m)
     for (auto &kv : phv) { m->phv[2 * kv.second] = kv.first.first; m->phv[2 * kv.second + 1] = kv.first.second; }
 }
 
+// The projection gather terms flattened per output matrix entry (same terms, same order as the
+// per-(R, R') lists): for output channel ch and entry (row, col) = ((R, a), (R', b)), each term is
+// the flat index of its source entry in the Fourier transforms [2][ncls][M][M] (high bit set when
+// the term enters with a minus sign) and its phase-table column.  The orbital index pairs follow the
+// channel layouts: P rows (s1,s2), columns (s4,s3); C rows (s1,s3), columns (s4,s2).
+void build_entry_tables(const tufrg_model *m, std::vector<int> ofs[2], std::vector<int2> terms[2],
+                        std::vector<double2> v0d[2])
+{
+    const int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = m->M;
+    const long M2 = (long)M * M;
+    for (int ch = 0; ch < 2; ch++) {
+        ofs[ch].assign(M2 + 1, 0);
+        terms[ch].clear();
+        v0d[ch].assign(M2, make_double2(0.0, 0.0));
+        for (int row = 0; row < M; row++)
+            for (int col = 0; col < M; col++) {
+                const int iR = row / ns2, rp = row % ns2, iRp = col / ns2, cp = col % ns2;
+                int s1, s2, s3, s4;
+                if (ch == 0) { s1 = rp / ns; s2 = rp % ns; s4 = cp / ns; s3 = cp % ns; }
+                else         { s1 = rp / ns; s3 = rp % ns; s4 = cp / ns; s2 = cp % ns; }
+                if (iR == 0 && iRp == 0) {
+                    const int v = ((s1 * ns + s2) * ns + s3) * ns + s4;
+                    v0d[ch][(long)row * M + col] = make_double2(m->V0[2 * v], m->V0[2 * v + 1]);
+                }
+                const int pair = iR * nff + iRp;
+                for (int t = m->gofs[ch][pair]; t < m->gofs[ch][pair + 1]; t++) {
+                    const tufrg::GatherTerm &g = m->gterms[ch][t];
+                    int sch, sr, sc;
+                    bool neg;
+                    switch (g.kind) {
+                    case 0: sch = 1; sr = s1 * ns + s3; sc = s4 * ns + s2; neg = false; break;   // P <- C
+                    case 1: sch = 1; sr = s1 * ns + s4; sc = s3 * ns + s2; neg = true; break;    // P <- D
+                    case 2: sch = 0; sr = s1 * ns + s2; sc = s4 * ns + s3; neg = false; break;   // C <- P
+                    default: sch = 1; sr = s1 * ns + s4; sc = s3 * ns + s2; neg = true; break;   // C <- D
+                    }
+                    const long idx = ((long)sch * m->ncls + g.cls) * M2 + (long)(g.i1 * ns2 + sr) * M + g.i2 * ns2 + sc;
+                    terms[ch].push_back(make_int2((int)idx | (neg ? INT_MIN : 0), g.ph));
+                }
+                ofs[ch][(long)row * M + col + 1] = (int)terms[ch].size();
+            }
+    }
+}
+
 // e^{i q.R} for every coarse q and every listed vector (exact lattice phases).
 std::vector<double2> phase_table(int Lq, const std::vector<int> &vecs)
 {
@@ -203,7 +247,8 @@ void release(tufrg_model *m)
                     m->d_dij, m->d_gofs[0], m->d_gofs[1], m->d_gterms[0], m->d_gterms[1], m->d_ph, m->d_clsph,
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
-                    m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow};
+                    m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
+                    m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -221,12 +266,20 @@ size_t state_elems(const tufrg_model *m) { return (size_t)2 * m->Nq * m->M * m->
 
 // One evaluation of the right-hand side into d_out at the temperature held in m->d_scal[0],
 // each channel scaled by c_X * m->d_scal[1] (1 for dX/dT, T for the flow variable ln T).
-tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double2 *d_out)
+// The split path evaluates on an FP32 copy of the state: d_state32 when the caller has already
+// written one (the flow's stage combinations do), else a conversion of d_state into m->d_X32.
+tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double2 *d_out, const float2 *d_state32)
 {
+    const bool split = m->precision != TUFRG_FP64;
+    if (split && !d_state32) {
+        CK(launch_to_f32(m, d_state, m->d_X32, state_elems(m)), "state conversion");
+        d_state32 = m->d_X32;
+    }
     CK(launch_fermi(m), "fermi tables");
     CK(launch_loops(m, mask), "loop k-sum");
-    CK(launch_dft(m, d_state, mask), "Fourier transform");
-    CK(launch_project(m, d_state, mask, m->d_A), "projections");
+    CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
+    // the split path's products read the FP32 copy only
+    CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A), "projections");
     CK(launch_vlv(m, m->d_A, mask, d_out), "V.L.V products");
     return TUFRG_OK;
 }
@@ -251,11 +304,14 @@ tufrg_status enqueue_attempt(tufrg_model *m, int mask)
     const size_t n = state_elems(m);
     double2 *k[7];
     for (int i = 0; i < 7; i++) k[i] = m->d_k[i];
+    const bool split = m->precision != TUFRG_FP64;
     for (int j = 1; j < 7; j++) {
-        double2 *dst = j == 6 ? m->d_yn : m->d_yt;
-        CK(launch_rk_combine(m, dst, m->d_y, m->d_flow, DP_A[j], k, j, n), "stage combination");
+        // the stage states are FP64 (and only the last one, the candidate solution, is kept); on the
+        // split path the combination writes the FP32 copy that the evaluation reads instead
+        double2 *dst = j == 6 ? m->d_yn : (split ? nullptr : m->d_yt);
+        CK(launch_rk_combine(m, dst, split ? m->d_X32 : nullptr, m->d_y, m->d_flow, DP_A[j], k, j, n), "stage combination");
         CK(launch_stage_scalars(m, m->d_flow, DP_C[j]), "stage temperature");
-        tufrg_status st = rhs_device(m, dst, mask, k[j]);
+        tufrg_status st = rhs_device(m, dst, mask, k[j], split ? m->d_X32 : nullptr);
         if (st != TUFRG_OK) return st;
     }
     CK(launch_rk_error(m, m->d_y, m->d_yn, m->d_flow, DP_E, k, 7, n), "error norm");
@@ -293,7 +349,7 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
     CK(surrogate_rearm(m), "re-arm surrogate");
     // k1 = f(x0, y0) and max|A| of the initial state
     CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
-    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0]);
+    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0], nullptr);
     if (st != TUFRG_OK) return st;
     CK(launch_flow_init(m, m->d_flow), "flow init");
     if (!m->step_graph || m->step_graph_mask != o->channel_mask) {
@@ -370,7 +426,7 @@ tufrg_status flow_finish(tufrg_model *m, void *d_state_out, tufrg_flow_result *r
     res->Tc = res->crossed ? f.Tc : res->T_last;
     // the last stage-7 projection belongs to the last accepted state when the flow stopped on an accepted step
     const size_t nA = state_elems(m), M2 = (size_t)m->M * m->M;
-    CK(launch_amax_locate(m, m->d_A, nA, res->amax), "locate maximum");
+    CK(launch_amax_locate(m, nA), "locate maximum");
     unsigned long long b[4];
     CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
     CK(cudaStreamSynchronize(m->stream), "sync");
@@ -473,6 +529,18 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(upload(&m->d_gofs[ch], m->gofs[ch], m->stream), "upload gather tables");
         CK(upload(&m->d_gterms[ch], m->gterms[ch], m->stream), "upload gather tables");
     }
+    if (2L * m->ncls * (long)m->M * m->M >= (long)INT_MAX) return fail(m, TUFRG_ETOOBIG, "projection tables exceed 2^31 entries");
+    {
+        std::vector<int> eofs[2];
+        std::vector<int2> eterms[2];
+        std::vector<double2> v0d[2];
+        build_entry_tables(m, eofs, eterms, v0d);
+        for (int ch = 0; ch < 2; ch++) {
+            CK(upload(&m->d_eofs[ch], eofs[ch], m->stream), "upload projection tables");
+            if (!eterms[ch].empty()) CK(upload(&m->d_eterms[ch], eterms[ch], m->stream), "upload projection tables");
+            CK(upload(&m->d_v0d[ch], v0d[ch], m->stream), "upload projection tables");
+        }
+    }
     {
         std::vector<double2> ph = phase_table(m->Lq, m->phv);
         CK(upload(&m->d_ph, ph, m->stream), "upload phase table");
@@ -497,6 +565,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(dalloc(&m->d_ft32, Nk * ns), "cudaMalloc Fermi table");
         CK(dalloc(&m->d_Lc32, 2 * (size_t)m->Nq * m->nd * ns4), "cudaMalloc loops");
         CK(dalloc(&m->d_A32, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");
+        CK(dalloc(&m->d_X32, 2 * (size_t)m->Nq * M2), "cudaMalloc state copy");
     }
     CK(dalloc(&m->d_Lc, 2 * (size_t)m->Nq * m->nd * ns4), "cudaMalloc loops");
     int ndyh = 0;
@@ -519,7 +588,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
        "cudaMalloc Fourier partials");
     if (split) CK(dalloc(&m->d_Xr32, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
     if (loops2_supported(m)) CK(dalloc(&m->d_rec, Nk * 3), "cudaMalloc loop records");
-    CK(dalloc(&m->d_A, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");
+    if (!split) CK(dalloc(&m->d_A, 2 * (size_t)m->Nq * M2), "cudaMalloc projections");   // split: FP32 copy only
     CK(dalloc(&m->d_amax, 4), "cudaMalloc reductions");
     CK(dalloc(&m->d_red, 512), "cudaMalloc reductions");
 
@@ -541,6 +610,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     } else {
         m->mu = d.mu;
     }
+    if (loops2_supported(m)) CK(launch_loop_records_static(m), "loop records");
     CK(cudaStreamSynchronize(m->stream), "init sync");
     if (split && d.products == TUFRG_PRODUCTS_AUTO) {
         // autotune the products backend on this model's sizes (the cost does not depend on the values)
@@ -658,8 +728,13 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
     if (!m || !d_state || !d_Ahat) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     const double2 *st = reinterpret_cast<const double2 *>(d_state);
-    CK(launch_dft(m, st, channel_mask), "Fourier transform");
-    CK(launch_project(m, st, channel_mask, reinterpret_cast<double2 *>(d_Ahat)), "projections");
+    const float2 *st32 = nullptr;
+    if (m->precision != TUFRG_FP64) {
+        CK(launch_to_f32(m, st, m->d_X32, state_elems(m)), "state conversion");
+        st32 = m->d_X32;
+    }
+    CK(launch_dft(m, st, st32, channel_mask), "Fourier transform");
+    CK(launch_project(m, st, st32, channel_mask, reinterpret_cast<double2 *>(d_Ahat)), "projections");
     if (h_amax) {
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, m->d_amax, sizeof(bits), cudaMemcpyDeviceToHost, m->stream), "copy max");
@@ -676,7 +751,8 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     CK(launch_set_scalars(m, T, 1.0), "set temperature");
     CK(surrogate_rearm(m), "re-arm surrogate");
-    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask, reinterpret_cast<double2 *>(d_dstate));
+    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask, reinterpret_cast<double2 *>(d_dstate),
+                      nullptr);
 }
 
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)

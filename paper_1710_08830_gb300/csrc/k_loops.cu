@@ -236,12 +236,15 @@ __global__ void __launch_bounds__(32 * WARPS) loops_ns2_kernel(LoopArgs<R> a)
     if (NABG > 2 && g == 3) loop_body<R, NDYH, NAB, (NABG > 2 ? 3 : 0), WHICH>(a, ptab, red);
 }
 
-// Sum the partials in a fixed order, scale by 1/Nk and write both Hermitian halves.
+// Sum the partials in a fixed order, scale by 1/Nk and write both Hermitian halves.  The sum runs in
+// the partials' own precision (FP32 on the split path: this GPU's FP64 rate would make the
+// reduction, not the memory traffic, its bound), with four loads in flight per thread.
 template <typename R>
-__global__ void loops_reduce_kernel(const typename cpx<R>::t *part, int n_part, int ndx, int ndyh,
+__global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
                                     const int *dslot, const int *deltas, int nd, int Nq, double inv_nk,
                                     double2 *out64, typename cpx<R>::t *out32, const int *skip)
 {
+    using C2 = typename cpx<R>::t;
     if (skip && *skip) return;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)Nq * nd * NS4;
@@ -254,18 +257,28 @@ __global__ void loops_reduce_kernel(const typename cpx<R>::t *part, int n_part, 
     const int ia = ab / NS2, ib = ab % NS2;
     const int src_ab = half ? ab : ib * NS2 + ia;
     const int slot = dslot[d];   // dxi * ndyh + dyi of the half-plane representative of +-delta
-    double re = 0.0, im = 0.0;
-    const R *pr = reinterpret_cast<const R *>(part);
-    for (int p = 0; p < n_part; p++) {
-        const size_t o = (((size_t)s * n_part + p) * ndx * ndyh + slot) * NS4 + src_ab;
-        re += (double)pr[2 * o];
-        im += (double)pr[2 * o + 1];
+    const size_t stride = (size_t)ndx * ndyh * NS4;
+    const C2 *src = part + (size_t)s * n_part * stride + (size_t)slot * NS4 + src_ab;
+    R re = 0, im = 0;
+    int p = 0;
+    for (; p + 4 <= n_part; p += 4) {
+        C2 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = src[(size_t)(p + j) * stride];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            re += v[j].x;
+            im += v[j].y;
+        }
     }
-    re *= inv_nk;
-    im *= inv_nk;
-    if (!half) im = -im;
-    if (out64) out64[idx] = make_double2(re, im);
-    if (out32) out32[idx] = mk(R(re), R(im));
+    for (; p < n_part; p++) {
+        const C2 v = src[(size_t)p * stride];
+        re += v.x;
+        im += v.y;
+    }
+    const double sre = (double)re * inv_nk, sim = (half ? 1.0 : -1.0) * (double)im * inv_nk;
+    if (out64) out64[idx] = make_double2(sre, sim);
+    if (out32) out32[idx] = mk(R(sre), R(sim));
 }
 
 template <typename R, int NDYH, int NAB, int WHICH>

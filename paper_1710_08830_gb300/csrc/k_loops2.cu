@@ -242,31 +242,44 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     }
 }
 
-// Per-temperature record of one fine k: band-0 projector and the Fermi data of both bands, FP32.
-__global__ void rec_kernel(const double *E, const double2 *U, int Nk, int Lf, double mu, double T_value,
-                           const double *Tp, float4 *rec)
+// Record of one fine k (FP32, three planes [j][ky][kx]): plane 0 = (rho00, Re rho01, Im rho01, e0),
+// plane 1 = (e1, g0, g1, g'0), plane 2 = (g'1, 0, 0, 0), with e = E - mu, g = dF/dT-type weight
+// derivative of the Fermi function and g' its derivative in e.  The projector and e do not depend on
+// T and are written once per model; only g and g' are refreshed per evaluation.
+__global__ void rec_static_kernel(const double *E, const double2 *U, int Nk, int Lf, double mu, float4 *rec)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nk) return;
-    const double T = Tp ? *Tp : T_value;   // device-resident temperature when given
-    float e[2], g[2], gp[2];
-#pragma unroll
-    for (int l = 0; l < 2; l++) {
-        const double x = (E[2 * k + l] - mu) / T, ax = fabs(x);
-        const double z = exp(-ax);
-        const double h = z / ((1.0 + z) * (1.0 + z));
-        e[l] = (float)(E[2 * k + l] - mu);
-        g[l] = (float)(x / T * h);
-        gp[l] = (float)(h / (T * T) * (1.0 - ax * (1.0 - z) / (1.0 + z)));
-    }
     // rho^0 = U_{.0} U*_{.0}: rho00 = |U_00|^2, rho01 = U_00 conj(U_10)
     const double2 u0 = U[(size_t)k * 4 + 0], u1 = U[(size_t)k * 4 + 2];
     const int kx = k / Lf, ky = k % Lf;
     const size_t t = (size_t)ky * Lf + kx, plane = (size_t)Lf * Lf;
     rec[t] = make_float4((float)(u0.x * u0.x + u0.y * u0.y), (float)(u0.x * u1.x + u0.y * u1.y),
-                         (float)(u0.y * u1.x - u0.x * u1.y), e[0]);
-    rec[plane + t] = make_float4(e[1], g[0], g[1], gp[0]);
-    rec[2 * plane + t] = make_float4(gp[1], 0.f, 0.f, 0.f);
+                         (float)(u0.y * u1.x - u0.x * u1.y), (float)(E[2 * k] - mu));
+    rec[plane + t] = make_float4((float)(E[2 * k + 1] - mu), 0.f, 0.f, 0.f);
+    rec[2 * plane + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// g = -df/dT = (x / T) f (1 - f) and g' = dg/de with x = e / T, in the overflow-safe form with
+// z = exp(-|x|): f (1 - f) = z / (1 + z)^2 and dg/de = f (1 - f) / T^2 (1 - |x| (1 - z) / (1 + z)).
+// FP32 (the split path's loop sums are FP32).
+__global__ void rec_T_kernel(int n, double T_value, const double *Tp, float4 *rec)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float invT = 1.f / (float)(Tp ? *Tp : T_value);   // device-resident temperature when given
+    const float e[2] = {rec[t].w, rec[n + t].x};
+    float g[2], gp[2];
+#pragma unroll
+    for (int l = 0; l < 2; l++) {
+        const float x = e[l] * invT, ax = fabsf(x);
+        const float z = expf(-ax), opz = 1.f + z;
+        const float h = z / (opz * opz);
+        g[l] = x * invT * h;
+        gp[l] = h * invT * invT * (1.f - ax * (1.f - z) / opz);
+    }
+    rec[n + t] = make_float4(e[1], g[0], g[1], gp[0]);
+    rec[2 * n + t] = make_float4(gp[1], 0.f, 0.f, 0.f);
 }
 
 template <int NDYH, int WHICH>
@@ -307,10 +320,16 @@ bool loops2_supported(const tufrg_model *m)
     return m->ns == 2 && m->precision != TUFRG_FP64 && ndyh <= 5 && (int)m->dxs.size() <= MAXD;
 }
 
+cudaError_t launch_loop_records_static(tufrg_model *m)
+{
+    rec_static_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->d_U, m->Nk, m->Lf, m->mu, m->d_rec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_loop_records(tufrg_model *m)
 {
     PhaseScope ps(m, PH_FERMI);
-    rec_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->d_U, m->Nk, m->Lf, m->mu, 0.0, m->d_scal, m->d_rec);
+    rec_T_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->Nk, 0.0, m->d_scal, m->d_rec);
     return cudaGetLastError();
 }
 
@@ -461,8 +480,9 @@ extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, c
     float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(base) + rec_bytes);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-    rec_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d_E, reinterpret_cast<const double2 *>(d_U), (int)Nk, Lf,
-                                                               mu, T, nullptr, rec);
+    rec_static_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d_E, reinterpret_cast<const double2 *>(d_U), (int)Nk,
+                                                                      Lf, mu, rec);
+    rec_T_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>((int)Nk, T, nullptr, rec);
     if (cudaGetLastError() != cudaSuccess) return TUFRG_ECUDA;
     Args2 a{};
     a.rec = rec;

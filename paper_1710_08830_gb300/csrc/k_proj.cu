@@ -14,10 +14,13 @@
 // state is read once from HBM; the split path accumulates in FP32.
 //
 // Projections: the bond arithmetic is done once on the host into int32 gather
-// tables (terms per output bond pair (R, R')).  One CTA per (R, R', q-tile,
-// channel) stages its term list in shared memory, so every warp walks the same
-// list; threads cover the orbital pairs x transfer momenta of the tile.  Each
-// term is one load from the (L2 resident) Fourier transform times a phase.
+// tables, flattened per output matrix entry: each term is the flat index of its
+// source in the Fourier transforms (sign in the high bit) and a phase-table column.
+// A thread owns one matrix entry and QT transfer momenta: it walks its term list
+// once, each source value (independent of q) is loaded once and applied with the
+// QT momenta's phases from shared memory, and the state is read and the result
+// written fully coalesced.  max |A| is reduced in the CTA and merged with one
+// atomic per CTA.  The split path reads the FP32 copy of the state.
 #include <algorithm>
 
 #include "tufrg_internal.cuh"
@@ -28,12 +31,16 @@ namespace {
 template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const double2 &v);
 template <> __device__ __forceinline__ double2 ld_as<double>(const double2 &v) { return v; }
 template <> __device__ __forceinline__ float2 ld_as<float>(const double2 &v) { return make_float2((float)v.x, (float)v.y); }
+template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const float2 &v);
+template <> __device__ __forceinline__ float2 ld_as<float>(const float2 &v) { return v; }
 
-template <typename R, int CPT>
-__global__ void dft_kernel(const double2 *X, int Nq, int M2, int ncls, int nchunk, const double2 *clsph, int u_per,
-                           typename cpx<R>::t *part)
+template <typename R, typename XT, int CPT>
+__global__ void __launch_bounds__(128) dft_kernel(const XT *__restrict__ X, int Nq, int M2, int ncls, int nchunk,
+                                                  const double2 *__restrict__ clsph, int u_per,
+                                                  typename cpx<R>::t *__restrict__ part)
 {
     using C2 = typename cpx<R>::t;
+    constexpr int UB = 8;   // loads in flight per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *ph = reinterpret_cast<C2 *>(smem_raw);   // [u_per][CPT]
     const int ch = blockIdx.z / nchunk, c0 = (blockIdx.z % nchunk) * CPT;
@@ -48,8 +55,23 @@ __global__ void dft_kernel(const double2 *X, int Nq, int M2, int ncls, int nchun
     C2 acc[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; c++) acc[c] = mk(R(0), R(0));
-    const double2 *src = X + ((size_t)ch * Nq + u0) * M2 + ij;
-    for (int u = u0; u < u1; u++, src += M2) {
+    const XT *src = X + ((size_t)ch * Nq + u0) * M2 + ij;
+    int u = u0;
+    for (; u + UB <= u1; u += UB, src += (size_t)UB * M2) {
+        C2 x[UB];
+#pragma unroll
+        for (int j = 0; j < UB; j++) x[j] = ld_as<R>(src[(size_t)j * M2]);
+#pragma unroll
+        for (int j = 0; j < UB; j++) {
+            const C2 *p = ph + (u + j - u0) * CPT;
+#pragma unroll
+            for (int c = 0; c < CPT; c++) {
+                acc[c].x = fma(p[c].x, x[j].x, fma(-p[c].y, x[j].y, acc[c].x));
+                acc[c].y = fma(p[c].x, x[j].y, fma(p[c].y, x[j].x, acc[c].y));
+            }
+        }
+    }
+    for (; u < u1; u++, src += M2) {
         const C2 x = ld_as<R>(*src);
         const C2 *p = ph + (u - u0) * CPT;
 #pragma unroll
@@ -81,85 +103,104 @@ __global__ void dft_reduce_kernel(const typename cpx<R>::t *part, int nsplit, in
     Xr[(size_t)ch * per + r] = mk(R(sx * inv_nq), R(sy * inv_nq));
 }
 
-template <typename R>
-__global__ void project_kernel(const double2 *X, const typename cpx<R>::t *Xr, const double2 *V0, const int *gofs0,
-                               const int *gofs1, const GatherTerm *gt0, const GatherTerm *gt1,
-                               const typename cpx<R>::t *ph, int nph, int Nq, int ns, int nff, int ncls, int chmask,
-                               int qt, double2 *A, float2 *A32, unsigned long long *amax)
+// |v|^2 with one explicit rounding order, shared by the projection and the arg-max search so that
+// both see the same bits
+__device__ __forceinline__ double abs2(double2 v) { return fma(v.x, v.x, v.y * v.y); }
+__device__ __forceinline__ float abs2(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+// max |A| as the double that the flow controller reads
+__device__ __forceinline__ double mag_of(double m2) { return sqrt(m2); }
+__device__ __forceinline__ double mag_of(float m2) { return (double)sqrtf(m2); }
+
+// Projected vertices A_X(q) for QT transfer momenta of one channel, one matrix entry per thread.
+// The plain path works in FP64; the split path forms A in FP32 (its only consumer is the FP32 V.L.V
+// product) and writes the FP64 copy only when asked (A != NULL).
+template <typename R, typename XT, int QT>
+__global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, const typename cpx<R>::t *__restrict__ Xr,
+                                                      const double2 *v0d0, const double2 *v0d1, const int *eofs0,
+                                                      const int *eofs1, const int2 *et0, const int2 *et1,
+                                                      const typename cpx<R>::t *ph, int nph, int Nq, int M2, int ncls,
+                                                      int chmask, double2 *A, float2 *A32, unsigned long long *amax)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GatherTerm *terms = reinterpret_cast<GatherTerm *>(smem_raw);
-    const int ns2 = ns * ns, ns4 = ns2 * ns2, M = nff * ns2;
-    const size_t M2 = (size_t)M * M;
-    const int pair = blockIdx.x, iR = pair / nff, iRp = pair % nff;
-    const int q0 = blockIdx.y * qt;
-    const int ch = blockIdx.z;
-    const bool on = (chmask >> ch) & 1;
-    const int *gofs = ch == 0 ? gofs0 : gofs1;
-    const GatherTerm *gt = ch == 0 ? gt0 : gt1;
-    const int tb = gofs[pair], nt = gofs[pair + 1] - tb;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) terms[t] = gt[tb + t];
-    __syncthreads();
-    double mag = 0.0;
-    for (int item = threadIdx.x; item < ns4 * qt; item += blockDim.x) {
-        const int q = q0 + item / ns4, combo = item % ns4;
-        if (q >= Nq) continue;
-        const int rp = combo / ns2, cp = combo % ns2;
-        const int row = iR * ns2 + rp, col = iRp * ns2 + cp;
-        int s1, s2, s3, s4;
-        if (ch == 0) { s1 = rp / ns; s2 = rp % ns; s4 = cp / ns; s3 = cp % ns; }   // P: (s1,s2),(s4,s3)
-        else         { s1 = rp / ns; s3 = rp % ns; s4 = cp / ns; s2 = cp % ns; }   // C: (s1,s3),(s4,s2)
-        const size_t o = ((size_t)ch * Nq + q) * M2 + (size_t)row * M + col;
-        double2 val = make_double2(0.0, 0.0);
-        if (on) {
-            val = X[o];
-            if (iR == 0 && iRp == 0) {
-                const double2 v0 = V0[((s1 * ns + s2) * ns + s3) * ns + s4];
-                val.x += v0.x;
-                val.y += v0.y;
-            }
-            R gx = 0, gy = 0;
-            for (int t = 0; t < nt; t++) {
-                const GatherTerm g = terms[t];
-                int sch, sr, sc;
-                R sgn;
-                switch (g.kind) {
-                case 0: sch = 1; sr = s1 * ns + s3; sc = s4 * ns + s2; sgn = R(1); break;    // P <- C
-                case 1: sch = 1; sr = s1 * ns + s4; sc = s3 * ns + s2; sgn = R(-1); break;   // P <- D
-                case 2: sch = 0; sr = s1 * ns + s2; sc = s4 * ns + s3; sgn = R(1); break;    // C <- P
-                default: sch = 1; sr = s1 * ns + s4; sc = s3 * ns + s2; sgn = R(-1); break;  // C <- D
-                }
-                if (!((chmask >> sch) & 1)) continue;
-                const C2 x = Xr[((size_t)sch * ncls + g.cls) * M2 + (size_t)(g.i1 * ns2 + sr) * M + g.i2 * ns2 + sc];
-                const C2 p = ph[(size_t)q * nph + g.ph];
-                gx += sgn * (p.x * x.x - p.y * x.y);
-                gy += sgn * (p.x * x.y + p.y * x.x);
-            }
-            val.x += (double)gx;
-            val.y += (double)gy;
-        }
-        A[o] = val;
-        if (A32) A32[o] = make_float2((float)val.x, (float)val.y);
-        mag = fmax(mag, sqrt(val.x * val.x + val.y * val.y));
+    C2 *phs = reinterpret_cast<C2 *>(smem_raw);   // [QT][nph]
+    const int ch = blockIdx.z, q0 = blockIdx.y * QT, nq = min(QT, Nq - q0);
+    for (int i = threadIdx.x; i < QT * nph; i += blockDim.x) {
+        const int qi = i / nph;
+        phs[i] = qi < nq ? ph[(size_t)(q0 + qi) * nph + (i - qi * nph)] : mk(R(0), R(0));
     }
-    // max |A|: non-negative doubles order like their bit patterns
-    for (int off = 16; off > 0; off >>= 1) mag = fmax(mag, __shfl_xor_sync(0xffffffffu, mag, off));
-    if ((threadIdx.x & 31) == 0 && mag > 0.0) atomicMax(amax, (unsigned long long)__double_as_longlong(mag));
+    __syncthreads();
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    R m2 = R(0);
+    if (e < M2) {
+        const bool on = (chmask >> ch) & 1;
+        const size_t base = ((size_t)ch * Nq + q0) * M2 + e;
+        C2 acc[QT];
+        if (on) {
+            const C2 v0 = ld_as<R>((ch == 0 ? v0d0 : v0d1)[e]);
+#pragma unroll
+            for (int qi = 0; qi < QT; qi++) {
+                acc[qi] = qi < nq ? ld_as<R>(X[base + (size_t)qi * M2]) : mk(R(0), R(0));
+                acc[qi].x += v0.x;
+                acc[qi].y += v0.y;
+            }
+            const int *eofs = ch == 0 ? eofs0 : eofs1;
+            const int2 *et = ch == 0 ? et0 : et1;
+            const int t1 = eofs[e + 1];
+            const int lim = ncls * M2;   // sources at or above lim belong to the C channel
+            for (int t = eofs[e]; t < t1; t++) {
+                const int2 g = et[t];
+                const int idx = g.x & 0x7fffffff;
+                if (!((chmask >> (idx >= lim ? 1 : 0)) & 1)) continue;
+                C2 x = Xr[idx];
+                if (g.x < 0) {
+                    x.x = -x.x;
+                    x.y = -x.y;
+                }
+                const C2 *p = phs + g.y;
+#pragma unroll
+                for (int qi = 0; qi < QT; qi++) {
+                    const C2 pq = p[qi * nph];
+                    acc[qi].x += pq.x * x.x - pq.y * x.y;
+                    acc[qi].y += pq.x * x.y + pq.y * x.x;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int qi = 0; qi < QT; qi++) acc[qi] = mk(R(0), R(0));
+        }
+#pragma unroll
+        for (int qi = 0; qi < QT; qi++) {
+            if (qi >= nq) break;
+            const size_t o = base + (size_t)qi * M2;
+            if (A) A[o] = make_double2((double)acc[qi].x, (double)acc[qi].y);
+            if (A32) A32[o] = make_float2((float)acc[qi].x, (float)acc[qi].y);
+            m2 = max(m2, abs2(acc[qi]));
+        }
+    }
+    // max |A| over the CTA, then one atomic (non-negative doubles order like their bit patterns)
+    __shared__ R wmax[8];
+    for (int off = 16; off > 0; off >>= 1) m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, off));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) m2 = max(m2, wmax[w]);
+        if (m2 > R(0)) atomicMax(amax, (unsigned long long)__double_as_longlong(mag_of(m2)));
+    }
 }
 
-// Locate the maximum: every entry equal to the reduced maximum records its flat index (atomicMin keeps the first).
-__global__ void amax_locate_kernel(const double2 *A, size_t n, const unsigned long long *amax, unsigned long long *where)
+// Locate the maximum: every entry whose magnitude equals the reduced maximum records its flat index
+// (atomicMin keeps the first).  The magnitude is formed exactly as in the projection.
+template <typename C2>
+__global__ void amax_locate_kernel(const C2 *A, size_t n, const unsigned long long *amax, unsigned long long *where)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double2 v = A[i];
-    const double mag = sqrt(v.x * v.x + v.y * v.y);
-    if ((unsigned long long)__double_as_longlong(mag) == *amax) atomicMin(where, (unsigned long long)i);
+    if ((unsigned long long)__double_as_longlong(mag_of(abs2(A[i]))) == *amax) atomicMin(where, (unsigned long long)i);
 }
 
-template <typename R, int CPT>
-cudaError_t dft_run(tufrg_model *m, const double2 *d_state, int ch_lo, int nch, typename cpx<R>::t *part,
+template <typename R, typename XT, int CPT>
+cudaError_t dft_run(tufrg_model *m, const XT *d_state, int ch_lo, int nch, typename cpx<R>::t *part,
                     typename cpx<R>::t *Xr)
 {
     const int M2 = m->M * m->M;
@@ -169,7 +210,7 @@ cudaError_t dft_run(tufrg_model *m, const double2 *d_state, int ch_lo, int nch, 
     const int nsplit = m->dft_nsplit;
     const int u_per = (m->Nq + nsplit - 1) / nsplit;
     const size_t smem = sizeof(typename cpx<R>::t) * u_per * CPT;
-    auto k = dft_kernel<R, CPT>;
+    auto k = dft_kernel<R, XT, CPT>;
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         PhaseScope ps(m, PH_DFT, 2);
@@ -190,52 +231,65 @@ cudaError_t dft_run(tufrg_model *m, const double2 *d_state, int ch_lo, int nch, 
 int dft_plan_nsplit(const tufrg_model *m)
 {
     const int xb = (m->M * m->M + 127) / 128;
-    const int cpt = m->precision == TUFRG_FP64 ? 8 : 16;
+    const int cpt = m->precision == TUFRG_FP64 ? 16 : 32;
     const int nchunk = (m->ncls + cpt - 1) / cpt;
     const long want = 4L * m->sm_count;
     long ns = (want + (long)xb * 2 * nchunk - 1) / ((long)xb * 2 * nchunk);
+    // the phases of a CTA's slice of the transfer mesh must fit in 96 KB of shared memory
+    const long esize = m->precision == TUFRG_FP64 ? 16 : 8;
+    const long cap = 96L * 1024 / (cpt * esize);
+    ns = std::max(ns, ((long)m->Nq + cap - 1) / cap);
     if (ns < 1) ns = 1;
     if (ns > m->Nq) ns = m->Nq;
     return (int)ns;
 }
 
-cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, int channel_mask)
+cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask)
 {
     const int ch_lo = (channel_mask & 1) ? 0 : 1, ch_hi = (channel_mask & 2) ? 1 : 0;
     if (ch_lo > ch_hi) return cudaSuccess;
     const int nch = ch_hi - ch_lo + 1;
     if (m->precision == TUFRG_FP64)
-        return dft_run<double, 8>(m, d_state, ch_lo, nch, reinterpret_cast<double2 *>(m->d_dftpart), m->d_Xr);
-    return dft_run<float, 16>(m, d_state, ch_lo, nch, reinterpret_cast<float2 *>(m->d_dftpart), m->d_Xr32);
+        return dft_run<double, double2, 16>(m, d_state, ch_lo, nch, reinterpret_cast<double2 *>(m->d_dftpart), m->d_Xr);
+    return dft_run<float, float2, 32>(m, d_state32, ch_lo, nch, reinterpret_cast<float2 *>(m->d_dftpart), m->d_Xr32);
 }
 
-cudaError_t launch_project(tufrg_model *m, const double2 *d_state, int channel_mask, double2 *d_A)
+constexpr int PROJ_QT = 8;   // transfer momenta per thread
+
+cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
+                           double2 *d_A)
 {
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax, 0, sizeof(unsigned long long), m->stream));
-    const int ns4 = m->ns * m->ns * m->ns * m->ns;
-    const int qt = ns4 >= 128 ? 1 : 128 / ns4;
-    dim3 grid(m->nff * m->nff, (m->Nq + qt - 1) / qt, 2);
-    const size_t smem = sizeof(GatherTerm) * (size_t)std::max(1, m->max_terms);
+    const int M2 = m->M * m->M;
+    dim3 grid((M2 + 255) / 256, (m->Nq + PROJ_QT - 1) / PROJ_QT, 2);
     PhaseScope ps(m, PH_PROJ);
     if (m->precision == TUFRG_FP64) {
-        project_kernel<double><<<grid, 128, smem, m->stream>>>(d_state, m->d_Xr, m->d_V0, m->d_gofs[0], m->d_gofs[1],
-                                                               m->d_gterms[0], m->d_gterms[1], m->d_ph, m->nph, m->Nq,
-                                                               m->ns, m->nff, m->ncls, channel_mask, qt, d_A, nullptr,
-                                                               m->d_amax);
+        const size_t smem = sizeof(double2) * PROJ_QT * m->nph;
+        auto k = project_kernel<double, double2, PROJ_QT>;
+        if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, 256, smem, m->stream>>>(d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_eofs[0], m->d_eofs[1],
+                                          m->d_eterms[0], m->d_eterms[1], m->d_ph, m->nph, m->Nq, M2, m->ncls,
+                                          channel_mask, d_A, nullptr, m->d_amax);
     } else {
-        project_kernel<float><<<grid, 128, smem, m->stream>>>(d_state, m->d_Xr32, m->d_V0, m->d_gofs[0], m->d_gofs[1],
-                                                              m->d_gterms[0], m->d_gterms[1], m->d_ph32, m->nph, m->Nq,
-                                                              m->ns, m->nff, m->ncls, channel_mask, qt, d_A, m->d_A32,
-                                                              m->d_amax);
+        const size_t smem = sizeof(float2) * PROJ_QT * m->nph;
+        auto k = project_kernel<float, float2, PROJ_QT>;
+        if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, 256, smem, m->stream>>>(d_state32, m->d_Xr32, m->d_v0d[0], m->d_v0d[1], m->d_eofs[0], m->d_eofs[1],
+                                          m->d_eterms[0], m->d_eterms[1], m->d_ph32, m->nph, m->Nq, M2, m->ncls,
+                                          channel_mask, d_A, m->d_A32, m->d_amax);   // d_A may be NULL here
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_amax_locate(tufrg_model *m, const double2 *d_A, size_t n, double)
+cudaError_t launch_amax_locate(tufrg_model *m, size_t n)
 {
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax + 1, 0xff, sizeof(unsigned long long), m->stream));
     m->launches++;
-    amax_locate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(d_A, n, m->d_amax, m->d_amax + 1);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (m->precision == TUFRG_FP64)
+        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A, n, m->d_amax, m->d_amax + 1);
+    else
+        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A32, n, m->d_amax, m->d_amax + 1);
     return cudaGetLastError();
 }
 

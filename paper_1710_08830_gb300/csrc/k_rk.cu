@@ -11,14 +11,25 @@ struct StageArgs {
     int nk;
 };
 
-// out = y + h * sum_j a_j k_j  (element-wise over doubles), h read from the device flow state
-__global__ void rk_combine_kernel(double *out, const double *y, const FlowDev *fs, StageArgs s, size_t n)
+// out = y + h * sum_j a_j k_j  (element-wise over doubles), h read from the device flow state; the
+// FP64 result goes to out and/or its FP32 rounding to out32 (either may be NULL)
+__global__ void rk_combine_kernel(double *out, float *out32, const double *y, const FlowDev *fs, StageArgs s, size_t n)
 {
     const double h = fs->h;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int j = 0; j < s.nk; j++) acc = fma(s.a[j], s.k[j][i], acc);
-        out[i] = fma(h, acc, y[i]);
+        const double v = fma(h, acc, y[i]);
+        if (out) out[i] = v;
+        if (out32) out32[i] = (float)v;
+    }
+}
+
+__global__ void to_f32_kernel(const double2 *x, float2 *y, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        y[i] = make_float2((float)v.x, (float)v.y);
     }
 }
 
@@ -126,8 +137,8 @@ int grid_for(const tufrg_model *m, size_t n)
 
 }  // namespace
 
-cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, const FlowDev *fs, const double *a,
-                              double2 *const *k, int nk, size_t n)
+cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const double2 *y, const FlowDev *fs,
+                              const double *a, double2 *const *k, int nk, size_t n)
 {
     StageArgs s{};
     s.nk = 0;
@@ -140,7 +151,16 @@ cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, co
     const size_t nd = 2 * n;
     PhaseScope ps(m, PH_RK);
     rk_combine_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
+                                                              reinterpret_cast<float *>(out32),
                                                               reinterpret_cast<const double *>(y), fs, s, nd);
+    return cudaGetLastError();
+}
+
+// timed with the Fourier transform, the first reader of the copy
+cudaError_t launch_to_f32(tufrg_model *m, const double2 *d_state, float2 *d_out, size_t n)
+{
+    PhaseScope ps(m, PH_DFT);
+    to_f32_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(d_state, d_out, n);
     return cudaGetLastError();
 }
 

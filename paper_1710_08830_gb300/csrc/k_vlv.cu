@@ -2,9 +2,15 @@
 // form of Eq. rge_Dmat (c_C = 2).  The M x M loop matrix is never stored: it is
 // expanded from the compact loops, L[(R1,a),(R2,b)] = Lc[d(R1-R2)][a][b].
 //
-// Small M (<= 64, every N_s = 2 bond set): one CTA per (q, channel) holds A, L and
-// the intermediate T = A L in shared memory and writes c * T A.  FP64 for the
-// plain path; FP32 arithmetic on the FP32 copies for the split path.
+// Small M (<= 64): one CTA per (q, channel) holds A, L and the intermediate
+// T = A L in shared memory and writes c * T A.  For two-band bond sets
+// (M = 4 N_ff) every thread owns a 4 x 4 tile of each product (16 complex FMAs
+// per four conflict-free 16-byte shared loads), and two M x M buffers serve
+// both products so that one wave of CTAs covers all transfer momenta.  FP64 for the plain path;
+// FP32 arithmetic on the FP32 copies for the split path, whose FP64 output is
+// widened exactly on the integer pipe (this GPU's FP64 pipe would bound it).
+#include <algorithm>
+
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -16,6 +22,113 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
     acc.x = fma(-a.y, b.y, acc.x);
     acc.y = fma(a.x, b.y, acc.y);
     acc.y = fma(a.y, b.x, acc.y);
+}
+
+// exact float -> double on the integer pipe; subnormal, inf and nan take the plain conversion
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    if (e == 0u && man == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // signed zero
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (man >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double2 out_c(float2 v, float sc) { return make_double2(widen(sc * v.x), widen(sc * v.y)); }
+__device__ __forceinline__ double2 out_c(double2 v, double sc) { return make_double2(sc * v.x, sc * v.y); }
+
+// two consecutive complex values from 16-byte aligned shared memory
+__device__ __forceinline__ void ld2(const float2 *p, float2 &a, float2 &b)
+{
+    const float4 u = *reinterpret_cast<const float4 *>(p);
+    a = make_float2(u.x, u.y);
+    b = make_float2(u.z, u.w);
+}
+__device__ __forceinline__ void ld2(const double2 *p, double2 &a, double2 &b)
+{
+    a = p[0];
+    b = p[1];
+}
+
+// acc[i][j] += sum_k X[k][row_i] Y[k][col_j] for the 4 x 4 tile with rows {r, r+1, r+h, r+h+1} and
+// columns {c, c+1, c+h, c+h+1} (h = M/2); X is stored transposed (k-major), so both operands are read
+// as pairs of 16-byte chunks that consecutive lanes take from consecutive addresses.
+template <typename C2>
+__device__ __forceinline__ void tile44(const C2 *Xt, const C2 *Y, int M, int r, int c, C2 acc[4][4])
+{
+    const int h = M / 2;
+    for (int k = 0; k < M; k++) {
+        C2 a[4], b[4];
+        ld2(Xt + k * M + r, a[0], a[1]);
+        ld2(Xt + k * M + h + r, a[2], a[3]);
+        ld2(Y + k * M + c, b[0], b[1]);
+        ld2(Y + k * M + h + c, b[2], b[3]);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) cfma(acc[i][j], a[i], b[j]);
+    }
+}
+
+// Two-band bond sets (N_s^2 = 4, M = 4 N_ff): one CTA per (q, channel), one 4 x 4 output tile per
+// thread (rows {2i, 2i+1, M/2 + 2i, M/2 + 2i + 1}, columns likewise).  Shared memory holds two
+// M x M buffers: A transposed and L for T = A L, then A (reloaded, row-major) and T transposed for
+// c T A, so one wave of CTAs covers all transfer momenta.
+template <typename R>
+__global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Lc,
+                                                        const int *dij, int Nq, int M, int nff, int nd, int chmask,
+                                                        const double *scal, double2 *out)
+{
+    using C2 = typename cpx<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *s0 = reinterpret_cast<C2 *>(smem_raw);   // A^T, then A
+    C2 *s1 = s0 + M * M;                         // L, then T^T
+    const int q = blockIdx.x, ch = blockIdx.y;
+    const int M2 = M * M, h = M / 2, nt = h / 2;   // nt x nt threads own tiles
+    double2 *o = out + ((size_t)ch * Nq + q) * M2;
+    if (!((chmask >> ch) & 1)) {
+        for (int i = threadIdx.x; i < M2; i += blockDim.x) o[i] = make_double2(0.0, 0.0);
+        return;
+    }
+    const C2 *a = A + ((size_t)ch * Nq + q) * M2;
+    const C2 *lc = Lc + ((size_t)ch * Nq + q) * nd * 16;
+    // A^T and the expanded loop matrix L[(R1,a),(R2,b)] = Lc[d(R1 - R2)][a][b] (coalesced reads)
+    for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+        const int r = i / M, c = i - r * M;
+        s0[c * M + r] = a[i];
+        s1[i] = lc[(dij[(r >> 2) * nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3)];
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    const bool active = t < nt * nt;
+    const int r = 2 * (t / nt), c = 2 * (t % nt);
+    C2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = mk(R(0), R(0));
+    if (active) tile44(s0, s1, M, r, c, acc);   // T = A L
+    __syncthreads();
+    const int rows[4] = {r, r + 1, h + r, h + r + 1}, cols[4] = {c, c + 1, h + c, h + c + 1};
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                s1[cols[j] * M + rows[i]] = acc[i][j];   // T^T
+                acc[i][j] = mk(R(0), R(0));
+            }
+    }
+    for (int i = threadIdx.x; i < M2; i += blockDim.x) s0[i] = a[i];   // A, row-major (L2-resident reread)
+    __syncthreads();
+    if (active) {
+        const R sc = R((ch == 0 ? 1.0 : 2.0) * scal[1]);   // c_P = 1, c_C = 2, times the output scale
+        tile44(s1, s0, M, r, c, acc);                      // c T A
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) o[rows[i] * M + cols[j]] = out_c(acc[i][j], sc);
+    }
 }
 
 template <typename R>
@@ -68,8 +181,25 @@ cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, dou
     if (M > 64) return launch_vlv_large(m, d_A, channel_mask, d_out);
     const int ns2 = m->ns * m->ns;
     dim3 grid(m->Nq, 2);
-    const int threads = 256;
     PhaseScope ps(m, PH_VLV);
+    if (ns2 == 4) {
+        const int threads = std::max(32, ((M / 4) * (M / 4) + 31) / 32 * 32);   // <= 256 for M <= 64
+        if (m->precision == TUFRG_FP64) {
+            const size_t smem = 2 * sizeof(double2) * M * M;
+            auto k = vlv_tiled_kernel<double>;
+            if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k<<<grid, threads, smem, m->stream>>>(d_A, m->d_Lc, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask,
+                                                  m->d_scal, d_out);
+        } else {
+            const size_t smem = 2 * sizeof(float2) * M * M;
+            auto k = vlv_tiled_kernel<float>;
+            if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k<<<grid, threads, smem, m->stream>>>(m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask,
+                                                  m->d_scal, d_out);
+        }
+        return cudaGetLastError();
+    }
+    const int threads = 256;
     if (m->precision == TUFRG_FP64) {
         const size_t smem = 3 * sizeof(double2) * M * M;
         auto k = vlv_small_kernel<double>;

@@ -97,6 +97,11 @@ struct tufrg_model {
     int *d_dij = nullptr;           // [nff][nff]
     int *d_gofs[2] = {nullptr, nullptr};
     tufrg::GatherTerm *d_gterms[2] = {nullptr, nullptr};
+    int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
+    int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
+                                               //  high bit = minus sign; phase-table column)
+    double2 *d_v0d[2] = {nullptr, nullptr};    // [M*M] bare vertex V0 at the onsite bond pair, 0 elsewhere
+    float2 *d_X32 = nullptr;        // [2][Nq][M][M] FP32 copy of the state being evaluated (split path)
     double2 *d_ph = nullptr;        // [Nq][nph] phase table e^{i q.R}
     double2 *d_clsph = nullptr;     // [Nq][ncls] e^{i q.R''} for the Fourier transform
     double2 *d_V0 = nullptr;        // [ns^4]
@@ -163,11 +168,14 @@ cudaError_t launch_density(tufrg_model *m, double mu, double T, double *h_out);
 cudaError_t launch_fermi(tufrg_model *m);
 cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
 cudaError_t launch_loops(tufrg_model *m, int channel_mask);
-cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, int channel_mask);
-cudaError_t launch_project(tufrg_model *m, const double2 *d_state, int channel_mask, double2 *d_A);
+// The split path reads the FP32 copy of the state (d_state32), the plain path the FP64 state.
+cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask);
+cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
+                           double2 *d_A);
+cudaError_t launch_to_f32(tufrg_model *m, const double2 *d_state, float2 *d_out, size_t n);
 cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
-cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, const double2 *y, const FlowDev *fs, const double *a,
-                              double2 *const *k, int nk, size_t n);
+cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const double2 *y, const FlowDev *fs,
+                              const double *a, double2 *const *k, int nk, size_t n);
 cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, const FlowDev *fs, const double *e,
                             double2 *const *k, int nk, size_t n);
 cudaError_t launch_stage_scalars(tufrg_model *m, const FlowDev *fs, double cj);
@@ -175,7 +183,7 @@ cudaError_t launch_flow_init(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_decide(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0,
                                const double2 *k6, size_t n);
-cudaError_t launch_amax_locate(tufrg_model *m, const double2 *d_A, size_t n, double amax);
+cudaError_t launch_amax_locate(tufrg_model *m, size_t n);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
 int dft_plan_nsplit(const tufrg_model *m);
 bool loops2_supported(const tufrg_model *m);
@@ -185,7 +193,8 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
 cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
 bool tc_supported(const tufrg_model *m);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out);
-cudaError_t launch_loop_records(tufrg_model *m);
+cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
+cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu
 cudaError_t launch_loops2(tufrg_model *m, int ch);
 cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_list, float2 *part, const int *skip);
 cudaError_t launch_surrogate(tufrg_model *m, int channel_mask);

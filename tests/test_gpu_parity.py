@@ -151,6 +151,20 @@ def test_projections(case, mask):
     assert amax == pytest.approx(amax_ref, rel=1e-14)
 
 
+@pytest.mark.parametrize("case", ["rashba_ff9_Lf25", "rashba_ff13_Lf30"])
+def test_projections_split(case):
+    """Split path: the projected vertices are formed in FP32 (max relative error per entry ~ 1e-7)."""
+    api = _api()
+    spec = CASES[case]()
+    m = api.Model(spec, api.SPLIT32)
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=5, scale=0.4)
+    A, amax = m.project(st, 3)
+    ref, amax_ref = o.project(st, 3)
+    assert rel(A.cpu().numpy(), ref) < 1e-6
+    assert amax == pytest.approx(amax_ref, rel=1e-6)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("T", [5.0, 0.3, 0.05])
 def test_rhs_fp64(case, T):
