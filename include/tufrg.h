@@ -89,7 +89,16 @@ typedef struct {
     int nc;                /* fine points per coarse cell per direction (>= 1) */
     int precision;         /* TUFRG_FP64 or TUFRG_SPLIT32 (see above) */
     int products;          /* TUFRG_PRODUCTS_AUTO / _TC / _SIMT (split path only) */
+    int symmetry;          /* TUFRG_SYMMETRY_AUTO or TUFRG_SYMMETRY_OFF (see below) */
 } tufrg_model_desc;
+
+/* Time reversal in the loop k-sums (split two-band path).  When every hopping matrix satisfies
+ * t_R = W t_R^* W^T with W = i sigma_y (H(-k) = W H(k)^* W^dagger), the band projectors obey
+ * P_l(-k) = W P_l(k)^* W^dagger and both loops satisfy
+ *   Lc(-q)[d][a][b] = (-1)^(popcount(a) + popcount(b)) conj(Lc(q)[d][3 - a][3 - b]),
+ * so with TUFRG_SYMMETRY_AUTO the k-sum runs for one momentum of each pair {q, -q} (and the
+ * self-conjugate ones) and the partner is written from it.  TUFRG_SYMMETRY_OFF sums every q. */
+enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1 };
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
 typedef struct {
@@ -132,6 +141,10 @@ tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int
 /* Products backend in use on the split path (TUFRG_PRODUCTS_TC or _SIMT; _SIMT for FP64 models)
  * and, when AUTO chose it, the two measured times in milliseconds (else -1). */
 tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt);
+
+/* Number of transfer momenta whose loop k-sums are evaluated directly (Nq unless time reversal
+ * halves them, see TUFRG_SYMMETRY_AUTO). */
+tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
 
 /* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */
 tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out);

@@ -19,6 +19,7 @@ STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA",
 
 FP64, SPLIT32 = 0, 1
 PRODUCTS_AUTO, PRODUCTS_TC, PRODUCTS_SIMT = 0, 1, 2
+SYMMETRY_AUTO, SYMMETRY_OFF = 0, 1
 CH_P, CH_C = 1, 2
 
 
@@ -26,7 +27,7 @@ class ModelDesc(C.Structure):
     _fields_ = [("n_s", C.c_int), ("n_hop", C.c_int), ("hop_R", C.c_void_p), ("hop_t", C.c_void_p),
                 ("mu", C.c_double), ("filling", C.c_double), ("T_mu", C.c_double), ("V0", C.c_void_p),
                 ("n_ff", C.c_int), ("ff_R", C.c_void_p), ("Lq", C.c_int), ("nc", C.c_int),
-                ("precision", C.c_int), ("products", C.c_int)]
+                ("precision", C.c_int), ("products", C.c_int), ("symmetry", C.c_int)]
 
 
 class FlowOpts(C.Structure):
@@ -70,6 +71,8 @@ def lib():
             L.tufrg_deltas.argtypes = [vp, vp]
             L.tufrg_model_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_model_info.restype = C.c_int
+            L.tufrg_loop_momenta.argtypes = [vp, ip]
+            L.tufrg_loop_momenta.restype = C.c_int
             L.tufrg_gather_table.argtypes = [vp, i, vp, i, ip]
             L.tufrg_bands.argtypes = [vp, vp, vp]
             L.tufrg_loops.argtypes = [vp, d, i, vp]
@@ -113,7 +116,7 @@ def lib():
 # names every header in include/ declares; the CPU test checks the exports against the headers
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
-           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info",
+           "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info", "tufrg_loop_momenta",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")

@@ -13,12 +13,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, FlowOpts, FlowResult,
-                   ModelDesc, TufrgError)
+from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRY_AUTO, SYMMETRY_OFF,
+                   FlowOpts, FlowResult, ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
-__all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "CH_P", "CH_C",
-           "TufrgError"]
+__all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "SYMMETRY_AUTO",
+           "SYMMETRY_OFF", "CH_P", "CH_C", "TufrgError"]
 
 
 def _ptr(t) -> int:
@@ -29,7 +29,7 @@ class Model:
     """A TU-fRG model on the current CUDA device (see include/tufrg.h for layouts)."""
 
     def __init__(self, spec: ModelSpec, precision: int = FP64, stream: Optional[torch.cuda.Stream] = None,
-                 mu: Optional[float] = None, products: int = PRODUCTS_AUTO):
+                 mu: Optional[float] = None, products: int = PRODUCTS_AUTO, symmetry: int = SYMMETRY_AUTO):
         if not torch.cuda.is_available():
             raise RuntimeError("libtufrg needs a CUDA device")
         self.spec = spec
@@ -45,7 +45,7 @@ class Model:
         d = ModelDesc(spec.n_s, self._hopR.shape[0], self._hopR.ctypes.data, self._hopt.ctypes.data,
                       float(spec.mu if mu is None else mu), float(spec.filling if use_fill else 0.0),
                       float(spec.T_mu), self._V0.ctypes.data, self._ffR.shape[0], self._ffR.ctypes.data,
-                      spec.Lq, spec.nc, int(precision), int(products))
+                      spec.Lq, spec.nc, int(precision), int(products), int(symmetry))
         h = C.c_void_p()
         st = self._L.tufrg_init_model(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h))
         self._h = h
@@ -65,6 +65,9 @@ class Model:
         self._check(self._L.tufrg_model_info(self._h, C.byref(pr), C.byref(t_tc), C.byref(t_simt)))
         self.products = {PRODUCTS_TC: "tc", PRODUCTS_SIMT: "simt"}.get(pr.value, "?")
         self.products_tuning_ms = {"tc": t_tc.value, "simt": t_simt.value}
+        nl = C.c_int()
+        self._check(self._L.tufrg_loop_momenta(self._h, C.byref(nl)))
+        self.n_loop_q = nl.value   # transfer momenta whose loop k-sums run directly
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, st: int):

@@ -248,7 +248,8 @@ void release(tufrg_model *m)
                     m->d_V0, m->d_Lc, m->d_Lc32, m->d_part, m->d_Xr, m->d_A, m->d_A32, m->d_T, m->d_amax,
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
                     m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
-                    m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32};
+                    m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
+                    m->d_trs_list};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -476,6 +477,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if ((long)d.Lq * d.nc > 4096) return fail(m, TUFRG_EINVAL, "fine mesh too large");
     if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
     if (d.products < TUFRG_PRODUCTS_AUTO || d.products > TUFRG_PRODUCTS_SIMT) return fail(m, TUFRG_EINVAL, "unknown products backend");
+    if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF) return fail(m, TUFRG_EINVAL, "unknown symmetry option");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
@@ -510,6 +512,38 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
 
     build_loop_tables(m);
     build_gather_tables(m);
+    // time reversal (TUFRG_SYMMETRY_AUTO): t_R = W t_R^* W^T with W = i sigma_y for every hopping
+    m->n_loop_q = m->Nq;
+    if (d.symmetry == TUFRG_SYMMETRY_AUTO && ns == 2 && loops2_supported(m)) {
+        bool ok = true;
+        const int W[2][2] = {{0, 1}, {-1, 0}};
+        for (int h = 0; h < m->nhop && ok; h++) {
+            const double *t = &m->hopt[2 * (size_t)h * 4];
+            double tmax = 0.0;
+            for (int i = 0; i < 4; i++) tmax = std::max(tmax, std::hypot(t[2 * i], t[2 * i + 1]));
+            for (int i = 0; i < 2; i++)
+                for (int j = 0; j < 2; j++) {
+                    double re = 0.0, im = 0.0;   // (W t^* W^T)_{ij}
+                    for (int a = 0; a < 2; a++)
+                        for (int b = 0; b < 2; b++) {
+                            re += W[i][a] * W[j][b] * t[2 * (a * 2 + b)];
+                            im -= W[i][a] * W[j][b] * t[2 * (a * 2 + b) + 1];
+                        }
+                    if (std::hypot(re - t[2 * (i * 2 + j)], im - t[2 * (i * 2 + j) + 1]) > 1e-12 * std::max(1.0, tmax)) ok = false;
+                }
+        }
+        if (ok) {
+            std::vector<int> half;
+            for (int q = 0; q < m->Nq; q++) {
+                const int qx = q / m->Lq, qy = q % m->Lq;
+                const int mq = ((m->Lq - qx) % m->Lq) * m->Lq + (m->Lq - qy) % m->Lq;
+                if (q <= mq) half.push_back(q);
+            }
+            m->trs = true;
+            m->n_loop_q = (int)half.size();
+            CK(upload(&m->d_trs_list, half, m->stream), "upload momentum list");
+        }
+    }
     m->plan = plan_loops(m);
 
     // ---- device memory
@@ -655,6 +689,13 @@ tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc
     if (products) *products = m->products;
     if (ms_tc) *ms_tc = m->tune_ms[0];
     if (ms_simt) *ms_simt = m->tune_ms[1];
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct)
+{
+    if (!m || !n_direct) return TUFRG_EINVAL;
+    *n_direct = m->n_loop_q;
     return TUFRG_OK;
 }
 

@@ -236,22 +236,15 @@ __global__ void __launch_bounds__(32 * WARPS) loops_ns2_kernel(LoopArgs<R> a)
     if (NABG > 2 && g == 3) loop_body<R, NDYH, NAB, (NABG > 2 ? 3 : 0), WHICH>(a, ptab, red);
 }
 
-// Sum the partials in a fixed order, scale by 1/Nk and write both Hermitian halves.  The sum runs in
-// the partials' own precision (FP32 on the split path: this GPU's FP64 rate would make the
-// reduction, not the memory traffic, its bound), with four loads in flight per thread.
+// Sum the partials of list position s in a fixed order and scale by 1/Nk; the half-plane partials
+// give both Hermitian halves.  The sum runs in the partials' own precision (FP32 on the split path:
+// this GPU's FP64 rate would make the reduction, not the memory traffic, its bound), with four loads
+// in flight per thread.
 template <typename R>
-__global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                    const int *dslot, const int *deltas, int nd, int Nq, double inv_nk,
-                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
+__device__ __forceinline__ double2 reduce_one(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
+                                              const int *dslot, const int *deltas, int s, int d, int ab, double inv_nk)
 {
     using C2 = typename cpx<R>::t;
-    if (skip && *skip) return;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t total = (size_t)Nq * nd * NS4;
-    if (idx >= total) return;
-    const int ab = idx % NS4;
-    const int d = (idx / NS4) % nd;
-    const int s = idx / ((size_t)NS4 * nd);
     const int dx = deltas[2 * d], dy = deltas[2 * d + 1];
     const bool half = dy > 0 || (dy == 0 && dx >= 0);
     const int ia = ab / NS2, ib = ab % NS2;
@@ -276,9 +269,54 @@ __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part,
         re += v.x;
         im += v.y;
     }
-    const double sre = (double)re * inv_nk, sim = (half ? 1.0 : -1.0) * (double)im * inv_nk;
-    if (out64) out64[idx] = make_double2(sre, sim);
-    if (out32) out32[idx] = mk(R(sre), R(sim));
+    return make_double2((double)re * inv_nk, (half ? 1.0 : -1.0) * (double)im * inv_nk);
+}
+
+template <typename R>
+__global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
+                                    const int *dslot, const int *deltas, int nd, int Nq, double inv_nk,
+                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
+{
+    if (skip && *skip) return;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)Nq * nd * NS4;
+    if (idx >= total) return;
+    const int ab = idx % NS4;
+    const int d = (idx / NS4) % nd;
+    const int s = idx / ((size_t)NS4 * nd);
+    const double2 v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, s, d, ab, inv_nk);
+    if (out64) out64[idx] = v;
+    if (out32) out32[idx] = mk(R(v.x), R(v.y));
+}
+
+// Time-reversal variant (two bands): list position i holds q = list[i]; the loops at -q follow as
+// Lc(-q)[d][3-a][3-b] = (-1)^(popcount(a) + popcount(b)) conj(Lc(q)[d][a][b]).
+template <typename R>
+__global__ void loops_reduce_trs_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
+                                        const int *dslot, const int *deltas, int nd, int n_list, const int *list, int Lq,
+                                        double inv_nk, double2 *out64, typename cpx<R>::t *out32, const int *skip)
+{
+    if (skip && *skip) return;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)n_list * nd * NS4;
+    if (idx >= total) return;
+    const int ab = idx % NS4;
+    const int d = (idx / NS4) % nd;
+    const int i = idx / ((size_t)NS4 * nd);
+    const double2 v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, i, d, ab, inv_nk);
+    const int q = list[i], qx = q / Lq, qy = q % Lq;
+    const int mq = ((Lq - qx) % Lq) * Lq + (Lq - qy) % Lq;
+    const size_t o = ((size_t)q * nd + d) * NS4 + ab;
+    if (out64) out64[o] = v;
+    if (out32) out32[o] = mk(R(v.x), R(v.y));
+    if (mq != q) {
+        const int a = ab / NS2, b = ab % NS2;
+        const double sg = ((__popc(a) + __popc(b)) & 1) ? -1.0 : 1.0;
+        const double2 w = make_double2(sg * v.x, -sg * v.y);
+        const size_t om = ((size_t)mq * nd + d) * NS4 + (NS2 - 1 - a) * NS2 + (NS2 - 1 - b);
+        if (out64) out64[om] = w;
+        if (out32) out32[om] = mk(R(w.x), R(w.y));
+    }
 }
 
 template <typename R, int NDYH, int NAB, int WHICH>
@@ -309,7 +347,7 @@ LoopPlan plan_loops(const tufrg_model *m)
     for (int c = 1; c <= 16; c++) {
         const int len = (m->Lf + c - 1) / c;
         if (len < 8) break;
-        const double ctas = (double)m->Nq * ctas_x * c * (m->precision == TUFRG_FP64 ? 2 : 1);
+        const double ctas = (double)m->n_loop_q * ctas_x * c * (m->precision == TUFRG_FP64 ? 2 : 1);
         const double waves = std::ceil(ctas / slots);
         const double cost = waves * (len + 8.0);
         if (cost < best * 0.999) { best = cost; best_c = c; }
@@ -347,12 +385,18 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
         const double inv_nk = 1.0 / (double)m->Nk;
         if (loops2_supported(m)) {
             TUFRG_CUDA_TRY(launch_loops2(m, ch));
-            const size_t total = (size_t)m->Nq * m->nd * NS4;
+            const size_t total = (size_t)m->n_loop_q * m->nd * NS4;
+            const size_t off = (size_t)ch * m->Nq * m->nd * NS4;
             PhaseScope ps(m, PH_LOOPRED);
-            loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
-                reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq,
-                inv_nk, m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4,
-                m->sur ? m->d_sur_flag : nullptr);
+            if (m->trs)
+                loops_reduce_trs_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
+                    m->n_loop_q, m->d_trs_list, m->Lq, inv_nk, m->d_Lc + off, m->d_Lc32 + off,
+                    m->sur ? m->d_sur_flag : nullptr);
+            else
+                loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
+                    m->Nq, inv_nk, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};

@@ -376,7 +376,9 @@ cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_li
 
 cudaError_t launch_loops2(tufrg_model *m, int ch)
 {
-    return launch_loops2_ex(m, ch, nullptr, 0, reinterpret_cast<float2 *>(m->d_part), m->sur ? m->d_sur_flag : nullptr);
+    // with time reversal only one momentum of each pair {q, -q} is summed (partial slots = list positions)
+    return launch_loops2_ex(m, ch, m->trs ? m->d_trs_list : nullptr, m->trs ? m->n_loop_q : 0,
+                            reinterpret_cast<float2 *>(m->d_part), m->sur ? m->d_sur_flag : nullptr);
 }
 
 }  // namespace tufrg

@@ -97,6 +97,9 @@ struct tufrg_model {
     int *d_dij = nullptr;           // [nff][nff]
     int *d_gofs[2] = {nullptr, nullptr};
     tufrg::GatherTerm *d_gterms[2] = {nullptr, nullptr};
+    bool trs = false;               // loops from time reversal for -q (see TUFRG_SYMMETRY_AUTO)
+    int n_loop_q = 0;               // transfer momenta summed directly (Nq, or the half list)
+    int *d_trs_list = nullptr;      // [n_loop_q] the directly summed momenta (one of each pair q, -q)
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)

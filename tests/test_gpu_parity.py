@@ -98,6 +98,44 @@ def test_loops_split(case, T):
         assert rel(L[ch], ref) < 2e-5, (ch, rel(L[ch], ref))
 
 
+def _zeeman(spec, B=0.15):
+    """The same model with an onsite Zeeman field B sigma_z (breaks time reversal)."""
+    hop_R = np.array(spec.hop_R, np.int32)
+    hop_t = np.array(spec.hop_t, np.complex128)
+    z = B * np.diag([1.0, -1.0]).astype(np.complex128)
+    onsite = [i for i, r in enumerate(hop_R) if r[0] == 0 and r[1] == 0]
+    if onsite:
+        hop_t[onsite[0]] += z
+    else:
+        hop_R = np.vstack([hop_R, [[0, 0]]]).astype(np.int32)
+        hop_t = np.concatenate([hop_t, z[None]])
+    return spec.with_(hop_R=hop_R, hop_t=hop_t)
+
+
+@pytest.mark.parametrize("case", ["rashba_ff9_Lf25", "hubbard_ff5_Lf24", "rashba_ff13_Lf30"])
+def test_loops_time_reversal(case):
+    """Time-reversal-symmetric models sum one momentum of each pair (q, -q) and derive the other;
+    the result equals the full k-sum (to FP32 rounding) and the oracle.  A Zeeman field breaks the
+    symmetry: every momentum is summed directly and the loops still match the oracle."""
+    api = _api()
+    spec = CASES[case]()
+    Lq = spec.Lq
+    n_self = 4 if Lq % 2 == 0 else 1
+    m = api.Model(spec, api.SPLIT32)
+    full = api.Model(spec, api.SPLIT32, symmetry=api.SYMMETRY_OFF)
+    assert m.n_loop_q == (Lq * Lq + n_self) // 2 and full.n_loop_q == Lq * Lq
+    for T in (2.0, 0.07):
+        L, Lfull = m.loops(T).cpu().numpy(), full.loops(T).cpu().numpy()
+        assert rel(L, Lfull) < 2e-6
+    zs = _zeeman(spec)
+    mz = api.Model(zs, api.SPLIT32)
+    assert mz.n_loop_q == Lq * Lq
+    o = oracle.Oracle(zs)
+    L = mz.loops(0.07).cpu().numpy()
+    for ch in (0, 1):
+        assert rel(L[ch], o.loops(0.07, ch)) < 2e-5
+
+
 def _paper_gather_terms(spec):
     """Independent enumeration of the gather terms from the printed projection formulas."""
     L = spec.Lq
