@@ -92,12 +92,14 @@ typedef struct {
     int symmetry;          /* TUFRG_SYMMETRY_AUTO or TUFRG_SYMMETRY_OFF (see below) */
 } tufrg_model_desc;
 
-/* Time reversal in the loop k-sums (split two-band path).  When every hopping matrix satisfies
- * t_R = W t_R^* W^T with W = i sigma_y (H(-k) = W H(k)^* W^dagger), the band projectors obey
- * P_l(-k) = W P_l(k)^* W^dagger and both loops satisfy
- *   Lc(-q)[d][a][b] = (-1)^(popcount(a) + popcount(b)) conj(Lc(q)[d][3 - a][3 - b]),
- * so with TUFRG_SYMMETRY_AUTO the k-sum runs for one momentum of each pair {q, -q} (and the
- * self-conjugate ones) and the partner is written from it.  TUFRG_SYMMETRY_OFF sums every q. */
+/* Symmetries of the loop k-sums (split two-band path).  A point operation G of the square lattice
+ * (rotations by multiples of 90 degrees, the four mirrors) with a spin unitary U such that every
+ * hopping satisfies t_{G R} = U t_R U^dagger maps the band projectors as P_l(G k) = U P_l(k) U^dagger,
+ * so both loops obey Lc(G q)[G Delta] = V Lc(q)[Delta] V^dagger (V = U (x) U on the P orbital pair,
+ * U (x) U^* on the C pair).  Time reversal, t_R = W t_R^* W^T with W = i sigma_y, gives
+ * Lc(-q)[Delta] = V conj(Lc(q)[Delta]) V^dagger with V built from W.  With TUFRG_SYMMETRY_AUTO the
+ * operations that hold (U searched among the monomial unitaries) are found at init, the k-sum runs
+ * for one momentum per orbit and the others are written from it.  TUFRG_SYMMETRY_OFF sums every q. */
 enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1 };
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
@@ -142,8 +144,8 @@ tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int
  * and, when AUTO chose it, the two measured times in milliseconds (else -1). */
 tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt);
 
-/* Number of transfer momenta whose loop k-sums are evaluated directly (Nq unless time reversal
- * halves them, see TUFRG_SYMMETRY_AUTO). */
+/* Number of transfer momenta whose loop k-sums are evaluated directly (Nq unless loop symmetries
+ * reduce them, see TUFRG_SYMMETRY_AUTO). */
 tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
 
 /* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */

@@ -2,6 +2,8 @@
 // Every entry point returns a tufrg_status and never throws across the boundary.
 #include <algorithm>
 #include <climits>
+#include <array>
+#include <complex>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -227,6 +229,163 @@ void build_entry_tables(const tufrg_model *m, std::vector<int> ofs[2], std::vect
     }
 }
 
+// ---- loop symmetries (two bands)
+// A unitary symmetry (G, U) of the hoppings, t_{G R} = U t_R U^dagger, maps the band projectors as
+// P_l(G k) = U P_l(k) U^dagger and the loops as Lc(G q)[G Delta] = V Lc(q)[Delta] V^dagger with
+// V = U (x) U on the P pair index (t2, t1) and V = U (x) U^* on the C pair index (t1, t2).  Time
+// reversal, t_R = W t_R^* W^T with W = i sigma_y, gives Lc(-q)[Delta] = V conj(Lc(q)[Delta]) V^dagger
+// with V = W (x) W (P) and W (x) W^* (C); composed with (G, U) it maps q -> -G q, Delta -> G Delta.
+// Candidates: the eight point operations of the square lattice, each with the monomial unitaries
+// diag(1, i^n) and antidiag(1, i^n) (global phases drop out of V . V^dagger).
+struct LoopSymmetry {
+    std::vector<int> list, orb_ofs, dfwd;
+    std::vector<int2> orb;
+    std::vector<tufrg::SymElem> elem;
+};
+
+void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
+{
+    using cd = std::complex<double>;
+    typedef std::array<std::array<cd, 2>, 2> M2c;
+    typedef std::array<std::array<cd, 4>, 4> M4c;
+    const int Gs[8][4] = {{1, 0, 0, 1}, {0, -1, 1, 0}, {-1, 0, 0, -1}, {0, 1, -1, 0},
+                          {-1, 0, 0, 1}, {1, 0, 0, -1}, {0, 1, 1, 0}, {0, -1, -1, 0}};
+    const int L = m->Lq, nd = m->nd;
+    auto hop = [&](int h, int i, int j) { return cd(m->hopt[2 * ((size_t)h * 4 + i * 2 + j)], m->hopt[2 * ((size_t)h * 4 + i * 2 + j) + 1]); };
+    auto find_hop = [&](int x, int y) {
+        for (int h = 0; h < m->nhop; h++)
+            if (m->hopR[2 * h] == x && m->hopR[2 * h + 1] == y) return h;
+        return -1;
+    };
+    auto find_delta = [&](int x, int y) {
+        for (int k = 0; k < nd; k++)
+            if (m->deltas[2 * k] == x && m->deltas[2 * k + 1] == y) return k;
+        return -1;
+    };
+    double tmax = 0.0;
+    for (int h = 0; h < m->nhop; h++)
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 2; j++) tmax = std::max(tmax, std::abs(hop(h, i, j)));
+    const double tol = 1e-12 * std::max(1.0, tmax);
+    // V on the orbital pair index of each channel
+    auto pairV = [&](const M2c &U, int ch) {
+        M4c V{};
+        for (int t1 = 0; t1 < 2; t1++)
+            for (int t2 = 0; t2 < 2; t2++)
+                for (int c1 = 0; c1 < 2; c1++)
+                    for (int c2 = 0; c2 < 2; c2++) {
+                        if (ch == 0) V[t2 * 2 + t1][c2 * 2 + c1] = U[t2][c2] * U[t1][c1];
+                        else V[t1 * 2 + t2][c1 * 2 + c2] = U[t1][c1] * std::conj(U[t2][c2]);
+                    }
+        return V;
+    };
+    struct Op { int Gq[4], Gd[4]; M4c V[2]; int conj; };
+    std::vector<Op> ops;
+    // unitary operations
+    for (const int *G : Gs) {
+        bool deltas_ok = true;
+        for (int k = 0; k < nd && deltas_ok; k++)
+            deltas_ok = find_delta(G[0] * m->deltas[2 * k] + G[1] * m->deltas[2 * k + 1],
+                                   G[2] * m->deltas[2 * k] + G[3] * m->deltas[2 * k + 1]) >= 0;
+        if (!deltas_ok) continue;
+        for (int c = 0; c < 8; c++) {
+            const cd p = std::pow(cd(0.0, 1.0), c / 2);
+            M2c U{};
+            if (c % 2 == 0) { U[0][0] = 1.0; U[1][1] = p; } else { U[0][1] = 1.0; U[1][0] = p; }
+            bool ok = true;
+            for (int h = 0; h < m->nhop && ok; h++) {
+                const int g = find_hop(G[0] * m->hopR[2 * h] + G[1] * m->hopR[2 * h + 1],
+                                       G[2] * m->hopR[2 * h] + G[3] * m->hopR[2 * h + 1]);
+                if (g < 0) { ok = false; break; }
+                for (int i = 0; i < 2 && ok; i++)
+                    for (int j = 0; j < 2 && ok; j++) {
+                        cd v = 0.0;   // (U t U^dagger)_{ij}
+                        for (int a = 0; a < 2; a++)
+                            for (int b = 0; b < 2; b++) v += U[i][a] * hop(h, a, b) * std::conj(U[j][b]);
+                        ok = std::abs(v - hop(g, i, j)) <= tol;
+                    }
+            }
+            if (!ok) continue;
+            Op o{};
+            std::copy(G, G + 4, o.Gq);
+            std::copy(G, G + 4, o.Gd);
+            o.V[0] = pairV(U, 0);
+            o.V[1] = pairV(U, 1);
+            o.conj = 0;
+            ops.push_back(o);
+            break;
+        }
+    }
+    // time reversal and its compositions with the unitary operations
+    bool trs = true;
+    {
+        const int W[2][2] = {{0, 1}, {-1, 0}};
+        for (int h = 0; h < m->nhop && trs; h++)
+            for (int i = 0; i < 2 && trs; i++)
+                for (int j = 0; j < 2 && trs; j++) {
+                    cd v = 0.0;   // (W t^* W^T)_{ij}
+                    for (int a = 0; a < 2; a++)
+                        for (int b = 0; b < 2; b++) v += (double)(W[i][a] * W[j][b]) * std::conj(hop(h, a, b));
+                    trs = std::abs(v - hop(h, i, j)) <= tol;
+                }
+    }
+    if (trs) {
+        M2c Wm{};
+        Wm[0][1] = 1.0;
+        Wm[1][0] = -1.0;
+        const M4c VT[2] = {pairV(Wm, 0), pairV(Wm, 1)};
+        const size_t nu = ops.size();
+        for (size_t i = 0; i < nu; i++) {
+            Op o{};
+            for (int k = 0; k < 4; k++) { o.Gq[k] = -ops[i].Gq[k]; o.Gd[k] = ops[i].Gd[k]; }
+            for (int ch = 0; ch < 2; ch++)   // V_T conj(V_g)
+                for (int a = 0; a < 4; a++)
+                    for (int b = 0; b < 4; b++) {
+                        cd v = 0.0;
+                        for (int c = 0; c < 4; c++) v += VT[ch][a][c] * std::conj(ops[i].V[ch][c][b]);
+                        o.V[ch][a][b] = v;
+                    }
+            o.conj = 1;
+            ops.push_back(o);
+        }
+    }
+    // group elements as permutation + phase tables (every V here is monomial)
+    for (const Op &o : ops) {
+        tufrg::SymElem e{};
+        e.conj = o.conj;
+        for (int ch = 0; ch < 2; ch++)
+            for (int a2 = 0; a2 < 4; a2++)
+                for (int a = 0; a < 4; a++)
+                    if (std::abs(o.V[ch][a2][a]) > 0.5) {   // V[a'][a] = i^qt: source a feeds target a'
+                        const cd v = o.V[ch][a2][a];
+                        e.pinv[ch][a] = a2;
+                        e.qt[ch][a2] = std::abs(v - 1.0) < 1e-9 ? 0 : std::abs(v - cd(0, 1)) < 1e-9 ? 1
+                                     : std::abs(v + 1.0) < 1e-9 ? 2 : 3;
+                    }
+        ls.elem.push_back(e);
+        for (int k = 0; k < nd; k++)
+            ls.dfwd.push_back(find_delta(o.Gd[0] * m->deltas[2 * k] + o.Gd[1] * m->deltas[2 * k + 1],
+                                         o.Gd[2] * m->deltas[2 * k] + o.Gd[3] * m->deltas[2 * k + 1]));
+    }
+    // orbits: the smallest momentum of each orbit is its representative
+    std::vector<char> done(m->Nq, 0);
+    ls.orb_ofs.push_back(0);
+    for (int q = 0; q < m->Nq; q++) {
+        if (done[q]) continue;
+        ls.list.push_back(q);
+        const int qx = q / L, qy = q % L;
+        for (size_t e = 0; e < ops.size(); e++) {
+            const int *G = ops[e].Gq;
+            const int x = ((G[0] * qx + G[1] * qy) % L + L) % L, y = ((G[2] * qx + G[3] * qy) % L + L) % L;
+            const int q2 = x * L + y;
+            if (done[q2]) continue;
+            done[q2] = 1;
+            ls.orb.push_back(make_int2(q2, (int)e));
+        }
+        ls.orb_ofs.push_back((int)ls.orb.size());
+    }
+}
+
 // e^{i q.R} for every coarse q and every listed vector (exact lattice phases).
 std::vector<double2> phase_table(int Lq, const std::vector<int> &vecs)
 {
@@ -249,7 +408,8 @@ void release(tufrg_model *m)
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
                     m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
-                    m->d_trs_list};
+                    m->d_loop_list, m->d_orb_ofs, m->d_orb, m->d_sym_elem, m->d_sym_dfwd, m->d_lph32,
+                    m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -512,36 +672,20 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
 
     build_loop_tables(m);
     build_gather_tables(m);
-    // time reversal (TUFRG_SYMMETRY_AUTO): t_R = W t_R^* W^T with W = i sigma_y for every hopping
+    // loop symmetries (TUFRG_SYMMETRY_AUTO, split two-band path)
     m->n_loop_q = m->Nq;
     if (d.symmetry == TUFRG_SYMMETRY_AUTO && ns == 2 && loops2_supported(m)) {
-        bool ok = true;
-        const int W[2][2] = {{0, 1}, {-1, 0}};
-        for (int h = 0; h < m->nhop && ok; h++) {
-            const double *t = &m->hopt[2 * (size_t)h * 4];
-            double tmax = 0.0;
-            for (int i = 0; i < 4; i++) tmax = std::max(tmax, std::hypot(t[2 * i], t[2 * i + 1]));
-            for (int i = 0; i < 2; i++)
-                for (int j = 0; j < 2; j++) {
-                    double re = 0.0, im = 0.0;   // (W t^* W^T)_{ij}
-                    for (int a = 0; a < 2; a++)
-                        for (int b = 0; b < 2; b++) {
-                            re += W[i][a] * W[j][b] * t[2 * (a * 2 + b)];
-                            im -= W[i][a] * W[j][b] * t[2 * (a * 2 + b) + 1];
-                        }
-                    if (std::hypot(re - t[2 * (i * 2 + j)], im - t[2 * (i * 2 + j) + 1]) > 1e-12 * std::max(1.0, tmax)) ok = false;
-                }
-        }
-        if (ok) {
-            std::vector<int> half;
-            for (int q = 0; q < m->Nq; q++) {
-                const int qx = q / m->Lq, qy = q % m->Lq;
-                const int mq = ((m->Lq - qx) % m->Lq) * m->Lq + (m->Lq - qy) % m->Lq;
-                if (q <= mq) half.push_back(q);
-            }
-            m->trs = true;
-            m->n_loop_q = (int)half.size();
-            CK(upload(&m->d_trs_list, half, m->stream), "upload momentum list");
+        LoopSymmetry ls;
+        build_loop_symmetry(m, ls);
+        if ((int)ls.list.size() < m->Nq) {
+            m->sym = true;
+            m->n_loop_q = (int)ls.list.size();
+            m->n_sym_elem = (int)ls.elem.size();
+            CK(upload(&m->d_loop_list, ls.list, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_orb_ofs, ls.orb_ofs, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_orb, ls.orb, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_sym_elem, ls.elem, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_sym_dfwd, ls.dfwd, m->stream), "upload symmetry tables");
         }
     }
     m->plan = plan_loops(m);
@@ -573,6 +717,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             CK(upload(&m->d_eofs[ch], eofs[ch], m->stream), "upload projection tables");
             if (!eterms[ch].empty()) CK(upload(&m->d_eterms[ch], eterms[ch], m->stream), "upload projection tables");
             CK(upload(&m->d_v0d[ch], v0d[ch], m->stream), "upload projection tables");
+            if (split) {
+                std::vector<float2> v32(v0d[ch].size());
+                for (size_t i = 0; i < v32.size(); i++) v32[i] = make_float2((float)v0d[ch][i].x, (float)v0d[ch][i].y);
+                CK(upload(&m->d_v0d32[ch], v32, m->stream), "upload projection tables");
+            }
         }
     }
     {
@@ -590,7 +739,28 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             m->max_terms = std::max(m->max_terms, m->gofs[ch][p + 1] - m->gofs[ch][p]);
     m->dft_nsplit = dft_plan_nsplit(m);
     // the Fourier transform uses e^{i u.R''} for the classes
-    CK(upload(&m->d_clsph, phase_table(m->Lq, m->cls), m->stream), "upload phase table");
+    {
+        const std::vector<double2> cph = phase_table(m->Lq, m->cls);
+        CK(upload(&m->d_clsph, cph, m->stream), "upload phase table");
+        if (split) {
+            std::vector<float2> c32(cph.size());
+            for (size_t i = 0; i < cph.size(); i++) c32[i] = make_float2((float)cph[i].x, (float)cph[i].y);
+            CK(upload(&m->d_clsph32, c32, m->stream), "upload phase table");
+            // e^{-2 pi i n / Lf} of the split loop kernel, with exact quarter-turn values
+            std::vector<float2> lph(m->Lf);
+            for (int n = 0; n < m->Lf; n++) {
+                const double a = 2.0 * M_PI * (double)n / (double)m->Lf;
+                double c = std::cos(a), sn = std::sin(a);
+                if ((4 * n) % m->Lf == 0) {
+                    const int quarter = (4 * n) / m->Lf;
+                    c = quarter == 0 ? 1.0 : quarter == 2 ? -1.0 : 0.0;
+                    sn = quarter == 1 ? 1.0 : quarter == 3 ? -1.0 : 0.0;
+                }
+                lph[n] = make_float2((float)c, (float)-sn);
+            }
+            CK(upload(&m->d_lph32, lph, m->stream), "upload phase table");
+        }
+    }
     CK(dalloc(&m->d_E, Nk * ns), "cudaMalloc eigenvalues");
     CK(dalloc(&m->d_U, Nk * ns2), "cudaMalloc eigenvectors");
     CK(dalloc(&m->d_ft, Nk * ns), "cudaMalloc Fermi table");

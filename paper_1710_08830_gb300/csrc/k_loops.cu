@@ -241,8 +241,9 @@ __global__ void __launch_bounds__(32 * WARPS) loops_ns2_kernel(LoopArgs<R> a)
 // this GPU's FP64 rate would make the reduction, not the memory traffic, its bound), with four loads
 // in flight per thread.
 template <typename R>
-__device__ __forceinline__ double2 reduce_one(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                              const int *dslot, const int *deltas, int s, int d, int ab, double inv_nk)
+__device__ __forceinline__ typename cpx<R>::t reduce_one(const typename cpx<R>::t *__restrict__ part, int n_part,
+                                                         int ndx, int ndyh, const int *dslot, const int *deltas, int s,
+                                                         int d, int ab, R inv_nk)
 {
     using C2 = typename cpx<R>::t;
     const int dx = deltas[2 * d], dy = deltas[2 * d + 1];
@@ -269,8 +270,11 @@ __device__ __forceinline__ double2 reduce_one(const typename cpx<R>::t *__restri
         re += v.x;
         im += v.y;
     }
-    return make_double2((double)re * inv_nk, (half ? 1.0 : -1.0) * (double)im * inv_nk);
+    return mk(re * inv_nk, (half ? im : -im) * inv_nk);
 }
+
+__device__ __forceinline__ double2 to64(double2 v) { return v; }
+__device__ __forceinline__ double2 to64(float2 v) { return make_double2(widen_f(v.x), widen_f(v.y)); }
 
 template <typename R>
 __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
@@ -284,17 +288,30 @@ __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part,
     const int ab = idx % NS4;
     const int d = (idx / NS4) % nd;
     const int s = idx / ((size_t)NS4 * nd);
-    const double2 v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, s, d, ab, inv_nk);
-    if (out64) out64[idx] = v;
-    if (out32) out32[idx] = mk(R(v.x), R(v.y));
+    const auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, s, d, ab, R(inv_nk));
+    if (out64) out64[idx] = to64(v);
+    if (out32) out32[idx] = v;
 }
 
-// Time-reversal variant (two bands): list position i holds q = list[i]; the loops at -q follow as
-// Lc(-q)[d][3-a][3-b] = (-1)^(popcount(a) + popcount(b)) conj(Lc(q)[d][a][b]).
+// Symmetry variant (two bands): list position i holds the representative of an orbit; every member
+// (q', element e) of the orbit receives Lc(q')[d'][a'][b'] = i^k (conj ? conj(v) : v) with
+// d' = dfwd[e][d], a' = pinv[a], b' = pinv[b], k = qt[a'] - qt[b'] (see SymElem): sign flips and swaps.
+template <typename C2>
+__device__ __forceinline__ C2 quarter_turn(C2 v, int k)
+{
+    switch (k & 3) {
+    case 0: return v;
+    case 1: return mk(-v.y, v.x);
+    case 2: return mk(-v.x, -v.y);
+    default: return mk(v.y, -v.x);
+    }
+}
+
 template <typename R>
-__global__ void loops_reduce_trs_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                        const int *dslot, const int *deltas, int nd, int n_list, const int *list, int Lq,
-                                        double inv_nk, double2 *out64, typename cpx<R>::t *out32, const int *skip)
+__global__ void loops_reduce_sym_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
+                                        const int *dslot, const int *deltas, int nd, int n_list, const int *orb_ofs,
+                                        const int2 *orb, const SymElem *elem, const int *dfwd, int ch, double inv_nk,
+                                        double2 *out64, typename cpx<R>::t *out32, const int *skip)
 {
     if (skip && *skip) return;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -303,19 +320,17 @@ __global__ void loops_reduce_trs_kernel(const typename cpx<R>::t *__restrict__ p
     const int ab = idx % NS4;
     const int d = (idx / NS4) % nd;
     const int i = idx / ((size_t)NS4 * nd);
-    const double2 v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, i, d, ab, inv_nk);
-    const int q = list[i], qx = q / Lq, qy = q % Lq;
-    const int mq = ((Lq - qx) % Lq) * Lq + (Lq - qy) % Lq;
-    const size_t o = ((size_t)q * nd + d) * NS4 + ab;
-    if (out64) out64[o] = v;
-    if (out32) out32[o] = mk(R(v.x), R(v.y));
-    if (mq != q) {
-        const int a = ab / NS2, b = ab % NS2;
-        const double sg = ((__popc(a) + __popc(b)) & 1) ? -1.0 : 1.0;
-        const double2 w = make_double2(sg * v.x, -sg * v.y);
-        const size_t om = ((size_t)mq * nd + d) * NS4 + (NS2 - 1 - a) * NS2 + (NS2 - 1 - b);
-        if (out64) out64[om] = w;
-        if (out32) out32[om] = mk(R(w.x), R(w.y));
+    const auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, i, d, ab, R(inv_nk));
+    const auto vc = mk(v.x, -v.y);
+    const int a = ab / NS2, b = ab % NS2;
+    for (int t = orb_ofs[i]; t < orb_ofs[i + 1]; t++) {
+        const int2 mem = orb[t];
+        const SymElem &e = elem[mem.y];
+        const int a2 = e.pinv[ch][a], b2 = e.pinv[ch][b];
+        const auto w = quarter_turn(e.conj ? vc : v, e.qt[ch][a2] - e.qt[ch][b2]);
+        const size_t o = ((size_t)mem.x * nd + dfwd[(size_t)mem.y * nd + d]) * NS4 + a2 * NS2 + b2;
+        if (out64) out64[o] = to64(w);
+        if (out32) out32[o] = w;
     }
 }
 
@@ -388,11 +403,11 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             const size_t total = (size_t)m->n_loop_q * m->nd * NS4;
             const size_t off = (size_t)ch * m->Nq * m->nd * NS4;
             PhaseScope ps(m, PH_LOOPRED);
-            if (m->trs)
-                loops_reduce_trs_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+            if (m->sym)
+                loops_reduce_sym_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    m->n_loop_q, m->d_trs_list, m->Lq, inv_nk, m->d_Lc + off, m->d_Lc32 + off,
-                    m->sur ? m->d_sur_flag : nullptr);
+                    m->n_loop_q, m->d_orb_ofs, m->d_orb, m->d_sym_elem, m->d_sym_dfwd, ch, inv_nk, m->d_Lc + off,
+                    m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
             else
                 loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,

@@ -44,6 +44,7 @@ struct Args2 {
     const double *Tp;        // device temperature: switch = 1e-2 * (*Tp)
     const int *s_list;       // optional: CTA x evaluates transfer momentum s_list[x] (partials indexed by x)
     const int *skip;         // optional: the whole launch returns at once when *skip != 0
+    const float2 *ptab;      // optional: e^{-2 pi i n / Lf}, n < Lf (computed in the kernel when null)
 };
 
 // (t1,t3,t2,t4) -> ab index of the compact loop (P: a=(t2,t1), b=(t4,t3); C: a=(t1,t2), b=(t3,t4))
@@ -73,10 +74,14 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     float2 *ptab = reinterpret_cast<float2 *>(smem_raw);
     float *red = reinterpret_cast<float *>(smem_raw + ((sizeof(float2) * a.Lf + 15) & ~size_t(15)));
     const int Lf = a.Lf;
-    for (int n = threadIdx.x; n < Lf; n += blockDim.x) {
-        double sn, cs;
-        sincospi(2.0 * (double)n / (double)Lf, &sn, &cs);
-        ptab[n] = make_float2((float)cs, (float)-sn);   // e^{-2 pi i n / Lf}
+    if (a.ptab) {
+        for (int n = threadIdx.x; n < Lf; n += blockDim.x) ptab[n] = a.ptab[n];
+    } else {
+        for (int n = threadIdx.x; n < Lf; n += blockDim.x) {
+            double sn, cs;
+            sincospi(2.0 * (double)n / (double)Lf, &sn, &cs);
+            ptab[n] = make_float2((float)cs, (float)-sn);   // e^{-2 pi i n / Lf}
+        }
     }
     __syncthreads();
 
@@ -363,6 +368,7 @@ cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_li
     a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
     a.thr = 0.f;
     a.Tp = m->d_scal;
+    a.ptab = m->d_lph32;
     const int n_s = s_list ? n_list : m->Nq;
     switch (ndyh) {
     case 1: return ch == 0 ? launch2<1, 0>(m, a, n_s) : launch2<1, 1>(m, a, n_s);
@@ -376,8 +382,8 @@ cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_li
 
 cudaError_t launch_loops2(tufrg_model *m, int ch)
 {
-    // with time reversal only one momentum of each pair {q, -q} is summed (partial slots = list positions)
-    return launch_loops2_ex(m, ch, m->trs ? m->d_trs_list : nullptr, m->trs ? m->n_loop_q : 0,
+    // with loop symmetries only the orbit representatives are summed (partial slots = list positions)
+    return launch_loops2_ex(m, ch, m->sym ? m->d_loop_list : nullptr, m->sym ? m->n_loop_q : 0,
                             reinterpret_cast<float2 *>(m->d_part), m->sur ? m->d_sur_flag : nullptr);
 }
 

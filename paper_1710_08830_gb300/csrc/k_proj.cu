@@ -36,7 +36,7 @@ template <> __device__ __forceinline__ float2 ld_as<float>(const float2 &v) { re
 
 template <typename R, typename XT, int CPT>
 __global__ void __launch_bounds__(128) dft_kernel(const XT *__restrict__ X, int Nq, int M2, int ncls, int nchunk,
-                                                  const double2 *__restrict__ clsph, int u_per,
+                                                  const XT *__restrict__ clsph, int u_per,
                                                   typename cpx<R>::t *__restrict__ part)
 {
     using C2 = typename cpx<R>::t;
@@ -116,7 +116,7 @@ __device__ __forceinline__ double mag_of(float m2) { return (double)sqrtf(m2); }
 // product) and writes the FP64 copy only when asked (A != NULL).
 template <typename R, typename XT, int QT>
 __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, const typename cpx<R>::t *__restrict__ Xr,
-                                                      const double2 *v0d0, const double2 *v0d1, const int *eofs0,
+                                                      const XT *v0d0, const XT *v0d1, const int *eofs0,
                                                       const int *eofs1, const int2 *et0, const int2 *et1,
                                                       const typename cpx<R>::t *ph, int nph, int Nq, int M2, int ncls,
                                                       int chmask, double2 *A, float2 *A32, unsigned long long *amax)
@@ -148,21 +148,38 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
             const int2 *et = ch == 0 ? et0 : et1;
             const int t1 = eofs[e + 1];
             const int lim = ncls * M2;   // sources at or above lim belong to the C channel
-            for (int t = eofs[e]; t < t1; t++) {
-                const int2 g = et[t];
-                const int idx = g.x & 0x7fffffff;
-                if (!((chmask >> (idx >= lim ? 1 : 0)) & 1)) continue;
-                C2 x = Xr[idx];
-                if (g.x < 0) {
-                    x.x = -x.x;
-                    x.y = -x.y;
-                }
-                const C2 *p = phs + g.y;
+            // two terms per iteration: both gathers are issued before either is used
+            int t = eofs[e];
+            for (; t + 2 <= t1; t += 2) {
+                const int2 g0 = et[t], g1 = et[t + 1];
+                const int i0 = g0.x & 0x7fffffff, i1 = g1.x & 0x7fffffff;
+                const bool on0 = (chmask >> (i0 >= lim ? 1 : 0)) & 1, on1 = (chmask >> (i1 >= lim ? 1 : 0)) & 1;
+                C2 x0 = on0 ? Xr[i0] : mk(R(0), R(0)), x1 = on1 ? Xr[i1] : mk(R(0), R(0));
+                if (g0.x < 0) { x0.x = -x0.x; x0.y = -x0.y; }
+                if (g1.x < 0) { x1.x = -x1.x; x1.y = -x1.y; }
+                const C2 *p0 = phs + g0.y, *p1 = phs + g1.y;
 #pragma unroll
                 for (int qi = 0; qi < QT; qi++) {
-                    const C2 pq = p[qi * nph];
-                    acc[qi].x += pq.x * x.x - pq.y * x.y;
-                    acc[qi].y += pq.x * x.y + pq.y * x.x;
+                    const C2 pa = p0[qi * nph], pb = p1[qi * nph];
+                    acc[qi].x += pa.x * x0.x - pa.y * x0.y;
+                    acc[qi].y += pa.x * x0.y + pa.y * x0.x;
+                    acc[qi].x += pb.x * x1.x - pb.y * x1.y;
+                    acc[qi].y += pb.x * x1.y + pb.y * x1.x;
+                }
+            }
+            if (t < t1) {
+                const int2 g = et[t];
+                const int idx = g.x & 0x7fffffff;
+                if ((chmask >> (idx >= lim ? 1 : 0)) & 1) {
+                    C2 x = Xr[idx];
+                    if (g.x < 0) { x.x = -x.x; x.y = -x.y; }
+                    const C2 *p = phs + g.y;
+#pragma unroll
+                    for (int qi = 0; qi < QT; qi++) {
+                        const C2 pq = p[qi * nph];
+                        acc[qi].x += pq.x * x.x - pq.y * x.y;
+                        acc[qi].y += pq.x * x.y + pq.y * x.x;
+                    }
                 }
             }
         } else {
@@ -200,7 +217,7 @@ __global__ void amax_locate_kernel(const C2 *A, size_t n, const unsigned long lo
 }
 
 template <typename R, typename XT, int CPT>
-cudaError_t dft_run(tufrg_model *m, const XT *d_state, int ch_lo, int nch, typename cpx<R>::t *part,
+cudaError_t dft_run(tufrg_model *m, const XT *d_state, const XT *clsph, int ch_lo, int nch, typename cpx<R>::t *part,
                     typename cpx<R>::t *Xr)
 {
     const int M2 = m->M * m->M;
@@ -216,8 +233,8 @@ cudaError_t dft_run(tufrg_model *m, const XT *d_state, int ch_lo, int nch, typen
         PhaseScope ps(m, PH_DFT, 2);
         dim3 grid(xb, nsplit, nch * nchunk);
         // channels are numbered from ch_lo inside the kernels
-        k<<<grid, threads, smem, m->stream>>>(d_state + (size_t)ch_lo * m->Nq * M2, m->Nq, M2, m->ncls, nchunk,
-                                               m->d_clsph, u_per, part);
+        k<<<grid, threads, smem, m->stream>>>(d_state + (size_t)ch_lo * m->Nq * M2, m->Nq, M2, m->ncls, nchunk, clsph,
+                                               u_per, part);
         TUFRG_CUDA_TRY(cudaGetLastError());
         const size_t total = (size_t)nch * m->ncls * M2;
         dft_reduce_kernel<R><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
@@ -250,8 +267,10 @@ cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_s
     if (ch_lo > ch_hi) return cudaSuccess;
     const int nch = ch_hi - ch_lo + 1;
     if (m->precision == TUFRG_FP64)
-        return dft_run<double, double2, 16>(m, d_state, ch_lo, nch, reinterpret_cast<double2 *>(m->d_dftpart), m->d_Xr);
-    return dft_run<float, float2, 32>(m, d_state32, ch_lo, nch, reinterpret_cast<float2 *>(m->d_dftpart), m->d_Xr32);
+        return dft_run<double, double2, 16>(m, d_state, m->d_clsph, ch_lo, nch, reinterpret_cast<double2 *>(m->d_dftpart),
+                                            m->d_Xr);
+    return dft_run<float, float2, 32>(m, d_state32, m->d_clsph32, ch_lo, nch, reinterpret_cast<float2 *>(m->d_dftpart),
+                                      m->d_Xr32);
 }
 
 constexpr int PROJ_QT = 8;   // transfer momenta per thread
@@ -274,7 +293,7 @@ cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 
         const size_t smem = sizeof(float2) * PROJ_QT * m->nph;
         auto k = project_kernel<float, float2, PROJ_QT>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, 256, smem, m->stream>>>(d_state32, m->d_Xr32, m->d_v0d[0], m->d_v0d[1], m->d_eofs[0], m->d_eofs[1],
+        k<<<grid, 256, smem, m->stream>>>(d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_eofs[0], m->d_eofs[1],
                                           m->d_eterms[0], m->d_eterms[1], m->d_ph32, m->nph, m->Nq, M2, m->ncls,
                                           channel_mask, d_A, m->d_A32, m->d_amax);   // d_A may be NULL here
     }

@@ -24,18 +24,26 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
     acc.y = fma(a.y, b.x, acc.y);
 }
 
-// exact float -> double on the integer pipe; subnormal, inf and nan take the plain conversion
-__device__ __forceinline__ double widen(float f)
+// bits of the exact double of a float, formed on the integer pipe (hi word, lo word); subnormal,
+// inf and nan take the plain conversion
+__device__ __forceinline__ uint2 widen_bits(float f)
 {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
-    if (e == 0u && man == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // signed zero
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (man >> 3);
-    return __hiloint2double((int)hi, (int)(u << 29));
+    if (e == 0u && man == 0u) return make_uint2(u & 0x80000000u, 0u);   // signed zero
+    if (e == 0u || e == 0xffu) {
+        const double d = (double)f;
+        return make_uint2((unsigned)__double2hiint(d), (unsigned)__double2loint(d));
+    }
+    return make_uint2((u & 0x80000000u) | ((e + 896u) << 20) | (man >> 3), u << 29);
 }
-__device__ __forceinline__ double2 out_c(float2 v, float sc) { return make_double2(widen(sc * v.x), widen(sc * v.y)); }
-__device__ __forceinline__ double2 out_c(double2 v, double sc) { return make_double2(sc * v.x, sc * v.y); }
+// one FP64 complex output (little-endian double2 = lo, hi, lo, hi words)
+__device__ __forceinline__ void store_c(double2 *o, float2 v, float sc)
+{
+    const uint2 re = widen_bits(sc * v.x), im = widen_bits(sc * v.y);
+    *reinterpret_cast<uint4 *>(o) = make_uint4(re.y, re.x, im.y, im.x);
+}
+__device__ __forceinline__ void store_c(double2 *o, double2 v, double sc) { *o = make_double2(sc * v.x, sc * v.y); }
 
 // two consecutive complex values from 16-byte aligned shared memory
 __device__ __forceinline__ void ld2(const float2 *p, float2 &a, float2 &b)
@@ -72,7 +80,7 @@ __device__ __forceinline__ void tile44(const C2 *Xt, const C2 *Y, int M, int r, 
 
 // Two-band bond sets (N_s^2 = 4, M = 4 N_ff): one CTA per (q, channel), one 4 x 4 output tile per
 // thread (rows {2i, 2i+1, M/2 + 2i, M/2 + 2i + 1}, columns likewise).  Shared memory holds two
-// M x M buffers: A transposed and L for T = A L, then A (reloaded, row-major) and T transposed for
+// M x M buffers: A transposed and L for T^T = L^T A^T, then A (reloaded, row-major) and T^T for
 // c T A, so one wave of CTAs covers all transfer momenta.
 template <typename R>
 __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Lc,
@@ -107,7 +115,9 @@ __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = mk(R(0), R(0));
-    if (active) tile44(s0, s1, M, r, c, acc);   // T = A L
+    // T^T = L^T A^T: tile rows index columns of L, tile columns rows of A, so the tile is stored
+    // row-major into T^T with consecutive lanes on consecutive addresses
+    if (active) tile44(s1, s0, M, r, c, acc);
     __syncthreads();
     const int rows[4] = {r, r + 1, h + r, h + r + 1}, cols[4] = {c, c + 1, h + c, h + c + 1};
     if (active) {
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t
         for (int i = 0; i < 4; i++)
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                s1[cols[j] * M + rows[i]] = acc[i][j];   // T^T
+                s1[rows[i] * M + cols[j]] = acc[i][j];   // T^T[rows_i][cols_j] = T[cols_j][rows_i]
                 acc[i][j] = mk(R(0), R(0));
             }
     }
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
-            for (int j = 0; j < 4; j++) o[rows[i] * M + cols[j]] = out_c(acc[i][j], sc);
+            for (int j = 0; j < 4; j++) store_c(o + rows[i] * M + cols[j], acc[i][j], sc);
     }
 }
 

@@ -47,6 +47,25 @@ struct FlowDev {
     int accepted;     // 1 if the last attempt was accepted
 };
 
+// One element of the loop symmetry group (two bands): Lc(q')[d'][a'][b'] =
+// i^(qt[ch][a'] - qt[ch][b']) * (conj ? conj(L) : L) with L = Lc(q)[d][a][b], a' = pinv[ch][a],
+// b' = pinv[ch][b], q' = G_q q and d' = index of G Delta_d (every phase is a power of i).
+struct SymElem {
+    int conj;
+    int pinv[2][4];
+    int qt[2][4];
+};
+
+// bits of the exact double of a float, formed on the integer pipe (this GPU's FP64 pipe is slow);
+// zero, subnormal, inf and nan take the plain conversion
+__device__ __forceinline__ double widen_f(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+
 struct LoopPlan {
     int kx_per_cta;     // threads (columns) per CTA
     int ky_chunks;      // number of ky ranges per column
@@ -97,14 +116,24 @@ struct tufrg_model {
     int *d_dij = nullptr;           // [nff][nff]
     int *d_gofs[2] = {nullptr, nullptr};
     tufrg::GatherTerm *d_gterms[2] = {nullptr, nullptr};
-    bool trs = false;               // loops from time reversal for -q (see TUFRG_SYMMETRY_AUTO)
-    int n_loop_q = 0;               // transfer momenta summed directly (Nq, or the half list)
-    int *d_trs_list = nullptr;      // [n_loop_q] the directly summed momenta (one of each pair q, -q)
+    // loop symmetries (TUFRG_SYMMETRY_AUTO): the k-sums run for one representative momentum per orbit
+    // of the symmetry group and the reduction writes every orbit member from it
+    bool sym = false;
+    int n_loop_q = 0;               // transfer momenta summed directly (Nq without symmetry)
+    int n_sym_elem = 0;             // group elements (identity included)
+    int *d_loop_list = nullptr;     // [n_loop_q] orbit representatives
+    int *d_orb_ofs = nullptr;       // [n_loop_q + 1] CSR offsets into d_orb
+    int2 *d_orb = nullptr;          // (member momentum, group element) of every orbit, representative first
+    tufrg::SymElem *d_sym_elem = nullptr;   // [n_sym_elem]
+    int *d_sym_dfwd = nullptr;      // [n_sym_elem][nd] index of G Delta_d
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
     double2 *d_v0d[2] = {nullptr, nullptr};    // [M*M] bare vertex V0 at the onsite bond pair, 0 elsewhere
     float2 *d_X32 = nullptr;        // [2][Nq][M][M] FP32 copy of the state being evaluated (split path)
+    float2 *d_lph32 = nullptr;      // [Lf] e^{-2 pi i n / Lf} for the split loop kernel
+    float2 *d_clsph32 = nullptr;    // [Nq][ncls] e^{i u.R''} (split-path Fourier transform)
+    float2 *d_v0d32[2] = {nullptr, nullptr};   // FP32 copies of d_v0d (split path)
     double2 *d_ph = nullptr;        // [Nq][nph] phase table e^{i q.R}
     double2 *d_clsph = nullptr;     // [Nq][ncls] e^{i q.R''} for the Fourier transform
     double2 *d_V0 = nullptr;        // [ns^4]

@@ -112,24 +112,42 @@ def _zeeman(spec, B=0.15):
     return spec.with_(hop_R=hop_R, hop_t=hop_t)
 
 
+C4V = [((1, 0), (0, 1)), ((0, -1), (1, 0)), ((-1, 0), (0, -1)), ((0, 1), (-1, 0)),
+       ((-1, 0), (0, 1)), ((1, 0), (0, -1)), ((0, 1), (1, 0)), ((0, -1), (-1, 0))]
+
+
+def _n_orbits(Lq, mats):
+    """Orbits of the Lq x Lq transfer mesh under the given point operations (brute force)."""
+    seen, n = set(), 0
+    for qx in range(Lq):
+        for qy in range(Lq):
+            if (qx, qy) in seen:
+                continue
+            n += 1
+            for (a, b), (c, d) in mats:
+                seen.add(((a * qx + b * qy) % Lq, (c * qx + d * qy) % Lq))
+    return n
+
+
 @pytest.mark.parametrize("case", ["rashba_ff9_Lf25", "hubbard_ff5_Lf24", "rashba_ff13_Lf30"])
-def test_loops_time_reversal(case):
-    """Time-reversal-symmetric models sum one momentum of each pair (q, -q) and derive the other;
-    the result equals the full k-sum (to FP32 rounding) and the oracle.  A Zeeman field breaks the
-    symmetry: every momentum is summed directly and the loops still match the oracle."""
+def test_loops_symmetry(case):
+    """Models with the square-lattice point group (spin rotations included) sum the loops for one
+    momentum per orbit and write the rest by symmetry; the result equals the full k-sum (to FP32
+    rounding) and the oracle.  An out-of-plane Zeeman field leaves only the four rotations: the orbits
+    of C4 are summed and the loops still match the oracle.  (Without spin-orbit coupling the field
+    keeps all eight operations, with diagonal spin unitaries.)"""
     api = _api()
     spec = CASES[case]()
     Lq = spec.Lq
-    n_self = 4 if Lq % 2 == 0 else 1
     m = api.Model(spec, api.SPLIT32)
     full = api.Model(spec, api.SPLIT32, symmetry=api.SYMMETRY_OFF)
-    assert m.n_loop_q == (Lq * Lq + n_self) // 2 and full.n_loop_q == Lq * Lq
+    assert m.n_loop_q == _n_orbits(Lq, C4V) and full.n_loop_q == Lq * Lq
     for T in (2.0, 0.07):
         L, Lfull = m.loops(T).cpu().numpy(), full.loops(T).cpu().numpy()
         assert rel(L, Lfull) < 2e-6
     zs = _zeeman(spec)
     mz = api.Model(zs, api.SPLIT32)
-    assert mz.n_loop_q == Lq * Lq
+    assert mz.n_loop_q == _n_orbits(Lq, C4V if case.startswith("hubbard") else C4V[:4])
     o = oracle.Oracle(zs)
     L = mz.loops(0.07).cpu().numpy()
     for ch in (0, 1):
