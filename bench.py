@@ -27,6 +27,14 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "rashba_hubbard_q24x24_k8x8_ff9"
 METRIC = "TU-fRG RHS evals/s (split precision, <=1e-4 vertex err) on Rashba-Hubbard 24x24 q / 8x8 k per cell"
 T_BENCH = 0.1
+# other model configurations that --workload selects (the JSON line then names them)
+WORKLOADS = {
+    "rashba": (WORKLOAD, METRIC),
+    "hubbard": ("hubbard_q8x8_k16x16_ff5",
+                "TU-fRG RHS evals/s (split precision, <=1e-4 vertex err) on Hubbard 8x8 q / 16x16 k per cell"),
+    "t2g": ("t2g_soc_q32x32_k6x6_ff9",
+            "TU-fRG RHS evals/s (split precision, <=1e-4 vertex err) on t2g+SOC (N_s = 6) 32x32 q / 6x6 k per cell"),
+}
 
 
 def _env_int(k, d):
@@ -172,6 +180,9 @@ def main():
     ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
     ap.add_argument("--batch-flows", type=int, default=0,
                     help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
+                    help="model configuration (default: the 24x24 / 8x8 Rashba-Hubbard benchmark workload)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path (and the accuracy check)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
@@ -212,10 +223,16 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    spec = inputs.rashba_q24_k8_ff9(seed=rank)     # one independent instance per rank
+    workload, metric = WORKLOADS[args.workload]
+    if args.workload == "rashba":
+        spec = inputs.rashba_q24_k8_ff9(seed=rank)     # one independent instance per rank
+    elif args.workload == "hubbard":
+        spec = inputs.hubbard_q8_k16_ff5()
+    else:
+        spec = inputs.t2g_q32_k6_ff9(seed=rank)
     stream = torch.cuda.current_stream()
     m32 = Model(spec, SPLIT32, stream=stream)
-    m64 = Model(spec, FP64, stream=stream)
+    m64 = None if args.no_fp64 else Model(spec, FP64, stream=stream)
     # a mid-flow state: the split flow from T0 = 10 down to the benchmark temperature
     state, _ = m32.flow(T_end=T_BENCH, stop=1e9)
     out = torch.empty_like(state)
@@ -256,25 +273,27 @@ def main():
     ms_per_step = dev_ms_max / args.steps
 
     # ---------------- accuracy of the split path against the FP64 GPU path (same state)
-    d32 = m32.rhs(T_BENCH, state).cpu().numpy()
-    d64 = m64.rhs(T_BENCH, state).cpu().numpy()
-    err_split = float(np.abs(d32 - d64).max() / np.abs(d64).max())
-
-    # ---------------- plain FP64 GPU right-hand sides
-    k64 = max(3, min(args.steps, 30))
-    for _ in range(2):
-        m64.rhs(T_BENCH, state, out=out)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k64):
-        m64.rhs(T_BENCH, state, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_rate = k64 / (e0.elapsed_time(e1) * 1e-3)
+    k64 = max(3, min(args.steps, 30))
+    err_split = fp64_rate = None
+    if m64 is not None:
+        d32 = m32.rhs(T_BENCH, state).cpu().numpy()
+        d64 = m64.rhs(T_BENCH, state).cpu().numpy()
+        err_split = float(np.abs(d32 - d64).max() / np.abs(d64).max())
+
+        # ---------------- plain FP64 GPU right-hand sides
+        for _ in range(2):
+            m64.rhs(T_BENCH, state, out=out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k64):
+            m64.rhs(T_BENCH, state, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_rate = k64 / (e0.elapsed_time(e1) * 1e-3)
 
     # ---------------- the same split path with every transfer momentum summed directly (the FP64
-    # path above does not use the time-reversal shortcut either)
+    # path above does not use the loop symmetries either)
     m_full = Model(spec, SPLIT32, stream=stream, symmetry=SYMMETRY_OFF)
     for _ in range(2):
         m_full.rhs(T_BENCH, state, out=out)
@@ -303,15 +322,16 @@ def main():
     # ---------------- time-to-Lambda_c (full flows from T0 = 10)
     flows = None
     if not args.no_flow:
+        def summary(r):
+            return {"wall_s": r["wall_s"], "Tc": r["Tc"], "crossed": r["crossed"], "n_rhs": r["n_rhs"],
+                    "n_steps": r["n_steps"], "lead_channel": "PC"[r["lead_channel"]], "lead_q": r["lead_q"],
+                    "amax": r["amax"]}
         _, r32 = m32.flow()
-        _, r64 = m64.flow()
-        flows = {"split": {"wall_s": r32["wall_s"], "Tc": r32["Tc"], "crossed": r32["crossed"],
-                           "n_rhs": r32["n_rhs"], "n_steps": r32["n_steps"], "lead_channel": "PC"[r32["lead_channel"]],
-                           "amax": r32["amax"]},
-                 "fp64": {"wall_s": r64["wall_s"], "Tc": r64["Tc"], "crossed": r64["crossed"],
-                          "n_rhs": r64["n_rhs"], "n_steps": r64["n_steps"], "lead_channel": "PC"[r64["lead_channel"]],
-                          "amax": r64["amax"]},
+        flows = {"split": summary(r32),
                  "note": "Tc is the crossing of max|A| = 50 when crossed == 1, else the end temperature 0.02"}
+        if m64 is not None:
+            _, r64 = m64.flow()
+            flows["fp64"] = summary(r64)
     batch = None
     if args.batch_flows > 0:
         from paper_1710_08830_gb300.api import flow_batch
@@ -348,13 +368,15 @@ def main():
     ns = spec.n_s
     ndy_half = int(sum(1 for d in np.unique(spec.ff_R[:, 1][:, None] - spec.ff_R[:, 1][None, :]) if d >= 0))
     unit_cfma = ns ** 4 + ns ** 5 + ndy_half * ns ** 4
-    # one launch sums every fine k for each directly evaluated transfer momentum (time reversal
-    # supplies the partners of the others)
+    # one launch sums every fine k for each directly evaluated transfer momentum (the loop symmetries
+    # supply the other momenta)
     flops_per_launch = 8.0 * m32.n_loop_q * spec.Nk * unit_cfma
     loop_ms_avg = phase_ms["loops"] / max(1, loop_launches)
     achieved = flops_per_launch / (loop_ms_avg * 1e-3) / 1e12
-    trec, _ = loop_traffic_record()
-    roofline = {"bound": "alu", "kernel": "loops2_kernel (split-precision two-band loop k-sum)",
+    trec = loop_traffic_record()[0] if args.workload == "rashba" else None   # recorded for that workload
+    kname = ("loops2_kernel (split-precision two-band loop k-sum)" if spec.n_s == 2
+             else "loops_gen_kernel (split-precision multi-orbital loop k-sum)")
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
                 "traffic": (trec["dram_bytes_per_launch"] if trec else None),
                 "peak_source": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
@@ -379,19 +401,20 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "metric": metric, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "Lq": spec.Lq, "nc": spec.nc, "Nq": spec.Nq, "Nk": spec.Nk,
-                       "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH, "precision": "split (FP32 loop sums, FP64 state)",
+            "config": {"workload": workload, "Lq": spec.Lq, "nc": spec.nc, "Nq": spec.Nq, "Nk": spec.Nk,
+                       "n_s": spec.n_s, "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH,
+                       "precision": "split (FP32 loop sums, FP64 state)",
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "loop_momenta_summed": m32.n_loop_q,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},
             "split_vs_fp64_maxrel": err_split,
-            "fp64_gpu": {"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate,
-                         "note": "every transfer momentum summed directly"},
+            "fp64_gpu": ({"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate,
+                          "note": "every transfer momentum summed directly"} if fp64_rate else None),
             "split_every_q_summed": {"value": full_rate, "unit": "RHS/s",
-                                     "note": "split path with the time-reversal shortcut off (same loop work as fp64_gpu)"},
+                                     "note": "split path with the loop symmetries off (same loop work as fp64_gpu)"},
             "time_to_lambda_c": flows,
             "phase_ms_per_rhs": {k: v / args.steps for k, v in phase_ms.items()},
             "gpu_launches": launches,

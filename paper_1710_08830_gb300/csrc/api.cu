@@ -238,8 +238,8 @@ void build_entry_tables(const tufrg_model *m, std::vector<int> ofs[2], std::vect
 // Candidates: the eight point operations of the square lattice, each with the monomial unitaries
 // diag(1, i^n) and antidiag(1, i^n) (global phases drop out of V . V^dagger).
 struct LoopSymmetry {
-    std::vector<int> list, orb_ofs, dfwd;
-    std::vector<int2> orb;
+    std::vector<int> list, dinv;
+    std::vector<int2> qmap;
     std::vector<tufrg::SymElem> elem;
 };
 
@@ -358,31 +358,30 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
                 for (int a = 0; a < 4; a++)
                     if (std::abs(o.V[ch][a2][a]) > 0.5) {   // V[a'][a] = i^qt: source a feeds target a'
                         const cd v = o.V[ch][a2][a];
-                        e.pinv[ch][a] = a2;
+                        e.src[ch][a2] = a;
                         e.qt[ch][a2] = std::abs(v - 1.0) < 1e-9 ? 0 : std::abs(v - cd(0, 1)) < 1e-9 ? 1
                                      : std::abs(v + 1.0) < 1e-9 ? 2 : 3;
                     }
         ls.elem.push_back(e);
+        std::vector<int> inv(nd, 0);   // Delta_d' = G Delta_d  ->  inv[d'] = d
         for (int k = 0; k < nd; k++)
-            ls.dfwd.push_back(find_delta(o.Gd[0] * m->deltas[2 * k] + o.Gd[1] * m->deltas[2 * k + 1],
-                                         o.Gd[2] * m->deltas[2 * k] + o.Gd[3] * m->deltas[2 * k + 1]));
+            inv[find_delta(o.Gd[0] * m->deltas[2 * k] + o.Gd[1] * m->deltas[2 * k + 1],
+                           o.Gd[2] * m->deltas[2 * k] + o.Gd[3] * m->deltas[2 * k + 1])] = k;
+        ls.dinv.insert(ls.dinv.end(), inv.begin(), inv.end());
     }
     // orbits: the smallest momentum of each orbit is its representative
-    std::vector<char> done(m->Nq, 0);
-    ls.orb_ofs.push_back(0);
+    ls.qmap.assign(m->Nq, make_int2(-1, -1));
     for (int q = 0; q < m->Nq; q++) {
-        if (done[q]) continue;
+        if (ls.qmap[q].x >= 0) continue;
+        const int pos = (int)ls.list.size();
         ls.list.push_back(q);
         const int qx = q / L, qy = q % L;
         for (size_t e = 0; e < ops.size(); e++) {
             const int *G = ops[e].Gq;
             const int x = ((G[0] * qx + G[1] * qy) % L + L) % L, y = ((G[2] * qx + G[3] * qy) % L + L) % L;
             const int q2 = x * L + y;
-            if (done[q2]) continue;
-            done[q2] = 1;
-            ls.orb.push_back(make_int2(q2, (int)e));
+            if (ls.qmap[q2].x < 0) ls.qmap[q2] = make_int2(pos, (int)e);
         }
-        ls.orb_ofs.push_back((int)ls.orb.size());
     }
 }
 
@@ -408,7 +407,7 @@ void release(tufrg_model *m)
                     m->d_red, m->d_y, m->d_yt, m->d_yn, m->d_state_in, m->d_state_out, m->d_rec, m->d_Xr32,
                     m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
-                    m->d_loop_list, m->d_orb_ofs, m->d_orb, m->d_sym_elem, m->d_sym_dfwd, m->d_lph32,
+                    m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -682,10 +681,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             m->n_loop_q = (int)ls.list.size();
             m->n_sym_elem = (int)ls.elem.size();
             CK(upload(&m->d_loop_list, ls.list, m->stream), "upload symmetry tables");
-            CK(upload(&m->d_orb_ofs, ls.orb_ofs, m->stream), "upload symmetry tables");
-            CK(upload(&m->d_orb, ls.orb, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_qmap, ls.qmap, m->stream), "upload symmetry tables");
             CK(upload(&m->d_sym_elem, ls.elem, m->stream), "upload symmetry tables");
-            CK(upload(&m->d_sym_dfwd, ls.dfwd, m->stream), "upload symmetry tables");
+            CK(upload(&m->d_sym_dinv, ls.dinv, m->stream), "upload symmetry tables");
         }
     }
     m->plan = plan_loops(m);

@@ -16,6 +16,8 @@
 // memory into one partial per warp; a second kernel adds the partials in a fixed
 // order (deterministic) and writes both halves.  All eigen data stay in L2
 // (a few MB), so the kernel is bound by FMA throughput, not by HBM.
+#include <algorithm>
+
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -276,26 +278,27 @@ __device__ __forceinline__ typename cpx<R>::t reduce_one(const typename cpx<R>::
 __device__ __forceinline__ double2 to64(double2 v) { return v; }
 __device__ __forceinline__ double2 to64(float2 v) { return make_double2(widen_f(v.x), widen_f(v.y)); }
 
+// Grid: blockIdx.y = transfer momentum (list position), threads over (d, ab) = t (t >> 4, t & 15):
+// no runtime integer division (this GPU issues its conversions to the slow FP64 pipe).
 template <typename R>
 __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                    const int *dslot, const int *deltas, int nd, int Nq, double inv_nk,
-                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
+                                    const int *dslot, const int *deltas, int nd, double inv_nk, double2 *out64,
+                                    typename cpx<R>::t *out32, const int *skip)
 {
     if (skip && *skip) return;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t total = (size_t)Nq * nd * NS4;
-    if (idx >= total) return;
-    const int ab = idx % NS4;
-    const int d = (idx / NS4) % nd;
-    const int s = idx / ((size_t)NS4 * nd);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nd * NS4) return;
+    const int s = blockIdx.y, d = t / NS4, ab = t % NS4;
     const auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, s, d, ab, R(inv_nk));
+    const size_t idx = (size_t)s * nd * NS4 + t;
     if (out64) out64[idx] = to64(v);
     if (out32) out32[idx] = v;
 }
 
-// Symmetry variant (two bands): list position i holds the representative of an orbit; every member
-// (q', element e) of the orbit receives Lc(q')[d'][a'][b'] = i^k (conj ? conj(v) : v) with
-// d' = dfwd[e][d], a' = pinv[a], b' = pinv[b], k = qt[a'] - qt[b'] (see SymElem): sign flips and swaps.
+// Symmetry variant (two bands), gather form: blockIdx.y = output momentum q'; qmap[q'] = (list
+// position i of its orbit representative, group element e).  Thread (d', a'b') reads the representative's
+// partial sums of d = dinv[e][d'], a = src[a'], b = src[b'] (L2 resident) and writes
+// Lc(q')[d'][a'][b'] = i^(qt[a'] - qt[b']) (conj ? conj(v) : v) coalesced (see SymElem).
 template <typename C2>
 __device__ __forceinline__ C2 quarter_turn(C2 v, int k)
 {
@@ -309,29 +312,23 @@ __device__ __forceinline__ C2 quarter_turn(C2 v, int k)
 
 template <typename R>
 __global__ void loops_reduce_sym_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                        const int *dslot, const int *deltas, int nd, int n_list, const int *orb_ofs,
-                                        const int2 *orb, const SymElem *elem, const int *dfwd, int ch, double inv_nk,
-                                        double2 *out64, typename cpx<R>::t *out32, const int *skip)
+                                        const int *dslot, const int *deltas, int nd, const int2 *qmap,
+                                        const SymElem *elem, const int *dinv, int ch, double inv_nk, double2 *out64,
+                                        typename cpx<R>::t *out32, const int *skip)
 {
     if (skip && *skip) return;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t total = (size_t)n_list * nd * NS4;
-    if (idx >= total) return;
-    const int ab = idx % NS4;
-    const int d = (idx / NS4) % nd;
-    const int i = idx / ((size_t)NS4 * nd);
-    const auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, i, d, ab, R(inv_nk));
-    const auto vc = mk(v.x, -v.y);
-    const int a = ab / NS2, b = ab % NS2;
-    for (int t = orb_ofs[i]; t < orb_ofs[i + 1]; t++) {
-        const int2 mem = orb[t];
-        const SymElem &e = elem[mem.y];
-        const int a2 = e.pinv[ch][a], b2 = e.pinv[ch][b];
-        const auto w = quarter_turn(e.conj ? vc : v, e.qt[ch][a2] - e.qt[ch][b2]);
-        const size_t o = ((size_t)mem.x * nd + dfwd[(size_t)mem.y * nd + d]) * NS4 + a2 * NS2 + b2;
-        if (out64) out64[o] = to64(w);
-        if (out32) out32[o] = w;
-    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nd * NS4) return;
+    const int q2 = blockIdx.y, d2 = t / NS4, a2 = (t / NS2) % NS2, b2 = t % NS2;
+    const int2 ie = qmap[q2];
+    const SymElem &e = elem[ie.y];
+    const int d = dinv[ie.y * nd + d2], a = e.src[ch][a2], b = e.src[ch][b2];
+    auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, ie.x, d, a * NS2 + b, R(inv_nk));
+    if (e.conj) v.y = -v.y;
+    const auto w = quarter_turn(v, e.qt[ch][a2] - e.qt[ch][b2]);
+    const size_t o = (size_t)q2 * nd * NS4 + t;
+    if (out64) out64[o] = to64(w);
+    if (out32) out32[o] = w;
 }
 
 template <typename R, int NDYH, int NAB, int WHICH>
@@ -372,16 +369,26 @@ LoopPlan plan_loops(const tufrg_model *m)
     return p;
 }
 
+// launch shape of the reductions: one row of CTAs per momentum, threads over (d, ab)
+static void reduce_shape(const tufrg_model *m, int n_s, dim3 &grid, int &thr)
+{
+    const int per = m->nd * NS4;
+    thr = std::min(1024, (per + 31) / 32 * 32);
+    grid = dim3((per + thr - 1) / thr, n_s);
+}
+
 cudaError_t launch_loops_reduce_f32(tufrg_model *m, const float2 *part, int n_s, double2 *out64, float2 *out32,
                                     const int *skip)
 {
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
-    const size_t total = (size_t)n_s * m->nd * NS4;
+    dim3 grid;
+    int thr;
+    reduce_shape(m, n_s, grid, thr);
     PhaseScope ps(m, PH_LOOPRED);
-    loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
-        part, m->plan.n_partials, (int)m->dxs.size(), ndyh, m->d_dslot, m->d_deltas, m->nd, n_s, 1.0 / (double)m->Nk,
-        out64, out32, skip);
+    loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(part, m->plan.n_partials, (int)m->dxs.size(), ndyh,
+                                                          m->d_dslot, m->d_deltas, m->nd, 1.0 / (double)m->Nk, out64,
+                                                          out32, skip);
     return cudaGetLastError();
 }
 
@@ -400,18 +407,20 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
         const double inv_nk = 1.0 / (double)m->Nk;
         if (loops2_supported(m)) {
             TUFRG_CUDA_TRY(launch_loops2(m, ch));
-            const size_t total = (size_t)m->n_loop_q * m->nd * NS4;
             const size_t off = (size_t)ch * m->Nq * m->nd * NS4;
+            dim3 grid;
+            int thr;
+            reduce_shape(m, m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
             if (m->sym)
-                loops_reduce_sym_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+                loops_reduce_sym_kernel<float><<<grid, thr, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    m->n_loop_q, m->d_orb_ofs, m->d_orb, m->d_sym_elem, m->d_sym_dfwd, ch, inv_nk, m->d_Lc + off,
-                    m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
+                    m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, inv_nk, m->d_Lc + off, m->d_Lc32 + off,
+                    m->sur ? m->d_sur_flag : nullptr);
             else
-                loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
+                loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    m->Nq, inv_nk, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
+                    inv_nk, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};
@@ -434,10 +443,12 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             if (ndyh <= 3) e = ch == 0 ? launch_one<double, 3, 8, 0>(m, a, 2) : launch_one<double, 3, 8, 1>(m, a, 2);
             else           e = ch == 0 ? launch_one<double, 5, 4, 0>(m, a, 4) : launch_one<double, 5, 4, 1>(m, a, 4);
             TUFRG_CUDA_TRY(e);
-            const size_t total = (size_t)m->Nq * m->nd * NS4;
+            dim3 grid;
+            int thr;
+            reduce_shape(m, m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
-            loops_reduce_kernel<double><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
-                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq, inv_nk,
+            loops_reduce_kernel<double><<<grid, thr, 0, m->stream>>>(
+                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk,
                 m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else {
@@ -461,10 +472,12 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             if (ndyh <= 3) e = ch == 0 ? launch_one<float, 3, 16, 0>(m, a, 1) : launch_one<float, 3, 16, 1>(m, a, 1);
             else           e = ch == 0 ? launch_one<float, 5, 8, 0>(m, a, 2) : launch_one<float, 5, 8, 1>(m, a, 2);
             TUFRG_CUDA_TRY(e);
-            const size_t total = (size_t)m->Nq * m->nd * NS4;
+            dim3 grid;
+            int thr;
+            reduce_shape(m, m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
-            loops_reduce_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, m->stream>>>(
-                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->Nq, inv_nk,
+            loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
+                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk,
                 m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         }

@@ -101,10 +101,20 @@ __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t
     const C2 *a = A + ((size_t)ch * Nq + q) * M2;
     const C2 *lc = Lc + ((size_t)ch * Nq + q) * nd * 16;
     // A^T and the expanded loop matrix L[(R1,a),(R2,b)] = Lc[d(R1 - R2)][a][b] (coalesced reads)
-    for (int i = threadIdx.x; i < M2; i += blockDim.x) {
-        const int r = i / M, c = i - r * M;
-        s0[c * M + r] = a[i];
-        s1[i] = lc[(dij[(r >> 2) * nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3)];
+    {
+        // (r, c) of i advanced incrementally (runtime integer division runs on this GPU's slow pipe)
+        const int dr = blockDim.x / M, dc = blockDim.x - dr * M;
+        int r = threadIdx.x / M, c = threadIdx.x - r * M;
+        for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+            s0[c * M + r] = a[i];
+            s1[i] = lc[(dij[(r >> 2) * nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3)];
+            r += dr;
+            c += dc;
+            if (c >= M) {
+                c -= M;
+                r++;
+            }
+        }
     }
     __syncthreads();
     const int t = threadIdx.x;

@@ -48,20 +48,21 @@ struct FlowDev {
 };
 
 // One element of the loop symmetry group (two bands): Lc(q')[d'][a'][b'] =
-// i^(qt[ch][a'] - qt[ch][b']) * (conj ? conj(L) : L) with L = Lc(q)[d][a][b], a' = pinv[ch][a],
-// b' = pinv[ch][b], q' = G_q q and d' = index of G Delta_d (every phase is a power of i).
+// i^(qt[ch][a'] - qt[ch][b']) * (conj ? conj(L) : L) with L = Lc(q)[d][src[ch][a']][src[ch][b']],
+// q' = G_q q, Delta_d' = G Delta_d (every phase is a power of i).
 struct SymElem {
     int conj;
-    int pinv[2][4];
+    int src[2][4];
     int qt[2][4];
 };
 
 // bits of the exact double of a float, formed on the integer pipe (this GPU's FP64 pipe is slow);
-// zero, subnormal, inf and nan take the plain conversion
+// subnormal, inf and nan take the plain conversion
 __device__ __forceinline__ double widen_f(float f)
 {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // signed zero
     if (e == 0u || e == 0xffu) return (double)f;
     return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
 }
@@ -122,10 +123,9 @@ struct tufrg_model {
     int n_loop_q = 0;               // transfer momenta summed directly (Nq without symmetry)
     int n_sym_elem = 0;             // group elements (identity included)
     int *d_loop_list = nullptr;     // [n_loop_q] orbit representatives
-    int *d_orb_ofs = nullptr;       // [n_loop_q + 1] CSR offsets into d_orb
-    int2 *d_orb = nullptr;          // (member momentum, group element) of every orbit, representative first
+    int2 *d_qmap = nullptr;         // [Nq] (list position of the orbit representative, group element)
     tufrg::SymElem *d_sym_elem = nullptr;   // [n_sym_elem]
-    int *d_sym_dfwd = nullptr;      // [n_sym_elem][nd] index of G Delta_d
+    int *d_sym_dinv = nullptr;      // [n_sym_elem][nd] source d of target d' (Delta_d' = G Delta_d)
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
