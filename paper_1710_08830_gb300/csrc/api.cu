@@ -229,29 +229,39 @@ void build_entry_tables(const tufrg_model *m, std::vector<int> ofs[2], std::vect
     }
 }
 
-// ---- loop symmetries (two bands)
+// ---- loop symmetries
 // A unitary symmetry (G, U) of the hoppings, t_{G R} = U t_R U^dagger, maps the band projectors as
 // P_l(G k) = U P_l(k) U^dagger and the loops as Lc(G q)[G Delta] = V Lc(q)[Delta] V^dagger with
 // V = U (x) U on the P pair index (t2, t1) and V = U (x) U^* on the C pair index (t1, t2).  Time
-// reversal, t_R = W t_R^* W^T with W = i sigma_y, gives Lc(-q)[Delta] = V conj(Lc(q)[Delta]) V^dagger
-// with V = W (x) W (P) and W (x) W^* (C); composed with (G, U) it maps q -> -G q, Delta -> G Delta.
-// Candidates: the eight point operations of the square lattice, each with the monomial unitaries
-// diag(1, i^n) and antidiag(1, i^n) (global phases drop out of V . V^dagger).
+// reversal, t_R = W t_R^* W^T, gives Lc(-q)[Delta] = V conj(Lc(q)[Delta]) V^dagger with V = W (x) W (P)
+// and W (x) W^* (C); composed with (G, U) it maps q -> -G q, Delta -> G Delta.
+// States are orbital (x) spin-1/2, index 2 * orbital + spin.  Candidates: the eight point operations of
+// the square lattice, each with U = (signed permutation of the orbitals) (x) (diag(1, i^n) or
+// antidiag(1, i^n) on the spin), and W = 1 (x) i sigma_y.  Every U, W and hence every V is monomial
+// (one entry of modulus one per row), which is how they are stored: row i has its entry in column
+// perm[i] with value ph[i] (global phases drop out of V . V^dagger).
 struct LoopSymmetry {
     std::vector<int> list, dinv;
     std::vector<int2> qmap;
     std::vector<tufrg::SymElem> elem;
 };
 
+struct Mono {
+    std::vector<int> perm;
+    std::vector<std::complex<double>> ph;
+};
+
 void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
 {
     using cd = std::complex<double>;
-    typedef std::array<std::array<cd, 2>, 2> M2c;
-    typedef std::array<std::array<cd, 4>, 4> M4c;
     const int Gs[8][4] = {{1, 0, 0, 1}, {0, -1, 1, 0}, {-1, 0, 0, -1}, {0, 1, -1, 0},
                           {-1, 0, 0, 1}, {1, 0, 0, -1}, {0, 1, 1, 0}, {0, -1, -1, 0}};
-    const int L = m->Lq, nd = m->nd;
-    auto hop = [&](int h, int i, int j) { return cd(m->hopt[2 * ((size_t)h * 4 + i * 2 + j)], m->hopt[2 * ((size_t)h * 4 + i * 2 + j) + 1]); };
+    const int L = m->Lq, nd = m->nd, ns = m->ns, ns2 = ns * ns, norb = ns / 2;
+    if (ns % 2 != 0 || ns2 > tufrg::SYM_MAXNS2) return;
+    auto hop = [&](int h, int i, int j) {
+        const size_t o = 2 * ((size_t)h * ns2 + (size_t)i * ns + j);
+        return cd(m->hopt[o], m->hopt[o + 1]);
+    };
     auto find_hop = [&](int x, int y) {
         for (int h = 0; h < m->nhop; h++)
             if (m->hopR[2 * h] == x && m->hopR[2 * h + 1] == y) return h;
@@ -264,109 +274,139 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
     };
     double tmax = 0.0;
     for (int h = 0; h < m->nhop; h++)
-        for (int i = 0; i < 2; i++)
-            for (int j = 0; j < 2; j++) tmax = std::max(tmax, std::abs(hop(h, i, j)));
+        for (int i = 0; i < ns; i++)
+            for (int j = 0; j < ns; j++) tmax = std::max(tmax, std::abs(hop(h, i, j)));
     const double tol = 1e-12 * std::max(1.0, tmax);
-    // V on the orbital pair index of each channel
-    auto pairV = [&](const M2c &U, int ch) {
-        M4c V{};
-        for (int t1 = 0; t1 < 2; t1++)
-            for (int t2 = 0; t2 < 2; t2++)
-                for (int c1 = 0; c1 < 2; c1++)
-                    for (int c2 = 0; c2 < 2; c2++) {
-                        if (ch == 0) V[t2 * 2 + t1][c2 * 2 + c1] = U[t2][c2] * U[t1][c1];
-                        else V[t1 * 2 + t2][c1 * 2 + c2] = U[t1][c1] * std::conj(U[t2][c2]);
-                    }
-        return V;
+    // (U t U^dagger)_{ij} = ph_i t_{perm i, perm j} conj(ph_j) for a monomial U
+    auto conj_ok = [&](const Mono &U, int h_from, int h_to, bool antiunitary) {
+        for (int i = 0; i < ns; i++)
+            for (int j = 0; j < ns; j++) {
+                cd t = hop(h_from, U.perm[i], U.perm[j]);
+                if (antiunitary) t = std::conj(t);
+                if (std::abs(U.ph[i] * t * std::conj(U.ph[j]) - hop(h_to, i, j)) > tol) return false;
+            }
+        return true;
     };
-    struct Op { int Gq[4], Gd[4]; M4c V[2]; int conj; };
+    // orbital signed permutations (x) spin monomials
+    std::vector<Mono> cands;
+    {
+        std::vector<int> p(norb);
+        for (int i = 0; i < norb; i++) p[i] = i;
+        do {
+            for (int sg = 0; sg < (1 << norb); sg++)
+                for (int c = 0; c < 8; c++) {
+                    const cd sp = std::pow(cd(0.0, 1.0), c / 2);
+                    Mono U;
+                    U.perm.resize(ns);
+                    U.ph.resize(ns);
+                    for (int o = 0; o < norb; o++)
+                        for (int s = 0; s < 2; s++) {
+                            const int row = 2 * o + s;
+                            const int scol = c % 2 == 0 ? s : 1 - s;   // diag(1, i^n) or antidiag(1, i^n)
+                            const cd sph = s == 0 ? cd(1.0) : sp;
+                            U.perm[row] = 2 * p[o] + scol;
+                            U.ph[row] = ((sg >> o) & 1 ? -1.0 : 1.0) * sph;
+                        }
+                    cands.push_back(U);
+                }
+        } while (std::next_permutation(p.begin(), p.end()));
+    }
+    struct Op { int Gq[4], Gd[4]; Mono U; int conj; };
     std::vector<Op> ops;
-    // unitary operations
     for (const int *G : Gs) {
         bool deltas_ok = true;
         for (int k = 0; k < nd && deltas_ok; k++)
             deltas_ok = find_delta(G[0] * m->deltas[2 * k] + G[1] * m->deltas[2 * k + 1],
                                    G[2] * m->deltas[2 * k] + G[3] * m->deltas[2 * k + 1]) >= 0;
         if (!deltas_ok) continue;
-        for (int c = 0; c < 8; c++) {
-            const cd p = std::pow(cd(0.0, 1.0), c / 2);
-            M2c U{};
-            if (c % 2 == 0) { U[0][0] = 1.0; U[1][1] = p; } else { U[0][1] = 1.0; U[1][0] = p; }
+        std::vector<int> img(m->nhop, -1);
+        bool hops_ok = true;
+        for (int h = 0; h < m->nhop && hops_ok; h++) {
+            img[h] = find_hop(G[0] * m->hopR[2 * h] + G[1] * m->hopR[2 * h + 1], G[2] * m->hopR[2 * h] + G[3] * m->hopR[2 * h + 1]);
+            hops_ok = img[h] >= 0;
+        }
+        if (!hops_ok) continue;
+        for (const Mono &U : cands) {
             bool ok = true;
-            for (int h = 0; h < m->nhop && ok; h++) {
-                const int g = find_hop(G[0] * m->hopR[2 * h] + G[1] * m->hopR[2 * h + 1],
-                                       G[2] * m->hopR[2 * h] + G[3] * m->hopR[2 * h + 1]);
-                if (g < 0) { ok = false; break; }
-                for (int i = 0; i < 2 && ok; i++)
-                    for (int j = 0; j < 2 && ok; j++) {
-                        cd v = 0.0;   // (U t U^dagger)_{ij}
-                        for (int a = 0; a < 2; a++)
-                            for (int b = 0; b < 2; b++) v += U[i][a] * hop(h, a, b) * std::conj(U[j][b]);
-                        ok = std::abs(v - hop(g, i, j)) <= tol;
-                    }
-            }
+            for (int h = 0; h < m->nhop && ok; h++) ok = conj_ok(U, h, img[h], false);   // t_{GR} = U t_R U^dagger
             if (!ok) continue;
             Op o{};
             std::copy(G, G + 4, o.Gq);
             std::copy(G, G + 4, o.Gd);
-            o.V[0] = pairV(U, 0);
-            o.V[1] = pairV(U, 1);
+            o.U = U;
             o.conj = 0;
             ops.push_back(o);
             break;
         }
     }
-    // time reversal and its compositions with the unitary operations
+    // time reversal W = 1 (x) i sigma_y: rows (2o, 2o+1) -> columns (2o+1, 2o) with values (1, -1)
+    Mono W;
+    W.perm.resize(ns);
+    W.ph.resize(ns);
+    for (int o = 0; o < norb; o++) {
+        W.perm[2 * o] = 2 * o + 1; W.ph[2 * o] = 1.0;
+        W.perm[2 * o + 1] = 2 * o; W.ph[2 * o + 1] = -1.0;
+    }
     bool trs = true;
-    {
-        const int W[2][2] = {{0, 1}, {-1, 0}};
-        for (int h = 0; h < m->nhop && trs; h++)
-            for (int i = 0; i < 2 && trs; i++)
-                for (int j = 0; j < 2 && trs; j++) {
-                    cd v = 0.0;   // (W t^* W^T)_{ij}
-                    for (int a = 0; a < 2; a++)
-                        for (int b = 0; b < 2; b++) v += (double)(W[i][a] * W[j][b]) * std::conj(hop(h, a, b));
-                    trs = std::abs(v - hop(h, i, j)) <= tol;
-                }
+    for (int h = 0; h < m->nhop && trs; h++) trs = conj_ok(W, h, h, true);   // t_R = W t_R^* W^T
+    // pair-index representation of V for a monomial U (P: a = t2 ns + t1 with U (x) U; C: a = t1 ns + t2 with U (x) U^*)
+    auto pairV = [&](const Mono &U, int ch) {
+        Mono V;
+        V.perm.resize(ns2);
+        V.ph.resize(ns2);
+        for (int a = 0; a < ns2; a++) {
+            const int x = a / ns, y = a % ns;
+            V.perm[a] = U.perm[x] * ns + U.perm[y];
+            V.ph[a] = ch == 0 ? U.ph[x] * U.ph[y] : U.ph[x] * std::conj(U.ph[y]);
+        }
+        return V;
+    };
+    struct Elem { int Gq[4], Gd[4]; Mono V[2]; int conj; };
+    std::vector<Elem> elems;
+    for (const Op &o : ops) {
+        Elem e{};
+        std::copy(o.Gq, o.Gq + 4, e.Gq);
+        std::copy(o.Gd, o.Gd + 4, e.Gd);
+        e.V[0] = pairV(o.U, 0);
+        e.V[1] = pairV(o.U, 1);
+        e.conj = 0;
+        elems.push_back(e);
     }
     if (trs) {
-        M2c Wm{};
-        Wm[0][1] = 1.0;
-        Wm[1][0] = -1.0;
-        const M4c VT[2] = {pairV(Wm, 0), pairV(Wm, 1)};
-        const size_t nu = ops.size();
+        const Mono VT[2] = {pairV(W, 0), pairV(W, 1)};
+        const size_t nu = elems.size();
         for (size_t i = 0; i < nu; i++) {
-            Op o{};
-            for (int k = 0; k < 4; k++) { o.Gq[k] = -ops[i].Gq[k]; o.Gd[k] = ops[i].Gd[k]; }
-            for (int ch = 0; ch < 2; ch++)   // V_T conj(V_g)
-                for (int a = 0; a < 4; a++)
-                    for (int b = 0; b < 4; b++) {
-                        cd v = 0.0;
-                        for (int c = 0; c < 4; c++) v += VT[ch][a][c] * std::conj(ops[i].V[ch][c][b]);
-                        o.V[ch][a][b] = v;
-                    }
-            o.conj = 1;
-            ops.push_back(o);
+            Elem e{};
+            for (int k = 0; k < 4; k++) { e.Gq[k] = -elems[i].Gq[k]; e.Gd[k] = elems[i].Gd[k]; }
+            for (int ch = 0; ch < 2; ch++) {   // V_T conj(V_g): row a -> perm_g(perm_T(a)), ph_T(a) conj(ph_g(perm_T(a)))
+                e.V[ch].perm.resize(ns2);
+                e.V[ch].ph.resize(ns2);
+                for (int a = 0; a < ns2; a++) {
+                    const int b = VT[ch].perm[a];
+                    e.V[ch].perm[a] = elems[i].V[ch].perm[b];
+                    e.V[ch].ph[a] = VT[ch].ph[a] * std::conj(elems[i].V[ch].ph[b]);
+                }
+            }
+            e.conj = 1;
+            elems.push_back(e);
         }
     }
-    // group elements as permutation + phase tables (every V here is monomial)
-    for (const Op &o : ops) {
+    // device tables: target a' reads source perm[a'] with phase i^qt[a']
+    for (const Elem &el : elems) {
         tufrg::SymElem e{};
-        e.conj = o.conj;
+        e.conj = el.conj;
         for (int ch = 0; ch < 2; ch++)
-            for (int a2 = 0; a2 < 4; a2++)
-                for (int a = 0; a < 4; a++)
-                    if (std::abs(o.V[ch][a2][a]) > 0.5) {   // V[a'][a] = i^qt: source a feeds target a'
-                        const cd v = o.V[ch][a2][a];
-                        e.src[ch][a2] = a;
-                        e.qt[ch][a2] = std::abs(v - 1.0) < 1e-9 ? 0 : std::abs(v - cd(0, 1)) < 1e-9 ? 1
-                                     : std::abs(v + 1.0) < 1e-9 ? 2 : 3;
-                    }
+            for (int a2 = 0; a2 < ns2; a2++) {
+                const cd v = el.V[ch].ph[a2];
+                e.src[ch][a2] = el.V[ch].perm[a2];
+                e.qt[ch][a2] = std::abs(v - 1.0) < 1e-9 ? 0 : std::abs(v - cd(0, 1)) < 1e-9 ? 1
+                             : std::abs(v + 1.0) < 1e-9 ? 2 : 3;
+            }
         ls.elem.push_back(e);
         std::vector<int> inv(nd, 0);   // Delta_d' = G Delta_d  ->  inv[d'] = d
         for (int k = 0; k < nd; k++)
-            inv[find_delta(o.Gd[0] * m->deltas[2 * k] + o.Gd[1] * m->deltas[2 * k + 1],
-                           o.Gd[2] * m->deltas[2 * k] + o.Gd[3] * m->deltas[2 * k + 1])] = k;
+            inv[find_delta(el.Gd[0] * m->deltas[2 * k] + el.Gd[1] * m->deltas[2 * k + 1],
+                           el.Gd[2] * m->deltas[2 * k] + el.Gd[3] * m->deltas[2 * k + 1])] = k;
         ls.dinv.insert(ls.dinv.end(), inv.begin(), inv.end());
     }
     // orbits: the smallest momentum of each orbit is its representative
@@ -376,8 +416,8 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
         const int pos = (int)ls.list.size();
         ls.list.push_back(q);
         const int qx = q / L, qy = q % L;
-        for (size_t e = 0; e < ops.size(); e++) {
-            const int *G = ops[e].Gq;
+        for (size_t e = 0; e < elems.size(); e++) {
+            const int *G = elems[e].Gq;
             const int x = ((G[0] * qx + G[1] * qy) % L + L) % L, y = ((G[2] * qx + G[3] * qy) % L + L) % L;
             const int q2 = x * L + y;
             if (ls.qmap[q2].x < 0) ls.qmap[q2] = make_int2(pos, (int)e);
@@ -673,7 +713,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     build_gather_tables(m);
     // loop symmetries (TUFRG_SYMMETRY_AUTO, split two-band path)
     m->n_loop_q = m->Nq;
-    if (d.symmetry == TUFRG_SYMMETRY_AUTO && ns == 2 && loops2_supported(m)) {
+    if (d.symmetry == TUFRG_SYMMETRY_AUTO && ((ns == 2 && loops2_supported(m)) || (ns != 2 && loops_gen_supported(m)))) {
         LoopSymmetry ls;
         build_loop_symmetry(m, ls);
         if ((int)ls.list.size() < m->Nq) {
@@ -775,7 +815,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     m->part_bytes = (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
     if (ns != 2) {
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
-        m->part_bytes = (size_t)m->Nq * m->nd * ns4 * sizeof(double2);   // FP64 accumulators of one channel
+        m->gen_chunks = plan_gen_chunks(m);
+        // FP64 accumulators of one channel: one slot per (kx range, directly summed momentum)
+        m->part_bytes = (size_t)m->gen_chunks * m->n_loop_q * m->nd * ns4 * sizeof(double2);
     }
     m->products = split ? (d.products == TUFRG_PRODUCTS_AUTO ? TUFRG_PRODUCTS_TC : d.products) : TUFRG_PRODUCTS_SIMT;
     if (m->M > 64 || split)

@@ -31,12 +31,16 @@ template <typename R>
 struct GenArgs {
     const typename cpx<R>::t *U;        // [Nk][NS][NS]
     const typename FTg<R>::t *ft;       // [Nk][NS]
-    double2 *acc;                       // [Nq][nd][NS^4] FP64 accumulators (zeroed), half plane filled
+    typename cpx<R>::t *acc;            // [kx range][slot][nd][NS^4] accumulators (zeroed), half plane filled;
+                                        // FP64 on the plain path, FP32 on the split path
     int Lq, nc, Lf, nd, ndx, ndyh;
     int dxs[GMAXD], dys[GMAXD];
     int dslot[GMAXD][GMAXD];            // [dxi][dyi] -> delta index (half plane), or -1
     R thr_factor;                       // degenerate-pair switch = thr_factor * T
     const double *Tp;                   // device temperature
+    const int *s_list;                  // optional: CTA x sums transfer momentum s_list[x] into accumulator slot x
+    int n_slot;                         // momenta per kx range (accumulator slots of one range)
+    int kx_len;                         // columns per kx range; CTA y covers [y kx_len, (y + 1) kx_len)
 };
 
 template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
@@ -81,14 +85,15 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
         sincospi(2.0 * (double)n / (double)Lf, &sn, &cs);
         ptab[n] = mk(R(cs), R(-sn));
     }
-    const int s = blockIdx.x;
+    const int s = a.s_list ? a.s_list[blockIdx.x] : blockIdx.x;
     const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
     const int ta = threadIdx.x / GB, tb = threadIdx.x % GB;
     const R thr = a.thr_factor * (R)(*a.Tp);
     const bool active = threadIdx.x < NT;
-    double2 *acc = a.acc + (size_t)s * a.nd * NS2 * NS2;
+    C2 *acc = a.acc + ((size_t)blockIdx.y * a.n_slot + blockIdx.x) * a.nd * NS2 * NS2;
+    const int kx_end = min(Lf, (int)(blockIdx.y + 1) * a.kx_len);
 
-    for (int kx = 0; kx < Lf; kx++) {
+    for (int kx = blockIdx.y * a.kx_len; kx < kx_end; kx++) {
         C2 W[NDYH][TA][TB];
 #pragma unroll
         for (int d = 0; d < NDYH; d++)
@@ -169,7 +174,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
                 }
             }
         }
-        // add e^{-i kx dx} W into this thread's FP64 accumulators (fixed order, no other writer)
+        // add e^{-i kx dx} W into this thread's accumulators (fixed order, no other writer)
         if (active) {
             for (int xi = 0; xi < a.ndx; xi++) {
                 const C2 phx = ptab[((kx * a.dxs[xi]) % Lf + Lf) % Lf];
@@ -188,9 +193,9 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
                             const int ra = WHICH == 0 ? t2 * NS + t1 : t1 * NS + t2;
                             const int cb = WHICH == 0 ? t4 * NS + t3 : t3 * NS + t4;
                             const C2 v = W[d][i][j];
-                            double2 &o = acc[((size_t)di * NS2 + ra) * NS2 + cb];
-                            o.x += (double)phx.x * (double)v.x - (double)phx.y * (double)v.y;
-                            o.y += (double)phx.x * (double)v.y + (double)phx.y * (double)v.x;
+                            C2 &o = acc[((size_t)di * NS2 + ra) * NS2 + cb];
+                            o.x += phx.x * v.x - phx.y * v.y;
+                            o.y += phx.x * v.y + phx.y * v.x;
                         }
                 }
             }
@@ -198,29 +203,72 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     }
 }
 
-// Mirror the half plane, L(-d)[b][a] = conj(L(d)[a][b]), and scale by 1/Nk.
-__global__ void loops_gen_finish(const double2 *acc, const int *deltas, int nd, int ns2, int Nq, double inv_nk,
-                                 const int *partner, double2 *out64, float2 *out32)
+// Mirror the half plane, L(-d)[b][a] = conj(L(d)[a][b]), sum the kx ranges (fixed order) and scale by
+// 1/Nk.  Grid: blockIdx.y = momentum, threads over (d, a, b).
+template <int NS, typename C2>
+__device__ __forceinline__ double2 gen_value(const C2 *acc, size_t chunk_stride, int nchunk, size_t base, int d,
+                                             int ia, int ib, const int *deltas, const int *partner)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t per = (size_t)nd * ns2 * ns2;
-    if (idx >= (size_t)Nq * per) return;
-    const int s = (int)(idx / per);
-    const int r = (int)(idx % per);
-    const int d = r / (ns2 * ns2), ab = r % (ns2 * ns2), ia = ab / ns2, ib = ab % ns2;
+    constexpr int NS2 = NS * NS;
     const int dx = deltas[2 * d], dy = deltas[2 * d + 1];
     const bool half = dy > 0 || (dy == 0 && dx >= 0);
-    double2 v;
-    if (half) {
-        v = acc[idx];
-    } else {
-        const double2 w = acc[(size_t)s * per + ((size_t)partner[d] * ns2 + ib) * ns2 + ia];
-        v = make_double2(w.x, -w.y);
+    const size_t o = half ? base + ((size_t)d * NS2 + ia) * NS2 + ib : base + ((size_t)partner[d] * NS2 + ib) * NS2 + ia;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; c++) {
+        const C2 w = acc[(size_t)c * chunk_stride + o];
+        re += (double)w.x;
+        im += (double)w.y;
     }
+    return make_double2(re, half ? im : -im);
+}
+
+template <int NS, typename C2>
+__global__ void loops_gen_finish(const C2 *acc, int nchunk, const int *deltas, int nd, int Nq, double inv_nk,
+                                 const int *partner, double2 *out64, float2 *out32)
+{
+    constexpr int NS2 = NS * NS, NS4 = NS2 * NS2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nd * NS4) return;
+    const int s = blockIdx.y, d = t / NS4, ia = (t / NS2) % NS2, ib = t % NS2;
+    const size_t per = (size_t)nd * NS4;
+    double2 v = gen_value<NS>(acc, (size_t)Nq * per, nchunk, (size_t)s * per, d, ia, ib, deltas, partner);   // C2 deduced
     v.x *= inv_nk;
     v.y *= inv_nk;
-    out64[idx] = v;
-    if (out32) out32[idx] = make_float2((float)v.x, (float)v.y);
+    const size_t o = (size_t)s * per + t;
+    out64[o] = v;
+    if (out32) out32[o] = make_float2((float)v.x, (float)v.y);
+}
+
+// Symmetric variant: blockIdx.y = output momentum q'; qmap[q'] = (accumulator slot of its orbit
+// representative, group element e); thread (d', a', b') reads the representative's (d, src a', src b')
+// (half plane or its Hermitian mirror) and writes i^(qt[a'] - qt[b']) (conj ? conj(v) : v) / Nk.
+template <int NS, typename C2>
+__global__ void loops_gen_finish_sym(const C2 *acc, int nchunk, int n_slot, const int *deltas, int nd,
+                                     double inv_nk, const int *partner, const int2 *qmap, const SymElem *elem,
+                                     const int *dinv, int ch, double2 *out64, float2 *out32)
+{
+    constexpr int NS2 = NS * NS, NS4 = NS2 * NS2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nd * NS4) return;
+    const int q2 = blockIdx.y, d2 = t / NS4, a2 = (t / NS2) % NS2, b2 = t % NS2;
+    const int2 ie = qmap[q2];
+    const SymElem &e = elem[ie.y];
+    const size_t per = (size_t)nd * NS4;
+    double2 v = gen_value<NS>(acc, (size_t)n_slot * per, nchunk, (size_t)ie.x * per, dinv[ie.y * nd + d2],
+                              e.src[ch][a2], e.src[ch][b2], deltas, partner);
+    if (e.conj) v.y = -v.y;
+    double2 w;
+    switch ((e.qt[ch][a2] - e.qt[ch][b2]) & 3) {
+    case 0: w = v; break;
+    case 1: w = make_double2(-v.y, v.x); break;
+    case 2: w = make_double2(-v.x, -v.y); break;
+    default: w = make_double2(v.y, -v.x); break;
+    }
+    w.x *= inv_nk;
+    w.y *= inv_nk;
+    const size_t o = (size_t)q2 * per + t;
+    out64[o] = w;
+    if (out32) out32[o] = make_float2((float)w.x, (float)w.y);
 }
 
 template <typename R, int NS, int TA, int TB, int NDYH, int WHICH>
@@ -234,7 +282,7 @@ cudaError_t launch_gen(tufrg_model *m, const GenArgs<R> &a)
     auto kern = loops_gen_kernel<R, NS, TA, TB, NDYH, WHICH>;
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PhaseScope ps(m, PH_LOOPS);
-    kern<<<m->Nq, threads, smem, m->stream>>>(a);
+    kern<<<dim3(a.n_slot, m->gen_chunks), threads, smem, m->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -277,30 +325,105 @@ bool loops_gen_supported(const tufrg_model *m)
     return (m->ns == 4 || m->ns == 6) && (int)m->dxs.size() <= GMAXD && ndyh <= 5 && m->nd <= GMAXND;
 }
 
+namespace {
+
+// Resident CTAs per SM of the instantiation the model launches, and the kx ranges per momentum that
+// fill the GPU (at least one wave, at least 4 columns per range).
+template <typename R, int NS, int TA, int TB>
+int gen_blocks_per_sm(const tufrg_model *m, int ndyh)
+{
+    using C2 = typename cpx<R>::t;
+    constexpr int NS2 = NS * NS, NT = (NS2 / TA) * (NS2 / TB);
+    const int threads = ((NT + 31) / 32) * 32;
+    const size_t smem = sizeof(C2) * (m->Lf + 3 * KB * NS * NS2) + sizeof(R) * KB * NS * NS;
+    int n = 0;
+    cudaError_t e = ndyh <= 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 3, 0>, threads, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 5, 0>, threads, smem);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+}  // namespace
+
+int plan_gen_chunks(const tufrg_model *m)
+{
+    int ndyh = 0;
+    for (int v : m->dys) ndyh += v >= 0;
+    int per_sm;
+    if (m->precision == TUFRG_FP64) per_sm = m->ns == 6 ? gen_blocks_per_sm<double, 6, 2, 3>(m, ndyh) : gen_blocks_per_sm<double, 4, 2, 2>(m, ndyh);
+    else per_sm = m->ns == 6 ? gen_blocks_per_sm<float, 6, 4, 3>(m, ndyh) : gen_blocks_per_sm<float, 4, 2, 2>(m, ndyh);
+    const long slots = (long)m->sm_count * per_sm;
+    int c = (int)((slots + m->n_loop_q - 1) / m->n_loop_q);
+    c = std::max(1, std::min(c, std::min(16, m->Lf / 4)));
+    return c;
+}
+
+namespace {
+
+template <typename R>
+void fill_chunks(const tufrg_model *m, GenArgs<R> &a)
+{
+    a.s_list = m->sym ? m->d_loop_list : nullptr;
+    a.n_slot = m->sym ? m->n_loop_q : m->Nq;
+    a.kx_len = (m->Lf + m->gen_chunks - 1) / m->gen_chunks;
+}
+
+}  // namespace
+
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask)
 {
     const size_t ns2 = (size_t)m->ns * m->ns, per = (size_t)m->Nq * m->nd * ns2 * ns2;
+    const int n_slot = m->sym ? m->n_loop_q : m->Nq;
+    const size_t acc_n = (size_t)m->gen_chunks * n_slot * m->nd * ns2 * ns2;
     for (int ch = 0; ch < 2; ch++) {
-        if (!((channel_mask >> ch) & 1)) continue;
-        double2 *acc = reinterpret_cast<double2 *>(m->d_part);
-        TUFRG_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double2) * per, m->stream));
+        if (!((channel_mask >> ch) & 1)) continue;        const bool fp64 = m->precision == TUFRG_FP64;
+        TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_part, 0, (fp64 ? sizeof(double2) : sizeof(float2)) * acc_n, m->stream));
         cudaError_t e;
-        if (m->precision == TUFRG_FP64) {
+        if (fp64) {
             GenArgs<double> a{};
-            a.U = m->d_U; a.ft = m->d_ft; a.acc = acc; a.thr_factor = 1e-5; a.Tp = m->d_scal;
+            a.U = m->d_U; a.ft = m->d_ft; a.acc = reinterpret_cast<double2 *>(m->d_part); a.thr_factor = 1e-5; a.Tp = m->d_scal;
             fill_args(m, a);
+            fill_chunks(m, a);
             e = m->ns == 6 ? dispatch_gen<double, 6, 2, 3>(m, a, ch) : dispatch_gen<double, 4, 2, 2>(m, a, ch);
         } else {
             GenArgs<float> a{};
-            a.U = m->d_U32; a.ft = m->d_ft32; a.acc = acc; a.thr_factor = 1e-2f; a.Tp = m->d_scal;
+            a.U = m->d_U32; a.ft = m->d_ft32; a.acc = reinterpret_cast<float2 *>(m->d_part); a.thr_factor = 1e-2f; a.Tp = m->d_scal;
             fill_args(m, a);
+            fill_chunks(m, a);
             e = m->ns == 6 ? dispatch_gen<float, 6, 4, 3>(m, a, ch) : dispatch_gen<float, 4, 2, 2>(m, a, ch);
         }
         TUFRG_CUDA_TRY(e);
         PhaseScope ps(m, PH_LOOPRED);
-        loops_gen_finish<<<(unsigned)((per + 255) / 256), 256, 0, m->stream>>>(
-            acc, m->d_deltas, m->nd, (int)ns2, m->Nq, 1.0 / (double)m->Nk, m->d_dpartner, m->d_Lc + ch * per,
-            m->precision == TUFRG_FP64 ? nullptr : m->d_Lc32 + ch * per);
+        double2 *o64 = m->d_Lc + ch * per;
+        float2 *o32 = fp64 ? nullptr : m->d_Lc32 + ch * per;
+        const int n4 = m->nd * (int)(ns2 * ns2);
+        const dim3 grid((n4 + 255) / 256, m->Nq);
+        const double inv_nk = 1.0 / (double)m->Nk;
+        const double2 *a64 = reinterpret_cast<const double2 *>(m->d_part);
+        const float2 *a32 = reinterpret_cast<const float2 *>(m->d_part);
+        const int nc = m->gen_chunks;
+        if (m->sym) {
+            if (m->ns == 6 && fp64)
+                loops_gen_finish_sym<6><<<grid, 256, 0, m->stream>>>(a64, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+            else if (m->ns == 6)
+                loops_gen_finish_sym<6><<<grid, 256, 0, m->stream>>>(a32, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+            else if (fp64)
+                loops_gen_finish_sym<4><<<grid, 256, 0, m->stream>>>(a64, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+            else
+                loops_gen_finish_sym<4><<<grid, 256, 0, m->stream>>>(a32, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+        } else {
+            if (m->ns == 6 && fp64)
+                loops_gen_finish<6><<<grid, 256, 0, m->stream>>>(a64, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
+            else if (m->ns == 6)
+                loops_gen_finish<6><<<grid, 256, 0, m->stream>>>(a32, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
+            else if (fp64)
+                loops_gen_finish<4><<<grid, 256, 0, m->stream>>>(a64, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
+            else
+                loops_gen_finish<4><<<grid, 256, 0, m->stream>>>(a32, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
+        }
         TUFRG_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;

@@ -47,13 +47,14 @@ struct FlowDev {
     int accepted;     // 1 if the last attempt was accepted
 };
 
-// One element of the loop symmetry group (two bands): Lc(q')[d'][a'][b'] =
-// i^(qt[ch][a'] - qt[ch][b']) * (conj ? conj(L) : L) with L = Lc(q)[d][src[ch][a']][src[ch][b']],
-// q' = G_q q, Delta_d' = G Delta_d (every phase is a power of i).
+// One element of the loop symmetry group: Lc(q')[d'][a'][b'] = i^(qt[ch][a'] - qt[ch][b']) *
+// (conj ? conj(L) : L) with L = Lc(q)[d][src[ch][a']][src[ch][b']], q' = G_q q, Delta_d' = G Delta_d
+// (orbital-pair indices a < N_s^2 <= 36; every phase is a power of i).
+constexpr int SYM_MAXNS2 = 36;
 struct SymElem {
     int conj;
-    int src[2][4];
-    int qt[2][4];
+    int src[2][SYM_MAXNS2];
+    int qt[2][SYM_MAXNS2];
 };
 
 // bits of the exact double of a float, formed on the integer pipe (this GPU's FP64 pipe is slow);
@@ -167,6 +168,7 @@ struct tufrg_model {
     int step_graph_mask = 0;
 
     tufrg::LoopPlan plan{};
+    int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
 
     // ---- learned loop surrogate (optional)
     tufrg_mlp *sur = nullptr;       // network (not owned)
@@ -217,6 +219,7 @@ cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, co
                                const double2 *k6, size_t n);
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
+int plan_gen_chunks(const tufrg_model *m);   // kx ranges per momentum of the multi-orbital loop kernel
 int dft_plan_nsplit(const tufrg_model *m);
 bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);

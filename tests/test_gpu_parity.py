@@ -379,6 +379,20 @@ def test_t2g_loops(case, prec):
 
 
 @pytest.mark.parametrize("case", list(T2G))
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_t2g_loops_symmetry(case, prec):
+    """The t2g model (orbitals yz, xz, xy with atomic SOC) has the point group with orbital x spin
+    unitaries: one momentum per orbit is summed and the result equals the full k-sum."""
+    api = _api()
+    spec = T2G[case]()
+    m = api.Model(spec, getattr(api, prec))
+    full = api.Model(spec, getattr(api, prec), symmetry=api.SYMMETRY_OFF)
+    assert m.n_loop_q == _n_orbits(spec.Lq, C4V) and full.n_loop_q == spec.Lq ** 2
+    L, Lfull = m.loops(0.15).cpu().numpy(), full.loops(0.15).cpu().numpy()
+    assert rel(L, Lfull) < (1e-13 if prec == "FP64" else 2e-6)
+
+
+@pytest.mark.parametrize("case", list(T2G))
 @pytest.mark.parametrize("prec", ["FP64", "SPLIT32", "SPLIT32_SIMT"])
 def test_t2g_rhs(case, prec):
     api = _api()
