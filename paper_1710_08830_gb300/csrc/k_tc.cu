@@ -1,31 +1,32 @@
 // Tensor-core V.L.V products for the split path: dX/dT(q) = c_X A(q) L(q) A(q) (Eq. RGE_spin and the
 // orbital form of Eq. rge_Dmat) on 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// Complex GEMM C = A B (M x K times K x N) as one real GEMM with interleaved real/imaginary indices:
-//   A'[m][2k+r] = (Re, Im) A[m][k]           (the complex row read as floats, K' = 2K)
-//   B'[2k][2n] = Re B, B'[2k+1][2n] = -Im B, B'[2k][2n+1] = Im B, B'[2k+1][2n+1] = Re B
-//   C'[m][2n] = Re C, C'[m][2n+1] = Im C.
-// Precision: 3xTF32 - every FP32 operand x is split into hi = tf32(x) and lo = x - hi, and
-// C' = A'hi B'hi + A'hi B'lo + A'lo B'hi is accumulated in FP32 in tensor memory (TMEM), which keeps
-// FP32-level accuracy on the TF32 datapath.
+// Complex GEMM C = A B as four real MMA streams into two TMEM accumulators:
+//   Cr += Ar Br - Ai Bi,   Ci += Ar Bi + Ai Br     (the minus by the descriptor's negate-A bit).
+// Precision: 3xTF32 - every FP32 operand x is split into hi = tf32(x) and lo = x - hi, and each real
+// product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory, which keeps FP32-level
+// accuracy on the TF32 datapath.
 //
-// One CTA (128 threads) owns a 128-row x NT-column output tile of one transfer momentum.  Per K slice
-// of KC = 32 real columns the threads stage A'hi/lo (128 x KC) and B'^T hi/lo (NT x KC) in shared memory
-// in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), one elected
-// thread issues the tcgen05.mma instructions (M = 128, N = NT, K = 8 each) and commits them to an
-// mbarrier; everybody waits (bounded) before the slice buffers are rewritten.  The epilogue reads the
-// accumulator with tcgen05.ld (one TMEM lane per output row) and writes complex outputs.
-// Every wait is bounded: on time-out the kernel records an error code, waits (bounded) for its own
-// MMAs, frees its TMEM and returns.
+// Operands are packed once per product by small kernels into the K-major, no-swizzle core-matrix
+// layout of the MMA (8 rows x 16 bytes per core matrix), as four planes (Re hi, Re lo, Im hi, Im lo)
+// per (row tile, 16-wide K stage), so that one pipeline stage of one operand is a single contiguous
+// block.  The GEMM kernel (one CTA = 128 output rows x NB complex columns of one transfer momentum)
+// runs a two-stage pipeline: thread 0 issues one bulk copy per operand and stage (cp.async.bulk with
+// mbarrier transaction counts), thread 32 issues the 24 MMAs of a stage (2 K-steps x 4 products x 3)
+// and commits them to the stage's "empty" barrier, so copies of stage s + 1 overlap the MMAs of s.
+// The first product writes T = A L directly in the packed left-operand layout of the second; the
+// second writes c T A in FP64.  Every wait is bounded: on time-out the kernel records an error code,
+// waits (bounded) for its own MMAs, frees its TMEM and returns.
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
 namespace {
 
 constexpr int TC_M = 128;        // MMA M (rows per CTA)
-constexpr int KC = 32;           // real K per shared-memory slice
+constexpr int KS = 16;           // K per pipeline stage (two MMA K-steps of 8)
 constexpr int TC_THREADS = 128;
-constexpr unsigned long long TC_WAIT_LIMIT = 1ull << 20;
+constexpr int TMEM_COLS = 512;   // Cr at [0, NB), Ci at [256, 256 + NB)
+constexpr unsigned long long TC_WAIT_LIMIT = 1ull << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -36,9 +37,9 @@ __device__ __forceinline__ float tf32_hi(float x)
     return __uint_as_float(r);
 }
 
-// byte offset of element (row r, k) in a K-major no-swizzle tile with R rows and KC columns of 4 bytes:
-// core matrix (r/8, k/4) at ((k/4) * (R/8) + r/8) * 128, row r%8 at 16 bytes, element k%4 at 4 bytes.
-__device__ __forceinline__ int core_off(int r, int k, int R) { return ((k >> 2) * (R >> 3) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 3) * 4; }
+// float offset of element (row r, k) in a K-major no-swizzle plane of R rows x KS columns:
+// core matrix (r/8, k/4) at ((k/4) * (R/8) + r/8) * 32 floats, row r%8 at 4 floats, element k%4.
+__device__ __forceinline__ int core_off(int r, int k, int R) { return ((k >> 2) * (R >> 3) + (r >> 3)) * 32 + (r & 7) * 4 + (k & 3); }
 
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr, int R)
 {
@@ -47,10 +48,11 @@ __device__ __forceinline__ unsigned long long smem_desc(unsigned addr, int R)
     return (unsigned long long)((addr & 0x3FFFF) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
 }
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = nt
-__device__ __forceinline__ unsigned idesc_tf32(int nt)
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = nb; bit 13 negates A
+__device__ __forceinline__ unsigned idesc_tf32(int nb, bool neg_a)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(nt >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | ((unsigned)(nb >> 3) << 17) |
+           ((unsigned)(TC_M >> 4) << 24);
 }
 
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
@@ -64,137 +66,226 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
     return false;
 }
 
-struct TcArgs {
-    const float2 *A;        // [Nq][M][M]
-    const float2 *B;        // [Nq][M][M] plain, or nullptr when the loop matrix is gathered
-    const float2 *Lc;       // [Nq][nd][ns2][ns2] compact loops (gather)
-    const int *dij;         // [nff][nff]
-    float2 *out32;          // [Nq][M][M] (pass 1) or nullptr
-    double2 *out64;         // [Nq][M][M] (pass 2) or nullptr
-    int *err;               // error flag (set to 1 on a wait time-out)
-    int M, nff, ns2, nd, nt, tmem_cols;
+__device__ __forceinline__ void mma(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc, unsigned acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem), "l"(da), "l"(db), "r"(idesc),
+                 "r"(acc) : "memory");
+}
+
+struct PackDims {
+    int M;          // complex matrix order
+    int nks;        // K stages (16 wide) covering M
+    int nb;         // complex columns per N tile (multiple of 16, <= 256)
+    int m_tiles;    // 128-row tiles covering M
+    int n_tiles;    // NB-column tiles covering M
+};
+
+// left operand: rows m of X[q] (M x M, row-major), K = columns; planes (Re hi, Re lo, Im hi, Im lo)
+// block (q, row tile, K stage) = 4 planes of 128 x 16 floats.  Grid (m_tiles, nks, Nq), 512 threads.
+__global__ void __launch_bounds__(512) pack_left_kernel(const float2 *X, PackDims pd, float *out)
+{
+    const int rt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;
+    const int r = threadIdx.x & 127, kg = threadIdx.x >> 7;
+    const int m = rt * TC_M + r, k0 = ks * KS + kg * 4;
+    float re[4], im[4];
+    const float2 *src = X + ((size_t)q * pd.M + m) * pd.M;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float2 v = (m < pd.M && k0 + j < pd.M) ? src[k0 + j] : make_float2(0.f, 0.f);
+        re[j] = v.x;
+        im[j] = v.y;
+    }
+    float *blk = out + (((size_t)q * pd.m_tiles + rt) * pd.nks + ks) * 4 * (TC_M * KS);
+    const int o = core_off(r, kg * 4, TC_M);
+    float4 h, l;
+    h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
+    l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
+    *reinterpret_cast<float4 *>(blk + 0 * TC_M * KS + o) = h;
+    *reinterpret_cast<float4 *>(blk + 1 * TC_M * KS + o) = l;
+    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
+    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
+    *reinterpret_cast<float4 *>(blk + 2 * TC_M * KS + o) = h;
+    *reinterpret_cast<float4 *>(blk + 3 * TC_M * KS + o) = l;
+}
+
+// right operand B[k][n] of one transfer momentum as rows n, K = k: B = Y[q] (row-major) or, when gidx is
+// given, the loop matrix gathered from the compact loops, B[k][n] = Lc[q][gidx[k][n]].
+// Grid (n_tiles, nks, Nq), block (nb, 4).
+__global__ void pack_right_kernel(const float2 *Y, const float2 *Lc, const int *gidx, int lper, PackDims pd, float *out)
+{
+    const int nt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;
+    const int nl = threadIdx.x, kg = threadIdx.y;
+    const int n = nt * pd.nb + nl, k0 = ks * KS + kg * 4;
+    float re[4], im[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int k = k0 + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (n < pd.M && k < pd.M)
+            v = gidx ? Lc[(size_t)q * lper + gidx[(size_t)k * pd.M + n]] : Y[((size_t)q * pd.M + k) * pd.M + n];
+        re[j] = v.x;
+        im[j] = v.y;
+    }
+    const int R = pd.nb;
+    float *blk = out + (((size_t)q * pd.n_tiles + nt) * pd.nks + ks) * 4 * ((size_t)R * KS);
+    const int o = core_off(nl, kg * 4, R);
+    float4 h, l;
+    h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
+    l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
+    *reinterpret_cast<float4 *>(blk + 0 * R * KS + o) = h;
+    *reinterpret_cast<float4 *>(blk + 1 * R * KS + o) = l;
+    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
+    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
+    *reinterpret_cast<float4 *>(blk + 2 * R * KS + o) = h;
+    *reinterpret_cast<float4 *>(blk + 3 * R * KS + o) = l;
+}
+
+struct GemmArgs {
+    const float *left;      // packed left operand [Nq][m_tiles][nks][4][128 x 16]
+    const float *right;     // packed right operand [Nq][n_tiles][nks][4][nb x 16]
+    float *out_left;        // first product: C written as the packed left operand of the second (or null)
+    double2 *out64;         // second product: scale * C, [Nq][M][M] FP64 (or null)
+    int *err;
+    PackDims pd;
     double scale;
     const double *scal;     // optional device scale factor (scal[1])
 };
 
-__global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int NT = a.nt;
-    float *Ahi = reinterpret_cast<float *>(smem);
-    float *Alo = Ahi + TC_M * KC;
-    float *Bhi = Alo + TC_M * KC;
-    float *Blo = Bhi + NT * KC;
-    __shared__ __align__(8) unsigned long long mbar;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int NB = a.pd.nb, nks = a.pd.nks;
+    const unsigned a_bytes = 4u * TC_M * KS * 4u, b_bytes = 4u * (unsigned)NB * KS * 4u;
+    // stage s: [A planes | B planes]; both sizes are multiples of 1024 bytes
+    unsigned char *stage[2] = {smem_raw, smem_raw + a_bytes + b_bytes};
+    __shared__ __align__(8) unsigned long long full[2], empty[2], done;
     __shared__ unsigned tmem_base_sh;
+    __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = blockIdx.z;
-    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * NT;   // n0 counts real (interleaved) columns
-    const int M = a.M, K2 = 2 * M;
-    const size_t M2 = (size_t)M * M;
-    const float *Aq = reinterpret_cast<const float *>(a.A + (size_t)q * M2);
-    const double scale = a.scal ? a.scale * a.scal[1] : a.scale;
+    const int nt = blockIdx.x, rt = blockIdx.y, q = blockIdx.z;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(a.tmem_cols) : "memory");
+                     "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base_sh;
-    const unsigned idesc = idesc_tf32(NT);
-    bool ok = true;
-    int slice = 0;
-    for (int k0 = 0; k0 < K2; k0 += KC, slice++) {
-        // ---- stage A' (rows m0.., real columns k0..k0+KC) as hi/lo
-        for (int e = tid; e < TC_M * KC; e += TC_THREADS) {
-            const int r = e / KC, k = e % KC;
-            const int gm = m0 + r, gk = k0 + k;
-            const float x = (gm < M && gk < K2) ? Aq[(size_t)gm * K2 + gk] : 0.f;
-            const float hi = tf32_hi(x);
-            const int o = core_off(r, k, TC_M) >> 2;
-            Ahi[o] = hi;
-            Alo[o] = x - hi;
+
+    const float *lsrc = a.left + (((size_t)q * a.pd.m_tiles + rt) * nks) * (a_bytes / 4);
+    const float *rsrc = a.right + (((size_t)q * a.pd.n_tiles + nt) * nks) * (b_bytes / 4);
+    if (tid == 0) {
+        // producer: one bulk copy per operand and stage
+        for (int s = 0; s < nks; s++) {
+            const int b = s & 1;
+            if (s >= 2 && !mbar_wait(smem_u32(&empty[b]), ((s >> 1) - 1) & 1)) { failed = 1; break; }
+            unsigned long long st;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                         : "=l"(st) : "r"(smem_u32(&full[b])), "r"(a_bytes + b_bytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(stage[b])), "l"(lsrc + (size_t)s * (a_bytes / 4)), "r"(a_bytes),
+                         "r"(smem_u32(&full[b])) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(stage[b] + a_bytes)), "l"(rsrc + (size_t)s * (b_bytes / 4)), "r"(b_bytes),
+                         "r"(smem_u32(&full[b])) : "memory");
         }
-        // ---- stage B'^T (NT interleaved output columns x KC real K) as hi/lo, one complex B entry -> 4 reals
-        for (int e = tid; e < (NT / 2) * (KC / 2); e += TC_THREADS) {
-            const int nn = e % (NT / 2), kk = e / (NT / 2);      // local complex column / complex k
-            const int gn = n0 / 2 + nn, gk = k0 / 2 + kk;
-            float2 v = make_float2(0.f, 0.f);
-            if (gn < M && gk < M) {
-                if (a.B) {
-                    v = a.B[(size_t)q * M2 + (size_t)gk * M + gn];
-                } else {
-                    const int d = a.dij[(gk / a.ns2) * a.nff + gn / a.ns2];
-                    v = a.Lc[(((size_t)q * a.nd + d) * a.ns2 + gk % a.ns2) * a.ns2 + gn % a.ns2];
-                }
-            }
-            const float vals[4] = {v.x, -v.y, v.y, v.x};   // (2n,2k), (2n,2k+1), (2n+1,2k), (2n+1,2k+1)
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int r = 2 * nn + (j >> 1), k = 2 * kk + (j & 1);
-                const float hi = tf32_hi(vals[j]);
-                const int o = core_off(r, k, NT) >> 2;
-                Bhi[o] = hi;
-                Blo[o] = vals[j] - hi;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == 32) {
+        // MMA issuer: per stage, 2 K-steps x (Ar Br, -Ai Bi, Ar Bi, Ai Br) x (hi hi, hi lo, lo hi)
+        const unsigned id = idesc_tf32(NB, false), idn = idesc_tf32(NB, true);
+        const unsigned tr = tmem, ti = tmem + 256;
+        bool ok = true;
+        for (int s = 0; s < nks && ok; s++) {
+            const int b = s & 1;
+            if (!mbar_wait(smem_u32(&full[b]), (s >> 1) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+            const unsigned sa = smem_u32(stage[b]), sb = sa + a_bytes;
+            const unsigned pa = TC_M * KS * 4, pb = (unsigned)NB * KS * 4;   // plane strides (bytes)
 #pragma unroll
-            for (int ks = 0; ks < KC / 8; ks++) {
-                const unsigned aoff = ks * 2 * (TC_M / 8) * 128, boff = ks * 2 * (NT / 8) * 128;
-                const unsigned long long dah = smem_desc(ah + aoff, TC_M), dal = smem_desc(al + aoff, TC_M);
-                const unsigned long long dbh = smem_desc(bh + boff, NT), dbl = smem_desc(bl + boff, NT);
-                const unsigned acc0 = (slice > 0 || ks > 0) ? 1u : 0u;
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem), "l"(dah),
-                             "l"(dbh), "r"(idesc), "r"(acc0) : "memory");
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem), "l"(dah),
-                             "l"(dbl), "r"(idesc), "r"(1u) : "memory");
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem), "l"(dal),
-                             "l"(dbh), "r"(idesc), "r"(1u) : "memory");
+            for (int kk = 0; kk < 2; kk++) {
+                const unsigned ao = kk * 2 * (TC_M / 8) * 128, bo = kk * 2 * (NB / 8) * 128;
+                const unsigned long long arh = smem_desc(sa + 0 * pa + ao, TC_M), arl = smem_desc(sa + 1 * pa + ao, TC_M);
+                const unsigned long long aih = smem_desc(sa + 2 * pa + ao, TC_M), ail = smem_desc(sa + 3 * pa + ao, TC_M);
+                const unsigned long long brh = smem_desc(sb + 0 * pb + bo, NB), brl = smem_desc(sb + 1 * pb + bo, NB);
+                const unsigned long long bih = smem_desc(sb + 2 * pb + bo, NB), bil = smem_desc(sb + 3 * pb + bo, NB);
+                const unsigned first = (s == 0 && kk == 0) ? 0u : 1u;
+                mma(tr, arh, brh, id, first);  mma(tr, arh, brl, id, 1u);  mma(tr, arl, brh, id, 1u);
+                mma(tr, aih, bih, idn, 1u);    mma(tr, aih, bil, idn, 1u); mma(tr, ail, bih, idn, 1u);
+                mma(ti, arh, bih, id, first);  mma(ti, arh, bil, id, 1u);  mma(ti, arl, bih, id, 1u);
+                mma(ti, aih, brh, id, 1u);     mma(ti, aih, brl, id, 1u);  mma(ti, ail, brh, id, 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar))
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[b]))
                          : "memory");
         }
-        // the slice buffers may be rewritten only after these MMAs have read them
-        if (!mbar_wait(smem_u32(&mbar), slice & 1)) { ok = false; break; }
+        if (!ok) failed = 1;
+        // completion of every MMA issued above
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
+                     : "memory");
     }
+    __syncwarp();
+    const bool fin = mbar_wait(smem_u32(&done), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
+    __syncthreads();
+    if (!fin || failed) {
         if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(smem_u32(&mbar), (slice & 1));   // give in-flight MMAs a second bounded chance before TMEM is freed
     } else {
-        // ---- epilogue: lane = output row; 8 TMEM columns (4 complex outputs) per load
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < NT; c0 += 8) {
-            unsigned r[8];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+        // epilogue: lane = output row; 8 TMEM columns (8 complex outputs) per load from each accumulator
+        const int r = warp * 32 + lane, row = rt * TC_M + r, M = a.pd.M;
+        const double scale = a.scal ? a.scale * a.scal[1] : a.scale;
+        for (int c0 = 0; c0 < NB; c0 += 8) {
+            unsigned vr[8], vi[8];
+            const unsigned lane_off = (unsigned)(warp * 32) << 16;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                         : "r"(taddr));
+                         : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7])
+                         : "r"(tmem + lane_off + (unsigned)c0));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7])
+                         : "r"(tmem + lane_off + 256u + (unsigned)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
+            const int n0 = nt * NB + c0;   // first complex output column of this group
+            if (a.out64) {
+                if (row < M) {
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int n = (n0 + c0) / 2 + j;
-                    if (n >= M) continue;
-                    const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
-                    const size_t o = (size_t)q * M2 + (size_t)row * M + n;
-                    if (a.out64) a.out64[o] = make_double2(scale * (double)re, scale * (double)im);
-                    else a.out32[o] = make_float2((float)(scale * re), (float)(scale * im));
+                    for (int j = 0; j < 8; j++) {
+                        const int n = n0 + j;
+                        if (n >= M) break;
+                        a.out64[((size_t)q * M + row) * M + n] =
+                            make_double2(scale * (double)__uint_as_float(vr[j]), scale * (double)__uint_as_float(vi[j]));
+                    }
+                }
+            } else {
+                // packed left operand of the next product: row tile rt, K = n (padding columns are zero here)
+#pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    const int k = n0 + 4 * g;
+                    if (k >= a.pd.nks * KS) break;
+                    float *blk = a.out_left + (((size_t)q * a.pd.m_tiles + rt) * a.pd.nks + k / KS) * 4 * (TC_M * KS);
+                    const int o = core_off(r, k % KS, TC_M);
+                    float re[4], im[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        re[j] = __uint_as_float(vr[4 * g + j]);
+                        im[j] = __uint_as_float(vi[4 * g + j]);
+                    }
+                    float4 h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
+                    float4 l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
+                    *reinterpret_cast<float4 *>(blk + 0 * TC_M * KS + o) = h;
+                    *reinterpret_cast<float4 *>(blk + 1 * TC_M * KS + o) = l;
+                    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
+                    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
+                    *reinterpret_cast<float4 *>(blk + 2 * TC_M * KS + o) = h;
+                    *reinterpret_cast<float4 *>(blk + 3 * TC_M * KS + o) = l;
                 }
             }
         }
@@ -203,55 +294,75 @@ __global__ void __launch_bounds__(TC_THREADS) tc_cgemm_kernel(TcArgs a)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
+}
+
+PackDims pack_dims(const tufrg_model *m)
+{
+    PackDims pd{};
+    pd.M = m->M;
+    pd.nks = (m->M + KS - 1) / KS;
+    pd.n_tiles = (m->M + 255) / 256;
+    pd.nb = ((m->M + pd.n_tiles - 1) / pd.n_tiles + 15) / 16 * 16;
+    pd.m_tiles = (m->M + TC_M - 1) / TC_M;
+    return pd;
 }
 
 }  // namespace
 
 bool tc_supported(const tufrg_model *m) { return m->precision == TUFRG_SPLIT32 && m->products == TUFRG_PRODUCTS_TC; }
 
+// bytes of the packed left and right operands of all transfer momenta
+void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right)
+{
+    const PackDims pd = pack_dims(m);
+    *left = sizeof(float) * (size_t)m->Nq * pd.m_tiles * pd.nks * 4 * TC_M * KS;
+    *right = sizeof(float) * (size_t)m->Nq * pd.n_tiles * pd.nks * 4 * (size_t)pd.nb * KS;
+}
+
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
 {
+    if (!m->d_tc_left[0] || !m->d_tc_right || !m->d_tc_gidx) return cudaErrorNotReady;
+    const PackDims pd = pack_dims(m);
     const int M = m->M, ns2 = m->ns * m->ns;
-    const size_t M2 = (size_t)M * M, lper = (size_t)m->Nq * m->nd * ns2 * ns2;
-    // N tiling of the 2M interleaved output columns: at most 256 per tile, multiple of 16
-    const int n_tiles = (2 * M + 255) / 256;
-    int nt = (2 * M + n_tiles - 1) / n_tiles;
-    nt = (nt + 15) / 16 * 16;
-    int cols = 32;
-    while (cols < nt) cols *= 2;
-    const size_t smem = sizeof(float) * (2 * TC_M * KC + 2 * (size_t)nt * KC) + 64 * 1024;   // + guard
+    const size_t M2 = (size_t)M * M, lper = (size_t)m->nd * ns2 * ns2;
+    const size_t smem = 2 * (4 * (size_t)TC_M * KS * 4 + 4 * (size_t)pd.nb * KS * 4);
     TUFRG_CUDA_TRY(cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const dim3 grid((2 * M + nt - 1) / nt, (M + TC_M - 1) / TC_M, m->Nq);
-    PhaseScope ps(m, PH_VLV, 4);
+    const dim3 ggrid(pd.n_tiles, pd.m_tiles, m->Nq);
+    const dim3 lgrid(pd.m_tiles, pd.nks, m->Nq), rgrid(pd.n_tiles, pd.nks, m->Nq), rblock(pd.nb, 4);
+    PhaseScope ps(m, PH_VLV, 8);
     for (int ch = 0; ch < 2; ch++) {
         double2 *o = d_out + (size_t)ch * m->Nq * M2;
         if (!((channel_mask >> ch) & 1)) {
             TUFRG_CUDA_TRY(cudaMemsetAsync(o, 0, sizeof(double2) * m->Nq * M2, m->stream));
             continue;
         }
-        TcArgs a{};
-        a.A = m->d_A32 + (size_t)ch * m->Nq * M2;
-        a.B = nullptr;
-        a.Lc = m->d_Lc32 + ch * lper;
-        a.dij = m->d_dij;
-        a.out32 = reinterpret_cast<float2 *>(m->d_T);
-        a.err = m->d_err;
-        a.M = M; a.nff = m->nff; a.ns2 = ns2; a.nd = m->nd; a.nt = nt; a.tmem_cols = cols;
-        a.scale = 1.0;
-        a.scal = nullptr;
-        tc_cgemm_kernel<<<grid, TC_THREADS, smem, m->stream>>>(a);           // T = A L
+        const float2 *A = m->d_A32 + (size_t)ch * m->Nq * M2;
+        // T = A L
+        pack_left_kernel<<<lgrid, 512, 0, m->stream>>>(A, pd, m->d_tc_left[0]);
+        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(nullptr, m->d_Lc32 + ch * m->Nq * lper, m->d_tc_gidx, (int)lper,
+                                                           pd, m->d_tc_right);
+        GemmArgs g{};
+        g.left = m->d_tc_left[0];
+        g.right = m->d_tc_right;
+        g.out_left = m->d_tc_left[1];
+        g.out64 = nullptr;
+        g.err = m->d_err;
+        g.pd = pd;
+        g.scale = 1.0;
+        g.scal = nullptr;
+        tc_cgemm_kernel<<<ggrid, TC_THREADS, smem, m->stream>>>(g);
         TUFRG_CUDA_TRY(cudaGetLastError());
-        TcArgs b = a;
-        b.A = reinterpret_cast<const float2 *>(m->d_T);
-        b.B = m->d_A32 + (size_t)ch * m->Nq * M2;
-        b.Lc = nullptr;
-        b.out32 = nullptr;
-        b.out64 = o;
-        b.scale = ch == 0 ? 1.0 : 2.0;
-        b.scal = m->d_scal;
-        tc_cgemm_kernel<<<grid, TC_THREADS, smem, m->stream>>>(b);           // dX = c T A
+        // dX = c T A
+        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(A, nullptr, nullptr, 0, pd, m->d_tc_right);
+        GemmArgs h = g;
+        h.left = m->d_tc_left[1];
+        h.out_left = nullptr;
+        h.out64 = o;
+        h.scale = ch == 0 ? 1.0 : 2.0;
+        h.scal = m->d_scal;
+        tc_cgemm_kernel<<<ggrid, TC_THREADS, smem, m->stream>>>(h);
         TUFRG_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;

@@ -132,6 +132,9 @@ struct tufrg_model {
                                                //  high bit = minus sign; phase-table column)
     double2 *d_v0d[2] = {nullptr, nullptr};    // [M*M] bare vertex V0 at the onsite bond pair, 0 elsewhere
     float2 *d_X32 = nullptr;        // [2][Nq][M][M] FP32 copy of the state being evaluated (split path)
+    float *d_tc_left[2] = {nullptr, nullptr};   // tensor-core products: packed left operands (A, then T)
+    float *d_tc_right = nullptr;    // packed right operand (L, then A)
+    int *d_tc_gidx = nullptr;       // [M][M] index of L[k][n] in one momentum's compact loops
     float2 *d_lph32 = nullptr;      // [Lf] e^{-2 pi i n / Lf} for the split loop kernel
     float2 *d_clsph32 = nullptr;    // [Nq][ncls] e^{i u.R''} (split-path Fourier transform)
     float2 *d_v0d32[2] = {nullptr, nullptr};   // FP32 copies of d_v0d (split path)
@@ -227,6 +230,7 @@ bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
 cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
 bool tc_supported(const tufrg_model *m);
+void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out);
 cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
 cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu
