@@ -110,6 +110,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def tf32_peak_tflops(peaks):
+    """Dense TF32 tensor peak: the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    return peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+
+
+def products_tf32_flop(M, Nq):
+    """3xTF32 work of one right-hand side's products: per transfer momentum and channel two complex
+    M^3 GEMMs, each four real GEMMs times three TF32 products, 2 flop per multiply-add."""
+    return 2.0 * 2 * 2 * 4 * 3 * float(M) ** 3 * Nq
+
+
 def loop_traffic_record():
     """DRAM bytes per loop-kernel launch from the committed ncu summary, if it matches the current source."""
     import hashlib
@@ -123,6 +134,41 @@ def loop_traffic_record():
     if rec.get("k_loops2_sha256_16") != h:
         return None, rec
     return rec, rec
+
+
+def run_products_sweep(args):
+    """Products phase per right-hand side, tensor cores (tcgen05, 3xTF32) vs CUDA cores (FP32)."""
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300 import inputs
+    from paper_1710_08830_gb300.api import PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, Model
+    peaks, src = measured_peaks()
+    tf32 = tf32_peak_tflops(peaks)
+    rows = []
+    for n_ff in (5, 9, 13):
+        spec = inputs.t2g_soc(0, 0.2, 2.0, 0.4, Lq=32, nc=1, n_ff=n_ff, filling=4.0, T_mu=0.05)
+        st = torch.from_numpy(inputs.random_state(spec, seed=1, scale=0.1)).cuda()
+        out = torch.empty_like(st)
+        row = {"n_ff": n_ff, "M": spec.M, "Nq": spec.Nq}
+        for name, prod in (("tc", PRODUCTS_TC), ("simt", PRODUCTS_SIMT)):
+            m = Model(spec, SPLIT32, products=prod)
+            for _ in range(2):
+                m.rhs(0.1, st, out=out)
+            k = 5
+            m.timing_begin()
+            for _ in range(k):
+                m.rhs(0.1, st, out=out)
+            ph, _, _ = m.timing_end()
+            row[f"{name}_ms"] = ph["vlv"] / k
+            m.close()
+        flop = products_tf32_flop(spec.M, spec.Nq)
+        row["tc_tf32_tflops"] = flop / (row["tc_ms"] * 1e-3) / 1e12
+        row["tc_frac_of_tf32_peak"] = row["tc_tf32_tflops"] / tf32
+        row["complex_fp32_equiv_tflops_tc"] = 2.0 * 2 * 2 * 4 * float(spec.M) ** 3 * spec.Nq / (row["tc_ms"] * 1e-3) / 1e12
+        rows.append(row)
+    print(json.dumps({"products_sweep": rows, "tf32_peak_tflops": tf32,
+                      "peak_source": f"{src} bf16 {peaks.get('bf16_tflops')} TFLOP/s x 1.1/2.25 (nominal TF32/BF16)",
+                      "note": "products phase of one right-hand side (both channels, packing included), CUDA events"}))
 
 
 def run_reference(args, rank, world):
@@ -183,6 +229,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
                     help="model configuration (default: the 24x24 / 8x8 Rashba-Hubbard benchmark workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path (and the accuracy check)")
+    ap.add_argument("--products-sweep", action="store_true",
+                    help="only time the V.L.V products (tensor cores vs CUDA cores) on t2g models with N_ff = 5, 9, 13 "
+                         "(M = 180, 324, 468) at Nq = 32 x 32")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
@@ -197,6 +246,9 @@ def main():
     from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, SYMMETRY_OFF, Model
 
     torch.cuda.set_device(local)
+    if args.products_sweep:
+        run_products_sweep(args)
+        return
     if args.profile_rhs > 0:
         # a short, fixed launch sequence for profilers: model set-up, then N right-hand sides
         spec = inputs.rashba_q24_k8_ff9(0)
@@ -421,6 +473,14 @@ def main():
             "e2e": {"value": e2e_rate, "unit": "RHS/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},
             "roofline": roofline,
+            "roofline_products": ({"bound": "tensor", "kernel": "tc_cgemm_kernel + operand packing (tcgen05, 3xTF32)",
+                                   "achieved": products_tf32_flop(spec.M, spec.Nq) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12,
+                                   "peak": tf32_peak_tflops(peaks), "unit": "TFLOP/s",
+                                   "frac": products_tf32_flop(spec.M, spec.Nq) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12
+                                           / tf32_peak_tflops(peaks),
+                                   "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
+                                   "work": "2 channels x 2 complex M^3 GEMMs x 4 real x 3 TF32 per momentum"}
+                                  if m32.products == "tc" else None),
             "cpu_baseline": cpu,
             "batch_flows": batch,
             "clocks": clocks,

@@ -24,19 +24,6 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
     acc.y = fma(a.y, b.x, acc.y);
 }
 
-// bits of the exact double of a float, formed on the integer pipe (hi word, lo word); subnormal,
-// inf and nan take the plain conversion
-__device__ __forceinline__ uint2 widen_bits(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
-    if (e == 0u && man == 0u) return make_uint2(u & 0x80000000u, 0u);   // signed zero
-    if (e == 0u || e == 0xffu) {
-        const double d = (double)f;
-        return make_uint2((unsigned)__double2hiint(d), (unsigned)__double2loint(d));
-    }
-    return make_uint2((u & 0x80000000u) | ((e + 896u) << 20) | (man >> 3), u << 29);
-}
 // one FP64 complex output (little-endian double2 = lo, hi, lo, hi words)
 __device__ __forceinline__ void store_c(double2 *o, float2 v, float sc)
 {

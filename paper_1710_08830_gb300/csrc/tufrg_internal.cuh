@@ -57,15 +57,23 @@ struct SymElem {
     int qt[2][SYM_MAXNS2];
 };
 
-// bits of the exact double of a float, formed on the integer pipe (this GPU's FP64 pipe is slow);
-// subnormal, inf and nan take the plain conversion
+// (hi, lo) words of the exact double of a float, formed on the integer pipe only (this GPU's FP64 pipe,
+// which also executes conversions, is slow; a branch to a plain conversion gets if-converted into an
+// unconditional one): normal, zero, subnormal (normalised with clz), inf and nan.
+__device__ __forceinline__ uint2 widen_bits(float f)
+{
+    const unsigned u = __float_as_uint(f), sign = u & 0x80000000u, e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    if (e == 0xffu) return make_uint2(sign | 0x7ff00000u | (man >> 3), man << 29);
+    if (e != 0u) return make_uint2(sign | ((e + 896u) << 20) | (man >> 3), man << 29);
+    if (man == 0u) return make_uint2(sign, 0u);
+    const int p = 31 - __clz((int)man);   // leading bit of the subnormal mantissa, value = man 2^-149
+    const unsigned long long fr = (unsigned long long)(man & ((1u << p) - 1u)) << (52 - p);
+    return make_uint2(sign | ((unsigned)(p - 149 + 1023) << 20) | (unsigned)(fr >> 32), (unsigned)fr);
+}
 __device__ __forceinline__ double widen_f(float f)
 {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u && (u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // signed zero
-    if (e == 0u || e == 0xffu) return (double)f;
-    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+    const uint2 w = widen_bits(f);
+    return __hiloint2double((int)w.x, (int)w.y);
 }
 
 struct LoopPlan {
