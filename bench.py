@@ -243,7 +243,7 @@ def main():
     import numpy as np
     import torch
     from paper_1710_08830_gb300 import inputs
-    from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, SYMMETRY_OFF, Model
+    from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, SYMMETRIC_STATE, SYMMETRY_OFF, Model
 
     torch.cuda.set_device(local)
     if args.products_sweep:
@@ -293,7 +293,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     for _ in range(args.warmup):
-        m32.rhs(T_BENCH, state, out=out)
+        m32.rhs(T_BENCH, state, out=out, symmetric=True)
     torch.cuda.synchronize()
 
     # ---------------- timed region: K split-precision right-hand sides
@@ -304,7 +304,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
-        m32.rhs(T_BENCH, state, out=out)
+        m32.rhs(T_BENCH, state, out=out, symmetric=True)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -315,7 +315,7 @@ def main():
     m32.timing_begin()
     for i in range(k_phase):
         flush.fill_(float(i))
-        m32.rhs(T_BENCH, state, out=out)
+        m32.rhs(T_BENCH, state, out=out, symmetric=True)
     phase_ms, launches, loop_launches = m32.timing_end()
     phase_ms = {k: v * args.steps / k_phase for k, v in phase_ms.items()}
     launches = launches * args.steps // k_phase
@@ -329,7 +329,7 @@ def main():
     k64 = max(3, min(args.steps, 30))
     err_split = fp64_rate = None
     if m64 is not None:
-        d32 = m32.rhs(T_BENCH, state).cpu().numpy()
+        d32 = m32.rhs(T_BENCH, state, symmetric=True).cpu().numpy()
         d64 = m64.rhs(T_BENCH, state).cpu().numpy()
         err_split = float(np.abs(d32 - d64).max() / np.abs(d64).max())
 
@@ -343,6 +343,18 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         fp64_rate = k64 / (e0.elapsed_time(e1) * 1e-3)
+
+    # ---------------- the same split path for a general state (projections and products at every momentum)
+    for _ in range(2):
+        m32.rhs(T_BENCH, state, out=out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    kg = max(3, min(args.steps, 100))
+    for _ in range(kg):
+        m32.rhs(T_BENCH, state, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    general_rate = kg / (e0.elapsed_time(e1) * 1e-3)
 
     # ---------------- the same split path with every transfer momentum summed directly (the FP64
     # path above does not use the loop symmetries either)
@@ -362,11 +374,11 @@ def main():
     hs = state.cpu().pin_memory()
     ho = torch.empty_like(hs).pin_memory()
     for _ in range(3):
-        m32.rhs_host(T_BENCH, hs, ho)
+        m32.rhs_host(T_BENCH, hs, ho, mask=3 | SYMMETRIC_STATE)
     ke = max(3, min(args.steps, 100))
     t = time.perf_counter()
     for _ in range(ke):
-        m32.rhs_host(T_BENCH, hs, ho)
+        m32.rhs_host(T_BENCH, hs, ho, mask=3 | SYMMETRIC_STATE)
     e2e_rate = ke / (time.perf_counter() - t)
     e2e_rate = world * ke / (allmax(ke / e2e_rate))
     state_bytes = int(hs.numel() * hs.element_size())
@@ -460,11 +472,14 @@ def main():
                        "n_s": spec.n_s, "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH,
                        "precision": "split (FP32 loop sums, FP64 state)",
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
-                       "loop_momenta_summed": m32.n_loop_q,
+                       "loop_momenta_summed": m32.n_loop_q, "symmetric_state": True,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},
             "split_vs_fp64_maxrel": err_split,
             "fp64_gpu": ({"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate,
                           "note": "every transfer momentum summed directly"} if fp64_rate else None),
+            "rhs_general_state": {"value": general_rate, "unit": "RHS/s",
+                                  "note": "tufrg_rhs without TUFRG_SYMMETRIC_STATE: projections and products at every "
+                                          "momentum (the timed loop evaluates the flow state, which has the symmetries)"},
             "split_every_q_summed": {"value": full_rate, "unit": "RHS/s",
                                      "note": "split path with the loop symmetries off (same loop work as fp64_gpu)"},
             "time_to_lambda_c": flows,

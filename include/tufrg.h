@@ -100,7 +100,9 @@ typedef struct {
  * Lc(-q)[Delta] = V conj(Lc(q)[Delta]) V^dagger with V built from W.  With TUFRG_SYMMETRY_AUTO the
  * operations that hold (U searched among the monomial unitaries) are found at init, the k-sum runs
  * for one momentum per orbit and the others are written from it.  TUFRG_SYMMETRY_OFF sums every q. */
-enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1 };
+/* For symmetric states (tufrg_rhs with TUFRG_SYMMETRIC_STATE, and every flow) the projections and products can
+ * run for the orbit representatives only; AUTO does so when a timing at init shows it faster, STATES always. */
+enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1, TUFRG_SYMMETRY_STATES = 2 };
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
 typedef struct {
@@ -177,7 +179,13 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
 
 /* Right-hand side dX/dT of the flow at temperature T (device buffers, no host sync):
  * loops, Fourier transform to bonds, projections, dP/dT = A L^- A, dC/dT = 2 A L^+ A.
- * d_state, d_dstate: [2][Nq][M][M] complex; channels outside the mask get zero. */
+ * d_state, d_dstate: [2][Nq][M][M] complex; channels outside the mask get zero.
+ * channel_mask may include TUFRG_SYMMETRIC_STATE: the caller asserts that the state has the model's loop
+ * symmetries (X(G q) = W X(q) W^dagger, W the bond permutation times the orbital-pair map of the symmetry;
+ * every state of a flow from X = 0 has them when the bare vertex does), and projections and products then
+ * run for the orbit representatives only, the other momenta being written from them.  For a state without
+ * those symmetries the result is wrong; the flag is ignored when the model has no usable symmetry. */
+enum { TUFRG_SYMMETRIC_STATE = 4 };
 tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate);
 
 /* Same right-hand side with host buffers: copies h_state to the device, evaluates,

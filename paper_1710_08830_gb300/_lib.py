@@ -19,7 +19,8 @@ STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA",
 
 FP64, SPLIT32 = 0, 1
 PRODUCTS_AUTO, PRODUCTS_TC, PRODUCTS_SIMT = 0, 1, 2
-SYMMETRY_AUTO, SYMMETRY_OFF = 0, 1
+SYMMETRY_AUTO, SYMMETRY_OFF, SYMMETRY_STATES = 0, 1, 2
+SYMMETRIC_STATE = 4   # tufrg_rhs flag: the state has the model's loop symmetries
 CH_P, CH_C = 1, 2
 
 

@@ -13,12 +13,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRY_AUTO, SYMMETRY_OFF,
+from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
+                   SYMMETRY_OFF, SYMMETRY_STATES,
                    FlowOpts, FlowResult, ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
 __all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "SYMMETRY_AUTO",
-           "SYMMETRY_OFF", "CH_P", "CH_C", "TufrgError"]
+           "SYMMETRY_OFF", "SYMMETRY_STATES", "SYMMETRIC_STATE", "CH_P", "CH_C", "TufrgError"]
 
 
 def _ptr(t) -> int:
@@ -134,11 +135,15 @@ class Model:
                                           C.byref(amax) if want_max else None))
         return out, amax.value
 
-    def rhs(self, T: float, state, mask: int = CH_P | CH_C, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    def rhs(self, T: float, state, mask: int = CH_P | CH_C, out: Optional[torch.Tensor] = None,
+            symmetric: bool = False) -> torch.Tensor:
+        """dX/dT at T.  symmetric=True asserts that the state has the model's loop symmetries (every state of a
+        flow from X = 0 does): projections and products then run for the orbit representatives only."""
         state = self._dev(state)
         if out is None:
             out = torch.empty_like(state)
-        self._check(self._L.tufrg_rhs(self._h, float(T), _ptr(state), int(mask), _ptr(out)))
+        flag = SYMMETRIC_STATE if symmetric else 0
+        self._check(self._L.tufrg_rhs(self._h, float(T), _ptr(state), int(mask) | flag, _ptr(out)))
         return out
 
     def rhs_host(self, T: float, state_host: torch.Tensor, out_host: torch.Tensor, mask: int = CH_P | CH_C):

@@ -244,6 +244,7 @@ struct LoopSymmetry {
     std::vector<int> list, dinv;
     std::vector<int2> qmap;
     std::vector<tufrg::SymElem> elem;
+    std::vector<int> ffinv;   // [elem][nff] source bond of each target bond (G R_src = R_target), -1 if none
 };
 
 struct Mono {
@@ -408,6 +409,14 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
             inv[find_delta(el.Gd[0] * m->deltas[2 * k] + el.Gd[1] * m->deltas[2 * k + 1],
                            el.Gd[2] * m->deltas[2 * k] + el.Gd[3] * m->deltas[2 * k + 1])] = k;
         ls.dinv.insert(ls.dinv.end(), inv.begin(), inv.end());
+        std::vector<int> finv(m->nff, -1);   // bonds: R_target = G R_source (modulo Lq)
+        for (int i = 0; i < m->nff; i++) {
+            const int x = el.Gd[0] * m->ffR[2 * i] + el.Gd[1] * m->ffR[2 * i + 1];
+            const int y = el.Gd[2] * m->ffR[2 * i] + el.Gd[3] * m->ffR[2 * i + 1];
+            const int j = ff_index_mod(m, x, y);
+            if (j >= 0) finv[j] = i;
+        }
+        ls.ffinv.insert(ls.ffinv.end(), finv.begin(), finv.end());
     }
     // orbits: the smallest momentum of each orbit is its representative
     ls.qmap.assign(m->Nq, make_int2(-1, -1));
@@ -449,7 +458,7 @@ void release(tufrg_model *m)
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
-                    m->d_tc_gidx};
+                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -469,9 +478,14 @@ size_t state_elems(const tufrg_model *m) { return (size_t)2 * m->Nq * m->M * m->
 // each channel scaled by c_X * m->d_scal[1] (1 for dX/dT, T for the flow variable ln T).
 // The split path evaluates on an FP32 copy of the state: d_state32 when the caller has already
 // written one (the flow's stage combinations do), else a conversion of d_state into m->d_X32.
-tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double2 *d_out, const float2 *d_state32)
+tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double2 *d_out, const float2 *d_state32,
+                        bool symmetric_state)
 {
     const bool split = m->precision != TUFRG_FP64;
+    // a symmetric state needs projections and products at the orbit representatives only
+    const bool sym = symmetric_state && m->sym_state && m->sym_state_pays;
+    const int *ql = sym ? m->d_loop_list : nullptr;
+    const int nl = sym ? m->n_loop_q : 0;
     if (split && !d_state32) {
         CK(launch_to_f32(m, d_state, m->d_X32, state_elems(m)), "state conversion");
         d_state32 = m->d_X32;
@@ -480,8 +494,9 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
     CK(launch_loops(m, mask), "loop k-sum");
     CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
     // the split path's products read the FP32 copy only
-    CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A), "projections");
-    CK(launch_vlv(m, m->d_A, mask, d_out), "V.L.V products");
+    CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A, ql, nl), "projections");
+    CK(launch_vlv(m, m->d_A, mask, d_out, ql, nl), "V.L.V products");
+    if (sym) CK(launch_sym_scatter(m, d_out), "symmetric scatter");
     return TUFRG_OK;
 }
 
@@ -512,7 +527,7 @@ tufrg_status enqueue_attempt(tufrg_model *m, int mask)
         double2 *dst = j == 6 ? m->d_yn : (split ? nullptr : m->d_yt);
         CK(launch_rk_combine(m, dst, split ? m->d_X32 : nullptr, m->d_y, m->d_flow, DP_A[j], k, j, n), "stage combination");
         CK(launch_stage_scalars(m, m->d_flow, DP_C[j]), "stage temperature");
-        tufrg_status st = rhs_device(m, dst, mask, k[j], split ? m->d_X32 : nullptr);
+        tufrg_status st = rhs_device(m, dst, mask, k[j], split ? m->d_X32 : nullptr, true);
         if (st != TUFRG_OK) return st;
     }
     CK(launch_rk_error(m, m->d_y, m->d_yn, m->d_flow, DP_E, k, 7, n), "error norm");
@@ -550,7 +565,7 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
     CK(surrogate_rearm(m), "re-arm surrogate");
     // k1 = f(x0, y0) and max|A| of the initial state
     CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
-    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0], nullptr);
+    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0], nullptr, true);
     if (st != TUFRG_OK) return st;
     CK(launch_flow_init(m, m->d_flow), "flow init");
     if (!m->step_graph || m->step_graph_mask != o->channel_mask) {
@@ -627,7 +642,7 @@ tufrg_status flow_finish(tufrg_model *m, void *d_state_out, tufrg_flow_result *r
     res->Tc = res->crossed ? f.Tc : res->T_last;
     // the last stage-7 projection belongs to the last accepted state when the flow stopped on an accepted step
     const size_t nA = state_elems(m), M2 = (size_t)m->M * m->M;
-    CK(launch_amax_locate(m, nA), "locate maximum");
+    CK(launch_amax_locate(m, nA, m->sym_state && m->sym_state_pays), "locate maximum");
     unsigned long long b[4];
     CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
     CK(cudaStreamSynchronize(m->stream), "sync");
@@ -677,7 +692,8 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if ((long)d.Lq * d.nc > 4096) return fail(m, TUFRG_EINVAL, "fine mesh too large");
     if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
     if (d.products < TUFRG_PRODUCTS_AUTO || d.products > TUFRG_PRODUCTS_SIMT) return fail(m, TUFRG_EINVAL, "unknown products backend");
-    if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF) return fail(m, TUFRG_EINVAL, "unknown symmetry option");
+    if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF && d.symmetry != TUFRG_SYMMETRY_STATES)
+        return fail(m, TUFRG_EINVAL, "unknown symmetry option");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
@@ -714,7 +730,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     build_gather_tables(m);
     // loop symmetries (TUFRG_SYMMETRY_AUTO, split two-band path)
     m->n_loop_q = m->Nq;
-    if (d.symmetry == TUFRG_SYMMETRY_AUTO && ((ns == 2 && loops2_supported(m)) || (ns != 2 && loops_gen_supported(m)))) {
+    if (d.symmetry != TUFRG_SYMMETRY_OFF && ((ns == 2 && loops2_supported(m)) || (ns != 2 && loops_gen_supported(m)))) {
         LoopSymmetry ls;
         build_loop_symmetry(m, ls);
         if ((int)ls.list.size() < m->Nq) {
@@ -725,6 +741,43 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             CK(upload(&m->d_qmap, ls.qmap, m->stream), "upload symmetry tables");
             CK(upload(&m->d_sym_elem, ls.elem, m->stream), "upload symmetry tables");
             CK(upload(&m->d_sym_dinv, ls.dinv, m->stream), "upload symmetry tables");
+            // symmetric states: every element must map the bond set onto itself and leave the bare vertex's
+            // onsite blocks invariant (a flow from X = 0 then stays symmetric)
+            bool ok = true;
+            for (int v : ls.ffinv) ok = ok && v >= 0;
+            const int nsq = ns * ns;
+            auto blk = [&](int ch, int a, int b) {   // onsite block of V0 in the channel's pair layout
+                int s1, s2, s3, s4;
+                if (ch == 0) { s1 = a / ns; s2 = a % ns; s4 = b / ns; s3 = b % ns; }
+                else         { s1 = a / ns; s3 = a % ns; s4 = b / ns; s2 = b % ns; }
+                const size_t o = 2 * ((((size_t)s1 * ns + s2) * ns + s3) * ns + s4);
+                return std::complex<double>(m->V0[o], m->V0[o + 1]);
+            };
+            for (size_t e = 0; e < ls.elem.size() && ok; e++)
+                for (int ch = 0; ch < 2 && ok; ch++)
+                    for (int a2 = 0; a2 < nsq && ok; a2++)
+                        for (int b2 = 0; b2 < nsq && ok; b2++) {
+                            const tufrg::SymElem &el = ls.elem[e];
+                            std::complex<double> v = blk(ch, el.src[ch][a2], el.src[ch][b2]);
+                            if (el.conj) v = std::conj(v);
+                            const int k = ((el.qt[ch][a2] - el.qt[ch][b2]) % 4 + 4) % 4;
+                            v *= std::pow(std::complex<double>(0.0, 1.0), k);
+                            ok = std::abs(v - blk(ch, a2, b2)) <= 1e-12 * (1.0 + std::abs(blk(ch, a2, b2)));
+                        }
+            if (ok) {
+                // per element and channel: source row (= column) index and quarter turns of every target index
+                std::vector<int> srow((size_t)ls.elem.size() * 2 * m->M), qrow((size_t)ls.elem.size() * 2 * m->M);
+                for (size_t e = 0; e < ls.elem.size(); e++)
+                    for (int ch = 0; ch < 2; ch++)
+                        for (int r = 0; r < m->M; r++) {
+                            const size_t o = (e * 2 + ch) * m->M + r;
+                            srow[o] = ls.ffinv[e * m->nff + r / nsq] * nsq + ls.elem[e].src[ch][r % nsq];
+                            qrow[o] = ls.elem[e].qt[ch][r % nsq];
+                        }
+                m->sym_state = true;
+                CK(upload(&m->d_sym_srow, srow, m->stream), "upload symmetry tables");
+                CK(upload(&m->d_sym_qrow, qrow, m->stream), "upload symmetry tables");
+            }
         }
     }
     m->plan = plan_loops(m);
@@ -905,6 +958,50 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
         if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
     }
+    if (m->sym_state) {
+        // symmetric states: products for the orbit representatives plus the gather of the other momenta,
+        // against products for every momentum (on zeroed operands: the cost does not depend on the values);
+        // the representatives' path is used only where it is faster
+        const size_t nA = 2 * (size_t)m->Nq * M2;
+        double2 *tmp = nullptr;
+        CK(dalloc(&tmp, nA), "cudaMalloc autotune output");
+        if (split) {
+            CK(cudaMemsetAsync(m->d_A32, 0, sizeof(float2) * nA, m->stream), "zero");
+            CK(cudaMemsetAsync(m->d_Lc32, 0, sizeof(float2) * 2 * (size_t)m->Nq * m->nd * ns4, m->stream), "zero");
+        } else {
+            CK(cudaMemsetAsync(m->d_A, 0, sizeof(double2) * nA, m->stream), "zero");
+            CK(cudaMemsetAsync(m->d_Lc, 0, sizeof(double2) * 2 * (size_t)m->Nq * m->nd * ns4, m->stream), "zero");
+        }
+        CK(launch_set_scalars(m, 1.0, 1.0), "set scalars");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        for (int c = 0; c < 2; c++) {
+            auto run = [&]() -> cudaError_t {
+                if (c == 0) return launch_vlv(m, m->d_A, 3, tmp);
+                cudaError_t e = launch_vlv(m, m->d_A, 3, tmp, m->d_loop_list, m->n_loop_q);
+                return e == cudaSuccess ? launch_sym_scatter(m, tmp) : e;
+            };
+            CK(run(), "symmetric-state autotune warm-up");
+            CK(cudaEventRecord(e0, m->stream), "event");
+            const int reps = 3;
+            for (int r = 0; r < reps; r++) CK(run(), "symmetric-state autotune");
+            CK(cudaEventRecord(e1, m->stream), "event");
+            CK(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+            m->sym_tune_ms[c] = ms / reps;
+        }
+        m->sym_state_pays = d.symmetry == TUFRG_SYMMETRY_STATES || m->sym_tune_ms[1] < m->sym_tune_ms[0];
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(tmp);
+        m->launches = 0;
+        m->loop_launches = 0;
+        int dev_err = 0;
+        CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
+        if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
+    }
     return TUFRG_OK;
 }
 
@@ -1014,11 +1111,12 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
 {
     if (!m || !d_state || !d_dstate) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
-    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    if (channel_mask & ~(3 | TUFRG_SYMMETRIC_STATE))
+        return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C, optionally with TUFRG_SYMMETRIC_STATE");
     CK(launch_set_scalars(m, T, 1.0), "set temperature");
     CK(surrogate_rearm(m), "re-arm surrogate");
-    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask, reinterpret_cast<double2 *>(d_dstate),
-                      nullptr);
+    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask & 3, reinterpret_cast<double2 *>(d_dstate),
+                      nullptr, (channel_mask & TUFRG_SYMMETRIC_STATE) != 0);
 }
 
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)

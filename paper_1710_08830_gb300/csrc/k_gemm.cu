@@ -24,12 +24,13 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
 template <typename R, bool GATHER, bool OUT64>
 __global__ void __launch_bounds__(256) cgemm_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Bm,
                                                     const typename cpx<R>::t *Lc, const int *dij, int M, int nff,
-                                                    int ns2, int nd, double scale, const double *scal, void *Cout)
+                                                    int ns2, int nd, double scale, const double *scal, const int *qlist,
+                                                    void *Cout)
 {
     using C2 = typename cpx<R>::t;
     __shared__ C2 As[BK][BM + 1];
     __shared__ C2 Bs[BK][BN + 1];
-    const int q = blockIdx.z;
+    const int q = qlist ? qlist[blockIdx.z] : blockIdx.z;
     const size_t M2 = (size_t)M * M;
     const C2 *a = A + (size_t)q * M2;
     const C2 *b = GATHER ? nullptr : Bm + (size_t)q * M2;
@@ -95,11 +96,11 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const typename cpx<R>::t *A,
 
 template <typename R>
 cudaError_t run(tufrg_model *m, const typename cpx<R>::t *A, const typename cpx<R>::t *Lc, int channel_mask,
-                double2 *out, typename cpx<R>::t *Tbuf)
+                double2 *out, typename cpx<R>::t *Tbuf, const int *qlist, int nlist)
 {
     const int M = m->M, ns2 = m->ns * m->ns;
     const size_t M2 = (size_t)M * M, lper = (size_t)m->Nq * m->nd * ns2 * ns2;
-    const dim3 grid((M + BN - 1) / BN, (M + BM - 1) / BM, m->Nq);
+    const dim3 grid((M + BN - 1) / BN, (M + BM - 1) / BM, qlist ? nlist : m->Nq);
     for (int ch = 0; ch < 2; ch++) {
         double2 *o = out + (size_t)ch * m->Nq * M2;
         if (!((channel_mask >> ch) & 1)) {
@@ -108,10 +109,10 @@ cudaError_t run(tufrg_model *m, const typename cpx<R>::t *A, const typename cpx<
         }
         const auto *a = A + (size_t)ch * m->Nq * M2;
         cgemm_kernel<R, true, false><<<grid, 256, 0, m->stream>>>(a, nullptr, Lc + ch * lper, m->d_dij, M, m->nff,
-                                                                  ns2, m->nd, 1.0, nullptr, Tbuf);
+                                                                  ns2, m->nd, 1.0, nullptr, qlist, Tbuf);
         TUFRG_CUDA_TRY(cudaGetLastError());
         cgemm_kernel<R, false, true><<<grid, 256, 0, m->stream>>>(Tbuf, a, nullptr, nullptr, M, m->nff, ns2, m->nd,
-                                                                  ch == 0 ? 1.0 : 2.0, m->d_scal, o);
+                                                                  ch == 0 ? 1.0 : 2.0, m->d_scal, qlist, o);
         TUFRG_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -119,11 +120,12 @@ cudaError_t run(tufrg_model *m, const typename cpx<R>::t *A, const typename cpx<
 
 }  // namespace
 
-cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out)
+cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist,
+                             int nlist)
 {
     PhaseScope ps(m, PH_VLV, 4);
-    if (m->precision == TUFRG_FP64) return run<double>(m, d_A, m->d_Lc, channel_mask, d_out, m->d_T);
-    return run<float>(m, m->d_A32, m->d_Lc32, channel_mask, d_out, reinterpret_cast<float2 *>(m->d_T));
+    if (m->precision == TUFRG_FP64) return run<double>(m, d_A, m->d_Lc, channel_mask, d_out, m->d_T, qlist, nlist);
+    return run<float>(m, m->d_A32, m->d_Lc32, channel_mask, d_out, reinterpret_cast<float2 *>(m->d_T), qlist, nlist);
 }
 
 }  // namespace tufrg

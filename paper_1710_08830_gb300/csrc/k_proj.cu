@@ -119,28 +119,32 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
                                                       const XT *v0d0, const XT *v0d1, const int *eofs0,
                                                       const int *eofs1, const int2 *et0, const int2 *et1,
                                                       const typename cpx<R>::t *ph, int nph, int Nq, int M2, int ncls,
-                                                      int chmask, double2 *A, float2 *A32, unsigned long long *amax)
+                                                      int chmask, const int *qlist, int nlist, double2 *A, float2 *A32,
+                                                      unsigned long long *amax)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *phs = reinterpret_cast<C2 *>(smem_raw);   // [QT][nph]
-    const int ch = blockIdx.z, q0 = blockIdx.y * QT, nq = min(QT, Nq - q0);
+    __shared__ int sq[QT];                         // transfer momenta of this CTA (list positions p0 ..)
+    const int ch = blockIdx.z, p0 = blockIdx.y * QT, nq = min(QT, nlist - p0);
+    if (threadIdx.x < QT) sq[threadIdx.x] = threadIdx.x < nq ? (qlist ? qlist[p0 + threadIdx.x] : p0 + threadIdx.x) : 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < QT * nph; i += blockDim.x) {
         const int qi = i / nph;
-        phs[i] = qi < nq ? ph[(size_t)(q0 + qi) * nph + (i - qi * nph)] : mk(R(0), R(0));
+        phs[i] = qi < nq ? ph[(size_t)sq[qi] * nph + (i - qi * nph)] : mk(R(0), R(0));
     }
     __syncthreads();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     R m2 = R(0);
     if (e < M2) {
         const bool on = (chmask >> ch) & 1;
-        const size_t base = ((size_t)ch * Nq + q0) * M2 + e;
+        const size_t base = (size_t)ch * Nq * M2 + e;   // + q M2
         C2 acc[QT];
         if (on) {
             const C2 v0 = ld_as<R>((ch == 0 ? v0d0 : v0d1)[e]);
 #pragma unroll
             for (int qi = 0; qi < QT; qi++) {
-                acc[qi] = qi < nq ? ld_as<R>(X[base + (size_t)qi * M2]) : mk(R(0), R(0));
+                acc[qi] = qi < nq ? ld_as<R>(X[base + (size_t)sq[qi] * M2]) : mk(R(0), R(0));
                 acc[qi].x += v0.x;
                 acc[qi].y += v0.y;
             }
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
 #pragma unroll
         for (int qi = 0; qi < QT; qi++) {
             if (qi >= nq) break;
-            const size_t o = base + (size_t)qi * M2;
+            const size_t o = base + (size_t)sq[qi] * M2;
             if (A) A[o] = make_double2((double)acc[qi].x, (double)acc[qi].y);
             if (A32) A32[o] = make_float2((float)acc[qi].x, (float)acc[qi].y);
             m2 = max(m2, abs2(acc[qi]));
@@ -208,11 +212,17 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
 
 // Locate the maximum: every entry whose magnitude equals the reduced maximum records its flat index
 // (atomicMin keeps the first).  The magnitude is formed exactly as in the projection.
+// With qmap / list (projections of orbit representatives only) other momenta hold stale values and are skipped.
 template <typename C2>
-__global__ void amax_locate_kernel(const C2 *A, size_t n, const unsigned long long *amax, unsigned long long *where)
+__global__ void amax_locate_kernel(const C2 *A, size_t n, const unsigned long long *amax, unsigned long long *where,
+                                   const int2 *qmap, const int *list, size_t M2, int Nq)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (qmap) {
+        const int q = (int)((i / M2) % (size_t)Nq);
+        if (list[qmap[q].x] != q) return;
+    }
     if ((unsigned long long)__double_as_longlong(mag_of(abs2(A[i]))) == *amax) atomicMin(where, (unsigned long long)i);
 }
 
@@ -276,11 +286,12 @@ cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_s
 constexpr int PROJ_QT = 8;   // transfer momenta per thread
 
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
-                           double2 *d_A)
+                           double2 *d_A, const int *qlist, int nlist)
 {
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax, 0, sizeof(unsigned long long), m->stream));
     const int M2 = m->M * m->M;
-    dim3 grid((M2 + 255) / 256, (m->Nq + PROJ_QT - 1) / PROJ_QT, 2);
+    if (!qlist) nlist = m->Nq;
+    dim3 grid((M2 + 255) / 256, (nlist + PROJ_QT - 1) / PROJ_QT, 2);
     PhaseScope ps(m, PH_PROJ);
     if (m->precision == TUFRG_FP64) {
         const size_t smem = sizeof(double2) * PROJ_QT * m->nph;
@@ -288,27 +299,29 @@ cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, 256, smem, m->stream>>>(d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_eofs[0], m->d_eofs[1],
                                           m->d_eterms[0], m->d_eterms[1], m->d_ph, m->nph, m->Nq, M2, m->ncls,
-                                          channel_mask, d_A, nullptr, m->d_amax);
+                                          channel_mask, qlist, nlist, d_A, nullptr, m->d_amax);
     } else {
         const size_t smem = sizeof(float2) * PROJ_QT * m->nph;
         auto k = project_kernel<float, float2, PROJ_QT>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, 256, smem, m->stream>>>(d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_eofs[0], m->d_eofs[1],
                                           m->d_eterms[0], m->d_eterms[1], m->d_ph32, m->nph, m->Nq, M2, m->ncls,
-                                          channel_mask, d_A, m->d_A32, m->d_amax);   // d_A may be NULL here
+                                          channel_mask, qlist, nlist, d_A, m->d_A32, m->d_amax);   // d_A may be NULL here
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_amax_locate(tufrg_model *m, size_t n)
+cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only)
 {
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax + 1, 0xff, sizeof(unsigned long long), m->stream));
     m->launches++;
     const unsigned grid = (unsigned)((n + 255) / 256);
+    const int2 *qm = reps_only ? m->d_qmap : nullptr;
+    const size_t M2 = (size_t)m->M * m->M;
     if (m->precision == TUFRG_FP64)
-        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A, n, m->d_amax, m->d_amax + 1);
+        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A, n, m->d_amax, m->d_amax + 1, qm, m->d_loop_list, M2, m->Nq);
     else
-        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A32, n, m->d_amax, m->d_amax + 1);
+        amax_locate_kernel<<<grid, 256, 0, m->stream>>>(m->d_A32, n, m->d_amax, m->d_amax + 1, qm, m->d_loop_list, M2, m->Nq);
     return cudaGetLastError();
 }
 

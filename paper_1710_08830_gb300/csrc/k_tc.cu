@@ -83,13 +83,14 @@ struct PackDims {
 
 // left operand: rows m of X[q] (M x M, row-major), K = columns; planes (Re hi, Re lo, Im hi, Im lo)
 // block (q, row tile, K stage) = 4 planes of 128 x 16 floats.  Grid (m_tiles, nks, Nq), 512 threads.
-__global__ void __launch_bounds__(512) pack_left_kernel(const float2 *X, PackDims pd, float *out)
+__global__ void __launch_bounds__(512) pack_left_kernel(const float2 *X, PackDims pd, const int *qlist, float *out)
 {
-    const int rt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;
+    const int rt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;   // q: packed slot
+    const int qs = qlist ? qlist[q] : q;                          // transfer momentum read
     const int r = threadIdx.x & 127, kg = threadIdx.x >> 7;
     const int m = rt * TC_M + r, k0 = ks * KS + kg * 4;
     float re[4], im[4];
-    const float2 *src = X + ((size_t)q * pd.M + m) * pd.M;
+    const float2 *src = X + ((size_t)qs * pd.M + m) * pd.M;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const float2 v = (m < pd.M && k0 + j < pd.M) ? src[k0 + j] : make_float2(0.f, 0.f);
@@ -112,9 +113,11 @@ __global__ void __launch_bounds__(512) pack_left_kernel(const float2 *X, PackDim
 // right operand B[k][n] of one transfer momentum as rows n, K = k: B = Y[q] (row-major) or, when gidx is
 // given, the loop matrix gathered from the compact loops, B[k][n] = Lc[q][gidx[k][n]].
 // Grid (n_tiles, nks, Nq), block (nb, 4).
-__global__ void pack_right_kernel(const float2 *Y, const float2 *Lc, const int *gidx, int lper, PackDims pd, float *out)
+__global__ void pack_right_kernel(const float2 *Y, const float2 *Lc, const int *gidx, int lper, PackDims pd,
+                                  const int *qlist, float *out)
 {
-    const int nt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;
+    const int nt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;   // q: packed slot
+    const int qs = qlist ? qlist[q] : q;                          // transfer momentum read
     const int nl = threadIdx.x, kg = threadIdx.y;
     const int n = nt * pd.nb + nl, k0 = ks * KS + kg * 4;
     float re[4], im[4];
@@ -123,7 +126,7 @@ __global__ void pack_right_kernel(const float2 *Y, const float2 *Lc, const int *
         const int k = k0 + j;
         float2 v = make_float2(0.f, 0.f);
         if (n < pd.M && k < pd.M)
-            v = gidx ? Lc[(size_t)q * lper + gidx[(size_t)k * pd.M + n]] : Y[((size_t)q * pd.M + k) * pd.M + n];
+            v = gidx ? Lc[(size_t)qs * lper + gidx[(size_t)k * pd.M + n]] : Y[((size_t)qs * pd.M + k) * pd.M + n];
         re[j] = v.x;
         im[j] = v.y;
     }
@@ -150,6 +153,7 @@ struct GemmArgs {
     PackDims pd;
     double scale;
     const double *scal;     // optional device scale factor (scal[1])
+    const int *qlist;       // optional: packed slot z holds transfer momentum qlist[z] (out64 index)
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
                     for (int j = 0; j < 8; j++) {
                         const int n = n0 + j;
                         if (n >= M) break;
-                        a.out64[((size_t)q * M + row) * M + n] =
+                        a.out64[((size_t)(a.qlist ? a.qlist[q] : q) * M + row) * M + n] =
                             make_double2(scale * (double)__uint_as_float(vr[j]), scale * (double)__uint_as_float(vi[j]));
                     }
                 }
@@ -321,7 +325,7 @@ void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right)
     *right = sizeof(float) * (size_t)m->Nq * pd.n_tiles * pd.nks * 4 * (size_t)pd.nb * KS;
 }
 
-cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
+cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist)
 {
     if (!m->d_tc_left[0] || !m->d_tc_right || !m->d_tc_gidx) return cudaErrorNotReady;
     const PackDims pd = pack_dims(m);
@@ -329,8 +333,9 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
     const size_t M2 = (size_t)M * M, lper = (size_t)m->nd * ns2 * ns2;
     const size_t smem = 2 * (4 * (size_t)TC_M * KS * 4 + 4 * (size_t)pd.nb * KS * 4);
     TUFRG_CUDA_TRY(cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const dim3 ggrid(pd.n_tiles, pd.m_tiles, m->Nq);
-    const dim3 lgrid(pd.m_tiles, pd.nks, m->Nq), rgrid(pd.n_tiles, pd.nks, m->Nq), rblock(pd.nb, 4);
+    const int nz = qlist ? nlist : m->Nq;
+    const dim3 ggrid(pd.n_tiles, pd.m_tiles, nz);
+    const dim3 lgrid(pd.m_tiles, pd.nks, nz), rgrid(pd.n_tiles, pd.nks, nz), rblock(pd.nb, 4);
     PhaseScope ps(m, PH_VLV, 8);
     for (int ch = 0; ch < 2; ch++) {
         double2 *o = d_out + (size_t)ch * m->Nq * M2;
@@ -340,9 +345,9 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
         }
         const float2 *A = m->d_A32 + (size_t)ch * m->Nq * M2;
         // T = A L
-        pack_left_kernel<<<lgrid, 512, 0, m->stream>>>(A, pd, m->d_tc_left[0]);
+        pack_left_kernel<<<lgrid, 512, 0, m->stream>>>(A, pd, qlist, m->d_tc_left[0]);
         pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(nullptr, m->d_Lc32 + ch * m->Nq * lper, m->d_tc_gidx, (int)lper,
-                                                           pd, m->d_tc_right);
+                                                           pd, qlist, m->d_tc_right);
         GemmArgs g{};
         g.left = m->d_tc_left[0];
         g.right = m->d_tc_right;
@@ -352,10 +357,11 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out)
         g.pd = pd;
         g.scale = 1.0;
         g.scal = nullptr;
+        g.qlist = qlist;
         tc_cgemm_kernel<<<ggrid, TC_THREADS, smem, m->stream>>>(g);
         TUFRG_CUDA_TRY(cudaGetLastError());
         // dX = c T A
-        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(A, nullptr, nullptr, 0, pd, m->d_tc_right);
+        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(A, nullptr, nullptr, 0, pd, qlist, m->d_tc_right);
         GemmArgs h = g;
         h.left = m->d_tc_left[1];
         h.out_left = nullptr;

@@ -72,13 +72,13 @@ __device__ __forceinline__ void tile44(const C2 *Xt, const C2 *Y, int M, int r, 
 template <typename R>
 __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Lc,
                                                         const int *dij, int Nq, int M, int nff, int nd, int chmask,
-                                                        const double *scal, double2 *out)
+                                                        const double *scal, const int *qlist, double2 *out)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *s0 = reinterpret_cast<C2 *>(smem_raw);   // A^T, then A
     C2 *s1 = s0 + M * M;                         // L, then T^T
-    const int q = blockIdx.x, ch = blockIdx.y;
+    const int q = qlist ? qlist[blockIdx.x] : blockIdx.x, ch = blockIdx.y;
     const int M2 = M * M, h = M / 2, nt = h / 2;   // nt x nt threads own tiles
     double2 *o = out + ((size_t)ch * Nq + q) * M2;
     if (!((chmask >> ch) & 1)) {
@@ -140,14 +140,14 @@ __global__ void __launch_bounds__(256) vlv_tiled_kernel(const typename cpx<R>::t
 
 template <typename R>
 __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx<R>::t *Lc, const int *dij, int Nq,
-                                 int M, int nff, int ns2, int nd, int chmask, const double *scal, double2 *out)
+                                 int M, int nff, int ns2, int nd, int chmask, const double *scal, const int *qlist, double2 *out)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *sA = reinterpret_cast<C2 *>(smem_raw);
     C2 *sL = sA + M * M;
     C2 *sT = sL + M * M;
-    const int q = blockIdx.x, ch = blockIdx.y;
+    const int q = qlist ? qlist[blockIdx.x] : blockIdx.x, ch = blockIdx.y;
     const size_t M2 = (size_t)M * M;
     double2 *o = out + ((size_t)ch * Nq + q) * M2;
     if (!((chmask >> ch) & 1)) {
@@ -181,13 +181,46 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 
 }  // namespace
 
-cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out)
+// dX/dT of a symmetric state at the momenta that are not orbit representatives, gathered from their
+// representative q (element e, qmap[q'] = (list position, e)):
+//   out[ch][q'][r'][c'] = i^(qrow[r'] - qrow[c']) (conj ? conj(v) : v),  v = out[ch][q][srow[r']][srow[c']]
+// (W X W^dagger with W the element's bond permutation times its orbital-pair map).  Grid (M, Nq, 2).
+__global__ void sym_scatter_kernel(double2 *out, int Nq, int M, const int2 *qmap, const int *list, const SymElem *elem,
+                                   const int *srow, const int *qrow)
+{
+    const int r2 = blockIdx.x, q2 = blockIdx.y, ch = blockIdx.z, c2 = threadIdx.x;
+    const int2 ie = qmap[q2];
+    const int q = list[ie.x];
+    if (q == q2 || c2 >= M) return;   // representatives hold their own result
+    const int *sr = srow + ((size_t)ie.y * 2 + ch) * M, *qr = qrow + ((size_t)ie.y * 2 + ch) * M;
+    double2 v = out[(((size_t)ch * Nq + q) * M + sr[r2]) * M + sr[c2]];
+    if (elem[ie.y].conj) v.y = -v.y;
+    double2 w;
+    switch ((qr[r2] - qr[c2]) & 3) {
+    case 0: w = v; break;
+    case 1: w = make_double2(-v.y, v.x); break;
+    case 2: w = make_double2(-v.x, -v.y); break;
+    default: w = make_double2(v.y, -v.x); break;
+    }
+    out[(((size_t)ch * Nq + q2) * M + r2) * M + c2] = w;
+}
+
+cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
+{
+    PhaseScope ps(m, PH_VLV);
+    const int threads = (m->M + 31) / 32 * 32;
+    sym_scatter_kernel<<<dim3(m->M, m->Nq, 2), threads, 0, m->stream>>>(d_out, m->Nq, m->M, m->d_qmap, m->d_loop_list,
+                                                                        m->d_sym_elem, m->d_sym_srow, m->d_sym_qrow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist, int nlist)
 {
     const int M = m->M;
-    if (tc_supported(m)) return launch_vlv_tc(m, channel_mask, d_out);
-    if (M > 64) return launch_vlv_large(m, d_A, channel_mask, d_out);
+    if (tc_supported(m)) return launch_vlv_tc(m, channel_mask, d_out, qlist, nlist);
+    if (M > 64) return launch_vlv_large(m, d_A, channel_mask, d_out, qlist, nlist);
     const int ns2 = m->ns * m->ns;
-    dim3 grid(m->Nq, 2);
+    dim3 grid(qlist ? nlist : m->Nq, 2);
     PhaseScope ps(m, PH_VLV);
     if (ns2 == 4) {
         const int threads = std::max(32, ((M / 4) * (M / 4) + 31) / 32 * 32);   // <= 256 for M <= 64
@@ -196,13 +229,13 @@ cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, dou
             auto k = vlv_tiled_kernel<double>;
             if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k<<<grid, threads, smem, m->stream>>>(d_A, m->d_Lc, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask,
-                                                  m->d_scal, d_out);
+                                                  m->d_scal, qlist, d_out);
         } else {
             const size_t smem = 2 * sizeof(float2) * M * M;
             auto k = vlv_tiled_kernel<float>;
             if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k<<<grid, threads, smem, m->stream>>>(m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask,
-                                                  m->d_scal, d_out);
+                                                  m->d_scal, qlist, d_out);
         }
         return cudaGetLastError();
     }
@@ -212,13 +245,13 @@ cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, dou
         auto k = vlv_small_kernel<double>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, threads, smem, m->stream>>>(d_A, m->d_Lc, m->d_dij, m->Nq, M, m->nff, ns2, m->nd, channel_mask,
-                                              m->d_scal, d_out);
+                                              m->d_scal, qlist, d_out);
     } else {
         const size_t smem = 3 * sizeof(float2) * M * M;
         auto k = vlv_small_kernel<float>;
         if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, threads, smem, m->stream>>>(m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, ns2, m->nd,
-                                              channel_mask, m->d_scal, d_out);
+                                              channel_mask, m->d_scal, qlist, d_out);
     }
     return cudaGetLastError();
 }

@@ -135,6 +135,14 @@ struct tufrg_model {
     int2 *d_qmap = nullptr;         // [Nq] (list position of the orbit representative, group element)
     tufrg::SymElem *d_sym_elem = nullptr;   // [n_sym_elem]
     int *d_sym_dinv = nullptr;      // [n_sym_elem][nd] source d of target d' (Delta_d' = G Delta_d)
+    // symmetric states (flows from X = 0 with a symmetric bare vertex): X(G q) = W X(q) W^dagger with W the
+    // element's bond permutation times its orbital-pair map, so projections and products run for the orbit
+    // representatives only and dX/dT of the other momenta is gathered from them
+    bool sym_state = false;
+    bool sym_state_pays = false;    // autotuned at init: the representatives' products are faster
+    double sym_tune_ms[2] = {-1.0, -1.0};   // products for every momentum / representatives + gather
+    int *d_sym_srow = nullptr;      // [n_sym_elem][2][M] source index of every target row / column
+    int *d_sym_qrow = nullptr;      // [n_sym_elem][2][M] quarter turns of every target row / column
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
@@ -215,10 +223,13 @@ cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
 cudaError_t launch_loops(tufrg_model *m, int channel_mask);
 // The split path reads the FP32 copy of the state (d_state32), the plain path the FP64 state.
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask);
+// qlist (nlist entries): only these transfer momenta (the orbit representatives of a symmetric state)
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
-                           double2 *d_A);
+                           double2 *d_A, const int *qlist = nullptr, int nlist = 0);
 cudaError_t launch_to_f32(tufrg_model *m, const double2 *d_state, float2 *d_out, size_t n);
-cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
+// qlist (nlist entries): only these transfer momenta
+cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist = nullptr,
+                       int nlist = 0);
 cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const double2 *y, const FlowDev *fs,
                               const double *a, double2 *const *k, int nk, size_t n);
 cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn, const FlowDev *fs, const double *e,
@@ -228,7 +239,7 @@ cudaError_t launch_flow_init(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_decide(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0,
                                const double2 *k6, size_t n);
-cudaError_t launch_amax_locate(tufrg_model *m, size_t n);   // on the last projection (d_A or d_A32)
+cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
 int plan_gen_chunks(const tufrg_model *m);   // kx ranges per momentum of the multi-orbital loop kernel
 int dft_plan_nsplit(const tufrg_model *m);
@@ -236,10 +247,12 @@ bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
-cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out);
+cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist,
+                             int nlist);
+cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
 void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
-cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out);
+cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);
 cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
 cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu
 cudaError_t launch_loops2(tufrg_model *m, int ch);

@@ -83,7 +83,7 @@ def test_bad_descriptors_are_rejected_before_device_use(libpath):
     assert st == 1
     st, msg = init(spec.ff_R, precision=7)
     assert st == 1
-    st, msg = init(spec.ff_R, symmetry=7)
+    st, msg = init(spec.ff_R, symmetry=7)   # AUTO, OFF, STATES are 0, 1, 2
     assert st == 1 and "symmetry" in msg
     bad = hopt.copy()
     bad[0] *= 2.0   # breaks t_{-R} = t_R^dagger

@@ -154,6 +154,40 @@ def test_loops_symmetry(case):
         assert rel(L[ch], o.loops(0.07, ch)) < 2e-5
 
 
+@pytest.mark.parametrize("case,prec", [("rashba_ff9_Lf25", "SPLIT32"), ("rashba_ff13_Lf30", "SPLIT32"),
+                                       ("hubbard_ff5_Lf24", "FP64"), ("rashba_ff5_Lf24", "FP64"),
+                                       ("t2g_ff5_Lf8", "SPLIT32"), ("t2g_ff9_Lf10", "FP64")])
+def test_rhs_symmetric_state(case, prec):
+    """A state one Euler step from X = 0 has the loop symmetries (X(G q) = W X(q) W^dagger); the right-hand
+    side evaluated for the orbit representatives and written to the other momenta by symmetry equals the
+    full evaluation, and the oracle's."""
+    api = _api()
+    spec = (CASES.get(case) or T2G[case])()
+    m = api.Model(spec, getattr(api, prec), symmetry=api.SYMMETRY_STATES)   # representatives' path always
+    zero = m.zeros_state()
+    X1 = 0.05 * m.rhs(0.5, zero)
+    full = m.rhs(0.4, X1).cpu().numpy()
+    sym = m.rhs(0.4, X1, symmetric=True).cpu().numpy()
+    assert rel(sym, full) < (1e-12 if prec == "FP64" else 2e-6)
+    ref, _ = oracle.Oracle(spec).rhs(0.4, X1.cpu().numpy(), 3)
+    assert rel(sym, ref) < (TOL64 if prec == "FP64" else TOL32)
+
+
+@pytest.mark.parametrize("case,prec", [("rashba_ff9_Lf25", "SPLIT32"), ("hubbard_ff5_Lf24", "FP64")])
+def test_flow_symmetric_state_path(case, prec):
+    """Flows evaluate their (symmetric) states for the orbit representatives only; the result matches the flow
+    with every symmetry off."""
+    api = _api()
+    spec = CASES[case]()
+    y1, r1 = api.Model(spec, getattr(api, prec), symmetry=api.SYMMETRY_STATES).flow(stop=6.0)
+    y0, r0 = api.Model(spec, getattr(api, prec), symmetry=api.SYMMETRY_OFF).flow(stop=6.0)
+    assert r1["crossed"] == r0["crossed"]
+    if prec == "FP64":
+        assert r1["n_steps"] == r0["n_steps"]
+    assert abs(r1["Tc"] / r0["Tc"] - 1) < (1e-9 if prec == "FP64" else 1e-4)
+    assert rel(y1.cpu().numpy(), y0.cpu().numpy()) < (1e-9 if prec == "FP64" else 1e-4)
+
+
 def _paper_gather_terms(spec):
     """Independent enumeration of the gather terms from the printed projection formulas."""
     L = spec.Lq
