@@ -224,6 +224,8 @@ def main():
     ap.add_argument("--profile-rhs", type=int, default=0,
                     help="only evaluate this many split-precision right-hand sides on a seeded state (for ncu)")
     ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--profile-symmetric-states", action="store_true",
+                    help="with --profile-rhs: force the orbit-representative projections and products")
     ap.add_argument("--batch-flows", type=int, default=0,
                     help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
@@ -243,7 +245,8 @@ def main():
     import numpy as np
     import torch
     from paper_1710_08830_gb300 import inputs
-    from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, SYMMETRIC_STATE, SYMMETRY_OFF, Model
+    from paper_1710_08830_gb300.api import (FP64, PRODUCTS_SIMT, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO, SYMMETRY_OFF,
+                                            SYMMETRY_STATES, Model)
 
     torch.cuda.set_device(local)
     if args.products_sweep:
@@ -252,10 +255,11 @@ def main():
     if args.profile_rhs > 0:
         # a short, fixed launch sequence for profilers: model set-up, then N right-hand sides
         spec = inputs.rashba_q24_k8_ff9(0)
-        m = Model(spec, SPLIT32 if args.profile_precision == "split" else FP64)
+        m = Model(spec, SPLIT32 if args.profile_precision == "split" else FP64,
+                  symmetry=SYMMETRY_STATES if args.profile_symmetric_states else SYMMETRY_AUTO)
         st = torch.from_numpy(inputs.random_state(spec, seed=1, scale=0.2)).cuda()
         for _ in range(args.profile_rhs):
-            m.rhs(T_BENCH, st)
+            m.rhs(T_BENCH, st, symmetric=True)   # the timed loop's path (the values do not change the launches)
         torch.cuda.synchronize()
         print(json.dumps({"profile_rhs": args.profile_rhs, "workload": WORKLOAD}))
         return
@@ -473,6 +477,8 @@ def main():
                        "precision": "split (FP32 loop sums, FP64 state)",
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "loop_momenta_summed": m32.n_loop_q, "symmetric_state": True,
+                       "symmetric_state_path": m32.symmetric_state_path,
+                       "symmetric_state_tuning_ms": m32.symmetric_state_tuning_ms,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},
             "split_vs_fp64_maxrel": err_split,
             "fp64_gpu": ({"value": fp64_rate, "unit": "RHS/s", "speedup_split": value / world / fp64_rate,

@@ -150,6 +150,13 @@ tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc
  * reduce them, see TUFRG_SYMMETRY_AUTO). */
 tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
 
+/* Symmetric-state path (TUFRG_SYMMETRIC_STATE): *in_use = 1 when calls that set the flag project and
+ * multiply at the orbit representatives only, 0 when they take the general path (the state symmetries
+ * do not hold for this model, or the representatives' path was not faster at init).  *ms_general and
+ * *ms_reps are the init-time timings of projections + products of both channels on the two paths in
+ * milliseconds (-1 when not measured).  Errors: TUFRG_EINVAL for NULL arguments. */
+tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps);
+
 /* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */
 tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out);
 

@@ -69,6 +69,10 @@ class Model:
         nl = C.c_int()
         self._check(self._L.tufrg_loop_momenta(self._h, C.byref(nl)))
         self.n_loop_q = nl.value   # transfer momenta whose loop k-sums run directly
+        su, t_gen, t_rep = C.c_int(), C.c_double(), C.c_double()
+        self._check(self._L.tufrg_symmetry_info(self._h, C.byref(su), C.byref(t_gen), C.byref(t_rep)))
+        self.symmetric_state_path = bool(su.value)   # rhs(symmetric=True) works at the representatives only
+        self.symmetric_state_tuning_ms = {"general": t_gen.value, "representatives": t_rep.value}
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, st: int):

@@ -458,7 +458,7 @@ void release(tufrg_model *m)
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
-                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow};
+                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -491,12 +491,13 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
         d_state32 = m->d_X32;
     }
     CK(launch_fermi(m), "fermi tables");
-    CK(launch_loops(m, mask), "loop k-sum");
+    // a symmetric state's products read the loops of the orbit representatives only
+    CK(launch_loops(m, mask, sym), "loop k-sum");
     CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
     // the split path's products read the FP32 copy only
     CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A, ql, nl), "projections");
-    CK(launch_vlv(m, m->d_A, mask, d_out, ql, nl), "V.L.V products");
-    if (sym) CK(launch_sym_scatter(m, d_out), "symmetric scatter");
+    if (sym) CK(launch_products_sym(m, mask, d_out), "V.L.V products (orbit representatives)");
+    else CK(launch_vlv(m, m->d_A, mask, d_out), "V.L.V products");
     return TUFRG_OK;
 }
 
@@ -777,6 +778,28 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                 m->sym_state = true;
                 CK(upload(&m->d_sym_srow, srow, m->stream), "upload symmetry tables");
                 CK(upload(&m->d_sym_qrow, qrow, m->stream), "upload symmetry tables");
+                if (orbit_products_supported(m)) {
+                    // fused orbit products: the momenta of every orbit and, per element and channel, the
+                    // source entry, quarter turns and conjugation of every target entry
+                    std::vector<int> ofs(m->n_loop_q + 1, 0), oq(m->Nq);
+                    for (int q = 0; q < m->Nq; q++) ofs[ls.qmap[q].x + 1]++;
+                    for (int p = 0; p < m->n_loop_q; p++) ofs[p + 1] += ofs[p];
+                    std::vector<int> fill(ofs.begin(), ofs.end() - 1);
+                    for (int q = 0; q < m->Nq; q++) oq[fill[ls.qmap[q].x]++] = q;
+                    const int M = m->M;
+                    std::vector<int> emap((size_t)ls.elem.size() * 2 * M * M);
+                    for (size_t e = 0; e < ls.elem.size(); e++)
+                        for (int ch = 0; ch < 2; ch++) {
+                            const int *sr = &srow[(e * 2 + ch) * M], *qr = &qrow[(e * 2 + ch) * M];
+                            for (int r = 0; r < M; r++)
+                                for (int c = 0; c < M; c++)
+                                    emap[((e * 2 + ch) * M + r) * M + c] =
+                                        (sr[r] * M + sr[c]) << 3 | ((qr[r] - qr[c]) & 3) << 1 | (ls.elem[e].conj ? 1 : 0);
+                        }
+                    CK(upload(&m->d_orb_ofs, ofs, m->stream), "upload symmetry tables");
+                    CK(upload(&m->d_orb_q, oq, m->stream), "upload symmetry tables");
+                    CK(upload(&m->d_sym_emap, emap, m->stream), "upload symmetry tables");
+                }
             }
         }
     }
@@ -870,8 +893,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if (ns != 2) {
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
         m->gen_chunks = plan_gen_chunks(m);
-        // FP64 accumulators of one channel: one slot per (kx range, directly summed momentum)
-        m->part_bytes = (size_t)m->gen_chunks * m->n_loop_q * m->nd * ns4 * sizeof(double2);
+        // accumulators of one channel: one slot per (kx range, directly summed momentum), plus the FP64
+        // range sums of the representatives under symmetry
+        m->part_bytes = gen_part_bytes(m);
     }
     m->products = split ? (d.products == TUFRG_PRODUCTS_AUTO ? TUFRG_PRODUCTS_TC : d.products) : TUFRG_PRODUCTS_SIMT;
     if (split && d.products != TUFRG_PRODUCTS_SIMT) {
@@ -959,17 +983,21 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
     }
     if (m->sym_state) {
-        // symmetric states: products for the orbit representatives plus the gather of the other momenta,
-        // against products for every momentum (on zeroed operands: the cost does not depend on the values);
-        // the representatives' path is used only where it is faster
+        // symmetric states: projections and products for the orbit representatives plus the gather of the
+        // other momenta, against both for every momentum (on zeroed operands: the cost does not depend on
+        // the values); the representatives' path is used only where it is faster
         const size_t nA = 2 * (size_t)m->Nq * M2;
         double2 *tmp = nullptr;
         CK(dalloc(&tmp, nA), "cudaMalloc autotune output");
+        CK(cudaMemsetAsync(tmp, 0, sizeof(double2) * nA, m->stream), "zero");
         if (split) {
             CK(cudaMemsetAsync(m->d_A32, 0, sizeof(float2) * nA, m->stream), "zero");
+            CK(cudaMemsetAsync(m->d_X32, 0, sizeof(float2) * nA, m->stream), "zero");
+            CK(cudaMemsetAsync(m->d_Xr32, 0, sizeof(float2) * 2 * (size_t)m->ncls * M2, m->stream), "zero");
             CK(cudaMemsetAsync(m->d_Lc32, 0, sizeof(float2) * 2 * (size_t)m->Nq * m->nd * ns4, m->stream), "zero");
         } else {
             CK(cudaMemsetAsync(m->d_A, 0, sizeof(double2) * nA, m->stream), "zero");
+            CK(cudaMemsetAsync(m->d_Xr, 0, sizeof(double2) * 2 * (size_t)m->ncls * M2, m->stream), "zero");
             CK(cudaMemsetAsync(m->d_Lc, 0, sizeof(double2) * 2 * (size_t)m->Nq * m->nd * ns4, m->stream), "zero");
         }
         CK(launch_set_scalars(m, 1.0, 1.0), "set scalars");
@@ -978,9 +1006,12 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaEventCreate(&e1), "event");
         for (int c = 0; c < 2; c++) {
             auto run = [&]() -> cudaError_t {
-                if (c == 0) return launch_vlv(m, m->d_A, 3, tmp);
-                cudaError_t e = launch_vlv(m, m->d_A, 3, tmp, m->d_loop_list, m->n_loop_q);
-                return e == cudaSuccess ? launch_sym_scatter(m, tmp) : e;
+                // the FP64 path projects the (zero) state in tmp into d_A; the products then overwrite tmp
+                const int *ql = c ? m->d_loop_list : nullptr;
+                const int nl = c ? m->n_loop_q : 0;
+                cudaError_t e = launch_project(m, tmp, split ? m->d_X32 : nullptr, 3, split ? nullptr : m->d_A, ql, nl);
+                if (e == cudaSuccess) e = c ? launch_products_sym(m, 3, tmp) : launch_vlv(m, m->d_A, 3, tmp);
+                return e;
             };
             CK(run(), "symmetric-state autotune warm-up");
             CK(cudaEventRecord(e0, m->stream), "event");
@@ -1018,6 +1049,15 @@ tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct)
 {
     if (!m || !n_direct) return TUFRG_EINVAL;
     *n_direct = m->n_loop_q;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps)
+{
+    if (!m || !in_use || !ms_general || !ms_reps) return TUFRG_EINVAL;
+    *in_use = m->sym_state && m->sym_state_pays ? 1 : 0;
+    *ms_general = m->sym_state ? m->sym_tune_ms[0] : -1.0;
+    *ms_reps = m->sym_state ? m->sym_tune_ms[1] : -1.0;
     return TUFRG_OK;
 }
 

@@ -279,18 +279,19 @@ __device__ __forceinline__ double2 to64(double2 v) { return v; }
 __device__ __forceinline__ double2 to64(float2 v) { return make_double2(widen_f(v.x), widen_f(v.y)); }
 
 // Grid: blockIdx.y = transfer momentum (list position), threads over (d, ab) = t (t >> 4, t & 15):
-// no runtime integer division (this GPU issues its conversions to the slow FP64 pipe).
+// no runtime integer division (this GPU issues its conversions to the slow FP64 pipe).  List position s
+// is written at momentum qout[s] (orbit representatives only) or at s.
 template <typename R>
 __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
-                                    const int *dslot, const int *deltas, int nd, double inv_nk, double2 *out64,
-                                    typename cpx<R>::t *out32, const int *skip)
+                                    const int *dslot, const int *deltas, int nd, double inv_nk, const int *qout,
+                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
 {
     if (skip && *skip) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nd * NS4) return;
     const int s = blockIdx.y, d = t / NS4, ab = t % NS4;
     const auto v = reduce_one<R>(part, n_part, ndx, ndyh, dslot, deltas, s, d, ab, R(inv_nk));
-    const size_t idx = (size_t)s * nd * NS4 + t;
+    const size_t idx = (size_t)(qout ? qout[s] : s) * nd * NS4 + t;
     if (out64) out64[idx] = to64(v);
     if (out32) out32[idx] = v;
 }
@@ -387,15 +388,16 @@ cudaError_t launch_loops_reduce_f32(tufrg_model *m, const float2 *part, int n_s,
     reduce_shape(m, n_s, grid, thr);
     PhaseScope ps(m, PH_LOOPRED);
     loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(part, m->plan.n_partials, (int)m->dxs.size(), ndyh,
-                                                          m->d_dslot, m->d_deltas, m->nd, 1.0 / (double)m->Nk, out64,
-                                                          out32, skip);
+                                                          m->d_dslot, m->d_deltas, m->nd, 1.0 / (double)m->Nk, nullptr,
+                                                          out64, out32, skip);
     return cudaGetLastError();
 }
 
-cudaError_t launch_loops(tufrg_model *m, int channel_mask)
+cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
 {
     if (m->sur) TUFRG_CUDA_TRY(launch_surrogate(m, channel_mask));
-    if (m->ns != NS) return loops_gen_supported(m) ? launch_loops_gen(m, channel_mask) : cudaErrorNotSupported;
+    reps_only = reps_only && m->sym;
+    if (m->ns != NS) return loops_gen_supported(m) ? launch_loops_gen(m, channel_mask, reps_only) : cudaErrorNotSupported;
     const LoopPlan &pl = m->plan;
     const int ndx = (int)m->dxs.size();
     int ndyh = 0;
@@ -410,9 +412,13 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             const size_t off = (size_t)ch * m->Nq * m->nd * NS4;
             dim3 grid;
             int thr;
-            reduce_shape(m, m->Nq, grid, thr);
+            reduce_shape(m, reps_only ? m->n_loop_q : m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
-            if (m->sym)
+            if (reps_only)   // the representatives' FP32 loops at their own momenta (what their products read)
+                loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
+                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
+                    inv_nk, m->d_loop_list, nullptr, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
+            else if (m->sym)
                 loops_reduce_sym_kernel<float><<<grid, thr, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, inv_nk, m->d_Lc + off, m->d_Lc32 + off,
@@ -420,7 +426,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             else
                 loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
                     reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    inv_nk, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
+                    inv_nk, nullptr, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};
@@ -448,7 +454,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             reduce_shape(m, m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<double><<<grid, thr, 0, m->stream>>>(
-                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk,
+                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk, nullptr,
                 m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else {
@@ -477,7 +483,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask)
             reduce_shape(m, m->Nq, grid, thr);
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
-                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk,
+                a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk, nullptr,
                 m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4, nullptr);
             TUFRG_CUDA_TRY(cudaGetLastError());
         }

@@ -14,6 +14,8 @@
 // e^{-i kx dx} W into the FP64 accumulator of its own entries (no other CTA touches this s, so no
 // atomics; the order is fixed).  A final kernel writes the other Hermitian half,
 // L(-d)[b][a] = conj(L(d)[a][b]), and scales by 1/Nk.
+#include <cmath>
+
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -54,6 +56,18 @@ template <typename C2> __device__ __forceinline__ void cfma(C2 &acc, C2 a, C2 b)
 __device__ __forceinline__ void ldft(const FermiEntry *p, double &e, double &g, double &gp) { e = p->e; g = p->g; gp = p->gp; }
 __device__ __forceinline__ void ldft(const FermiEntry32 *p, float &e, float &g, float &gp) { e = p->e; g = p->g; gp = p->gp; }
 
+// v in [0, 2 L) -> v mod L without a division
+__device__ __forceinline__ int wrap1(int v, int L) { return v >= L ? v - L : v; }
+
+// Shared memory of one CTA: phase table [Lf], rho1 / T / rho2' [KB][NS][NS^2] each, batch phases
+// [KB][NDYH], pair weights [KB][NS][NS].
+template <typename R, int NS, int NDYH>
+size_t gen_smem(int Lf)
+{
+    using C2 = typename cpx<R>::t;
+    return sizeof(C2) * (Lf + 3 * KB * NS * NS * NS + KB * NDYH) + sizeof(R) * KB * NS * NS;
+}
+
 template <int WHICH, typename R>
 __device__ __forceinline__ R gweight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr)
 {
@@ -73,12 +87,14 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     constexpr int NS2 = NS * NS;
     constexpr int GA = NS2 / TA, GB = NS2 / TB;     // thread grid over (a, b) tiles
     constexpr int NT = GA * GB;
+    static_assert(NT >= KB * NDYH, "batch phases are staged by one thread each");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *ptab = reinterpret_cast<C2 *>(smem_raw);                    // [Lf] e^{-2 pi i n / Lf}
     C2 *sA = ptab + a.Lf;                                          // [KB][NS][NS2] rho1
     C2 *sB = sA + KB * NS * NS2;                                   // [KB][NS][NS2] T
     C2 *sR2 = sB + KB * NS * NS2;                                  // [KB][NS][NS2] rho2'
-    R *sW = reinterpret_cast<R *>(sR2 + KB * NS * NS2);            // [KB][NS][NS] pair weights
+    C2 *sPh = sR2 + KB * NS * NS2;                                 // [KB][NDYH] e^{-i ky dy} of the batch
+    R *sW = reinterpret_cast<R *>(sPh + KB * NDYH);                // [KB][NS][NS] pair weights
     const int Lf = a.Lf;
     for (int n = threadIdx.x; n < Lf; n += blockDim.x) {
         double sn, cs;
@@ -101,16 +117,22 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             for (int i = 0; i < TA; i++)
 #pragma unroll
                 for (int j = 0; j < TB; j++) W[d][i][j] = mk(R(0), R(0));
+        // row offsets of the shifted columns: (s - k)_x (P) and (k - s)_x (C) on the fine mesh
+        const int k1x = wrap1(sx - kx + Lf, Lf) * Lf, k2x = wrap1(kx - sx + Lf, Lf) * Lf;
         for (int ky0 = 0; ky0 < Lf; ky0 += KB) {
             const int nb = min(KB, Lf - ky0);
             __syncthreads();   // previous batch fully consumed
+            if (threadIdx.x < KB * NDYH) {
+                const int kb = threadIdx.x / NDYH, d = threadIdx.x % NDYH;
+                if (kb < nb && d < a.ndyh) sPh[threadIdx.x] = ptab[((ky0 + kb) * a.dys[d]) % Lf];
+            }
             // stage projectors of the batch: rho1 (k1 side) into sA, rho2' (k2 side) into sR2
             for (int idx = threadIdx.x; idx < nb * NS * NS2; idx += blockDim.x) {
                 const int kb = idx / (NS * NS2), r = idx % (NS * NS2), l = r / NS2, p = r % NS2;
                 const int t = p / NS, tp = p % NS;
                 const int ky = ky0 + kb;
-                const int k1 = WHICH == 0 ? ((sx - kx + Lf) % Lf) * Lf + (sy - ky + Lf) % Lf : kx * Lf + ky;
-                const int k2 = WHICH == 0 ? kx * Lf + ky : ((kx - sx + Lf) % Lf) * Lf + (ky - sy + Lf) % Lf;
+                const int k1 = WHICH == 0 ? k1x + wrap1(sy - ky + Lf, Lf) : kx * Lf + ky;
+                const int k2 = WHICH == 0 ? kx * Lf + ky : k2x + wrap1(ky - sy + Lf, Lf);
                 const C2 u = a.U[(size_t)k1 * NS2 + t * NS + l], v = a.U[(size_t)k1 * NS2 + tp * NS + l];
                 sA[idx] = mk(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);          // u conj(v)
                 const C2 x = a.U[(size_t)k2 * NS2 + t * NS + l], y = a.U[(size_t)k2 * NS2 + tp * NS + l];
@@ -120,8 +142,8 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             for (int idx = threadIdx.x; idx < nb * NS * NS; idx += blockDim.x) {
                 const int kb = idx / (NS * NS), l1 = (idx / NS) % NS, l2 = idx % NS;
                 const int ky = ky0 + kb;
-                const int k1 = WHICH == 0 ? ((sx - kx + Lf) % Lf) * Lf + (sy - ky + Lf) % Lf : kx * Lf + ky;
-                const int k2 = WHICH == 0 ? kx * Lf + ky : ((kx - sx + Lf) % Lf) * Lf + (ky - sy + Lf) % Lf;
+                const int k1 = WHICH == 0 ? k1x + wrap1(sy - ky + Lf, Lf) : kx * Lf + ky;
+                const int k2 = WHICH == 0 ? kx * Lf + ky : k2x + wrap1(ky - sy + Lf, Lf);
                 R e1, g1, gp1, e2, g2, gp2;
                 ldft(&a.ft[(size_t)k1 * NS + l1], e1, g1, gp1);
                 ldft(&a.ft[(size_t)k2 * NS + l2], e2, g2, gp2);
@@ -144,7 +166,6 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             __syncthreads();
             if (active) {
                 for (int kb = 0; kb < nb; kb++) {
-                    const int ky = ky0 + kb;
                     C2 Y[TA][TB];
 #pragma unroll
                     for (int i = 0; i < TA; i++)
@@ -165,7 +186,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
 #pragma unroll
                     for (int d = 0; d < NDYH; d++) {
                         if (d >= a.ndyh) break;
-                        const C2 ph = ptab[(ky * a.dys[d]) % Lf];
+                        const C2 ph = sPh[kb * NDYH + d];
 #pragma unroll
                         for (int i = 0; i < TA; i++)
 #pragma unroll
@@ -222,21 +243,41 @@ __device__ __forceinline__ double2 gen_value(const C2 *acc, size_t chunk_stride,
     return make_double2(re, half ? im : -im);
 }
 
+// blockIdx.y = accumulator slot s (n_slot of them), written at momentum qout[s] (orbit representatives
+// only) or at s.
 template <int NS, typename C2>
-__global__ void loops_gen_finish(const C2 *acc, int nchunk, const int *deltas, int nd, int Nq, double inv_nk,
-                                 const int *partner, double2 *out64, float2 *out32)
+__global__ void loops_gen_finish(const C2 *acc, int nchunk, int n_slot, const int *deltas, int nd, double inv_nk,
+                                 const int *partner, const int *qout, double2 *out64, float2 *out32)
 {
     constexpr int NS2 = NS * NS, NS4 = NS2 * NS2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nd * NS4) return;
     const int s = blockIdx.y, d = t / NS4, ia = (t / NS2) % NS2, ib = t % NS2;
     const size_t per = (size_t)nd * NS4;
-    double2 v = gen_value<NS>(acc, (size_t)Nq * per, nchunk, (size_t)s * per, d, ia, ib, deltas, partner);   // C2 deduced
+    double2 v = gen_value<NS>(acc, (size_t)n_slot * per, nchunk, (size_t)s * per, d, ia, ib, deltas, partner);   // C2 deduced
     v.x *= inv_nk;
     v.y *= inv_nk;
-    const size_t o = (size_t)s * per + t;
-    out64[o] = v;
+    const size_t o = (size_t)(qout ? qout[s] : s) * per + t;
+    if (out64) out64[o] = v;
     if (out32) out32[o] = make_float2((float)v.x, (float)v.y);
+}
+
+// Sum of the kx ranges per accumulator slot (fixed order, FP64), before the symmetric gather: the gather
+// reads every slot Nq / n_slot times, so it must read one L2-resident value, not one per range from DRAM.
+// Grid: (elements / 256, slot).
+template <typename C2>
+__global__ void loops_gen_chunk_sum(const C2 *acc, int nchunk, int n_slot, int per, double2 *red)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= per) return;
+    const size_t o = (size_t)blockIdx.y * per + t, stride = (size_t)n_slot * per;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; c++) {
+        const C2 w = acc[(size_t)c * stride + o];
+        re += (double)w.x;
+        im += (double)w.y;
+    }
+    red[o] = make_double2(re, im);
 }
 
 // Symmetric variant: blockIdx.y = output momentum q'; qmap[q'] = (accumulator slot of its orbit
@@ -278,7 +319,7 @@ cudaError_t launch_gen(tufrg_model *m, const GenArgs<R> &a)
     constexpr int NS2 = NS * NS;
     constexpr int NT = (NS2 / TA) * (NS2 / TB);
     const int threads = ((NT + 31) / 32) * 32;
-    const size_t smem = sizeof(C2) * (m->Lf + 3 * KB * NS * NS2) + sizeof(R) * KB * NS * NS;
+    const size_t smem = gen_smem<R, NS, NDYH>(m->Lf);
     auto kern = loops_gen_kernel<R, NS, TA, TB, NDYH, WHICH>;
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PhaseScope ps(m, PH_LOOPS);
@@ -328,21 +369,31 @@ bool loops_gen_supported(const tufrg_model *m)
 namespace {
 
 // Resident CTAs per SM of the instantiation the model launches, and the kx ranges per momentum that
-// fill the GPU (at least one wave, at least 4 columns per range).
+// fill the GPU best (at least 4 columns per range).
 template <typename R, int NS, int TA, int TB>
 int gen_blocks_per_sm(const tufrg_model *m, int ndyh)
 {
-    using C2 = typename cpx<R>::t;
     constexpr int NS2 = NS * NS, NT = (NS2 / TA) * (NS2 / TB);
     const int threads = ((NT + 31) / 32) * 32;
-    const size_t smem = sizeof(C2) * (m->Lf + 3 * KB * NS * NS2) + sizeof(R) * KB * NS * NS;
     int n = 0;
-    cudaError_t e = ndyh <= 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 3, 0>, threads, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 5, 0>, threads, smem);
+    cudaError_t e = ndyh <= 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 3, 0>, threads, gen_smem<R, NS, 3>(m->Lf))
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops_gen_kernel<R, NS, TA, TB, 5, 0>, threads, gen_smem<R, NS, 5>(m->Lf));
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 }  // namespace
+
+size_t gen_red_offset(const tufrg_model *m)
+{
+    const size_t ns2 = (size_t)m->ns * m->ns;
+    return (size_t)m->gen_chunks * m->n_loop_q * m->nd * ns2 * ns2 * sizeof(double2);
+}
+
+size_t gen_part_bytes(const tufrg_model *m)
+{
+    const size_t ns2 = (size_t)m->ns * m->ns;
+    return gen_red_offset(m) + (m->sym ? (size_t)m->n_loop_q * m->nd * ns2 * ns2 * sizeof(double2) : 0);
+}
 
 int plan_gen_chunks(const tufrg_model *m)
 {
@@ -351,10 +402,16 @@ int plan_gen_chunks(const tufrg_model *m)
     int per_sm;
     if (m->precision == TUFRG_FP64) per_sm = m->ns == 6 ? gen_blocks_per_sm<double, 6, 2, 3>(m, ndyh) : gen_blocks_per_sm<double, 4, 2, 2>(m, ndyh);
     else per_sm = m->ns == 6 ? gen_blocks_per_sm<float, 6, 4, 3>(m, ndyh) : gen_blocks_per_sm<float, 4, 2, 2>(m, ndyh);
+    // minimise (waves) x (columns per range): a grid just over one wave doubles the time
     const long slots = (long)m->sm_count * per_sm;
-    int c = (int)((slots + m->n_loop_q - 1) / m->n_loop_q);
-    c = std::max(1, std::min(c, std::min(16, m->Lf / 4)));
-    return c;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int c = 1; c <= std::min(16, std::max(1, m->Lf / 4)); c++) {
+        const double waves = std::ceil((double)m->n_loop_q * c / (double)slots);
+        const double cost = waves * std::ceil((double)m->Lf / c);
+        if (cost < best_cost * 0.999) { best_cost = cost; best = c; }
+    }
+    return best;
 }
 
 namespace {
@@ -369,13 +426,14 @@ void fill_chunks(const tufrg_model *m, GenArgs<R> &a)
 
 }  // namespace
 
-cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask)
+cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only)
 {
     const size_t ns2 = (size_t)m->ns * m->ns, per = (size_t)m->Nq * m->nd * ns2 * ns2;
     const int n_slot = m->sym ? m->n_loop_q : m->Nq;
     const size_t acc_n = (size_t)m->gen_chunks * n_slot * m->nd * ns2 * ns2;
     for (int ch = 0; ch < 2; ch++) {
-        if (!((channel_mask >> ch) & 1)) continue;        const bool fp64 = m->precision == TUFRG_FP64;
+        if (!((channel_mask >> ch) & 1)) continue;
+        const bool fp64 = m->precision == TUFRG_FP64;
         TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_part, 0, (fp64 ? sizeof(double2) : sizeof(float2)) * acc_n, m->stream));
         cudaError_t e;
         if (fp64) {
@@ -401,28 +459,33 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask)
         const double2 *a64 = reinterpret_cast<const double2 *>(m->d_part);
         const float2 *a32 = reinterpret_cast<const float2 *>(m->d_part);
         const int nc = m->gen_chunks;
-        if (m->sym) {
+        auto finish = [&](dim3 g, int n_s, const int *qout, double2 *w64, float2 *w32) {
             if (m->ns == 6 && fp64)
-                loops_gen_finish_sym<6><<<grid, 256, 0, m->stream>>>(a64, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
-                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+                loops_gen_finish<6><<<g, 256, 0, m->stream>>>(a64, nc, n_s, m->d_deltas, m->nd, inv_nk, m->d_dpartner, qout, w64, w32);
             else if (m->ns == 6)
-                loops_gen_finish_sym<6><<<grid, 256, 0, m->stream>>>(a32, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
-                                                                     m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
+                loops_gen_finish<6><<<g, 256, 0, m->stream>>>(a32, nc, n_s, m->d_deltas, m->nd, inv_nk, m->d_dpartner, qout, w64, w32);
             else if (fp64)
-                loops_gen_finish_sym<4><<<grid, 256, 0, m->stream>>>(a64, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                loops_gen_finish<4><<<g, 256, 0, m->stream>>>(a64, nc, n_s, m->d_deltas, m->nd, inv_nk, m->d_dpartner, qout, w64, w32);
+            else
+                loops_gen_finish<4><<<g, 256, 0, m->stream>>>(a32, nc, n_s, m->d_deltas, m->nd, inv_nk, m->d_dpartner, qout, w64, w32);
+        };
+        if (reps_only) {
+            // the representatives at their own momenta; the split path's products read the FP32 loops only
+            finish(dim3((n4 + 255) / 256, n_slot), n_slot, m->d_loop_list, fp64 ? o64 : nullptr, o32);
+        } else if (m->sym) {
+            // the kx ranges summed per representative (same order as the plain finish), then the gather
+            double2 *red = reinterpret_cast<double2 *>(static_cast<char *>(m->d_part) + gen_red_offset(m));
+            const dim3 g1((n4 + 255) / 256, n_slot);
+            if (fp64) loops_gen_chunk_sum<<<g1, 256, 0, m->stream>>>(a64, nc, n_slot, n4, red);
+            else loops_gen_chunk_sum<<<g1, 256, 0, m->stream>>>(a32, nc, n_slot, n4, red);
+            if (m->ns == 6)
+                loops_gen_finish_sym<6><<<grid, 256, 0, m->stream>>>(red, 1, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
                                                                      m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
             else
-                loops_gen_finish_sym<4><<<grid, 256, 0, m->stream>>>(a32, nc, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
+                loops_gen_finish_sym<4><<<grid, 256, 0, m->stream>>>(red, 1, n_slot, m->d_deltas, m->nd, inv_nk, m->d_dpartner,
                                                                      m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, o64, o32);
         } else {
-            if (m->ns == 6 && fp64)
-                loops_gen_finish<6><<<grid, 256, 0, m->stream>>>(a64, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
-            else if (m->ns == 6)
-                loops_gen_finish<6><<<grid, 256, 0, m->stream>>>(a32, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
-            else if (fp64)
-                loops_gen_finish<4><<<grid, 256, 0, m->stream>>>(a64, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
-            else
-                loops_gen_finish<4><<<grid, 256, 0, m->stream>>>(a32, nc, m->d_deltas, m->nd, m->Nq, inv_nk, m->d_dpartner, o64, o32);
+            finish(grid, m->Nq, nullptr, o64, o32);
         }
         TUFRG_CUDA_TRY(cudaGetLastError());
     }

@@ -285,30 +285,41 @@ cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_s
 
 constexpr int PROJ_QT = 8;   // transfer momenta per thread
 
+// FP64 tables on the plain path, their FP32 copies on the split path (where d_A may be NULL)
+template <typename R, typename XT, int QT>
+cudaError_t project_run(tufrg_model *m, const XT *d_state, const typename cpx<R>::t *Xr, const XT *v0d0, const XT *v0d1,
+                        const typename cpx<R>::t *ph, int channel_mask, const int *qlist, int nlist, double2 *d_A,
+                        float2 *d_A32)
+{
+    const int M2 = m->M * m->M;
+    const dim3 grid((M2 + 255) / 256, (nlist + QT - 1) / QT, 2);
+    const size_t smem = sizeof(typename cpx<R>::t) * QT * m->nph;
+    auto k = project_kernel<R, XT, QT>;
+    if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, 256, smem, m->stream>>>(d_state, Xr, v0d0, v0d1, m->d_eofs[0], m->d_eofs[1], m->d_eterms[0],
+                                      m->d_eterms[1], ph, m->nph, m->Nq, M2, m->ncls, channel_mask, qlist, nlist, d_A,
+                                      d_A32, m->d_amax);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
                            double2 *d_A, const int *qlist, int nlist)
 {
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax, 0, sizeof(unsigned long long), m->stream));
     const int M2 = m->M * m->M;
     if (!qlist) nlist = m->Nq;
-    dim3 grid((M2 + 255) / 256, (nlist + PROJ_QT - 1) / PROJ_QT, 2);
+    const int xb = (M2 + 255) / 256;
+    // QT momenta share each gathered source value; a short list (orbit representatives) takes QT = 2 so
+    // that its grid still covers the GPU
+    const bool short_list = (long)((nlist + PROJ_QT - 1) / PROJ_QT) * xb * 2 < 2L * m->sm_count;
     PhaseScope ps(m, PH_PROJ);
     if (m->precision == TUFRG_FP64) {
-        const size_t smem = sizeof(double2) * PROJ_QT * m->nph;
-        auto k = project_kernel<double, double2, PROJ_QT>;
-        if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, 256, smem, m->stream>>>(d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_eofs[0], m->d_eofs[1],
-                                          m->d_eterms[0], m->d_eterms[1], m->d_ph, m->nph, m->Nq, M2, m->ncls,
-                                          channel_mask, qlist, nlist, d_A, nullptr, m->d_amax);
-    } else {
-        const size_t smem = sizeof(float2) * PROJ_QT * m->nph;
-        auto k = project_kernel<float, float2, PROJ_QT>;
-        if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, 256, smem, m->stream>>>(d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_eofs[0], m->d_eofs[1],
-                                          m->d_eterms[0], m->d_eterms[1], m->d_ph32, m->nph, m->Nq, M2, m->ncls,
-                                          channel_mask, qlist, nlist, d_A, m->d_A32, m->d_amax);   // d_A may be NULL here
+        auto run = short_list ? project_run<double, double2, 2> : project_run<double, double2, PROJ_QT>;
+        return run(m, d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_ph, channel_mask, qlist, nlist, d_A, nullptr);
     }
-    return cudaGetLastError();
+    auto run = short_list ? project_run<float, float2, 2> : project_run<float, float2, PROJ_QT>;
+    return run(m, d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_ph32, channel_mask, qlist, nlist, d_A,
+               m->d_A32);
 }
 
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only)

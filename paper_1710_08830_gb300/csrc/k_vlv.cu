@@ -65,6 +65,130 @@ __device__ __forceinline__ void tile44(const C2 *Xt, const C2 *Y, int M, int r, 
     }
 }
 
+// The same contraction for the 2 x 2 tile with rows {r, r+1} and columns {c, c+1} (r, c even): every
+// output element sees the same sequence of complex FMAs over k as in tile44.
+template <typename C2>
+__device__ __forceinline__ void tile22(const C2 *Xt, const C2 *Y, int M, int r, int c, C2 acc[2][2])
+{
+    for (int k = 0; k < M; k++) {
+        C2 a0, a1, b0, b1;
+        ld2(Xt + k * M + r, a0, a1);
+        ld2(Y + k * M + c, b0, b1);
+        cfma(acc[0][0], a0, b0);
+        cfma(acc[0][1], a0, b1);
+        cfma(acc[1][0], a1, b0);
+        cfma(acc[1][1], a1, b1);
+    }
+}
+
+// an FP32 value widened exactly to FP64 on the integer pipe
+__device__ __forceinline__ void store_w(double2 *o, float2 v)
+{
+    const uint2 re = widen_bits(v.x), im = widen_bits(v.y);
+    *reinterpret_cast<uint4 *>(o) = make_uint4(re.y, re.x, im.y, im.x);
+}
+
+__device__ __forceinline__ float2 quarter_turn(float2 v, int k)
+{
+    switch (k & 3) {
+    case 0: return v;
+    case 1: return make_float2(-v.y, v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    default: return make_float2(v.y, -v.x);
+    }
+}
+
+// Symmetric states, two-band bond sets (M = 4 N_ff <= 64), split path.  One CTA per (orbit
+// representative q, channel) forms c A L A at q with one 2 x 2 output tile per thread ((M/2)^2 threads;
+// per element the same FP32 arithmetic as vlv_tiled_kernel) and writes dX/dT of every momentum q' of the
+// orbit from the result R held in shared memory:
+//   out[q'][t] = i^turns (conj ? conj(R[src]) : R[src]),   emap[e][ch][t] = src << 3 | turns << 1 | conj,
+// e the element that maps q to q' (the representative itself is written as is).  The stores are
+// coalesced and no second pass re-reads the representatives' results.
+__global__ void __launch_bounds__(1024) vlv_orbit_kernel(const float2 *A, const float2 *Lc, const int *dij, int Nq,
+                                                         int M, int nff, int nd, int chmask, const double *scal,
+                                                         const int *list, const int *orb_ofs, const int *orb_q,
+                                                         const int2 *qmap, const int *emap, double2 *out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s0 = reinterpret_cast<float2 *>(smem_raw);   // A^T, then A, then the result R
+    float2 *s1 = s0 + M * M;                              // L, then T^T
+    const int p = blockIdx.x, ch = blockIdx.y, q = list[p];
+    const int M2 = M * M, nt = M / 2;
+    const int m0 = orb_ofs[p], m1 = orb_ofs[p + 1];
+    if (!((chmask >> ch) & 1)) {
+        for (int k = m0; k < m1; k++) {
+            double2 *o = out + ((size_t)ch * Nq + orb_q[k]) * M2;
+            for (int i = threadIdx.x; i < M2; i += blockDim.x) o[i] = make_double2(0.0, 0.0);
+        }
+        return;
+    }
+    const float2 *a = A + ((size_t)ch * Nq + q) * M2;
+    const float2 *lc = Lc + ((size_t)ch * Nq + q) * nd * 16;
+    // (r, c) of entry i advanced incrementally: blockDim = dr M + dc with dc < M
+    const int dr = blockDim.x / M, dc = blockDim.x - dr * M;
+    {
+        int r = threadIdx.x / M, c = threadIdx.x - r * M;
+        for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+            s0[c * M + r] = a[i];
+            s1[i] = lc[(dij[(r >> 2) * nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3)];
+            r += dr;
+            c += dc;
+            if (c >= M) {
+                c -= M;
+                r++;
+            }
+        }
+    }
+    __syncthreads();
+    const bool active = (int)threadIdx.x < nt * nt;
+    const int ti = threadIdx.x / nt, tj = threadIdx.x - ti * nt;
+    const int r = 2 * ti, c = 2 * tj;
+    float2 acc[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) acc[i][j] = make_float2(0.f, 0.f);
+    if (active) tile22(s1, s0, M, r, c, acc);   // T^T = L^T A^T
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                s1[(r + i) * M + c + j] = acc[i][j];
+                acc[i][j] = make_float2(0.f, 0.f);
+            }
+    }
+    for (int i = threadIdx.x; i < M2; i += blockDim.x) s0[i] = a[i];   // A, row-major (L2-resident reread)
+    __syncthreads();
+    if (active) tile22(s1, s0, M, r, c, acc);   // T A
+    __syncthreads();                            // every read of A done before R overwrites it
+    if (active) {
+        const float sc = (float)((ch == 0 ? 1.0 : 2.0) * scal[1]);   // c_P = 1, c_C = 2, times the output scale
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) s0[(r + i) * M + c + j] = make_float2(sc * acc[i][j].x, sc * acc[i][j].y);
+    }
+    __syncthreads();
+    for (int k = m0; k < m1; k++) {
+        const int q2 = orb_q[k];
+        double2 *o = out + ((size_t)ch * Nq + q2) * M2;
+        if (q2 == q) {
+            for (int i = threadIdx.x; i < M2; i += blockDim.x) store_w(o + i, s0[i]);
+        } else {
+            const int *em = emap + ((size_t)qmap[q2].y * 2 + ch) * M2;
+            for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+                const int code = em[i];
+                float2 v = s0[code >> 3];
+                if (code & 1) v.y = -v.y;
+                store_w(o + i, quarter_turn(v, code >> 1));
+            }
+        }
+    }
+}
+
 // Two-band bond sets (N_s^2 = 4, M = 4 N_ff): one CTA per (q, channel), one 4 x 4 output tile per
 // thread (rows {2i, 2i+1, M/2 + 2i, M/2 + 2i + 1}, columns likewise).  Shared memory holds two
 // M x M buffers: A transposed and L for T^T = L^T A^T, then A (reloaded, row-major) and T^T for
@@ -181,36 +305,77 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 
 }  // namespace
 
-// dX/dT of a symmetric state at the momenta that are not orbit representatives, gathered from their
-// representative q (element e, qmap[q'] = (list position, e)):
-//   out[ch][q'][r'][c'] = i^(qrow[r'] - qrow[c']) (conj ? conj(v) : v),  v = out[ch][q][srow[r']][srow[c']]
-// (W X W^dagger with W the element's bond permutation times its orbital-pair map).  Grid (M, Nq, 2).
-__global__ void sym_scatter_kernel(double2 *out, int Nq, int M, const int2 *qmap, const int *list, const SymElem *elem,
-                                   const int *srow, const int *qrow)
+// Symmetric states: dX/dT(q') = W dX/dT(q) W^dagger for the non-representative momenta q' (W maps row
+// r' to source row srow[r'] with i^qrow[r'], conjugated for time-reversed elements).  One CTA per
+// (q', channel) walks the M^2 entries; the element's row tables sit in shared memory and the entry
+// indices advance incrementally (blockDim = dr M + dc).
+__global__ void __launch_bounds__(256) sym_scatter_kernel(double2 *out, int Nq, int M, int dr, int dc, const int2 *qmap,
+                                                          const int *list, const SymElem *elem, const int *srow,
+                                                          const int *qrow)
 {
-    const int r2 = blockIdx.x, q2 = blockIdx.y, ch = blockIdx.z, c2 = threadIdx.x;
+    extern __shared__ int s_tab[];   // [M] source rows, [M] quarter turns
+    const int q2 = blockIdx.x, ch = blockIdx.y;
     const int2 ie = qmap[q2];
     const int q = list[ie.x];
-    if (q == q2 || c2 >= M) return;   // representatives hold their own result
+    if (q == q2) return;             // representatives hold their own result
     const int *sr = srow + ((size_t)ie.y * 2 + ch) * M, *qr = qrow + ((size_t)ie.y * 2 + ch) * M;
-    double2 v = out[(((size_t)ch * Nq + q) * M + sr[r2]) * M + sr[c2]];
-    if (elem[ie.y].conj) v.y = -v.y;
-    double2 w;
-    switch ((qr[r2] - qr[c2]) & 3) {
-    case 0: w = v; break;
-    case 1: w = make_double2(-v.y, v.x); break;
-    case 2: w = make_double2(-v.x, -v.y); break;
-    default: w = make_double2(v.y, -v.x); break;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        s_tab[i] = sr[i];
+        s_tab[M + i] = qr[i];
     }
-    out[(((size_t)ch * Nq + q2) * M + r2) * M + c2] = w;
+    __syncthreads();
+    const bool conj = elem[ie.y].conj;
+    const double2 *src = out + ((size_t)ch * Nq + q) * M * M;
+    double2 *dst = out + ((size_t)ch * Nq + q2) * M * M;
+    const int M2 = M * M;
+    int r = threadIdx.x / M, c = threadIdx.x - r * M;
+    for (int t = threadIdx.x; t < M2; t += blockDim.x) {
+        double2 v = src[(size_t)s_tab[r] * M + s_tab[c]];
+        if (conj) v.y = -v.y;
+        double2 w;
+        switch ((s_tab[M + r] - s_tab[M + c]) & 3) {
+        case 0: w = v; break;
+        case 1: w = make_double2(-v.y, v.x); break;
+        case 2: w = make_double2(-v.x, -v.y); break;
+        default: w = make_double2(v.y, -v.x); break;
+        }
+        dst[t] = w;
+        r += dr;
+        c += dc;
+        if (c >= M) { c -= M; r++; }
+    }
 }
 
 cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
 {
     PhaseScope ps(m, PH_VLV);
-    const int threads = (m->M + 31) / 32 * 32;
-    sym_scatter_kernel<<<dim3(m->M, m->Nq, 2), threads, 0, m->stream>>>(d_out, m->Nq, m->M, m->d_qmap, m->d_loop_list,
-                                                                        m->d_sym_elem, m->d_sym_srow, m->d_sym_qrow);
+    const int threads = 256;
+    sym_scatter_kernel<<<dim3(m->Nq, 2), threads, 2 * sizeof(int) * m->M, m->stream>>>(
+        d_out, m->Nq, m->M, threads / m->M, threads % m->M, m->d_qmap, m->d_loop_list, m->d_sym_elem, m->d_sym_srow,
+        m->d_sym_qrow);
+    return cudaGetLastError();
+}
+
+bool orbit_products_supported(const tufrg_model *m)
+{
+    return m->ns == 2 && m->M <= 64 && m->M % 2 == 0 && m->precision != TUFRG_FP64;
+}
+
+cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out)
+{
+    if (!m->d_sym_emap) {
+        TUFRG_CUDA_TRY(launch_vlv(m, m->d_A, channel_mask, d_out, m->d_loop_list, m->n_loop_q));
+        return launch_sym_scatter(m, d_out);
+    }
+    const int M = m->M, nt = M / 2;
+    const int threads = (nt * nt + 31) / 32 * 32;
+    const size_t smem = 2 * sizeof(float2) * M * M;
+    if (smem > 48 * 1024)
+        TUFRG_CUDA_TRY(cudaFuncSetAttribute(vlv_orbit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PhaseScope ps(m, PH_VLV);
+    vlv_orbit_kernel<<<dim3(m->n_loop_q, 2), threads, smem, m->stream>>>(
+        m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask, m->d_scal, m->d_loop_list, m->d_orb_ofs,
+        m->d_orb_q, m->d_qmap, m->d_sym_emap, d_out);
     return cudaGetLastError();
 }
 

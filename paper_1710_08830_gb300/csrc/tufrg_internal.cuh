@@ -140,9 +140,12 @@ struct tufrg_model {
     // representatives only and dX/dT of the other momenta is gathered from them
     bool sym_state = false;
     bool sym_state_pays = false;    // autotuned at init: the representatives' products are faster
-    double sym_tune_ms[2] = {-1.0, -1.0};   // products for every momentum / representatives + gather
+    double sym_tune_ms[2] = {-1.0, -1.0};   // projections + products at every momentum / representatives + gather
     int *d_sym_srow = nullptr;      // [n_sym_elem][2][M] source index of every target row / column
     int *d_sym_qrow = nullptr;      // [n_sym_elem][2][M] quarter turns of every target row / column
+    int *d_orb_ofs = nullptr;       // [n_loop_q + 1] orbit of each representative: momenta orb_q[ofs[p] .. ofs[p+1])
+    int *d_orb_q = nullptr;         // [Nq]
+    int *d_sym_emap = nullptr;      // [n_sym_elem][2][M^2] source entry << 3 | quarter turns << 1 | conj (small M)
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
@@ -220,7 +223,9 @@ cudaError_t launch_bands(tufrg_model *m);
 cudaError_t launch_density(tufrg_model *m, double mu, double T, double *h_out);
 cudaError_t launch_fermi(tufrg_model *m);
 cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
-cudaError_t launch_loops(tufrg_model *m, int channel_mask);
+// reps_only (with loop symmetries): the FP32 loops of the orbit representatives only, at their own
+// momenta, and no FP64 copy on the split path (what the symmetric-state products read)
+cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only = false);
 // The split path reads the FP32 copy of the state (d_state32), the plain path the FP64 state.
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask);
 // qlist (nlist entries): only these transfer momenta (the orbit representatives of a symmetric state)
@@ -242,14 +247,20 @@ cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, co
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
 int plan_gen_chunks(const tufrg_model *m);   // kx ranges per momentum of the multi-orbital loop kernel
+size_t gen_red_offset(const tufrg_model *m);   // byte offset of the representatives' range sums in d_part
+size_t gen_part_bytes(const tufrg_model *m);   // loop scratch of the multi-orbital kernel
 int dft_plan_nsplit(const tufrg_model *m);
 bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
-cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask);
+cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only);
 cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist,
                              int nlist);
-cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);   // symmetric states: non-representative momenta
+cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);
+// symmetric states: products at the orbit representatives and dX/dT of every momentum (the fused orbit
+// kernel where its tables exist, else the representatives' products plus the scatter)
+cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out);
+bool orbit_products_supported(const tufrg_model *m);   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
 void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);

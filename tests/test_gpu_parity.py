@@ -171,6 +171,12 @@ def test_rhs_symmetric_state(case, prec):
     assert rel(sym, full) < (1e-12 if prec == "FP64" else 2e-6)
     ref, _ = oracle.Oracle(spec).rhs(0.4, X1.cpu().numpy(), 3)
     assert rel(sym, ref) < (TOL64 if prec == "FP64" else TOL32)
+    for mask in (api.CH_P, api.CH_C):   # one channel (the other's sources and dX/dT are zero)
+        one = m.rhs(0.4, X1, mask=mask, symmetric=True).cpu().numpy()
+        one_full = m.rhs(0.4, X1, mask=mask).cpu().numpy()
+        ch = 0 if mask == api.CH_P else 1
+        assert rel(one[ch], one_full[ch]) < (1e-12 if prec == "FP64" else 2e-6)
+        assert not np.any(one[1 - ch])
 
 
 @pytest.mark.parametrize("case,prec", [("rashba_ff9_Lf25", "SPLIT32"), ("hubbard_ff5_Lf24", "FP64")])
