@@ -150,6 +150,12 @@ tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc
  * reduce them, see TUFRG_SYMMETRY_AUTO). */
 tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
 
+/* Round n FP64 values at d_in to FP32 at d_out (device buffers, no overlap), to nearest with ties to
+ * even: the rounding the split path applies to states, loop data and tables.  Stream ordered on
+ * cuda_stream (NULL = legacy default stream).  Errors: TUFRG_EINVAL for NULL buffers with n > 0,
+ * TUFRG_ECUDA for a failed launch. */
+tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda_stream);
+
 /* Symmetric-state path (TUFRG_SYMMETRIC_STATE): *in_use = 1 when calls that set the flag project and
  * multiply at the orbit representatives only, 0 when they take the general path (the state symmetries
  * do not hold for this model, or the representatives' path was not faster at init).  *ms_general and

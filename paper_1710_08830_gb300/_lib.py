@@ -76,6 +76,8 @@ def lib():
             L.tufrg_loop_momenta.restype = C.c_int
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_symmetry_info.restype = C.c_int
+            L.tufrg_round_f32.argtypes = [vp, vp, C.c_size_t, vp]
+            L.tufrg_round_f32.restype = C.c_int
             L.tufrg_gather_table.argtypes = [vp, i, vp, i, ip]
             L.tufrg_bands.argtypes = [vp, vp, vp]
             L.tufrg_loops.argtypes = [vp, d, i, vp]
@@ -120,7 +122,7 @@ def lib():
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
            "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info", "tufrg_loop_momenta",
-           "tufrg_symmetry_info",
+           "tufrg_symmetry_info", "tufrg_round_f32",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")

@@ -458,7 +458,8 @@ void release(tufrg_model *m)
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
-                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap};
+                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp,
+                    m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -486,7 +487,9 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
     const bool sym = symmetric_state && m->sym_state && m->sym_state_pays;
     const int *ql = sym ? m->d_loop_list : nullptr;
     const int nl = sym ? m->n_loop_q : 0;
-    if (split && !d_state32) {
+    // without an FP32 copy the separable transform writes one as it reads the FP64 state (the sliced
+    // direct transform reads a converted copy)
+    if (split && !d_state32 && m->dft_warps == 0) {
         CK(launch_to_f32(m, d_state, m->d_X32, state_elems(m)), "state conversion");
         d_state32 = m->d_X32;
     }
@@ -494,6 +497,7 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
     // a symmetric state's products read the loops of the orbit representatives only
     CK(launch_loops(m, mask, sym), "loop k-sum");
     CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
+    if (split && !d_state32) d_state32 = m->d_X32;
     // the split path's products read the FP32 copy only
     CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A, ql, nl), "projections");
     if (sym) CK(launch_products_sym(m, mask, d_out), "V.L.V products (orbit representatives)");
@@ -778,12 +782,14 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                 m->sym_state = true;
                 CK(upload(&m->d_sym_srow, srow, m->stream), "upload symmetry tables");
                 CK(upload(&m->d_sym_qrow, qrow, m->stream), "upload symmetry tables");
-                if (orbit_products_supported(m)) {
+                std::vector<int> ofs(m->n_loop_q + 1, 0), oq(m->Nq);
+                for (int q = 0; q < m->Nq; q++) ofs[ls.qmap[q].x + 1]++;
+                int max_orbit = 0;
+                for (int p = 0; p < m->n_loop_q; p++) max_orbit = std::max(max_orbit, ofs[p + 1]);
+                for (int p = 0; p < m->n_loop_q; p++) ofs[p + 1] += ofs[p];
+                if (orbit_products_supported(m) && max_orbit <= orbit_max_size()) {
                     // fused orbit products: the momenta of every orbit and, per element and channel, the
                     // source entry, quarter turns and conjugation of every target entry
-                    std::vector<int> ofs(m->n_loop_q + 1, 0), oq(m->Nq);
-                    for (int q = 0; q < m->Nq; q++) ofs[ls.qmap[q].x + 1]++;
-                    for (int p = 0; p < m->n_loop_q; p++) ofs[p + 1] += ofs[p];
                     std::vector<int> fill(ofs.begin(), ofs.end() - 1);
                     for (int q = 0; q < m->Nq; q++) oq[fill[ls.qmap[q].x]++] = q;
                     const int M = m->M;
@@ -796,6 +802,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                                     emap[((e * 2 + ch) * M + r) * M + c] =
                                         (sr[r] * M + sr[c]) << 3 | ((qr[r] - qr[c]) & 3) << 1 | (ls.elem[e].conj ? 1 : 0);
                         }
+                    std::vector<int> lexp((size_t)M * M);
+                    for (int r = 0; r < M; r++)
+                        for (int c = 0; c < M; c++)
+                            lexp[(size_t)r * M + c] = (m->dij[(r >> 2) * m->nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3);
+                    CK(upload(&m->d_orb_lexp, lexp, m->stream), "upload symmetry tables");
                     CK(upload(&m->d_orb_ofs, ofs, m->stream), "upload symmetry tables");
                     CK(upload(&m->d_orb_q, oq, m->stream), "upload symmetry tables");
                     CK(upload(&m->d_sym_emap, emap, m->stream), "upload symmetry tables");
@@ -853,6 +864,53 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         for (int p = 0; p < m->nff * m->nff; p++)
             m->max_terms = std::max(m->max_terms, m->gofs[ch][p + 1] - m->gofs[ch][p]);
     m->dft_nsplit = dft_plan_nsplit(m);
+    {
+        // separable Fourier transform: the distinct R_y and R_x of the classes, classes grouped by R_y
+        std::vector<int> ry, rx;
+        for (int c = 0; c < m->ncls; c++) {
+            if (std::find(ry.begin(), ry.end(), m->cls[2 * c + 1]) == ry.end()) ry.push_back(m->cls[2 * c + 1]);
+            if (std::find(rx.begin(), rx.end(), m->cls[2 * c]) == rx.end()) rx.push_back(m->cls[2 * c]);
+        }
+        m->dft_nry = (int)ry.size();
+        m->dft_nrx = (int)rx.size();
+        dft_sep_plan(m, &m->dft_warps, &m->dft_epw_log2);
+        if (m->dft_warps > 0) {
+            std::vector<int> tabs(2 * m->ncls + m->dft_nry + 1, 0);
+            int pos = 0;
+            for (int r = 0; r < m->dft_nry; r++) {
+                tabs[2 * m->ncls + r] = pos;
+                for (int c = 0; c < m->ncls; c++)
+                    if (m->cls[2 * c + 1] == ry[r]) {
+                        tabs[pos] = c;
+                        tabs[m->ncls + pos] = (int)(std::find(rx.begin(), rx.end(), m->cls[2 * c]) - rx.begin());
+                        pos++;
+                    }
+            }
+            tabs[2 * m->ncls + m->dft_nry] = pos;
+            // e^{i 2 pi u R / Lq} with u R reduced modulo Lq (exact lattice phases, as in phase_table)
+            auto one_dim = [&](const std::vector<int> &v) {
+                std::vector<double2> t((size_t)m->Lq * v.size());
+                for (int u = 0; u < m->Lq; u++)
+                    for (size_t j = 0; j < v.size(); j++) {
+                        const long k = ((long)u * v[j]) % m->Lq;
+                        const double a = 2.0 * M_PI * (double)((k + m->Lq) % m->Lq) / (double)m->Lq;
+                        t[(size_t)u * v.size() + j] = make_double2(std::cos(a), std::sin(a));
+                    }
+                return t;
+            };
+            const std::vector<double2> py = one_dim(ry), px = one_dim(rx);
+            CK(upload(&m->d_dft_tabs, tabs, m->stream), "upload Fourier tables");
+            CK(upload(&m->d_dft_phy, py, m->stream), "upload Fourier tables");
+            CK(upload(&m->d_dft_phx, px, m->stream), "upload Fourier tables");
+            if (split) {
+                std::vector<float2> py32(py.size()), px32(px.size());
+                for (size_t i = 0; i < py.size(); i++) py32[i] = make_float2((float)py[i].x, (float)py[i].y);
+                for (size_t i = 0; i < px.size(); i++) px32[i] = make_float2((float)px[i].x, (float)px[i].y);
+                CK(upload(&m->d_dft_phy32, py32, m->stream), "upload Fourier tables");
+                CK(upload(&m->d_dft_phx32, px32, m->stream), "upload Fourier tables");
+            }
+        }
+    }
     // the Fourier transform uses e^{i u.R''} for the classes
     {
         const std::vector<double2> cph = phase_table(m->Lq, m->cls);
@@ -1052,6 +1110,14 @@ tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct)
     return TUFRG_OK;
 }
 
+tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda_stream)
+{
+    if (n > 0 && (!d_in || !d_out)) return TUFRG_EINVAL;
+    const cudaError_t e = launch_round_f32(static_cast<const double *>(d_in), static_cast<float *>(d_out), n,
+                                           static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? TUFRG_OK : TUFRG_ECUDA;
+}
+
 tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps)
 {
     if (!m || !in_use || !ms_general || !ms_reps) return TUFRG_EINVAL;
@@ -1132,11 +1198,12 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     const double2 *st = reinterpret_cast<const double2 *>(d_state);
     const float2 *st32 = nullptr;
-    if (m->precision != TUFRG_FP64) {
+    if (m->precision != TUFRG_FP64 && m->dft_warps == 0) {
         CK(launch_to_f32(m, st, m->d_X32, state_elems(m)), "state conversion");
         st32 = m->d_X32;
     }
     CK(launch_dft(m, st, st32, channel_mask), "Fourier transform");
+    if (m->precision != TUFRG_FP64 && !st32) st32 = m->d_X32;   // written by the separable transform
     CK(launch_project(m, st, st32, channel_mask, reinterpret_cast<double2 *>(d_Ahat)), "projections");
     if (h_amax) {
         unsigned long long bits = 0;

@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(32 * WARPS) loops_ns2_kernel(LoopArgs<R> a)
 
 // Sum the partials of list position s in a fixed order and scale by 1/Nk; the half-plane partials
 // give both Hermitian halves.  The sum runs in the partials' own precision (FP32 on the split path:
-// this GPU's FP64 rate would make the reduction, not the memory traffic, its bound), with four loads
-// in flight per thread.
+// this GPU's FP64 rate would make the reduction, not the memory traffic, its bound), with 16 loads
+// in flight per thread (the additions keep their sequential order).
 template <typename R>
 __device__ __forceinline__ typename cpx<R>::t reduce_one(const typename cpx<R>::t *__restrict__ part, int n_part,
                                                          int ndx, int ndyh, const int *dslot, const int *deltas, int s,
@@ -256,13 +256,14 @@ __device__ __forceinline__ typename cpx<R>::t reduce_one(const typename cpx<R>::
     const size_t stride = (size_t)ndx * ndyh * NS4;
     const C2 *src = part + (size_t)s * n_part * stride + (size_t)slot * NS4 + src_ab;
     R re = 0, im = 0;
+    constexpr int UB = 16;
     int p = 0;
-    for (; p + 4 <= n_part; p += 4) {
-        C2 v[4];
+    for (; p + UB <= n_part; p += UB) {
+        C2 v[UB];
 #pragma unroll
-        for (int j = 0; j < 4; j++) v[j] = src[(size_t)(p + j) * stride];
+        for (int j = 0; j < UB; j++) v[j] = src[(size_t)(p + j) * stride];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < UB; j++) {
             re += v[j].x;
             im += v[j].y;
         }

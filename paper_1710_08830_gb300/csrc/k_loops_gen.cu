@@ -224,6 +224,31 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     }
 }
 
+// re, im += the n values p[c stride] in order c = 0, 1, ... (FP64), eight loads in flight
+__device__ __forceinline__ double wide(float v) { return widen_f(v); }
+__device__ __forceinline__ double wide(double v) { return v; }
+template <typename C2>
+__device__ __forceinline__ void sum_ranges(const C2 *p, size_t stride, int n, double &re, double &im)
+{
+    constexpr int UB = 8;
+    int c = 0;
+    for (; c + UB <= n; c += UB) {
+        C2 w[UB];
+#pragma unroll
+        for (int j = 0; j < UB; j++) w[j] = p[(size_t)(c + j) * stride];
+#pragma unroll
+        for (int j = 0; j < UB; j++) {
+            re += wide(w[j].x);
+            im += wide(w[j].y);
+        }
+    }
+    for (; c < n; c++) {
+        const C2 w = p[(size_t)c * stride];
+        re += wide(w.x);
+        im += wide(w.y);
+    }
+}
+
 // Mirror the half plane, L(-d)[b][a] = conj(L(d)[a][b]), sum the kx ranges (fixed order) and scale by
 // 1/Nk.  Grid: blockIdx.y = momentum, threads over (d, a, b).
 template <int NS, typename C2>
@@ -235,11 +260,7 @@ __device__ __forceinline__ double2 gen_value(const C2 *acc, size_t chunk_stride,
     const bool half = dy > 0 || (dy == 0 && dx >= 0);
     const size_t o = half ? base + ((size_t)d * NS2 + ia) * NS2 + ib : base + ((size_t)partner[d] * NS2 + ib) * NS2 + ia;
     double re = 0.0, im = 0.0;
-    for (int c = 0; c < nchunk; c++) {
-        const C2 w = acc[(size_t)c * chunk_stride + o];
-        re += (double)w.x;
-        im += (double)w.y;
-    }
+    sum_ranges(acc + o, chunk_stride, nchunk, re, im);
     return make_double2(re, half ? im : -im);
 }
 
@@ -272,11 +293,7 @@ __global__ void loops_gen_chunk_sum(const C2 *acc, int nchunk, int n_slot, int p
     if (t >= per) return;
     const size_t o = (size_t)blockIdx.y * per + t, stride = (size_t)n_slot * per;
     double re = 0.0, im = 0.0;
-    for (int c = 0; c < nchunk; c++) {
-        const C2 w = acc[(size_t)c * stride + o];
-        re += (double)w.x;
-        im += (double)w.y;
-    }
+    sum_ranges(acc + o, stride, nchunk, re, im);
     red[o] = make_double2(re, im);
 }
 

@@ -30,7 +30,7 @@ namespace {
 
 template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const double2 &v);
 template <> __device__ __forceinline__ double2 ld_as<double>(const double2 &v) { return v; }
-template <> __device__ __forceinline__ float2 ld_as<float>(const double2 &v) { return make_float2((float)v.x, (float)v.y); }
+template <> __device__ __forceinline__ float2 ld_as<float>(const double2 &v) { return make_float2(narrow_f(v.x), narrow_f(v.y)); }
 template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const float2 &v);
 template <> __device__ __forceinline__ float2 ld_as<float>(const float2 &v) { return v; }
 
@@ -83,6 +83,107 @@ __global__ void __launch_bounds__(128) dft_kernel(const XT *__restrict__ X, int 
 #pragma unroll
     for (int c = 0; c < CPT; c++)
         if (c0 + c < ncls) part[(((size_t)blockIdx.y * 2 + ch) * ncls + c0 + c) * M2 + ij] = acc[c];
+}
+
+// Separable form of the same transform, u = (u_x, u_y), R'' = (R_x, R_y):
+//   Z(u_x, R_y) = sum_{u_y} e^{i u_y R_y} X(u_x, u_y),   X(R'') = (1/Nq) sum_{u_x} e^{i u_x R_x} Z(u_x, R_y),
+// Lq (n_Ry + n_cls / Lq) complex FMAs per entry and class instead of Nq.  One CTA owns EPW = 2^epw_log2
+// consecutive matrix entries of one channel; lane = (sub, el) of a warp takes entry el of the block and
+// the rows u_x = w G + sub, + W G, ... (G = 32 / EPW rows side by side), forms Z for the distinct R_y
+// of the classes (in registers) and adds e^{i u_x R_x} Z into its own shared-memory column; the W G
+// columns of an entry are summed in a fixed order at the end (deterministic, one pass over the state, no
+// partials in HBM).  Classes are visited grouped by R_y: sorted position c has class id cid[c], R_x
+// index rxi[c], and the group of the r-th R_y is [ryo[r], ryo[r+1]).  Reading the FP64 state on the split
+// path, the kernel also writes its FP32 rounding to x32 (the copy the projections read).
+constexpr int DFT_MAXRY = 9;
+constexpr int DFT_MAXW = 24;      // FP32 accumulators
+constexpr int DFT_MAXW64 = 12;    // FP64 accumulators (twice the registers and shared memory per warp)
+
+__device__ __forceinline__ void put32(float2 *p, float2 v) { *p = v; }
+__device__ __forceinline__ void put32(float2 *, double2) {}
+
+template <typename R, typename XT>
+__global__ void __launch_bounds__(32 * (sizeof(R) == 8 ? DFT_MAXW64 : DFT_MAXW)) dft_sep_kernel(
+    const XT *__restrict__ X, int Lq, int M2, int ncls, int nry, int nrx, int epw_log2, const int *__restrict__ tabs,
+    const typename cpx<R>::t *__restrict__ phy, const typename cpx<R>::t *__restrict__ phx, int ch_lo, double inv_nq,
+    typename cpx<R>::t *__restrict__ Xr, float2 *__restrict__ x32)
+{
+    using C2 = typename cpx<R>::t;
+    constexpr int UB = 8;   // loads in flight per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int EPW = 1 << epw_log2, G = 32 >> epw_log2, sub = lane >> epw_log2, el = lane & (EPW - 1);
+    C2 *part = reinterpret_cast<C2 *>(smem_raw);            // [W][ncls][32]
+    C2 *sphy = part + (size_t)W * ncls * 32;               // [Lq][nry]  e^{i u_y R_y}
+    C2 *sphx = sphy + Lq * nry;                             // [Lq][nrx]  e^{i u_x R_x}
+    int *stab = reinterpret_cast<int *>(sphx + Lq * nrx);   // cid [ncls], rxi [ncls], ryo [nry + 1]
+    for (int i = threadIdx.x; i < Lq * nry; i += blockDim.x) sphy[i] = phy[i];
+    for (int i = threadIdx.x; i < Lq * nrx; i += blockDim.x) sphx[i] = phx[i];
+    for (int i = threadIdx.x; i < 2 * ncls + nry + 1; i += blockDim.x) stab[i] = tabs[i];
+    C2 *mine = part + (size_t)w * ncls * 32;
+    for (int c = 0; c < ncls; c++) mine[c * 32 + lane] = mk(R(0), R(0));
+    __syncthreads();
+    const int *cid = stab, *rxi = stab + ncls, *ryo = stab + 2 * ncls;
+    const int ch = ch_lo + blockIdx.y, e = blockIdx.x * EPW + el;
+    const bool valid = e < M2;
+    const size_t Nq = (size_t)Lq * Lq;
+    for (int ux = w * G + sub; ux < Lq; ux += W * G) {
+        C2 z[DFT_MAXRY];
+#pragma unroll
+        for (int r = 0; r < DFT_MAXRY; r++) z[r] = mk(R(0), R(0));
+        const size_t row = ((size_t)ch * Nq + (size_t)ux * Lq) * M2 + (valid ? e : 0);
+        for (int uy0 = 0; uy0 < Lq; uy0 += UB) {
+            // all loads of the batch first, then the roundings (and the FP32 copy)
+            XT raw[UB];
+#pragma unroll
+            for (int j = 0; j < UB; j++) {
+                raw[j].x = 0;
+                raw[j].y = 0;
+                if (valid && uy0 + j < Lq) raw[j] = X[row + (size_t)(uy0 + j) * M2];
+            }
+            C2 x[UB];
+#pragma unroll
+            for (int j = 0; j < UB; j++) {
+                x[j] = ld_as<R>(raw[j]);
+                if (x32 && valid && uy0 + j < Lq) put32(x32 + row + (size_t)(uy0 + j) * M2, x[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < UB; j++) {
+                if (uy0 + j >= Lq) break;
+                const C2 *p = sphy + (uy0 + j) * nry;
+#pragma unroll
+                for (int r = 0; r < DFT_MAXRY; r++) {
+                    if (r >= nry) break;
+                    const C2 ph = p[r];
+                    z[r].x = fma(ph.x, x[j].x, fma(-ph.y, x[j].y, z[r].x));
+                    z[r].y = fma(ph.x, x[j].y, fma(ph.y, x[j].x, z[r].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < DFT_MAXRY; r++) {
+            if (r >= nry) break;
+            for (int c = ryo[r]; c < ryo[r + 1]; c++) {
+                const C2 ph = sphx[ux * nrx + rxi[c]];
+                C2 &o = mine[c * 32 + lane];
+                o.x = fma(ph.x, z[r].x, fma(-ph.y, z[r].y, o.x));
+                o.y = fma(ph.x, z[r].y, fma(ph.y, z[r].x, o.y));
+            }
+        }
+    }
+    __syncthreads();
+    const R scale = R(inv_nq);
+    for (int o = threadIdx.x; o < (ncls << epw_log2); o += blockDim.x) {
+        const int c = o >> epw_log2, l = o & (EPW - 1), e2 = blockIdx.x * EPW + l;
+        R sx = 0, sy = 0;
+        for (int k = 0; k < W; k++)
+            for (int g = 0; g < G; g++) {
+                const C2 v = part[((size_t)k * ncls + c) * 32 + (g << epw_log2) + l];
+                sx += v.x;
+                sy += v.y;
+            }
+        if (e2 < M2) Xr[((size_t)ch * ncls + cid[c]) * M2 + e2] = mk(sx * scale, sy * scale);
+    }
 }
 
 template <typename R>
@@ -152,26 +253,33 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
             const int2 *et = ch == 0 ? et0 : et1;
             const int t1 = eofs[e + 1];
             const int lim = ncls * M2;   // sources at or above lim belong to the C channel
-            // two terms per iteration: both gathers are issued before either is used
+            // TB terms per iteration: every term's gathers are issued before any is used (the terms are
+            // still added in their order)
+            constexpr int TB = 4;
             int t = eofs[e];
-            for (; t + 2 <= t1; t += 2) {
-                const int2 g0 = et[t], g1 = et[t + 1];
-                const int i0 = g0.x & 0x7fffffff, i1 = g1.x & 0x7fffffff;
-                const bool on0 = (chmask >> (i0 >= lim ? 1 : 0)) & 1, on1 = (chmask >> (i1 >= lim ? 1 : 0)) & 1;
-                C2 x0 = on0 ? Xr[i0] : mk(R(0), R(0)), x1 = on1 ? Xr[i1] : mk(R(0), R(0));
-                if (g0.x < 0) { x0.x = -x0.x; x0.y = -x0.y; }
-                if (g1.x < 0) { x1.x = -x1.x; x1.y = -x1.y; }
-                const C2 *p0 = phs + g0.y, *p1 = phs + g1.y;
+            for (; t + TB <= t1; t += TB) {
+                int2 g[TB];
+                C2 x[TB];
 #pragma unroll
-                for (int qi = 0; qi < QT; qi++) {
-                    const C2 pa = p0[qi * nph], pb = p1[qi * nph];
-                    acc[qi].x += pa.x * x0.x - pa.y * x0.y;
-                    acc[qi].y += pa.x * x0.y + pa.y * x0.x;
-                    acc[qi].x += pb.x * x1.x - pb.y * x1.y;
-                    acc[qi].y += pb.x * x1.y + pb.y * x1.x;
+                for (int j = 0; j < TB; j++) g[j] = et[t + j];
+#pragma unroll
+                for (int j = 0; j < TB; j++) {
+                    const int idx = g[j].x & 0x7fffffff;
+                    x[j] = ((chmask >> (idx >= lim ? 1 : 0)) & 1) ? Xr[idx] : mk(R(0), R(0));
+                }
+#pragma unroll
+                for (int j = 0; j < TB; j++) {
+                    if (g[j].x < 0) { x[j].x = -x[j].x; x[j].y = -x[j].y; }
+                    const C2 *pj = phs + g[j].y;
+#pragma unroll
+                    for (int qi = 0; qi < QT; qi++) {
+                        const C2 pq = pj[qi * nph];
+                        acc[qi].x += pq.x * x[j].x - pq.y * x[j].y;
+                        acc[qi].y += pq.x * x[j].y + pq.y * x[j].x;
+                    }
                 }
             }
-            if (t < t1) {
+            for (; t < t1; t++) {
                 const int2 g = et[t];
                 const int idx = g.x & 0x7fffffff;
                 if ((chmask >> (idx >= lim ? 1 : 0)) & 1) {
@@ -271,14 +379,62 @@ int dft_plan_nsplit(const tufrg_model *m)
     return (int)ns;
 }
 
+// launch shape of the separable transform: entries per warp (2^epw_log2, small enough that the grid
+// covers the GPU twice) and warps per CTA (0: not applicable, the sliced direct sum runs instead)
+void dft_sep_plan(const tufrg_model *m, int *warps, int *epw_log2)
+{
+    *warps = 0;
+    *epw_log2 = 5;
+    if (m->dft_nry < 1 || m->dft_nry > DFT_MAXRY) return;
+    const int M2 = m->M * m->M;
+    while (*epw_log2 > 3 && 2L * ((M2 + (1 << *epw_log2) - 1) >> *epw_log2) < 2L * m->sm_count) (*epw_log2)--;
+    const int G = 32 >> *epw_log2;                          // rows side by side in a warp
+    const size_t c2 = m->precision == TUFRG_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t fixed = c2 * m->Lq * (m->dft_nry + m->dft_nrx) + sizeof(int) * (2 * m->ncls + m->dft_nry + 1);
+    const size_t per_warp = c2 * m->ncls * 32, cap = 200 * 1024;
+    if (fixed + per_warp > cap) return;
+    const int wmax = (int)std::min<size_t>(m->precision == TUFRG_FP64 ? DFT_MAXW64 : DFT_MAXW, (cap - fixed) / per_warp);
+    const int need = (m->Lq + G - 1) / G;                  // warps for one row each
+    const int rows = (need + wmax - 1) / wmax;             // row groups per warp
+    *warps = (need + rows - 1) / rows;
+}
+
+template <typename R, typename XT>
+cudaError_t dft_sep_run(tufrg_model *m, const XT *d_state, const typename cpx<R>::t *phy, const typename cpx<R>::t *phx,
+                        int ch_lo, int nch, typename cpx<R>::t *Xr, float2 *x32)
+{
+    using C2 = typename cpx<R>::t;
+    const int W = m->dft_warps, M2 = m->M * m->M, EPW = 1 << m->dft_epw_log2;
+    const size_t smem = sizeof(C2) * ((size_t)W * m->ncls * 32 + (size_t)m->Lq * (m->dft_nry + m->dft_nrx)) +
+                        sizeof(int) * (2 * m->ncls + m->dft_nry + 1);
+    auto k = dft_sep_kernel<R, XT>;
+    if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PhaseScope ps(m, PH_DFT);
+    k<<<dim3((M2 + EPW - 1) / EPW, nch), 32 * W, smem, m->stream>>>(d_state, m->Lq, M2, m->ncls, m->dft_nry, m->dft_nrx,
+                                                                   m->dft_epw_log2, m->d_dft_tabs, phy, phx, ch_lo,
+                                                                   1.0 / m->Nq, Xr, x32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask)
 {
     const int ch_lo = (channel_mask & 1) ? 0 : 1, ch_hi = (channel_mask & 2) ? 1 : 0;
     if (ch_lo > ch_hi) return cudaSuccess;
     const int nch = ch_hi - ch_lo + 1;
+    if (m->dft_warps > 0) {
+        if (m->precision == TUFRG_FP64)
+            return dft_sep_run<double, double2>(m, d_state, m->d_dft_phy, m->d_dft_phx, ch_lo, nch, m->d_Xr, nullptr);
+        // the split path reads the FP32 copy where one exists, else the FP64 state, writing its rounding to
+        // the model's copy as it reads
+        if (d_state32)
+            return dft_sep_run<float, float2>(m, d_state32, m->d_dft_phy32, m->d_dft_phx32, ch_lo, nch, m->d_Xr32,
+                                              nullptr);
+        return dft_sep_run<float, double2>(m, d_state, m->d_dft_phy32, m->d_dft_phx32, ch_lo, nch, m->d_Xr32, m->d_X32);
+    }
     if (m->precision == TUFRG_FP64)
         return dft_run<double, double2, 16>(m, d_state, m->d_clsph, ch_lo, nch, reinterpret_cast<double2 *>(m->d_dftpart),
                                             m->d_Xr);
+    if (!d_state32) return cudaErrorInvalidValue;   // callers convert first when the separable form does not apply
     return dft_run<float, float2, 32>(m, d_state32, m->d_clsph32, ch_lo, nch, reinterpret_cast<float2 *>(m->d_dftpart),
                                       m->d_Xr32);
 }
@@ -317,6 +473,7 @@ cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 
         auto run = short_list ? project_run<double, double2, 2> : project_run<double, double2, PROJ_QT>;
         return run(m, d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_ph, channel_mask, qlist, nlist, d_A, nullptr);
     }
+    if (!d_state32) return cudaErrorInvalidValue;   // the split path projects the FP32 copy
     auto run = short_list ? project_run<float, float2, 2> : project_run<float, float2, PROJ_QT>;
     return run(m, d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_ph32, channel_mask, qlist, nlist, d_A,
                m->d_A32);

@@ -1,5 +1,7 @@
 // Dormand-Prince 5(4) stage combinations and the error norm, FP64, on the device.
 // The flow state is HBM resident; these kernels stream it once per stage.
+#include <algorithm>
+
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -21,7 +23,7 @@ __global__ void rk_combine_kernel(double *out, float *out32, const double *y, co
         for (int j = 0; j < s.nk; j++) acc = fma(s.a[j], s.k[j][i], acc);
         const double v = fma(h, acc, y[i]);
         if (out) out[i] = v;
-        if (out32) out32[i] = (float)v;
+        if (out32) out32[i] = narrow_f(v);
     }
 }
 
@@ -29,8 +31,14 @@ __global__ void to_f32_kernel(const double2 *x, float2 *y, size_t n)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const double2 v = x[i];
-        y[i] = make_float2((float)v.x, (float)v.y);
+        y[i] = make_float2(narrow_f(v.x), narrow_f(v.y));
     }
+}
+
+__global__ void round_f32_kernel(const double *x, float *y, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = narrow_f(x[i]);
 }
 
 // max over complex entries of |h sum_j e_j k_j| / (atol + rtol max(|y|, |yn|)); non-finite -> +inf
@@ -153,6 +161,14 @@ cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const
     rk_combine_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
                                                               reinterpret_cast<float *>(out32),
                                                               reinterpret_cast<const double *>(y), fs, s, nd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_f32(const double *d_in, float *d_out, size_t n, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 8192);
+    round_f32_kernel<<<(unsigned)blocks, 256, 0, stream>>>(d_in, d_out, n);
     return cudaGetLastError();
 }
 

@@ -103,35 +103,47 @@ __device__ __forceinline__ float2 quarter_turn(float2 v, int k)
 // per element the same FP32 arithmetic as vlv_tiled_kernel) and writes dX/dT of every momentum q' of the
 // orbit from the result R held in shared memory:
 //   out[q'][t] = i^turns (conj ? conj(R[src]) : R[src]),   emap[e][ch][t] = src << 3 | turns << 1 | conj,
-// e the element that maps q to q' (the representative itself is written as is).  The stores are
-// coalesced and no second pass re-reads the representatives' results.
-__global__ void __launch_bounds__(1024) vlv_orbit_kernel(const float2 *A, const float2 *Lc, const int *dij, int Nq,
-                                                         int M, int nff, int nd, int chmask, const double *scal,
-                                                         const int *list, const int *orb_ofs, const int *orb_q,
-                                                         const int2 *qmap, const int *emap, double2 *out)
+// e the element that maps q to q' (the representative itself is written as is).  Every thread owns at
+// most ORB_UNITS entries of each matrix pass; the loads of a pass are issued before their uses, the
+// orbit's momenta and elements sit in shared memory, and the stores are coalesced.  lexp[t] is the
+// compact-loop index of expanded entry t, L[(R1,a),(R2,b)] = Lc[d(R1-R2)][a][b].
+constexpr int ORB_MAX = 32;     // orbit size bound (the square lattice's 8 operations, times time reversal)
+constexpr int ORB_UNITS = 4;    // entries per thread per pass (blockDim >= M^2 / 4)
+
+__global__ void __launch_bounds__(1024) vlv_orbit_kernel(const float2 *__restrict__ A, const float2 *__restrict__ Lc,
+                                                         const int *__restrict__ lexp, int Nq, int M, int nd,
+                                                         int chmask, const double *scal, const int *list,
+                                                         const int *orb_ofs, const int *orb_q, const int2 *qmap,
+                                                         const int *__restrict__ emap, double2 *__restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s0 = reinterpret_cast<float2 *>(smem_raw);   // A^T, then A, then the result R
     float2 *s1 = s0 + M * M;                              // L, then T^T
+    __shared__ int s_q2[ORB_MAX], s_e[ORB_MAX];           // the orbit's momenta and elements (-1: q itself)
     const int p = blockIdx.x, ch = blockIdx.y, q = list[p];
-    const int M2 = M * M, nt = M / 2;
-    const int m0 = orb_ofs[p], m1 = orb_ofs[p + 1];
-    if (!((chmask >> ch) & 1)) {
-        for (int k = m0; k < m1; k++) {
-            double2 *o = out + ((size_t)ch * Nq + orb_q[k]) * M2;
-            for (int i = threadIdx.x; i < M2; i += blockDim.x) o[i] = make_double2(0.0, 0.0);
-        }
-        return;
+    const int M2 = M * M, nt = M / 2, B = blockDim.x;
+    const int m0 = orb_ofs[p], nmem = orb_ofs[p + 1] - m0;
+    if ((int)threadIdx.x < nmem) {
+        const int q2 = orb_q[m0 + threadIdx.x];
+        s_q2[threadIdx.x] = q2;
+        s_e[threadIdx.x] = q2 == q ? -1 : qmap[q2].y;
     }
+    const bool on = (chmask >> ch) & 1;
     const float2 *a = A + ((size_t)ch * Nq + q) * M2;
     const float2 *lc = Lc + ((size_t)ch * Nq + q) * nd * 16;
-    // (r, c) of entry i advanced incrementally: blockDim = dr M + dc with dc < M
-    const int dr = blockDim.x / M, dc = blockDim.x - dr * M;
-    {
+    float2 av[ORB_UNITS];
+    if (on) {
+        // A^T and the expanded loop matrix; (r, c) of entry i advance incrementally (B = dr M + dc, dc < M)
+        const int dr = B / M, dc = B - dr * M;
+        int li[ORB_UNITS], rr[ORB_UNITS], cc[ORB_UNITS];
         int r = threadIdx.x / M, c = threadIdx.x - r * M;
-        for (int i = threadIdx.x; i < M2; i += blockDim.x) {
-            s0[c * M + r] = a[i];
-            s1[i] = lc[(dij[(r >> 2) * nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3)];
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) {
+            const int i = threadIdx.x + u * B;
+            av[u] = i < M2 ? a[i] : make_float2(0.f, 0.f);
+            li[u] = i < M2 ? lexp[i] : 0;
+            rr[u] = r;
+            cc[u] = c;
             r += dr;
             c += dc;
             if (c >= M) {
@@ -139,52 +151,89 @@ __global__ void __launch_bounds__(1024) vlv_orbit_kernel(const float2 *A, const 
                 r++;
             }
         }
+        float2 lv[ORB_UNITS];
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) lv[u] = threadIdx.x + u * B < M2 ? lc[li[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) {
+            const int i = threadIdx.x + u * B;
+            if (i < M2) {
+                s0[cc[u] * M + rr[u]] = av[u];
+                s1[i] = lv[u];
+            }
+        }
     }
     __syncthreads();
-    const bool active = (int)threadIdx.x < nt * nt;
-    const int ti = threadIdx.x / nt, tj = threadIdx.x - ti * nt;
-    const int r = 2 * ti, c = 2 * tj;
-    float2 acc[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 2; j++) acc[i][j] = make_float2(0.f, 0.f);
-    if (active) tile22(s1, s0, M, r, c, acc);   // T^T = L^T A^T
-    __syncthreads();
-    if (active) {
+    if (on) {
+        const bool active = (int)threadIdx.x < nt * nt;
+        const int ti = threadIdx.x / nt, tj = threadIdx.x - ti * nt;
+        const int r = 2 * ti, c = 2 * tj;
+        float2 acc[2][2];
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
-                s1[(r + i) * M + c + j] = acc[i][j];
-                acc[i][j] = make_float2(0.f, 0.f);
-            }
-    }
-    for (int i = threadIdx.x; i < M2; i += blockDim.x) s0[i] = a[i];   // A, row-major (L2-resident reread)
-    __syncthreads();
-    if (active) tile22(s1, s0, M, r, c, acc);   // T A
-    __syncthreads();                            // every read of A done before R overwrites it
-    if (active) {
-        const float sc = (float)((ch == 0 ? 1.0 : 2.0) * scal[1]);   // c_P = 1, c_C = 2, times the output scale
+            for (int j = 0; j < 2; j++) acc[i][j] = make_float2(0.f, 0.f);
+        if (active) tile22(s1, s0, M, r, c, acc);   // T^T = L^T A^T
+        __syncthreads();
+        if (active) {
 #pragma unroll
-        for (int i = 0; i < 2; i++)
+            for (int i = 0; i < 2; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) s0[(r + i) * M + c + j] = make_float2(sc * acc[i][j].x, sc * acc[i][j].y);
+                for (int j = 0; j < 2; j++) {
+                    s1[(r + i) * M + c + j] = acc[i][j];
+                    acc[i][j] = make_float2(0.f, 0.f);
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++)   // A, row-major, from registers
+            if (threadIdx.x + u * B < M2) s0[threadIdx.x + u * B] = av[u];
+        __syncthreads();
+        if (active) tile22(s1, s0, M, r, c, acc);   // T A
+        __syncthreads();                            // every read of A done before R overwrites it
+        if (active) {
+            const float sc = (float)((ch == 0 ? 1.0 : 2.0) * scal[1]);   // c_P = 1, c_C = 2, times the output scale
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) s0[(r + i) * M + c + j] = make_float2(sc * acc[i][j].x, sc * acc[i][j].y);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int k = m0; k < m1; k++) {
-        const int q2 = orb_q[k];
-        double2 *o = out + ((size_t)ch * Nq + q2) * M2;
-        if (q2 == q) {
-            for (int i = threadIdx.x; i < M2; i += blockDim.x) store_w(o + i, s0[i]);
-        } else {
-            const int *em = emap + ((size_t)qmap[q2].y * 2 + ch) * M2;
-            for (int i = threadIdx.x; i < M2; i += blockDim.x) {
-                const int code = em[i];
-                float2 v = s0[code >> 3];
-                if (code & 1) v.y = -v.y;
-                store_w(o + i, quarter_turn(v, code >> 1));
+    // the orbit's matrices, (member k, entry i) advanced incrementally over nmem x M^2
+    const int total = nmem * M2;
+    int k = 0, i = threadIdx.x;
+    while (i >= M2) {
+        i -= M2;
+        k++;
+    }
+    for (int base = threadIdx.x; base < total; base += ORB_UNITS * B) {
+        int kk[ORB_UNITS], ii[ORB_UNITS], code[ORB_UNITS];
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) {
+            kk[u] = k;
+            ii[u] = i;
+            i += B;
+            while (i >= M2) {
+                i -= M2;
+                k++;
             }
+        }
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) {
+            const bool ok = on && base + u * B < total;
+            const int e = ok ? s_e[kk[u]] : -1;
+            code[u] = e >= 0 ? emap[((size_t)e * 2 + ch) * M2 + ii[u]] : ii[u] << 3;
+        }
+#pragma unroll
+        for (int u = 0; u < ORB_UNITS; u++) {
+            if (base + u * B >= total) break;
+            float2 v = make_float2(0.f, 0.f);
+            if (on) {
+                v = s0[code[u] >> 3];
+                if (code[u] & 1) v.y = -v.y;
+                v = quarter_turn(v, code[u] >> 1);
+            }
+            store_w(out + ((size_t)ch * Nq + s_q2[kk[u]]) * M2 + ii[u], v);
         }
     }
 }
@@ -356,6 +405,8 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
     return cudaGetLastError();
 }
 
+int orbit_max_size() { return ORB_MAX; }
+
 bool orbit_products_supported(const tufrg_model *m)
 {
     return m->ns == 2 && m->M <= 64 && m->M % 2 == 0 && m->precision != TUFRG_FP64;
@@ -374,7 +425,7 @@ cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out
         TUFRG_CUDA_TRY(cudaFuncSetAttribute(vlv_orbit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PhaseScope ps(m, PH_VLV);
     vlv_orbit_kernel<<<dim3(m->n_loop_q, 2), threads, smem, m->stream>>>(
-        m->d_A32, m->d_Lc32, m->d_dij, m->Nq, M, m->nff, m->nd, channel_mask, m->d_scal, m->d_loop_list, m->d_orb_ofs,
+        m->d_A32, m->d_Lc32, m->d_orb_lexp, m->Nq, M, m->nd, channel_mask, m->d_scal, m->d_loop_list, m->d_orb_ofs,
         m->d_orb_q, m->d_qmap, m->d_sym_emap, d_out);
     return cudaGetLastError();
 }

@@ -76,6 +76,47 @@ __device__ __forceinline__ double widen_f(float f)
     return __hiloint2double((int)w.x, (int)w.y);
 }
 
+// FP64 -> FP32 rounding to nearest, ties to even (IEEE 754 convertFormat), on the integer pipe for the
+// same reason, without branches (a branch per value stalls the loads that feed it): the 53-bit
+// significand (hidden bit included) is shifted right by 29 places, more for a subnormal or zero result,
+// and rounded on the discarded bits; a carry out of the significand increments the exponent field,
+// which also turns the largest finite values into infinity where they round up.  Results beyond the
+// FP32 range, infinities and NaNs (quiet, top payload bits kept) are selected at the end.
+static __device__ __noinline__ float narrow_general(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned long long man = b & 0xfffffffffffffull;
+    const int E0 = e - 896;                                     // biased FP32 exponent of a normal result
+    const int shift = min(29 + max(0, 1 - E0), 63);
+    const unsigned long long sig = man | (e ? (1ull << 52) : 0ull);
+    const unsigned long long kept = sig >> shift, rem = sig & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+    const unsigned r = (unsigned)kept + ((rem > half || (rem == half && (kept & 1ull))) ? 1u : 0u);
+    // normal: (E - 1) << 23 plus the significand with its hidden bit; subnormal: the significand alone
+    unsigned bits = (E0 > 0 ? (unsigned)(E0 - 1) << 23 : 0u) + r;
+    bits = E0 >= 255 ? 0x7f800000u : bits;
+    bits = e == 0x7ff ? 0x7f800000u | (man ? 0x400000u | (unsigned)(man >> 29) : 0u) : bits;
+    return __uint_as_float(sign | bits);
+}
+
+// The same rounding with a 32-bit fast path for zeros and normal FP32 results (biased FP64 exponent in
+// [897, 1150]): the FP32 exponent and significand are the FP64 fields above the 29 discarded bits,
+// rebiased; the rest takes the general path.
+__device__ __forceinline__ float narrow_f(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b, habs = hi & 0x7fffffffu;
+    if (habs - (897u << 20) < (254u << 20)) {
+        const unsigned f = __funnelshift_l(lo, habs - (896u << 20), 3);   // rebiased exponent | top 23 bits
+        const unsigned rem = lo & 0x1fffffffu;
+        const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+        return __uint_as_float((hi & 0x80000000u) | (f + up));
+    }
+    if ((habs | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return narrow_general(x);
+}
+
 struct LoopPlan {
     int kx_per_cta;     // threads (columns) per CTA
     int ky_chunks;      // number of ky ranges per column
@@ -146,6 +187,7 @@ struct tufrg_model {
     int *d_orb_ofs = nullptr;       // [n_loop_q + 1] orbit of each representative: momenta orb_q[ofs[p] .. ofs[p+1])
     int *d_orb_q = nullptr;         // [Nq]
     int *d_sym_emap = nullptr;      // [n_sym_elem][2][M^2] source entry << 3 | quarter turns << 1 | conj (small M)
+    int *d_orb_lexp = nullptr;      // [M^2] compact-loop index of every expanded loop-matrix entry (small M)
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
@@ -173,6 +215,12 @@ struct tufrg_model {
     float2 *d_ph32 = nullptr;       // [Nq][nph] phase table (split path)
     void *d_dftpart = nullptr;      // Fourier-transform partial sums (scratch)
     int dft_nsplit = 1;             // transfer-mesh slices of the Fourier transform
+    // separable Fourier transform: distinct R_y / R_x of the classes, warps per CTA (0 = not used),
+    // int tables (class id by R_y group, R_x index, R_y group offsets) and phases [Lq][n_Ry], [Lq][n_Rx]
+    int dft_nry = 0, dft_nrx = 0, dft_warps = 0, dft_epw_log2 = 5;
+    int *d_dft_tabs = nullptr;
+    double2 *d_dft_phy = nullptr, *d_dft_phx = nullptr;
+    float2 *d_dft_phy32 = nullptr, *d_dft_phx32 = nullptr;
     int max_terms = 0;              // largest gather-term list of one (R, R') pair
     unsigned long long *d_amax = nullptr;   // [4] reductions (max|A|, argmax, err)
     int *d_err = nullptr;           // device-side error flag (bounded waits)
@@ -227,11 +275,14 @@ cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
 // momenta, and no FP64 copy on the split path (what the symmetric-state products read)
 cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only = false);
 // The split path reads the FP32 copy of the state (d_state32), the plain path the FP64 state.
+// launch shape of the separable transform (warps per CTA, 0 if it does not apply; entries per warp)
+void dft_sep_plan(const tufrg_model *m, int *warps, int *epw_log2);
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask);
 // qlist (nlist entries): only these transfer momenta (the orbit representatives of a symmetric state)
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
                            double2 *d_A, const int *qlist = nullptr, int nlist = 0);
 cudaError_t launch_to_f32(tufrg_model *m, const double2 *d_state, float2 *d_out, size_t n);
+cudaError_t launch_round_f32(const double *d_in, float *d_out, size_t n, cudaStream_t stream);
 // qlist (nlist entries): only these transfer momenta
 cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist = nullptr,
                        int nlist = 0);
@@ -260,7 +311,8 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);
 // symmetric states: products at the orbit representatives and dX/dT of every momentum (the fused orbit
 // kernel where its tables exist, else the representatives' products plus the scatter)
 cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out);
-bool orbit_products_supported(const tufrg_model *m);   // symmetric states: non-representative momenta
+bool orbit_products_supported(const tufrg_model *m);
+int orbit_max_size();   // largest orbit the fused orbit kernel takes   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
 void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);
