@@ -797,10 +797,12 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                     for (size_t e = 0; e < ls.elem.size(); e++)
                         for (int ch = 0; ch < 2; ch++) {
                             const int *sr = &srow[(e * 2 + ch) * M], *qr = &qrow[(e * 2 + ch) * M];
+                            // i^k (conj ? conj(w) : w) as (swap, negate re, negate im), indexed [conj][k]
+                            static const int compose[2][4] = {{0, 6, 3, 5}, {1, 4, 2, 7}};
                             for (int r = 0; r < M; r++)
                                 for (int c = 0; c < M; c++)
                                     emap[((e * 2 + ch) * M + r) * M + c] =
-                                        (sr[r] * M + sr[c]) << 3 | ((qr[r] - qr[c]) & 3) << 1 | (ls.elem[e].conj ? 1 : 0);
+                                        (sr[r] * M + sr[c]) << 3 | compose[ls.elem[e].conj ? 1 : 0][(qr[r] - qr[c]) & 3];
                         }
                     std::vector<int> lexp((size_t)M * M);
                     for (int r = 0; r < M; r++)
@@ -947,7 +949,8 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     CK(dalloc(&m->d_Lc, 2 * (size_t)m->Nq * m->nd * ns4), "cudaMalloc loops");
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
-    m->part_bytes = (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
+    // partial sums of both channels (the split two-band path sums P and C before one reduction)
+    m->part_bytes = 2 * (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
     if (ns != 2) {
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
         m->gen_chunks = plan_gen_chunks(m);

@@ -279,15 +279,22 @@ __device__ __forceinline__ typename cpx<R>::t reduce_one(const typename cpx<R>::
 __device__ __forceinline__ double2 to64(double2 v) { return v; }
 __device__ __forceinline__ double2 to64(float2 v) { return make_double2(widen_f(v.x), widen_f(v.y)); }
 
-// Grid: blockIdx.y = transfer momentum (list position), threads over (d, ab) = t (t >> 4, t & 15):
+// Grid: blockIdx.y = transfer momentum (list position), blockIdx.z = channel (skipped when not in chmask;
+// its partials and outputs are offset by part_cs and out_cs), threads over (d, ab) = t (t >> 4, t & 15):
 // no runtime integer division (this GPU issues its conversions to the slow FP64 pipe).  List position s
 // is written at momentum qout[s] (orbit representatives only) or at s.
 template <typename R>
 __global__ void loops_reduce_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
                                     const int *dslot, const int *deltas, int nd, double inv_nk, const int *qout,
-                                    double2 *out64, typename cpx<R>::t *out32, const int *skip)
+                                    double2 *out64, typename cpx<R>::t *out32, const int *skip, int chmask,
+                                    size_t part_cs, size_t out_cs)
 {
     if (skip && *skip) return;
+    const int ch = blockIdx.z;
+    if (!((chmask >> ch) & 1)) return;
+    part += ch * part_cs;
+    if (out64) out64 += ch * out_cs;
+    if (out32) out32 += ch * out_cs;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nd * NS4) return;
     const int s = blockIdx.y, d = t / NS4, ab = t % NS4;
@@ -315,10 +322,16 @@ __device__ __forceinline__ C2 quarter_turn(C2 v, int k)
 template <typename R>
 __global__ void loops_reduce_sym_kernel(const typename cpx<R>::t *__restrict__ part, int n_part, int ndx, int ndyh,
                                         const int *dslot, const int *deltas, int nd, const int2 *qmap,
-                                        const SymElem *elem, const int *dinv, int ch, double inv_nk, double2 *out64,
-                                        typename cpx<R>::t *out32, const int *skip)
+                                        const SymElem *elem, const int *dinv, double inv_nk, double2 *out64,
+                                        typename cpx<R>::t *out32, const int *skip, int chmask, size_t part_cs,
+                                        size_t out_cs)
 {
     if (skip && *skip) return;
+    const int ch = blockIdx.z;   // as in loops_reduce_kernel
+    if (!((chmask >> ch) & 1)) return;
+    part += ch * part_cs;
+    out64 += ch * out_cs;
+    out32 += ch * out_cs;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nd * NS4) return;
     const int q2 = blockIdx.y, d2 = t / NS4, a2 = (t / NS2) % NS2, b2 = t % NS2;
@@ -390,7 +403,7 @@ cudaError_t launch_loops_reduce_f32(tufrg_model *m, const float2 *part, int n_s,
     PhaseScope ps(m, PH_LOOPRED);
     loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(part, m->plan.n_partials, (int)m->dxs.size(), ndyh,
                                                           m->d_dslot, m->d_deltas, m->nd, 1.0 / (double)m->Nk, nullptr,
-                                                          out64, out32, skip);
+                                                          out64, out32, skip, 1, 0, 0);
     return cudaGetLastError();
 }
 
@@ -405,31 +418,40 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
     int dys[MAXD];
     for (int v : m->dys)
         if (v >= 0) dys[ndyh++] = v;
+    if (loops2_supported(m)) {
+        // both channels' k-sums into their own halves of the partial buffer, then one reduction launch
+        const int n_s = m->sym ? m->n_loop_q : m->Nq;
+        const size_t part_cs = (size_t)n_s * pl.n_partials * ndx * ndyh * NS4, out_cs = (size_t)m->Nq * m->nd * NS4;
+        float2 *part = reinterpret_cast<float2 *>(m->d_part);
+        const int *skip = m->sur ? m->d_sur_flag : nullptr;
+        for (int ch = 0; ch < 2; ch++)
+            if ((channel_mask >> ch) & 1)
+                TUFRG_CUDA_TRY(launch_loops2_ex(m, ch, m->sym ? m->d_loop_list : nullptr, m->sym ? m->n_loop_q : 0,
+                                                part + ch * part_cs, skip));
+        dim3 grid;
+        int thr;
+        reduce_shape(m, reps_only ? m->n_loop_q : m->Nq, grid, thr);
+        grid.z = 2;
+        const double inv_nk = 1.0 / (double)m->Nk;
+        PhaseScope ps(m, PH_LOOPRED);
+        if (reps_only)   // the representatives' FP32 loops at their own momenta (what their products read)
+            loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas,
+                                                                  m->nd, inv_nk, m->d_loop_list, nullptr, m->d_Lc32, skip,
+                                                                  channel_mask, part_cs, out_cs);
+        else if (m->sym)
+            loops_reduce_sym_kernel<float><<<grid, thr, 0, m->stream>>>(
+                part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, m->d_qmap, m->d_sym_elem, m->d_sym_dinv,
+                inv_nk, m->d_Lc, m->d_Lc32, skip, channel_mask, part_cs, out_cs);
+        else
+            loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas,
+                                                                  m->nd, inv_nk, nullptr, m->d_Lc, m->d_Lc32, skip,
+                                                                  channel_mask, part_cs, out_cs);
+        return cudaGetLastError();
+    }
     for (int ch = 0; ch < 2; ch++) {
         if (!((channel_mask >> ch) & 1)) continue;
         const double inv_nk = 1.0 / (double)m->Nk;
-        if (loops2_supported(m)) {
-            TUFRG_CUDA_TRY(launch_loops2(m, ch));
-            const size_t off = (size_t)ch * m->Nq * m->nd * NS4;
-            dim3 grid;
-            int thr;
-            reduce_shape(m, reps_only ? m->n_loop_q : m->Nq, grid, thr);
-            PhaseScope ps(m, PH_LOOPRED);
-            if (reps_only)   // the representatives' FP32 loops at their own momenta (what their products read)
-                loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
-                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    inv_nk, m->d_loop_list, nullptr, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
-            else if (m->sym)
-                loops_reduce_sym_kernel<float><<<grid, thr, 0, m->stream>>>(
-                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    m->d_qmap, m->d_sym_elem, m->d_sym_dinv, ch, inv_nk, m->d_Lc + off, m->d_Lc32 + off,
-                    m->sur ? m->d_sur_flag : nullptr);
-            else
-                loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
-                    reinterpret_cast<float2 *>(m->d_part), pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd,
-                    inv_nk, nullptr, m->d_Lc + off, m->d_Lc32 + off, m->sur ? m->d_sur_flag : nullptr);
-            TUFRG_CUDA_TRY(cudaGetLastError());
-        } else if (m->precision == TUFRG_FP64) {
+        if (m->precision == TUFRG_FP64) {
             LoopArgs<double> a{};
             a.U = m->d_U; a.ft = m->d_ft; a.part = reinterpret_cast<double2 *>(m->d_part);
             a.Lq = m->Lq; a.nc = m->nc; a.Lf = m->Lf; a.ndx = ndx; a.ndyh = ndyh;
@@ -456,7 +478,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<double><<<grid, thr, 0, m->stream>>>(
                 a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk, nullptr,
-                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr, nullptr);
+                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, nullptr, nullptr, 1, 0, 0);
             TUFRG_CUDA_TRY(cudaGetLastError());
         } else {
             LoopArgs<float> a{};
@@ -485,7 +507,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
             PhaseScope ps(m, PH_LOOPRED);
             loops_reduce_kernel<float><<<grid, thr, 0, m->stream>>>(
                 a.part, pl.n_partials, ndx, ndyh, m->d_dslot, m->d_deltas, m->nd, inv_nk, nullptr,
-                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4, nullptr);
+                m->d_Lc + (size_t)ch * m->Nq * m->nd * NS4, m->d_Lc32 + (size_t)ch * m->Nq * m->nd * NS4, nullptr, 1, 0, 0);
             TUFRG_CUDA_TRY(cudaGetLastError());
         }
     }

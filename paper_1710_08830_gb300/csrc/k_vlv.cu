@@ -88,22 +88,14 @@ __device__ __forceinline__ void store_w(double2 *o, float2 v)
     *reinterpret_cast<uint4 *>(o) = make_uint4(re.y, re.x, im.y, im.x);
 }
 
-__device__ __forceinline__ float2 quarter_turn(float2 v, int k)
-{
-    switch (k & 3) {
-    case 0: return v;
-    case 1: return make_float2(-v.y, v.x);
-    case 2: return make_float2(-v.x, -v.y);
-    default: return make_float2(v.y, -v.x);
-    }
-}
-
 // Symmetric states, two-band bond sets (M = 4 N_ff <= 64), split path.  One CTA per (orbit
 // representative q, channel) forms c A L A at q with one 2 x 2 output tile per thread ((M/2)^2 threads;
 // per element the same FP32 arithmetic as vlv_tiled_kernel) and writes dX/dT of every momentum q' of the
 // orbit from the result R held in shared memory:
-//   out[q'][t] = i^turns (conj ? conj(R[src]) : R[src]),   emap[e][ch][t] = src << 3 | turns << 1 | conj,
-// e the element that maps q to q' (the representative itself is written as is).  Every thread owns at
+//   out[q'][t] = i^turns (conj ? conj(R[src]) : R[src]),
+// e the element that maps q to q' (the representative itself is written as is).  The index map holds the
+// composed transform, emap[e][ch][t] = src << 3 | swap << 2 | negate_re << 1 | negate_im: with
+// w = R[src], out = (+-(swap ? w.y : w.x), +-(swap ? w.x : w.y)).  Every thread owns at
 // most ORB_UNITS entries of each matrix pass; the loads of a pass are issued before their uses, the
 // orbit's momenta and elements sit in shared memory, and the stores are coalesced.  lexp[t] is the
 // compact-loop index of expanded entry t, L[(R1,a),(R2,b)] = Lc[d(R1-R2)][a][b].
@@ -229,9 +221,10 @@ __global__ void __launch_bounds__(1024) vlv_orbit_kernel(const float2 *__restric
             if (base + u * B >= total) break;
             float2 v = make_float2(0.f, 0.f);
             if (on) {
-                v = s0[code[u] >> 3];
-                if (code[u] & 1) v.y = -v.y;
-                v = quarter_turn(v, code[u] >> 1);
+                const float2 w = s0[code[u] >> 3];
+                const bool sw = code[u] & 4;
+                v.x = __uint_as_float(__float_as_uint(sw ? w.y : w.x) ^ ((unsigned)(code[u] & 2) << 30));
+                v.y = __uint_as_float(__float_as_uint(sw ? w.x : w.y) ^ ((unsigned)(code[u] & 1) << 31));
             }
             store_w(out + ((size_t)ch * Nq + s_q2[kk[u]]) * M2 + ii[u], v);
         }

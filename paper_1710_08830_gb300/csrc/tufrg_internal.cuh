@@ -60,7 +60,7 @@ struct SymElem {
 // (hi, lo) words of the exact double of a float, formed on the integer pipe only (this GPU's FP64 pipe,
 // which also executes conversions, is slow; a branch to a plain conversion gets if-converted into an
 // unconditional one): normal, zero, subnormal (normalised with clz), inf and nan.
-__device__ __forceinline__ uint2 widen_bits(float f)
+static __device__ __noinline__ uint2 widen_general(float f)
 {
     const unsigned u = __float_as_uint(f), sign = u & 0x80000000u, e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
     if (e == 0xffu) return make_uint2(sign | 0x7ff00000u | (man >> 3), man << 29);
@@ -70,6 +70,16 @@ __device__ __forceinline__ uint2 widen_bits(float f)
     const unsigned long long fr = (unsigned long long)(man & ((1u << p) - 1u)) << (52 - p);
     return make_uint2(sign | ((unsigned)(p - 149 + 1023) << 20) | (unsigned)(fr >> 32), (unsigned)fr);
 }
+// The same with a fast path for normal values and zeros (the exponent rebiased, the significand moved
+// down 3 bits into the high word, its low 3 bits to the top of the low word).
+__device__ __forceinline__ uint2 widen_bits(float f)
+{
+    const unsigned u = __float_as_uint(f), a = u & 0x7fffffffu, sign = u & 0x80000000u;
+    if (a - 0x00800000u < 0x7f000000u) return make_uint2(sign | ((a >> 3) + (896u << 20)), a << 29);
+    if (a == 0u) return make_uint2(sign, 0u);
+    return widen_general(f);
+}
+
 __device__ __forceinline__ double widen_f(float f)
 {
     const uint2 w = widen_bits(f);
