@@ -67,7 +67,10 @@ typedef enum {
  * FP32-accurate products; the state and its update stay FP64. */
 enum { TUFRG_FP64 = 0, TUFRG_SPLIT32 = 1 };
 /* Backend of the V.L.V products on the split path: tensor cores (tcgen05, 3xTF32, FP32 accumulation in
- * tensor memory) or FP32 CUDA cores; AUTO times both on the model's sizes at init and keeps the faster. */
+ * tensor memory) or FP32 CUDA cores; AUTO times both on the model's sizes at init and keeps the faster.
+ * Timed choices (this one and the symmetric-state one below) are made once per shape in the process
+ * (device, precision and sizes) and reused by later models of that shape, so that equal models take
+ * equal paths and give equal results. */
 enum { TUFRG_PRODUCTS_AUTO = 0, TUFRG_PRODUCTS_TC = 1, TUFRG_PRODUCTS_SIMT = 2 };
 enum { TUFRG_CH_P = 1, TUFRG_CH_C = 2 };
 
@@ -101,7 +104,8 @@ typedef struct {
  * operations that hold (U searched among the monomial unitaries) are found at init, the k-sum runs
  * for one momentum per orbit and the others are written from it.  TUFRG_SYMMETRY_OFF sums every q. */
 /* For symmetric states (tufrg_rhs with TUFRG_SYMMETRIC_STATE, and every flow) the projections and products can
- * run for the orbit representatives only; AUTO does so when a timing at init shows it faster, STATES always. */
+ * run for the orbit representatives only; AUTO does so when a timing at init shows it faster (one timing
+ * per shape in the process, see TUFRG_PRODUCTS_AUTO), STATES always. */
 enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1, TUFRG_SYMMETRY_STATES = 2 };
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */

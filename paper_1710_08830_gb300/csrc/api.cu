@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 
@@ -432,6 +433,40 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
             if (ls.qmap[q2].x < 0) ls.qmap[q2] = make_int2(pos, (int)e);
         }
     }
+}
+
+// Autotuner decisions, shared by every model of the same shape in the process: the first model of a
+// shape times the alternatives, later ones reuse its choice, so that equal models take equal paths (and
+// give equal results) whatever the timing noise.  Key: device, decision kind and the sizes the costs
+// depend on.
+struct TuneResult {
+    double ms[2];
+    int choice;
+};
+std::mutex g_tune_mutex;
+std::map<std::vector<int>, TuneResult> g_tune_cache;
+
+std::vector<int> tune_key(const tufrg_model *m, int kind)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return {dev, kind, m->precision, m->ns, m->M, m->Lq, m->nc, m->nd, m->nff, m->n_loop_q, m->n_sym_elem,
+            m->d_sym_emap ? 1 : 0};
+}
+
+bool tune_lookup(const tufrg_model *m, int kind, TuneResult *r)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(tune_key(m, kind));
+    if (it == g_tune_cache.end()) return false;
+    *r = it->second;
+    return true;
+}
+
+void tune_store(const tufrg_model *m, int kind, const TuneResult &r)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.emplace(tune_key(m, kind), r);   // a concurrent first store wins
 }
 
 // e^{i q.R} for every coarse q and every listed vector (exact lattice phases).
@@ -1009,7 +1044,12 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     }
     if (loops2_supported(m)) CK(launch_loop_records_static(m), "loop records");
     CK(cudaStreamSynchronize(m->stream), "init sync");
-    if (split && d.products == TUFRG_PRODUCTS_AUTO) {
+    TuneResult cached{};
+    if (split && d.products == TUFRG_PRODUCTS_AUTO && tune_lookup(m, 0, &cached)) {
+        m->products = cached.choice;
+        m->tune_ms[0] = cached.ms[0];
+        m->tune_ms[1] = cached.ms[1];
+    } else if (split && d.products == TUFRG_PRODUCTS_AUTO) {
         // autotune the products backend on this model's sizes (the cost does not depend on the values)
         const size_t nA = 2 * (size_t)m->Nq * M2;
         double2 *tmp = nullptr;
@@ -1034,6 +1074,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             m->tune_ms[c] = ms / reps;
         }
         m->products = m->tune_ms[0] <= m->tune_ms[1] ? TUFRG_PRODUCTS_TC : TUFRG_PRODUCTS_SIMT;
+        tune_store(m, 0, TuneResult{{m->tune_ms[0], m->tune_ms[1]}, m->products});
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaFree(tmp);
@@ -1043,7 +1084,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
         if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
     }
-    if (m->sym_state) {
+    if (m->sym_state && d.symmetry != TUFRG_SYMMETRY_STATES && tune_lookup(m, 1 + m->products, &cached)) {
+        m->sym_state_pays = cached.choice != 0;
+        m->sym_tune_ms[0] = cached.ms[0];
+        m->sym_tune_ms[1] = cached.ms[1];
+    } else if (m->sym_state) {
         // symmetric states: projections and products for the orbit representatives plus the gather of the
         // other momenta, against both for every momentum (on zeroed operands: the cost does not depend on
         // the values); the representatives' path is used only where it is faster
@@ -1084,7 +1129,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             CK(cudaEventElapsedTime(&ms, e0, e1), "event");
             m->sym_tune_ms[c] = ms / reps;
         }
-        m->sym_state_pays = d.symmetry == TUFRG_SYMMETRY_STATES || m->sym_tune_ms[1] < m->sym_tune_ms[0];
+        m->sym_state_pays = m->sym_tune_ms[1] < m->sym_tune_ms[0];
+        if (d.symmetry != TUFRG_SYMMETRY_STATES) tune_store(m, 1 + m->products, TuneResult{{m->sym_tune_ms[0], m->sym_tune_ms[1]}, m->sym_state_pays ? 1 : 0});
+        m->sym_state_pays = m->sym_state_pays || d.symmetry == TUFRG_SYMMETRY_STATES;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaFree(tmp);
