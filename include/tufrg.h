@@ -68,9 +68,8 @@ typedef enum {
 enum { TUFRG_FP64 = 0, TUFRG_SPLIT32 = 1 };
 /* Backend of the V.L.V products on the split path: tensor cores (tcgen05, 3xTF32, FP32 accumulation in
  * tensor memory) or FP32 CUDA cores; AUTO times both on the model's sizes at init and keeps the faster.
- * Timed choices (this one and the symmetric-state one below) are made once per shape in the process
- * (device, precision and sizes) and reused by later models of that shape, so that equal models take
- * equal paths and give equal results. */
+ * The timed choice is made once per shape in the process (device, precision and sizes) and reused by
+ * later models of that shape, so that equal models take equal paths and give equal results. */
 enum { TUFRG_PRODUCTS_AUTO = 0, TUFRG_PRODUCTS_TC = 1, TUFRG_PRODUCTS_SIMT = 2 };
 enum { TUFRG_CH_P = 1, TUFRG_CH_C = 2 };
 
@@ -104,8 +103,8 @@ typedef struct {
  * operations that hold (U searched among the monomial unitaries) are found at init, the k-sum runs
  * for one momentum per orbit and the others are written from it.  TUFRG_SYMMETRY_OFF sums every q. */
 /* For symmetric states (tufrg_rhs with TUFRG_SYMMETRIC_STATE, and every flow) the projections and products can
- * run for the orbit representatives only; AUTO does so when a timing at init shows it faster (one timing
- * per shape in the process, see TUFRG_PRODUCTS_AUTO), STATES always. */
+ * run for the orbit representatives only, and do so whenever the state symmetries hold (AUTO and STATES
+ * alike; OFF disables every symmetry).  Both paths are timed at init for tufrg_symmetry_info. */
 enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1, TUFRG_SYMMETRY_STATES = 2 };
 
 /* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
@@ -162,9 +161,9 @@ tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda
 
 /* Symmetric-state path (TUFRG_SYMMETRIC_STATE): *in_use = 1 when calls that set the flag project and
  * multiply at the orbit representatives only, 0 when they take the general path (the state symmetries
- * do not hold for this model, or the representatives' path was not faster at init).  *ms_general and
- * *ms_reps are the init-time timings of projections + products of both channels on the two paths in
- * milliseconds (-1 when not measured).  Errors: TUFRG_EINVAL for NULL arguments. */
+ * do not hold for this model).  *ms_general and *ms_reps are the init-time timings of projections +
+ * products of both channels on the two paths in milliseconds (-1 when not measured).
+ * Errors: TUFRG_EINVAL for NULL arguments. */
 tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps);
 
 /* Host copy of the sorted bond-difference list [n_delta][2] used by the compact loops. */

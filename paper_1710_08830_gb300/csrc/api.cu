@@ -519,7 +519,7 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
 {
     const bool split = m->precision != TUFRG_FP64;
     // a symmetric state needs projections and products at the orbit representatives only
-    const bool sym = symmetric_state && m->sym_state && m->sym_state_pays;
+    const bool sym = symmetric_state && m->sym_state;
     const int *ql = sym ? m->d_loop_list : nullptr;
     const int nl = sym ? m->n_loop_q : 0;
     // without an FP32 copy the separable transform writes one as it reads the FP64 state (the sliced
@@ -682,7 +682,7 @@ tufrg_status flow_finish(tufrg_model *m, void *d_state_out, tufrg_flow_result *r
     res->Tc = res->crossed ? f.Tc : res->T_last;
     // the last stage-7 projection belongs to the last accepted state when the flow stopped on an accepted step
     const size_t nA = state_elems(m), M2 = (size_t)m->M * m->M;
-    CK(launch_amax_locate(m, nA, m->sym_state && m->sym_state_pays), "locate maximum");
+    CK(launch_amax_locate(m, nA, m->sym_state), "locate maximum");
     unsigned long long b[4];
     CK(cudaMemcpyAsync(b, m->d_amax, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy scalars");
     CK(cudaStreamSynchronize(m->stream), "sync");
@@ -1084,14 +1084,14 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
         if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
     }
-    if (m->sym_state && d.symmetry != TUFRG_SYMMETRY_STATES && tune_lookup(m, 1 + m->products, &cached)) {
-        m->sym_state_pays = cached.choice != 0;
+    if (m->sym_state && tune_lookup(m, 1 + m->products, &cached)) {
         m->sym_tune_ms[0] = cached.ms[0];
         m->sym_tune_ms[1] = cached.ms[1];
     } else if (m->sym_state) {
         // symmetric states: projections and products for the orbit representatives plus the gather of the
         // other momenta, against both for every momentum (on zeroed operands: the cost does not depend on
-        // the values); the representatives' path is used only where it is faster
+        // the values).  Reported only: the representatives' path is taken whenever the symmetries hold (a
+        // timing-based choice would differ between processes, e.g. under a profiler)
         const size_t nA = 2 * (size_t)m->Nq * M2;
         double2 *tmp = nullptr;
         CK(dalloc(&tmp, nA), "cudaMalloc autotune output");
@@ -1129,9 +1129,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             CK(cudaEventElapsedTime(&ms, e0, e1), "event");
             m->sym_tune_ms[c] = ms / reps;
         }
-        m->sym_state_pays = m->sym_tune_ms[1] < m->sym_tune_ms[0];
-        if (d.symmetry != TUFRG_SYMMETRY_STATES) tune_store(m, 1 + m->products, TuneResult{{m->sym_tune_ms[0], m->sym_tune_ms[1]}, m->sym_state_pays ? 1 : 0});
-        m->sym_state_pays = m->sym_state_pays || d.symmetry == TUFRG_SYMMETRY_STATES;
+        tune_store(m, 1 + m->products, TuneResult{{m->sym_tune_ms[0], m->sym_tune_ms[1]}, 1});
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaFree(tmp);
@@ -1171,7 +1169,7 @@ tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda
 tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps)
 {
     if (!m || !in_use || !ms_general || !ms_reps) return TUFRG_EINVAL;
-    *in_use = m->sym_state && m->sym_state_pays ? 1 : 0;
+    *in_use = m->sym_state ? 1 : 0;
     *ms_general = m->sym_state ? m->sym_tune_ms[0] : -1.0;
     *ms_reps = m->sym_state ? m->sym_tune_ms[1] : -1.0;
     return TUFRG_OK;

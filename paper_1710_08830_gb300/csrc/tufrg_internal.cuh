@@ -190,7 +190,6 @@ struct tufrg_model {
     // element's bond permutation times its orbital-pair map, so projections and products run for the orbit
     // representatives only and dX/dT of the other momenta is gathered from them
     bool sym_state = false;
-    bool sym_state_pays = false;    // autotuned at init: the representatives' products are faster
     double sym_tune_ms[2] = {-1.0, -1.0};   // projections + products at every momentum / representatives + gather
     int *d_sym_srow = nullptr;      // [n_sym_elem][2][M] source index of every target row / column
     int *d_sym_qrow = nullptr;      // [n_sym_elem][2][M] quarter turns of every target row / column
