@@ -443,6 +443,8 @@ def main():
     # one launch sums every fine k for each directly evaluated transfer momentum (the loop symmetries
     # supply the other momenta)
     flops_per_launch = 8.0 * m32.n_loop_q * spec.Nk * unit_cfma
+    # the timed loop's products run at the orbit representatives when the state symmetries hold
+    n_products = m32.n_loop_q if m32.symmetric_state_path else spec.Nq
     loop_ms_avg = phase_ms["loops"] / max(1, loop_launches)
     achieved = flops_per_launch / (loop_ms_avg * 1e-3) / 1e12
     trec = loop_traffic_record()[0] if args.workload == "rashba" else None   # recorded for that workload
@@ -499,12 +501,13 @@ def main():
                     "d2h_bytes_per_step": state_bytes},
             "roofline": roofline,
             "roofline_products": ({"bound": "tensor", "kernel": "tc_cgemm_kernel + operand packing (tcgen05, 3xTF32)",
-                                   "achieved": products_tf32_flop(spec.M, spec.Nq) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12,
+                                   "achieved": products_tf32_flop(spec.M, n_products) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12,
                                    "peak": tf32_peak_tflops(peaks), "unit": "TFLOP/s",
-                                   "frac": products_tf32_flop(spec.M, spec.Nq) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12
+                                   "frac": products_tf32_flop(spec.M, n_products) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12
                                            / tf32_peak_tflops(peaks),
                                    "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
-                                   "work": "2 channels x 2 complex M^3 GEMMs x 4 real x 3 TF32 per momentum"}
+                                   "work": f"2 channels x 2 complex M^3 GEMMs x 4 real x 3 TF32 per multiplied momentum "
+                                           f"({n_products} of {spec.Nq}); the phase time includes the symmetric scatter"}
                                   if m32.products == "tc" else None),
             "cpu_baseline": cpu,
             "batch_flows": batch,
