@@ -31,6 +31,30 @@ constexpr int MAXD = 9;
 constexpr int WARPS = 2;
 
 constexpr int RECF4 = 3;         // float4 planes per record
+constexpr int RING = 4;          // rows of records in flight per thread (asynchronous copies into shared memory)
+
+// Shared memory of one CTA: the phase table, then one region per warp that holds the warp's ring of
+// record rows during the k-sum ([RING][2 sides x 3 planes][32 lanes] float4) and its flush buffer
+// (32 x (2 NDYH 16 + 1) floats) after it.
+__host__ __device__ constexpr size_t warp_region_bytes(int ndyh)
+{
+    return ((sizeof(float) * 32 * (2 * ndyh * 16 + 1) > sizeof(float4) * RING * 2 * RECF4 * 32
+                 ? sizeof(float) * 32 * (2 * ndyh * 16 + 1)
+                 : sizeof(float4) * RING * 2 * RECF4 * 32) + 15) & ~size_t(15);
+}
+inline size_t loops2_smem_bytes(int Lf, int ndyh)
+{
+    return ((sizeof(float2) * Lf + 15) & ~size_t(15)) + WARPS * warp_region_bytes(ndyh);
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), and the waits on this thread's own copy groups
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 struct Args2 {
     const float4 *rec;       // [3][Lf][Lf] planes, index [j][ky][kx]:
@@ -72,7 +96,6 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.skip && *a.skip) return;   // uniform over the grid
     float2 *ptab = reinterpret_cast<float2 *>(smem_raw);
-    float *red = reinterpret_cast<float *>(smem_raw + ((sizeof(float2) * a.Lf + 15) & ~size_t(15)));
     const int Lf = a.Lf;
     if (a.ptab) {
         for (int n = threadIdx.x; n < Lf; n += blockDim.x) ptab[n] = a.ptab[n];
@@ -90,6 +113,8 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     const int sq = a.s_list ? a.s_list[blockIdx.x] : blockIdx.x;  // transfer momentum
     const int sx = (sq / a.Lq) * a.nc, sy = (sq % a.Lq) * a.nc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *region = smem_raw + ((sizeof(float2) * Lf + 15) & ~size_t(15)) + warp * warp_region_bytes(NDYH);
+    float4 *ring = reinterpret_cast<float4 *>(region);   // [RING][6][32]: rows in flight of this warp's columns
     const int kx = blockIdx.y * NT + threadIdx.x;
     const float thr = a.Tp ? (float)(1e-2 * *a.Tp) : a.thr;
     const bool valid = kx < Lf;
@@ -120,24 +145,36 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
         int k1y = WHICH == 0 ? ((sy - ky0) % Lf + Lf) % Lf : ky0;
         int k2y = WHICH == 0 ? ky0 : ((ky0 - sy) % Lf + Lf) % Lf;
         const size_t plane = (size_t)Lf * Lf;
-        const float4 *P0 = a.rec, *P1 = a.rec + plane, *P2 = a.rec + 2 * plane;
-        int o1 = k1y * Lf + k1x, o2 = k2y * Lf + k2x;        // offsets of the row being loaded
-        float4 n0 = __ldg(P0 + o1), n1 = __ldg(P1 + o1), n2 = __ldg(P2 + o1);
-        float4 m0 = __ldg(P0 + o2), m1 = __ldg(P1 + o2), m2 = __ldg(P2 + o2);
+        int o1 = k1y * Lf + k1x, o2 = k2y * Lf + k2x;        // offsets of the next row to be copied
+        const int wrap = (Lf - 1) * Lf;
+        // copy one row (both sides, three planes) into ring slot sl, then step the offsets to the next
+        // row: the q side moves by +Lf, the s - q side by -Lf (P), both +Lf (C), with wrap
+        auto issue_row = [&](int sl) {
+            float4 *r = ring + sl * 2 * RECF4 * 32 + lane;
+#pragma unroll
+            for (int pl = 0; pl < RECF4; pl++) {
+                cp_async16(r + pl * 32, a.rec + pl * plane + o1);
+                cp_async16(r + (RECF4 + pl) * 32, a.rec + pl * plane + o2);
+            }
+            if (WHICH == 0) { o1 = o1 >= Lf ? o1 - Lf : o1 + wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
+            else            { o1 = o1 < wrap ? o1 + Lf : o1 - wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
+        };
+#pragma unroll
+        for (int i = 0; i < RING - 1; i++) {   // rows ky0 .. ky0 + RING - 2 in flight
+            if (ky0 + i < ky1) issue_row(i);
+            cp_async_commit();
+        }
         int pn[MAXD];
 #pragma unroll
         for (int i = 1; i < NDYH; i++) pn[i] = (int)(((long)ky0 * a.dys[i]) % Lf);
         const float sgn = WHICH == 0 ? 1.f : -1.f;
-        const int wrap = (Lf - 1) * Lf;
         for (int ky = ky0; ky < ky1; ky++) {
-            const float4 a0 = n0, a1 = n1, a2 = n2, b0 = m0, b1 = m1, b2 = m2;
-            // next row: the q side moves by +Lf, the s - q side by -Lf (P), both +Lf (C), with wrap
-            if (WHICH == 0) { o1 = o1 >= Lf ? o1 - Lf : o1 + wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
-            else            { o1 = o1 < wrap ? o1 + Lf : o1 - wrap; o2 = o2 < wrap ? o2 + Lf : o2 - wrap; }
-            if (ky + 1 < ky1) {
-                n0 = __ldg(P0 + o1); n1 = __ldg(P1 + o1); n2 = __ldg(P2 + o1);
-                m0 = __ldg(P0 + o2); m1 = __ldg(P1 + o2); m2 = __ldg(P2 + o2);
-            }
+            const int it = ky - ky0;
+            if (ky + RING - 1 < ky1) issue_row((it + RING - 1) & (RING - 1));
+            cp_async_commit();
+            cp_async_wait<RING - 1>();   // this thread's copies of row ky have landed
+            const float4 *r = ring + (it & (RING - 1)) * 2 * RECF4 * 32 + lane;
+            const float4 a0 = r[0], a1 = r[32], a2 = r[64], b0 = r[96], b1 = r[128], b2 = r[160];
             // pair weights w[l1][l2]: l1 on k1, l2 on k2
             const float e1[2] = {a0.w, a1.x}, g1[2] = {a1.y, a1.z}, gp1[2] = {a1.w, a2.x};
             const float e2[2] = {b0.w, b1.x}, g2[2] = {b1.y, b1.z}, gp2[2] = {b1.w, b2.x};
@@ -188,6 +225,7 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
                 }
             }
         }
+        cp_async_wait<0>();   // nothing in flight before the region is reused below (trailing groups are empty)
     }
 
     // ---- rebuild W[dy][ab] from the paired sums
@@ -218,7 +256,8 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     // ---- flush: per distinct dx, multiply by e^{-i kx dx}, sum the warp through smem
     constexpr int NV = 2 * NDYH * 16;
     constexpr int PITCH = NV + 1;
-    float *buf = red + warp * 32 * PITCH;
+    float *buf = reinterpret_cast<float *>(region);
+    __syncwarp();   // every lane of the warp is done with its ring entries (lanes past Lf skipped the k-sum)
     const int n_part = gridDim.y * WARPS * gridDim.z;
     const int p = (blockIdx.y * WARPS + warp) * gridDim.z + kyc;
     for (int dxi = 0; dxi < a.ndx; dxi++) {
@@ -291,8 +330,7 @@ template <int NDYH, int WHICH>
 cudaError_t launch2(tufrg_model *m, const Args2 &a, int n_s)
 {
     dim3 grid(n_s, (m->Lf + 32 * WARPS - 1) / (32 * WARPS), a.ky_chunks);
-    const size_t flush = sizeof(float) * WARPS * 32 * (2 * NDYH * 16 + 1);
-    const size_t smem = ((sizeof(float2) * m->Lf + 15) & ~size_t(15)) + flush;
+    const size_t smem = loops2_smem_bytes(m->Lf, NDYH);
     auto kern = loops2_kernel<NDYH, WHICH>;
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PhaseScope ps(m, PH_LOOPS);
@@ -307,7 +345,7 @@ int loops2_blocks_per_sm(const tufrg_model *m)
 {
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
-    const size_t smem = ((sizeof(float2) * m->Lf + 15) & ~size_t(15)) + sizeof(float) * WARPS * 32 * (2 * ndyh * 16 + 1);
+    const size_t smem = loops2_smem_bytes(m->Lf, ndyh);
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     if (ndyh == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, loops2_kernel<1, 0>, 32 * WARPS, smem);
@@ -520,8 +558,7 @@ extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, c
         const int yi = (int)(std::find(dyh.begin(), dyh.end(), dy) - dyh.begin());
         t.slot[k] = xi * ndyh + yi;
     }
-    const size_t flush = sizeof(float) * WARPS * 32 * (2 * ndyh * 16 + 1);
-    const size_t smem = ((sizeof(float2) * Lf + 15) & ~size_t(15)) + flush;
+    const size_t smem = loops2_smem_bytes(Lf, ndyh);
     const dim3 grid(Nq, ctas_x, 1);
     const size_t per = (size_t)Nq * nd * 16;
     for (int ch = 0; ch < 2; ch++) {
