@@ -208,6 +208,16 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
  * copies dX/dT back into h_dstate and synchronises the stream. */
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate);
 
+/* n right-hand sides from and to host memory with the transfers overlapped: step i reads the state at
+ * h_states[i] and writes dX/dT at T[i] to h_dstates[i] (host buffers in the layout of tufrg_rhs, pinned
+ * for the copies to overlap; a pointer may repeat).  The host -> device copy of step i + 1 and the
+ * device -> host copy of step i - 1 run on two copy streams of the model while step i is evaluated on the
+ * model's stream (two device buffers per direction, allocated at the first call).  Returns when every
+ * result has arrived.  channel_mask as for tufrg_rhs (TUFRG_SYMMETRIC_STATE included).  Errors as for
+ * tufrg_rhs_host; the host buffers are not in use any more when the call returns, also on error. */
+tufrg_status tufrg_rhs_host_batch(tufrg_model *m, int n, const double *T, const void *const *h_states, int channel_mask,
+                                  void *const *h_dstates);
+
 /* Adaptive flow from X(T0) = 0 (Eqs. def_VP... at Lambda_0) down to T_end or to
  * max|A| > opts->stop.  The Dormand-Prince controller runs on the device: one attempt
  * (six stage right-hand sides, error norm, accept/reject, FSAL commit) is captured once as

@@ -84,6 +84,8 @@ def lib():
             L.tufrg_project.argtypes = [vp, vp, i, vp, C.POINTER(d)]
             L.tufrg_rhs.argtypes = [vp, d, vp, i, vp]
             L.tufrg_rhs_host.argtypes = [vp, d, vp, i, vp]
+            L.tufrg_rhs_host_batch.argtypes = [vp, i, C.POINTER(d), C.POINTER(vp), i, C.POINTER(vp)]
+            L.tufrg_rhs_host_batch.restype = C.c_int
             L.tufrg_flow.argtypes = [vp, C.POINTER(FlowOpts), vp, C.POINTER(FlowResult)]
             L.tufrg_loops_noalloc.argtypes = [i, i, vp, vp, d, d, i, vp, i, vp, vp]
             L.tufrg_loops_noalloc.restype = C.c_int
@@ -122,7 +124,7 @@ def lib():
 EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "tufrg_deltas",
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
            "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info", "tufrg_loop_momenta",
-           "tufrg_symmetry_info", "tufrg_round_f32",
+           "tufrg_symmetry_info", "tufrg_round_f32", "tufrg_rhs_host_batch",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")

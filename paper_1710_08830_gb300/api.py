@@ -163,6 +163,27 @@ class Model:
         self._check(self._L.tufrg_rhs_host(self._h, float(T), _ptr(state_host), int(mask), _ptr(out_host)))
         return out_host
 
+    def rhs_host_batch(self, T, states_host, outs_host, mask: int = CH_P | CH_C, symmetric: bool = False):
+        """dX/dT for a sequence of host (ideally pinned) states, the transfers of neighbouring steps overlapped with
+        the evaluations: step i reads states_host[i] at T[i] (a scalar T applies to every step) and writes
+        outs_host[i].  A tensor may repeat in either list."""
+        n = len(states_host)
+        if len(outs_host) != n:
+            raise ValueError("states_host and outs_host differ in length")
+        for t in list(states_host) + list(outs_host):
+            if t.device.type != "cpu" or not t.is_contiguous() or t.dtype != torch.complex128 \
+                    or tuple(t.shape) != self.state_shape():
+                raise ValueError(f"rhs_host_batch needs C-contiguous complex128 host tensors of shape {self.state_shape()}")
+        Ts = [float(T)] * n if np.ndim(T) == 0 else [float(x) for x in T]
+        if len(Ts) != n:
+            raise ValueError("T has the wrong length")
+        t_arr = (C.c_double * max(n, 1))(*Ts)
+        s_arr = (C.c_void_p * max(n, 1))(*[t.data_ptr() for t in states_host])
+        o_arr = (C.c_void_p * max(n, 1))(*[t.data_ptr() for t in outs_host])
+        flag = SYMMETRIC_STATE if symmetric else 0
+        self._check(self._L.tufrg_rhs_host_batch(self._h, n, t_arr, s_arr, int(mask) | flag, o_arr))
+        return outs_host
+
     PHASES = ("fermi", "loops", "loop_reduce", "dft", "project", "vlv", "rk")
 
     def timing_begin(self):

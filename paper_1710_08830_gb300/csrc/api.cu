@@ -506,6 +506,15 @@ void release(tufrg_model *m)
     if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
     if (m->flow_ev) cudaEventDestroy(m->flow_ev);
     if (m->flow_stream) cudaStreamDestroy(m->flow_stream);
+    for (int b = 0; b < 2; b++) {
+        if (m->d_bin[b]) cudaFree(m->d_bin[b]);
+        if (m->d_bout[b]) cudaFree(m->d_bout[b]);
+        if (m->ev_in[b]) cudaEventDestroy(m->ev_in[b]);
+        if (m->ev_comp[b]) cudaEventDestroy(m->ev_comp[b]);
+        if (m->ev_out[b]) cudaEventDestroy(m->ev_out[b]);
+    }
+    if (m->s_h2d) cudaStreamDestroy(m->s_h2d);
+    if (m->s_d2h) cudaStreamDestroy(m->s_d2h);
 }
 
 size_t state_elems(const tufrg_model *m) { return (size_t)2 * m->Nq * m->M * m->M; }
@@ -1291,6 +1300,60 @@ tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int c
     CK(cudaStreamSynchronize(m->stream), "sync");
     if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up");
     return TUFRG_OK;
+}
+
+tufrg_status tufrg_rhs_host_batch(tufrg_model *m, int n, const double *T, const void *const *h_states, int channel_mask,
+                                  void *const *h_dstates)
+{
+    if (!m) return TUFRG_EINVAL;
+    if (n < 0 || (n > 0 && (!T || !h_states || !h_dstates))) return fail(m, TUFRG_EINVAL, "bad batch arguments");
+    if (channel_mask & ~(3 | TUFRG_SYMMETRIC_STATE))
+        return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C, optionally with TUFRG_SYMMETRIC_STATE");
+    for (int i = 0; i < n; i++) {
+        if (!(T[i] > 0) || !std::isfinite(T[i])) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
+        if (!h_states[i] || !h_dstates[i]) return fail(m, TUFRG_EINVAL, "NULL host buffer");
+    }
+    if (n == 0) return TUFRG_OK;
+    const size_t bytes = sizeof(double2) * state_elems(m);
+    if (!m->d_bin[0]) {
+        for (int b = 0; b < 2; b++) {
+            CK(cudaMalloc(&m->d_bin[b], bytes), "cudaMalloc state");
+            CK(cudaMalloc(&m->d_bout[b], bytes), "cudaMalloc state");
+            CK(cudaEventCreateWithFlags(&m->ev_in[b], cudaEventDisableTiming), "event");
+            CK(cudaEventCreateWithFlags(&m->ev_comp[b], cudaEventDisableTiming), "event");
+            CK(cudaEventCreateWithFlags(&m->ev_out[b], cudaEventDisableTiming), "event");
+        }
+        CK(cudaStreamCreateWithFlags(&m->s_h2d, cudaStreamNonBlocking), "stream");
+        CK(cudaStreamCreateWithFlags(&m->s_d2h, cudaStreamNonBlocking), "stream");
+    }
+    // step i uses buffer pair b = i mod 2: its input copy waits until step i - 2 has been evaluated, its
+    // evaluation until the input has arrived and step i - 2's output has left, its output copy until it
+    // has been evaluated
+    tufrg_status st = TUFRG_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && st == TUFRG_OK && e == cudaSuccess; i++) {
+        const int b = i & 1;
+        if (i >= 2) e = cudaStreamWaitEvent(m->s_h2d, m->ev_comp[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_bin[b], h_states[i], bytes, cudaMemcpyHostToDevice, m->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(m->ev_in[b], m->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->stream, m->ev_in[b], 0);
+        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(m->stream, m->ev_out[b], 0);
+        if (e != cudaSuccess) break;
+        st = tufrg_rhs(m, T[i], m->d_bin[b], channel_mask, m->d_bout[b]);
+        if (st != TUFRG_OK) break;
+        e = cudaEventRecord(m->ev_comp[b], m->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->s_d2h, m->ev_comp[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_dstates[i], m->d_bout[b], bytes, cudaMemcpyDeviceToHost, m->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(m->ev_out[b], m->s_d2h);
+    }
+    // the host buffers stay in use until every queued copy has finished, also after an error
+    const cudaError_t e1 = cudaStreamSynchronize(m->s_h2d), e2 = cudaStreamSynchronize(m->stream),
+                      e3 = cudaStreamSynchronize(m->s_d2h);
+    if (st != TUFRG_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(m, e, "pipelined host-buffer evaluation");
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return cuda_fail(m, e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3, "pipelined host-buffer evaluation");
+    return read_device_error(m);
 }
 
 tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_out, tufrg_flow_result *res)

@@ -239,6 +239,11 @@ struct tufrg_model {
     // flow work buffers
     double2 *d_y = nullptr, *d_yt = nullptr, *d_yn = nullptr, *d_k[7] = {};
     double2 *d_state_in = nullptr, *d_state_out = nullptr;   // host-buffer entry points
+    // pipelined host-buffer evaluations: two device buffers per direction, one stream per copy direction,
+    // and per buffer the events "input copied", "evaluated", "output copied"
+    double2 *d_bin[2] = {nullptr, nullptr}, *d_bout[2] = {nullptr, nullptr};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     tufrg::FlowDev *d_flow = nullptr;        // device controller state
     tufrg::FlowDev *h_flow = nullptr;        // pinned host mirror
     cudaGraphExec_t step_graph = nullptr;    // one captured Dormand-Prince attempt

@@ -315,6 +315,34 @@ def test_rhs_host_buffers_match_device():
     assert torch.equal(d_dev, ho)
 
 
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_rhs_host_batch_matches_device(prec):
+    """The pipelined host-buffer entry point (copies of neighbouring steps overlapped with the evaluations) gives,
+    step by step, exactly the device right-hand side: distinct states and temperatures, a repeated input buffer,
+    pinned and pageable host memory, odd and even batch lengths, the symmetric-state flag."""
+    api = _api()
+    spec = CASES["rashba_ff9_Lf25"]()
+    m = api.Model(spec, getattr(api, prec))
+    states = [torch.from_numpy(inputs.random_state(spec, seed=s, scale=0.3)) for s in (1, 2, 3)]
+    Ts = [0.4, 0.25, 0.9, 0.4, 0.6]
+    ins = [states[0].pin_memory(), states[1].pin_memory(), states[2], states[0].pin_memory(), states[1]]
+    outs = [torch.empty_like(states[0]).pin_memory() for _ in range(4)] + [torch.empty_like(states[0])]
+    for n in (1, 2, 5):
+        m.rhs_host_batch(Ts[:n], ins[:n], outs[:n])
+        for i in range(n):
+            assert torch.equal(outs[i], m.rhs(Ts[i], ins[i]).cpu()), (n, i)
+    zero = m.zeros_state()
+    X1 = (0.05 * m.rhs(0.5, zero)).cpu().contiguous()     # a symmetric state (one Euler step from X = 0)
+    hs = [X1.pin_memory(), X1.pin_memory()]
+    ho = [torch.empty_like(X1).pin_memory() for _ in range(3)]
+    m.rhs_host_batch(0.4, [hs[0], hs[1], hs[0]], ho, symmetric=True)
+    want = m.rhs(0.4, X1, symmetric=True).cpu()
+    for o in ho:
+        assert torch.equal(o, want)
+    with pytest.raises(api.TufrgError):
+        m.rhs_host_batch([0.4, -1.0], ins[:2], outs[:2])
+
+
 def test_rhs_deterministic():
     api = _api()
     spec = CASES["rashba_ff9_Lf120"]()
