@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
 class _Model(C.Structure):
     _fields_ = [("ns", C.c_int), ("nhop", C.c_int), ("hopR", C.c_void_p), ("hopt", C.c_void_p),
                 ("V0", C.c_void_p), ("nff", C.c_int), ("ffR", C.c_void_p),
-                ("Lq", C.c_int), ("nc", C.c_int), ("mu", C.c_double)]
+                ("Lq", C.c_int), ("nc", C.c_int), ("mu", C.c_double), ("reg", C.c_int), ("T_reg", C.c_double)]
 
 
 class FlowOpts(C.Structure):
@@ -69,6 +69,12 @@ def lib():
             L.or_fermi.argtypes = [d, d, vp, vp, vp]
             for fn in ("or_wm", "or_wp", "or_Fm", "or_Fp"):
                 getattr(L, fn).argtypes = [d, d, d]
+                getattr(L, fn).restype = d
+            for fn in ("or_chi", "or_dchi"):
+                getattr(L, fn).argtypes = [d, d]
+                getattr(L, fn).restype = d
+            for fn in ("or_wm_shell", "or_wp_shell"):
+                getattr(L, fn).argtypes = [d, d, d, d]
                 getattr(L, fn).restype = d
             L.or_delta_list.argtypes = [vp, vp]
             L.or_delta_list.restype = i
@@ -142,7 +148,8 @@ class Oracle:
         self._V0 = np.ascontiguousarray(spec.V0, np.complex128)
         self._ffR = np.ascontiguousarray(spec.ff_R, np.int32)
         self.m = _Model(spec.n_s, self._hopR.shape[0], _ptr(self._hopR), _ptr(self._hopt),
-                        _ptr(self._V0), self._ffR.shape[0], _ptr(self._ffR), spec.Lq, spec.nc, 0.0)
+                        _ptr(self._V0), self._ffR.shape[0], _ptr(self._ffR), spec.Lq, spec.nc, 0.0,
+                        int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)))
         self.E, self.U = self.bands()
         if mu is not None:
             self.mu = float(mu)

@@ -17,8 +17,12 @@
  *     silent; reading: mu fixed once and held constant).
  *  3. Orbital loops by the direct fine-mesh k-sum (Eqs. loopminus/loopplus
  *     transcribed to the orbital basis with Eq. trafo, cf. Eq. loop_orbital).
- *     Regulator: temperature flow, Lambda = T, chi = 1, L = d/dT F (Eqs.
- *     def_lmp, disc_2a, disc_2b).
+ *     Regulator (Eq. def_lmp): temperature flow, Lambda = T, chi = 1,
+ *     L = d/dT F (Eqs. disc_2a, disc_2b); or the momentum-shell regulator the
+ *     paper writes, chi_Lambda(e) = e^2 / (e^2 + Lambda^2) (a smooth
+ *     suppression of |e| < Lambda around the Fermi surfaces), with
+ *     L = d/dLambda [chi_Lambda(e1) chi_Lambda(e2)] F(e1, e2) and F at a fixed
+ *     temperature.
  *  4. Lattice Fourier transform of P and C (Sec. 3.3, after Eq. zw_1).
  *  5. Projections A_P, A_C from Eq. sum_P and the four printed gathers
  *     (Eq. proj_PD, the D->P formula after it, the P->C formula and
@@ -62,6 +66,8 @@ typedef struct {
     const int *ffR;    /* [nff][2] */
     int Lq, nc;
     double mu;
+    int reg;           /* 0: temperature flow (scale = T); 1: momentum shell (scale = Lambda) */
+    double T_reg;      /* momentum shell: temperature of the Fermi functions in F */
 } or_model;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -268,6 +274,37 @@ double or_Fp(double e1, double e2, double T)
     return -0.5 * (f1 * (1 - f1) + f2 * (1 - f2)) / T;
 }
 
+/* Momentum-shell regulator of Eq. def_lmp: chi_Lambda(e) = e^2 / (e^2 + Lambda^2) and its
+ * Lambda-derivative -2 Lambda e^2 / (e^2 + Lambda^2)^2. */
+double or_chi(double e, double lam) { return e * e / (e * e + lam * lam); }
+double or_dchi(double e, double lam)
+{
+    double d = e * e + lam * lam;
+    return -2.0 * lam * e * e / (d * d);
+}
+
+/* L^-/+ weight with the momentum-shell regulator: d/dLambda [chi(e1) chi(e2)] F^-/+(e1, e2) at T. */
+double or_wm_shell(double e1, double e2, double lam, double T)
+{
+    return (or_dchi(e1, lam) * or_chi(e2, lam) + or_chi(e1, lam) * or_dchi(e2, lam)) * or_Fm(e1, e2, T);
+}
+double or_wp_shell(double e1, double e2, double lam, double T)
+{
+    return (or_dchi(e1, lam) * or_chi(e2, lam) + or_chi(e1, lam) * or_dchi(e2, lam)) * or_Fp(e1, e2, T);
+}
+
+/* The loop weight of channel `which' at scale s (T or Lambda): kind 0 the flowing loop, kind 1 the
+ * quantity whose s-derivative it is (the bubble F, or chi chi F with the momentum shell). */
+static double loop_weight(const or_model *m, int which, int kind, double a, double b, double s)
+{
+    if (m->reg == 1) {
+        if (kind) return or_chi(a, s) * or_chi(b, s) * (which == 0 ? or_Fm(a, b, m->T_reg) : or_Fp(a, b, m->T_reg));
+        return which == 0 ? or_wm_shell(a, b, s, m->T_reg) : or_wp_shell(a, b, s, m->T_reg);
+    }
+    if (which == 0) return kind ? or_Fm(a, b, s) : or_wm(a, b, s);
+    return kind ? or_Fp(a, b, s) : or_wp(a, b, s);
+}
+
 /* n(mu) = (1/Nk) sum_{k,l} f(E_l(k) - mu): electrons per site. */
 double or_density(const or_model *m, const double *E, double mu, double T)
 {
@@ -345,8 +382,9 @@ static int ff_index_mod(const or_model *m, int x, int y)
  * which = 1 (crossed particle-hole, u on the coarse mesh):
  *   [L^+_{t1t2t3t4}(u)]_{R1R2} = (1/Nk) sum_q e^{-iq.(R1-R2)}
  *        sum_{l1 l2} U_{t1 l1}(q) U*_{t3 l1}(q) w^+_{l1 l2}(q, q-u) U*_{t2 l2}(q-u) U_{t4 l2}(q-u)
- * kind = 0: w = d/dT F (the flowing loop, Eq. def_lmp with chi = 1 and Lambda = T)
- * kind = 1: w = F itself (the bubble, used only by the closed-form pins).
+ * kind = 0: w = the flowing loop at scale T (d/dT F, Eq. def_lmp with chi = 1 and Lambda = T), or at
+ *           Lambda with the momentum-shell regulator (d/dLambda [chi chi] F, see loop_weight)
+ * kind = 1: w = F itself, or chi chi F (the bubbles, used only by the closed-form pins).
  * Output Lc[q][d][a][b] in the matrix pair order given in the file header.
  */
 /* the k-sum for one transfer momentum s (coarse index), accumulated into acc[nd][ns^4] */
@@ -369,8 +407,7 @@ static void loops_one(const or_model *m, const double *E, const cplx *U, double 
             for (int l1 = 0; l1 < ns; l1++)
                 for (int l2 = 0; l2 < ns; l2++) {
                     double a = e1[l1] - m->mu, b = e2[l2] - m->mu;
-                    if (which == 0) w[l1 * ns + l2] = kind ? or_Fm(a, b, T) : or_wm(a, b, T);
-                    else            w[l1 * ns + l2] = kind ? or_Fp(a, b, T) : or_wp(a, b, T);
+                    w[l1 * ns + l2] = loop_weight(m, which, kind, a, b, T);
                 }
             /* Y[t1 t2 t3 t4] = sum_{l1 l2} (...) */
             for (int t1 = 0; t1 < ns; t1++)
@@ -419,8 +456,9 @@ static cplx *loop_phase_table(const or_model *m, const int *dl, int nd)
  * which = 1 (crossed particle-hole, u on the coarse mesh):
  *   [L^+_{t1t2t3t4}(u)]_{R1R2} = (1/Nk) sum_q e^{-iq.(R1-R2)}
  *        sum_{l1 l2} U_{t1 l1}(q) U*_{t3 l1}(q) w^+_{l1 l2}(q, q-u) U*_{t2 l2}(q-u) U_{t4 l2}(q-u)
- * kind = 0: w = d/dT F (the flowing loop, Eq. def_lmp with chi = 1 and Lambda = T)
- * kind = 1: w = F itself (the bubble, used only by the closed-form pins).
+ * kind = 0: w = the flowing loop at scale T (d/dT F, Eq. def_lmp with chi = 1 and Lambda = T), or at
+ *           Lambda with the momentum-shell regulator (d/dLambda [chi chi] F, see loop_weight)
+ * kind = 1: w = F itself, or chi chi F (the bubbles, used only by the closed-form pins).
  * Output Lc[q][d][a][b] in the matrix pair order given in the file header.
  */
 void or_loops(const or_model *m, const double *E, const double *Uin, double T, int which, int kind,

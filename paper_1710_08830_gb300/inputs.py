@@ -49,6 +49,8 @@ class ModelSpec:
     filling: float = 0.0       # electrons per site (all spin-orbitals); > 0 => mu is bisected
     T_mu: float = 0.02         # temperature at which mu is fixed by the filling
     params: dict = field(default_factory=dict)
+    regulator: int = 0         # 0: temperature flow (scale = T); 1: momentum shell (scale = Lambda, Eq. def_lmp)
+    T_reg: float = 0.05        # momentum shell: temperature of the Fermi functions in the bubbles
 
     @property
     def n_ff(self) -> int:

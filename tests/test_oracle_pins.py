@@ -8,7 +8,10 @@ it would catch.  The pins are:
   * the paper's closed-form particle-particle solution (Sec. 4, Eq. sol_spin);
   * second-order perturbation theory (the bubble itself, not its derivative);
   * the q -> 0 compressibility of the single-band particle-hole loop;
-  * hermiticity, SU(2) and bookkeeping invariants.
+  * hermiticity, SU(2) and bookkeeping invariants;
+  * the momentum-shell regulator of Eq. def_lmp: its defining properties, finite differences in Lambda of
+    chi chi F (F from Eqs. disc_2a/2b written out here), the closed forms with Lambda as the flow variable, and
+    its Lambda -> 0 limit against the temperature-flow bubble.
 """
 import numpy as np
 import pytest
@@ -197,13 +200,14 @@ def _pair_structure(ns):
     return A
 
 
-@pytest.mark.parametrize("alpha,tp", [(0.3, -0.2), (0.0, -0.25)])
-def test_particle_particle_closed_form(alpha, tp):
+@pytest.mark.parametrize("alpha,tp,reg", [(0.3, -0.2, 0), (0.0, -0.25, 0), (0.3, -0.2, 1)])
+def test_particle_particle_closed_form(alpha, tp, reg):
     """Eq. sol_spin: two-band TRS model, onsite U, P-only flow.  P stays local,
-    P = -(g+U)/2 (d13 d24 - d14 d23) with g = -U/(1 + U [B(T) - B(T0)]), B from the
-    bubble F^- itself (not its T-derivative), so the integrator is pinned too."""
+    P = -(g+U)/2 (d13 d24 - d14 d23) with g = -U/(1 + U [B(s) - B(s0)]), B from the
+    bubble F^- itself (not its T-derivative), so the integrator is pinned too.  With the momentum-shell
+    regulator (reg = 1) the scale s is Lambda and the bubble is chi chi F^- at the fixed temperature."""
     U = 2.5
-    spec = inputs.rashba_hubbard(tp=tp, alpha=alpha, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5)
+    spec = inputs.rashba_hubbard(tp=tp, alpha=alpha, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5).with_(regulator=reg, T_reg=0.1)
     o = oracle.Oracle(spec)
     T0, T1 = 10.0, 0.3
     state, res = o.flow(T0=T0, T_end=T1, rtol=1e-10, atol=1e-12, chmask=1, stop=1e9)
@@ -231,10 +235,12 @@ def test_particle_particle_closed_form(alpha, tp):
     assert np.abs(state[1]).max() == 0.0
 
 
-def test_second_order_perturbation_theory():
+@pytest.mark.parametrize("reg", [0, 1])
+def test_second_order_perturbation_theory(reg):
     """At O(U^2): P(T) = V0 [B^-(T) - B^-(T0)] V0 and C(T) = 2 V0 [B^+(T) - B^+(T0)] V0 with
-    the bubble matrices built from F^-, F^+ directly; the remainder is O(U^3)."""
-    base = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, mu=-0.8, Lq=4, nc=2, n_ff=5)
+    the bubble matrices built from F^-, F^+ directly (chi chi F^-/+ with the momentum shell, reg = 1);
+    the remainder is O(U^3)."""
+    base = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, mu=-0.8, Lq=4, nc=2, n_ff=5).with_(regulator=reg, T_reg=0.1)
     T0, T1 = 10.0, 0.4
     res = []
     for U in (0.2, 0.1):
@@ -345,3 +351,69 @@ def test_su2_relations_without_soc():
                         if a + b != c + d:
                             assert np.abs(X(a, b, c, d)).max() < 1e-13
     assert np.abs(Pt(0, 1, 0, 1)).max() > 1e-3 and np.abs(Ct(0, 1, 0, 1)).max() > 1e-3
+
+
+# ---------------------------------------------------------------- momentum-shell regulator (Eq. def_lmp)
+
+def _fermi(e, T):
+    return 0.5 * (1.0 - np.tanh(0.5 * e / T))
+
+
+def test_shell_regulator_definition():
+    """chi_Lambda suppresses a shell of thickness Lambda around the Fermi surface: chi = 0 on it, 1/2 at
+    |e| = Lambda, -> 1 far from it, monotone in |e|; d chi / d Lambda and the loop weight
+    d/dLambda [chi(e1) chi(e2)] F^-/+(e1, e2) against central differences in Lambda, with F written out from
+    Eqs. disc_2a/2b here (a dropped term of the product rule or a wrong sign fails)."""
+    L = oracle.lib()
+    for lam in (0.05, 0.7, 3.0):
+        assert L.or_chi(0.0, lam) == 0.0
+        assert L.or_chi(lam, lam) == pytest.approx(0.5, abs=1e-15)
+        assert L.or_chi(-lam, lam) == pytest.approx(0.5, abs=1e-15)
+        assert L.or_chi(1e4 * lam, lam) == pytest.approx(1.0, abs=1e-7)
+        es = np.linspace(0, 5 * lam, 50)
+        assert np.all(np.diff([L.or_chi(e, lam) for e in es]) > 0)
+    rng = np.random.default_rng(3)
+    T = 0.07
+    for _ in range(40):
+        e1, e2 = rng.uniform(-1.5, 1.5, 2)
+        lam = rng.uniform(0.05, 2.0)
+        h = 1e-5 * lam
+        fd = (L.or_chi(e1, lam + h) - L.or_chi(e1, lam - h)) / (2 * h)
+        assert L.or_dchi(e1, lam) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        Fm = (1 - _fermi(e1, T) - _fermi(e2, T)) / (e1 + e2)
+        Fp = (_fermi(e1, T) - _fermi(e2, T)) / (e1 - e2)
+
+        def cc(l):
+            return L.or_chi(e1, l) * L.or_chi(e2, l)
+
+        dcc = (cc(lam + h) - cc(lam - h)) / (2 * h)
+        assert L.or_wm_shell(e1, e2, lam, T) == pytest.approx(dcc * Fm, rel=1e-6, abs=1e-9)
+        assert L.or_wp_shell(e1, e2, lam, T) == pytest.approx(dcc * Fp, rel=1e-6, abs=1e-9)
+
+
+def test_shell_flow_reaches_temperature_bubble():
+    """Lambda -> 0 with Lambda_0 -> infinity, chi chi F^- runs from 0 to F^- itself: the P-only shell flow
+    (Eq. sol_spin structure) from Lambda_0 = 1e3 to 1e-5 must land on the closed form built from the
+    temperature-flow bubble F^-(T_reg) of the same mesh (kind = 1 loops of a temperature-regulated oracle), a
+    cross-check between the two regulators."""
+    U, Treg = 2.5, 0.1
+    base = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5)
+    o_sh = oracle.Oracle(base.with_(regulator=1, T_reg=Treg))
+    state, res = o_sh.flow(T0=1e3, T_end=1e-5, rtol=1e-10, atol=1e-12, chmask=1, stop=1e9)
+    o_t = oracle.Oracle(base)
+    ns = 2
+    d0 = [i for i, (x, y) in enumerate(o_t.deltas) if x == 0 and y == 0][0]
+    Lb = o_t.loops(Treg, 0, kind=1)[:, d0].reshape(base.Nq, ns, ns, ns, ns)
+    B = np.zeros(base.Nq, complex)
+    for t1 in range(ns):
+        for t2 in range(ns):
+            B += 0.5 * (Lb[:, t2, t1, t2, t1] - Lb[:, t2, t1, t1, t2])
+    g = -U / (1 + U * B)
+    A = _pair_structure(ns)
+    expect = np.zeros((base.Nq, base.M, base.M), complex)
+    for s1 in range(ns):
+        for s2 in range(ns):
+            for s3 in range(ns):
+                for s4 in range(ns):
+                    expect[:, s1 * ns + s2, s4 * ns + s3] = -0.5 * (g + U) * A[s1, s2, s3, s4]
+    assert np.abs(state[0] - expect).max() < 1e-6 * max(1.0, np.abs(expect).max())
