@@ -234,6 +234,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
                     help="model configuration (default: the 24x24 / 8x8 Rashba-Hubbard benchmark workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path (and the accuracy check)")
+    ap.add_argument("--regulator", choices=["temperature", "shell"], default="temperature",
+                    help="loop regulator: the temperature flow (default) or the momentum shell of Eq. def_lmp "
+                         "(flow scale Lambda, Fermi functions at T_reg = 0.05)")
     ap.add_argument("--products-sweep", action="store_true",
                     help="only time the V.L.V products (tensor cores vs CUDA cores) on t2g models with N_ff = 5, 9, 13 "
                          "(M = 180, 324, 468) at Nq = 32 x 32")
@@ -290,6 +293,10 @@ def main():
         spec = inputs.hubbard_q8_k16_ff5()
     else:
         spec = inputs.t2g_q32_k6_ff9(seed=rank)
+    if args.regulator == "shell":
+        spec = spec.with_(regulator=1, T_reg=0.05)
+        workload += "_shell"
+        metric += " with the momentum-shell regulator (flow scale Lambda, T_reg = 0.05)"
     stream = torch.cuda.current_stream()
     m32 = Model(spec, SPLIT32, stream=stream)
     m64 = None if args.no_fp64 else Model(spec, FP64, stream=stream)
@@ -487,7 +494,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": workload, "Lq": spec.Lq, "nc": spec.nc, "Nq": spec.Nq, "Nk": spec.Nk,
-                       "n_s": spec.n_s, "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH,
+                       "n_s": spec.n_s, "n_ff": spec.n_ff, "M": spec.M, "T": T_BENCH, "regulator": args.regulator,
                        "precision": "split (FP32 loop sums, FP64 state)",
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "loop_momenta_summed": m32.n_loop_q, "symmetric_state": True,

@@ -12,9 +12,12 @@
  * with A_X the projected vertex of Sec. 3.3 (Eq. sum_P and the four gathers
  * Eq. proj_PD ... Eq. proj_DC) and L^- / L^+ the loop matrices of Eqs.
  * loopminus / loopplus dressed into the orbital basis (Eq. loop_orbital).
- * The flow parameter is the temperature: Lambda = T, the regulator chi = 1,
- * so the single-scale loops of Eq. def_lmp are d/dT of the bubbles F^-/F^+
- * (Eqs. disc_2a, disc_2b).
+ * The flow parameter is the temperature by default: Lambda = T, the regulator
+ * chi = 1, so the single-scale loops of Eq. def_lmp are d/dT of the bubbles
+ * F^-/F^+ (Eqs. disc_2a, disc_2b).  With the momentum-shell regulator
+ * (TUFRG_REG_MOMENTUM_SHELL below) the flow parameter is Lambda itself and the
+ * loops are d/dLambda [chi chi] F^-/+ at a fixed temperature; every argument
+ * named T below is then Lambda, and d/dT reads d/dLambda.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -92,7 +95,17 @@ typedef struct {
     int precision;         /* TUFRG_FP64 or TUFRG_SPLIT32 (see above) */
     int products;          /* TUFRG_PRODUCTS_AUTO / _TC / _SIMT (split path only) */
     int symmetry;          /* TUFRG_SYMMETRY_AUTO or TUFRG_SYMMETRY_OFF (see below) */
+    int regulator;         /* TUFRG_REG_TEMPERATURE or TUFRG_REG_MOMENTUM_SHELL (see below) */
+    double T_reg;          /* momentum shell: temperature of the Fermi functions in the bubbles (> 0) */
 } tufrg_model_desc;
+
+/* Regulator of the loops (Eq. def_lmp, L = d/dLambda [chi(e1) chi(e2)] F(e1, e2)).
+ * TEMPERATURE: the flow scale is the temperature, chi = 1, L = d/dT F(e1, e2; T).
+ * MOMENTUM_SHELL: the flow scale is Lambda, chi_Lambda(e) = e^2 / (e^2 + Lambda^2) suppresses a shell of
+ * thickness Lambda around the Fermi surfaces, and F is taken at the fixed temperature T_reg.
+ * The scale argument of tufrg_loops / tufrg_rhs and the T0 / T_end range of a flow are T or Lambda
+ * accordingly; the learned surrogate and tufrg_loops_noalloc support the temperature flow only. */
+enum { TUFRG_REG_TEMPERATURE = 0, TUFRG_REG_MOMENTUM_SHELL = 1 };
 
 /* Symmetries of the loop k-sums (split two-band path).  A point operation G of the square lattice
  * (rotations by multiples of 90 degrees, the four mirrors) with a spin unitary U such that every
@@ -107,9 +120,10 @@ typedef struct {
  * alike; OFF disables every symmetry).  Both paths are timed at init for tufrg_symmetry_info. */
 enum { TUFRG_SYMMETRY_AUTO = 0, TUFRG_SYMMETRY_OFF = 1, TUFRG_SYMMETRY_STATES = 2 };
 
-/* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end). */
+/* Adaptive flow options (Dormand-Prince 5(4) in x = ln T, from T0 down to T_end; T is Lambda with the
+ * momentum-shell regulator). */
 typedef struct {
-    double T0, T_end;      /* start and end temperature, T0 > T_end > 0 */
+    double T0, T_end;      /* start and end of the flow scale, T0 > T_end > 0 */
     double rtol, atol;     /* error norm max_i |err_i| / (atol + rtol max(|y_i|, |y'_i|)) <= 1 */
     double h0;             /* first step in ln T (negative) */
     double stop;           /* stop when max |A_X(q)| over channels, q, entries exceeds this */

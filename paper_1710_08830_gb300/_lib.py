@@ -21,6 +21,7 @@ FP64, SPLIT32 = 0, 1
 PRODUCTS_AUTO, PRODUCTS_TC, PRODUCTS_SIMT = 0, 1, 2
 SYMMETRY_AUTO, SYMMETRY_OFF, SYMMETRY_STATES = 0, 1, 2
 SYMMETRIC_STATE = 4   # tufrg_rhs flag: the state has the model's loop symmetries
+REG_TEMPERATURE, REG_MOMENTUM_SHELL = 0, 1   # regulators of the loops (Eq. def_lmp)
 CH_P, CH_C = 1, 2
 
 
@@ -28,7 +29,8 @@ class ModelDesc(C.Structure):
     _fields_ = [("n_s", C.c_int), ("n_hop", C.c_int), ("hop_R", C.c_void_p), ("hop_t", C.c_void_p),
                 ("mu", C.c_double), ("filling", C.c_double), ("T_mu", C.c_double), ("V0", C.c_void_p),
                 ("n_ff", C.c_int), ("ff_R", C.c_void_p), ("Lq", C.c_int), ("nc", C.c_int),
-                ("precision", C.c_int), ("products", C.c_int), ("symmetry", C.c_int)]
+                ("precision", C.c_int), ("products", C.c_int), ("symmetry", C.c_int), ("regulator", C.c_int),
+                ("T_reg", C.c_double)]
 
 
 class FlowOpts(C.Structure):

@@ -46,7 +46,8 @@ class Model:
         d = ModelDesc(spec.n_s, self._hopR.shape[0], self._hopR.ctypes.data, self._hopt.ctypes.data,
                       float(spec.mu if mu is None else mu), float(spec.filling if use_fill else 0.0),
                       float(spec.T_mu), self._V0.ctypes.data, self._ffR.shape[0], self._ffR.ctypes.data,
-                      spec.Lq, spec.nc, int(precision), int(products), int(symmetry))
+                      spec.Lq, spec.nc, int(precision), int(products), int(symmetry),
+                      int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)))
         h = C.c_void_p()
         st = self._L.tufrg_init_model(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h))
         self._h = h

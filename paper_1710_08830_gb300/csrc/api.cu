@@ -744,6 +744,12 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF && d.symmetry != TUFRG_SYMMETRY_STATES)
         return fail(m, TUFRG_EINVAL, "unknown symmetry option");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
+    if (d.regulator != TUFRG_REG_TEMPERATURE && d.regulator != TUFRG_REG_MOMENTUM_SHELL)
+        return fail(m, TUFRG_EINVAL, "unknown regulator");
+    if (d.regulator == TUFRG_REG_MOMENTUM_SHELL && !(d.T_reg > 0 && std::isfinite(d.T_reg)))
+        return fail(m, TUFRG_EINVAL, "the momentum-shell regulator needs T_reg > 0");
+    m->regulator = d.regulator;
+    m->T_reg = d.T_reg;
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
     m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -1052,6 +1058,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         m->mu = d.mu;
     }
     if (loops2_supported(m)) CK(launch_loop_records_static(m), "loop records");
+    if (m->regulator == TUFRG_REG_MOMENTUM_SHELL) {
+        // the Fermi data of the momentum-shell loops do not depend on the flow scale: written once
+        if (loops2_supported(m)) CK(launch_loop_records_shell(m), "loop records");
+        else CK(launch_fermi_shell(m), "Fermi tables");
+    }
     CK(cudaStreamSynchronize(m->stream), "init sync");
     TuneResult cached{};
     if (split && d.products == TUFRG_PRODUCTS_AUTO && tune_lookup(m, 0, &cached)) {

@@ -168,6 +168,17 @@ __global__ void fermi_kernel(const double *E, int n, double mu, const double *sc
     if (ft32) ft32[i] = FermiEntry32{(float)e, (float)g, (float)gp, 0.f};
 }
 
+// Momentum-shell tables: (e, f, h) with h = f (1 - f) / T at the fixed temperature T (once per model).
+__global__ void fermi_shell_kernel(const double *E, int n, double mu, double T, FermiEntry *ft, FermiEntry32 *ft32)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double e = E[i] - mu, z = exp(-fabs(e) / T);
+    const double f = e > 0 ? z / (1.0 + z) : 1.0 / (1.0 + z), h = z / ((1.0 + z) * (1.0 + z)) / T;
+    ft[i] = FermiEntry{e, f, h};
+    if (ft32) ft32[i] = FermiEntry32{(float)e, (float)f, (float)h, 0.f};
+}
+
 // n(mu) partial sums: fixed-order tree in each block, then one block sums the partials.
 __global__ void density_partial(const double *E, int n, double mu, double T, double *part)
 {
@@ -227,9 +238,18 @@ cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale)
     return cudaGetLastError();
 }
 
+cudaError_t launch_fermi_shell(tufrg_model *m)
+{
+    const int n = m->Nk * m->ns;
+    fermi_shell_kernel<<<(n + 255) / 256, 256, 0, m->stream>>>(m->d_E, n, m->mu, m->T_reg, m->d_ft,
+                                                                 m->precision == TUFRG_FP64 ? nullptr : m->d_ft32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fermi(tufrg_model *m)
 {
     if (loops2_supported(m)) return launch_loop_records(m);   // the split two-band kernel reads its own per-k records
+    if (m->regulator == TUFRG_REG_MOMENTUM_SHELL) return cudaSuccess;   // tables fixed at init (no Lambda dependence)
     const int n = m->Nk * m->ns;
     FermiEntry32 *ft32 = m->precision == TUFRG_FP64 ? nullptr : m->d_ft32;
     PhaseScope ps(m, PH_FERMI);

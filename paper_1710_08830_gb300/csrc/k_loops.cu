@@ -45,7 +45,8 @@ struct LoopArgs {
     unsigned needed[MAXD];              // bit dyi set if (dx, dy) is a needed half-plane difference
     int ky_chunks, ky_len;
     R thr_factor;                       // degenerate-pair switch = thr_factor * T
-    const double *Tp;                   // device temperature
+    const double *Tp;                   // device flow scale (T, or Lambda with the momentum shell)
+    R shell_T;                          // > 0: momentum-shell regulator at this temperature (tables hold e, f, h)
     int which;                          // 0 = P, 1 = C (uniform, also a template arg below)
 };
 
@@ -74,10 +75,12 @@ __device__ __forceinline__ void load_ft(const FermiEntry32 *p, float &e, float &
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 
-// d/dT F^-(e1, e2) (P) and d/dT F^+(e1, e2) (C); analytic limit for near-degenerate pairs.
+// d/dT F^-(e1, e2) (P) and d/dT F^+(e1, e2) (C); analytic limit for near-degenerate pairs.  With the
+// momentum shell (lam > 0) the entries hold (e, f, h) and the weight is d/dLambda [chi chi] F.
 template <int WHICH, typename R>
-__device__ __forceinline__ R pair_weight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr)
+__device__ __forceinline__ R pair_weight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr, R lam)
 {
+    if (lam > R(0)) return shell_weight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);
     if (WHICH == 0) {
         R s = e1 + e2;
         return fabs(s) > thr ? -fdiv(g1 + g2, s) : R(-0.5) * (gp1 + gp2);
@@ -98,7 +101,9 @@ __device__ __forceinline__ void loop_body(const LoopArgs<R> &a, const typename c
     const int kx = blockIdx.y * (32 * WARPS) + threadIdx.x;
     const bool valid = kx < Lf;
     const int kyc = blockIdx.z % a.ky_chunks;   // the ab group is blockIdx.z / ky_chunks
-    const R thr = a.thr_factor * (R)(*a.Tp);
+    const bool shell = a.shell_T > R(0);
+    const R lam = shell ? (R)(*a.Tp) : R(0);
+    const R thr = a.thr_factor * (shell ? a.shell_T : (R)(*a.Tp));
     const int ky0 = kyc * a.ky_len;
     const int ky1 = min(Lf, ky0 + a.ky_len);
 
@@ -148,7 +153,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs<R> &a, const typename c
                 R w[NS];
 #pragma unroll
                 for (int l2 = 0; l2 < NS; l2++)
-                    w[l2] = pair_weight<WHICH, R>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr);
+                    w[l2] = pair_weight<WHICH, R>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr, lam);
 #pragma unroll
                 for (int t2 = 0; t2 < NS; t2++)
 #pragma unroll
@@ -468,6 +473,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
             }
             a.ky_chunks = pl.ky_chunks; a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
             a.thr_factor = 1e-5; a.Tp = m->d_scal; a.which = ch;
+            a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? m->T_reg : 0.0;
             cudaError_t e;
             if (ndyh <= 3) e = ch == 0 ? launch_one<double, 3, 8, 0>(m, a, 2) : launch_one<double, 3, 8, 1>(m, a, 2);
             else           e = ch == 0 ? launch_one<double, 5, 4, 0>(m, a, 4) : launch_one<double, 5, 4, 1>(m, a, 4);
@@ -497,6 +503,7 @@ cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only)
             }
             a.ky_chunks = pl.ky_chunks; a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
             a.thr_factor = 1e-2f; a.Tp = m->d_scal; a.which = ch;
+            a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? (float)m->T_reg : 0.f;
             cudaError_t e;
             if (ndyh <= 3) e = ch == 0 ? launch_one<float, 3, 16, 0>(m, a, 1) : launch_one<float, 3, 16, 1>(m, a, 1);
             else           e = ch == 0 ? launch_one<float, 5, 8, 0>(m, a, 2) : launch_one<float, 5, 8, 1>(m, a, 2);

@@ -65,7 +65,8 @@ struct Args2 {
     unsigned needed[MAXD];
     int ky_chunks, ky_len;
     float thr;               // degenerate-pair switch, used when Tp is null
-    const double *Tp;        // device temperature: switch = 1e-2 * (*Tp)
+    const double *Tp;        // device flow scale (T, or Lambda with the momentum shell): switch = 1e-2 * T
+    float shell_T;           // > 0: momentum-shell regulator at this fixed temperature (records hold f, h)
     const int *s_list;       // optional: CTA x evaluates transfer momentum s_list[x] (partials indexed by x)
     const int *skip;         // optional: the whole launch returns at once when *skip != 0
     const float2 *ptab;      // optional: e^{-2 pi i n / Lf}, n < Lf (computed in the kernel when null)
@@ -78,9 +79,10 @@ __host__ __device__ constexpr int abx(int t1, int t3, int t2, int t4)
     return WHICH == 0 ? ((t2 * 2 + t1) * 4 + t4 * 2 + t3) : ((t1 * 2 + t2) * 4 + t3 * 2 + t4);
 }
 
-template <int WHICH>
-__device__ __forceinline__ float pw(float e1, float g1, float gp1, float e2, float g2, float gp2, float thr)
+template <int WHICH, bool SHELL>
+__device__ __forceinline__ float pw(float e1, float g1, float gp1, float e2, float g2, float gp2, float thr, float lam)
 {
+    if (SHELL) return shell_weight<WHICH, float>(e1, g1, gp1, e2, g2, gp2, thr, lam);   // (g, gp) = (f, h)
     if (WHICH == 0) {
         const float s = e1 + e2;
         return fabsf(s) > thr ? -__fdividef(g1 + g2, s) : -0.5f * (gp1 + gp2);
@@ -90,7 +92,8 @@ __device__ __forceinline__ float pw(float e1, float g1, float gp1, float e2, flo
     }
 }
 
-template <int NDYH, int WHICH>
+// SHELL: momentum-shell regulator (a separate instantiation, so that the temperature flow's code is unchanged)
+template <int NDYH, int WHICH, bool SHELL = false>
 __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -116,7 +119,9 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
     unsigned char *region = smem_raw + ((sizeof(float2) * Lf + 15) & ~size_t(15)) + warp * warp_region_bytes(NDYH);
     float4 *ring = reinterpret_cast<float4 *>(region);   // [RING][6][32]: rows in flight of this warp's columns
     const int kx = blockIdx.y * NT + threadIdx.x;
-    const float thr = a.Tp ? (float)(1e-2 * *a.Tp) : a.thr;
+    // temperature flow: the scale is T; momentum shell: the scale is Lambda and the temperature is fixed
+    const float lam = SHELL ? (float)*a.Tp : 0.f;
+    const float thr = SHELL ? 1e-2f * a.shell_T : (a.Tp ? (float)(1e-2 * *a.Tp) : a.thr);
     const bool valid = kx < Lf;
     const int kyc = blockIdx.z;
     const int ky0 = kyc * a.ky_len;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(32 * WARPS) loops2_kernel(Args2 a)
 #pragma unroll
             for (int l1 = 0; l1 < 2; l1++)
 #pragma unroll
-                for (int l2 = 0; l2 < 2; l2++) w[l1][l2] = pw<WHICH>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr);
+                for (int l2 = 0; l2 < 2; l2++) w[l1][l2] = pw<WHICH, SHELL>(e1[l1], g1[l1], gp1[l1], e2[l2], g2[l2], gp2[l2], thr, lam);
             // T^{l1} = w_{l1 1} 1 + (w_{l1 0} - w_{l1 1}) rho2'^0 ;  D = T^0 - T^1
             const float A2 = b0.x, C2r = b0.y, C2i = sgn * b0.z;    // rho2' = rho2 (P) or conj(rho2) (C)
             const float dw0 = w[0][0] - w[0][1], dw1 = w[1][0] - w[1][1];
@@ -326,12 +331,31 @@ __global__ void rec_T_kernel(int n, double T_value, const double *Tp, float4 *re
     rec[2 * n + t] = make_float4(gp[1], 0.f, 0.f, 0.f);
 }
 
+// Momentum-shell records: (f, h) = (f(e), f (1 - f) / T) at the fixed temperature T in the slots of
+// (g, g'), from the FP64 energies (written once per model; the shell weight needs no T-dependent data).
+__global__ void rec_shell_kernel(const double *E, int Nk, int Lf, double mu, double T, float4 *rec)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nk) return;
+    const int kx = k / Lf, ky = k % Lf;
+    const size_t t = (size_t)ky * Lf + kx, plane = (size_t)Lf * Lf;
+    double f[2], h[2];
+    for (int l = 0; l < 2; l++) {
+        const double e = E[2 * k + l] - mu, z = exp(-fabs(e) / T);
+        f[l] = e > 0 ? z / (1.0 + z) : 1.0 / (1.0 + z);
+        h[l] = z / ((1.0 + z) * (1.0 + z)) / T;
+    }
+    const float e1 = rec[plane + t].x;
+    rec[plane + t] = make_float4(e1, (float)f[0], (float)f[1], (float)h[0]);
+    rec[2 * plane + t] = make_float4((float)h[1], 0.f, 0.f, 0.f);
+}
+
 template <int NDYH, int WHICH>
 cudaError_t launch2(tufrg_model *m, const Args2 &a, int n_s)
 {
     dim3 grid(n_s, (m->Lf + 32 * WARPS - 1) / (32 * WARPS), a.ky_chunks);
     const size_t smem = loops2_smem_bytes(m->Lf, NDYH);
-    auto kern = loops2_kernel<NDYH, WHICH>;
+    auto kern = a.shell_T > 0.f ? loops2_kernel<NDYH, WHICH, true> : loops2_kernel<NDYH, WHICH, false>;
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PhaseScope ps(m, PH_LOOPS);
     kern<<<grid, 32 * WARPS, smem, m->stream>>>(a);
@@ -369,8 +393,15 @@ cudaError_t launch_loop_records_static(tufrg_model *m)
     return cudaGetLastError();
 }
 
+cudaError_t launch_loop_records_shell(tufrg_model *m)
+{
+    rec_shell_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->d_E, m->Nk, m->Lf, m->mu, m->T_reg, m->d_rec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_loop_records(tufrg_model *m)
 {
+    if (m->regulator == TUFRG_REG_MOMENTUM_SHELL) return cudaSuccess;   // the shell records do not depend on Lambda
     PhaseScope ps(m, PH_FERMI);
     rec_T_kernel<<<(m->Nk + 255) / 256, 256, 0, m->stream>>>(m->Nk, 0.0, m->d_scal, m->d_rec);
     return cudaGetLastError();
@@ -406,6 +437,7 @@ cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_li
     a.ky_len = (m->Lf + pl.ky_chunks - 1) / pl.ky_chunks;
     a.thr = 0.f;
     a.Tp = m->d_scal;
+    a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? (float)m->T_reg : 0.f;
     a.ptab = m->d_lph32;
     const int n_s = s_list ? n_list : m->Nq;
     switch (ndyh) {

@@ -39,7 +39,8 @@ struct GenArgs {
     int dxs[GMAXD], dys[GMAXD];
     int dslot[GMAXD][GMAXD];            // [dxi][dyi] -> delta index (half plane), or -1
     R thr_factor;                       // degenerate-pair switch = thr_factor * T
-    const double *Tp;                   // device temperature
+    const double *Tp;                   // device flow scale (T, or Lambda with the momentum shell)
+    R shell_T;                          // > 0: momentum-shell regulator at this temperature (tables hold e, f, h)
     const int *s_list;                  // optional: CTA x sums transfer momentum s_list[x] into accumulator slot x
     int n_slot;                         // momenta per kx range (accumulator slots of one range)
     int kx_len;                         // columns per kx range; CTA y covers [y kx_len, (y + 1) kx_len)
@@ -69,8 +70,9 @@ size_t gen_smem(int Lf)
 }
 
 template <int WHICH, typename R>
-__device__ __forceinline__ R gweight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr)
+__device__ __forceinline__ R gweight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr, R lam)
 {
+    if (lam > R(0)) return shell_weight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);   // (g, gp) = (f, h)
     if (WHICH == 0) {
         const R s = e1 + e2;
         return fabs(s) > thr ? -(g1 + g2) / s : R(-0.5) * (gp1 + gp2);
@@ -104,7 +106,9 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     const int s = a.s_list ? a.s_list[blockIdx.x] : blockIdx.x;
     const int sx = (s / a.Lq) * a.nc, sy = (s % a.Lq) * a.nc;
     const int ta = threadIdx.x / GB, tb = threadIdx.x % GB;
-    const R thr = a.thr_factor * (R)(*a.Tp);
+    const bool shell = a.shell_T > R(0);
+    const R lam = shell ? (R)(*a.Tp) : R(0);
+    const R thr = a.thr_factor * (shell ? a.shell_T : (R)(*a.Tp));
     const bool active = threadIdx.x < NT;
     C2 *acc = a.acc + ((size_t)blockIdx.y * a.n_slot + blockIdx.x) * a.nd * NS2 * NS2;
     const int kx_end = min(Lf, (int)(blockIdx.y + 1) * a.kx_len);
@@ -147,7 +151,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
                 R e1, g1, gp1, e2, g2, gp2;
                 ldft(&a.ft[(size_t)k1 * NS + l1], e1, g1, gp1);
                 ldft(&a.ft[(size_t)k2 * NS + l2], e2, g2, gp2);
-                sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr);
+                sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);
             }
             __syncthreads();
             // T^{l1}_{p} = sum_l2 w_{l1 l2} rho2'^{l2}_p
@@ -456,12 +460,14 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only)
         if (fp64) {
             GenArgs<double> a{};
             a.U = m->d_U; a.ft = m->d_ft; a.acc = reinterpret_cast<double2 *>(m->d_part); a.thr_factor = 1e-5; a.Tp = m->d_scal;
+            a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? m->T_reg : 0.0;
             fill_args(m, a);
             fill_chunks(m, a);
             e = m->ns == 6 ? dispatch_gen<double, 6, 2, 3>(m, a, ch) : dispatch_gen<double, 4, 2, 2>(m, a, ch);
         } else {
             GenArgs<float> a{};
             a.U = m->d_U32; a.ft = m->d_ft32; a.acc = reinterpret_cast<float2 *>(m->d_part); a.thr_factor = 1e-2f; a.Tp = m->d_scal;
+            a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? (float)m->T_reg : 0.f;
             fill_args(m, a);
             fill_chunks(m, a);
             e = m->ns == 6 ? dispatch_gen<float, 6, 4, 3>(m, a, ch) : dispatch_gen<float, 4, 2, 2>(m, a, ch);

@@ -186,6 +186,10 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
         m->err = "tufrg_set_surrogate: bad arguments";
         return TUFRG_EINVAL;
     }
+    if (m->regulator != TUFRG_REG_TEMPERATURE) {
+        m->err = "the loop surrogate is trained on the temperature flow";
+        return TUFRG_ENOTSUP;
+    }
     if (!loops2_supported(m)) {
         m->err = "the loop surrogate needs a split-precision two-band model";
         return TUFRG_ENOTSUP;

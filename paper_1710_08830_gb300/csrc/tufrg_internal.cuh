@@ -27,6 +27,31 @@ struct FermiEntry {
 struct FermiEntry32 {
     float e, g, gp, pad;
 };
+// With the momentum-shell regulator the same entries hold (e, f, h) at the fixed temperature T_reg:
+// f = f(e), h = f (1 - f) / T_reg = -df/de (written once per model).
+
+// Momentum-shell loop weight of one band pair (Eq. def_lmp): with (f, h) at the fixed temperature,
+// F^- = (1 - f1 - f2) / (e1 + e2) (limit (h1 + h2) / 2), F^+ = (f1 - f2) / (e1 - e2) (limit
+// -(h1 + h2) / 2), chi = e^2 / (e^2 + lam^2) and w = d/dlam [chi(e1) chi(e2)] F.
+template <typename R> __device__ __forceinline__ R wdiv(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float wdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <int WHICH, typename R>
+__device__ __forceinline__ R shell_weight(R e1, R f1, R h1, R e2, R f2, R h2, R thr, R lam)
+{
+    R F;
+    if (WHICH == 0) {
+        const R s = e1 + e2;
+        F = fabs(s) > thr ? wdiv<R>(R(1) - f1 - f2, s) : R(0.5) * (h1 + h2);
+    } else {
+        const R d = e1 - e2;
+        F = fabs(d) > thr ? wdiv<R>(f1 - f2, d) : R(-0.5) * (h1 + h2);
+    }
+    const R l2 = lam * lam, a1 = e1 * e1, a2 = e2 * e2;
+    const R q1 = a1 + l2, q2 = a2 + l2;
+    // d/dlam [a1 a2 / (q1 q2)] = -2 lam a1 a2 (q1 + q2) / (q1 q2)^2
+    const R p = q1 * q2;
+    return wdiv<R>(R(-2) * lam * a1 * a2 * (q1 + q2), p * p) * F;
+}
 
 // Everything the projection kernel needs about one gather term.
 // kind: 0 = P<-C, 1 = P<-D, 2 = C<-P, 3 = C<-D.
@@ -140,6 +165,8 @@ struct tufrg_mlp;
 struct tufrg_model {
     // ---- descriptor copy
     int ns = 0, nhop = 0, nff = 0, Lq = 0, nc = 0, Lf = 0, Nq = 0, Nk = 0, M = 0, precision = 0;
+    int regulator = 0;      // TUFRG_REG_TEMPERATURE / TUFRG_REG_MOMENTUM_SHELL
+    double T_reg = 0.0;     // momentum shell: temperature of the Fermi functions
     std::vector<int> hopR, ffR;
     std::vector<double> hopt, V0;
     double mu = 0.0;
@@ -332,6 +359,8 @@ void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);
 cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
 cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu
+cudaError_t launch_loop_records_shell(tufrg_model *m);    // once per model (momentum shell): f, h at T_reg
+cudaError_t launch_fermi_shell(tufrg_model *m);           // once per model (momentum shell): (e, f, h) tables
 cudaError_t launch_loops2(tufrg_model *m, int ch);
 cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_list, float2 *part, const int *skip);
 cudaError_t launch_surrogate(tufrg_model *m, int channel_mask);
