@@ -84,6 +84,8 @@ def lib():
             L.or_project.restype = d
             L.or_vlv.argtypes = [vp, vp, vp, vp, i, vp]
             L.or_rhs.argtypes = [vp, vp, vp, d, vp, i, vp, vp]
+            L.or_band_transform.argtypes = [vp, vp, vp, vp]
+            L.or_band_transform.restype = None
             L.or_rhs.restype = d
             L.or_rhs_at.argtypes = [vp, vp, vp, d, vp, i, i, vp, vp]
             L.or_flow.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -208,6 +210,16 @@ class Oracle:
         LcC = np.ascontiguousarray(LcC, np.complex128)
         out = np.zeros_like(A)
         lib().or_vlv(C.byref(self.m), _ptr(A), _ptr(LcP), _ptr(LcC), chmask, _ptr(out))
+        return out
+
+    def band_transform(self, Ub: np.ndarray, state: np.ndarray) -> np.ndarray:
+        """Exchange propagators P, C of ``state`` in the band basis of the eigenvectors ``Ub[k][sigma][n]``
+        (Sec. 3.4, Eqs. mat_trafo_P, mat_trafo_D)."""
+        s = self.spec
+        Ub = np.ascontiguousarray(Ub, np.complex128).reshape(s.Nk, s.n_s, s.n_s)
+        st = np.ascontiguousarray(state, np.complex128).reshape(2, s.Nq, s.M, s.M)
+        out = np.zeros_like(st)
+        lib().or_band_transform(C.byref(self.m), _ptr(Ub), _ptr(st), _ptr(out))
         return out
 
     def rhs(self, T: float, state: np.ndarray, chmask: int = 3, want_A: bool = False):

@@ -31,6 +31,9 @@
  *     form of Eq. rge_Dmat), by naive triple loops.
  *  7. Dormand-Prince 5(4) integration in ln T (the paper only says "ordinary
  *     differential equations"; scheme chosen for this build).
+ *  8. Band-basis exchange propagators from the orbital ones with the
+ *     transformation matrices U(s), X(u) (Sec. 3.4, Eqs. trafo_P,
+ *     mat_trafo_P, mat_trafo_D), from their k-sum definitions.
  *
  * Parity status of each function is pinned by tests under tests/ (see the
  * oracle pin tests); nothing here is unpinned.
@@ -734,6 +737,72 @@ void or_vlv(const or_model *m, const double *Ahat, const double *LcP, const doub
                     D[(size_t)q * M2 + (size_t)i * M + j] = cx * s;
                 }
             free(Lm); free(Tm);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 8. Band basis (Sec. 3.4: Eqs. trafo_P, mat_trafo_P, mat_trafo_D)            */
+/* ------------------------------------------------------------------------ */
+
+/* The transformation matrices, from their definitions with f_R(k) = e^{-ik.R} and N = N_k (fine mesh):
+ *   U^{RR'}_{s1 s2 n1 n2}(s) = (1/N) sum_k f_R(k) f*_R'(k) U_{s1 n1}(s - k) U_{s2 n2}(k)
+ *   X^{RR'}_{s1 s2 n1 n2}(u) = (1/N) sum_k f_R(k) f*_R'(k) U_{s1 n1}(k) U*_{s2 n2}(k - u)
+ * and the exchange propagators in the band basis
+ *   P_band(s) = sum_sigma [U_{s2 s1 n2 n1}(s)]^dagger P(s) U_{s3 s4 n3 n4}(s)      (Eq. mat_trafo_P)
+ *   C_band(u) = sum_sigma [X_{s1 s3 n1 n3}(u)]^dagger C(u) X_{s4 s2 n4 n2}(u)      (Eq. mat_trafo_D)
+ * in the layouts of the orbital matrices (P: row (R,(n1,n2)), col (R',(n4,n3)); C: row (R,(n1,n3)),
+ * col (R',(n4,n2))).  As M x M matrices, T[(R1,(a,b)),(R,(c,d))] = U^{R1 R}_{b a d c}(s) for P and
+ * X^{R1 R}_{a b c d}(u) for C, and the band matrices are T^dagger X T.  Ub[k][sigma][n] are the
+ * eigenvectors to use (the band basis depends on their gauge). */
+void or_band_transform(const or_model *m, const double *Ub_in, const double *state, double *out)
+{
+    int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = nff * ns2;
+    int Lq = m->Lq, nc = m->nc, Lf = Lq * nc, Nk = Lf * Lf, Nq = Lq * Lq;
+    const cplx *Ub = (const cplx *)Ub_in;
+    const cplx *X = (const cplx *)state;
+    cplx *Y = (cplx *)out;
+    for (int ch = 0; ch < 2; ch++) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int s = 0; s < Nq; s++) {
+            int sx = (s / Lq) * nc, sy = (s % Lq) * nc;
+            cplx *T = calloc((size_t)M * M, sizeof(cplx));
+            cplx *W = calloc((size_t)M * M, sizeof(cplx));
+            for (int i1 = 0; i1 < nff; i1++)
+                for (int i = 0; i < nff; i++) {
+                    int Dx = m->ffR[2 * i1] - m->ffR[2 * i], Dy = m->ffR[2 * i1 + 1] - m->ffR[2 * i + 1];
+                    for (int kx = 0; kx < Lf; kx++)
+                        for (int ky = 0; ky < Lf; ky++) {
+                            cplx ph = conj(lattice_phase((long)kx * Dx + (long)ky * Dy, Lf));   /* f_R1 f*_R */
+                            int k = kx * Lf + ky;
+                            int k2 = ch == 0 ? imod(sx - kx, Lf) * Lf + imod(sy - ky, Lf)      /* s - k */
+                                             : imod(kx - sx, Lf) * Lf + imod(ky - sy, Lf);     /* k - u */
+                            for (int a = 0; a < ns; a++)
+                                for (int b = 0; b < ns; b++)
+                                    for (int c = 0; c < ns; c++)
+                                        for (int d = 0; d < ns; d++) {
+                                            cplx v = ch == 0 ? Ub[(size_t)k2 * ns2 + b * ns + d] * Ub[(size_t)k * ns2 + a * ns + c]
+                                                             : Ub[(size_t)k * ns2 + a * ns + c] * conj(Ub[(size_t)k2 * ns2 + b * ns + d]);
+                                            T[(size_t)(i1 * ns2 + a * ns + b) * M + i * ns2 + c * ns + d] += ph * v / (double)Nk;
+                                        }
+                        }
+                }
+            const cplx *Xs = X + ((size_t)ch * Nq + s) * M * M;
+            cplx *Ys = Y + ((size_t)ch * Nq + s) * M * M;
+            for (int r = 0; r < M; r++)          /* W = X T */
+                for (int c = 0; c < M; c++) {
+                    cplx acc = 0.0;
+                    for (int j = 0; j < M; j++) acc += Xs[(size_t)r * M + j] * T[(size_t)j * M + c];
+                    W[(size_t)r * M + c] = acc;
+                }
+            for (int r = 0; r < M; r++)          /* Y = T^dagger W */
+                for (int c = 0; c < M; c++) {
+                    cplx acc = 0.0;
+                    for (int j = 0; j < M; j++) acc += conj(T[(size_t)j * M + r]) * W[(size_t)j * M + c];
+                    Ys[(size_t)r * M + c] = acc;
+                }
+            free(T);
+            free(W);
         }
     }
 }

@@ -417,3 +417,86 @@ def test_shell_flow_reaches_temperature_bubble():
                 for s4 in range(ns):
                     expect[:, s1 * ns + s2, s4 * ns + s3] = -0.5 * (g + U) * A[s1, s2, s3, s4]
     assert np.abs(state[0] - expect).max() < 1e-6 * max(1.0, np.abs(expect).max())
+
+
+# ---------------------------------------------------------------- band basis (Sec. 3.4)
+
+def _schober_gauge(spec):
+    """Two-band H = eps 1 + g.sigma (g_z = 0): U_{sigma n}(k) = (1, n e^{i phi(k)}) / sqrt(2), n = -1 (lower band,
+    column 0) and +1 (upper, column 1), phi the polar angle of g(k) read off H(k) = sum_R t_R e^{i k.R}."""
+    Lf = spec.Lf
+    kx, ky = np.meshgrid(np.arange(Lf), np.arange(Lf), indexing="ij")
+    H = np.zeros((Lf, Lf, 2, 2), complex)
+    for R, t in zip(spec.hop_R, spec.hop_t):
+        H += t[None, None] * np.exp(2j * np.pi * (kx * R[0] + ky * R[1]) / Lf)[:, :, None, None]
+    gx, gy = H[..., 0, 1].real, -H[..., 0, 1].imag
+    phi = np.arctan2(gy, gx).reshape(-1)
+    Ub = np.zeros((Lf * Lf, 2, 2), complex)
+    for j, n in enumerate((-1, 1)):
+        Ub[:, 0, j] = 1 / np.sqrt(2)
+        Ub[:, 1, j] = n * np.exp(1j * phi) / np.sqrt(2)
+    # sanity: eigenvectors of H(k) with eigenvalues eps -/+ |g|
+    Hf = H.reshape(-1, 2, 2)
+    for j, n in enumerate((-1, 1)):
+        lam = Hf[:, 0, 0] + n * np.hypot(gx, gy).reshape(-1)
+        assert np.allclose(np.einsum("kab,kb->ka", Hf, Ub[:, :, j]), lam[:, None] * Ub[:, :, j], atol=1e-12)
+    return Ub, phi
+
+
+def test_band_basis_particle_particle_closed_form():
+    """Eq. Pinband (P2): the local particle-particle propagator of Eq. sol_spin, P = -(g+U)/2 (d13 d24 - d14 d23)
+    at R = R' = 0 with any g(s), transformed with Eq. mat_trafo_P in the gauge U_{sigma n} = (1, n e^{i phi})/sqrt 2,
+    is -(g+U)/8 (1/N^2) sum_{k,k'} f_R(k) f*_R'(k') [n1 n3 e^{i phi(s-k') - i phi(k)} + n2 n4 e^{i phi(k') - i phi(s-k)}
+    - n1 n4 e^{i phi(k') - i phi(k)} - n2 n3 e^{i phi(s-k') - i phi(s-k)}], written out here as factorised k-sums.
+    A transposed pair index or a missing conjugation in the transformation law fails it."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=4, nc=3, n_ff=5)
+    o = oracle.Oracle(spec)
+    Ub, phi = _schober_gauge(spec)
+    ns, M, Nq, Lq, nc, Lf = 2, spec.M, spec.Nq, spec.Lq, spec.nc, spec.Lf
+    rng = np.random.default_rng(11)
+    gU = rng.standard_normal(Nq) + 1j * rng.standard_normal(Nq)      # (g + U)(s), arbitrary
+    A = _pair_structure(ns)
+    st = np.zeros((2, Nq, M, M), complex)
+    for s1 in range(ns):
+        for s2 in range(ns):
+            for s3 in range(ns):
+                for s4 in range(ns):
+                    st[0, :, s1 * ns + s2, s4 * ns + s3] = -0.5 * gU * A[s1, s2, s3, s4]
+    out = o.band_transform(Ub, st)
+    assert np.abs(out[1]).max() == 0.0
+    k = np.arange(Lf * Lf)
+    kx, ky = k // Lf, k % Lf
+    ffR = spec.ff_R
+    f = np.exp(-2j * np.pi * (kx[None, :] * ffR[:, 0:1] + ky[None, :] * ffR[:, 1:2]) / Lf)   # f_R(k), [nff][Nk]
+    N = Lf * Lf
+    nn = (-1, 1)
+    for s in range(Nq):
+        sx, sy = (s // Lq) * nc, (s % Lq) * nc
+        smk = ((sx - kx) % Lf) * Lf + (sy - ky) % Lf                    # s - k on the fine mesh
+        e_k, e_smk = np.exp(1j * phi), np.exp(1j * phi[smk])
+        # (1/N) sum_k f_R(k) e^{-i phi(k)} etc. and (1/N) sum_k' f*_R'(k') e^{i phi(k')} etc.
+        a_k = f @ e_k.conj() / N
+        a_smk = f @ e_smk.conj() / N
+        b_k = f.conj() @ e_k / N
+        b_smk = f.conj() @ e_smk / N
+        for i, n1 in enumerate(nn):
+            for j, n2 in enumerate(nn):
+                for p, n3 in enumerate(nn):
+                    for q, n4 in enumerate(nn):
+                        term = (n1 * n3 * np.outer(a_k, b_smk) + n2 * n4 * np.outer(a_smk, b_k)
+                                - n1 * n4 * np.outer(a_k, b_k) - n2 * n3 * np.outer(a_smk, b_smk))
+                        want = -gU[s] / 8 * term                        # [R][R']
+                        got = out[0, s][np.ix_(np.arange(spec.n_ff) * 4 + i * 2 + j, np.arange(spec.n_ff) * 4 + q * 2 + p)]
+                        assert np.abs(got - want).max() < 1e-12 * max(1.0, np.abs(want).max()), (s, n1, n2, n3, n4)
+
+
+def test_band_basis_transformation_is_unitary_with_the_complete_set():
+    """With the complete form-factor set of a 3x3 torus (N_ff = N_k = 9) the truncated unity is exact and U(s),
+    X(u) are unitary: the transform of the identity is the identity in both channels, for the model's own
+    (Jacobi) eigenvectors."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.35, U=2.0, mu=-0.7, Lq=3, nc=1).with_(ff_R=inputs.ff_complete(3))
+    o = oracle.Oracle(spec)
+    M, Nq = spec.M, spec.Nq
+    eye = np.broadcast_to(np.eye(M), (2, Nq, M, M)).astype(complex)
+    out = o.band_transform(o.U, eye)
+    assert np.abs(out - eye).max() < 1e-12
