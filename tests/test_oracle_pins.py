@@ -500,3 +500,44 @@ def test_band_basis_transformation_is_unitary_with_the_complete_set():
     eye = np.broadcast_to(np.eye(M), (2, Nq, M, M)).astype(complex)
     out = o.band_transform(o.U, eye)
     assert np.abs(out - eye).max() < 1e-12
+
+
+def test_band_basis_maps_orbital_loops_to_band_diagonal_loops():
+    """Eq. loop_orbital is exact with the complete form-factor set: the transformation maps the orbital loop matrices
+    (the oracle's direct k-sums with the U dressing, pinned above against the brute-force fRG) onto the band-basis
+    loops, diagonal in the band pairs, [L_{l1 l2}]_{RR'}(s) = (1/N) sum_k f_R(k) f*_R'(k) w(e_l1(k1), e_l2(k2)) with
+    (k1, k2) = (s - k, k) for P and (k, k - u) for C.  Every entry of U(s), X(u) enters, so a swapped or
+    conjugated index fails it (the closed-form pin above is blind to the swap of the pair order, its state
+    being antisymmetric in both pairs)."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.35, U=2.0, mu=-0.7, Lq=3, nc=1).with_(ff_R=inputs.ff_complete(3))
+    o = oracle.Oracle(spec)
+    T = 0.3
+    ns, nff, M, Nq, Lf = 2, spec.n_ff, spec.M, spec.Nq, spec.Lf
+    d_of = {tuple(d): i for i, d in enumerate(o.deltas)}
+    X = np.zeros((2, Nq, M, M), complex)
+    for ch in (0, 1):
+        Lc = o.loops(T, ch)
+        for i1 in range(nff):
+            for i2 in range(nff):
+                di = d_of[tuple(spec.ff_R[i1] - spec.ff_R[i2])]
+                X[ch, :, i1 * 4:(i1 + 1) * 4, i2 * 4:(i2 + 1) * 4] = Lc[:, di]
+    out = o.band_transform(o.U, X)
+    e = o.E - o.mu                                             # [Nk][band]
+    k = np.arange(Lf * Lf)
+    kx, ky = k // Lf, k % Lf
+    f = np.exp(-2j * np.pi * (kx[None, :] * spec.ff_R[:, 0:1] + ky[None, :] * spec.ff_R[:, 1:2]) / Lf)
+    for ch, w in ((0, oracle.wm), (1, oracle.wp)):
+        for s in range(Nq):
+            sx, sy = s // spec.Lq, s % spec.Lq
+            other = (((sx - kx) % Lf) * Lf + (sy - ky) % Lf) if ch == 0 else (((kx - sx) % Lf) * Lf + (ky - sy) % Lf)
+            want = np.zeros((M, M), complex)
+            for l1 in range(ns):
+                for l2 in range(ns):
+                    e1 = e[other, l1] if ch == 0 else e[k, l1]
+                    e2 = e[k, l2] if ch == 0 else e[other, l2]
+                    wk = np.array([w(a, b, T) for a, b in zip(e1, e2)])
+                    B = (f * wk[None, :]) @ f.conj().T / (Lf * Lf)      # [R][R']
+                    # band pair index of the layouts: P (l2, l1) in rows and columns, C (l1, l2)
+                    p = l2 * ns + l1 if ch == 0 else l1 * ns + l2
+                    want[np.ix_(np.arange(nff) * 4 + p, np.arange(nff) * 4 + p)] = B
+            assert np.abs(out[ch, s] - want).max() < 1e-12 * max(1.0, np.abs(want).max()), (ch, s)
