@@ -167,6 +167,19 @@ tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc
  * reduce them, see TUFRG_SYMMETRY_AUTO). */
 tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
 
+/* Exchange propagators of a state in the band basis of the model's eigenvectors (Sec. 3.4, Eqs. trafo_P,
+ * mat_trafo_P, mat_trafo_D): with f_R(k) = e^{-ik.R}, N the fine mesh's k-points and U the eigenvectors of
+ * tufrg_bands,
+ *   U^{RR'}_{s1 s2 n1 n2}(s) = (1/N) sum_k f_R(k) f*_R'(k) U_{s1 n1}(s - k) U_{s2 n2}(k),
+ *   X^{RR'}_{s1 s2 n1 n2}(u) = (1/N) sum_k f_R(k) f*_R'(k) U_{s1 n1}(k) U*_{s2 n2}(k - u),
+ *   P_band(s) = sum_sigma [U_{s2 s1 n2 n1}(s)]^dagger P(s) U_{s3 s4 n3 n4}(s),
+ *   C_band(u) = sum_sigma [X_{s1 s3 n1 n3}(u)]^dagger C(u) X_{s4 s2 n4 n2}(u).
+ * d_state, d_out: [2][Nq][M][M] complex device buffers in the layouts of the orbital matrices with band
+ * indices in place of the orbital ones (P: row (R,(n1,n2)), col (R',(n4,n3)); C: row (R,(n1,n3)),
+ * col (R',(n4,n2))).  The result depends on the gauge of the eigenvectors.  FP64 models compute in FP64,
+ * split models in FP32.  Two-band models with M <= 64 (else TUFRG_ENOTSUP); stream ordered, no host sync. */
+tufrg_status tufrg_band_basis(tufrg_model *m, const void *d_state, void *d_out);
+
 /* Round n FP64 values at d_in to FP32 at d_out (device buffers, no overlap), to nearest with ties to
  * even: the rounding the split path applies to states, loop data and tables.  Stream ordered on
  * cuda_stream (NULL = legacy default stream).  Errors: TUFRG_EINVAL for NULL buffers with n > 0,

@@ -79,6 +79,8 @@ def lib():
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_symmetry_info.restype = C.c_int
             L.tufrg_round_f32.argtypes = [vp, vp, C.c_size_t, vp]
+            L.tufrg_band_basis.argtypes = [vp, vp, vp]
+            L.tufrg_band_basis.restype = C.c_int
             L.tufrg_round_f32.restype = C.c_int
             L.tufrg_gather_table.argtypes = [vp, i, vp, i, ip]
             L.tufrg_bands.argtypes = [vp, vp, vp]
@@ -127,6 +129,7 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_gather_table", "tufrg_bands", "tufrg_loops", "tufrg_project", "tufrg_rhs", "tufrg_rhs_host",
            "tufrg_flow", "tufrg_timing_begin", "tufrg_timing_end", "tufrg_loops_noalloc", "tufrg_model_info", "tufrg_loop_momenta",
            "tufrg_symmetry_info", "tufrg_round_f32", "tufrg_rhs_host_batch",
+           "tufrg_band_basis",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")

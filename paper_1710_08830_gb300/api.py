@@ -164,6 +164,15 @@ class Model:
         self._check(self._L.tufrg_rhs_host(self._h, float(T), _ptr(state_host), int(mask), _ptr(out_host)))
         return out_host
 
+    def band_basis(self, state, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The exchange propagators P, C of ``state`` in the band basis of the model's eigenvectors (``bands()``),
+        two-band models (Sec. 3.4, Eqs. mat_trafo_P, mat_trafo_D)."""
+        state = self._dev(state)
+        if out is None:
+            out = torch.empty_like(state)
+        self._check(self._L.tufrg_band_basis(self._h, _ptr(state), _ptr(out)))
+        return out
+
     def rhs_host_batch(self, T, states_host, outs_host, mask: int = CH_P | CH_C, symmetric: bool = False):
         """dX/dT for a sequence of host (ideally pinned) states, the transfers of neighbouring steps overlapped with
         the evaluations: step i reads states_host[i] at T[i] (a scalar T applies to every step) and writes

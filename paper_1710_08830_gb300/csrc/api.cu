@@ -493,7 +493,7 @@ void release(tufrg_model *m)
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
-                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp,
+                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1175,6 +1175,16 @@ tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct)
 {
     if (!m || !n_direct) return TUFRG_EINVAL;
     *n_direct = m->n_loop_q;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_band_basis(tufrg_model *m, const void *d_state, void *d_out)
+{
+    if (!m || !d_state || !d_out) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!band_basis_supported(m))
+        return fail(m, TUFRG_ENOTSUP, "the band-basis transformation supports two-band models with M <= 64");
+    CK(launch_band_basis(m, reinterpret_cast<const double2 *>(d_state), reinterpret_cast<double2 *>(d_out)),
+       "band-basis transformation");
     return TUFRG_OK;
 }
 

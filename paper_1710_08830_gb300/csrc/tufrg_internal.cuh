@@ -224,6 +224,7 @@ struct tufrg_model {
     int *d_orb_q = nullptr;         // [Nq]
     int *d_sym_emap = nullptr;      // [n_sym_elem][2][M^2] source entry << 3 | quarter turns << 1 | conj (small M)
     int *d_orb_lexp = nullptr;      // [M^2] compact-loop index of every expanded loop-matrix entry (small M)
+    void *d_band_tc = nullptr;      // [2][Nq][n_delta][16] compact band-basis transformation matrices
     int *d_eofs[2] = {nullptr, nullptr};       // per output channel: CSR offsets per matrix entry, [M*M + 1]
     int2 *d_eterms[2] = {nullptr, nullptr};    // per entry terms: (flat index into the Fourier transforms,
                                                //  high bit = minus sign; phase-table column)
@@ -352,6 +353,9 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);
 // symmetric states: products at the orbit representatives and dX/dT of every momentum (the fused orbit
 // kernel where its tables exist, else the representatives' products plus the scatter)
 cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out);
+// band-basis exchange propagators of a two-band model's state (Sec. 3.4)
+bool band_basis_supported(const tufrg_model *m);
+cudaError_t launch_band_basis(tufrg_model *m, const double2 *d_state, double2 *d_out);
 bool orbit_products_supported(const tufrg_model *m);
 int orbit_max_size();   // largest orbit the fused orbit kernel takes   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
