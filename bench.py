@@ -406,6 +406,23 @@ def main():
     e2e_single = world * ke / (allmax(ke / e2e_single))
     state_bytes = int(hs[0].numel() * hs[0].element_size())
 
+    # ---------------- band-basis exchange propagators of the benchmark state (outside the timed region)
+    band = None
+    if spec.n_s == 2 and spec.M <= 64:
+        bout = torch.empty_like(state)
+        for _ in range(3):
+            m32.band_basis(state, out=bout)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nb = 20
+        b0.record(stream)
+        for _ in range(nb):
+            m32.band_basis(state, out=bout)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        band = {"ms": b0.elapsed_time(b1) / nb, "precision": "FP32 (split model)",
+                "note": "tufrg_band_basis: transformation matrices U(s), X(u) by a k-sum over the fine mesh, then "
+                        "U^dagger P U and X^dagger C X for every momentum (Sec. 3.4)"}
+
     # ---------------- time-to-Lambda_c (full flows from T0 = 10)
     flows = None
     if not args.no_flow:
@@ -527,6 +544,7 @@ def main():
                                   if m32.products == "tc" else None),
             "cpu_baseline": cpu,
             "batch_flows": batch,
+            "band_basis": band,
             "clocks": clocks,
             "peaks_source": peak_src,
             "wall_s_timed": t_wall,
