@@ -37,6 +37,33 @@ WORKLOADS = {
 }
 
 
+class RankGroup:
+    """Barrier and maximum over the ranks of one job: NCCL tensors on the GPUs, gloo on CPU tensors in the
+    multi-process tests; a single process (dist None) is a group of one."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist, self.device = dist, device
+        self.world = dist.get_world_size() if dist is not None else 1
+        self.rank = dist.get_rank() if dist is not None else 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(units: float, seconds: float, group: RankGroup) -> float:
+    """Units processed by all ranks (each rank the same number: weak scaling) over the slowest rank's time."""
+    return group.world * units / group.max(seconds)
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -275,16 +302,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    group = RankGroup(dist, "cuda")
+    barrier, allmax = group.barrier, group.max
 
     workload, metric = WORKLOADS[args.workload]
     if args.workload == "rashba":
@@ -336,7 +355,7 @@ def main():
     launches = launches * args.steps // k_phase
     loop_launches = loop_launches * args.steps // k_phase
     dev_ms_max = allmax(dev_ms)
-    value = world * args.steps / (dev_ms_max * 1e-3)
+    value = whole_job_rate(args.steps, dev_ms * 1e-3, group)
     ms_per_step = dev_ms_max / args.steps
 
     # ---------------- accuracy of the split path against the FP64 GPU path (same state)
@@ -394,16 +413,14 @@ def main():
     barrier()
     t = time.perf_counter()
     m32.rhs_host_batch(T_BENCH, [hs[i % 2] for i in range(ke)], [ho[i % 2] for i in range(ke)], symmetric=True)
-    e2e_rate = ke / (time.perf_counter() - t)
-    e2e_rate = world * ke / (allmax(ke / e2e_rate))
+    e2e_rate = whole_job_rate(ke, time.perf_counter() - t, group)
     # one blocking call per step (tufrg_rhs_host), for comparison
     for _ in range(3):
         m32.rhs_host(T_BENCH, hs[0], ho[0], mask=3 | SYMMETRIC_STATE)
     t = time.perf_counter()
     for _ in range(ke):
         m32.rhs_host(T_BENCH, hs[0], ho[0], mask=3 | SYMMETRIC_STATE)
-    e2e_single = ke / (time.perf_counter() - t)
-    e2e_single = world * ke / (allmax(ke / e2e_single))
+    e2e_single = whole_job_rate(ke, time.perf_counter() - t, group)
     state_bytes = int(hs[0].numel() * hs[0].element_size())
 
     # ---------------- band-basis exchange propagators of the benchmark state (outside the timed region)
