@@ -47,15 +47,6 @@ inline size_t loops2_smem_bytes(int Lf, int ndyh)
     return ((sizeof(float2) * Lf + 15) & ~size_t(15)) + WARPS * warp_region_bytes(ndyh);
 }
 
-// 16-byte asynchronous copy global -> shared (L2 only), and the waits on this thread's own copy groups
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 struct Args2 {
     const float4 *rec;       // [3][Lf][Lf] planes, index [j][ky][kx]:
                              //   (rho00, Re rho01, Im rho01, e0), (e1, g0, g1, gp0), (gp1, -, -, -)

@@ -60,13 +60,19 @@ __device__ __forceinline__ void ldft(const FermiEntry32 *p, float &e, float &g, 
 // v in [0, 2 L) -> v mod L without a division
 __device__ __forceinline__ int wrap1(int v, int L) { return v >= L ? v - L : v; }
 
-// Shared memory of one CTA: phase table [Lf], rho1 / T / rho2' [KB][NS][NS^2] each, batch phases
-// [KB][NDYH], pair weights [KB][NS][NS].
+// Shared memory of one CTA: two buffers of the raw eigenvectors [2 sides][KB][NS^2] and Fermi entries
+// [2 sides][KB][NS] of a batch (side 0: k1, side 1: k2; filled by cp.async one batch ahead), then the phase
+// table [Lf], rho1 / T / rho2' [KB][NS][NS^2] each, batch phases [KB][NDYH], pair weights [KB][NS][NS].
+template <typename R, int NS>
+constexpr size_t gen_raw_bytes()
+{
+    return 2 * (sizeof(typename cpx<R>::t) * 2 * KB * NS * NS + sizeof(typename FTg<R>::t) * 2 * KB * NS);
+}
 template <typename R, int NS, int NDYH>
 size_t gen_smem(int Lf)
 {
     using C2 = typename cpx<R>::t;
-    return sizeof(C2) * (Lf + 3 * KB * NS * NS * NS + KB * NDYH) + sizeof(R) * KB * NS * NS;
+    return gen_raw_bytes<R, NS>() + sizeof(C2) * (Lf + 3 * KB * NS * NS * NS + KB * NDYH) + sizeof(R) * KB * NS * NS;
 }
 
 template <int WHICH, typename R>
@@ -89,9 +95,14 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     constexpr int NS2 = NS * NS;
     constexpr int GA = NS2 / TA, GB = NS2 / TB;     // thread grid over (a, b) tiles
     constexpr int NT = GA * GB;
+    using FT = typename FTg<R>::t;
     static_assert(NT >= KB * NDYH, "batch phases are staged by one thread each");
+    constexpr int CU = NS2 * (int)sizeof(C2) / 16, CF = NS * (int)sizeof(FT) / 16, CK = CU + CF;
+    static_assert(CU * 16 == NS2 * (int)sizeof(C2) && CF * 16 == NS * (int)sizeof(FT), "rows of 16-byte chunks");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C2 *ptab = reinterpret_cast<C2 *>(smem_raw);                    // [Lf] e^{-2 pi i n / Lf}
+    C2 *sUr = reinterpret_cast<C2 *>(smem_raw);                     // [2 buffers][2 sides][KB][NS2]
+    FT *sFr = reinterpret_cast<FT *>(sUr + 2 * 2 * KB * NS2);       // [2 buffers][2 sides][KB][NS]
+    C2 *ptab = reinterpret_cast<C2 *>(smem_raw + gen_raw_bytes<R, NS>());   // [Lf] e^{-2 pi i n / Lf}
     C2 *sA = ptab + a.Lf;                                          // [KB][NS][NS2] rho1
     C2 *sB = sA + KB * NS * NS2;                                   // [KB][NS][NS2] T
     C2 *sR2 = sB + KB * NS * NS2;                                  // [KB][NS][NS2] rho2'
@@ -112,6 +123,30 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
     const bool active = threadIdx.x < NT;
     C2 *acc = a.acc + ((size_t)blockIdx.y * a.n_slot + blockIdx.x) * a.nd * NS2 * NS2;
     const int kx_end = min(Lf, (int)(blockIdx.y + 1) * a.kx_len);
+    // fine-mesh indices of row ky of column kx: k1 = s - k, k2 = k (P); k1 = k, k2 = k - s (C)
+    auto k_of = [&](int side, int kx, int ky) {
+        if (side == (WHICH == 0 ? 1 : 0)) return kx * Lf + ky;                      // the point k itself
+        return WHICH == 0 ? wrap1(sx - kx + Lf, Lf) * Lf + wrap1(sy - ky + Lf, Lf)  // s - k
+                          : wrap1(kx - sx + Lf, Lf) * Lf + wrap1(ky - sy + Lf, Lf); // k - s
+    };
+    // copies of the raw eigenvectors and Fermi entries of the rows [ky0, ky0 + KB) of column kx into buffer buf
+    auto stage_raw = [&](int kx, int ky0, int buf) {
+        const int nb = min(KB, Lf - ky0), per_side = nb * CK;
+        for (int idx = threadIdx.x; idx < 2 * per_side; idx += blockDim.x) {
+            const int side = idx >= per_side, r = idx - side * per_side, kb = r / CK, c = r % CK;
+            const int k = k_of(side, kx, ky0 + kb);
+            const int slot = (buf * 2 + side) * KB + kb;
+            if (c < CU)
+                cp_async16(reinterpret_cast<char *>(sUr + (size_t)slot * NS2) + 16 * c,
+                           reinterpret_cast<const char *>(a.U + (size_t)k * NS2) + 16 * c);
+            else
+                cp_async16(reinterpret_cast<char *>(sFr + (size_t)slot * NS) + 16 * (c - CU),
+                           reinterpret_cast<const char *>(a.ft + (size_t)k * NS) + 16 * (c - CU));
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (blockIdx.y * a.kx_len < kx_end) stage_raw(blockIdx.y * a.kx_len, 0, 0);
 
     for (int kx = blockIdx.y * a.kx_len; kx < kx_end; kx++) {
         C2 W[NDYH][TA][TB];
@@ -121,11 +156,17 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             for (int i = 0; i < TA; i++)
 #pragma unroll
                 for (int j = 0; j < TB; j++) W[d][i][j] = mk(R(0), R(0));
-        // row offsets of the shifted columns: (s - k)_x (P) and (k - s)_x (C) on the fine mesh
-        const int k1x = wrap1(sx - kx + Lf, Lf) * Lf, k2x = wrap1(kx - sx + Lf, Lf) * Lf;
-        for (int ky0 = 0; ky0 < Lf; ky0 += KB) {
+        for (int ky0 = 0; ky0 < Lf; ky0 += KB, buf ^= 1) {
             const int nb = min(KB, Lf - ky0);
-            __syncthreads();   // previous batch fully consumed
+            // copies of the next batch (this column's next rows, else the next column's first) go out before
+            // this batch is used; the raw buffer they fill was last read before the previous batch's products
+            if (ky0 + KB < Lf) stage_raw(kx, ky0 + KB, buf ^ 1);
+            else if (kx + 1 < kx_end) stage_raw(kx + 1, 0, buf ^ 1);
+            else cp_async_commit();   // an empty group keeps the count of one group in flight
+            cp_async_wait<1>();        // this thread's copies of the current batch have landed
+            __syncthreads();           // everyone's copies landed; previous batch fully consumed
+            const C2 *rU1 = sUr + (size_t)(buf * 2 + 0) * KB * NS2, *rU2 = sUr + (size_t)(buf * 2 + 1) * KB * NS2;
+            const FT *rF1 = sFr + (size_t)(buf * 2 + 0) * KB * NS, *rF2 = sFr + (size_t)(buf * 2 + 1) * KB * NS;
             if (threadIdx.x < KB * NDYH) {
                 const int kb = threadIdx.x / NDYH, d = threadIdx.x % NDYH;
                 if (kb < nb && d < a.ndyh) sPh[threadIdx.x] = ptab[((ky0 + kb) * a.dys[d]) % Lf];
@@ -134,23 +175,17 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             for (int idx = threadIdx.x; idx < nb * NS * NS2; idx += blockDim.x) {
                 const int kb = idx / (NS * NS2), r = idx % (NS * NS2), l = r / NS2, p = r % NS2;
                 const int t = p / NS, tp = p % NS;
-                const int ky = ky0 + kb;
-                const int k1 = WHICH == 0 ? k1x + wrap1(sy - ky + Lf, Lf) : kx * Lf + ky;
-                const int k2 = WHICH == 0 ? kx * Lf + ky : k2x + wrap1(ky - sy + Lf, Lf);
-                const C2 u = a.U[(size_t)k1 * NS2 + t * NS + l], v = a.U[(size_t)k1 * NS2 + tp * NS + l];
+                const C2 u = rU1[kb * NS2 + t * NS + l], v = rU1[kb * NS2 + tp * NS + l];
                 sA[idx] = mk(u.x * v.x + u.y * v.y, u.y * v.x - u.x * v.y);          // u conj(v)
-                const C2 x = a.U[(size_t)k2 * NS2 + t * NS + l], y = a.U[(size_t)k2 * NS2 + tp * NS + l];
+                const C2 x = rU2[kb * NS2 + t * NS + l], y = rU2[kb * NS2 + tp * NS + l];
                 sR2[idx] = WHICH == 0 ? mk(x.x * y.x + x.y * y.y, x.y * y.x - x.x * y.y)    // x conj(y)
                                       : mk(x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x);   // conj(x) y
             }
             for (int idx = threadIdx.x; idx < nb * NS * NS; idx += blockDim.x) {
                 const int kb = idx / (NS * NS), l1 = (idx / NS) % NS, l2 = idx % NS;
-                const int ky = ky0 + kb;
-                const int k1 = WHICH == 0 ? k1x + wrap1(sy - ky + Lf, Lf) : kx * Lf + ky;
-                const int k2 = WHICH == 0 ? kx * Lf + ky : k2x + wrap1(ky - sy + Lf, Lf);
                 R e1, g1, gp1, e2, g2, gp2;
-                ldft(&a.ft[(size_t)k1 * NS + l1], e1, g1, gp1);
-                ldft(&a.ft[(size_t)k2 * NS + l2], e2, g2, gp2);
+                ldft(&rF1[kb * NS + l1], e1, g1, gp1);
+                ldft(&rF2[kb * NS + l2], e2, g2, gp2);
                 sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);
             }
             __syncthreads();
@@ -226,6 +261,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
             }
         }
     }
+    cp_async_wait<0>();   // nothing in flight at exit (the last group is empty)
 }
 
 // re, im += the n values p[c stride] in order c = 0, 1, ... (FP64), eight loads in flight

@@ -152,6 +152,15 @@ __device__ __forceinline__ float narrow_f(double x)
     return narrow_general(x);
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and the waits on this thread's own copy groups
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 struct LoopPlan {
     int kx_per_cta;     // threads (columns) per CTA
     int ky_chunks;      // number of ky ranges per column
