@@ -353,6 +353,95 @@ def test_su2_relations_without_soc():
     assert np.abs(Pt(0, 1, 0, 1)).max() > 1e-3 and np.abs(Ct(0, 1, 0, 1)).max() > 1e-3
 
 
+# The square-lattice point group C4v as integer matrices acting on (x, y): the four rotations, then the four mirrors.
+_C4V = [np.array(g) for g in (((1, 0), (0, 1)), ((0, -1), (1, 0)), ((-1, 0), (0, -1)), ((0, 1), (-1, 0)),
+                              ((-1, 0), (0, 1)), ((1, 0), (0, -1)), ((0, 1), (1, 0)), ((0, -1), (-1, 0)))]
+_SX = np.array([[0, 1], [1, 0]], complex)
+_SY = np.array([[0, -1j], [1j, 0]])
+_SZ = np.diag([1.0 + 0j, -1.0])
+
+
+def _spin_rep(g):
+    """SU(2) matrix of a C4v element acting on a spin (an axial vector): a rotation by theta about z is
+    exp(-i theta/2 sigma_z); a mirror acts on an axial vector as the rotation by pi about its normal n."""
+    if round(np.linalg.det(g)) == 1:
+        th = np.arctan2(g[1, 0], g[0, 0])
+        return np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)])
+    w, v = np.linalg.eigh(g.astype(float))
+    n = v[:, np.argmin(w)]                                  # the mirror's normal (eigenvalue -1)
+    return -1j * (n[0] * _SX + n[1] * _SY)
+
+
+def _h_of_k(spec, k):
+    return np.einsum("h,hab->ab", np.exp(1j * (spec.hop_R @ k)), spec.hop_t)
+
+
+def _mat(spec, X):
+    """[Nq][M][M] -> [Nq][n_ff][ns^2][n_ff][ns^2]."""
+    ns2 = spec.n_s ** 2
+    return X.reshape(spec.Nq, spec.n_ff, ns2, spec.n_ff, ns2)
+
+
+def test_point_group_and_time_reversal_of_loops_and_flow():
+    """The Rashba model has C4v with spins rotating along, H(gk) = W_g H(k) W_g^+, and time reversal,
+    H(-k) = Theta H(k)^* Theta^+ with Theta = i sigma_y (Sec. 4).  With U(gk) = W_g U(k) in the projectors
+    rho = U U^+ of Eq. loop_orbital and plain-wave form factors, the loop matrices obey
+        L_X(g q)[(g R1, a), (g R2, b)] = (V_X L_X(q) V_X^+)[(R1, a), (R2, b)],
+        L_X(-q)[(R1, a), (R2, b)]      = (V'_X L_X(q)^* V'_X^+)[(R1, a), (R2, b)],
+    where the P pair (t2, t1) carries two eigenvector (U) indices, V_P = W (x) W, and the C pair (t1, t2) one
+    U and one U^* index, V_C = W (x) W^*; V' likewise with Theta.  The flowing P and C are built from these loops
+    by Eq. RGE_spin and the projections, so they transform in the same way: checked at T = 0.3 after a flow from
+    T0 = 10."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=5, nc=2, n_ff=9)
+    o = oracle.Oracle(spec)
+    rng = np.random.default_rng(3)
+    # the setup itself: the Hamiltonian of the descriptor reproduces the oracle's bands and has the symmetries
+    Lf = spec.Lq * spec.nc
+    for idx in (0, 7, 33):
+        k = 2 * np.pi * np.array([idx // Lf, idx % Lf]) / Lf
+        assert np.allclose(np.linalg.eigvalsh(_h_of_k(spec, k)), o.E[idx], atol=1e-12)
+    theta = 1j * _SY
+    for g in _C4V:
+        W = _spin_rep(g)
+        for _ in range(3):
+            k = rng.uniform(-np.pi, np.pi, 2)
+            assert np.allclose(_h_of_k(spec, g @ k), W @ _h_of_k(spec, k) @ W.conj().T, atol=1e-13)
+    k = rng.uniform(-np.pi, np.pi, 2)
+    assert np.allclose(_h_of_k(spec, -k), theta @ _h_of_k(spec, k).conj() @ theta.conj().T, atol=1e-13)
+
+    L = {w: _mat(spec, _expand_all(spec, o, o.loops(0.3, w))) for w in (0, 1)}
+    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
+    X = {0: _mat(spec, st[0]), 1: _mat(spec, st[1])}
+    bond = {tuple(r): i for i, r in enumerate(spec.ff_R)}
+    Lq = spec.Lq
+
+    def qmap(q, g):
+        x, y = g @ np.array([q // Lq, q % Lq])
+        return (x % Lq) * Lq + (y % Lq)
+
+    def pair_rep(w, Wm):
+        return np.kron(Wm, Wm) if w == 0 else np.kron(Wm, Wm.conj())
+
+    checked = 0
+    for w in (0, 1):
+        for Y in (L[w], X[w]):
+            scale = np.abs(Y).max()
+            assert scale > 1e-3
+            for g in _C4V:
+                V = pair_rep(w, _spin_rep(g))
+                perm = [bond[tuple(g @ r)] for r in spec.ff_R]
+                for q in range(spec.Nq):
+                    lhs = Y[qmap(q, g)][np.ix_(perm, range(Y.shape[2]), perm, range(Y.shape[4]))]
+                    rhs = np.einsum("ab,ibjc,dc->iajd", V, Y[q], V.conj())
+                    assert np.abs(lhs - rhs).max() < 1e-12 * scale, (w, g.tolist(), q)
+                    checked += 1
+            Vt = pair_rep(w, theta)
+            for q in range(spec.Nq):
+                rhs = np.einsum("ab,ibjc,dc->iajd", Vt, Y[q].conj(), Vt.conj())
+                assert np.abs(Y[qmap(q, -np.eye(2, dtype=int))] - rhs).max() < 1e-12 * scale, (w, q)
+    assert checked == 2 * 2 * len(_C4V) * spec.Nq
+
+
 # ---------------------------------------------------------------- momentum-shell regulator (Eq. def_lmp)
 
 def _fermi(e, T):
