@@ -376,70 +376,98 @@ def _h_of_k(spec, k):
     return np.einsum("h,hab->ab", np.exp(1j * (spec.hop_R @ k)), spec.hop_t)
 
 
-def _mat(spec, X):
-    """[Nq][M][M] -> [Nq][n_ff][ns^2][n_ff][ns^2]."""
-    ns2 = spec.n_s ** 2
-    return X.reshape(spec.Nq, spec.n_ff, ns2, spec.n_ff, ns2)
+def _orbital_rep(g):
+    """Representation of a C4v element on the t2g orbitals (yz, xz, xy), polar quadratic forms in (x, y, z):
+    (O_g f)(r) = f(G^-1 r) with G = g (+) 1 maps the form Q_j to G Q_j G^T = sum_i D_ij Q_i."""
+    G = np.eye(3)
+    G[:2, :2] = g
+    Q = []
+    for a, b in ((1, 2), (0, 2), (0, 1)):
+        q = np.zeros((3, 3))
+        q[a, b] = q[b, a] = 1.0
+        Q.append(q)
+    return np.array([[np.sum(Qi * (G @ Qj @ G.T)) / 2.0 for Qj in Q] for Qi in Q])
 
 
-def test_point_group_and_time_reversal_of_loops_and_flow():
-    """The Rashba model has C4v with spins rotating along, H(gk) = W_g H(k) W_g^+, and time reversal,
-    H(-k) = Theta H(k)^* Theta^+ with Theta = i sigma_y (Sec. 4).  With U(gk) = W_g U(k) in the projectors
-    rho = U U^+ of Eq. loop_orbital and plain-wave form factors, the loop matrices obey
-        L_X(g q)[(g R1, a), (g R2, b)] = (V_X L_X(q) V_X^+)[(R1, a), (R2, b)],
-        L_X(-q)[(R1, a), (R2, b)]      = (V'_X L_X(q)^* V'_X^+)[(R1, a), (R2, b)],
-    where the P pair (t2, t1) carries two eigenvector (U) indices, V_P = W (x) W, and the C pair (t1, t2) one
-    U and one U^* index, V_C = W (x) W^*; V' likewise with Theta.  The flowing P and C are built from these loops
-    by Eq. RGE_spin and the projections, so they transform in the same way: checked at T = 0.3 after a flow from
-    T0 = 10."""
-    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=5, nc=2, n_ff=9)
-    o = oracle.Oracle(spec)
+def _check_setup(spec, o, reps, theta):
+    """The Hamiltonian of the descriptor reproduces the oracle's bands and has the symmetries used below."""
     rng = np.random.default_rng(3)
-    # the setup itself: the Hamiltonian of the descriptor reproduces the oracle's bands and has the symmetries
     Lf = spec.Lq * spec.nc
-    for idx in (0, 7, 33):
+    for idx in (0, 7, Lf + 2):
         k = 2 * np.pi * np.array([idx // Lf, idx % Lf]) / Lf
         assert np.allclose(np.linalg.eigvalsh(_h_of_k(spec, k)), o.E[idx], atol=1e-12)
-    theta = 1j * _SY
-    for g in _C4V:
-        W = _spin_rep(g)
+    for g, W in zip(_C4V, reps):
         for _ in range(3):
             k = rng.uniform(-np.pi, np.pi, 2)
             assert np.allclose(_h_of_k(spec, g @ k), W @ _h_of_k(spec, k) @ W.conj().T, atol=1e-13)
     k = rng.uniform(-np.pi, np.pi, 2)
     assert np.allclose(_h_of_k(spec, -k), theta @ _h_of_k(spec, k).conj() @ theta.conj().T, atol=1e-13)
 
-    L = {w: _mat(spec, _expand_all(spec, o, o.loops(0.3, w))) for w in (0, 1)}
-    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
-    X = {0: _mat(spec, st[0]), 1: _mat(spec, st[1])}
+
+def _check_covariance(spec, Y, w, reps, theta):
+    """Y: [Nq][M][M] of channel w (0 = P, 1 = C); the group action written out from the definitions:
+        Y(g q)[(g R1, a), (g R2, b)] = (V Y(q) V^+)[(R1, a), (R2, b)],  Y(-q) = V' Y(q)^* V'^+,
+    with the pair representation V = W (x) W for the P pair (t2, t1) (two eigenvector indices) and
+    W (x) W^* for the C pair (t1, t2) (one U and one U^* index); V' likewise with Theta."""
+    scale = np.abs(Y).max()
+    assert scale > 1e-3
     bond = {tuple(r): i for i, r in enumerate(spec.ff_R)}
-    Lq = spec.Lq
+    Lq, ns2, one = spec.Lq, spec.n_s ** 2, np.eye(spec.n_ff)
 
     def qmap(q, g):
         x, y = g @ np.array([q // Lq, q % Lq])
         return (x % Lq) * Lq + (y % Lq)
 
-    def pair_rep(w, Wm):
+    def pair_rep(Wm):
         return np.kron(Wm, Wm) if w == 0 else np.kron(Wm, Wm.conj())
 
-    checked = 0
+    for g, W in zip(_C4V, reps):
+        V = np.kron(one, pair_rep(W))                        # the pair representation on every bond block
+        rows = [bond[tuple(g @ r)] * ns2 + a for r in spec.ff_R for a in range(ns2)]   # (R, a) -> (g R, a)
+        for q in range(spec.Nq):
+            lhs = Y[qmap(q, g)][np.ix_(rows, rows)]
+            assert np.abs(lhs - V @ Y[q] @ V.conj().T).max() < 1e-12 * scale, (w, g.tolist(), q)
+    Vt = np.kron(one, pair_rep(theta))
+    for q in range(spec.Nq):
+        rhs = Vt @ Y[q].conj() @ Vt.conj().T
+        assert np.abs(Y[qmap(q, -np.eye(2, dtype=int))] - rhs).max() < 1e-12 * scale, (w, q)
+
+
+def test_point_group_and_time_reversal_rashba():
+    """The Rashba model (Sec. 4) has C4v with the spins rotating along, H(gk) = W_g H(k) W_g^+, and time
+    reversal, H(-k) = Theta H(k)^* Theta^+ with Theta = i sigma_y.  With U(gk) = W_g U(k) in the projectors
+    rho = U U^+ of Eq. loop_orbital and plain-wave form factors (g k . g R = k . R), both loop channels
+    transform as stated in _check_covariance; the flowing P and C, built from them by Eq. RGE_spin and the
+    projections, transform alike: checked at every momentum of a 5x5 mesh at T = 0.3 after a flow from T0 = 10.
+    Swapping the C pair rule for the P rule, dropping the bond permutation or taking another element's W
+    fails it."""
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=5, nc=2, n_ff=9)
+    o = oracle.Oracle(spec)
+    reps, theta = [_spin_rep(g) for g in _C4V], 1j * _SY
+    _check_setup(spec, o, reps, theta)
+    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
     for w in (0, 1):
-        for Y in (L[w], X[w]):
-            scale = np.abs(Y).max()
-            assert scale > 1e-3
-            for g in _C4V:
-                V = pair_rep(w, _spin_rep(g))
-                perm = [bond[tuple(g @ r)] for r in spec.ff_R]
-                for q in range(spec.Nq):
-                    lhs = Y[qmap(q, g)][np.ix_(perm, range(Y.shape[2]), perm, range(Y.shape[4]))]
-                    rhs = np.einsum("ab,ibjc,dc->iajd", V, Y[q], V.conj())
-                    assert np.abs(lhs - rhs).max() < 1e-12 * scale, (w, g.tolist(), q)
-                    checked += 1
-            Vt = pair_rep(w, theta)
-            for q in range(spec.Nq):
-                rhs = np.einsum("ab,ibjc,dc->iajd", Vt, Y[q].conj(), Vt.conj())
-                assert np.abs(Y[qmap(q, -np.eye(2, dtype=int))] - rhs).max() < 1e-12 * scale, (w, q)
-    assert checked == 2 * 2 * len(_C4V) * spec.Nq
+        _check_covariance(spec, _expand_all(spec, o, o.loops(0.3, w)), w, reps, theta)
+        _check_covariance(spec, st[w], w, reps, theta)
+
+
+def test_point_group_and_time_reversal_t2g():
+    """The t2g model with atomic SOC: C4v acts on orbitals and spins, W_g = D_g (x) S_g (orbitals as polar
+    quadratic forms, spins as an axial vector), and time reversal is 1 (x) i sigma_y on the real orbitals.
+    Loops of both channels and two right-hand sides (at X = 0, where only the Kanamori vertex is projected,
+    and at the covariant state X1 = 0.2 dX/dT(X = 0)) at every momentum of a 5x5 mesh."""
+    spec = inputs.t2g_soc(seed=1, Lq=5, nc=1, n_ff=5, filling=4.0, T_mu=0.05)
+    o = oracle.Oracle(spec)
+    reps = [np.kron(_orbital_rep(g), _spin_rep(g)) for g in _C4V]
+    theta = np.kron(np.eye(3), 1j * _SY)
+    _check_setup(spec, o, reps, theta)
+    zero = np.zeros((2, spec.Nq, spec.M, spec.M), complex)
+    d1, _ = o.rhs(0.5, zero, 3)
+    d2, _ = o.rhs(0.4, 0.2 * d1, 3)
+    for w in (0, 1):
+        _check_covariance(spec, _expand_all(spec, o, o.loops(0.5, w)), w, reps, theta)
+        _check_covariance(spec, d1[w], w, reps, theta)
+        _check_covariance(spec, d2[w], w, reps, theta)
 
 
 # ---------------------------------------------------------------- momentum-shell regulator (Eq. def_lmp)
