@@ -146,7 +146,11 @@ typedef struct {
  * the fine mesh (Sec. 3.1; FP64), bisects mu if requested, builds the bond
  * and projection gather tables (Sec. 3.3) and allocates all work memory.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
- * Errors: TUFRG_EINVAL (bad descriptor, non-Hermitian H), TUFRG_ENOMEM, TUFRG_ECUDA. */
+ * Errors: TUFRG_EINVAL (bad descriptor, non-Hermitian H, bonds not distinct modulo Lq), TUFRG_ENOTSUP (n_s other
+ * than 2, 4, 6), TUFRG_ENOMEM, TUFRG_ECUDA.  Ownership: on success and on every failure after the model object was
+ * allocated, *out holds it (on failure with the message for tufrg_last_error and whatever device memory was already
+ * allocated); the caller releases it with tufrg_free in both cases.  *out is NULL only when out or desc is NULL
+ * or the host allocation of the object itself failed. */
 tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, tufrg_model **out);
 
 /* Release every resource of the model (NULL is ignored). */
