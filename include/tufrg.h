@@ -63,7 +63,8 @@ typedef enum {
     TUFRG_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
     TUFRG_EFALLBACK = 7,   /* surrogate rejected, direct loops used (informational) */
     TUFRG_ENOTSUP = 8,     /* configuration not supported by this build */
-    TUFRG_ETOOBIG = 9      /* problem larger than the fixed scratch of tufrg_loops_noalloc */
+    TUFRG_ETOOBIG = 9      /* problem larger than the fixed scratch of tufrg_loops_noalloc, or projection
+                              tables beyond 2^31 entries at init */
 } tufrg_status;
 
 /* TUFRG_FP64: every step in FP64.  TUFRG_SPLIT32: FP32 loop sums, FP32 Fourier transform and gathers,
@@ -147,7 +148,8 @@ typedef struct {
  * and projection gather tables (Sec. 3.3) and allocates all work memory.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: TUFRG_EINVAL (bad descriptor, non-Hermitian H, bonds not distinct modulo Lq), TUFRG_ENOTSUP (n_s other
- * than 2, 4, 6), TUFRG_ENOMEM, TUFRG_ECUDA.  Ownership: on success and on every failure after the model object was
+ * than 2, 4, 6), TUFRG_ETOOBIG (projection tables beyond 2^31 entries), TUFRG_ENOMEM, TUFRG_ECUDA,
+ * TUFRG_ETIMEOUT (a bounded device-side wait gave up while the products backends were timed).  Ownership: on success and on every failure after the model object was
  * allocated, *out holds it (on failure with the message for tufrg_last_error and whatever device memory was already
  * allocated); the caller releases it with tufrg_free in both cases.  *out is NULL only when out or desc is NULL
  * or the host allocation of the object itself failed. */
@@ -159,8 +161,12 @@ void tufrg_free(tufrg_model *m);
 /* Human-readable description of the last error on this model ("" if none). */
 const char *tufrg_last_error(const tufrg_model *m);
 
-/* Sizes: Nq, M, n_delta (loop bond differences), Nk and the chemical potential in use. */
-/* (tufrg_model_info below also reports the products backend chosen at init.) */
+/* Sizes: Nq, M, n_delta (loop bond differences), Nk and the chemical potential in use (host outputs).
+ * (tufrg_model_info below also reports the products backend chosen at init.)
+ * The host queries below (tufrg_dims, tufrg_model_info, tufrg_loop_momenta, tufrg_deltas,
+ * tufrg_gather_table) touch no device memory and return TUFRG_EINVAL for a NULL model; in tufrg_dims and
+ * tufrg_model_info any output may be NULL (not written), the others need theirs (tufrg_gather_table: h_out
+ * may be NULL to count only; channel must be 0 or 1 and cap >= 0, else TUFRG_EINVAL). */
 tufrg_status tufrg_dims(const tufrg_model *m, int *Nq, int *M, int *n_delta, int *Nk, double *mu);
 
 /* Products backend in use on the split path (TUFRG_PRODUCTS_TC or _SIMT; _SIMT for FP64 models)
@@ -208,19 +214,22 @@ tufrg_status tufrg_deltas(const tufrg_model *m, int *h_out);
  * D kinds.  Writes at most cap terms, returns the total count in *n_terms. */
 tufrg_status tufrg_gather_table(const tufrg_model *m, int channel, int *h_out, int cap, int *n_terms);
 
-/* Eigensystem on the fine mesh: d_E [Nk][n_s] doubles (ascending E, not shifted
- * by mu), d_U [Nk][n_s][n_s] complex, column l the eigenvector of E_l. */
+/* Eigensystem on the fine mesh (Sec. 3.1, Eq. trafo; computed in FP64 at init): d_E [Nk][n_s] doubles
+ * (ascending E, not shifted by mu), d_U [Nk][n_s][n_s] complex, column l the eigenvector of E_l.
+ * Errors: TUFRG_EINVAL (NULL argument), TUFRG_ECUDA. */
 tufrg_status tufrg_bands(tufrg_model *m, double *d_E, double *d_U);
 
 /* Compact loops d/dT F at temperature T (Eqs. loopminus, loopplus, loop_orbital,
  * fine-mesh direct k-sum).  d_loops: [2][Nq][n_delta][n_s^2][n_s^2] complex; the
- * channels not in channel_mask are left untouched. */
+ * channels not in channel_mask are left untouched.  Errors: TUFRG_EINVAL (NULL argument, T not positive
+ * and finite, channel_mask not a subset of P|C), TUFRG_ECUDA. */
 tufrg_status tufrg_loops(tufrg_model *m, double T, int channel_mask, void *d_loops);
 
 /* Projected vertices A_P(s), A_C(u) of a state (Eq. sum_P, Eq. proj_PD, the
  * D->P gather, the P->C gather, Eq. proj_DC).  d_state, d_Ahat: [2][Nq][M][M]
  * complex.  A channel outside channel_mask is treated as zero and its A is
- * zero-filled.  *h_amax (may be NULL) receives max |A| (synchronises). */
+ * zero-filled.  *h_amax (may be NULL) receives max |A| (synchronises).
+ * Errors: TUFRG_EINVAL (NULL argument, channel_mask not a subset of P|C), TUFRG_ECUDA. */
 tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask, void *d_Ahat,
                            double *h_amax);
 
@@ -231,12 +240,14 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
  * symmetries (X(G q) = W X(q) W^dagger, W the bond permutation times the orbital-pair map of the symmetry;
  * every state of a flow from X = 0 has them when the bare vertex does), and projections and products then
  * run for the orbit representatives only, the other momenta being written from them.  For a state without
- * those symmetries the result is wrong; the flag is ignored when the model has no usable symmetry. */
+ * those symmetries the result is wrong; the flag is ignored when the model has no usable symmetry.
+ * Errors: TUFRG_EINVAL (NULL argument, T not positive and finite, bad channel_mask), TUFRG_ECUDA. */
 enum { TUFRG_SYMMETRIC_STATE = 4 };
 tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate);
 
 /* Same right-hand side with host buffers: copies h_state to the device, evaluates,
- * copies dX/dT back into h_dstate and synchronises the stream. */
+ * copies dX/dT back into h_dstate and synchronises the stream.  Errors: those of tufrg_rhs, and
+ * TUFRG_ETIMEOUT when a bounded device-side wait gave up (the device error flag is read after the sync). */
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate);
 
 /* n right-hand sides from and to host memory with the transfers overlapped: step i reads the state at
@@ -253,8 +264,12 @@ tufrg_status tufrg_rhs_host_batch(tufrg_model *m, int n, const double *T, const 
  * max|A| > opts->stop.  The Dormand-Prince controller runs on the device: one attempt
  * (six stage right-hand sides, error norm, accept/reject, FSAL commit) is captured once as
  * a CUDA graph and replayed; the host only polls the controller state between attempts.
- * d_state_out (may be NULL): [2][Nq][M][M] complex, the last accepted state.
- * Errors: TUFRG_ENONFINITE, TUFRG_ENOTCONV, TUFRG_ETIMEOUT, ... */
+ * d_state_out (may be NULL): [2][Nq][M][M] complex, the last accepted state.  *res (and d_state_out) are
+ * filled on success and on TUFRG_ENOTCONV / TUFRG_ENONFINITE (the state reached so far).
+ * Errors: TUFRG_EINVAL (NULL argument, not T0 > T_end > 0, rtol <= 0, atol < 0, h0 >= 0, channel_mask
+ * empty or beyond P|C, max_steps < 1), TUFRG_ENOTCONV (step limit reached or step size underflow),
+ * TUFRG_ENONFINITE (non-finite right-hand side or error norm), TUFRG_ETIMEOUT (a bounded device-side wait
+ * gave up), TUFRG_ECUDA. */
 tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_state_out, tufrg_flow_result *res);
 
 /* Loop k-sum that allocates nothing (no counterpart in the paper; an interface addition).
