@@ -13,6 +13,47 @@ def _bf16(x):
     return r.astype(np.uint32).view(np.float32)
 
 
+def leading_form_factor(ff_R, n_s, A):
+    """Form-factor content of the leading instability: the eigenspace of the projected vertex A_X(q*) (M x M,
+    rows (R, pair)) of the eigenvalue of largest modulus (eigenvalues within 1% of it; with time reversal and
+    C4v it is often degenerate, so single eigenvectors are not unique), its weight per bond
+    w_R = (1/d) sum_{v in the space} sum_pair |v_(R,pair)|^2, and the bond shell (|R|^2 class: onsite, nearest,
+    next-nearest, ...) holding the largest weight."""
+    lam, vec = np.linalg.eigh(A)
+    top = lam[np.argmax(np.abs(lam))]
+    V = vec[:, np.abs(lam - top) <= 1e-2 * abs(top)]
+    w = (np.abs(V) ** 2).sum(axis=1).reshape(len(ff_R), n_s * n_s).sum(axis=1) / V.shape[1]
+    r2 = np.array([int(r[0]) ** 2 + int(r[1]) ** 2 for r in ff_R])
+    shells = sorted(set(r2.tolist()))
+    per_shell = np.array([w[r2 == s].sum() for s in shells])
+    return shells[int(np.argmax(per_shell))], w
+
+
+def test_leading_form_factor_of_a_planted_vertex():
+    """The helper on vertices with a known leading eigenspace: a d pattern on the four nearest bonds, an onsite
+    and a next-nearest one, each over a background of smaller eigenvalues, and a doubly degenerate leading pair
+    (p_x, p_y on the nearest bonds) whose eigenspace weights do not depend on the basis inside it."""
+    ff_R = np.array([(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (1, -1), (-1, 1), (-1, -1)])
+    ns, M = 2, 9 * 4
+    rng = np.random.default_rng(4)
+    B = rng.normal(size=(M, M)) + 1j * rng.normal(size=(M, M))
+    B = 0.05 * (B + B.conj().T) / np.sqrt(M)
+    for pattern, shell in (((0, 1, -1, 1, -1, 0, 0, 0, 0), 1), ((1, 0, 0, 0, 0, 0, 0, 0, 0), 0),
+                           ((0, 0, 0, 0, 0, 1, 1, 1, 1), 2)):
+        v = np.kron(np.array(pattern, float), np.array([0, 1, -1, 0]) / np.sqrt(2))
+        v /= np.linalg.norm(v)
+        A = B - 3.0 * np.outer(v, v)                       # an attractive leading eigenvalue
+        got, w = leading_form_factor(ff_R, ns, A)
+        assert got == shell
+        assert np.allclose(w, np.array(pattern, float) ** 2 / np.sum(np.array(pattern, float) ** 2), atol=0.02)
+    px = np.kron(np.array((0, 1, -1, 0, 0, 0, 0, 0, 0), float), np.array([1, 0, 0, 0])) / np.sqrt(2)
+    py = np.kron(np.array((0, 0, 0, 1, -1, 0, 0, 0, 0), float), np.array([0, 0, 0, 1])) / np.sqrt(2)
+    for c, s in ((1.0, 0.0), (0.6, 0.8)):                  # two bases of the same degenerate pair
+        a, b = c * px + s * py, -s * px + c * py
+        got, w = leading_form_factor(ff_R, ns, B - 3.0 * (np.outer(a, a) + np.outer(b, b)))
+        assert got == 1 and np.allclose(w, [0, 0.25, 0.25, 0.25, 0.25, 0, 0, 0, 0], atol=0.02)
+
+
 def test_cpu_network_gradient_vs_finite_differences():
     """The FP64 reference network's backward pass against central differences (relative 1e-7)."""
     rng = np.random.default_rng(0)
@@ -143,7 +184,9 @@ def test_surrogate_trained_on_the_family_inside_a_flow(gpu):
     error is at the percent level), the surrogate switches off and the flow is the direct flow exactly;
     the cost is the one network evaluation plus device-side early exits.  At tolerance 0.1 the network
     serves the high-temperature stretch; the figures (critical scale, evaluations, wall time) are
-    printed, the critical scale must stay within 2% with the same leading channel and transfer momentum."""
+    printed, the critical scale must stay within 2% with the same leading channel, transfer momentum and form
+    factor (the bond shell carrying most of the leading eigenvector of the projected vertex, per-bond weights
+    within 0.05)."""
     from paper_1710_08830_gb300 import inputs, surrogate
     from paper_1710_08830_gb300.api import PRODUCTS_SIMT, SPLIT32, Model
     train = surrogate.generate(200_000, seed=1)
@@ -164,6 +207,13 @@ def test_surrogate_trained_on_the_family_inside_a_flow(gpu):
     y0, r0 = direct.flow(stop=stop)
     assert r0["crossed"]
     print(f"direct: Tc {r0['Tc']:.5f}, {r0['n_rhs']} evaluations, {r0['wall_s'] * 1e3:.1f} ms")
+
+    def form_factor(model, y, r):
+        A, _ = model.project(y, want_max=False)
+        return leading_form_factor(spec.ff_R, spec.n_s, A[r["lead_channel"], r["lead_q"]].cpu().numpy())
+
+    ff0, w0 = form_factor(direct, y0, r0)
+    print(f"direct: leading form factor shell |R|^2 = {ff0}, bond weights {np.round(w0, 3).tolist()}")
     for tol in (1e-3, 1e-1):
         m = Model(spec, SPLIT32, products=PRODUCTS_SIMT)
         surrogate.attach(m, tr, alpha, tp, mu, tol=tol)
@@ -176,6 +226,8 @@ def test_surrogate_trained_on_the_family_inside_a_flow(gpu):
               f"kept {acc}, rejected {rej}, skipped {skip}")
         assert r1["crossed"] and r1["lead_channel"] == r0["lead_channel"] and r1["lead_q"] == r0["lead_q"]
         assert abs(r1["Tc"] / r0["Tc"] - 1) < 0.02
+        ff1, w1 = form_factor(m, y1, r1)
+        assert ff1 == ff0 and np.abs(w1 - w0).max() < 0.05, (ff1, w1, w0)
         if tol == 1e-3:
             assert (acc, rej, skip) == (0, 1, r1["n_rhs"] - 1)
             assert torch.equal(y0, y1) and r1["Tc"] == r0["Tc"]
