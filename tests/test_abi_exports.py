@@ -89,3 +89,20 @@ def test_bad_descriptors_are_rejected_before_device_use(libpath):
     bad[0] *= 2.0   # breaks t_{-R} = t_R^dagger
     st, msg = init(spec.ff_R, hop_t=bad.ctypes.data)
     assert st == 1 and "Hermitian" in msg
+    # every remaining check of the descriptor, each before the first CUDA call
+    EINVAL, ENOTSUP = 1, 8
+    cases = [
+        (dict(n_s=0), EINVAL, "n_s"), (dict(n_s=9), EINVAL, "n_s"), (dict(n_s=3), ENOTSUP, "n_s = 2, 4, 6"),
+        (dict(n_hop=0), EINVAL, "hopping"), (dict(V0=None), EINVAL, "V0"), (dict(n_ff=0), EINVAL, "bond set"),
+        (dict(nc=0), EINVAL, "Lq >= 2"), (dict(Lq=64, nc=65), EINVAL, "fine mesh"),
+        (dict(products=9), EINVAL, "products"), (dict(filling=0.5, T_mu=0.0), EINVAL, "T_mu"),
+        (dict(regulator=7), EINVAL, "regulator"), (dict(regulator=1, T_reg=0.0), EINVAL, "T_reg"),
+        (dict(regulator=1, T_reg=float("nan")), EINVAL, "T_reg"),
+        (dict(n_hop=hopR.shape[0] - 1), EINVAL, "t_{-R}"),      # the last hop loses its partner
+    ]
+    for kw, want, text in cases:
+        st, msg = init(spec.ff_R, **kw)
+        assert st == want and text in msg, (kw, st, msg)
+    # the largest fine mesh (Lq nc = 4096) passes the size check and stops at the next one
+    st, msg = init(spec.ff_R, Lq=64, nc=64, precision=7)
+    assert st == EINVAL and "precision" in msg
