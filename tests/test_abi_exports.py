@@ -52,6 +52,32 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.tufrg_dims(None, None, None, None, None, None) == 1
     assert L.tufrg_rhs(None, 1.0, None, 3, None) == 1
     assert L.tufrg_last_error(None) == b"model handle is NULL"
+    # every other entry point taking a model or network handle, and the NULL-buffer cases of the free functions
+    i, d = ctypes.c_int(), ctypes.c_double()
+    ll = ctypes.c_longlong()
+    calls = {
+        "tufrg_model_info": (None, None, None, None), "tufrg_loop_momenta": (None, ctypes.byref(i)),
+        "tufrg_symmetry_info": (None, ctypes.byref(i), ctypes.byref(d), ctypes.byref(d)),
+        "tufrg_deltas": (None, None), "tufrg_gather_table": (None, 0, None, 0, ctypes.byref(i)),
+        "tufrg_bands": (None, None, None), "tufrg_loops": (None, 1.0, 3, None),
+        "tufrg_project": (None, None, 3, None, None), "tufrg_rhs_host": (None, 1.0, None, 3, None),
+        "tufrg_rhs_host_batch": (None, 0, None, None, 3, None), "tufrg_band_basis": (None, None, None),
+        "tufrg_flow": (None, None, None, None), "tufrg_flow_batch": (None, 1, None, None),
+        "tufrg_set_surrogate": (None, None, None, None, None, 1e-3, 0, None),
+        "tufrg_surrogate_stats": (None, ctypes.byref(ll), ctypes.byref(ll), ctypes.byref(ll)),
+        "tufrg_timing_begin": (None,), "tufrg_timing_end": (None, None, 0, None, None),
+        "tufrg_mlp_create": (4, 8, 1, 2, 0, None, None), "tufrg_mlp_get_params": (None, None),
+        "tufrg_mlp_set_params": (None, None), "tufrg_mlp_forward": (None, None, 1, None),
+        "tufrg_mlp_gradients": (None, None, None, 1, None, None), "tufrg_mlp_train_step": (None, None, None, 1, 1e-3, None),
+        "tufrg_round_f32": (None, None, 5, None),
+        "tufrg_loops_noalloc": (4, 2, None, None, 0.0, 0.1, 5, None, 3, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == 1, name                # TUFRG_EINVAL
+    assert L.tufrg_mlp_num_params(None) == -1
+    assert L.tufrg_mlp_last_error(None) == b"network handle is NULL"
+    L.tufrg_free(None)
+    L.tufrg_mlp_free(None)
 
 
 def test_bad_descriptors_are_rejected_before_device_use(libpath):
