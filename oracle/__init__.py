@@ -22,17 +22,26 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tufrg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# The mutation test (tests/test_oracle_mutants.py) compiles copies of the oracle with one planted mistake
+# each and runs the pin tests against them in a subprocess with this variable naming the copy; nothing
+# else sets it.
+MUTANT_ENV = "TUFRG_ORACLE_MUTANT_LIB"
 _lock = threading.Lock()
 _lib = None
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 -fopenmp (no -march) of one oracle source file into the shared library out."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (OpenMP, -O2, no -march)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 
@@ -57,8 +66,8 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            path = os.environ.get(MUTANT_ENV) or build()
+            L = C.CDLL(path)
             vp, d, i = C.c_void_p, C.c_double, C.c_int
             L.or_eigh.argtypes = [i, vp, vp, vp]
             L.or_bands.argtypes = [vp, vp, vp]

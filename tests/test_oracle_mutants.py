@@ -1,0 +1,91 @@
+"""Mutation test of the oracle's pins: each case plants one plausible mistake in a copy of the oracle's C
+source (a dropped term, a wrong sign, a wrong index or momentum, a transposed or wrongly conjugated operand, a
+mistyped integrator coefficient), compiles the copy, and runs the pin tests of tests/test_oracle_pins.py against it in
+a subprocess.  At least one pin must fail for every mutant, and all of them must pass for an unmodified copy
+built the same way (the control).  The mistakes are planted on the CPU only; the oracle itself is untouched.
+
+The two truncated-projection pins (about a minute together) are left out of these runs; every mutant below is
+caught by a faster pin."""
+import importlib.util
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# name -> (text in the oracle, replacement): one plausible mistake each
+MUTANTS = {
+    # Eq. loop_orbital: the projector of the first pair transposed, U*_{t1} U_{t3} for U_{t1} U*_{t3}
+    "projector_transposed": ("cplx left = U1[t1 * ns + l1] * conj(U1[t3 * ns + l1]);",
+                             "cplx left = U1[t3 * ns + l1] * conj(U1[t1 * ns + l1]);"),
+    # Eq. loopplus in the orbital basis: the conjugation on the wrong eigenvector of the second pair
+    "crossed_pair_conjugation": ("conj(U2[t2 * ns + l2]) * U2[t4 * ns + l2]",
+                                 "U2[t2 * ns + l2] * conj(U2[t4 * ns + l2])"),
+    # Eq. loopminus: the partner momentum s + q instead of s - q
+    "pp_momentum_sign": ("k1 = imod(sx - qx, Lf) * Lf + imod(sy - qy, Lf);",
+                         "k1 = imod(sx + qx, Lf) * Lf + imod(sy + qy, Lf);"),
+    # form factors: e^{+iq.(R1-R2)} in the loop k-sum
+    "loop_phase_sign": ("= conj(lattice_phase((long)qx * dl[2 * d] + (long)qy * dl[2 * d + 1], Lf));",
+                        "= lattice_phase((long)qx * dl[2 * d] + (long)qy * dl[2 * d + 1], Lf);"),
+    # Eq. disc_2a: the degenerate branch of d/dT F^- with the wrong sign
+    "pp_degenerate_sign": ("return -0.5 * (gp1 + gp2);", "return 0.5 * (gp1 + gp2);"),
+    # Eq. disc_2b: the divided difference of d/dT F^+ reversed
+    "ph_difference_order": ("if (fabs(d) > OR_DEGEN * T) return (g1 - g2) / d;",
+                            "if (fabs(d) > OR_DEGEN * T) return (g2 - g1) / d;"),
+    # d g / d e: a dropped term of the derivative of the Fermi weight
+    "fermi_derivative_term": ("*gp = h / (T * T) * (1.0 - ax * (1.0 - z) / (1.0 + z));", "*gp = h / (T * T);"),
+    # Sec. 3.3: the Fourier transform of the exchange propagators with the wrong sign
+    "fourier_sign": ("cplx ph = lattice_phase((long)(u / Lq) * Rx + (long)(u % Lq) * Ry, Lq);",
+                     "cplx ph = lattice_phase(-((long)(u / Lq) * Rx + (long)(u % Lq) * Ry), Lq);"),
+    # the D -> P gather (second term of Eq. proj_PD's family) dropped
+    "dropped_D_to_P": ("val -= ph2 * Cr[(size_t)k * M2 + sr * M + sc];", "(void)ph2;"),
+    # the P -> C gather with the legs 3 and 4 of the source exchanged
+    "P_to_C_legs": ("size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s4 * ns + s3;",
+                    "size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s3 * ns + s4;"),
+    # the bare vertex projected with legs 3 and 4 exchanged (its sign flipped, V0 being antisymmetric)
+    "bare_vertex_legs": ("V0[((s1 * ns + s2) * ns + s3) * ns + s4]", "V0[((s1 * ns + s2) * ns + s4) * ns + s3]"),
+    # Eq. RGE_spin / the C equation: c_C = 1 instead of 2
+    "crossed_prefactor": ("double cx = (ch == 0) ? 1.0 : 2.0;", "double cx = 1.0;"),
+    # a Dormand-Prince stage time mistyped (c_3 = 3/11 for 3/10): the integrator loses its order
+    "dp45_stage_time": ("DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10,", "DP_C[7] = {0.0, 1.0 / 5, 3.0 / 11,"),
+}
+# (A mistyped 5th-order weight b_1 is caught as well, but only after the step controller, whose error
+# estimate no longer shrinks with the step, has spent minutes on the first adaptive flow.)
+
+
+def _run_pins(tmp_path, src_text):
+    src = tmp_path / "oracle_copy.c"
+    src.write_text(src_text)
+    so = oracle.compile_source(str(src), str(tmp_path / "liboracle_copy.so"))
+    env = dict(os.environ, **{oracle.MUTANT_ENV: so})
+    args = [sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider", "-k", "not truncated_projections"]
+    if importlib.util.find_spec("pytest_timeout"):
+        args += ["--timeout", "120"]   # a pin that a mutant slows beyond this fails as well
+    return subprocess.run(args, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
+
+
+def _source():
+    with open(oracle._SRC) as f:
+        return f.read()
+
+
+def test_control_copy_passes_the_pins(tmp_path):
+    r = _run_pins(tmp_path, _source())
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, name
+    r = _run_pins(tmp_path, src.replace(old, new))
+    assert r.returncode == 1, (name, r.returncode, r.stdout[-3000:])   # 1: a test failed
+    failed = [ln for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
+    assert failed, r.stdout[-3000:]
+    print(f"{name}: caught by {failed[0].split()[1]}")
