@@ -7,8 +7,9 @@
 //
 // For fixed (s, q) the orbital dressing is the rank-N_s product Y = A B with A[(t1t3)][l] = rho1 and
 // B[l][(t2t4)] = T, an N_s^2 x N_s^2 complex matrix.  One CTA owns one transfer momentum; it walks the fine
-// mesh column by column; for each batch of KB rows it stages A and B of those k-points in shared memory
-// (all threads cooperate: projectors, pair weights, T), then every thread updates its TA x TB tile of
+// mesh column by column in batches of KB rows.  The raw eigenvectors and Fermi entries of a batch arrive in
+// shared memory by cp.async while the batch before it is multiplied (two buffers); from them all threads
+// form A and B of the batch (projectors, pair weights, T), then every thread updates its TA x TB tile of
 //     W[dy][(t1t3),(t2t4)] += e^{-i ky dy} Y(k)
 // for the non-negative dy of the bond differences.  At the end of a column the thread adds
 // e^{-i kx dx} W into the FP64 accumulator of its own entries (no other CTA touches this s, so no
