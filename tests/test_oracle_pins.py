@@ -619,6 +619,43 @@ def test_band_basis_transformation_is_unitary_with_the_complete_set():
     assert np.abs(out - eye).max() < 1e-12
 
 
+def test_form_factor_convergence_orbital_vs_band_basis():
+    """Sec. 3.4: the form-factor expansion converges faster in the orbital basis than in the band basis.  The
+    local particle-particle propagator of the ladder (Eq. sol_spin: R = R' = 0 only) is captured completely by the
+    onsite bond in the orbital basis; transformed to the band basis (Eq. mat_trafo_P, the paper's gauge, complete
+    set of a 6x6 torus, so no weight is lost) it spreads over many bond shells.  Captured weight
+    sum_{|R|^2, |R'|^2 <= r} |P^{RR'}|^2 / sum |P|^2 per cut r: the orbital basis is at 1 from r = 0, the band basis
+    below 1e-2 at r = 0, below 0.9 with the nearest bonds and below 0.95 up to |R|^2 = 5, reaching 1 only with
+    the complete set."""
+    L = 6
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=L, nc=1).with_(ff_R=inputs.ff_complete(L))
+    o = oracle.Oracle(spec)
+    Ub, _ = _schober_gauge(spec)
+    ns, M, Nq = 2, spec.M, spec.Nq
+    A = _pair_structure(ns)
+    st = np.zeros((2, Nq, M, M), complex)
+    for s1 in range(ns):
+        for s2 in range(ns):
+            for s3 in range(ns):
+                for s4 in range(ns):
+                    st[0, :, s1 * ns + s2, s4 * ns + s3] = -0.5 * A[s1, s2, s3, s4]
+    band = o.band_transform(Ub, st)[0]
+    r2 = np.repeat([int(r[0]) ** 2 + int(r[1]) ** 2 for r in spec.ff_R], ns * ns)   # |R|^2 per row / column
+    cuts = sorted(set(r2.tolist()))
+
+    def captured(X):
+        W = np.abs(X) ** 2
+        return np.array([W[:, r2 <= c][:, :, r2 <= c].sum() for c in cuts]) / W.sum()
+
+    orb, bnd = captured(st[0]), captured(band)
+    print("\n|R|^2 cut, captured weight orbital / band: " +
+          ", ".join(f"{c}: {a:.4f} / {b:.4f}" for c, a, b in zip(cuts, orb, bnd)))
+    assert np.abs(band).max() > 0 and abs((np.abs(band) ** 2).sum() / (np.abs(st[0]) ** 2).sum() - 1) < 1e-12
+    assert np.all(orb == 1.0)
+    assert bnd[0] < 1e-2 and bnd[1] < 0.9 and bnd[cuts.index(5)] < 0.95
+    assert np.all(np.diff(bnd) >= -1e-15) and abs(bnd[-1] - 1) < 1e-12
+
+
 def test_band_basis_maps_orbital_loops_to_band_diagonal_loops():
     """Eq. loop_orbital is exact with the complete form-factor set: the transformation maps the orbital loop matrices
     (the oracle's direct k-sums with the U dressing, pinned above against the brute-force fRG) onto the band-basis
