@@ -6,6 +6,7 @@ built the same way (the control).  The mistakes are planted on the CPU only; the
 
 The two truncated-projection pins (about a minute together) are left out of these runs; every mutant below is
 caught by a faster pin."""
+import concurrent.futures
 import importlib.util
 import os
 import subprocess
@@ -53,38 +54,66 @@ MUTANTS = {
     "crossed_prefactor": ("double cx = (ch == 0) ? 1.0 : 2.0;", "double cx = 1.0;"),
     # a Dormand-Prince stage time mistyped (c_3 = 3/11 for 3/10): the integrator loses its order
     "dp45_stage_time": ("DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10,", "DP_C[7] = {0.0, 1.0 / 5, 3.0 / 11,"),
+    # the Fermi function's two branches exchanged (1 - f for f)
+    "fermi_branches": ("return e > 0 ? z / (1.0 + z) : 1.0 / (1.0 + z);", "return e > 0 ? 1.0 / (1.0 + z) : z / (1.0 + z);"),
+    # Eq. def_lmp with the momentum shell: the product rule of d/dLambda [chi chi] shortened to one doubled term
+    "shell_product_rule": ("(or_dchi(e1, lam) * or_chi(e2, lam) + or_chi(e1, lam) * or_dchi(e2, lam)) * or_Fm(e1, e2, T)",
+                           "2.0 * or_dchi(e1, lam) * or_chi(e2, lam) * or_Fm(e1, e2, T)"),
+    # d chi / d Lambda with the wrong sign
+    "shell_dchi_sign": ("return -2.0 * lam * e * e / (d * d);", "return 2.0 * lam * e * e / (d * d);"),
+    # Eq. mat_trafo_P: the orbital indices of the two eigenvectors exchanged
+    "band_P_pair_swap": ("Ub[(size_t)k2 * ns2 + b * ns + d] * Ub[(size_t)k * ns2 + a * ns + c]",
+                         "Ub[(size_t)k2 * ns2 + a * ns + d] * Ub[(size_t)k * ns2 + b * ns + c]"),
+    # Eq. mat_trafo_D: the conjugation of the second eigenvector dropped
+    "band_C_conjugation": ("Ub[(size_t)k * ns2 + a * ns + c] * conj(Ub[(size_t)k2 * ns2 + b * ns + d])",
+                           "Ub[(size_t)k * ns2 + a * ns + c] * Ub[(size_t)k2 * ns2 + b * ns + d]"),
+    # the band-basis transformation T^T X T instead of T^dagger X T
+    "band_transpose_for_adjoint": ("acc += conj(T[(size_t)j * M + r]) * W[(size_t)j * M + c];",
+                                   "acc += T[(size_t)j * M + r] * W[(size_t)j * M + c];"),
 }
 # (A mistyped 5th-order weight b_1 is caught as well, but only after the step controller, whose error
 # estimate no longer shrinks with the step, has spent minutes on the first adaptive flow.)
 
 
-def _run_pins(tmp_path, src_text):
-    src = tmp_path / "oracle_copy.c"
-    src.write_text(src_text)
-    so = oracle.compile_source(str(src), str(tmp_path / "liboracle_copy.so"))
-    env = dict(os.environ, **{oracle.MUTANT_ENV: so})
+def _run_pins(work, name, src_text):
+    """Compile one copy of the oracle and run the pins against it (two OpenMP threads per copy)."""
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, f"{name}.c")
+    with open(src, "w") as f:
+        f.write(src_text)
+    so = oracle.compile_source(src, os.path.join(work, f"lib{name}.so"))
+    env = dict(os.environ, **{oracle.MUTANT_ENV: so, "OMP_NUM_THREADS": "2"})
     args = [sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider", "-k", "not truncated_projections"]
     if importlib.util.find_spec("pytest_timeout"):
         args += ["--timeout", "120"]   # a pin that a mutant slows beyond this fails as well
     return subprocess.run(args, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
 
 
-def _source():
+@pytest.fixture(scope="module")
+def runs(tmp_path_factory):
+    """The control and every mutant, run concurrently: name -> CompletedProcess."""
     with open(oracle._SRC) as f:
-        return f.read()
+        src = f.read()
+    texts = {"control": src}
+    # the integrator mutant runs longest (its adaptive flows take many steps before the pin fails): start it first
+    for name, (old, new) in sorted(MUTANTS.items(), key=lambda kv: kv[0] != "dp45_stage_time"):
+        assert src.count(old) == 1, name
+        texts[name] = src.replace(old, new)
+    work = str(tmp_path_factory.mktemp("oracle_mutants"))
+    workers = max(1, min(len(texts), (os.cpu_count() or 2) // 2))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        futs = {n: ex.submit(_run_pins, work, n, t) for n, t in texts.items()}
+        return {n: f.result() for n, f in futs.items()}
 
 
-def test_control_copy_passes_the_pins(tmp_path):
-    r = _run_pins(tmp_path, _source())
+def test_control_copy_passes_the_pins(runs):
+    r = runs["control"]
     assert r.returncode == 0, r.stdout[-3000:]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_fails_a_pin(tmp_path, name):
-    old, new = MUTANTS[name]
-    src = _source()
-    assert src.count(old) == 1, name
-    r = _run_pins(tmp_path, src.replace(old, new))
+def test_planted_mistake_fails_a_pin(runs, name):
+    r = runs[name]
     assert r.returncode == 1, (name, r.returncode, r.stdout[-3000:])   # 1: a test failed
     failed = [ln for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
     assert failed, r.stdout[-3000:]
