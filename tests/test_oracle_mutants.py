@@ -4,7 +4,7 @@ mistyped integrator coefficient), compiles the copy, and runs the pin tests of t
 a subprocess.  At least one pin must fail for every mutant, and all of them must pass for an unmodified copy
 built the same way (the control).  The mistakes are planted on the CPU only; the oracle itself is untouched.
 
-The two truncated-projection pins (about a minute together) are left out of these runs; every mutant below is
+The two truncated-projection pins (about 20 s together) are left out of these runs; every mutant below is
 caught by a faster pin."""
 import concurrent.futures
 import importlib.util

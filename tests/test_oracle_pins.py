@@ -165,12 +165,13 @@ def test_flow_equals_full_momentum_flow():
     assert np.abs(V_bf - spec.V0[None, None, None]).max() > 1e-2   # the flow did something
 
 
-@pytest.mark.parametrize("nff", [5, 9])
-def test_truncated_projections_vs_double_k_sums(nff):
+@pytest.mark.parametrize("Lq,nff", [(8, 5), (6, 9)])
+def test_truncated_projections_vs_double_k_sums(Lq, nff):
     """Eq. proj_PD and the D->P, P->C, D->C gathers against the defining double
     k-sums (Eq. def_P and analogues) for exchange propagators supported on a
-    truncated bond set (8x8 coarse mesh)."""
-    spec = inputs.rashba_hubbard(Lq=8, nc=1, n_ff=nff, mu=-0.8)
+    truncated bond set (8x8 and 6x6 coarse meshes; on the 6x6 torus shifted bonds
+    with |x| = 3 wrap, so the modular R'' arithmetic is exercised too)."""
+    spec = inputs.rashba_hubbard(Lq=Lq, nc=1, n_ff=nff, mu=-0.8)
     o = oracle.Oracle(spec)
     bf = bruteforce.Torus(spec, o.mu)
     st = inputs.random_state(spec, seed=11, hermitian=False)
