@@ -333,7 +333,8 @@ def test_hermiticity_of_loops_and_flow():
 
 
 def test_su2_relations_without_soc():
-    """Zero SOC: X_{uuuu} = X_{udud} + X_{uddu}, spin conservation and up/down symmetry."""
+    """Zero SOC: X_{uuuu} = X_{udud} + X_{uddu}, spin conservation, up/down symmetry, and the decoupling of
+    singlet and triplet pairs (P) and of charge and spin (C)."""
     spec = inputs.hubbard_square(tp=-0.25, U=3.0, Lq=4, nc=2, filling=0.0, mu=-0.7)
     o = oracle.Oracle(spec)
     st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
@@ -352,6 +353,18 @@ def test_su2_relations_without_soc():
                         if a + b != c + d:
                             assert np.abs(X(a, b, c, d)).max() < 1e-13
     assert np.abs(Pt(0, 1, 0, 1)).max() > 1e-3 and np.abs(Ct(0, 1, 0, 1)).max() > 1e-3
+    # singlet and triplet pairs decouple in P; charge and spin decouple in C.  Pair index (a, b) = 2 a + b over
+    # (up, down); P rows carry (s1, s2) and columns (s4, s3), C rows (s1, s3) and columns (s4, s2).
+    r = 1 / np.sqrt(2)
+    pp = np.array([[0, r, -r, 0],                       # singlet (ud - du) / sqrt 2
+                   [1, 0, 0, 0], [0, r, r, 0], [0, 0, 0, 1]])   # triplets uu, (ud + du) / sqrt 2, dd
+    ph = np.array([[r, 0, 0, r],                        # charge (uu + dd) / sqrt 2
+                   [r, 0, 0, -r], [0, 1, 0, 0], [0, 0, 1, 0]])  # spin: (uu - dd) / sqrt 2, ud, du
+    for X, B in ((st[0], pp), (st[1], ph)):
+        Bf = np.kron(np.eye(nff), B)
+        Y = (Bf @ X @ Bf.conj().T).reshape(spec.Nq, nff, 4, nff, 4)
+        assert np.abs(Y[:, :, 0, :, 1:]).max() < 1e-13 and np.abs(Y[:, :, 1:, :, 0]).max() < 1e-13
+        assert np.abs(Y[:, :, 0, :, 0]).max() > 1e-3 and np.abs(Y[:, :, 1:, :, 1:]).max() > 1e-3
 
 
 # The square-lattice point group C4v as integer matrices acting on (x, y): the four rotations, then the four mirrors.
