@@ -54,6 +54,8 @@ MUTANTS = {
     "crossed_prefactor": ("double cx = (ch == 0) ? 1.0 : 2.0;", "double cx = 1.0;"),
     # a Dormand-Prince stage time mistyped (c_3 = 3/11 for 3/10): the integrator loses its order
     "dp45_stage_time": ("DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10,", "DP_C[7] = {0.0, 1.0 / 5, 3.0 / 11,"),
+    # the density n(mu) with the sign of mu flipped (the bisection then hits the filling at -mu)
+    "density_mu_sign": ("s += fermi(E[(size_t)k * ns + l] - mu, T);", "s += fermi(E[(size_t)k * ns + l] + mu, T);"),
     # the Fermi function's two branches exchanged (1 - f for f)
     "fermi_branches": ("return e > 0 ? z / (1.0 + z) : 1.0 / (1.0 + z);", "return e > 0 ? 1.0 / (1.0 + z) : z / (1.0 + z);"),
     # Eq. def_lmp with the momentum shell: the product rule of d/dLambda [chi chi] shortened to one doubled term

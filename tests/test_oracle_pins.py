@@ -120,9 +120,23 @@ def test_form_factor_orthonormality(L, nff):
 
 
 def test_mu_bisection_hits_filling():
-    spec = inputs.hubbard_square(Lq=4, nc=4, filling=0.9, T_mu=0.05)
-    o = oracle.Oracle(spec)
-    assert abs(o.density(o.mu, 0.05) - 0.9) < 1e-13
+    """mu by bisection of the filling (reading R11), checked with a density computed here from numpy's eigenvalues
+    of H(k) and the logistic form of f, n(mu) = (1/Nk) sum_{k,l} 1/(1 + e^{(E_l(k) - mu)/T}); also for the t2g
+    model at 4 electrons in 6 states."""
+    from scipy.special import expit
+    for spec in (inputs.hubbard_square(Lq=4, nc=4, filling=0.9, T_mu=0.05),
+                 inputs.t2g_soc(seed=2, Lq=4, nc=2, n_ff=1, filling=4.0, T_mu=0.05)):
+        o = oracle.Oracle(spec)
+        L = spec.Lf
+        kx, ky = np.divmod(np.arange(spec.Nk), L)
+        H = np.zeros((spec.Nk, spec.n_s, spec.n_s), complex)
+        for R, t in zip(spec.hop_R, spec.hop_t):
+            H += np.exp(2j * np.pi * (kx * R[0] + ky * R[1]) / L)[:, None, None] * t
+        E = np.linalg.eigvalsh(H)
+        n = lambda mu: float(expit(-(E - mu) / spec.T_mu).sum(axis=1).mean())
+        assert abs(n(o.mu) - spec.filling) < 1e-12
+        for mu in (o.mu - 0.3, o.mu + 0.2):
+            assert abs(o.density(mu, spec.T_mu) - n(mu)) < 1e-12
 
 
 # ---------------------------------------------------------------- brute-force exactness (Secs. 3.1-3.3)
