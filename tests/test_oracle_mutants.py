@@ -54,6 +54,12 @@ MUTANTS = {
     "crossed_prefactor": ("double cx = (ch == 0) ? 1.0 : 2.0;", "double cx = 1.0;"),
     # a Dormand-Prince stage time mistyped (c_3 = 3/11 for 3/10): the integrator loses its order
     "dp45_stage_time": ("DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10,", "DP_C[7] = {0.0, 1.0 / 5, 3.0 / 11,"),
+    # the Jacobi eigensolver: the phase step applied to the eigenvector column with the wrong sign
+    "jacobi_vector_phase": ("for (int k = 0; k < n; k++) V[k * n + q] *= conj(ph);",
+                            "for (int k = 0; k < n; k++) V[k * n + q] *= ph;"),
+    # the Bloch Hamiltonian with e^{-ik.R} for e^{ik.R} (H(-k) for H(k))
+    "bloch_phase_sign": ("cplx ph = lattice_phase((long)kx * m->hopR[2 * h] + (long)ky * m->hopR[2 * h + 1], Lf);",
+                         "cplx ph = conj(lattice_phase((long)kx * m->hopR[2 * h] + (long)ky * m->hopR[2 * h + 1], Lf));"),
     # the density n(mu) with the sign of mu flipped (the bisection then hits the filling at -mu)
     "density_mu_sign": ("s += fermi(E[(size_t)k * ns + l] - mu, T);", "s += fermi(E[(size_t)k * ns + l] + mu, T);"),
     # the Fermi function's two branches exchanged (1 - f for f)
