@@ -48,6 +48,11 @@ MUTANTS = {
     # the P -> C gather with the legs 3 and 4 of the source exchanged
     "P_to_C_legs": ("size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s4 * ns + s3;",
                     "size_t sr = (size_t)i1 * ns2 + s1 * ns + s2, sc = (size_t)i2 * ns2 + s3 * ns + s4;"),
+    # Eq. proj_DC: the D -> C gather added instead of subtracted (D = -C with legs 3, 4 exchanged)
+    "D_to_C_sign": ("val -= ph * Cr[(size_t)cm * M2 + sr * M + sc];", "val += ph * Cr[(size_t)cm * M2 + sr * M + sc];"),
+    # the P -> C gather with the phase e^{-iu.R''} for e^{iu.R''}
+    "P_to_C_phase": ("cplx ph = lattice_phase((long)qx * c->cls[2 * k] + (long)qy * c->cls[2 * k + 1], Lq);",
+                     "cplx ph = conj(lattice_phase((long)qx * c->cls[2 * k] + (long)qy * c->cls[2 * k + 1], Lq));"),
     # the bare vertex projected with legs 3 and 4 exchanged (its sign flipped, V0 being antisymmetric)
     "bare_vertex_legs": ("V0[((s1 * ns + s2) * ns + s3) * ns + s4]", "V0[((s1 * ns + s2) * ns + s4) * ns + s3]"),
     # Eq. RGE_spin / the C equation: c_C = 1 instead of 2
