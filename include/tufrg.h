@@ -62,7 +62,7 @@ typedef enum {
     TUFRG_ENOTCONV = 5,    /* step size underflow or step limit in the flow */
     TUFRG_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
     TUFRG_EFALLBACK = 7,   /* surrogate rejected, direct loops used (informational) */
-    TUFRG_ENOTSUP = 8,     /* configuration not supported by this build */
+    TUFRG_ENOTSUP = 8,     /* configuration not supported by the library */
     TUFRG_ETOOBIG = 9      /* problem larger than the fixed scratch of tufrg_loops_noalloc, or projection
                               tables beyond 2^31 entries at init */
 } tufrg_status;

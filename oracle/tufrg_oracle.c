@@ -2,7 +2,7 @@
  * tufrg_oracle.c -- plain FP64 CPU oracle of the TU-fRG right-hand side and flow.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
- * baseline leg of the benchmark may load this library.  It shares no code,
+ * baseline and reference legs of the benchmark may load this library.  It shares no code,
  * header, table or constant generator with the CUDA library; both read the
  * same model descriptor (bonds, hoppings, V0, meshes) and nothing else.
  *
@@ -29,14 +29,17 @@
  *     Eq. proj_DC), each evaluated literally.
  *  6. dP/dT = A_P L^- A_P (Eq. RGE_spin), dC/dT = 2 A_C L^+ A_C (orbital
  *     form of Eq. rge_Dmat), by naive triple loops.
- *  7. Dormand-Prince 5(4) integration in ln T (the paper only says "ordinary
- *     differential equations"; scheme chosen for this build).
+ *  7. Dormand-Prince 5(4) integration in ln T (the paper names no integration
+ *     scheme; this one is the implementation's choice).
  *  8. Band-basis exchange propagators from the orbital ones with the
  *     transformation matrices U(s), X(u) (Sec. 3.4, Eqs. trafo_P,
  *     mat_trafo_P, mat_trafo_D), from their k-sum definitions.
  *
  * Parity status of each function is pinned by tests under tests/ (see the
- * oracle pin tests); nothing here is unpinned.
+ * oracle pin tests); nothing here is unpinned.  A mutation test compiles
+ * copies of this file with one planted mistake each (a dropped term, a wrong
+ * sign, index, momentum or conjugation, a mistyped coefficient) and requires
+ * every copy to fail a pin.
  *
  * Index layouts (all complex numbers stored as interleaved re,im doubles):
  *   E[k][l], U[k][tau][l]                      fine mesh k = kx*Lf + ky

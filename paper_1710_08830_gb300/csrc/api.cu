@@ -732,7 +732,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     *out = m;   // so that tufrg_last_error works even when set-up fails
     const tufrg_model_desc &d = *desc;
     if (d.n_s < 1 || d.n_s > 8) return fail(m, TUFRG_EINVAL, "n_s must be in [1, 8]");
-    if (d.n_s != 2 && d.n_s != 4 && d.n_s != 6) return fail(m, TUFRG_ENOTSUP, "this build supports n_s = 2, 4, 6");
+    if (d.n_s != 2 && d.n_s != 4 && d.n_s != 6) return fail(m, TUFRG_ENOTSUP, "the library supports n_s = 2, 4, 6");
     if (d.n_hop < 1 || !d.hop_R || !d.hop_t) return fail(m, TUFRG_EINVAL, "empty hopping list");
     if (!d.V0) return fail(m, TUFRG_EINVAL, "V0 is NULL");
     if (d.n_ff < 1 || !d.ff_R) return fail(m, TUFRG_EINVAL, "empty bond set");
