@@ -8,7 +8,6 @@ from paper_1710_08830_gb300 import inputs
 
 SX = np.array([[0, 1], [1, 0]], complex)
 SY = np.array([[0, -1j], [1j, 0]])
-SZ = np.diag([1.0 + 0j, -1.0])
 
 
 def h_of_k(spec, k):
