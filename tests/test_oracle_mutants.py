@@ -7,8 +7,10 @@ built the same way (the control).  The mistakes are planted on the CPU only; the
 The two truncated-projection pins (about 20 s together) are left out of these runs; every mutant below is
 caught by a faster pin."""
 import concurrent.futures
+import contextlib
 import importlib.util
 import os
+import shutil
 import subprocess
 import sys
 
@@ -103,8 +105,9 @@ def _run_pins(work, name, src_text):
 
 
 @pytest.fixture(scope="module")
-def runs(tmp_path_factory):
-    """The control and every mutant, run concurrently: name -> CompletedProcess."""
+def runs():
+    """The control and every mutant, run concurrently: name -> CompletedProcess.  The copies are built in a
+    git-ignored folder of the repository (oracle/_build/mutants), removed afterwards."""
     with open(oracle._SRC) as f:
         src = f.read()
     texts = {"control": src}
@@ -112,11 +115,16 @@ def runs(tmp_path_factory):
     for name, (old, new) in sorted(MUTANTS.items(), key=lambda kv: kv[0] != "dp45_stage_time"):
         assert src.count(old) == 1, name
         texts[name] = src.replace(old, new)
-    work = str(tmp_path_factory.mktemp("oracle_mutants"))
+    work = os.path.join(ROOT, "oracle", "_build", "mutants")
     workers = max(1, min(len(texts), (os.cpu_count() or 2) // 2))
-    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
-        futs = {n: ex.submit(_run_pins, work, n, t) for n, t in texts.items()}
-        return {n: f.result() for n, f in futs.items()}
+    try:
+        with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+            futs = {n: ex.submit(_run_pins, work, n, t) for n, t in texts.items()}
+            yield {n: f.result() for n, f in futs.items()}
+    finally:
+        shutil.rmtree(work, ignore_errors=True)
+        with contextlib.suppress(OSError):
+            os.rmdir(os.path.dirname(work))   # oracle/_build, when nothing else is in it
 
 
 def test_control_copy_passes_the_pins(runs):
