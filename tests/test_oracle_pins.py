@@ -166,6 +166,22 @@ def test_rhs_equals_full_momentum_rge(model, T):
     assert np.abs(d[1] - dC).max() < 1e-12 * scale
 
 
+def test_rhs_equals_full_momentum_rge_multiorbital():
+    """The same exactness for the three-orbital t2g model with atomic SOC and the Kanamori vertex (N_s = 6,
+    M = 324): complete form factors on a 3x3 torus, a consistent random state, T = 0.3.  It pins the oracle's
+    loops, projections and products for more than two spin-orbitals."""
+    spec = inputs.t2g_soc(seed=1, Lq=3, nc=1, n_ff=1, filling=4.0, T_mu=0.1).with_(ff_R=inputs.ff_complete(3))
+    o = oracle.Oracle(spec)
+    bf = bruteforce.Torus(spec, o.mu)
+    P, C, _, _ = bf.random_consistent_state(np.random.default_rng(7))
+    dP, dC = bf.channel_rhs(bf.vertex_from_channels(spec.V0, P, C), 0.3)
+    d, _ = o.rhs(0.3, np.stack([P, C]), 3)
+    scale = max(np.abs(dP).max(), np.abs(dC).max())
+    assert scale > 0.1
+    assert np.abs(d[0] - dP).max() < 1e-12 * scale
+    assert np.abs(d[1] - dC).max() < 1e-12 * scale
+
+
 def test_flow_equals_full_momentum_flow():
     """Same exactness for a whole flow: fixed-step RK4 of the full vertex vs the
     (P, C) flow, compared on the reconstructed vertex V0 + V^P + V^C + V^D."""
