@@ -223,6 +223,37 @@ def rashba_hubbard(t=1.0, tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, *, Lq=24, nc=8, n_
                      params=dict(t=t, tp=tp, alpha=alpha, U=U, mu=mu))
 
 
+def rashba_bilayer(t=1.0, tp=-0.2, alpha=0.3, t_perp=0.4, U=2.5, mu=-0.9, *, Lq=8, nc=4, n_ff=5,
+                   filling=0.0, T_mu=0.02, name="rashba_bilayer") -> ModelSpec:
+    """Two Rashba-Hubbard layers (N_s = 4, index layer * 2 + spin) with opposite Rashba couplings, so that the
+    pair is inversion symmetric, coupled by an onsite interlayer hopping t_perp.
+
+    Each layer: eps(k) 1 + (-1)^layer g(k).sigma with the lattice Rashba g(k) = alpha (-sin ky, sin kx, 0);
+    between the layers -t_perp (sigma_x in layer space) (x) 1_spin; an onsite Hubbard U within each layer.
+    """
+    h = _Hops(4)
+    one = np.eye(2)
+    Lz = np.diag([1.0, -1.0])
+    for R in [(1, 0), (0, 1)]:
+        h.add_pair(R, -t * np.eye(4))
+    for R in [(1, 1), (1, -1)]:
+        h.add_pair(R, -tp * np.eye(4))
+    h.add_pair((0, 1), np.kron(Lz, (1j * alpha / 2.0) * SIGMA_X))
+    h.add_pair((1, 0), np.kron(Lz, (-1j * alpha / 2.0) * SIGMA_Y))
+    h.add((0, 0), -t_perp * np.kron(np.array([[0.0, 1.0], [1.0, 0.0]]), one))
+    R, tt = h.arrays()
+    W = np.zeros((4,) * 4, np.complex128)
+    for t1 in range(4):
+        for t2 in range(4):
+            l1, s1 = divmod(t1, 2)
+            l2, s2 = divmod(t2, 2)
+            if l1 == l2:
+                W[t1, t2, t1, t2] = U              # U delta(s1 s3) delta(s2 s4) within one layer
+    V0 = 0.5 * (W - W.transpose(0, 1, 3, 2))
+    return ModelSpec(name, 4, R, tt, V0, ff_set(n_ff), Lq, nc, mu=mu, filling=filling, T_mu=T_mu,
+                     params=dict(t=t, tp=tp, alpha=alpha, t_perp=t_perp, U=U, mu=mu))
+
+
 def t2g_soc(seed=0, lam=0.2, U=2.0, J=0.4, *, Lq=32, nc=6, n_ff=9, filling=4.0,
             T_mu=0.02, name="t2g") -> ModelSpec:
     """Three-orbital (yz, xz, xy) square-lattice model with atomic SOC.

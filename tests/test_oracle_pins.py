@@ -166,11 +166,17 @@ def test_rhs_equals_full_momentum_rge(model, T):
     assert np.abs(d[1] - dC).max() < 1e-12 * scale
 
 
-def test_rhs_equals_full_momentum_rge_multiorbital():
-    """The same exactness for the three-orbital t2g model with atomic SOC and the Kanamori vertex (N_s = 6,
-    M = 324): complete form factors on a 3x3 torus, a consistent random state, T = 0.3.  It pins the oracle's
-    loops, projections and products for more than two spin-orbitals."""
-    spec = inputs.t2g_soc(seed=1, Lq=3, nc=1, n_ff=1, filling=4.0, T_mu=0.1).with_(ff_R=inputs.ff_complete(3))
+@pytest.mark.parametrize("model", ["t2g", "bilayer"])
+def test_rhs_equals_full_momentum_rge_multiorbital(model):
+    """The same exactness with more than two spin-orbitals: the three-orbital t2g model with atomic SOC and the
+    Kanamori vertex (N_s = 6, M = 324) and the Rashba bilayer (N_s = 4, M = 144); complete form factors on a 3x3
+    torus, a consistent random state, T = 0.3.  It pins the oracle's loops, projections and products for
+    N_s = 4 and 6."""
+    if model == "t2g":
+        spec = inputs.t2g_soc(seed=1, Lq=3, nc=1, n_ff=1, filling=4.0, T_mu=0.1)
+    else:
+        spec = inputs.rashba_bilayer(Lq=3, nc=1)
+    spec = spec.with_(ff_R=inputs.ff_complete(3))
     o = oracle.Oracle(spec)
     bf = bruteforce.Torus(spec, o.mu)
     P, C, _, _ = bf.random_consistent_state(np.random.default_rng(7))

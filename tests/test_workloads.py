@@ -83,6 +83,21 @@ def test_t2g_workload():
     assert np.allclose(V, -V.transpose(0, 1, 3, 2))
 
 
+def test_bilayer_model():
+    """The N_s = 4 Rashba bilayer: each layer eps(k) + (-1)^layer alpha (-sin ky sigma_x + sin kx sigma_y),
+    -t_perp between the layers at the same site, an onsite Hubbard U within each layer and none between them."""
+    s = inputs.rashba_bilayer(tp=-0.2, alpha=0.3, t_perp=0.4, U=2.5, Lq=4, nc=2, n_ff=5)
+    assert (s.n_s, s.M) == (4, 80)
+    for k in _ks(seed=3):
+        g = 0.3 * (-np.sin(k[1]) * SX + np.sin(k[0]) * SY)
+        want = eps(k, 1.0, -0.2) * np.eye(4) + np.kron(np.diag([1.0, -1.0]), g) \
+            - 0.4 * np.kron(np.array([[0, 1], [1, 0]]), np.eye(2))
+        assert np.allclose(h_of_k(s, k), want, atol=1e-14)
+    one = inputs.onsite_hubbard_vertex(2.5)
+    assert np.allclose(s.V0[:2, :2, :2, :2], one) and np.allclose(s.V0[2:, 2:, 2:, 2:], one)
+    assert np.abs(s.V0[0, 2, 0, 2]) == 0 and np.abs(s.V0[0, 3, 0, 3]) == 0
+
+
 def test_batch_workload():
     """64 uneven Rashba/Hubbard instances: t' in [-0.3, 0], alpha in [0, 0.4], U in [1.5, 3.5],
     Lq in {16, 24, 32, 48}, N_ff in {5, 9, 13}, mu in [-1.2, -0.6]; reproducible from the seed."""
