@@ -958,7 +958,12 @@ int or_flow(const or_model *m, const double *E, const double *U, const or_flow_o
     res->n_rhs++;
     res->amax = amax_prev;
     int status = 0;
-    while (res->n_steps < o->max_steps) {
+    /* max|A| above the stop value already at T0: the flow is critical before its first step, Lambda_c = T0 */
+    if (amax_prev > o->stop) {
+        res->crossed = 1;
+        res->Tc = exp(x);
+    }
+    while (!res->crossed && res->n_steps < o->max_steps) {
         if (x + h < xend) h = xend - x;
         for (int j = 1; j < 7; j++) {
             for (size_t i = 0; i < n; i++) {

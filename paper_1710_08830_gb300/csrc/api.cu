@@ -642,6 +642,10 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
         if (ce != cudaSuccess) return cuda_fail(m, ce, "graph instantiate");
         m->step_graph_mask = o->channel_mask;
     }
+    // the controller state after the initial evaluation: a flow whose initial max|A| already exceeds the stop
+    // value is critical at T0 and runs no attempt
+    CK(cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream), "copy flow state");
+    CK(cudaStreamSynchronize(m->stream), "sync");
     return TUFRG_OK;
 }
 
@@ -1387,7 +1391,7 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_
     if ((st = flow_enter(m, &user)) != TUFRG_OK) return st;
     st = flow_prepare(m, o);
     // replay the captured attempt until the device controller stops the flow
-    while (st == TUFRG_OK) {
+    while (st == TUFRG_OK && m->h_flow->status == 0) {
         cudaError_t e = cudaGraphLaunch(m->step_graph, m->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
@@ -1422,6 +1426,11 @@ tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flo
         if (st == TUFRG_OK) {
             entered[i] = 1;
             st = flow_prepare(models[i], o);
+        }
+        if (st == TUFRG_OK && models[i]->h_flow->status != 0) {   // stopped before the first attempt
+            active[i] = 0;
+            st = read_device_error(models[i]);
+            if (st == TUFRG_OK) st = flow_finish(models[i], nullptr, &res[i]);
         }
         if (st != TUFRG_OK) {
             active[i] = 0;

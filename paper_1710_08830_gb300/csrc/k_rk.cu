@@ -78,7 +78,12 @@ __global__ void flow_init_kernel(FlowDev *fs, const unsigned long long *red)
     const double amax = __longlong_as_double((long long)red[0]);
     fs->amax = amax;
     fs->amax_prev = amax;
-    if (!isfinite(amax)) fs->status = 4;
+    if (!isfinite(amax)) {
+        fs->status = 4;
+    } else if (amax > fs->stop) {   // already above the stop value at T0: critical before the first step
+        fs->Tc = exp(fs->x);
+        fs->status = 1;
+    }
 }
 
 // Accept or reject the attempt just computed (error norm in red[2], max|A| at the candidate in red[0]).

@@ -478,6 +478,45 @@ def test_t2g_rhs(case, prec):
     assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32)
 
 
+BILAYER = {   # N_s = 4: two Rashba layers with opposite couplings, interlayer hopping, onsite U per layer
+    "bilayer_ff5_Lf10": lambda: inputs.rashba_bilayer(Lq=5, nc=2, n_ff=5),                            # M = 80
+    "bilayer_ff9_Lf8": lambda: inputs.rashba_bilayer(Lq=4, nc=2, n_ff=9, alpha=0.25, t_perp=0.3),    # M = 144
+}
+
+
+@pytest.mark.parametrize("case", list(BILAYER))
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_bilayer_loops_and_rhs(case, prec):
+    """N_s = 4 (the multi-orbital loop kernel with 2 x 2 tiles, products at M = 16 N_ff, symmetry tables for a
+    4-state unitary): loops and right-hand sides against the oracle."""
+    api = _api()
+    spec = BILAYER[case]()
+    m = api.Model(spec, getattr(api, prec))
+    o = oracle.Oracle(spec)
+    L = m.loops(0.15).cpu().numpy()
+    for ch in (0, 1):
+        assert rel(L[ch], o.loops(0.15, ch)) < (TOL64 if prec == "FP64" else 2e-5), ch
+    st = inputs.random_state(spec, seed=13, scale=0.15)
+    ref, _ = o.rhs(0.2, st, 3)
+    assert rel(m.rhs(0.2, st).cpu().numpy(), ref) < (TOL64 if prec == "FP64" else TOL32)
+
+
+def test_bilayer_flows():
+    """N_s = 4 flows: the FP64 flow takes the oracle's step sequence and reaches its state and critical scale to
+    1e-9; the split flow (symmetric states, representatives and scatter) stays within 1% of the FP64 critical
+    scale with the same leading channel."""
+    api = _api()
+    spec = BILAYER["bilayer_ff5_Lf10"]()
+    st_ref, r_ref = oracle.Oracle(spec).flow(T0=10.0, T_end=1e-3, stop=6.0)
+    st, r = api.Model(spec, api.FP64).flow(T0=10.0, T_end=1e-3, stop=6.0)
+    assert r["n_steps"] == r_ref["n_steps"] and r["n_reject"] == r_ref["n_reject"] and r["crossed"] == r_ref["crossed"]
+    assert r["Tc"] == pytest.approx(r_ref["Tc"], rel=1e-9)
+    assert rel(st.cpu().numpy(), st_ref) < 1e-9
+    _, r32 = api.Model(spec, api.SPLIT32).flow(T0=10.0, T_end=1e-3, stop=6.0)
+    assert r32["crossed"] == r["crossed"] and abs(r32["Tc"] / r["Tc"] - 1) < 0.01
+    assert r32["lead_channel"] == r["lead_channel"]
+
+
 @pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
 def test_t2g_full_size_sampled_loops(prec):
     """The 32x32 / 6x6-per-cell t2g workload (N_s = 6, M = 324): loops at sampled transfer momenta."""
@@ -515,6 +554,26 @@ def test_flow_batch_matches_single_flows():
             assert r1["n_steps"] == r2["n_steps"] and r1["n_reject"] == r2["n_reject"]
             assert r1["crossed"] == r2["crossed"]
             assert r1["Tc"] == r2["Tc"]
+
+
+def test_flow_critical_at_start():
+    """max|A| of the bare vertex already above the stop value: the flow is critical at T0 (Lambda_c = T0, no
+    step, one evaluation), alone and inside a batch next to a flow that runs; the oracle agrees."""
+    api = _api()
+    specs = [inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=6, nc=2, n_ff=5),     # max|V0| = 1.6
+             inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=2.8, mu=-0.8, Lq=6, nc=2, n_ff=5)]     # max|V0| = 1.4
+    _, ref = oracle.Oracle(specs[0]).flow(stop=1.5)
+    assert ref["crossed"] == 1 and ref["n_steps"] == 0 and ref["Tc"] == pytest.approx(10.0)
+    for prec in (api.FP64, api.SPLIT32):
+        _, r = api.Model(specs[0], prec).flow(stop=1.5)
+        assert r["crossed"] == 1 and r["n_steps"] == 0 and r["n_rhs"] == 1 and r["Tc"] == pytest.approx(10.0)
+        assert r["amax"] == pytest.approx(1.6, rel=1e-6)
+        streams = [torch.cuda.Stream() for _ in specs]
+        models = [api.Model(sp, prec, stream=s) for sp, s in zip(specs, streams)]
+        batch = api.flow_batch(models, stop=1.5)
+        assert batch[0]["crossed"] == 1 and batch[0]["n_steps"] == 0 and batch[0]["Tc"] == pytest.approx(10.0)
+        _, r1 = api.Model(specs[1], prec).flow(stop=1.5)
+        assert batch[1]["n_steps"] == r1["n_steps"] > 0 and batch[1]["Tc"] == r1["Tc"]
 
 
 def test_flow_batch_matches_oracle():

@@ -188,6 +188,18 @@ def test_rhs_equals_full_momentum_rge_multiorbital(model):
     assert np.abs(d[1] - dC).max() < 1e-12 * scale
 
 
+def test_flow_critical_at_start():
+    """A flow whose bare vertex already exceeds the stop value (max|A| = U/2 at T0) is critical at T0: no step,
+    Lambda_c = T0 (reading R14); just below that value it runs."""
+    spec = inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=4, nc=2, n_ff=5)
+    o = oracle.Oracle(spec)
+    _, r = o.flow(T0=10.0, stop=1.5)
+    assert r["crossed"] == 1 and r["n_steps"] == 0 and r["n_rhs"] == 1
+    assert r["Tc"] == pytest.approx(10.0) and r["amax"] == pytest.approx(1.6)
+    _, r2 = o.flow(T0=10.0, T_end=2.0, stop=1.7)
+    assert r2["n_steps"] > 0 and r2["Tc"] < 10.0
+
+
 def test_flow_equals_full_momentum_flow():
     """Same exactness for a whole flow: fixed-step RK4 of the full vertex vs the
     (P, C) flow, compared on the reconstructed vertex V0 + V^P + V^C + V^D."""
