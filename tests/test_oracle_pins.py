@@ -513,6 +513,21 @@ def test_point_group_and_time_reversal_rashba():
         _check_covariance(spec, st[w], w, reps, theta)
 
 
+def test_point_group_and_time_reversal_bilayer():
+    """The N_s = 4 Rashba bilayer: C4v acts on the spins of both layers alike, W_g = 1_layer (x) S_g (the two
+    layers' opposite Rashba couplings are each invariant), time reversal is 1 (x) i sigma_y.  Loops of both
+    channels and the flowing P, C after a flow from T0 = 10 to T = 0.3 on a 5x5 mesh."""
+    spec = inputs.rashba_bilayer(Lq=5, nc=2, n_ff=5)
+    o = oracle.Oracle(spec)
+    reps = [np.kron(np.eye(2), _spin_rep(g)) for g in _C4V]
+    theta = np.kron(np.eye(2), 1j * _SY)
+    _check_setup(spec, o, reps, theta)
+    st, _ = o.flow(T0=10.0, T_end=0.3, chmask=3, stop=1e9)
+    for w in (0, 1):
+        _check_covariance(spec, _expand_all(spec, o, o.loops(0.3, w)), w, reps, theta)
+        _check_covariance(spec, st[w], w, reps, theta)
+
+
 def test_point_group_and_time_reversal_t2g():
     """The t2g model with atomic SOC: C4v acts on orbitals and spins, W_g = D_g (x) S_g (orbitals as polar
     quadratic forms, spins as an axial vector), and time reversal is 1 (x) i sigma_y on the real orbitals.
