@@ -265,7 +265,9 @@ tufrg_status tufrg_rhs_host_batch(tufrg_model *m, int n, const double *T, const 
  * (six stage right-hand sides, error norm, accept/reject, FSAL commit) is captured once as
  * a CUDA graph and replayed; the host only polls the controller state between attempts.
  * d_state_out (may be NULL): [2][Nq][M][M] complex, the last accepted state.  *res (and d_state_out) are
- * filled on success and on TUFRG_ENOTCONV / TUFRG_ENONFINITE (the state reached so far).
+ * filled on success and on TUFRG_ENOTCONV / TUFRG_ENONFINITE (the state reached so far).  A flow whose
+ * max |A| already exceeds opts->stop at T0 (the bare vertex alone) is critical there: crossed = 1, Tc = T0,
+ * n_steps = 0, n_rhs = 1.
  * Errors: TUFRG_EINVAL (NULL argument, not T0 > T_end > 0, rtol <= 0, atol < 0, h0 >= 0, channel_mask
  * empty or beyond P|C, max_steps < 1), TUFRG_ENOTCONV (step limit reached or step size underflow),
  * TUFRG_ENONFINITE (non-finite right-hand side or error norm), TUFRG_ETIMEOUT (a bounded device-side wait
