@@ -576,6 +576,24 @@ def test_flow_critical_at_start():
         assert batch[1]["n_steps"] == r1["n_steps"] > 0 and batch[1]["Tc"] == r1["Tc"]
 
 
+def test_flow_step_limit_and_bad_options():
+    """The step limit (accepted + rejected attempts) ends a flow with TUFRG_ENOTCONV; options outside their
+    ranges are rejected with TUFRG_EINVAL before any work; the model stays usable after both."""
+    api = _api()
+    spec = inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=2.8, mu=-0.8, Lq=6, nc=2, n_ff=5)
+    m = api.Model(spec, api.FP64)
+    with pytest.raises(api.TufrgError) as e:
+        m.flow(stop=50.0, max_steps=2)
+    assert e.value.status == 5
+    for bad in (dict(T0=0.1, T_end=0.2), dict(rtol=0.0), dict(h0=0.05), dict(mask=0), dict(max_steps=0)):
+        with pytest.raises(api.TufrgError) as e:
+            m.flow(**bad)
+        assert e.value.status == 1, bad
+    _, r = m.flow(T0=10.0, T_end=1.0, stop=50.0)
+    _, ref = oracle.Oracle(spec).flow(T0=10.0, T_end=1.0, stop=50.0)
+    assert r["n_steps"] == ref["n_steps"] and r["Tc"] == pytest.approx(ref["Tc"], rel=1e-12)
+
+
 def test_flow_batch_matches_oracle():
     api = _api()
     specs = [inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=6, nc=2, n_ff=5),
