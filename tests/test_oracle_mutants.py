@@ -71,6 +71,8 @@ MUTANTS = {
                          "cplx ph = conj(lattice_phase((long)kx * m->hopR[2 * h] + (long)ky * m->hopR[2 * h + 1], Lf));"),
     # the density n(mu) with the sign of mu flipped (the bisection then hits the filling at -mu)
     "density_mu_sign": ("s += fermi(E[(size_t)k * ns + l] - mu, T);", "s += fermi(E[(size_t)k * ns + l] + mu, T);"),
+    # Lambda_c reported at the end of the crossing step instead of interpolated in ln T
+    "critical_scale_endpoint": ("res->Tc = exp(x_prev + t * (x - x_prev));", "res->Tc = exp(x); (void)t;"),
     # the Fermi function's two branches exchanged (1 - f for f)
     "fermi_branches": ("return e > 0 ? z / (1.0 + z) : 1.0 / (1.0 + z);", "return e > 0 ? 1.0 / (1.0 + z) : z / (1.0 + z);"),
     # Eq. def_lmp with the momentum shell: the product rule of d/dLambda [chi chi] shortened to one doubled term

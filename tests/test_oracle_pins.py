@@ -284,6 +284,33 @@ def test_particle_particle_closed_form(alpha, tp, reg):
     assert np.abs(state[1]).max() == 0.0
 
 
+@pytest.mark.parametrize("stop", [2.0, 4.0])
+def test_critical_scale_of_the_ladder(stop):
+    """Lambda_c as reported (reading R14): for the P-only ladder with an attractive onsite U (the Cooper channel),
+    A_P(s) = V0 + P = -(g_T(s) / 2) (d13 d24 - d14 d23) at R = R' = 0 by Eq. sol_spin, so max|A| = max_s |g_T(s)| / 2
+    with g_T = -U / (1 + U [B(T) - B(T0)]).  The closed form's crossing of the stop value (bisection in ln T) equals the
+    flow's Lambda_c, a linear interpolation in ln T between the accepted states around the crossing, to 1e-3 (one
+    step is about 6% in T, so reporting either end of it fails)."""
+    U, ns = -2.5, 2
+    spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=U, mu=-0.9, Lq=6, nc=2, n_ff=5)
+    o = oracle.Oracle(spec)
+    d0 = [i for i, (x, y) in enumerate(o.deltas) if x == 0 and y == 0][0]
+
+    def Bbar(T):
+        L = o.loops(T, 0, kind=1)[:, d0].reshape(spec.Nq, ns, ns, ns, ns)   # [s][t2][t1][t4][t3]
+        return sum(0.5 * (L[:, t2, t1, t2, t1] - L[:, t2, t1, t1, t2]) for t1 in range(ns) for t2 in range(ns))
+
+    B0 = Bbar(10.0)
+    amax = lambda lnT: np.abs(-U / (1 + U * (Bbar(np.exp(lnT)) - B0))).max() / 2
+    lo, hi = np.log(1e-3), np.log(10.0)
+    assert amax(lo) > stop > amax(hi)
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if amax(mid) > stop else (lo, mid)
+    _, res = o.flow(T0=10.0, T_end=1e-3, rtol=1e-10, atol=1e-12, chmask=1, stop=stop)
+    assert res["crossed"] == 1 and res["Tc"] == pytest.approx(np.exp(0.5 * (lo + hi)), rel=1e-3)
+
+
 @pytest.mark.parametrize("reg", [0, 1])
 def test_second_order_perturbation_theory(reg):
     """At O(U^2): P(T) = V0 [B^-(T) - B^-(T0)] V0 and C(T) = 2 V0 [B^+(T) - B^+(T0)] V0 with
