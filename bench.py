@@ -148,17 +148,27 @@ def products_tf32_flop(M, Nq):
     return 2.0 * 2 * 2 * 4 * 3 * float(M) ** 3 * Nq
 
 
-def loop_traffic_record():
-    """DRAM bytes per loop-kernel launch from the committed ncu summary, if it matches the current source."""
+LOOP_KERNEL_SOURCES = ("paper_1710_08830_gb300/csrc/k_loops2.cu", "paper_1710_08830_gb300/csrc/tufrg_internal.cuh")
+
+
+def loop_sources_hash() -> str:
+    """First 16 hex digits of the SHA-256 over every source file the two-band loop kernel is compiled from."""
     import hashlib
+    h = hashlib.sha256()
+    for rel in LOOP_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def loop_traffic_record():
+    """DRAM bytes per loop-kernel launch from the committed ncu summary, if it was taken on the current sources
+    (the kernel's file and the header it includes)."""
     p = os.path.join(ROOT, "profiles", "loops_traffic.json")
-    src = os.path.join(ROOT, "paper_1710_08830_gb300", "csrc", "k_loops2.cu")
     if not os.path.exists(p):
         return None, None
     with open(p) as f:
         rec = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("k_loops2_sha256_16") != h:
+    if rec.get("sources_sha256_16") != loop_sources_hash():
         return None, rec
     return rec, rec
 

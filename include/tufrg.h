@@ -300,9 +300,12 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *opts, void *d_sta
  * The scratch must hold Lf*Lf*48 bytes of records plus the partial sums of one
  * channel, Lq*Lq * 2*ceil(Lf/64) * n_dx * n_dy * 128 bytes (n_dx distinct x and n_dy
  * non-negative y components of the bond differences); a larger problem returns
- * TUFRG_ETOOBIG before any work.  The first call on each device looks up the
- * device address of the scratch with cudaGetSymbolAddress (the device must be
- * current); make that first call before any stream capture.  Calls share the
+ * TUFRG_ETOOBIG before any work.  Every call made outside stream capture looks
+ * up the device address of the scratch with cudaGetSymbolAddress (the device must
+ * be current), so a device reset between calls is harmless; a call made while its
+ * stream is being captured reuses the address of the last uncaptured call on the
+ * device, so make one call before any capture (and again after a device reset);
+ * without one it returns TUFRG_ECUDA.  Calls share the
  * scratch: calls that overlap on the GPU (other streams, other threads) race and
  * give wrong results.  Nothing in the scratch needs to start at zero: every record
  * and every partial that is read is first written by the same call.
@@ -358,6 +361,14 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
  * that skipped it because it was off (synchronises; any pointer may be NULL). */
 tufrg_status tufrg_surrogate_stats(tufrg_model *m, long long *accepted, long long *rejected, long long *skipped);
 
+
+/* Set (value != 0) or clear (value == 0) the model's device error flag, the flag a bounded device-side wait
+ * (tensor-core pipeline barriers) raises when it gives up; an interface addition without a counterpart in the
+ * paper.  While it is set, every call that reads it (tufrg_rhs_host, tufrg_rhs_host_batch, tufrg_flow,
+ * tufrg_flow_batch) returns TUFRG_ETIMEOUT, so callers can test their handling of a time-out from the host without
+ * making a device wait run out; clearing it makes the model usable again after a real time-out.  Synchronises
+ * the model's stream.  Errors: TUFRG_EINVAL (NULL model), TUFRG_ECUDA. */
+tufrg_status tufrg_set_device_error(tufrg_model *m, int value);
 
 /* Optional CUDA-event timing on the model's stream (used by the benchmark).
  * tufrg_timing_begin resets the counters and starts recording; every later

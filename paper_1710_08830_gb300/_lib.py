@@ -114,6 +114,8 @@ def lib():
             L.tufrg_set_surrogate.restype = C.c_int
             L.tufrg_surrogate_stats.argtypes = [vp] + [C.POINTER(C.c_longlong)] * 3
             L.tufrg_surrogate_stats.restype = C.c_int
+            L.tufrg_set_device_error.argtypes = [vp, i]
+            L.tufrg_set_device_error.restype = C.c_int
             L.tufrg_timing_begin.argtypes = [vp]
             L.tufrg_timing_end.argtypes = [vp, vp, i, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
             for fn in ("tufrg_init_model", "tufrg_dims", "tufrg_deltas", "tufrg_gather_table", "tufrg_bands",
@@ -132,4 +134,4 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_band_basis",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
-           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats")
+           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error")

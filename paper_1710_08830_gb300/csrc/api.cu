@@ -1506,6 +1506,15 @@ PhaseScope::~PhaseScope()
 
 extern "C" {
 
+tufrg_status tufrg_set_device_error(tufrg_model *m, int value)
+{
+    if (!m) return TUFRG_EINVAL;
+    const int v = value ? 1 : 0;
+    CK(cudaMemcpyAsync(m->d_err, &v, sizeof(int), cudaMemcpyHostToDevice, m->stream), "write error flag");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    return TUFRG_OK;
+}
+
 tufrg_status tufrg_timing_begin(tufrg_model *m)
 {
     if (!m) return TUFRG_EINVAL;

@@ -532,22 +532,28 @@ extern "C" tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, c
     const size_t rec_bytes = ((Nk * RECF4 * sizeof(float4)) + 255) & ~size_t(255);
     const size_t part_bytes = (size_t)Nq * n_part * ndx * ndyh * 16 * sizeof(float2);
     if (rec_bytes + part_bytes > (size_t)TUFRG_NOALLOC_SCRATCH_BYTES) return TUFRG_ETOOBIG;
-    // device address of the static scratch, looked up once per device (the device must be current)
+    // device address of the static scratch (the device must be current).  Outside stream capture it is looked
+    // up on every call, so that a device reset or a new primary context never leaves a stale address behind;
+    // during capture the address of the last uncaptured call on this device is used.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAXDEV) return TUFRG_ECUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+    if (capturing) (void)cudaGetLastError();   // clear the (non-sticky) error a refused capture query leaves
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        if (!capturing) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TUFRG_ECUDA;
             g_noalloc_addr[dev] = p;
         }
         base = g_noalloc_addr[dev];
     }
+    if (!base) return TUFRG_ECUDA;   // first call on this device inside a capture: nothing looked up yet
     float4 *rec = reinterpret_cast<float4 *>(base);
     float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(base) + rec_bytes);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
     rec_static_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d_E, reinterpret_cast<const double2 *>(d_U), (int)Nk,
                                                                       Lf, mu, rec);

@@ -16,7 +16,7 @@
 // and commits them to the stage's "empty" barrier, so copies of stage s + 1 overlap the MMAs of s.
 // The first product writes T = A L directly in the packed left-operand layout of the second; the
 // second writes c T A in FP64.  Every wait is bounded: on time-out the kernel records an error code,
-// waits (bounded) for its own MMAs, frees its TMEM and returns.
+// waits (bounded) for its own MMAs and for the bulk copies it issued, frees its TMEM and returns.
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
     __shared__ __align__(8) unsigned long long full[2], empty[2], done;
     __shared__ unsigned tmem_base_sh;
     __shared__ int failed;
+    __shared__ int last_issued[2];   // last stage whose copies went to buffer b (-1: none)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nt = blockIdx.x, rt = blockIdx.y, q = blockIdx.z;
 
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
+        last_issued[0] = last_issued[1] = -1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          ::"r"(smem_u32(stage[b] + a_bytes)), "l"(rsrc + (size_t)s * (b_bytes / 4)), "r"(b_bytes),
                          "r"(smem_u32(&full[b])) : "memory");
+            last_issued[b] = s;
         }
     } else if (tid == 32) {
         // MMA issuer: per stage, 2 K-steps x (Ar Br, -Ai Bi, Ar Bi, Ai Br) x (hi hi, hi lo, lo hi)
@@ -242,7 +245,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (!fin || failed) {
-        if (tid == 0) atomicExch(a.err, 1);
+        if (tid == 0) {
+            atomicExch(a.err, 1);
+            // bulk copies issued into this CTA's shared memory may still be in flight (the MMA thread gave up
+            // before consuming them): wait, bounded, until the last one of each buffer has landed
+            for (int b = 0; b < 2; b++)
+                if (last_issued[b] >= 0) (void)mbar_wait(smem_u32(&full[b]), (last_issued[b] >> 1) & 1);
+        }
     } else {
         // epilogue: lane = output row; 8 TMEM columns (8 complex outputs) per load from each accumulator
         const int r = warp * 32 + lane, row = rt * TC_M + r, M = a.pd.M;

@@ -403,6 +403,54 @@ def test_rhs_full_size_rashba_24x24(prec):
     assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32)
 
 
+@pytest.fixture(scope="module")
+def full_size_flow_state():
+    """The state the benchmark evaluates: the split flow of the 24x24 / 8x8 Rashba workload from T0 = 10 down to
+    T = 0.1.  Every state of a flow from X = 0 carries the loop symmetries exactly (dX/dT of the other momenta
+    is written from the orbit representatives), so it may be evaluated with TUFRG_SYMMETRIC_STATE."""
+    api = _api()
+    spec = inputs.rashba_q24_k8_ff9(0)
+    m = api.Model(spec, api.SPLIT32)
+    st, r = m.flow(T_end=0.1, stop=1e9)
+    assert r["T_last"] == pytest.approx(0.1) and m.symmetric_state_path
+    return spec, st
+
+
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+def test_rhs_full_size_symmetric_state_path(full_size_flow_state, prec):
+    """The benchmark's timed call itself at full size (Lq = 24, nc = 8, N_ff = 9, M = 36, T = 0.1): tufrg_rhs with
+    TUFRG_SYMMETRIC_STATE on the mid-flow state - loop k-sums at the 91 orbit representatives, their reduction,
+    projections and orbit products at the representatives, dX/dT of all 576 momenta written through the orbit
+    index maps - against the oracle's full right-hand side, element by element: FP64 <= 1e-10, split <= 1e-4."""
+    api = _api()
+    spec, st = full_size_flow_state
+    m = api.Model(spec, getattr(api, prec))
+    assert m.n_loop_q == 91 and m.symmetric_state_path
+    d = m.rhs(0.1, st, symmetric=True).cpu().numpy()
+    ref, _ = oracle.Oracle(spec).rhs(0.1, st.cpu().numpy(), 3)
+    assert np.abs(ref).max() > 1.0
+    assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32), rel(d, ref)
+
+
+def test_flow_full_size_hubbard_fp64_matches_oracle():
+    """The single-band Hubbard workload at full size (8x8 transfer mesh, 16x16 fine points per cell, N_ff = 5,
+    filling 0.45 per spin, U = 3): the FP64 GPU flow from T0 = 10 to T_end = 0.02 (the integration of the flow
+    equations, Sec. 3.1) takes the oracle's step sequence - the same accepted and rejected steps - and ends on
+    the oracle's state within 1e-9."""
+    api = _api()
+    spec = inputs.hubbard_q8_k16_ff5()
+    o = oracle.Oracle(spec)
+    st_ref, r_ref = o.flow()
+    m = api.Model(spec, api.FP64)
+    assert abs(m.mu - o.mu) < 1e-12
+    st, r = m.flow()
+    assert r["n_steps"] == r_ref["n_steps"] and r["n_reject"] == r_ref["n_reject"]
+    assert r["crossed"] == r_ref["crossed"]
+    assert r["Tc"] == pytest.approx(r_ref["Tc"], rel=1e-9)
+    assert r["amax"] == pytest.approx(r_ref["amax"], rel=1e-9)
+    assert rel(st.cpu().numpy(), st_ref) < 1e-9
+
+
 def test_invalid_temperature_is_rejected():
     api = _api()
     m = api.Model(CASES["rashba_ff5_Lf24"](), api.FP64)
@@ -605,3 +653,28 @@ def test_flow_batch_matches_oracle():
         _, ref = oracle.Oracle(sp).flow(stop=4.0)
         assert r["n_steps"] == ref["n_steps"]
         assert r["Tc"] == pytest.approx(ref["Tc"], rel=1e-9)
+
+
+def test_device_timeout_flag_propagates_to_the_host():
+    """TUFRG_ETIMEOUT reaches the caller of every entry point that reads the device error flag, raised from the
+    host (tufrg_set_device_error writes the flag a bounded device wait sets when it gives up; no device wait is
+    made to run out), and the model works again once the flag is cleared."""
+    api = _api()
+    spec = inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=2.8, mu=-0.8, Lq=6, nc=2, n_ff=5)
+    m = api.Model(spec, api.SPLIT32)
+    hs = m.zeros_state().cpu().pin_memory()
+    ho = torch.empty_like(hs).pin_memory()
+    assert m._L.tufrg_set_device_error(m._h, 1) == 0
+    with pytest.raises(api.TufrgError) as e:
+        m.rhs_host(0.4, hs, ho)
+    assert e.value.status == 6
+    with pytest.raises(api.TufrgError) as e:
+        m.rhs_host_batch(0.4, [hs, hs], [ho, ho])
+    assert e.value.status == 6
+    with pytest.raises(api.TufrgError) as e:
+        m.flow(T0=10.0, T_end=5.0)
+    assert e.value.status == 6
+    assert m._L.tufrg_set_device_error(m._h, 0) == 0
+    m.rhs_host(0.4, hs, ho)
+    _, r = m.flow(T0=10.0, T_end=5.0)
+    assert r["T_last"] == pytest.approx(5.0)

@@ -86,6 +86,13 @@ MUTANTS = {
     # Eq. mat_trafo_D: the conjugation of the second eigenvector dropped
     "band_C_conjugation": ("Ub[(size_t)k * ns2 + a * ns + c] * conj(Ub[(size_t)k2 * ns2 + b * ns + d])",
                            "Ub[(size_t)k * ns2 + a * ns + c] * Ub[(size_t)k2 * ns2 + b * ns + d]"),
+    # the sampled right-hand side (bounded CPU timings): c_C = 1 instead of 2
+    "rhs_at_crossed_prefactor": ("double cx = ch == 0 ? 1.0 : 2.0;", "double cx = 1.0;"),
+    # the sampled right-hand side projected at the list position instead of the listed momentum
+    "rhs_at_momentum_index": ("proj_one(&c, s_list[i], AP, AC);", "proj_one(&c, i, AP, AC);"),
+    # the sampled right-hand side with the first product's operands exchanged (L A for A L)
+    "rhs_at_operand_order": ("sacc += A[(size_t)r * M + k] * Lm[(size_t)k * M + col];",
+                             "sacc += Lm[(size_t)r * M + k] * A[(size_t)k * M + col];"),
     # the band-basis transformation T^T X T instead of T^dagger X T
     "band_transpose_for_adjoint": ("acc += conj(T[(size_t)j * M + r]) * W[(size_t)j * M + c];",
                                    "acc += T[(size_t)j * M + r] * W[(size_t)j * M + c];"),

@@ -188,6 +188,32 @@ def test_rhs_equals_full_momentum_rge_multiorbital(model):
     assert np.abs(d[1] - dC).max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("model,mask", [("rashba", 3), ("rashba", 1), ("rashba", 2), ("t2g", 3)])
+def test_rhs_at_equals_rows_of_the_full_rhs(model, mask):
+    """The sampled right-hand side (the oracle's restriction of one evaluation to listed transfer momenta, used
+    for bounded CPU timings) equals the listed rows of the full right-hand side, which the brute-force pins above
+    tie to the paper's equations: loops at the listed momenta only, projections from the whole-mesh Fourier
+    transform, c A L A with c_P = 1, c_C = 2 (Eq. RGE_spin and the C equation).  A swapped operand order, c_C = 1
+    or a momentum taken from the list position instead of the list fails it."""
+    if model == "rashba":
+        spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=5, nc=2, n_ff=9)
+        qs = [3, 0, 17, 24]
+    else:
+        spec = inputs.t2g_soc(seed=2, Lq=4, nc=1, n_ff=5, filling=4.0, T_mu=0.05)
+        qs = [9, 1, 14]
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=11, scale=0.3)
+    full, _ = o.rhs(0.2, st, mask)
+    part = o.rhs_at(0.2, st, qs, mask)
+    for ch in (0, 1):
+        ref = full[ch][qs]
+        if (mask >> ch) & 1:
+            assert np.abs(ref).max() > 1e-3
+            assert np.abs(part[ch] - ref).max() <= 1e-13 * np.abs(ref).max()
+        else:
+            assert not np.any(part[ch]) and not np.any(ref)
+
+
 def test_flow_critical_at_start():
     """A flow whose bare vertex already exceeds the stop value (max|A| = U/2 at T0) is critical at T0: no step,
     Lambda_c = T0 (reading R14); just below that value it runs."""
