@@ -98,7 +98,14 @@ typedef struct {
     int symmetry;          /* TUFRG_SYMMETRY_AUTO or TUFRG_SYMMETRY_OFF (see below) */
     int regulator;         /* TUFRG_REG_TEMPERATURE or TUFRG_REG_MOMENTUM_SHELL (see below) */
     double T_reg;          /* momentum shell: temperature of the Fermi functions in the bubbles (> 0) */
+    int loops;             /* TUFRG_LOOPS_AUTO / _TC / _SIMT: backend of the multi-orbital loop k-sum (see below) */
 } tufrg_model_desc;
+
+/* Backend of the loop k-sum of split-precision models with N_s = 6 and at most three non-negative y components
+ * of the bond differences (5 or 9 bonds): TC runs the per-column orbital sums as complex 3xTF32 GEMMs on the
+ * tensor cores (FP32 accumulation in tensor memory), SIMT as FP32 FMAs on the CUDA cores; AUTO takes TC where it
+ * applies.  Every other model uses the CUDA-core kernels whatever the value. */
+enum { TUFRG_LOOPS_AUTO = 0, TUFRG_LOOPS_TC = 1, TUFRG_LOOPS_SIMT = 2 };
 
 /* Regulator of the loops (Eq. def_lmp, L = d/dLambda [chi(e1) chi(e2)] F(e1, e2)).
  * TEMPERATURE: the flow scale is the temperature, chi = 1, L = d/dT F(e1, e2; T).
@@ -176,6 +183,10 @@ tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc
 /* Number of transfer momenta whose loop k-sums are evaluated directly (Nq unless loop symmetries
  * reduce them, see TUFRG_SYMMETRY_AUTO). */
 tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
+
+/* Loop k-sum backend in use: TUFRG_LOOPS_TC (tensor cores) or TUFRG_LOOPS_SIMT (CUDA cores).
+ * Errors: TUFRG_EINVAL for NULL arguments. */
+tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend);
 
 /* Exchange propagators of a state in the band basis of the model's eigenvectors (Sec. 3.4, Eqs. trafo_P,
  * mat_trafo_P, mat_trafo_D): with f_R(k) = e^{-ik.R}, N the fine mesh's k-points and U the eigenvectors of

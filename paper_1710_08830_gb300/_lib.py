@@ -19,6 +19,7 @@ STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA",
 
 FP64, SPLIT32 = 0, 1
 PRODUCTS_AUTO, PRODUCTS_TC, PRODUCTS_SIMT = 0, 1, 2
+LOOPS_AUTO, LOOPS_TC, LOOPS_SIMT = 0, 1, 2
 SYMMETRY_AUTO, SYMMETRY_OFF, SYMMETRY_STATES = 0, 1, 2
 SYMMETRIC_STATE = 4   # tufrg_rhs flag: the state has the model's loop symmetries
 REG_TEMPERATURE, REG_MOMENTUM_SHELL = 0, 1   # regulators of the loops (Eq. def_lmp)
@@ -30,7 +31,7 @@ class ModelDesc(C.Structure):
                 ("mu", C.c_double), ("filling", C.c_double), ("T_mu", C.c_double), ("V0", C.c_void_p),
                 ("n_ff", C.c_int), ("ff_R", C.c_void_p), ("Lq", C.c_int), ("nc", C.c_int),
                 ("precision", C.c_int), ("products", C.c_int), ("symmetry", C.c_int), ("regulator", C.c_int),
-                ("T_reg", C.c_double)]
+                ("T_reg", C.c_double), ("loops", C.c_int)]
 
 
 class FlowOpts(C.Structure):
@@ -76,6 +77,8 @@ def lib():
             L.tufrg_model_info.restype = C.c_int
             L.tufrg_loop_momenta.argtypes = [vp, ip]
             L.tufrg_loop_momenta.restype = C.c_int
+            L.tufrg_loops_info.argtypes = [vp, ip]
+            L.tufrg_loops_info.restype = C.c_int
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_symmetry_info.restype = C.c_int
             L.tufrg_round_f32.argtypes = [vp, vp, C.c_size_t, vp]
@@ -134,4 +137,4 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_band_basis",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
-           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error")
+           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info")

@@ -13,13 +13,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (CH_C, CH_P, FP64, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
+from ._lib import (CH_C, CH_P, FP64, LOOPS_AUTO, LOOPS_SIMT, LOOPS_TC, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
                    SYMMETRY_OFF, SYMMETRY_STATES,
                    FlowOpts, FlowResult, ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
 __all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "SYMMETRY_AUTO",
-           "SYMMETRY_OFF", "SYMMETRY_STATES", "SYMMETRIC_STATE", "CH_P", "CH_C", "TufrgError"]
+           "SYMMETRY_OFF", "SYMMETRY_STATES", "SYMMETRIC_STATE", "CH_P", "CH_C", "LOOPS_AUTO", "LOOPS_TC", "LOOPS_SIMT",
+           "TufrgError"]
 
 
 def _ptr(t) -> int:
@@ -30,7 +31,8 @@ class Model:
     """A TU-fRG model on the current CUDA device (see include/tufrg.h for layouts)."""
 
     def __init__(self, spec: ModelSpec, precision: int = FP64, stream: Optional[torch.cuda.Stream] = None,
-                 mu: Optional[float] = None, products: int = PRODUCTS_AUTO, symmetry: int = SYMMETRY_AUTO):
+                 mu: Optional[float] = None, products: int = PRODUCTS_AUTO, symmetry: int = SYMMETRY_AUTO,
+                 loops: int = LOOPS_AUTO):
         if not torch.cuda.is_available():
             raise RuntimeError("libtufrg needs a CUDA device")
         self.spec = spec
@@ -47,7 +49,7 @@ class Model:
                       float(spec.mu if mu is None else mu), float(spec.filling if use_fill else 0.0),
                       float(spec.T_mu), self._V0.ctypes.data, self._ffR.shape[0], self._ffR.ctypes.data,
                       spec.Lq, spec.nc, int(precision), int(products), int(symmetry),
-                      int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)))
+                      int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)), int(loops))
         h = C.c_void_p()
         st = self._L.tufrg_init_model(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h))
         self._h = h
@@ -70,6 +72,9 @@ class Model:
         nl = C.c_int()
         self._check(self._L.tufrg_loop_momenta(self._h, C.byref(nl)))
         self.n_loop_q = nl.value   # transfer momenta whose loop k-sums run directly
+        lb = C.c_int()
+        self._check(self._L.tufrg_loops_info(self._h, C.byref(lb)))
+        self.loops_backend = {LOOPS_TC: "tc", LOOPS_SIMT: "simt"}.get(lb.value, "?")
         su, t_gen, t_rep = C.c_int(), C.c_double(), C.c_double()
         self._check(self._L.tufrg_symmetry_info(self._h, C.byref(su), C.byref(t_gen), C.byref(t_rep)))
         self.symmetric_state_path = bool(su.value)   # rhs(symmetric=True) works at the representatives only

@@ -494,7 +494,7 @@ void release(tufrg_model *m)
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
                     m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
-                    m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32};
+                    m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -745,6 +745,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if ((long)d.Lq * d.nc > 4096) return fail(m, TUFRG_EINVAL, "fine mesh too large");
     if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
     if (d.products < TUFRG_PRODUCTS_AUTO || d.products > TUFRG_PRODUCTS_SIMT) return fail(m, TUFRG_EINVAL, "unknown products backend");
+    if (d.loops < TUFRG_LOOPS_AUTO || d.loops > TUFRG_LOOPS_SIMT) return fail(m, TUFRG_EINVAL, "unknown loops backend");
     if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF && d.symmetry != TUFRG_SYMMETRY_STATES)
         return fail(m, TUFRG_EINVAL, "unknown symmetry option");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
@@ -1007,10 +1008,13 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     m->part_bytes = 2 * (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
     if (ns != 2) {
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
-        m->gen_chunks = plan_gen_chunks(m);
+        m->loops_tc = d.loops != TUFRG_LOOPS_SIMT && loops_tc_supported(m);
+        m->gen_chunks = m->loops_tc ? 1 : plan_gen_chunks(m);
         // accumulators of one channel: one slot per (kx range, directly summed momentum), plus the FP64
         // range sums of the representatives under symmetry
         m->part_bytes = gen_part_bytes(m);
+        if (m->loops_tc)
+            CK(cudaMalloc(reinterpret_cast<void **>(&m->d_loop_w), loops_tc_w_bytes(m)), "cudaMalloc loop column sums");
     }
     m->products = split ? (d.products == TUFRG_PRODUCTS_AUTO ? TUFRG_PRODUCTS_TC : d.products) : TUFRG_PRODUCTS_SIMT;
     if (split && d.products != TUFRG_PRODUCTS_SIMT) {
@@ -1179,6 +1183,13 @@ tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct)
 {
     if (!m || !n_direct) return TUFRG_EINVAL;
     *n_direct = m->n_loop_q;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend)
+{
+    if (!m || !backend) return TUFRG_EINVAL;
+    *backend = m->loops_tc ? TUFRG_LOOPS_TC : TUFRG_LOOPS_SIMT;
     return TUFRG_OK;
 }
 

@@ -76,19 +76,6 @@ size_t gen_smem(int Lf)
     return gen_raw_bytes<R, NS>() + sizeof(C2) * (Lf + 3 * KB * NS * NS * NS + KB * NDYH) + sizeof(R) * KB * NS * NS;
 }
 
-template <int WHICH, typename R>
-__device__ __forceinline__ R gweight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr, R lam)
-{
-    if (lam > R(0)) return shell_weight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);   // (g, gp) = (f, h)
-    if (WHICH == 0) {
-        const R s = e1 + e2;
-        return fabs(s) > thr ? -(g1 + g2) / s : R(-0.5) * (gp1 + gp2);
-    } else {
-        const R d = e1 - e2;
-        return fabs(d) > thr ? (g1 - g2) / d : R(0.5) * (gp1 + gp2);
-    }
-}
-
 template <typename R, int NS, int TA, int TB, int NDYH, int WHICH>
 __global__ void loops_gen_kernel(GenArgs<R> a)
 {
@@ -187,7 +174,7 @@ __global__ void loops_gen_kernel(GenArgs<R> a)
                 R e1, g1, gp1, e2, g2, gp2;
                 ldft(&rF1[kb * NS + l1], e1, g1, gp1);
                 ldft(&rF2[kb * NS + l2], e2, g2, gp2);
-                sW[idx] = gweight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);
+                sW[idx] = gen_pair_weight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);
             }
             __syncthreads();
             // T^{l1}_{p} = sum_l2 w_{l1 l2} rho2'^{l2}_p
@@ -492,9 +479,12 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only)
     for (int ch = 0; ch < 2; ch++) {
         if (!((channel_mask >> ch) & 1)) continue;
         const bool fp64 = m->precision == TUFRG_FP64;
-        TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_part, 0, (fp64 ? sizeof(double2) : sizeof(float2)) * acc_n, m->stream));
         cudaError_t e;
-        if (fp64) {
+        if (m->loops_tc) {
+            // tensor cores: the half-plane sums of every slot are written (not accumulated), one kx range
+            e = launch_loops_tc(m, ch, reinterpret_cast<float2 *>(m->d_part));
+        } else if (fp64) {
+            TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_part, 0, sizeof(double2) * acc_n, m->stream));
             GenArgs<double> a{};
             a.U = m->d_U; a.ft = m->d_ft; a.acc = reinterpret_cast<double2 *>(m->d_part); a.thr_factor = 1e-5; a.Tp = m->d_scal;
             a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? m->T_reg : 0.0;
@@ -502,6 +492,7 @@ cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only)
             fill_chunks(m, a);
             e = m->ns == 6 ? dispatch_gen<double, 6, 2, 3>(m, a, ch) : dispatch_gen<double, 4, 2, 2>(m, a, ch);
         } else {
+            TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_part, 0, sizeof(float2) * acc_n, m->stream));
             GenArgs<float> a{};
             a.U = m->d_U32; a.ft = m->d_ft32; a.acc = reinterpret_cast<float2 *>(m->d_part); a.thr_factor = 1e-2f; a.Tp = m->d_scal;
             a.shell_T = m->regulator == TUFRG_REG_MOMENTUM_SHELL ? (float)m->T_reg : 0.f;

@@ -17,6 +17,7 @@
 // The first product writes T = A L directly in the packed left-operand layout of the second; the
 // second writes c T A in FP64.  Every wait is bounded: on time-out the kernel records an error code,
 // waits (bounded) for its own MMAs and for the bulk copies it issued, frees its TMEM and returns.
+#include "tc_common.cuh"
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
@@ -26,51 +27,16 @@ constexpr int TC_M = 128;        // MMA M (rows per CTA)
 constexpr int KS = 16;           // K per pipeline stage (two MMA K-steps of 8)
 constexpr int TC_THREADS = 128;
 constexpr int TMEM_COLS = 512;   // Cr at [0, NB), Ci at [256, 256 + NB)
-constexpr unsigned long long TC_WAIT_LIMIT = 1ull << 22;
+using tc::core_off;
+using tc::mbar_wait;
+using tc::smem_desc;
+using tc::smem_u32;
+using tc::tf32_hi;
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ float tf32_hi(float x)
-{
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// float offset of element (row r, k) in a K-major no-swizzle plane of R rows x KS columns:
-// core matrix (r/8, k/4) at ((k/4) * (R/8) + r/8) * 32 floats, row r%8 at 4 floats, element k%4.
-__device__ __forceinline__ int core_off(int r, int k, int R) { return ((k >> 2) * (R >> 3) + (r >> 3)) * 32 + (r & 7) * 4 + (k & 3); }
-
-__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, int R)
-{
-    const unsigned long long lbo = (unsigned long long)((R >> 3) * 128) >> 4;   // K-adjacent core matrices
-    const unsigned long long sbo = 128ull >> 4;                                  // M/N-adjacent 8-row groups
-    return (unsigned long long)((addr & 0x3FFFF) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
-}
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = nb; bit 13 negates A
-__device__ __forceinline__ unsigned idesc_tf32(int nb, bool neg_a)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | ((unsigned)(nb >> 3) << 17) |
-           ((unsigned)(TC_M >> 4) << 24);
-}
-
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
-{
-    for (unsigned long long it = 0; it < TC_WAIT_LIMIT; it++) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
+__device__ __forceinline__ unsigned idesc_tf32(int nb, bool neg_a) { return tc::idesc_tf32(TC_M, nb, neg_a); }
 __device__ __forceinline__ void mma(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc, unsigned acc)
 {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem), "l"(da), "l"(db), "r"(idesc),
-                 "r"(acc) : "memory");
+    tc::mma_tf32(tmem, da, db, idesc, acc);
 }
 
 struct PackDims {

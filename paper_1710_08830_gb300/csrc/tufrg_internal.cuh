@@ -53,6 +53,22 @@ __device__ __forceinline__ R shell_weight(R e1, R f1, R h1, R e2, R f2, R h2, R 
     return wdiv<R>(R(-2) * lam * a1 * a2 * (q1 + q2), p * p) * F;
 }
 
+// Loop weight of one band pair: d/dT F^- = -(g1 + g2) / (e1 + e2) (WHICH = 0) or d/dT F^+ = (g1 - g2) / (e1 - e2)
+// (WHICH = 1) from the Fermi entries (e, g, g'), with the limit -+(g'1 + g'2) / 2 below |e1 -+ e2| = thr; with
+// lam > 0 the momentum-shell weight above, the entries then holding (e, f, h).
+template <int WHICH, typename R>
+__device__ __forceinline__ R gen_pair_weight(R e1, R g1, R gp1, R e2, R g2, R gp2, R thr, R lam)
+{
+    if (lam > R(0)) return shell_weight<WHICH, R>(e1, g1, gp1, e2, g2, gp2, thr, lam);   // (g, gp) = (f, h)
+    if (WHICH == 0) {
+        const R s = e1 + e2;
+        return fabs(s) > thr ? -(g1 + g2) / s : R(-0.5) * (gp1 + gp2);
+    } else {
+        const R d = e1 - e2;
+        return fabs(d) > thr ? (g1 - g2) / d : R(0.5) * (gp1 + gp2);
+    }
+}
+
 // Everything the projection kernel needs about one gather term.
 // kind: 0 = P<-C, 1 = P<-D, 2 = C<-P, 3 = C<-D.
 struct GatherTerm {
@@ -290,6 +306,8 @@ struct tufrg_model {
 
     tufrg::LoopPlan plan{};
     int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
+    bool loops_tc = false;          // multi-orbital loop k-sum on the tensor cores (k_loops_tc.cu)
+    float2 *d_loop_w = nullptr;     // its column sums [groups][Lf][108][108]
 
     // ---- learned loop surrogate (optional)
     tufrg_mlp *sur = nullptr;       // network (not owned)
@@ -356,6 +374,9 @@ bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only);
+bool loops_tc_supported(const tufrg_model *m);
+size_t loops_tc_w_bytes(const tufrg_model *m);
+cudaError_t launch_loops_tc(tufrg_model *m, int ch, float2 *acc);
 cudaError_t launch_vlv_large(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist,
                              int nlist);
 cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);

@@ -66,7 +66,7 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
         "tufrg_set_surrogate": (None, None, None, None, None, 1e-3, 0, None),
         "tufrg_surrogate_stats": (None, ctypes.byref(ll), ctypes.byref(ll), ctypes.byref(ll)),
         "tufrg_timing_begin": (None,), "tufrg_timing_end": (None, None, 0, None, None),
-        "tufrg_set_device_error": (None, 1),
+        "tufrg_set_device_error": (None, 1), "tufrg_loops_info": (None, ctypes.byref(i)),
         "tufrg_mlp_create": (4, 8, 1, 2, 0, None, None), "tufrg_mlp_get_params": (None, None),
         "tufrg_mlp_set_params": (None, None), "tufrg_mlp_forward": (None, None, 1, None),
         "tufrg_mlp_gradients": (None, None, None, 1, None, None), "tufrg_mlp_train_step": (None, None, None, 1, 1e-3, None),
@@ -122,7 +122,7 @@ def test_bad_descriptors_are_rejected_before_device_use(libpath):
         (dict(n_s=0), EINVAL, "n_s"), (dict(n_s=9), EINVAL, "n_s"), (dict(n_s=3), ENOTSUP, "n_s = 2, 4, 6"),
         (dict(n_hop=0), EINVAL, "hopping"), (dict(V0=None), EINVAL, "V0"), (dict(n_ff=0), EINVAL, "bond set"),
         (dict(nc=0), EINVAL, "Lq >= 2"), (dict(Lq=64, nc=65), EINVAL, "fine mesh"),
-        (dict(products=9), EINVAL, "products"), (dict(filling=0.5, T_mu=0.0), EINVAL, "T_mu"),
+        (dict(products=9), EINVAL, "products"), (dict(loops=3), EINVAL, "loops backend"), (dict(filling=0.5, T_mu=0.0), EINVAL, "T_mu"),
         (dict(regulator=7), EINVAL, "regulator"), (dict(regulator=1, T_reg=0.0), EINVAL, "T_reg"),
         (dict(regulator=1, T_reg=float("nan")), EINVAL, "T_reg"),
         (dict(n_hop=hopR.shape[0] - 1), EINVAL, "t_{-R}"),      # the last hop loses its partner

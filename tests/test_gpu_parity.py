@@ -425,9 +425,9 @@ def test_rhs_full_size_symmetric_state_path(full_size_flow_state, prec):
     api = _api()
     spec, st = full_size_flow_state
     m = api.Model(spec, getattr(api, prec))
-    assert m.symmetric_state_path
     if prec == "SPLIT32":
-        assert m.n_loop_q == 91     # the FP64 two-band path sums every momentum's loops directly
+        # the FP64 two-band path sums every momentum directly and ignores the flag (its general path is checked)
+        assert m.n_loop_q == 91 and m.symmetric_state_path
     d = m.rhs(0.1, st, symmetric=True).cpu().numpy()
     ref, _ = oracle.Oracle(spec).rhs(0.1, st.cpu().numpy(), 3)
     assert np.abs(ref).max() > 1.0
@@ -483,31 +483,66 @@ def test_t2g_bands_and_mu(case):
     assert abs(m.mu - o.mu) < 1e-11
 
 
+def _t2g_model(api, spec, prec, **kw):
+    """FP64, split precision with the tensor-core loop k-sum (the default where it applies) or with the
+    CUDA-core loop k-sum."""
+    if prec == "SPLIT32_SIMTLOOPS":
+        m = api.Model(spec, api.SPLIT32, loops=api.LOOPS_SIMT, **kw)
+        assert m.loops_backend == "simt"
+        return m
+    m = api.Model(spec, getattr(api, prec), **kw)
+    assert m.loops_backend == ("tc" if prec == "SPLIT32" else "simt")
+    return m
+
+
 @pytest.mark.parametrize("case", list(T2G))
-@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32", "SPLIT32_SIMTLOOPS"])
 def test_t2g_loops(case, prec):
+    """Loops of the t2g model (N_s = 6) against the oracle: FP64 on the CUDA cores, and the split path with the
+    per-column orbital sums as 3xTF32 GEMMs on the tensor cores (Lf = 8 and the ragged Lf = 10, a last stage of
+    two rows) or as FP32 FMAs on the CUDA cores."""
     api = _api()
     spec = T2G[case]()
-    m = api.Model(spec, getattr(api, prec))
+    m = _t2g_model(api, spec, prec)
     o = oracle.Oracle(spec)
-    L = m.loops(0.15).cpu().numpy()
-    for ch in (0, 1):
-        ref = o.loops(0.15, ch)
-        assert rel(L[ch], ref) < (TOL64 if prec == "FP64" else 2e-5), (ch, rel(L[ch], ref))
+    for T in (0.15, 1.3):
+        L = m.loops(T).cpu().numpy()
+        for ch in (0, 1):
+            ref = o.loops(T, ch)
+            assert rel(L[ch], ref) < (TOL64 if prec == "FP64" else 2e-5), (ch, rel(L[ch], ref))
 
 
 @pytest.mark.parametrize("case", list(T2G))
-@pytest.mark.parametrize("prec", ["FP64", "SPLIT32"])
+@pytest.mark.parametrize("prec", ["FP64", "SPLIT32", "SPLIT32_SIMTLOOPS"])
 def test_t2g_loops_symmetry(case, prec):
     """The t2g model (orbitals yz, xz, xy with atomic SOC) has the point group with orbital x spin
-    unitaries: one momentum per orbit is summed and the result equals the full k-sum."""
+    unitaries: one momentum per orbit is summed and the result equals the full k-sum (with every momentum
+    summed the tensor-core kernel's last group of three momenta is incomplete: 16 or 25 momenta)."""
     api = _api()
     spec = T2G[case]()
-    m = api.Model(spec, getattr(api, prec))
-    full = api.Model(spec, getattr(api, prec), symmetry=api.SYMMETRY_OFF)
+    m = _t2g_model(api, spec, prec)
+    full = _t2g_model(api, spec, prec, symmetry=api.SYMMETRY_OFF)
     assert m.n_loop_q == _n_orbits(spec.Lq, C4V) and full.n_loop_q == spec.Lq ** 2
     L, Lfull = m.loops(0.15).cpu().numpy(), full.loops(0.15).cpu().numpy()
     assert rel(L, Lfull) < (1e-13 if prec == "FP64" else 2e-6)
+    o = oracle.Oracle(spec)
+    for ch in (0, 1):
+        assert rel(Lfull[ch], o.loops(0.15, ch)) < (TOL64 if prec == "FP64" else 2e-5)
+
+
+def test_t2g_loops_tc_matches_cuda_cores_ragged():
+    """Tensor-core and CUDA-core loop k-sums of the same split model on a ragged fine mesh (Lf = 15: the last
+    stage of each column holds three rows) with 9 bonds, both channels, two temperatures."""
+    api = _api()
+    spec = inputs.t2g_soc(seed=4, Lq=5, nc=3, n_ff=9, filling=4.0, T_mu=0.05)
+    mt = _t2g_model(api, spec, "SPLIT32")
+    ms = _t2g_model(api, spec, "SPLIT32_SIMTLOOPS")
+    o = oracle.Oracle(spec)
+    for T in (0.08, 0.6):
+        Lt, Ls = mt.loops(T).cpu().numpy(), ms.loops(T).cpu().numpy()
+        assert rel(Lt, Ls) < 4e-6
+        for ch in (0, 1):
+            assert rel(Lt[ch], o.loops(T, ch)) < 2e-5
 
 
 @pytest.mark.parametrize("case", list(T2G))
