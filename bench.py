@@ -263,9 +263,10 @@ def main():
     ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
     ap.add_argument("--profile-symmetric-states", action="store_true",
                     help="with --profile-rhs: force the orbit-representative projections and products")
-    ap.add_argument("--profile-model", choices=["rashba", "t2g_q8"], default="rashba",
+    ap.add_argument("--profile-model", choices=["rashba", "t2g_q8", "t2g_q16"], default="rashba",
                     help="with --profile-rhs: the benchmark workload, or t2g + SOC at 8x8 q / 6x6 k (a small case "
-                         "of the multi-orbital kernels for full profiler captures)")
+                         "of the multi-orbital kernels for full profiler captures), or t2g + SOC at 16x16 q / 12x12 k "
+                         "(the fine mesh of the 32x32 / 6x6 workload, Lf = 192, at a quarter of its momenta)")
     ap.add_argument("--batch-flows", type=int, default=0,
                     help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
@@ -297,8 +298,9 @@ def main():
         return
     if args.profile_rhs > 0:
         # a short, fixed launch sequence for profilers: model set-up, then N right-hand sides
-        spec = (inputs.rashba_q24_k8_ff9(0) if args.profile_model == "rashba"
-                else inputs.t2g_soc(0, Lq=8, nc=6, n_ff=9, filling=4.0, T_mu=0.05))
+        spec = {"rashba": lambda: inputs.rashba_q24_k8_ff9(0),
+                "t2g_q8": lambda: inputs.t2g_soc(0, Lq=8, nc=6, n_ff=9, filling=4.0, T_mu=0.05),
+                "t2g_q16": lambda: inputs.t2g_soc(0, Lq=16, nc=12, n_ff=9, filling=4.0, T_mu=0.05)}[args.profile_model]()
         m = Model(spec, SPLIT32 if args.profile_precision == "split" else FP64,
                   symmetry=SYMMETRY_STATES if args.profile_symmetric_states else SYMMETRY_AUTO)
         st = torch.from_numpy(inputs.random_state(spec, seed=1, scale=0.2)).cuda()

@@ -16,12 +16,12 @@
 // V.L.V products.  The x phases e^{-+ i kx dx} are applied afterwards by loops_tc_xsum over the written columns.
 //
 // One persistent CTA per SM walks its (momentum group, column) items.  Warp roles:
-//   warps 0-7   producers: per stage (4 ky rows = K of 24) they stage the raw eigenvectors and Fermi entries of
-//               the 4 summation points and their 12 partners (cp.async, one stage ahead), form the pair weights,
-//               then write the operands' TF32 hi/lo planes in the K-major core-matrix layout (each thread one
-//               row of A and one row of B for two ky rows);
-//   warp 8      TMEM allocation and the MMA issuer (one thread): 36 MMAs per stage;
-//   warps 9-12  epilogue: tensor memory -> W in global memory (coalesced, row index fastest).
+//   warps 0-15  producers: per stage (4 ky rows = K of 24) they stage the raw eigenvectors and Fermi entries of
+//               the 4 summation points and their 12 partners (cp.async, two stages ahead, four buffers), form
+//               the pair weights and row phases, then write the operands' TF32 hi/lo planes in the K-major
+//               core-matrix layout (each thread one ky row of one row of A and of B);
+//   warp 16     TMEM allocation and the MMA issuer (one thread): 36 MMAs per stage;
+//   warps 17-20 epilogue: tensor memory -> W in global memory (coalesced, row index fastest).
 // Two stage buffers (mbarriers full / empty) and two tensor-memory accumulators (mbarriers acc_full / acc_empty),
 // so operand generation, MMAs and the epilogue of the previous column overlap.  Every wait is bounded; on time-out
 // the kernel raises the error flag, every role stops, the MMAs in flight are waited for (bounded), the
@@ -44,9 +44,10 @@ constexpr int TM = 128;                      // MMA M
 constexpr int TN = 112;                      // MMA N: COLS padded to a multiple of 16
 constexpr int KB = 4;                        // ky rows per stage
 constexpr int KST = KB * NS;                 // K per stage: 24 = three MMA K-steps of 8
-constexpr int NPROD = 256;                   // producer threads, warps 0-7
-constexpr int MMA_WARP = 8;                  // warps 9-12: epilogue
-constexpr int NTHREADS = 13 * 32;
+constexpr int NPROD = 512;                   // producer threads, warps 0-15: thread (ky row kb, operand row r)
+constexpr int MMA_WARP = 16;                 // warps 17-20: epilogue
+constexpr int NTHREADS = 21 * 32;
+constexpr int NRAW = 4;                      // raw staging buffers (stage n + 2 is fetched while n is formed)
 constexpr unsigned A_PLANE = TM * KST * 4, B_PLANE = TN * KST * 4;   // bytes per plane and stage
 constexpr unsigned STAGE_BYTES = 4 * (A_PLANE + B_PLANE);           // planes: Re hi, Re lo, Im hi, Im lo
 constexpr int NPTS = KB * (1 + GRP);         // raw points per stage: 4 summation points, then [j][kb] partners
@@ -54,7 +55,7 @@ constexpr int CU = NS2 * 8 / 16, CF = NS * 16 / 16, CP = CU + CF;   // 16-byte c
 constexpr unsigned RAW_U = NPTS * NS2 * 8, RAW_BYTES = RAW_U + NPTS * NS * 16;
 constexpr unsigned TMEM_COLS = 512;          // accumulator c: Re at 256 c, Im at 256 c + 128
 constexpr unsigned SW_BYTES = GRP * KB * NS * 8 * 4;         // pair weights, rows padded to 8
-constexpr size_t SMEM_BYTES = 2 * (size_t)STAGE_BYTES + 2 * (size_t)RAW_BYTES + SW_BYTES + KB * NDYM * 8 + 2 * NPTS * 4;
+constexpr size_t SMEM_BYTES = 2 * (size_t)STAGE_BYTES + NRAW * (size_t)RAW_BYTES + SW_BYTES + KB * NDYM * 8 + 4 * NPTS * 4;
 
 struct LtArgs {
     const float2 *U;            // [Nk][NS][NS] eigenvectors (row orbital, column band), FP32
@@ -102,21 +103,52 @@ __device__ __forceinline__ float tc_pair_weight(float e1, float g1, float gp1, f
     return fabsf(d) > thr ? __fdividef(g1 - g2, d) : 0.5f * (gp1 + gp2);
 }
 
-__device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
+// TF32 part of x by truncation (the 13 low mantissa bits cleared; one logic operation): x - hi is exact and below
+// 2^-10 |x|, so hi + lo keeps FP32 accuracy through the three products of 3xTF32
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 // writes 4 consecutive K values of one row of a plane group (Re hi, Re lo, Im hi, Im lo) as TF32 hi / lo parts
 __device__ __forceinline__ void put4(float *planes, unsigned plane_floats, int off, float2 v0, float2 v1, float2 v2, float2 v3)
 {
     float4 h, l;
-    h = make_float4(tc::tf32_hi(v0.x), tc::tf32_hi(v1.x), tc::tf32_hi(v2.x), tc::tf32_hi(v3.x));
+    h = make_float4(tf32_trunc(v0.x), tf32_trunc(v1.x), tf32_trunc(v2.x), tf32_trunc(v3.x));
     l = make_float4(v0.x - h.x, v1.x - h.y, v2.x - h.z, v3.x - h.w);
     *reinterpret_cast<float4 *>(planes + 0 * plane_floats + off) = h;
     *reinterpret_cast<float4 *>(planes + 1 * plane_floats + off) = l;
-    h = make_float4(tc::tf32_hi(v0.y), tc::tf32_hi(v1.y), tc::tf32_hi(v2.y), tc::tf32_hi(v3.y));
+    h = make_float4(tf32_trunc(v0.y), tf32_trunc(v1.y), tf32_trunc(v2.y), tf32_trunc(v3.y));
     l = make_float4(v0.y - h.x, v1.y - h.y, v2.y - h.z, v3.y - h.w);
     *reinterpret_cast<float4 *>(planes + 2 * plane_floats + off) = h;
     *reinterpret_cast<float4 *>(planes + 3 * plane_floats + off) = l;
 }
+
+// two consecutive K values (an even k) of one row
+__device__ __forceinline__ void put2(float *planes, unsigned plane_floats, int off, float2 v0, float2 v1)
+{
+    float2 h, l;
+    h = make_float2(tf32_trunc(v0.x), tf32_trunc(v1.x));
+    l = make_float2(v0.x - h.x, v1.x - h.y);
+    *reinterpret_cast<float2 *>(planes + 0 * plane_floats + off) = h;
+    *reinterpret_cast<float2 *>(planes + 1 * plane_floats + off) = l;
+    h = make_float2(tf32_trunc(v0.y), tf32_trunc(v1.y));
+    l = make_float2(v0.y - h.x, v1.y - h.y);
+    *reinterpret_cast<float2 *>(planes + 2 * plane_floats + off) = h;
+    *reinterpret_cast<float2 *>(planes + 3 * plane_floats + off) = l;
+}
+
+// the six K values kb * 6 + l (l = 0..5) of row r of an R-row operand: 4 + 2 or 2 + 4 along the 4-wide groups
+__device__ __forceinline__ void put6(float *planes, unsigned plane_floats, int r, int kb, int R, const float2 (&v)[NS])
+{
+    const int k0 = 6 * kb;
+    if ((kb & 1) == 0) {
+        put4(planes, plane_floats, tc::core_off(r, k0, R), v[0], v[1], v[2], v[3]);
+        put2(planes, plane_floats, tc::core_off(r, k0 + 4, R), v[4], v[5]);
+    } else {
+        put2(planes, plane_floats, tc::core_off(r, k0, R), v[0], v[1]);
+        put4(planes, plane_floats, tc::core_off(r, k0 + 2, R), v[2], v[3], v[4], v[5]);
+    }
+}
+
+__device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
 
 template <int WHICH>
 __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
@@ -125,9 +157,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
     // stage buffer b at smem + b STAGE_BYTES, raw buffer b at smem + 2 STAGE_BYTES + b RAW_BYTES
     auto stage = [&](int b) { return smem + (size_t)b * STAGE_BYTES; };
     auto raw = [&](int b) { return smem + 2 * (size_t)STAGE_BYTES + (size_t)b * RAW_BYTES; };
-    float *sW = reinterpret_cast<float *>(smem + 2 * STAGE_BYTES + 2 * RAW_BYTES);   // [GRP][KB][NS][8]
-    float2 *sPh = reinterpret_cast<float2 *>(smem + 2 * STAGE_BYTES + 2 * RAW_BYTES + SW_BYTES);   // [KB][NDYM]
-    int *sPt = reinterpret_cast<int *>(sPh + KB * NDYM);                                   // [2][NPTS]
+    float *sW = reinterpret_cast<float *>(smem + 2 * STAGE_BYTES + NRAW * RAW_BYTES);   // [GRP][KB][NS][8]
+    float2 *sPh = reinterpret_cast<float2 *>(smem + 2 * STAGE_BYTES + NRAW * RAW_BYTES + SW_BYTES);   // [KB][NDYM]
+    int *sPt = reinterpret_cast<int *>(sPh + KB * NDYM);                                   // [4][NPTS]
     __shared__ __align__(8) unsigned long long full[2], empty[2], accf[2], acce[2], done;
     __shared__ unsigned tmem_base;
     __shared__ int abort_flag, stop;
@@ -177,13 +209,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
         const bool shell = a.shell_T > 0.f;
         const float lam = shell ? (float)(*a.Tp) : 0.f;
         const float thr = a.thr_factor * (shell ? a.shell_T : (float)(*a.Tp));
-        const int half = tid >> 7, r = tid & 127;
+        const int kb = tid >> 7, r = tid & 127;   // ky row of the stage (warp-uniform) and operand row
         // fine-mesh index of raw point p of stage n (-1 when its row or momentum does not exist); evaluated once
-        // per stage and point, two stages ahead, into sPt
+        // per stage and point, three stages ahead, into sPt[n % 4]
         auto point = [&](int n, int p) {
             const int item = (int)blockIdx.x + (n / spc) * (int)gridDim.x, st = n % spc;
             const int g = item / Lf, kx = item % Lf;
-            const int kb = p & (KB - 1), ky = st * KB + kb;
+            const int pk = p & (KB - 1), ky = st * KB + pk;
             if (n >= n_stages || ky >= Lf) return -1;
             if (p < KB) return kx * Lf + ky;
             const int slot = g * GRP + (p - KB) / KB;
@@ -194,11 +226,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
         };
         auto fetch = [&](int n) {
             if (n < n_stages) {
-                unsigned char *rb = raw(n & 1);
-                const int *pts = sPt + (n & 1) * NPTS;
+                unsigned char *rb = raw(n % NRAW);
+                const int *pts = sPt + (n & 3) * NPTS;
                 for (int i = tid; i < NPTS * CP; i += NPROD) {
                     const int p = i / CP, c = i % CP, k = pts[p];
-                    if (k < 0) continue;
+                    if (k < 0) {   // a row or momentum that does not exist: zeros (no operand value then depends on it)
+                        unsigned char *d = c < CU ? rb + (size_t)p * NS2 * 8 + 16 * c : rb + RAW_U + (size_t)p * NS * 16 + 16 * (c - CU);
+                        *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        continue;
+                    }
                     if (c < CU) cp_async16(rb + (size_t)p * NS2 * 8 + 16 * c, reinterpret_cast<const char *>(Ug + (size_t)k * NS2) + 16 * c);
                     else cp_async16(rb + RAW_U + (size_t)p * NS * 16 + 16 * (c - CU),
                                     reinterpret_cast<const char *>(Fg + (size_t)k * NS) + 16 * (c - CU));
@@ -206,108 +242,111 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
             }
             cp_async_commit();
         };
-        if (tid < 2 * NPTS) sPt[tid] = point(tid / NPTS, tid % NPTS);
+        if (tid < 3 * NPTS) sPt[tid] = point(tid / NPTS, tid % NPTS);
         bar_producers();
         fetch(0);
+        fetch(1);
         int item = (int)blockIdx.x, st = 0;   // item and stage within the column of stage n
         for (int n = 0; n < n_stages; n++) {
             const int g = item / Lf;
             const int buf = n & 1;
-            bar_producers();          // every producer is done with the raw buffer of stage n - 1 and with sPt of n
-            fetch(n + 1);
-            cp_async_wait<1>();
-            bar_producers();          // the raw data of stage n has landed
-            const float2 *rU = reinterpret_cast<const float2 *>(raw(n & 1));
-            const FermiEntry32 *rF = reinterpret_cast<const FermiEntry32 *>(raw(n & 1) + RAW_U);
-            // pair weights [j][kb][l1][8] (rows padded to 8), the row phases [kb][dy] and the points of stage n + 2
-            for (int i = tid; i < GRP * KB * NS * NS; i += NPROD) {
-                const int j = i / (KB * NS * NS), kb = (i / (NS * NS)) % KB, l1 = (i / NS) % NS, l2 = i % NS;
-                const int pp = KB + j * KB + kb;
+            // raw buffer (n + 2) % 4 was last read by stage n - 2, which every producer has finished
+            fetch(n + 2);
+            cp_async_wait<2>();
+            bar_producers();          // raw data of stage n landed; stage n - 1 fully formed (sW, sPh, sPt free)
+            const float2 *rU = reinterpret_cast<const float2 *>(raw(n % NRAW));
+            const FermiEntry32 *rF = reinterpret_cast<const FermiEntry32 *>(raw(n % NRAW) + RAW_U);
+            // pair weights [j][kb][l1][8] (rows padded to 8), the row phases [kb][dy] and the points of stage n + 3
+            if (tid < GRP * KB * NS * NS) {
+                const int i = tid, j = i / (KB * NS * NS), wk = (i / (NS * NS)) % KB, l1 = (i / NS) % NS, l2 = i % NS;
+                const int pp = KB + j * KB + wk;
                 float w = 0.f;
-                if (st * KB + kb < Lf && g * GRP + j < n_slot) {
-                    const FermiEntry32 f1 = rF[kb * NS + l1], f2 = rF[pp * NS + l2];
+                if (st * KB + wk < Lf && g * GRP + j < n_slot) {
+                    const FermiEntry32 f1 = rF[wk * NS + l1], f2 = rF[pp * NS + l2];
                     w = tc_pair_weight<WHICH>(f1.e, f1.g, f1.gp, f2.e, f2.g, f2.gp, thr, lam);
                 }
-                sW[((j * KB + kb) * NS + l1) * 8 + l2] = w;
-            }
-            if (tid >= NPROD - KB * NDYM) {
-                const int i = tid - (NPROD - KB * NDYM), kb = i / NDYM, dyi = i % NDYM, ky = st * KB + kb;
+                sW[((j * KB + wk) * NS + l1) * 8 + l2] = w;
+            } else if (tid >= NPROD - KB * NDYM) {
+                const int i = tid - (NPROD - KB * NDYM), pk = i / NDYM, dyi = i % NDYM, ky = st * KB + pk;
                 const int dyv = dyi == 0 ? a.dys[0] : dyi == 1 ? a.dys[1] : a.dys[2];
                 float sn = 0.f, cs = 0.f;
                 if (ky < Lf && dyi < a.ndyh) sincospif(2.0f * (float)wrapm(ky * dyv, Lf) / (float)Lf, &sn, &cs);
                 sPh[i] = make_float2(cs, WHICH == 0 ? sn : -sn);   // zero for missing rows and y components
             } else if (tid >= NPROD - KB * NDYM - NPTS) {
                 const int p = tid - (NPROD - KB * NDYM - NPTS);
-                sPt[(n & 1) * NPTS + p] = point(n + 2, p);
+                sPt[((n + 3) & 3) * NPTS + p] = point(n + 3, p);
             }
-            if (tid == 0) {
-                // the MMAs that read this stage buffer two stages ago must be complete
-                if (n >= 2 && !tc::mbar_wait_or_abort(tc::smem_u32(&empty[buf]), ((n >> 1) - 1) & 1, &abort_flag)) {
-                    atomicExch(&abort_flag, 1);
-                    atomicExch(a.err, 1);
-                }
-                stop = *(volatile int *)&abort_flag;
-            }
+            if (tid == 0) stop = *(volatile int *)&abort_flag;
             bar_producers();
-            if (stop) break;
+            if (stop) break;   // every producer reads the same value: they leave the loop together
             float *pa = reinterpret_cast<float *>(stage(buf)), *pb = pa + 4 * (A_PLANE / 4);
+            float2 va[NS], vb[NS];
             if (r < ROWS) {
-                // A row r = (dy, t1 t3): e^{-+ i ky dy} rho^l_{t1 t3}(k) at K = kb * 6 + l
-                const int dyi = r / NS2, ab = r % NS2, t1 = ab / NS, t3 = ab % NS;
-                float2 v[12];
-#pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    const int kb = 2 * half + q;
+                // A row r = (dy, t1 t3): e^{-+ i ky dy} rho^l_{t1 t3}(k) at K = kb * 6 + l (zero for a missing row: the
+                // phase is zero there, and so are the raw values of a point that does not exist)
+                {
+                    const int dyi = r / NS2, ab = r % NS2, t1 = ab / NS, t3 = ab % NS;
                     const float2 ph = sPh[kb * NDYM + dyi];
                     float2 u[NS], w[NS];
                     ld6(rU + kb * NS2 + t1 * NS, u);
                     ld6(rU + kb * NS2 + t3 * NS, w);
 #pragma unroll
                     for (int l = 0; l < NS; l++) {
-                        // rho = u conj(w); a point that was not fetched has ph = 0 and must not reach the product
-                        const float2 rho = make_float2(u[l].x * w[l].x + u[l].y * w[l].y, u[l].y * w[l].x - u[l].x * w[l].y);
-                        const bool ok = ph.x != 0.f || ph.y != 0.f;
-                        v[q * NS + l] = ok ? make_float2(ph.x * rho.x - ph.y * rho.y, ph.x * rho.y + ph.y * rho.x)
-                                           : make_float2(0.f, 0.f);
+                        // rho = u conj(w) = u w.x + (u.y, -u.x) w.y;  ph rho = rho ph.x + (-rho.y, rho.x) ph.y
+                        const float2 rho = __ffma2_rn(make_float2(u[l].y, -u[l].x), make_float2(w[l].y, w[l].y),
+                                                      __fmul2_rn(u[l], make_float2(w[l].x, w[l].x)));
+                        va[l] = __ffma2_rn(make_float2(-rho.y, rho.x), make_float2(ph.y, ph.y),
+                                           __fmul2_rn(rho, make_float2(ph.x, ph.x)));
                     }
                 }
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    put4(pa, A_PLANE / 4, tc::core_off(r, 12 * half + 4 * c, TM), v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-                // B row r = (s_j, t2 t4): T^l_{t2 t4} = sum_l2 w_{l l2} rho'^{l2}_{t2 t4} at K = kb * 6 + l
-                const int j = r / NS2, cd = r % NS2, t2 = cd / NS, t4 = cd % NS;
-#pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    const int kb = 2 * half + q, pp = KB + j * KB + kb;
-                    const bool ok = st * KB + kb < Lf && g * GRP + j < n_slot;
+                // B row r = (s_j, t2 t4): T^l_{t2 t4} = sum_l2 w_{l l2} rho'^{l2}_{t2 t4} at K = kb * 6 + l (the weights
+                // of a missing row or momentum are zero)
+                {
+                    const int j = r / NS2, cd = r % NS2, t2 = cd / NS, t4 = cd % NS, pp = KB + j * KB + kb;
                     float2 x[NS], y[NS];
                     ld6(rU + pp * NS2 + t2 * NS, x);
                     ld6(rU + pp * NS2 + t4 * NS, y);
                     float2 rho[NS];
 #pragma unroll
                     for (int l2 = 0; l2 < NS; l2++)
-                        rho[l2] = WHICH == 0 ? make_float2(x[l2].x * y[l2].x + x[l2].y * y[l2].y, x[l2].y * y[l2].x - x[l2].x * y[l2].y)    // x conj(y)
-                                             : make_float2(x[l2].x * y[l2].x + x[l2].y * y[l2].y, x[l2].x * y[l2].y - x[l2].y * y[l2].x);   // conj(x) y
+                        rho[l2] = WHICH == 0
+                                      // x conj(y) = x y.x + (x.y, -x.x) y.y
+                                      ? __ffma2_rn(make_float2(x[l2].y, -x[l2].x), make_float2(y[l2].y, y[l2].y),
+                                                   __fmul2_rn(x[l2], make_float2(y[l2].x, y[l2].x)))
+                                      // conj(x) y = y x.x + (y.y, -y.x) x.y
+                                      : __ffma2_rn(make_float2(y[l2].y, -y[l2].x), make_float2(x[l2].y, x[l2].y),
+                                                   __fmul2_rn(y[l2], make_float2(x[l2].x, x[l2].x)));
 #pragma unroll
                     for (int l1 = 0; l1 < NS; l1++) {
                         const float4 w0 = *reinterpret_cast<const float4 *>(sW + ((j * KB + kb) * NS + l1) * 8);
                         const float2 w1 = *reinterpret_cast<const float2 *>(sW + ((j * KB + kb) * NS + l1) * 8 + 4);
                         const float wl[NS] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
-                        float2 t = make_float2(0.f, 0.f);
+                        float2 t = __fmul2_rn(make_float2(wl[0], wl[0]), rho[0]);
 #pragma unroll
-                        for (int l2 = 0; l2 < NS; l2++) {
-                            t.x = fmaf(wl[l2], rho[l2].x, t.x);
-                            t.y = fmaf(wl[l2], rho[l2].y, t.y);
-                        }
-                        v[q * NS + l1] = ok ? t : make_float2(0.f, 0.f);
+                        for (int l2 = 1; l2 < NS; l2++) t = __ffma2_rn(make_float2(wl[l2], wl[l2]), rho[l2], t);
+                        vb[l1] = t;
                     }
                 }
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    put4(pb, B_PLANE / 4, tc::core_off(r, 12 * half + 4 * c, TN), v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
             }
-            tc::fence_smem_async();
-            tc::mbar_arrive(tc::smem_u32(&full[buf]));
+            // the MMAs that read this stage buffer two stages ago must be complete before it is overwritten
+            int ok = 1;
+            if (n >= 2 && lane == 0)
+                ok = tc::mbar_wait_or_abort(tc::smem_u32(&empty[buf]), ((n >> 1) - 1) & 1, &abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                // raise the flag and keep the producers in step: all of them leave at the next stage's check
+                if (lane == 0) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(a.err, 1);
+                }
+            } else {
+                if (r < ROWS) {
+                    put6(pa, A_PLANE / 4, r, kb, TM, va);
+                    put6(pb, B_PLANE / 4, r, kb, TN, vb);
+                }
+                tc::fence_smem_async();
+                tc::mbar_arrive(tc::smem_u32(&full[buf]));
+            }
             if (++st == spc) {
                 st = 0;
                 item += (int)gridDim.x;
@@ -440,17 +479,25 @@ __global__ void loops_tc_xsum(XsArgs x)
         inc[xi] = xi < x.ndx ? ((x.dxs[xi] % Lf) + Lf) % Lf : 0;
     }
     const float2 *w = x.W + (size_t)g * Lf * COLS * ROWS + (size_t)j * ROWS + r;
-    for (int kx = 0; kx < Lf; kx++) {
-        const float2 v = w[(size_t)kx * COLS * ROWS];
+    constexpr int UB = 8;   // columns loaded ahead (independent loads in flight)
+    for (int kx0 = 0; kx0 < Lf; kx0 += UB) {
+        float2 vb[UB];
 #pragma unroll
-        for (int xi = 0; xi < 9; xi++) {
-            if (xi >= x.ndx) break;
-            float2 p = ptab[ix[xi]];
-            if (WHICH == 0) p.y = -p.y;
-            acc[xi].x = fmaf(p.x, v.x, fmaf(-p.y, v.y, acc[xi].x));
-            acc[xi].y = fmaf(p.x, v.y, fmaf(p.y, v.x, acc[xi].y));
-            ix[xi] += inc[xi];
-            if (ix[xi] >= Lf) ix[xi] -= Lf;
+        for (int u = 0; u < UB; u++) vb[u] = kx0 + u < Lf ? w[(size_t)(kx0 + u) * COLS * ROWS] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < UB; u++) {
+            if (kx0 + u >= Lf) break;
+            const float2 v = vb[u];
+#pragma unroll
+            for (int xi = 0; xi < 9; xi++) {
+                if (xi >= x.ndx) break;
+                float2 p = ptab[ix[xi]];
+                if (WHICH == 0) p.y = -p.y;
+                acc[xi].x = fmaf(p.x, v.x, fmaf(-p.y, v.y, acc[xi].x));
+                acc[xi].y = fmaf(p.x, v.y, fmaf(p.y, v.x, acc[xi].y));
+                ix[xi] += inc[xi];
+                if (ix[xi] >= Lf) ix[xi] -= Lf;
+            }
         }
     }
     int sx = 0, sy = 0;
