@@ -208,6 +208,199 @@ def run_products_sweep(args):
                       "note": "products phase of one right-hand side (both channels, packing included), CUDA events"}))
 
 
+def loops_tc_tensor_flop(n_direct, Lf, Nk, ndyh):
+    """3xTF32 work of one launch of the tensor-core loop k-sum (N_s = 6): executed = MMAs as issued (128 x 112 x 8
+    per instruction, 36 per stage of 4 fine-mesh rows, stages padded to 4 rows, groups of 3 momenta padded to 3);
+    useful = the unpadded operands (3 dy x 36 rows, 3 momenta x 36 columns, K = 6 per fine point): per (q, k)
+    2 flop x 3 TF32 passes x 4 real products x (ndyh 36) x 36 x 6."""
+    groups = (n_direct + 2) // 3
+    stages = (Lf + 3) // 4
+    executed = float(groups) * Lf * stages * 36 * 2 * 128 * 112 * 8
+    useful = float(n_direct) * Nk * 2 * 3 * 4 * (ndyh * 36) * 36 * 6
+    return executed, useful
+
+
+def time_rhs(m, T, state, out, k, stream, symmetric=True):
+    """Mean device milliseconds of k right-hand sides (CUDA events on the model's stream), after two warm-ups."""
+    import torch
+    for _ in range(2):
+        m.rhs(T, state, out=out, symmetric=symmetric)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        m.rhs(T, state, out=out, symmetric=symmetric)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def run_config_t2g(stream, peaks, fp32_peak, seed=0, k=10):
+    """Three-orbital t2g + SOC (N_s = 6, M = 324), 32x32 q / 6x6 k per cell, split precision: RHS/s at T = 0.1 on
+    the mid-flow state, the loop k-sum's roofline counted both ways (the method's complex FP32 work, and the
+    3xTF32 MMA work of the tensor-core kernel), the products' roofline, and the split-vs-FP64 error."""
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300 import inputs
+    from paper_1710_08830_gb300.api import FP64, SPLIT32, Model
+    spec = inputs.t2g_q32_k6_ff9(seed)
+    t0 = time.perf_counter()
+    m = Model(spec, SPLIT32, stream=stream)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    state, rf = m.flow(T_end=T_BENCH, stop=1e9)
+    out = torch.empty_like(state)
+    ms = time_rhs(m, T_BENCH, state, out, k, stream)
+    m.timing_begin()
+    for _ in range(3):
+        m.rhs(T_BENCH, state, out=out, symmetric=True)
+    ph, _, nloop = m.timing_end()
+    ph = {kk: v / 3 for kk, v in ph.items()}
+    loop_ms = ph["loops"] * 3 / max(1, nloop)
+    ndyh = int(sum(1 for d in np.unique(spec.ff_R[:, 1][:, None] - spec.ff_R[:, 1][None, :]) if d >= 0))
+    unit = spec.n_s ** 4 + spec.n_s ** 5 + ndyh * spec.n_s ** 4
+    fp32_flop = 8.0 * m.n_loop_q * spec.Nk * unit
+    tf32 = tf32_peak_tflops(peaks)
+    loops = {"kernel": "loops_tc_kernel" if m.loops_backend == "tc" else "loops_gen_kernel",
+             "backend": m.loops_backend, "avg_launch_ms": loop_ms,
+             "units_per_launch": f"{m.n_loop_q} directly summed q x {spec.Nk} k",
+             "method_fp32": {"unit_work": f"(N_s^4 + N_s^5 + {ndyh} N_s^4) = {unit} complex FMA per (q, k)",
+                             "achieved_tflops": fp32_flop / (loop_ms * 1e-3) / 1e12, "peak_tflops": fp32_peak,
+                             "frac": fp32_flop / (loop_ms * 1e-3) / 1e12 / fp32_peak,
+                             "note": "the method's complex FP32 work against the FP32 FMA peak (the count used for the "
+                                     "CUDA-core kernel)"}}
+    if m.loops_backend == "tc":
+        ex, us = loops_tc_tensor_flop(m.n_loop_q, spec.Lf, spec.Nk, ndyh)
+        loops["tensor_3xtf32"] = {
+            "bound": "tensor", "peak_tflops": tf32, "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
+            "executed_tflops": ex / (loop_ms * 1e-3) / 1e12, "executed_frac": ex / (loop_ms * 1e-3) / 1e12 / tf32,
+            "useful_tflops": us / (loop_ms * 1e-3) / 1e12, "useful_frac": us / (loop_ms * 1e-3) / 1e12 / tf32,
+            "note": "executed counts the MMAs as issued (padded 128 x 112 tiles), useful the unpadded 108 x 108 operands; "
+                    "three TF32 passes per real product, four real products per complex one"}
+    n_products = m.n_loop_q if m.symmetric_state_path else spec.Nq
+    prod = None
+    if m.products == "tc":
+        fl = products_tf32_flop(spec.M, n_products)
+        prod = {"bound": "tensor", "kernel": "tc_cgemm_kernel + operand packing (tcgen05, 3xTF32)", "phase_ms": ph["vlv"],
+                "tf32_3pass_tflops": fl / (ph["vlv"] * 1e-3) / 1e12, "frac_tf32_3pass": fl / (ph["vlv"] * 1e-3) / 1e12 / tf32,
+                "method_complex_fp32_tflops": fl / 3 / (ph["vlv"] * 1e-3) / 1e12,
+                "frac_method_of_tf32_peak": fl / 3 / (ph["vlv"] * 1e-3) / 1e12 / tf32,
+                "work": f"2 channels x 2 complex M^3 GEMMs per multiplied momentum ({n_products} of {spec.Nq}); the "
+                        "3-pass count multiplies by the three TF32 products"}
+    # accuracy: the same state through the plain FP64 path (one right-hand side)
+    m64 = Model(spec, FP64, stream=stream)
+    d64 = m64.rhs(T_BENCH, state).cpu().numpy()
+    d32 = m.rhs(T_BENCH, state, symmetric=True).cpu().numpy()
+    err = float(np.abs(d32 - d64).max() / np.abs(d64).max())
+    del m64
+    m.close()
+    return {"workload": "t2g_soc_q32x32_k6x6_ff9", "Nq": spec.Nq, "Nk": spec.Nk, "M": spec.M, "n_s": spec.n_s,
+            "rhs_per_s": 1e3 / ms, "ms_per_rhs": ms, "init_s": init_s, "T": T_BENCH,
+            "phase_ms_per_rhs": ph, "roofline_loops": loops, "roofline_products": prod,
+            "split_vs_fp64_maxrel": err, "products": m.products, "loops_backend": m.loops_backend,
+            "flow_to_T_steps": rf["n_steps"], "note": "state: the split flow from T0 = 10 down to T = 0.1"}
+
+
+def flow_summary(r):
+    return {"wall_s": r["wall_s"], "Tc": r["Tc"], "crossed": r["crossed"], "n_rhs": r["n_rhs"], "n_steps": r["n_steps"],
+            "n_reject": r["n_reject"], "lead_channel": "PC"[r["lead_channel"]], "lead_q": r["lead_q"], "amax": r["amax"]}
+
+
+def run_config_hubbard(stream, k=50):
+    """Single-band Hubbard 8x8 q / 16x16 k per cell, N_ff = 5: split and FP64 RHS/s at T = 0.1 and the flows
+    T0 = 10 -> T_end = 0.02 of both (no crossing of max|A| = 50 above T_end: a time to T_end)."""
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300 import inputs
+    from paper_1710_08830_gb300.api import FP64, SPLIT32, Model
+    spec = inputs.hubbard_q8_k16_ff5()
+    res = {"workload": "hubbard_q8x8_k16x16_ff5", "Nq": spec.Nq, "Nk": spec.Nk, "M": spec.M}
+    states = {}
+    for name, prec in (("split", SPLIT32), ("fp64", FP64)):
+        t0 = time.perf_counter()
+        m = Model(spec, prec, stream=stream)
+        torch.cuda.synchronize()
+        init_s = time.perf_counter() - t0
+        st, _ = m.flow(T_end=T_BENCH, stop=1e9)
+        out = torch.empty_like(st)
+        ms = time_rhs(m, T_BENCH, st, out, k if name == "split" else 10, stream)
+        y, r = m.flow()
+        states[name] = y.cpu().numpy()
+        res[name] = {"rhs_per_s": 1e3 / ms, "init_s": init_s, "flow": flow_summary(r)}
+        m.close()
+    res["final_state_split_vs_fp64_maxrel"] = float(np.abs(states["split"] - states["fp64"]).max() /
+                                                    np.abs(states["fp64"]).max())
+    res["note"] = ("time to T_end = 0.02 (max|A| stays below the stop value 50); the flows integrate the same "
+                   "equations from T0 = 10 with rtol 1e-6")
+    return res
+
+
+def run_batch_flows(stream, n, seed=0):
+    """n uneven Rashba/Hubbard flows (Lq in {16, 24, 32, 48}, N_ff in {5, 9, 13}) through tufrg_flow_batch and one by
+    one, split precision; then the first crossing instance (smallest problem) again in FP64: its critical scale
+    and final state against the split flow."""
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300 import inputs
+    from paper_1710_08830_gb300.api import FP64, PRODUCTS_SIMT, SPLIT32, Model, flow_batch
+    specs = inputs.rashba_batch(seed=seed, n=n)
+    streams = [torch.cuda.Stream() for _ in specs]
+    models = [Model(sp, SPLIT32, stream=st, products=PRODUCTS_SIMT) for sp, st in zip(specs, streams)]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    rb = flow_batch(models)
+    t_batch = time.perf_counter() - t
+    del models
+    seq = []
+    t = time.perf_counter()
+    for sp in specs:
+        m = Model(sp, SPLIT32, products=PRODUCTS_SIMT)
+        _, r = m.flow(want_state=False)
+        seq.append(r)
+        m.close()
+    t_seq = time.perf_counter() - t
+    same = all(a["Tc"] == b["Tc"] and a["n_steps"] == b["n_steps"] for a, b in zip(rb, seq))
+    batch = {"instances": len(specs), "wall_s_batch": t_batch, "wall_s_one_by_one": t_seq,
+             "flows_per_s": len(specs) / t_batch, "speedup": t_seq / t_batch,
+             "rhs_total": int(sum(r["n_rhs"] for r in rb)), "crossed": int(sum(r["crossed"] for r in rb)),
+             "identical_to_single_flows": same,
+             "mix": {"Lq": sorted(set(sp.Lq for sp in specs)), "n_ff": sorted(set(sp.n_ff for sp in specs))}}
+    crossing = None
+    cand = [i for i, r in enumerate(rb) if r["crossed"]]
+    if cand:
+        i = min(cand, key=lambda j: specs[j].Nq * specs[j].Nk * specs[j].M)
+        sp = specs[i]
+        out = {}
+        for name, prec in (("split", SPLIT32), ("fp64", FP64)):
+            m = Model(sp, prec, stream=stream)
+            y, r = m.flow()
+            out[name] = (y.cpu().numpy(), r)
+            m.close()
+        y32, r32 = out["split"]
+        y64, r64 = out["fp64"]
+        # the vertex near the instability is ill-conditioned (it diverges at Lambda_c); compare the two flows also
+        # at a fixed scale above it, T_end = 1.25 Lambda_c (no stop)
+        above = {}
+        for name, prec in (("split", SPLIT32), ("fp64", FP64)):
+            m = Model(sp, prec, stream=stream)
+            y, r = m.flow(T_end=1.25 * r64["Tc"], stop=1e9)
+            above[name] = (y.cpu().numpy(), r)
+            m.close()
+        ya32, ya64 = above["split"][0], above["fp64"][0]
+        crossing = {"instance": i, "Lq": sp.Lq, "n_ff": sp.n_ff, "params": {k2: round(v, 6) for k2, v in sp.params.items()}
+                    if isinstance(sp.params, dict) else None,
+                    "split": flow_summary(r32), "fp64": flow_summary(r64),
+                    "lambda_c_ratio_split_over_fp64": r32["Tc"] / r64["Tc"],
+                    "final_vertex_split_vs_fp64_maxrel": float(np.abs(y32 - y64).max() / np.abs(y64).max()),
+                    "vertex_at_1p25_lambda_c_split_vs_fp64_maxrel": float(np.abs(ya32 - ya64).max() / np.abs(ya64).max()),
+                    "amax_at_1p25_lambda_c": above["fp64"][1]["amax"],
+                    "speedup_split_over_fp64": r64["wall_s"] / r32["wall_s"],
+                    "note": "max|A| crosses the stop value 50: Lambda_c interpolated in ln T; final_vertex compares the last "
+                            "accepted states (just past the crossing, where the vertex diverges and small differences "
+                            "grow), the second error the two flows stopped at T = 1.25 Lambda_c"}
+    return batch, crossing
+
+
 def run_reference(args, rank, world):
     """The CPU oracle, as it stands, on bounded samples of the same workload (rank 0 only)."""
     if rank != 0:
@@ -267,8 +460,11 @@ def main():
                     help="with --profile-rhs: the benchmark workload, or t2g + SOC at 8x8 q / 6x6 k (a small case "
                          "of the multi-orbital kernels for full profiler captures), or t2g + SOC at 16x16 q / 12x12 k "
                          "(the fine mesh of the 32x32 / 6x6 workload, Lf = 192, at a quarter of its momenta)")
-    ap.add_argument("--batch-flows", type=int, default=0,
-                    help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one")
+    ap.add_argument("--batch-flows", type=int, default=64,
+                    help="also run N uneven Rashba/Hubbard flows together (tufrg_flow_batch) and one by one, and the first "
+                         "crossing instance in FP64 (0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (t2g + SOC 32x32 / 6x6, Hubbard 8x8 / 16x16) in the JSON line")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rashba",
                     help="model configuration (default: the 24x24 / 8x8 Rashba-Hubbard benchmark workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path (and the accuracy check)")
@@ -329,8 +525,15 @@ def main():
         workload += "_shell"
         metric += " with the momentum-shell regulator (flow scale Lambda, T_reg = 0.05)"
     stream = torch.cuda.current_stream()
+    t_init = time.perf_counter()
     m32 = Model(spec, SPLIT32, stream=stream)
+    torch.cuda.synchronize()
+    init_s = {"split": time.perf_counter() - t_init}
+    t_init = time.perf_counter()
     m64 = None if args.no_fp64 else Model(spec, FP64, stream=stream)
+    torch.cuda.synchronize()
+    if m64 is not None:
+        init_s["fp64"] = time.perf_counter() - t_init
     # a mid-flow state: the split flow from T0 = 10 down to the benchmark temperature
     state, _ = m32.flow(T_end=T_BENCH, stop=1e9)
     out = torch.empty_like(state)
@@ -460,36 +663,21 @@ def main():
                     "n_steps": r["n_steps"], "lead_channel": "PC"[r["lead_channel"]], "lead_q": r["lead_q"],
                     "amax": r["amax"]}
         _, r32 = m32.flow()
-        flows = {"split": summary(r32),
-                 "note": "Tc is the crossing of max|A| = 50 when crossed == 1, else the end temperature 0.02"}
+        flows = {"split": summary(r32), "init_s": init_s,
+                 "note": "Tc is the crossing of max|A| = 50 when crossed == 1, else the end temperature 0.02 (a time to "
+                         "T_end); init_s is the model set-up (eigensystem, tables, autotuning), not part of wall_s"}
         if m64 is not None:
             _, r64 = m64.flow()
             flows["fp64"] = summary(r64)
-    batch = None
-    if args.batch_flows > 0:
-        from paper_1710_08830_gb300.api import flow_batch
-        specs = inputs.rashba_batch(seed=rank, n=args.batch_flows)
-        streams = [torch.cuda.Stream() for _ in specs]
-        models = [Model(sp, SPLIT32, stream=st, products=PRODUCTS_SIMT) for sp, st in zip(specs, streams)]
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        rb = flow_batch(models)
-        t_batch = time.perf_counter() - t
-        del models
-        seq = []
-        t = time.perf_counter()
-        for sp in specs:
-            m = Model(sp, SPLIT32, products=PRODUCTS_SIMT)
-            _, r = m.flow()
-            seq.append(r)
-            del m
-        t_seq = time.perf_counter() - t
-        same = all(a["Tc"] == b["Tc"] and a["n_steps"] == b["n_steps"] for a, b in zip(rb, seq))
-        batch = {"instances": len(specs), "wall_s_batch": t_batch, "wall_s_one_by_one": t_seq,
-                 "flows_per_s": len(specs) / t_batch, "speedup": t_seq / t_batch,
-                 "rhs_total": int(sum(r["n_rhs"] for r in rb)), "crossed": int(sum(r["crossed"] for r in rb)),
-                 "identical_to_single_flows": same,
-                 "mix": {"Lq": sorted(set(sp.Lq for sp in specs)), "n_ff": sorted(set(sp.n_ff for sp in specs))}}
+    batch = crossing = None
+    if args.batch_flows > 0 and args.workload == "rashba":
+        batch, crossing = run_batch_flows(stream, args.batch_flows, seed=rank)
+    configs = None
+    if not args.no_configs and args.workload == "rashba":
+        peaks0, _ = measured_peaks()
+        props0 = torch.cuda.get_device_properties(local)
+        fp32_peak0 = props0.multi_processor_count * 128 * 2 * peaks0.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        configs = {"t2g": run_config_t2g(stream, peaks0, fp32_peak0, seed=rank), "hubbard": run_config_hubbard(stream)}
     clocks = sampler.stop()
 
     # ---------------- roofline of the dominant kernel (the loop k-sum)
@@ -573,6 +761,8 @@ def main():
                                   if m32.products == "tc" else None),
             "cpu_baseline": cpu,
             "batch_flows": batch,
+            "flow_to_lambda_c": crossing,
+            "other_configs": configs,
             "band_basis": band,
             "clocks": clocks,
             "peaks_source": peak_src,
