@@ -256,6 +256,32 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
 enum { TUFRG_SYMMETRIC_STATE = 4 };
 tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate);
 
+/* ------------------------------------------------------------------------------------------
+ * The right-hand side split over shards of transfer momenta (one shard per GPU / rank).
+ * Loops, projections and products of a transfer momentum need only that momentum, except for the
+ * lattice Fourier transform of the exchange propagators to the bond classes R'' (Sec. 3.3, the
+ * transform after Eq. zw_1), X(R'') = (1/Nq) sum_u e^{i u.R''} X(u), a sum over the whole transfer mesh.
+ * A shard holds the state rows of its own momenta only, in list order: state_local [2][n_q][M][M]
+ * complex (channel, list position, layout of tufrg_rhs).  One evaluation is
+ *   1. tufrg_rhs_shard_transform: this shard's part of the transforms, d_xr [2][ncls][M][M] complex;
+ *   2. the caller sums d_xr over all shards (an all-reduce of 2 ncls M^2 complex numbers, e.g. NCCL);
+ *   3. tufrg_rhs_shard_finish: loops at the shard's momenta, projections from the summed transforms,
+ *      products: d_dstate_local [2][n_q][M][M], dX/dT of the shard's momenta in list order.
+ * With the shards partitioning the mesh, the rows equal those of tufrg_rhs.  h_q_list: n_q distinct
+ * momenta in [0, Nq) (host memory); the model keeps full-size work buffers, the shard's rows alone are
+ * read and written.  The loops are summed at the listed momenta (the FP64 two-band path sums every
+ * momentum); the general (not symmetric-state) path is taken; a model with an attached surrogate is
+ * refused (TUFRG_ENOTSUP).  Stream ordered, no host synchronisation beyond the list upload.
+ * Errors: TUFRG_EINVAL (NULL argument, bad list, T not positive and finite, bad mask), TUFRG_ENOTSUP,
+ * TUFRG_ENOMEM, TUFRG_ECUDA.
+ * ------------------------------------------------------------------------------------------ */
+/* Number of bond classes ncls of the transforms and, when h_cls is not NULL, the classes [ncls][2] (mod Lq). */
+tufrg_status tufrg_shard_classes(const tufrg_model *m, int *ncls, int *h_cls);
+tufrg_status tufrg_rhs_shard_transform(tufrg_model *m, const void *d_state_local, int n_q, const int *h_q_list,
+                                       int channel_mask, void *d_xr);
+tufrg_status tufrg_rhs_shard_finish(tufrg_model *m, double T, const void *d_state_local, int n_q, const int *h_q_list,
+                                    const void *d_xr, int channel_mask, void *d_dstate_local);
+
 /* Same right-hand side with host buffers: copies h_state to the device, evaluates,
  * copies dX/dT back into h_dstate and synchronises the stream.  Errors: those of tufrg_rhs, and
  * TUFRG_ETIMEOUT when a bounded device-side wait gave up (the device error flag is read after the sync). */

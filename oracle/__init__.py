@@ -97,6 +97,12 @@ def lib():
             L.or_band_transform.restype = None
             L.or_rhs.restype = d
             L.or_rhs_at.argtypes = [vp, vp, vp, d, vp, i, i, vp, vp]
+            L.or_shard_classes.argtypes = [vp, vp]
+            L.or_shard_classes.restype = i
+            L.or_shard_transform.argtypes = [vp, vp, i, vp, i, vp]
+            L.or_shard_transform.restype = None
+            L.or_shard_finish.argtypes = [vp, vp, vp, d, vp, i, vp, vp, i, vp]
+            L.or_shard_finish.restype = None
             L.or_flow.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_flow.restype = i
             L.or_num_threads.restype = i
@@ -248,6 +254,35 @@ class Oracle:
         out = np.zeros((2, sl.shape[0], s.M, s.M), np.complex128)
         lib().or_rhs_at(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, _ptr(state), chmask, sl.shape[0], _ptr(sl),
                         _ptr(out))
+        return out
+
+    # ------------------------------------------------------------ the right-hand side split over shards of momenta
+    def shard_classes(self) -> np.ndarray:
+        """Bond classes R'' (mod Lq) of the shard transforms, [ncls][2]."""
+        cls = np.zeros((4096, 2), np.int32)
+        n = lib().or_shard_classes(C.byref(self.m), _ptr(cls))
+        return cls[:n].copy()
+
+    def shard_transform(self, state_local: np.ndarray, q_list, chmask: int = 3) -> np.ndarray:
+        """This shard's part of the Fourier transform of Sec. 3.3: [2][ncls][M][M], summed over the listed momenta
+        (state_local [2][n][M][M] holds their rows in list order)."""
+        s = self.spec
+        ql = np.ascontiguousarray(q_list, np.int32)
+        st = np.ascontiguousarray(state_local, np.complex128)
+        ncls = self.shard_classes().shape[0]
+        out = np.zeros((2, ncls, s.M, s.M), np.complex128)
+        lib().or_shard_transform(C.byref(self.m), _ptr(st), ql.shape[0], _ptr(ql), chmask, _ptr(out))
+        return out
+
+    def shard_finish(self, T: float, state_local: np.ndarray, q_list, xr: np.ndarray, chmask: int = 3) -> np.ndarray:
+        """dX/dT of the listed momenta [2][n][M][M] from their rows and the transforms summed over all shards."""
+        s = self.spec
+        ql = np.ascontiguousarray(q_list, np.int32)
+        st = np.ascontiguousarray(state_local, np.complex128)
+        xr = np.ascontiguousarray(xr, np.complex128)
+        out = np.zeros((2, ql.shape[0], s.M, s.M), np.complex128)
+        lib().or_shard_finish(C.byref(self.m), _ptr(self.E), _ptr(self.U), T, _ptr(st), ql.shape[0], _ptr(ql), _ptr(xr),
+                              chmask, _ptr(out))
         return out
 
     def flow(self, T0=10.0, T_end=0.02, rtol=1e-6, atol=1e-8, h0=-0.05, stop=50.0, chmask=3,

@@ -536,15 +536,14 @@ typedef struct {
     cplx *Pr, *Cr;
 } proj_ctx;
 
-/* Fourier transforms of P and C to every bond class that can occur, plus bond look-ups */
-static void proj_prepare(const or_model *m, const double *state, int chmask, proj_ctx *c)
+/* The bond classes R'' and the bond look-ups of the projections; Pr, Cr allocated (zero), not yet filled */
+static void proj_tables(const or_model *m, int chmask, proj_ctx *c)
 {
-    int ns2 = m->ns * m->ns, nff = m->nff, M = nff * ns2, Lq = m->Lq, Nq = Lq * Lq;
+    int ns2 = m->ns * m->ns, nff = m->nff, M = nff * ns2, Lq = m->Lq;
     size_t M2 = (size_t)M * M;
     c->m = m;
     c->chmask = chmask;
-    c->P = (const cplx *)state;
-    c->C = c->P + (size_t)Nq * M2;
+    c->P = c->C = NULL;
     /* R'' classes modulo Lq that can give a non-zero term: differences of two bonds */
     c->cls = malloc(sizeof(int) * 2 * nff * nff);
     int ncls = 0;
@@ -558,11 +557,6 @@ static void proj_prepare(const or_model *m, const double *state, int chmask, pro
     c->ncls = ncls;
     c->Pr = calloc((size_t)ncls * M2, sizeof(cplx));
     c->Cr = calloc((size_t)ncls * M2, sizeof(cplx));
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int k = 0; k < ncls; k++) {
-        if (chmask & 1) dft_to_bond(m, c->P, c->cls[2 * k], c->cls[2 * k + 1], c->Pr + (size_t)k * M2);
-        if (chmask & 2) dft_to_bond(m, c->C, c->cls[2 * k], c->cls[2 * k + 1], c->Cr + (size_t)k * M2);
-    }
     /* bond look-ups (pure bookkeeping of which shifted bonds are in the set) */
     c->plus = malloc(sizeof(int) * nff * ncls);
     c->minus = malloc(sizeof(int) * nff * ncls);
@@ -586,20 +580,36 @@ static void proj_prepare(const or_model *m, const double *state, int chmask, pro
     }
 }
 
+/* Fourier transforms of P and C to every bond class that can occur, plus bond look-ups */
+static void proj_prepare(const or_model *m, const double *state, int chmask, proj_ctx *c)
+{
+    int M = m->nff * m->ns * m->ns, Nq = m->Lq * m->Lq;
+    size_t M2 = (size_t)M * M;
+    proj_tables(m, chmask, c);
+    c->P = (const cplx *)state;
+    c->C = c->P + (size_t)Nq * M2;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < c->ncls; k++) {
+        if (chmask & 1) dft_to_bond(m, c->P, c->cls[2 * k], c->cls[2 * k + 1], c->Pr + (size_t)k * M2);
+        if (chmask & 2) dft_to_bond(m, c->C, c->cls[2 * k], c->cls[2 * k + 1], c->Cr + (size_t)k * M2);
+    }
+}
+
 static void proj_free(proj_ctx *c)
 {
     free(c->Pr); free(c->Cr); free(c->cls); free(c->plus); free(c->minus); free(c->negminus); free(c->negcls);
     free(c->dcidx);
 }
 
-/* A_P(q) and A_C(q) of one transfer momentum; returns max |A| over both */
-static double proj_one(const proj_ctx *c, int q, cplx *AP, cplx *AC)
+/* A_P(q) and A_C(q) of one transfer momentum from its own state rows Pq = P(q), Cq = C(q) and the Fourier
+ * transforms in c; returns max |A| over both */
+static double proj_one(const proj_ctx *c, int q, const cplx *Pq, const cplx *Cq, cplx *AP, cplx *AC)
 {
     const or_model *m = c->m;
     int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = nff * ns2, Lq = m->Lq, ncls = c->ncls;
     size_t M2 = (size_t)M * M;
     const cplx *V0 = (const cplx *)m->V0;
-    const cplx *P = c->P, *C = c->C, *Pr = c->Pr, *Cr = c->Cr;
+    const cplx *Pr = c->Pr, *Cr = c->Cr;
     int i0 = ff_index_mod(m, 0, 0);
     int onP = c->chmask & 1, onC = (c->chmask >> 1) & 1;
     int qx = q / Lq, qy = q % Lq;
@@ -615,7 +625,7 @@ static double proj_one(const proj_ctx *c, int q, cplx *AP, cplx *AC)
                             /* ---- P channel entry (R,(s1,s2)),(R',(s4,s3)) ---- */
                             if (onP) {
                                 size_t row = (size_t)iR * ns2 + s1 * ns + s2, col = (size_t)iRp * ns2 + s4 * ns + s3;
-                                cplx val = v0 + P[(size_t)q * M2 + row * M + col];
+                                cplx val = v0 + Pq[row * M + col];
                                 if (onC) {
                                     for (int k = 0; k < ncls; k++) {
                                         int Ux = c->cls[2 * k], Uy = c->cls[2 * k + 1];   /* R'' */
@@ -642,7 +652,7 @@ static double proj_one(const proj_ctx *c, int q, cplx *AP, cplx *AC)
                             /* ---- C channel entry (R,(s1,s3)),(R',(s4,s2)) ---- */
                             if (onC) {
                                 size_t row = (size_t)iR * ns2 + s1 * ns + s3, col = (size_t)iRp * ns2 + s4 * ns + s2;
-                                cplx val = v0 + C[(size_t)q * M2 + row * M + col];
+                                cplx val = v0 + Cq[row * M + col];
                                 if (onP) {
                                     for (int k = 0; k < ncls; k++) {
                                         int i1 = c->plus[iR * ncls + k], i2 = c->minus[iRp * ncls + k];
@@ -681,7 +691,7 @@ double or_project(const or_model *m, const double *state, int chmask, double *Ah
     double amax = 0.0;
 #pragma omp parallel for schedule(static) reduction(max : amax)
     for (int q = 0; q < Nq; q++) {
-        double a = proj_one(&c, q, AP + (size_t)q * M2, AC + (size_t)q * M2);
+        double a = proj_one(&c, q, c.P + (size_t)q * M2, c.C + (size_t)q * M2, AP + (size_t)q * M2, AC + (size_t)q * M2);
         if (a > amax) amax = a;
     }
     proj_free(&c);
@@ -830,11 +840,11 @@ double or_rhs(const or_model *m, const double *E, const double *U, double T, con
     return amax;
 }
 
-/* dX/dT for a list of n transfer momenta only (a bounded sample of one right-hand side):
- * out [2][n][M][M].  Same steps as or_rhs, restricted to the listed momenta where possible
- * (the Fourier transform always runs over the whole mesh). */
-void or_rhs_at(const or_model *m, const double *E, const double *U, double T, const double *state, int chmask,
-               int n, const int *s_list, double *out)
+/* dX/dT at the n listed transfer momenta from the projection context c (Fourier transforms and bond
+ * look-ups) and the momenta's own state rows: P(s_list[i]) at Prows + i Mrow_stride, C likewise:
+ * loops at the listed momenta, the projections, then c_X A L A with c_P = 1, c_C = 2.  out [2][n][M][M]. */
+static void rhs_rows(const or_model *m, const double *E, const double *U, double T, const proj_ctx *c,
+                     const cplx *Prows, const cplx *Crows, int n, const int *s_list, int chmask, double *out)
 {
     int ns2 = m->ns * m->ns, M = m->nff * ns2, ns4 = ns2 * ns2;
     size_t M2 = (size_t)M * M;
@@ -843,14 +853,12 @@ void or_rhs_at(const or_model *m, const double *E, const double *U, double T, co
     cplx *Lp = calloc((size_t)n * nd * ns4, sizeof(cplx)), *Lcc = calloc((size_t)n * nd * ns4, sizeof(cplx));
     if (chmask & 1) or_loops_at(m, E, U, T, 0, 0, n, s_list, (double *)Lp);
     if (chmask & 2) or_loops_at(m, E, U, T, 1, 0, n, s_list, (double *)Lcc);
-    proj_ctx c;
-    proj_prepare(m, state, chmask, &c);
     cplx *o = (cplx *)out;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < n; i++) {
         cplx *AP = malloc(sizeof(cplx) * M2), *AC = malloc(sizeof(cplx) * M2);
         cplx *Lm = malloc(sizeof(cplx) * M2), *Tm = malloc(sizeof(cplx) * M2);
-        proj_one(&c, s_list[i], AP, AC);
+        proj_one(c, s_list[i], Prows + (size_t)i * M2, Crows + (size_t)i * M2, AP, AC);
         for (int ch = 0; ch < 2; ch++) {
             cplx *D = o + ((size_t)ch * n + i) * M2;
             if (!((chmask >> ch) & 1)) { memset(D, 0, sizeof(cplx) * M2); continue; }
@@ -872,8 +880,89 @@ void or_rhs_at(const or_model *m, const double *E, const double *U, double T, co
         }
         free(AP); free(AC); free(Lm); free(Tm);
     }
-    proj_free(&c);
     free(Lp); free(Lcc);
+}
+
+/* dX/dT for a list of n transfer momenta only (a bounded sample of one right-hand side):
+ * out [2][n][M][M].  Same steps as or_rhs, restricted to the listed momenta where possible
+ * (the Fourier transform always runs over the whole mesh). */
+void or_rhs_at(const or_model *m, const double *E, const double *U, double T, const double *state, int chmask,
+               int n, const int *s_list, double *out)
+{
+    int M = m->nff * m->ns * m->ns, Nq = m->Lq * m->Lq;
+    size_t M2 = (size_t)M * M;
+    proj_ctx c;
+    proj_prepare(m, state, chmask, &c);
+    /* the listed momenta's own rows, in list order */
+    cplx *rows = malloc(sizeof(cplx) * 2 * (size_t)(n > 0 ? n : 1) * M2);
+    for (int i = 0; i < n; i++) {
+        memcpy(rows + (size_t)i * M2, c.P + (size_t)s_list[i] * M2, sizeof(cplx) * M2);
+        memcpy(rows + ((size_t)n + i) * M2, c.C + (size_t)s_list[i] * M2, sizeof(cplx) * M2);
+    }
+    (void)Nq;
+    rhs_rows(m, E, U, T, &c, rows, rows + (size_t)n * M2, n, s_list, chmask, out);
+    free(rows);
+    proj_free(&c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 6b. The right-hand side with the transfer momenta split into shards        */
+/* ------------------------------------------------------------------------ */
+/* A shard is a list of n transfer momenta with their own rows of the state, state_local [2][n][M][M].  The
+ * only quantity that couples momenta is the Fourier transform of Sec. 3.3, a sum over the whole mesh: each
+ * shard forms its part over its own momenta, the parts are summed (an all-reduce), and each shard finishes
+ * its own rows from the sum. */
+
+/* Bond classes R'' (mod Lq) of the transforms, [ncls][2], in the order of the xr arrays below; returns ncls */
+int or_shard_classes(const or_model *m, int *cls_out)
+{
+    proj_ctx c;
+    proj_tables(m, 3, &c);
+    for (int k = 0; k < c.ncls; k++) { cls_out[2 * k] = c.cls[2 * k]; cls_out[2 * k + 1] = c.cls[2 * k + 1]; }
+    int n = c.ncls;
+    proj_free(&c);
+    return n;
+}
+
+/* xr [2][ncls][M][M] = (1/Nq) sum_i e^{i q_i.R''} X_local[ch][i] over the listed momenta q_i */
+void or_shard_transform(const or_model *m, const double *state_local, int n, const int *q_list, int chmask, double *xr)
+{
+    int M = m->nff * m->ns * m->ns, Lq = m->Lq, Nq = Lq * Lq;
+    size_t M2 = (size_t)M * M;
+    proj_ctx c;
+    proj_tables(m, chmask, &c);
+    const cplx *X = (const cplx *)state_local;
+    cplx *o = (cplx *)xr;
+    memset(o, 0, sizeof(cplx) * 2 * (size_t)c.ncls * M2);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < c.ncls; k++)
+        for (int ch = 0; ch < 2; ch++) {
+            if (!((chmask >> ch) & 1)) continue;
+            cplx *dst = o + ((size_t)ch * c.ncls + k) * M2;
+            for (int i = 0; i < n; i++) {
+                int u = q_list[i];
+                cplx ph = lattice_phase((long)(u / Lq) * c.cls[2 * k] + (long)(u % Lq) * c.cls[2 * k + 1], Lq);
+                const cplx *Xu = X + ((size_t)ch * n + i) * M2;
+                for (size_t e = 0; e < M2; e++) dst[e] += ph * Xu[e];
+            }
+            for (size_t e = 0; e < M2; e++) dst[e] /= (double)Nq;
+        }
+    proj_free(&c);
+}
+
+/* dX/dT at the listed momenta from their own rows and the summed transforms xr: out_local [2][n][M][M] */
+void or_shard_finish(const or_model *m, const double *E, const double *U, double T, const double *state_local, int n,
+                     const int *q_list, const double *xr, int chmask, double *out_local)
+{
+    int M = m->nff * m->ns * m->ns;
+    size_t M2 = (size_t)M * M;
+    proj_ctx c;
+    proj_tables(m, chmask, &c);
+    memcpy(c.Pr, xr, sizeof(cplx) * (size_t)c.ncls * M2);
+    memcpy(c.Cr, (const cplx *)xr + (size_t)c.ncls * M2, sizeof(cplx) * (size_t)c.ncls * M2);
+    const cplx *X = (const cplx *)state_local;
+    rhs_rows(m, E, U, T, &c, X, X + (size_t)n * M2, n, q_list, chmask, out_local);
+    proj_free(&c);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -77,6 +77,12 @@ def lib():
             L.tufrg_model_info.restype = C.c_int
             L.tufrg_loop_momenta.argtypes = [vp, ip]
             L.tufrg_loop_momenta.restype = C.c_int
+            L.tufrg_shard_classes.argtypes = [vp, ip, vp]
+            L.tufrg_shard_classes.restype = C.c_int
+            L.tufrg_rhs_shard_transform.argtypes = [vp, vp, i, vp, i, vp]
+            L.tufrg_rhs_shard_transform.restype = C.c_int
+            L.tufrg_rhs_shard_finish.argtypes = [vp, d, vp, i, vp, vp, i, vp]
+            L.tufrg_rhs_shard_finish.restype = C.c_int
             L.tufrg_loops_info.argtypes = [vp, ip]
             L.tufrg_loops_info.restype = C.c_int
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
@@ -137,4 +143,5 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_band_basis",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
-           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info")
+           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info",
+           "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish")

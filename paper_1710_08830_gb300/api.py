@@ -199,6 +199,38 @@ class Model:
         self._check(self._L.tufrg_rhs_host_batch(self._h, n, t_arr, s_arr, int(mask) | flag, o_arr))
         return outs_host
 
+    # ------------------------------------------------------------------ right-hand side over shards of momenta
+    def shard_classes(self) -> np.ndarray:
+        """Bond classes R'' (mod Lq) of the shard transforms, [ncls][2]."""
+        n = C.c_int()
+        self._check(self._L.tufrg_shard_classes(self._h, C.byref(n), None))
+        cls = np.zeros((n.value, 2), np.int32)
+        self._check(self._L.tufrg_shard_classes(self._h, C.byref(n), cls.ctypes.data))
+        return cls
+
+    def shard_transform(self, state_local, q_list, mask: int = CH_P | CH_C) -> torch.Tensor:
+        """This shard's part of the Fourier transform to the bond classes, [2][ncls][M][M] complex128 on the device;
+        state_local [2][len(q_list)][M][M] holds the rows of the listed momenta."""
+        ql = np.ascontiguousarray(q_list, np.int32)
+        st = self._dev(state_local)
+        if tuple(st.shape) != (2, ql.shape[0], self.M, self.M):
+            raise ValueError("state_local must be [2][len(q_list)][M][M]")
+        ncls = self.shard_classes().shape[0]
+        out = torch.zeros((2, ncls, self.M, self.M), dtype=torch.complex128, device=st.device)
+        self._check(self._L.tufrg_rhs_shard_transform(self._h, _ptr(st), ql.shape[0], ql.ctypes.data, int(mask), _ptr(out)))
+        return out
+
+    def shard_finish(self, T: float, state_local, q_list, xr, mask: int = CH_P | CH_C) -> torch.Tensor:
+        """dX/dT of the listed momenta, [2][len(q_list)][M][M], from their rows and the transforms summed over all
+        shards."""
+        ql = np.ascontiguousarray(q_list, np.int32)
+        st = self._dev(state_local)
+        xr = self._dev(xr)
+        out = torch.empty_like(st)
+        self._check(self._L.tufrg_rhs_shard_finish(self._h, float(T), _ptr(st), ql.shape[0], ql.ctypes.data, _ptr(xr),
+                                                   int(mask), _ptr(out)))
+        return out
+
     PHASES = ("fermi", "loops", "loop_reduce", "dft", "project", "vlv", "rk")
 
     def timing_begin(self):

@@ -494,7 +494,8 @@ void release(tufrg_model *m)
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
                     m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
-                    m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w};
+                    m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
+                    m->d_shard_q, m->d_shard_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -1317,6 +1318,75 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
     CK(surrogate_rearm(m), "re-arm surrogate");
     return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask & 3, reinterpret_cast<double2 *>(d_dstate),
                       nullptr, (channel_mask & TUFRG_SYMMETRIC_STATE) != 0);
+}
+
+// ------------------------------------------------------------------ right-hand side over shards of momenta
+
+namespace {
+// checks a shard's momentum list (distinct momenta in [0, Nq)) and uploads it to the model's list buffer
+tufrg_status upload_shard(tufrg_model *m, int n_q, const int *h_q_list)
+{
+    if (n_q < 1 || n_q > m->Nq || !h_q_list) return fail(m, TUFRG_EINVAL, "the shard needs 1 to Nq momenta");
+    std::vector<char> seen(m->Nq, 0);
+    for (int i = 0; i < n_q; i++) {
+        const int q = h_q_list[i];
+        if (q < 0 || q >= m->Nq || seen[q]) return fail(m, TUFRG_EINVAL, "shard momenta must be distinct and in [0, Nq)");
+        seen[q] = 1;
+    }
+    if (m->sur) return fail(m, TUFRG_ENOTSUP, "the sharded right-hand side does not use the loop surrogate: detach it");
+    if (!m->d_shard_q) CK(dalloc(&m->d_shard_q, m->Nq), "cudaMalloc shard list");
+    CK(cudaMemcpyAsync(m->d_shard_q, h_q_list, sizeof(int) * n_q, cudaMemcpyHostToDevice, m->stream), "upload shard list");
+    return TUFRG_OK;
+}
+}  // namespace
+
+tufrg_status tufrg_shard_classes(const tufrg_model *m, int *ncls, int *h_cls)
+{
+    if (!m || !ncls) return TUFRG_EINVAL;
+    *ncls = m->ncls;
+    if (h_cls) std::copy(m->cls.begin(), m->cls.end(), h_cls);
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_rhs_shard_transform(tufrg_model *m, const void *d_state_local, int n_q, const int *h_q_list,
+                                       int channel_mask, void *d_xr)
+{
+    if (!m || !d_state_local || !d_xr) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    tufrg_status st = upload_shard(m, n_q, h_q_list);
+    if (st != TUFRG_OK) return st;
+    CK(launch_shard_dft(m, reinterpret_cast<const double2 *>(d_state_local), n_q, m->d_shard_q, channel_mask,
+                        reinterpret_cast<double2 *>(d_xr)), "shard Fourier transform");
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_rhs_shard_finish(tufrg_model *m, double T, const void *d_state_local, int n_q, const int *h_q_list,
+                                    const void *d_xr, int channel_mask, void *d_dstate_local)
+{
+    if (!m || !d_state_local || !d_xr || !d_dstate_local) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
+    if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
+    tufrg_status st = upload_shard(m, n_q, h_q_list);
+    if (st != TUFRG_OK) return st;
+    const bool split = m->precision != TUFRG_FP64;
+    const size_t M2 = (size_t)m->M * m->M, nx = 2 * (size_t)m->ncls * M2;
+    const double2 *xr = reinterpret_cast<const double2 *>(d_xr);
+    const double2 *X = reinterpret_cast<const double2 *>(d_state_local);
+    // the summed transforms in the model's working precision
+    if (split) CK(launch_to_f32(m, xr, m->d_Xr32, nx), "transform conversion");
+    else CK(cudaMemcpyAsync(m->d_Xr, xr, sizeof(double2) * nx, cudaMemcpyDeviceToDevice, m->stream), "copy transforms");
+    CK(launch_set_scalars(m, T, 1.0), "set temperature");
+    CK(launch_fermi(m), "fermi tables");
+    CK(launch_loops_list(m, channel_mask, m->d_shard_q, n_q), "loop k-sum of the shard");
+    // the shard's rows in FP32 for the split path (list order, in the front of the model's copy)
+    if (split) CK(launch_to_f32(m, X, m->d_X32, 2 * (size_t)n_q * M2), "state conversion");
+    CK(launch_project_local(m, X, split ? m->d_X32 : nullptr, channel_mask, split ? nullptr : m->d_A, m->d_shard_q, n_q),
+       "projections of the shard");
+    if (!m->d_shard_out) CK(dalloc(&m->d_shard_out, state_elems(m)), "cudaMalloc shard products");
+    CK(launch_vlv(m, m->d_A, channel_mask, m->d_shard_out, m->d_shard_q, n_q), "V.L.V products of the shard");
+    CK(launch_shard_gather(m, m->d_shard_out, n_q, m->d_shard_q, reinterpret_cast<double2 *>(d_dstate_local)),
+       "gather of the shard's rows");
+    return TUFRG_OK;
 }
 
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)

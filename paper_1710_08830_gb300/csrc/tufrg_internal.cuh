@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -306,6 +307,8 @@ struct tufrg_model {
 
     tufrg::LoopPlan plan{};
     int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
+    int *d_shard_q = nullptr;       // [Nq] momenta of a shard (sharded right-hand side)
+    double2 *d_shard_out = nullptr; // [2][Nq][M][M] products of a shard's momenta before they are gathered
     bool loops_tc = false;          // multi-orbital loop k-sum on the tensor cores (k_loops_tc.cu)
     float2 *d_loop_w = nullptr;     // its column sums [groups][Lf][108][108]
 
@@ -374,6 +377,14 @@ bool loops2_supported(const tufrg_model *m);
 int loops2_blocks_per_sm(const tufrg_model *m);
 bool loops_gen_supported(const tufrg_model *m);
 cudaError_t launch_loops_gen(tufrg_model *m, int channel_mask, bool reps_only);
+// sharded right-hand side (k_shard.cu): a shard's part of the Fourier transform, the gather of its rows, and the
+// loops at a list of momenta
+cudaError_t launch_shard_dft(tufrg_model *m, const double2 *d_state_local, int n, const int *d_q, int mask, double2 *d_xr);
+cudaError_t launch_shard_gather(tufrg_model *m, const double2 *d_full, int n, const int *d_q, double2 *d_out);
+cudaError_t launch_loops_list(tufrg_model *m, int mask, const int *d_list, int n);
+// projections of the listed momenta whose state rows are stored in list order, [2][nlist][M][M]
+cudaError_t launch_project_local(tufrg_model *m, const double2 *d_state_local, const float2 *d_state32_local,
+                                 int channel_mask, double2 *d_A, const int *qlist, int nlist);
 bool loops_tc_supported(const tufrg_model *m);
 size_t loops_tc_w_bytes(const tufrg_model *m);
 cudaError_t launch_loops_tc(tufrg_model *m, int ch, float2 *acc);

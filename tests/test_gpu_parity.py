@@ -715,3 +715,39 @@ def test_device_timeout_flag_propagates_to_the_host():
     m.rhs_host(0.4, hs, ho)
     _, r = m.flow(T0=10.0, T_end=5.0)
     assert r["T_last"] == pytest.approx(5.0)
+
+
+@pytest.mark.parametrize("case,prec", [("rashba_ff9_Lf25", "SPLIT32"), ("rashba_ff5_Lf24", "FP64"),
+                                       ("t2g_ff5_Lf8", "SPLIT32"), ("t2g_ff9_Lf10", "FP64"), ("hubbard_ff5_Lf24", "SPLIT32")])
+def test_rhs_shards_emulated_on_one_gpu(case, prec):
+    """The right-hand side split over shards of transfer momenta through the C ABI (tufrg_rhs_shard_transform, the
+    sum of the parts, tufrg_rhs_shard_finish), three uneven shards run one after the other on one GPU (the sum
+    stands in for the all-reduce between GPUs): every shard's rows equal those of tufrg_rhs and of the oracle.
+    With loop symmetries the loop scratch holds fewer momenta than a shard lists (t2g: 6 orbit representatives),
+    so the listed loops run in chunks."""
+    from paper_1710_08830_gb300 import shard
+    api = _api()
+    spec = (CASES.get(case) or T2G[case])()
+    m = api.Model(spec, getattr(api, prec))
+    st = inputs.random_state(spec, seed=21, scale=0.25)
+    rng = np.random.default_rng(3)
+    perm = rng.permutation(spec.Nq)
+    cut = [0, spec.Nq // 4, (2 * spec.Nq) // 3, spec.Nq]
+    shards = [np.sort(perm[cut[i]:cut[i + 1]]) if i != 1 else perm[cut[i]:cut[i + 1]] for i in range(3)]
+    xr = sum(m.shard_transform(st[:, s], s) for s in shards)
+    full = m.rhs(0.3, st).cpu().numpy()
+    ref, _ = oracle.Oracle(spec).rhs(0.3, st, 3)
+    tol = TOL64 if prec == "FP64" else TOL32
+    for s in shards:
+        d = m.shard_finish(0.3, st[:, s], s, xr).cpu().numpy()
+        assert rel(d, full[:, s]) < (1e-12 if prec == "FP64" else 2e-6)
+        assert np.abs(d - ref[:, s]).max() < tol * np.abs(ref).max()
+    # the partition helper's shards give the same rows
+    q0 = shard.partition(spec.Nq, 2, 0)
+    q1 = shard.partition(spec.Nq, 2, 1)
+    xr2 = m.shard_transform(st[:, q0], q0) + m.shard_transform(st[:, q1], q1)
+    d1 = m.shard_finish(0.3, st[:, q1], q1, xr2).cpu().numpy()
+    assert np.abs(d1 - ref[:, q1]).max() < tol * np.abs(ref).max()
+    with pytest.raises(api.TufrgError) as e:
+        m.shard_transform(st[:, [0, 0]], [0, 0])                 # repeated momentum
+    assert e.value.status == 1

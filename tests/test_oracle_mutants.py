@@ -88,8 +88,9 @@ MUTANTS = {
                            "Ub[(size_t)k * ns2 + a * ns + c] * Ub[(size_t)k2 * ns2 + b * ns + d]"),
     # the sampled right-hand side (bounded CPU timings): c_C = 1 instead of 2
     "rhs_at_crossed_prefactor": ("double cx = ch == 0 ? 1.0 : 2.0;", "double cx = 1.0;"),
-    # the sampled right-hand side projected at the list position instead of the listed momentum
-    "rhs_at_momentum_index": ("proj_one(&c, s_list[i], AP, AC);", "proj_one(&c, i, AP, AC);"),
+    # the sampled (and sharded) right-hand side projected at the list position instead of the listed momentum
+    "rhs_at_momentum_index": ("proj_one(c, s_list[i], Prows + (size_t)i * M2, Crows + (size_t)i * M2, AP, AC);",
+                              "proj_one(c, i, Prows + (size_t)i * M2, Crows + (size_t)i * M2, AP, AC);"),
     # the sampled right-hand side with the first product's operands exchanged (L A for A L)
     "rhs_at_operand_order": ("sacc += A[(size_t)r * M + k] * Lm[(size_t)k * M + col];",
                              "sacc += Lm[(size_t)r * M + k] * A[(size_t)k * M + col];"),
