@@ -99,7 +99,21 @@ typedef struct {
     int regulator;         /* TUFRG_REG_TEMPERATURE or TUFRG_REG_MOMENTUM_SHELL (see below) */
     double T_reg;          /* momentum shell: temperature of the Fermi functions in the bubbles (> 0) */
     int loops;             /* TUFRG_LOOPS_AUTO / _TC / _SIMT: backend of the multi-orbital loop k-sum (see below) */
+    int basis;             /* TUFRG_BASIS_ORBITAL or TUFRG_BASIS_BAND: the single-particle basis of the flow (below) */
 } tufrg_model_desc;
+
+/* Single-particle basis of the exchange propagators and of the flow (Sec. 3.2, Sec. 3.4).
+ * ORBITAL: states in the orbital (spin) basis, loops of Eq. loop_orbital (the library's default).
+ * BAND: the flow in the band basis of the model's eigenvectors U(k), Eqs. rge_Pmat and rge_Dmat: the loops are
+ * band-diagonal (Eqs. loopminus, loopplus with the weights of Eqs. disc_2a, disc_2b), and the bare vertex, onsite
+ * in the orbital basis, enters through its band-basis projections P^[V0](s) = T_P^dagger P^[V0]_orb T_P and
+ * C^[V0](u) = T_C^dagger C^[V0]_orb T_C (Eqs. mat_trafo_P, mat_trafo_D, the transformation of tufrg_band_basis),
+ * which depend on the transfer momentum.  States, loops and right-hand sides are band-basis objects in the
+ * layouts of the orbital ones with band indices in place of orbital indices; they depend on the gauge of the
+ * eigenvectors.  With the complete bond set the two bases give the same flow (related by the transformation);
+ * truncated, the band basis needs more bonds (Sec. 3.4).  Two-band models with M <= 64 (else TUFRG_ENOTSUP); the
+ * loop symmetries are not used; no surrogate; tufrg_bands then reports unit eigenvectors. */
+enum { TUFRG_BASIS_ORBITAL = 0, TUFRG_BASIS_BAND = 1 };
 
 /* Backend of the loop k-sum of split-precision models with N_s = 6 and at most three non-negative y components
  * of the bond differences (5 or 9 bonds): TC runs the per-column orbital sums as complex 3xTF32 GEMMs on the

@@ -48,7 +48,8 @@ def build(force: bool = False) -> str:
 class _Model(C.Structure):
     _fields_ = [("ns", C.c_int), ("nhop", C.c_int), ("hopR", C.c_void_p), ("hopt", C.c_void_p),
                 ("V0", C.c_void_p), ("nff", C.c_int), ("ffR", C.c_void_p),
-                ("Lq", C.c_int), ("nc", C.c_int), ("mu", C.c_double), ("reg", C.c_int), ("T_reg", C.c_double)]
+                ("Lq", C.c_int), ("nc", C.c_int), ("mu", C.c_double), ("reg", C.c_int), ("T_reg", C.c_double),
+                ("V0q", C.c_void_p)]
 
 
 class FlowOpts(C.Structure):
@@ -94,6 +95,8 @@ def lib():
             L.or_vlv.argtypes = [vp, vp, vp, vp, i, vp]
             L.or_rhs.argtypes = [vp, vp, vp, d, vp, i, vp, vp]
             L.or_band_transform.argtypes = [vp, vp, vp, vp]
+            L.or_bare_state.argtypes = [vp, vp]
+            L.or_bare_state.restype = None
             L.or_band_transform.restype = None
             L.or_rhs.restype = d
             L.or_rhs_at.argtypes = [vp, vp, vp, d, vp, i, i, vp, vp]
@@ -156,9 +159,16 @@ def Fp(e1, e2, T):
 
 
 class Oracle:
-    """The oracle bound to one model descriptor (``inputs.ModelSpec``)."""
+    """The oracle bound to one model descriptor (``inputs.ModelSpec``).
 
-    def __init__(self, spec, mu: float | None = None):
+    basis="band": the flow in the band basis (Sec. 3.2, Eqs. rge_Pmat, rge_Dmat): the loops are band-diagonal
+    (the eigenvectors replaced by unit vectors, Eqs. loopminus, loopplus with Eqs. disc_2a, disc_2b) and the bare
+    vertex enters through its band-basis projections, P^[V0](s) and C^[V0](u) transformed with Eqs. mat_trafo_P,
+    mat_trafo_D from the orbital ones (V0 onsite, Sec. 4), with the eigenvectors band_U [Nk][N_s][N_s] (default:
+    the oracle's own; the band basis depends on their gauge).  States, loops and right-hand sides are then
+    band-basis objects in the layouts of the orbital ones with band indices in place of orbital indices."""
+
+    def __init__(self, spec, mu: float | None = None, basis: str = "orbital", band_U=None):
         self.spec = spec
         self._hopR = np.ascontiguousarray(spec.hop_R, np.int32)
         self._hopt = np.ascontiguousarray(spec.hop_t, np.complex128)
@@ -166,7 +176,7 @@ class Oracle:
         self._ffR = np.ascontiguousarray(spec.ff_R, np.int32)
         self.m = _Model(spec.n_s, self._hopR.shape[0], _ptr(self._hopR), _ptr(self._hopt),
                         _ptr(self._V0), self._ffR.shape[0], _ptr(self._ffR), spec.Lq, spec.nc, 0.0,
-                        int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)))
+                        int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)), None)
         self.E, self.U = self.bands()
         if mu is not None:
             self.mu = float(mu)
@@ -178,6 +188,23 @@ class Oracle:
         dl = np.zeros((4096, 2), np.int32)
         nd = lib().or_delta_list(C.byref(self.m), _ptr(dl))
         self.deltas = dl[:nd].copy()
+        self.basis = basis
+        if basis == "band":
+            Ub = self.U if band_U is None else np.ascontiguousarray(band_U, np.complex128).reshape(self.U.shape)
+            s0 = np.zeros((2, spec.Nq, spec.M, spec.M), np.complex128)
+            lib().or_bare_state(C.byref(self.m), _ptr(s0))
+            self._V0q = np.ascontiguousarray(self.band_transform(Ub, s0))
+            self.m.V0q = _ptr(self._V0q)
+            self.U = np.ascontiguousarray(np.broadcast_to(np.eye(spec.n_s, dtype=np.complex128), self.U.shape))
+        elif basis != "orbital":
+            raise ValueError("basis must be 'orbital' or 'band'")
+
+    def bare_state(self) -> np.ndarray:
+        """The bare vertex as a state [2][Nq][M][M] (its projections at every momentum), orbital basis."""
+        s = self.spec
+        out = np.zeros((2, s.Nq, s.M, s.M), np.complex128)
+        lib().or_bare_state(C.byref(self.m), _ptr(out))
+        return out
 
     @property
     def nd(self) -> int:

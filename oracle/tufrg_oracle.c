@@ -74,6 +74,9 @@ typedef struct {
     double mu;
     int reg;           /* 0: temperature flow (scale = T); 1: momentum shell (scale = Lambda) */
     double T_reg;      /* momentum shell: temperature of the Fermi functions in F */
+    const double *V0q; /* NULL, or [2][Nq][M][M] complex: the projected bare vertex P^[V0](q), C^[V0](q) in the
+                          layouts of the state, used in place of the onsite V0 (the band-basis flow, where the
+                          bare vertex depends on the momenta) */
 } or_model;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -608,7 +611,7 @@ static double proj_one(const proj_ctx *c, int q, const cplx *Pq, const cplx *Cq,
     const or_model *m = c->m;
     int ns = m->ns, ns2 = ns * ns, nff = m->nff, M = nff * ns2, Lq = m->Lq, ncls = c->ncls;
     size_t M2 = (size_t)M * M;
-    const cplx *V0 = (const cplx *)m->V0;
+    const cplx *V0 = (const cplx *)m->V0, *V0q = (const cplx *)m->V0q;
     const cplx *Pr = c->Pr, *Cr = c->Cr;
     int i0 = ff_index_mod(m, 0, 0);
     int onP = c->chmask & 1, onC = (c->chmask >> 1) & 1;
@@ -621,10 +624,11 @@ static double proj_one(const proj_ctx *c, int q, const cplx *Pq, const cplx *Cq,
                 for (int s2 = 0; s2 < ns; s2++)
                     for (int s3 = 0; s3 < ns; s3++)
                         for (int s4 = 0; s4 < ns; s4++) {
-                            cplx v0 = (iR == i0 && iRp == i0) ? V0[((s1 * ns + s2) * ns + s3) * ns + s4] : 0.0;
+                            const cplx v0on = (iR == i0 && iRp == i0) ? V0[((s1 * ns + s2) * ns + s3) * ns + s4] : 0.0;
                             /* ---- P channel entry (R,(s1,s2)),(R',(s4,s3)) ---- */
                             if (onP) {
                                 size_t row = (size_t)iR * ns2 + s1 * ns + s2, col = (size_t)iRp * ns2 + s4 * ns + s3;
+                                cplx v0 = V0q ? V0q[(size_t)q * M2 + row * M + col] : v0on;
                                 cplx val = v0 + Pq[row * M + col];
                                 if (onC) {
                                     for (int k = 0; k < ncls; k++) {
@@ -652,6 +656,7 @@ static double proj_one(const proj_ctx *c, int q, const cplx *Pq, const cplx *Cq,
                             /* ---- C channel entry (R,(s1,s3)),(R',(s4,s2)) ---- */
                             if (onC) {
                                 size_t row = (size_t)iR * ns2 + s1 * ns + s3, col = (size_t)iRp * ns2 + s4 * ns + s2;
+                                cplx v0 = V0q ? V0q[((size_t)Lq * Lq + q) * M2 + row * M + col] : v0on;
                                 cplx val = v0 + Cq[row * M + col];
                                 if (onP) {
                                     for (int k = 0; k < ncls; k++) {
@@ -696,6 +701,30 @@ double or_project(const or_model *m, const double *state, int chmask, double *Ah
     }
     proj_free(&c);
     return amax;
+}
+
+/* The bare vertex as a state: P(q) and C(q) equal to its projections at every q, the onsite V0 of Sec. 4 in the
+ * (R, R') = (0, 0) block, P entry (0,(s1,s2)),(0,(s4,s3)) and C entry (0,(s1,s3)),(0,(s4,s2)) = V0_{s1 s2 s3 s4};
+ * out [2][Nq][M][M] complex.  Transformed with or_band_transform it is the bare vertex of the band-basis flow. */
+void or_bare_state(const or_model *m, double *out)
+{
+    int ns = m->ns, ns2 = ns * ns, M = m->nff * ns2, Nq = m->Lq * m->Lq;
+    size_t M2 = (size_t)M * M;
+    const cplx *V0 = (const cplx *)m->V0;
+    cplx *o = (cplx *)out;
+    memset(o, 0, sizeof(cplx) * 2 * (size_t)Nq * M2);
+    int i0 = ff_index_mod(m, 0, 0);
+    for (int q = 0; q < Nq; q++)
+        for (int s1 = 0; s1 < ns; s1++)
+            for (int s2 = 0; s2 < ns; s2++)
+                for (int s3 = 0; s3 < ns; s3++)
+                    for (int s4 = 0; s4 < ns; s4++) {
+                        cplx v = V0[(((size_t)s1 * ns + s2) * ns + s3) * ns + s4];
+                        size_t rP = (size_t)i0 * ns2 + s1 * ns + s2, cP = (size_t)i0 * ns2 + s4 * ns + s3;
+                        size_t rC = (size_t)i0 * ns2 + s1 * ns + s3, cC = (size_t)i0 * ns2 + s4 * ns + s2;
+                        o[(size_t)q * M2 + rP * M + cP] = v;
+                        o[((size_t)Nq + q) * M2 + rC * M + cC] = v;
+                    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -20,6 +20,7 @@ STATUS = {0: "TUFRG_OK", 1: "TUFRG_EINVAL", 2: "TUFRG_ENOMEM", 3: "TUFRG_ECUDA",
 FP64, SPLIT32 = 0, 1
 PRODUCTS_AUTO, PRODUCTS_TC, PRODUCTS_SIMT = 0, 1, 2
 LOOPS_AUTO, LOOPS_TC, LOOPS_SIMT = 0, 1, 2
+BASIS_ORBITAL, BASIS_BAND = 0, 1
 SYMMETRY_AUTO, SYMMETRY_OFF, SYMMETRY_STATES = 0, 1, 2
 SYMMETRIC_STATE = 4   # tufrg_rhs flag: the state has the model's loop symmetries
 REG_TEMPERATURE, REG_MOMENTUM_SHELL = 0, 1   # regulators of the loops (Eq. def_lmp)
@@ -31,7 +32,7 @@ class ModelDesc(C.Structure):
                 ("mu", C.c_double), ("filling", C.c_double), ("T_mu", C.c_double), ("V0", C.c_void_p),
                 ("n_ff", C.c_int), ("ff_R", C.c_void_p), ("Lq", C.c_int), ("nc", C.c_int),
                 ("precision", C.c_int), ("products", C.c_int), ("symmetry", C.c_int), ("regulator", C.c_int),
-                ("T_reg", C.c_double), ("loops", C.c_int)]
+                ("T_reg", C.c_double), ("loops", C.c_int), ("basis", C.c_int)]
 
 
 class FlowOpts(C.Structure):

@@ -13,14 +13,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (CH_C, CH_P, FP64, LOOPS_AUTO, LOOPS_SIMT, LOOPS_TC, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
+from ._lib import (BASIS_BAND, BASIS_ORBITAL, CH_C, CH_P, FP64, LOOPS_AUTO, LOOPS_SIMT, LOOPS_TC, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
                    SYMMETRY_OFF, SYMMETRY_STATES,
                    FlowOpts, FlowResult, ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
 __all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "SYMMETRY_AUTO",
            "SYMMETRY_OFF", "SYMMETRY_STATES", "SYMMETRIC_STATE", "CH_P", "CH_C", "LOOPS_AUTO", "LOOPS_TC", "LOOPS_SIMT",
-           "TufrgError"]
+           "BASIS_ORBITAL", "BASIS_BAND", "TufrgError"]
 
 
 def _ptr(t) -> int:
@@ -32,11 +32,12 @@ class Model:
 
     def __init__(self, spec: ModelSpec, precision: int = FP64, stream: Optional[torch.cuda.Stream] = None,
                  mu: Optional[float] = None, products: int = PRODUCTS_AUTO, symmetry: int = SYMMETRY_AUTO,
-                 loops: int = LOOPS_AUTO):
+                 loops: int = LOOPS_AUTO, basis: int = BASIS_ORBITAL):
         if not torch.cuda.is_available():
             raise RuntimeError("libtufrg needs a CUDA device")
         self.spec = spec
         self.precision = precision
+        self.basis = basis
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._L = _lib.lib()
         # keep the descriptor arrays alive for the duration of the init call
@@ -49,7 +50,7 @@ class Model:
                       float(spec.mu if mu is None else mu), float(spec.filling if use_fill else 0.0),
                       float(spec.T_mu), self._V0.ctypes.data, self._ffR.shape[0], self._ffR.ctypes.data,
                       spec.Lq, spec.nc, int(precision), int(products), int(symmetry),
-                      int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)), int(loops))
+                      int(getattr(spec, "regulator", 0)), float(getattr(spec, "T_reg", 0.05)), int(loops), int(basis))
         h = C.c_void_p()
         st = self._L.tufrg_init_model(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h))
         self._h = h

@@ -495,7 +495,7 @@ void release(tufrg_model *m)
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
                     m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
-                    m->d_shard_q, m->d_shard_out};
+                    m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -747,6 +747,8 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     if (d.precision != TUFRG_FP64 && d.precision != TUFRG_SPLIT32) return fail(m, TUFRG_EINVAL, "unknown precision");
     if (d.products < TUFRG_PRODUCTS_AUTO || d.products > TUFRG_PRODUCTS_SIMT) return fail(m, TUFRG_EINVAL, "unknown products backend");
     if (d.loops < TUFRG_LOOPS_AUTO || d.loops > TUFRG_LOOPS_SIMT) return fail(m, TUFRG_EINVAL, "unknown loops backend");
+    if (d.basis != TUFRG_BASIS_ORBITAL && d.basis != TUFRG_BASIS_BAND) return fail(m, TUFRG_EINVAL, "unknown basis");
+    m->basis = d.basis;
     if (d.symmetry != TUFRG_SYMMETRY_AUTO && d.symmetry != TUFRG_SYMMETRY_OFF && d.symmetry != TUFRG_SYMMETRY_STATES)
         return fail(m, TUFRG_EINVAL, "unknown symmetry option");
     if (d.filling > 0 && !(d.T_mu > 0)) return fail(m, TUFRG_EINVAL, "T_mu must be > 0 when filling > 0");
@@ -791,7 +793,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     build_gather_tables(m);
     // loop symmetries (TUFRG_SYMMETRY_AUTO, split two-band path)
     m->n_loop_q = m->Nq;
-    if (d.symmetry != TUFRG_SYMMETRY_OFF && ((ns == 2 && loops2_supported(m)) || (ns != 2 && loops_gen_supported(m)))) {
+    if (m->basis == TUFRG_BASIS_BAND && !band_basis_supported(m))
+        return fail(m, TUFRG_ENOTSUP, "the band-basis flow needs a two-band model with M <= 64");
+    // the loop symmetries act on orbital indices; the band basis does not use them
+    if (d.symmetry != TUFRG_SYMMETRY_OFF && m->basis == TUFRG_BASIS_ORBITAL &&
+        ((ns == 2 && loops2_supported(m)) || (ns != 2 && loops_gen_supported(m)))) {
         LoopSymmetry ls;
         build_loop_symmetry(m, ls);
         if ((int)ls.list.size() < m->Nq) {
@@ -1066,6 +1072,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     } else {
         m->mu = d.mu;
     }
+    // band basis: the bare vertex's projections transformed with the eigenvectors, then unit eigenvectors for the
+    // band-diagonal loops (before the loop records, which hold projectors)
+    if (m->basis == TUFRG_BASIS_BAND) CK(setup_band_flow(m), "band-basis set-up");
     if (loops2_supported(m)) CK(launch_loop_records_static(m), "loop records");
     if (m->regulator == TUFRG_REG_MOMENTUM_SHELL) {
         // the Fermi data of the momentum-shell loops do not depend on the flow scale: written once

@@ -169,6 +169,56 @@ cudaError_t band_run(tufrg_model *m, const typename cpx<R>::t *U, const BandTabs
 
 }  // namespace
 
+namespace {
+// S[ch][q][e] = v0d[ch][e] for every q: the bare vertex's projections in the orbital basis (onsite)
+__global__ void bare_state_kernel(const double2 *v0d0, const double2 *v0d1, int Nq, size_t M2, double2 *S)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * (size_t)Nq * M2) return;
+    const size_t e = t % M2;
+    S[t] = (t / M2) < (size_t)Nq ? v0d0[e] : v0d1[e];
+}
+
+template <typename C2>
+__global__ void unit_eigvec_kernel(C2 *U, size_t Nk, int ns)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Nk * ns * ns) return;
+    const int tl = (int)(t % ((size_t)ns * ns));
+    U[t] = mk((decltype(U[t].x))(tl / ns == tl % ns ? 1 : 0), (decltype(U[t].x))0);
+}
+}  // namespace
+
+cudaError_t setup_band_flow(tufrg_model *m)
+{
+    const size_t M2 = (size_t)m->M * m->M, n = 2 * (size_t)m->Nq * M2;
+    double2 *S = nullptr;
+    TUFRG_CUDA_TRY(cudaMalloc(&S, sizeof(double2) * n));
+    cudaError_t e = cudaMalloc(&m->d_v0q, sizeof(double2) * n);
+    if (e == cudaSuccess) {
+        bare_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(m->d_v0d[0], m->d_v0d[1], m->Nq, M2, S);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_band_basis(m, S, m->d_v0q);   // with the model's eigenvectors
+    if (e == cudaSuccess && m->precision != TUFRG_FP64) {
+        e = cudaMalloc(&m->d_v0q32, sizeof(float2) * n);
+        if (e == cudaSuccess) e = launch_to_f32(m, m->d_v0q, m->d_v0q32, n);
+    }
+    // the loops of the band basis: unit eigenvectors (stream ordered after the transformation above)
+    const size_t nu = (size_t)m->Nk * m->ns * m->ns;
+    if (e == cudaSuccess) {
+        unit_eigvec_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, m->stream>>>(m->d_U, (size_t)m->Nk, m->ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && m->d_U32) {
+        unit_eigvec_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, m->stream>>>(m->d_U32, (size_t)m->Nk, m->ns);
+        e = cudaGetLastError();
+    }
+    cudaStreamSynchronize(m->stream);
+    cudaFree(S);
+    return e;
+}
+
 bool band_basis_supported(const tufrg_model *m)
 {
     const size_t c2 = m->precision == TUFRG_FP64 ? sizeof(double2) : sizeof(float2);

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
                                                       const int *eofs1, const int2 *et0, const int2 *et1,
                                                       const typename cpx<R>::t *ph, int nph, int Nq, int M2, int ncls,
                                                       int chmask, const int *qlist, int nlist, double2 *A, float2 *A32,
-                                                      unsigned long long *amax, int x_local)
+                                                      unsigned long long *amax, int x_local, const XT *v0q)
 {
     using C2 = typename cpx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,8 +248,10 @@ __global__ void __launch_bounds__(256) project_kernel(const XT *__restrict__ X, 
 #pragma unroll
             for (int qi = 0; qi < QT; qi++) {
                 acc[qi] = qi < nq ? ld_as<R>(X[xbase + (size_t)(x_local ? qi : sq[qi]) * M2]) : mk(R(0), R(0));
-                acc[qi].x += v0.x;
-                acc[qi].y += v0.y;
+                // the bare vertex: onsite (one value for every momentum), or per momentum in the band basis
+                const C2 vq = v0q && qi < nq ? ld_as<R>(v0q[((size_t)ch * Nq + sq[qi]) * M2 + e]) : v0;
+                acc[qi].x += vq.x;
+                acc[qi].y += vq.y;
             }
             const int *eofs = ch == 0 ? eofs0 : eofs1;
             const int2 *et = ch == 0 ? et0 : et1;
@@ -447,7 +449,7 @@ constexpr int PROJ_QT = 8;   // transfer momenta per thread
 template <typename R, typename XT, int QT>
 cudaError_t project_run(tufrg_model *m, const XT *d_state, const typename cpx<R>::t *Xr, const XT *v0d0, const XT *v0d1,
                         const typename cpx<R>::t *ph, int channel_mask, const int *qlist, int nlist, double2 *d_A,
-                        float2 *d_A32, int x_local)
+                        float2 *d_A32, int x_local, const XT *v0q)
 {
     const int M2 = m->M * m->M;
     const dim3 grid((M2 + 255) / 256, (nlist + QT - 1) / QT, 2);
@@ -456,7 +458,7 @@ cudaError_t project_run(tufrg_model *m, const XT *d_state, const typename cpx<R>
     if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, 256, smem, m->stream>>>(d_state, Xr, v0d0, v0d1, m->d_eofs[0], m->d_eofs[1], m->d_eterms[0],
                                       m->d_eterms[1], ph, m->nph, m->Nq, M2, m->ncls, channel_mask, qlist, nlist, d_A,
-                                      d_A32, m->d_amax, x_local);
+                                      d_A32, m->d_amax, x_local, v0q);
     return cudaGetLastError();
 }
 
@@ -473,12 +475,13 @@ cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 
     PhaseScope ps(m, PH_PROJ);
     if (m->precision == TUFRG_FP64) {
         auto run = short_list ? project_run<double, double2, 2> : project_run<double, double2, PROJ_QT>;
-        return run(m, d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_ph, channel_mask, qlist, nlist, d_A, nullptr, 0);
+        return run(m, d_state, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_ph, channel_mask, qlist, nlist, d_A, nullptr, 0,
+                   m->d_v0q);
     }
     if (!d_state32) return cudaErrorInvalidValue;   // the split path projects the FP32 copy
     auto run = short_list ? project_run<float, float2, 2> : project_run<float, float2, PROJ_QT>;
     return run(m, d_state32, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_ph32, channel_mask, qlist, nlist, d_A,
-               m->d_A32, 0);
+               m->d_A32, 0, m->d_v0q32);
 }
 
 cudaError_t launch_project_local(tufrg_model *m, const double2 *d_state_local, const float2 *d_state32_local,
@@ -488,9 +491,9 @@ cudaError_t launch_project_local(tufrg_model *m, const double2 *d_state_local, c
     PhaseScope ps(m, PH_PROJ);
     if (m->precision == TUFRG_FP64)
         return project_run<double, double2, 2>(m, d_state_local, m->d_Xr, m->d_v0d[0], m->d_v0d[1], m->d_ph, channel_mask,
-                                               qlist, nlist, d_A, nullptr, 1);
+                                               qlist, nlist, d_A, nullptr, 1, m->d_v0q);
     return project_run<float, float2, 2>(m, d_state32_local, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_ph32,
-                                         channel_mask, qlist, nlist, d_A, m->d_A32, 1);
+                                         channel_mask, qlist, nlist, d_A, m->d_A32, 1, m->d_v0q32);
 }
 
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only)

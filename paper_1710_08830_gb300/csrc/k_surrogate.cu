@@ -190,8 +190,8 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
         m->err = "the loop surrogate is trained on the temperature flow";
         return TUFRG_ENOTSUP;
     }
-    if (!loops2_supported(m)) {
-        m->err = "the loop surrogate needs a split-precision two-band model";
+    if (!loops2_supported(m) || m->basis != TUFRG_BASIS_ORBITAL) {
+        m->err = "the loop surrogate needs a split-precision two-band model in the orbital basis";
         return TUFRG_ENOTSUP;
     }
     const int n_out = 2 * m->nd * 16 * 2;

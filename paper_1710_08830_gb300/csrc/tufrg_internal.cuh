@@ -307,6 +307,9 @@ struct tufrg_model {
 
     tufrg::LoopPlan plan{};
     int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
+    int basis = TUFRG_BASIS_ORBITAL;   // single-particle basis of the flow
+    double2 *d_v0q = nullptr;       // band basis: [2][Nq][M][M] projected bare vertex per momentum (FP64)
+    float2 *d_v0q32 = nullptr;      // its FP32 copy (split path)
     int *d_shard_q = nullptr;       // [Nq] momenta of a shard (sharded right-hand side)
     double2 *d_shard_out = nullptr; // [2][Nq][M][M] products of a shard's momenta before they are gathered
     bool loops_tc = false;          // multi-orbital loop k-sum on the tensor cores (k_loops_tc.cu)
@@ -396,6 +399,8 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out);
 cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out);
 // band-basis exchange propagators of a two-band model's state (Sec. 3.4)
 bool band_basis_supported(const tufrg_model *m);
+// band-basis flow: the projected bare vertex per momentum from the model's eigenvectors, then unit eigenvectors
+cudaError_t setup_band_flow(tufrg_model *m);
 cudaError_t launch_band_basis(tufrg_model *m, const double2 *d_state, double2 *d_out);
 bool orbit_products_supported(const tufrg_model *m);
 int orbit_max_size();   // largest orbit the fused orbit kernel takes   // symmetric states: non-representative momenta

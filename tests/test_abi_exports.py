@@ -124,7 +124,8 @@ def test_bad_descriptors_are_rejected_before_device_use(libpath):
         (dict(n_s=0), EINVAL, "n_s"), (dict(n_s=9), EINVAL, "n_s"), (dict(n_s=3), ENOTSUP, "n_s = 2, 4, 6"),
         (dict(n_hop=0), EINVAL, "hopping"), (dict(V0=None), EINVAL, "V0"), (dict(n_ff=0), EINVAL, "bond set"),
         (dict(nc=0), EINVAL, "Lq >= 2"), (dict(Lq=64, nc=65), EINVAL, "fine mesh"),
-        (dict(products=9), EINVAL, "products"), (dict(loops=3), EINVAL, "loops backend"), (dict(filling=0.5, T_mu=0.0), EINVAL, "T_mu"),
+        (dict(products=9), EINVAL, "products"), (dict(loops=3), EINVAL, "loops backend"),
+        (dict(basis=2), EINVAL, "basis"), (dict(filling=0.5, T_mu=0.0), EINVAL, "T_mu"),
         (dict(regulator=7), EINVAL, "regulator"), (dict(regulator=1, T_reg=0.0), EINVAL, "T_reg"),
         (dict(regulator=1, T_reg=float("nan")), EINVAL, "T_reg"),
         (dict(n_hop=hopR.shape[0] - 1), EINVAL, "t_{-R}"),      # the last hop loses its partner

@@ -825,3 +825,66 @@ def test_band_basis_maps_orbital_loops_to_band_diagonal_loops():
                     p = l2 * ns + l1 if ch == 0 else l1 * ns + l2
                     want[np.ix_(np.arange(nff) * 4 + p, np.arange(nff) * 4 + p)] = B
             assert np.abs(out[ch, s] - want).max() < 1e-12 * max(1.0, np.abs(want).max()), (ch, s)
+
+
+# ---------------------------------------------------------------- the flow in the band basis (Sec. 3.2, Sec. 3.4)
+
+@pytest.mark.parametrize("model,mask", [("rashba", 3), ("rashba", 1), ("hubbard", 3)])
+def test_band_basis_flow_equals_transformed_orbital_flow(model, mask):
+    """Eqs. rge_Pmat, rge_Dmat in the band basis (band-diagonal loops of Eqs. loopminus, loopplus; the bare vertex
+    through its band-basis projections) against the orbital flow: with the complete form-factor set of a 3x3
+    torus both are exact reformulations of the same one-loop RGE, so the band-basis flow equals the orbital flow
+    transformed with Eqs. mat_trafo_P, mat_trafo_D (pinned above by Eq. Pinband and unitarity), step by step
+    (fixed-step RK4 from T0 = 2 to 0.4).  A wrong loop (orbital projectors left in), the bare vertex missing its
+    momentum dependence, or a wrong prefactor fails it."""
+    if model == "rashba":
+        spec = inputs.rashba_hubbard(tp=-0.2, alpha=0.4, U=2.0, mu=-0.7, Lq=3, nc=1)
+    else:
+        spec = inputs.hubbard_square(tp=-0.25, U=2.0, Lq=3, nc=1, filling=0.0, mu=-0.5)
+    spec = spec.with_(ff_R=inputs.ff_complete(3))
+    o = oracle.Oracle(spec)
+    ob = oracle.Oracle(spec, basis="band", band_U=o.U)
+    assert np.array_equal(ob.U[5], np.eye(2))
+    y, _ = o.flow(T0=2.0, T_end=0.4, fixed_n=4, chmask=mask)
+    yb, _ = ob.flow(T0=2.0, T_end=0.4, fixed_n=4, chmask=mask)
+    yt = o.band_transform(o.U, y)
+    assert np.abs(yt).max() > 1e-2
+    assert np.abs(yb - yt).max() < 1e-12 * np.abs(yt).max()
+    if model == "rashba":
+        # with spin-orbit coupling the orbital-basis loops are not band-diagonal: a different computation
+        assert np.abs(yb - y).max() > 1e-3 * np.abs(y).max()
+    else:
+        # without it the eigenvectors are the unit vectors (degenerate bands): the two bases coincide
+        assert np.abs(yb - y).max() < 1e-12 * np.abs(y).max()
+
+
+def test_form_factor_convergence_of_the_flows_orbital_vs_band():
+    """Sec. 3.4: a form-factor expansion converges faster in the orbital basis than in the band basis.  The
+    particle-particle flow of the onsite Rashba-Hubbard vertex (P only, a 6x6 torus, T0 = 2 -> 0.5) keeps its
+    propagator in the onsite block in the orbital basis (Eq. sol_spin), so 5 bonds already give the complete set's
+    result; in the band basis the bare vertex and the propagator spread over many bonds (Eq. Pinband), and the
+    truncated flows approach the complete-set flow only as bonds are added."""
+    base = inputs.rashba_hubbard(tp=-0.2, alpha=0.3, U=2.5, mu=-0.9, Lq=6, nc=1)
+    full = base.with_(ff_R=inputs.ff_complete(6))
+    o_full = oracle.Oracle(full)
+    ob_full = oracle.Oracle(full, basis="band", band_U=o_full.U)
+    y_full, _ = o_full.flow(T0=2.0, T_end=0.5, fixed_n=3, chmask=1)
+    yb_full, _ = ob_full.flow(T0=2.0, T_end=0.5, fixed_n=3, chmask=1)
+
+    def onsite(y, spec):
+        i0 = [i for i, r in enumerate(spec.ff_R) if r[0] == 0 and r[1] == 0][0]
+        return y[0][:, i0 * 4:(i0 + 1) * 4, i0 * 4:(i0 + 1) * 4]
+
+    err_orb, err_band = [], []
+    for n_ff in (5, 9, 13):
+        sp = base.with_(ff_R=inputs.ff_set(n_ff))
+        o = oracle.Oracle(sp)
+        ob = oracle.Oracle(sp, basis="band", band_U=o.U)
+        y, _ = o.flow(T0=2.0, T_end=0.5, fixed_n=3, chmask=1)
+        yb, _ = ob.flow(T0=2.0, T_end=0.5, fixed_n=3, chmask=1)
+        ref_o, ref_b = onsite(y_full, full), onsite(yb_full, full)
+        err_orb.append(np.abs(onsite(y, sp) - ref_o).max() / np.abs(ref_o).max())
+        err_band.append(np.abs(onsite(yb, sp) - ref_b).max() / np.abs(ref_b).max())
+    assert max(err_orb) < 1e-12                        # the orbital flow is local: any bond set holds it
+    assert min(err_band) > 1e-4                        # the band flow needs more bonds
+    assert err_band[-1] < err_band[0]                  # and approaches the complete set as they are added
