@@ -335,6 +335,35 @@ def run_config_hubbard(stream, k=50):
     return res
 
 
+def leading_form_factor(spec, state, res, stream):
+    """Leading channel, momentum and form factor of a flow's last state (the survey's reading of the report): the
+    eigenvector of A_X(q*) with the largest eigenvalue in modulus, its weight per irrep form factor of C4v (the
+    library's tufrg_irrep_basis of the projected vertex), and the (shell, irrep) holding the most."""
+    import numpy as np
+    import torch
+    from paper_1710_08830_gb300.api import FP64, Model
+    m = Model(spec, FP64, stream=stream)
+    try:
+        W, lab = m.form_factors()
+    except Exception:
+        m.close()
+        return None
+    A, _ = m.project(torch.from_numpy(state).cuda())
+    Ai = m.irrep_basis(A).cpu().numpy()[res["lead_channel"], res["lead_q"]]
+    m.close()
+    ev, vec = np.linalg.eigh(0.5 * (Ai + Ai.conj().T))
+    v = vec[:, int(np.argmax(np.abs(ev)))]
+    w = (np.abs(v) ** 2).reshape(spec.n_ff, spec.n_s ** 2).sum(axis=1)
+    names = ("A1", "A2", "B1", "B2", "E")
+    per = {}
+    for i, (shell, gi, _) in enumerate(lab):
+        key = f"shell {int(shell)} {names[int(gi)]}"
+        per[key] = per.get(key, 0.0) + float(w[i])
+    best = max(per, key=per.get)
+    return {"channel": "PC"[res["lead_channel"]], "q": res["lead_q"], "form_factor": best, "weight": per[best],
+            "weights": {k: round(v2, 4) for k, v2 in sorted(per.items(), key=lambda kv: -kv[1]) if v2 > 1e-3}}
+
+
 def run_batch_flows(stream, n, seed=0):
     """n uneven Rashba/Hubbard flows (Lq in {16, 24, 32, 48}, N_ff in {5, 9, 13}) through tufrg_flow_batch and one by
     one, split precision; then the first crossing instance (smallest problem) again in FP64: its critical scale
@@ -378,6 +407,7 @@ def run_batch_flows(stream, n, seed=0):
             m.close()
         y32, r32 = out["split"]
         y64, r64 = out["fp64"]
+        lead_ff = leading_form_factor(sp, y64, r64, stream)
         # the vertex near the instability is ill-conditioned (it diverges at Lambda_c); compare the two flows also
         # at a fixed scale above it, T_end = 1.25 Lambda_c (no stop)
         above = {}
@@ -395,6 +425,7 @@ def run_batch_flows(stream, n, seed=0):
                     "vertex_at_1p25_lambda_c_split_vs_fp64_maxrel": float(np.abs(ya32 - ya64).max() / np.abs(ya64).max()),
                     "amax_at_1p25_lambda_c": above["fp64"][1]["amax"],
                     "speedup_split_over_fp64": r64["wall_s"] / r32["wall_s"],
+                    "leading_form_factor": lead_ff,
                     "note": "max|A| crosses the stop value 50: Lambda_c interpolated in ln T; final_vertex compares the last "
                             "accepted states (just past the crossing, where the vertex diverges and small differences "
                             "grow), the second error the two flows stopped at T = 1.25 Lambda_c"}

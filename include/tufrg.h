@@ -215,6 +215,22 @@ tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend);
  * split models in FP32.  Two-band models with M <= 64 (else TUFRG_ENOTSUP); stream ordered, no host sync. */
 tufrg_status tufrg_band_basis(tufrg_model *m, const void *d_state, void *d_out);
 
+/* Form factors of the irreducible representations of the point group C4v (Sec. 2: linear combinations of the plane
+ * waves that transform under an irreducible representation).  For a bond set closed under the eight point
+ * operations of the square lattice (as integer vectors), the bonds fall into shells (orbits) and each shell's
+ * combinations are f_i(k) = sum_R W[i][R] f_R(k), W real orthogonal: h_W [n_ff][n_ff] (row i over the bonds in the
+ * order of ff_R), h_labels [n_ff][3] = (shell, irrep, partner) with irrep 0..4 = A1, A2, B1, B2, E (e.g. the nearest-
+ * neighbour shell gives the extended s-wave A1, d_{x^2-y^2} B1 and the two p-waves E).  Within an E space (and a
+ * repeated irrep of a larger shell) the basis is one orthonormal choice.  Errors: TUFRG_EINVAL (NULL argument),
+ * TUFRG_ENOTSUP (bond set not closed under C4v). */
+tufrg_status tufrg_form_factors(const tufrg_model *m, double *h_W, int *h_labels);
+
+/* Exchange propagators in the irrep form factors: d_out = (W x 1) X (W x 1)^T per momentum and channel (inverse != 0:
+ * W^T in place of W, back to the bonds); d_state, d_out [2][Nq][M][M] complex device buffers (not the same buffer),
+ * rows and columns (form factor i, orbital pair) in the layouts of the state.  FP64; stream ordered.
+ * Errors: TUFRG_EINVAL, TUFRG_ENOTSUP (bond set not closed under C4v), TUFRG_ECUDA. */
+tufrg_status tufrg_irrep_basis(tufrg_model *m, const void *d_state, int inverse, void *d_out);
+
 /* Round n FP64 values at d_in to FP32 at d_out (device buffers, no overlap), to nearest with ties to
  * even: the rounding the split path applies to states, loop data and tables.  Stream ordered on
  * cuda_stream (NULL = legacy default stream).  Errors: TUFRG_EINVAL for NULL buffers with n > 0,

@@ -78,6 +78,10 @@ def lib():
             L.tufrg_model_info.restype = C.c_int
             L.tufrg_loop_momenta.argtypes = [vp, ip]
             L.tufrg_loop_momenta.restype = C.c_int
+            L.tufrg_form_factors.argtypes = [vp, vp, vp]
+            L.tufrg_form_factors.restype = C.c_int
+            L.tufrg_irrep_basis.argtypes = [vp, vp, i, vp]
+            L.tufrg_irrep_basis.restype = C.c_int
             L.tufrg_shard_classes.argtypes = [vp, ip, vp]
             L.tufrg_shard_classes.restype = C.c_int
             L.tufrg_rhs_shard_transform.argtypes = [vp, vp, i, vp, i, vp]
@@ -145,4 +149,5 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info",
-           "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish")
+           "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish", "tufrg_form_factors",
+           "tufrg_irrep_basis")

@@ -200,6 +200,25 @@ class Model:
         self._check(self._L.tufrg_rhs_host_batch(self._h, n, t_arr, s_arr, int(mask) | flag, o_arr))
         return outs_host
 
+    # ------------------------------------------------------------------ irrep form factors (C4v)
+    IRREPS = ("A1", "A2", "B1", "B2", "E")
+
+    def form_factors(self):
+        """(W [n_ff][n_ff], labels [n_ff][3] = (shell, irrep index, partner)): the form factors of the irreducible
+        representations of C4v over the bonds; raises (TUFRG_ENOTSUP) for a bond set not closed under the group."""
+        n = self.spec.n_ff
+        W = np.zeros((n, n))
+        lab = np.zeros((n, 3), np.int32)
+        self._check(self._L.tufrg_form_factors(self._h, W.ctypes.data, lab.ctypes.data))
+        return W, lab
+
+    def irrep_basis(self, state, inverse: bool = False, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The state with its form factors changed to the irrep combinations, (W x 1) X (W x 1)^T (inverse: back)."""
+        st = self._dev(state)
+        out = torch.empty_like(st) if out is None else out
+        self._check(self._L.tufrg_irrep_basis(self._h, _ptr(st), 1 if inverse else 0, _ptr(out)))
+        return out
+
     # ------------------------------------------------------------------ right-hand side over shards of momenta
     def shard_classes(self) -> np.ndarray:
         """Bond classes R'' (mod Lq) of the shard transforms, [ncls][2]."""

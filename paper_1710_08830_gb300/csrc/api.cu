@@ -495,7 +495,7 @@ void release(tufrg_model *m)
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
                     m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
-                    m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32};
+                    m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32, m->d_ffW};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -791,6 +791,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
 
     build_loop_tables(m);
     build_gather_tables(m);
+    build_irrep_basis(m);   // empty when the bond set is not closed under the point group
     // loop symmetries (TUFRG_SYMMETRY_AUTO, split two-band path)
     m->n_loop_q = m->Nq;
     if (m->basis == TUFRG_BASIS_BAND && !band_basis_supported(m))
@@ -1348,6 +1349,25 @@ tufrg_status upload_shard(tufrg_model *m, int n_q, const int *h_q_list)
     return TUFRG_OK;
 }
 }  // namespace
+
+tufrg_status tufrg_form_factors(const tufrg_model *m, double *h_W, int *h_labels)
+{
+    if (!m || !h_W || !h_labels) return TUFRG_EINVAL;
+    if (m->ffW.empty()) return TUFRG_ENOTSUP;
+    std::copy(m->ffW.begin(), m->ffW.end(), h_W);
+    std::copy(m->ff_labels.begin(), m->ff_labels.end(), h_labels);
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_irrep_basis(tufrg_model *m, const void *d_state, int inverse, void *d_out)
+{
+    if (!m || !d_state || !d_out) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (m->ffW.empty()) return fail(m, TUFRG_ENOTSUP, "the bond set is not closed under the point group");
+    if (d_state == d_out) return fail(m, TUFRG_EINVAL, "the transformation does not work in place");
+    CK(launch_irrep_basis(m, reinterpret_cast<const double2 *>(d_state), inverse ? 1 : 0, reinterpret_cast<double2 *>(d_out)),
+       "irrep form factors");
+    return TUFRG_OK;
+}
 
 tufrg_status tufrg_shard_classes(const tufrg_model *m, int *ncls, int *h_cls)
 {

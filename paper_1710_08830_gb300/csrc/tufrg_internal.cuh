@@ -308,6 +308,9 @@ struct tufrg_model {
     tufrg::LoopPlan plan{};
     int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
     int basis = TUFRG_BASIS_ORBITAL;   // single-particle basis of the flow
+    std::vector<double> ffW;        // [nff][nff] irrep form factors over the bonds (empty: set not C4v-closed)
+    std::vector<int> ff_labels;     // [nff][3] (shell, irrep A1 A2 B1 B2 E, partner)
+    double *d_ffW = nullptr;
     double2 *d_v0q = nullptr;       // band basis: [2][Nq][M][M] projected bare vertex per momentum (FP64)
     float2 *d_v0q32 = nullptr;      // its FP32 copy (split path)
     int *d_shard_q = nullptr;       // [Nq] momenta of a shard (sharded right-hand side)
@@ -388,6 +391,9 @@ cudaError_t launch_loops_list(tufrg_model *m, int mask, const int *d_list, int n
 // projections of the listed momenta whose state rows are stored in list order, [2][nlist][M][M]
 cudaError_t launch_project_local(tufrg_model *m, const double2 *d_state_local, const float2 *d_state32_local,
                                  int channel_mask, double2 *d_A, const int *qlist, int nlist);
+// form factors of the irreducible representations of C4v (k_irrep.cu)
+bool build_irrep_basis(tufrg_model *m);
+cudaError_t launch_irrep_basis(tufrg_model *m, const double2 *d_state, int inverse, double2 *d_out);
 bool loops_tc_supported(const tufrg_model *m);
 size_t loops_tc_w_bytes(const tufrg_model *m);
 cudaError_t launch_loops_tc(tufrg_model *m, int ch, float2 *acc);

@@ -888,3 +888,74 @@ def test_form_factor_convergence_of_the_flows_orbital_vs_band():
     assert max(err_orb) < 1e-12                        # the orbital flow is local: any bond set holds it
     assert min(err_band) > 1e-4                        # the band flow needs more bonds
     assert err_band[-1] < err_band[0]                  # and approaches the complete set as they are added
+
+
+# ---------------------------------------------------------------- irrep form factors (Sec. 2)
+
+@pytest.mark.parametrize("n_ff", [5, 9, 13])
+def test_irrep_form_factors_transform_under_the_point_group(n_ff):
+    """Sec. 2: linear combinations of the plane waves that transform under an irreducible representation of the point
+    group, orthonormal (the only property the method needs).  W is orthogonal; each A1 / A2 / B1 / B2 row is an
+    eigenvector of every bond permutation D(g) with the character of its irrep as eigenvalue; each E space is
+    invariant with the E character as trace; (1/N) sum_k f_i f_j* = delta_ij on a mesh."""
+    from oracle import irreps
+    ff = inputs.ff_set(n_ff)
+    W, lab = irreps.basis(ff)
+    assert W.shape == (n_ff, n_ff)
+    assert np.abs(W @ W.T - np.eye(n_ff)).max() < 1e-13
+    chi = {"A1": [1, 1, 1, 1, 1], "A2": [1, 1, 1, -1, -1], "B1": [1, -1, 1, 1, -1], "B2": [1, -1, 1, -1, 1],
+           "E": [2, 0, -2, 0, 0]}
+    cls = {"E": 0, "C4": 1, "C2": 2, "sv": 3, "sd": 4}
+    for g, c in irreps.operations():
+        D = irreps.perm_rep(ff, g)
+        for s in sorted({l[0] for l in lab}):
+            for gi, name in enumerate(irreps.IRREPS):
+                rows = [i for i, l in enumerate(lab) if l[0] == s and l[1] == gi]
+                if not rows:
+                    continue
+                B = W[rows]                                   # [d][n]
+                img = B @ D.T                                 # rows D(g) w
+                if name != "E":
+                    assert np.abs(img - chi[name][cls[c]] * B).max() < 1e-12
+                else:
+                    rep = img @ B.T                           # the E space is invariant: img = rep B
+                    assert np.abs(rep @ B - img).max() < 1e-12
+                    assert np.trace(rep) == pytest.approx(chi["E"][cls[c]] * len(rows) / 2, abs=1e-12)
+    L = 8
+    kx, ky = np.divmod(np.arange(L * L), L)
+    f = np.exp(-2j * np.pi * (np.outer(kx, ff[:, 0]) + np.outer(ky, ff[:, 1])) / L)   # [k][R]
+    fi = f @ W.T
+    assert np.abs(fi.T @ fi.conj() / (L * L) - np.eye(n_ff)).max() < 1e-13
+
+
+def test_irrep_form_factors_closed_forms():
+    """The familiar functions: on the nearest-neighbour shell the extended s-wave (cos kx + cos ky), d_{x^2-y^2}
+    (cos kx - cos ky) and the p-waves (sin kx, sin ky); on the next-nearest shell cos kx cos ky (A1) and
+    sin kx sin ky (B2, d_xy), each up to its normalisation and sign."""
+    from oracle import irreps
+    ff = inputs.ff_set(9)
+    W, lab = irreps.basis(ff)
+    k = np.random.default_rng(3).uniform(-np.pi, np.pi, (40, 2))
+    f = np.exp(-1j * (np.outer(k[:, 0], ff[:, 0]) + np.outer(k[:, 1], ff[:, 1]))) @ W.T   # [k][i]
+    cx, cy, sx, sy = np.cos(k[:, 0]), np.cos(k[:, 1]), np.sin(k[:, 0]), np.sin(k[:, 1])
+
+    def proportional(a, b):
+        c = np.vdot(b, a) / np.vdot(b, b)
+        return abs(c) > 0.1 and np.abs(a - c * b).max() < 1e-12
+
+    shells = {}
+    for i, (s, gi, p) in enumerate(lab):
+        shells.setdefault(s, {}).setdefault(irreps.IRREPS[gi], []).append(i)
+    nn = [s for s in shells if len(shells[s].get("B1", [])) == 1 and len(shells[s]["A1"]) == 1
+          and np.abs(ff[[i for i in range(9) if np.abs(W[shells[s]["A1"][0], i]) > 1e-9]]).sum(axis=1).max() == 1]
+    nnn = [s for s in shells if "B2" in shells[s]]
+    assert len(nn) == 1 and len(nnn) == 1
+    s1, s2 = nn[0], nnn[0]
+    assert proportional(f[:, shells[s1]["A1"][0]], cx + cy)
+    assert proportional(f[:, shells[s1]["B1"][0]], cx - cy)
+    E = f[:, shells[s1]["E"]]                                    # spans sin kx, sin ky
+    for target in (sx, sy):
+        c, *_ = np.linalg.lstsq(E, target.astype(complex), rcond=None)
+        assert np.abs(E @ c - target).max() < 1e-12
+    assert proportional(f[:, shells[s2]["A1"][0]], cx * cy)
+    assert proportional(f[:, shells[s2]["B2"][0]], sx * sy)
