@@ -6,9 +6,10 @@
 // Inference keeps the activations in FP32, so the network is a smooth function of its inputs (BF16
 // inputs and activations would make it a staircase in log T that an adaptive integrator resolves with
 // ever smaller steps).  Loss: mean squared error.
-// Kernels: a tiled BF16 GEMM with optional transposes (64 x 64 tiles, FP32 accumulation, fixed
-// summation order), GELU forward/backward, the loss gradient, bias gradients as fixed-order column
-// sums, and Adam.  Nothing here is part of the paper: it serves the surrogate of the loops.
+// Kernels: the GEMMs on the tensor cores (k_mlp_tc.cu: BF16 x BF16 for training, FP32 activations split into
+// TF32 parts x BF16 weights for inference, FP32 accumulation, fixed summation order), GELU forward/backward, the
+// loss gradient, bias gradients as fixed-order column sums, and Adam.  Nothing here is part of the paper: it
+// serves the surrogate of the loops.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -39,64 +40,13 @@ struct tufrg_mlp {
     __nv_bfloat16 *dZ16 = nullptr;         // BF16 copy of dZ
     float *dZ = nullptr;                   // FP32 dZ
     float *loss = nullptr;                 // [1]
+    void *ws = nullptr;                    // packed GEMM operands (tensor cores)
+    size_t ws_bytes = 0;
+    int *d_err = nullptr;                  // raised when a bounded device wait of a GEMM gave up
 };
 
 namespace tufrg {
 namespace {
-
-constexpr int GB = 64, GK = 16;
-
-__device__ __forceinline__ float to_f(float x) { return x; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
-
-// C[M][N] = op(A)[M][K] op(B)[K][N] (+ bias[N]); A is BF16 (training) or FP32 (inference activations)
-template <typename TA>
-__global__ void __launch_bounds__(256) gemm_bf16_kernel(const TA *A, int lda, int ta, const __nv_bfloat16 *B,
-                                                        int ldb, int tb, float *C, int ldc, int M, int N, int K,
-                                                        const float *bias, const int *skip)
-{
-    if (skip && *skip) return;   // uniform over the grid
-    __shared__ float As[GK][GB + 1];
-    __shared__ float Bs[GK][GB + 1];
-    const int row0 = blockIdx.y * GB, col0 = blockIdx.x * GB;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int e = threadIdx.x; e < GB * GK; e += 256) {
-            const int r = e / GK, kk = e % GK, gr = row0 + r, gk = k0 + kk;
-            float v = 0.f;
-            if (gr < M && gk < K) v = to_f(ta ? A[(size_t)gk * lda + gr] : A[(size_t)gr * lda + gk]);
-            As[kk][r] = v;
-        }
-        for (int e = threadIdx.x; e < GK * GB; e += 256) {
-            const int kk = e / GB, c = e % GB, gk = k0 + kk, gc = col0 + c;
-            float v = 0.f;
-            if (gk < K && gc < N) v = __bfloat162float(tb ? B[(size_t)gc * ldb + gk] : B[(size_t)gk * ldb + gc]);
-            Bs[kk][c] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; kk++) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int r = row0 + ty * 4 + i, c = col0 + tx * 4 + j;
-            if (r < M && c < N) C[(size_t)r * ldc + c] = acc[i][j] + (bias ? bias[c] : 0.f);
-        }
-}
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x)
@@ -179,15 +129,6 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, __nv_b
 
 int gsz(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
 
-template <typename TA>
-cudaError_t gemm(cudaStream_t s, const TA *A, int lda, int ta, const __nv_bfloat16 *B, int ldb, int tb, float *C,
-                 int ldc, int M, int N, int K, const float *bias, const int *skip = nullptr)
-{
-    const dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
-    gemm_bf16_kernel<<<grid, 256, 0, s>>>(A, lda, ta, B, ldb, tb, C, ldc, M, N, K, bias, skip);
-    return cudaGetLastError();
-}
-
 tufrg_status mfail(tufrg_mlp *n, tufrg_status st, const std::string &msg)
 {
     if (n) n->err = msg;
@@ -199,6 +140,15 @@ tufrg_status mfail(tufrg_mlp *n, tufrg_status st, const std::string &msg)
         cudaError_t _e = (expr);                                                             \
         if (_e != cudaSuccess) return mfail(n, TUFRG_ECUDA, std::string(where) + ": " + cudaGetErrorString(_e)); \
     } while (0)
+
+// C = op(A) op(B) (+ bias) on the tensor cores with the network's operand scratch
+template <typename TA>
+cudaError_t gemm(tufrg_mlp *n, cudaStream_t s, const TA *A, int lda, int ta, const __nv_bfloat16 *B, int ldb, int tb,
+                 float *C, int ldc, int M, int N, int K, const float *bias, const int *skip = nullptr)
+{
+    if (mlp_tc_scratch_bytes(M, N, K) > n->ws_bytes) return cudaErrorInvalidValue;   // sized by ensure_capacity
+    return mlp_gemm_tc<TA>(s, A, lda, ta, B, ldb, tb, C, ldc, M, N, K, bias, skip, n->ws, n->d_err);
+}
 
 tufrg_status ensure_capacity(tufrg_mlp *n, int batch)
 {
@@ -219,6 +169,20 @@ tufrg_status ensure_capacity(tufrg_mlp *n, int batch)
     MK(cudaMalloc(&n->dA2, sizeof(float) * (size_t)batch * wmax), "cudaMalloc gradients");
     MK(cudaMalloc(&n->dZ, sizeof(float) * (size_t)batch * wmax), "cudaMalloc gradients");
     MK(cudaMalloc(&n->dZ16, sizeof(__nv_bfloat16) * (size_t)batch * wmax), "cudaMalloc gradients");
+    // operand scratch of the largest GEMM: the forward (batch x dout x din), weight-gradient (din x dout x batch)
+    // and input-gradient (batch x din x dout) products of every layer
+    size_t ws = 0;
+    for (int l = 0; l < n->n_layers; l++) {
+        ws = std::max(ws, mlp_tc_scratch_bytes(batch, n->dout[l], n->din[l]));
+        ws = std::max(ws, mlp_tc_scratch_bytes(n->din[l], n->dout[l], batch));
+        ws = std::max(ws, mlp_tc_scratch_bytes(batch, n->din[l], n->dout[l]));
+    }
+    if (ws > n->ws_bytes) {
+        cudaFree(n->ws);
+        n->ws = nullptr;
+        MK(cudaMalloc(&n->ws, ws), "cudaMalloc GEMM operands");
+        n->ws_bytes = ws;
+    }
     n->cap = batch;
     return TUFRG_OK;
 }
@@ -236,7 +200,7 @@ tufrg_status forward(tufrg_mlp *n, const float *X, int batch, float *Y)
     for (int l = 0; l < n->n_layers; l++) {
         const bool last = l == n->n_layers - 1;
         float *out = last ? Y : n->Z[l];
-        MK(gemm(s, n->H[l], n->din[l], 0, n->d_w16 + n->woff[l], n->dout[l], 0, out, n->dout[l], batch, n->dout[l],
+        MK(gemm(n, s, n->H[l], n->din[l], 0, n->d_w16 + n->woff[l], n->dout[l], 0, out, n->dout[l], batch, n->dout[l],
                 n->din[l], n->d_w + n->boff[l]), "layer GEMM");
         if (!last) {
             gelu_fwd_kernel<<<gsz((size_t)batch * n->dout[l]), 256, 0, s>>>(n->Z[l], n->H[l + 1], (size_t)batch * n->dout[l],
@@ -258,7 +222,7 @@ tufrg_status infer(tufrg_mlp *n, const float *X, int batch, float *Y, const int 
     for (int l = 0; l < n->n_layers; l++) {
         const bool last = l == n->n_layers - 1;
         float *out = last ? Y : n->Z[l];
-        MK(gemm(s, in, n->din[l], 0, n->d_w16 + n->woff[l], n->dout[l], 0, out, n->dout[l], batch, n->dout[l], n->din[l],
+        MK(gemm(n, s, in, n->din[l], 0, n->d_w16 + n->woff[l], n->dout[l], 0, out, n->dout[l], batch, n->dout[l], n->din[l],
                 n->d_w + n->boff[l], skip), "layer GEMM");
         if (!last) {
             gelu_fwd_kernel<<<gsz((size_t)batch * n->dout[l]), 256, 0, s>>>(n->Z[l], n->Z[l], (size_t)batch * n->dout[l],
@@ -281,14 +245,14 @@ tufrg_status backward(tufrg_mlp *n, int batch, const float *dY, float *g)
         act_bwd_kernel<<<gsz(cnt), 256, 0, s>>>(up, n->Z[l], hidden ? 1 : 0, n->dZ, n->dZ16, cnt);
         MK(cudaGetLastError(), "activation backward");
         // dW = H^T dZ  (din x dout), db = column sums of dZ
-        MK(gemm(s, n->H[l], n->din[l], 1, n->dZ16, n->dout[l], 0, g + n->woff[l], n->dout[l], n->din[l], n->dout[l],
+        MK(gemm(n, s, n->H[l], n->din[l], 1, n->dZ16, n->dout[l], 0, g + n->woff[l], n->dout[l], n->din[l], n->dout[l],
                 batch, nullptr), "weight gradient");
         colsum_kernel<<<(n->dout[l] + 127) / 128, 128, 0, s>>>(n->dZ, batch, n->dout[l], g + n->boff[l]);
         MK(cudaGetLastError(), "bias gradient");
         if (l > 0) {
             // dH = dZ W^T  (batch x din)
             float *dst = (up == n->dA) ? n->dA2 : n->dA;
-            MK(gemm(s, n->dZ16, n->dout[l], 0, n->d_w16 + n->woff[l], n->dout[l], 1, dst, n->din[l], batch, n->din[l],
+            MK(gemm(n, s, n->dZ16, n->dout[l], 0, n->d_w16 + n->woff[l], n->dout[l], 1, dst, n->din[l], batch, n->din[l],
                     n->dout[l], nullptr), "input gradient");
             up = dst;
         }
@@ -341,6 +305,8 @@ tufrg_status tufrg_mlp_create(int n_in, int width, int depth, int n_out, unsigne
     MK(cudaMalloc(&n->d_m, sizeof(float) * off), "cudaMalloc moments");
     MK(cudaMalloc(&n->d_v, sizeof(float) * off), "cudaMalloc moments");
     MK(cudaMalloc(&n->loss, sizeof(float)), "cudaMalloc loss");
+    MK(cudaMalloc(&n->d_err, sizeof(int)), "cudaMalloc error flag");
+    MK(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream), "zero");
     MK(cudaMemcpyAsync(n->d_w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice, n->stream), "copy parameters");
     MK(cudaMemsetAsync(n->d_m, 0, sizeof(float) * off, n->stream), "zero");
     MK(cudaMemsetAsync(n->d_v, 0, sizeof(float) * off, n->stream), "zero");
@@ -356,7 +322,7 @@ void tufrg_mlp_free(tufrg_mlp *n)
     cudaStreamSynchronize(n->stream);
     for (auto p : n->Z) cudaFree(p);
     for (auto p : n->H) cudaFree(p);
-    void *ptrs[] = {n->d_w, n->d_w16, n->d_g, n->d_m, n->d_v, n->loss, n->dA, n->dA2, n->dZ16, n->dZ};
+    void *ptrs[] = {n->d_w, n->d_w16, n->d_g, n->d_m, n->d_v, n->loss, n->dA, n->dA2, n->dZ16, n->dZ, n->ws, n->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete n;
@@ -407,8 +373,11 @@ tufrg_status tufrg_mlp_gradients(tufrg_mlp *n, const float *d_X, const float *d_
     MK(cudaGetLastError(), "loss");
     if ((st = backward(n, batch, dY, d_grad)) != TUFRG_OK) return st;
     if (h_loss) {
+        int e = 0;
         MK(cudaMemcpyAsync(h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream), "copy loss");
+        MK(cudaMemcpyAsync(&e, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream), "copy error flag");
         MK(cudaStreamSynchronize(n->stream), "sync");
+        if (e) return mfail(n, TUFRG_ETIMEOUT, "a bounded device-side wait of a GEMM gave up");
     }
     return TUFRG_OK;
 }

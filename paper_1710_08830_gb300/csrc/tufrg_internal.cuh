@@ -421,6 +421,11 @@ cudaError_t launch_loops2(tufrg_model *m, int ch);
 cudaError_t launch_loops2_ex(tufrg_model *m, int ch, const int *s_list, int n_list, float2 *part, const int *skip);
 cudaError_t launch_surrogate(tufrg_model *m, int channel_mask);
 cudaError_t mlp_forward_on(tufrg_mlp *n, cudaStream_t s, const float *X, int batch, float *Y, const int *skip);
+// the network's GEMMs on the tensor cores (k_mlp_tc.cu); TA = __nv_bfloat16 (training) or float (inference)
+size_t mlp_tc_scratch_bytes(int M, int N, int K);
+template <typename TA>
+cudaError_t mlp_gemm_tc(cudaStream_t s, const TA *A, int lda, int ta, const struct __nv_bfloat16 *B, int ldb, int tb,
+                        float *C, int ldc, int M, int N, int K, const float *bias, const int *skip, void *ws, int *err);
 cudaError_t surrogate_rearm(tufrg_model *m);
 void mlp_dims(const tufrg_mlp *n, int *n_in, int *n_out);
 

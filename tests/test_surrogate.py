@@ -234,3 +234,18 @@ def test_surrogate_trained_on_the_family_inside_a_flow(gpu):
         else:
             assert acc > 0
         m.close()
+    # the configuration as it is stated: residual tolerance 1e-3, the stop value 50, down to T_end = 0.02 (no member
+    # of the family crosses: a time to T_end); what the network gains or loses in wall time against the direct flow
+    direct.flow(stop=50.0)
+    y50, r50 = direct.flow(stop=50.0)
+    m = Model(spec, SPLIT32, products=PRODUCTS_SIMT)
+    surrogate.attach(m, tr, alpha, tp, mu, tol=1e-3)
+    m.flow(stop=50.0)
+    surrogate.attach(m, tr, alpha, tp, mu, tol=1e-3)
+    y51, r51 = m.flow(stop=50.0)
+    acc, rej, skip = surrogate.stats(m)
+    print(f"as stated (tolerance 1e-3, stop 50, T_end 0.02): direct {r50['wall_s'] * 1e3:.1f} ms, with the network "
+          f"{r51['wall_s'] * 1e3:.1f} ms (gain {r50['wall_s'] / r51['wall_s'] - 1:+.1%}); kept {acc}, rejected {rej}, "
+          f"skipped {skip}")
+    assert torch.equal(y50, y51) and (acc, rej) == (0, 1)
+    m.close()
