@@ -15,15 +15,18 @@
 // product as four real MMA streams (the minus of -Ai Bi by the descriptor's negate-A bit), exactly like the
 // V.L.V products.  The x phases e^{-+ i kx dx} are applied afterwards by loops_tc_xsum over the written columns.
 //
+// The left operand (the phased projectors, four TF32 planes) lives in tensor memory: the producers write it with
+// tcgen05.st, and the MMAs read it from there, so shared memory carries only the right operand.
 // One persistent CTA per SM walks its (momentum group, column) items.  Warp roles:
 //   warps 0-15  producers: per stage (4 ky rows = K of 24) they stage the raw eigenvectors and Fermi entries of
 //               the 4 summation points and their 12 partners (cp.async, two stages ahead, four buffers), form
-//               the pair weights and row phases, then write the operands' TF32 hi/lo planes in the K-major
-//               core-matrix layout (each thread one ky row of one row of A and of B);
+//               the pair weights and row phases, then write the operands' TF32 hi/lo planes: A into tensor memory
+//               (lane = row), B into shared memory in the K-major core-matrix layout (each thread one ky row of
+//               one row of A and of B);
 //   warp 16     TMEM allocation and the MMA issuer (one thread): 36 MMAs per stage;
 //   warps 17-20 epilogue: tensor memory -> W in global memory (coalesced, row index fastest).
-// Two stage buffers (mbarriers full / empty) and two tensor-memory accumulators (mbarriers acc_full / acc_empty),
-// so operand generation, MMAs and the epilogue of the previous column overlap.  Every wait is bounded; on time-out
+// Two stage buffers (mbarriers full / empty) so operand generation and MMAs overlap; one tensor-memory accumulator
+// (mbarriers acc_full / acc_empty): the next column's MMAs start once the epilogue has read the previous one.  Every wait is bounded; on time-out
 // the kernel raises the error flag, every role stops, the MMAs in flight are waited for (bounded), the
 // cp.async copies drained, and the tensor memory is freed.
 #include <algorithm>
@@ -48,12 +51,15 @@ constexpr int NPROD = 512;                   // producer threads, warps 0-15: th
 constexpr int MMA_WARP = 16;                 // warps 17-20: epilogue
 constexpr int NTHREADS = 21 * 32;
 constexpr int NRAW = 4;                      // raw staging buffers (stage n + 2 is fetched while n is formed)
-constexpr unsigned A_PLANE = TM * KST * 4, B_PLANE = TN * KST * 4;   // bytes per plane and stage
-constexpr unsigned STAGE_BYTES = 4 * (A_PLANE + B_PLANE);           // planes: Re hi, Re lo, Im hi, Im lo
+constexpr unsigned B_PLANE = TN * KST * 4;   // bytes per plane and stage of the right operand (shared memory)
+constexpr unsigned STAGE_BYTES = 4 * B_PLANE;   // planes: Re hi, Re lo, Im hi, Im lo
+// tensor memory: accumulator Re at [0, TN), Im at [128, 128 + TN); left operand of stage b at 256 + 128 b, plane p
+// at + 32 p (K = 24 columns used)
+constexpr unsigned ACC_IM = 128, A_COL0 = 256, A_STAGE_COLS = 128, A_PLANE_COLS = 32;
 constexpr int NPTS = KB * (1 + GRP);         // raw points per stage: 4 summation points, then [j][kb] partners
 constexpr int CU = NS2 * 8 / 16, CF = NS * 16 / 16, CP = CU + CF;   // 16-byte chunks per point: U, Fermi entries
 constexpr unsigned RAW_U = NPTS * NS2 * 8, RAW_BYTES = RAW_U + NPTS * NS * 16;
-constexpr unsigned TMEM_COLS = 512;          // accumulator c: Re at 256 c, Im at 256 c + 128
+constexpr unsigned TMEM_COLS = 512;
 constexpr unsigned SW_BYTES = GRP * KB * NS * 8 * 4;         // pair weights, rows padded to 8
 constexpr size_t SMEM_BYTES = 2 * (size_t)STAGE_BYTES + NRAW * (size_t)RAW_BYTES + SW_BYTES + KB * NDYM * 8 + 4 * NPTS * 4;
 
@@ -148,6 +154,32 @@ __device__ __forceinline__ void put6(float *planes, unsigned plane_floats, int r
     }
 }
 
+// the six K values kb * 6 + l of this lane's row of the left operand into tensor memory: four planes (Re hi, Re lo,
+// Im hi, Im lo, truncation split) at columns col0 + 32 p + 6 kb + l, as a 4 + 2 (kb even) or 2 + 4 (kb odd) column
+// split so that every store starts at a multiple of its width; warp-collective (every lane of the warp)
+__device__ __forceinline__ void put6_tmem(unsigned col0, int kb, const float2 (&v)[NS])
+{
+    const unsigned c = col0 + 6 * kb;
+    const bool even = (kb & 1) == 0;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        float t[NS];
+#pragma unroll
+        for (int l = 0; l < NS; l++) {
+            const float x = p < 2 ? v[l].x : v[l].y;
+            t[l] = (p & 1) ? x - tf32_trunc(x) : tf32_trunc(x);
+        }
+        const unsigned cp = c + p * A_PLANE_COLS;
+        if (even) {
+            tc::tmem_st4(cp, t[0], t[1], t[2], t[3]);
+            tc::tmem_st2(cp + 4u, t[4], t[5]);
+        } else {
+            tc::tmem_st2(cp, t[0], t[1]);
+            tc::tmem_st4(cp + 2u, t[2], t[3], t[4], t[5]);
+        }
+    }
+}
+
 __device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
 
 template <int WHICH>
@@ -187,14 +219,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
         abort_flag = 0;
         stop = 0;
     }
-    // padding rows (A rows 108..127, B rows 108..111) are zero in both stage buffers for the whole kernel
-    for (int i = tid; i < 2 * 4 * (TM - ROWS + TN - COLS) * KST; i += NTHREADS) {
-        const int per_buf = 4 * (TM - ROWS + TN - COLS) * KST, b = i / per_buf, r0 = i % per_buf;
-        const int plane = r0 / ((TM - ROWS + TN - COLS) * KST), r1 = r0 % ((TM - ROWS + TN - COLS) * KST);
+    // padding rows of B (108..111) are zero in both stage buffers for the whole kernel (the padding lanes of A are
+    // written as zeros with every stage)
+    for (int i = tid; i < 2 * 4 * (TN - COLS) * KST; i += NTHREADS) {
+        const int per_buf = 4 * (TN - COLS) * KST, b = i / per_buf, r0 = i % per_buf;
+        const int plane = r0 / ((TN - COLS) * KST), r1 = r0 % ((TN - COLS) * KST);
         const int row = r1 / KST, k = r1 % KST;
         float *base = reinterpret_cast<float *>(stage(b));
-        if (row < TM - ROWS) base[plane * (A_PLANE / 4) + tc::core_off(ROWS + row, k, TM)] = 0.f;
-        else base[4 * (A_PLANE / 4) + plane * (B_PLANE / 4) + tc::core_off(COLS + row - (TM - ROWS), k, TN)] = 0.f;
+        base[plane * (B_PLANE / 4) + tc::core_off(COLS + row, k, TN)] = 0.f;
     }
     tc::fence_smem_async();
     tc::fence_before();
@@ -279,31 +311,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
             if (tid == 0) stop = *(volatile int *)&abort_flag;
             bar_producers();
             if (stop) break;   // every producer reads the same value: they leave the loop together
-            float *pa = reinterpret_cast<float *>(stage(buf)), *pb = pa + 4 * (A_PLANE / 4);
-            float2 va[NS], vb[NS];
+            float *pb = reinterpret_cast<float *>(stage(buf));
+            float2 va[NS];
+#pragma unroll
+            for (int l = 0; l < NS; l++) va[l] = make_float2(0.f, 0.f);   // the padding lanes of A (rows 108..127)
             if (r < ROWS) {
                 // A row r = (dy, t1 t3): e^{-+ i ky dy} rho^l_{t1 t3}(k) at K = kb * 6 + l (zero for a missing row: the
                 // phase is zero there, and so are the raw values of a point that does not exist)
-                {
-                    const int dyi = r / NS2, ab = r % NS2, t1 = ab / NS, t3 = ab % NS;
-                    const float2 ph = sPh[kb * NDYM + dyi];
-                    float2 u[NS], w[NS];
-                    ld6(rU + kb * NS2 + t1 * NS, u);
-                    ld6(rU + kb * NS2 + t3 * NS, w);
+                const int dyi = r / NS2, ab = r % NS2, t1 = ab / NS, t3 = ab % NS;
+                const float2 ph = sPh[kb * NDYM + dyi];
+                float2 u[NS], w[NS];
+                ld6(rU + kb * NS2 + t1 * NS, u);
+                ld6(rU + kb * NS2 + t3 * NS, w);
 #pragma unroll
-                    for (int l = 0; l < NS; l++) {
-                        // rho = u conj(w) = u w.x + (u.y, -u.x) w.y;  ph rho = rho ph.x + (-rho.y, rho.x) ph.y
-                        const float2 rho = __ffma2_rn(make_float2(u[l].y, -u[l].x), make_float2(w[l].y, w[l].y),
-                                                      __fmul2_rn(u[l], make_float2(w[l].x, w[l].x)));
-                        va[l] = __ffma2_rn(make_float2(-rho.y, rho.x), make_float2(ph.y, ph.y),
-                                           __fmul2_rn(rho, make_float2(ph.x, ph.x)));
-                    }
+                for (int l = 0; l < NS; l++) {
+                    // rho = u conj(w) = u w.x + (u.y, -u.x) w.y;  ph rho = rho ph.x + (-rho.y, rho.x) ph.y
+                    const float2 rho = __ffma2_rn(make_float2(u[l].y, -u[l].x), make_float2(w[l].y, w[l].y),
+                                                  __fmul2_rn(u[l], make_float2(w[l].x, w[l].x)));
+                    va[l] = __ffma2_rn(make_float2(-rho.y, rho.x), make_float2(ph.y, ph.y),
+                                       __fmul2_rn(rho, make_float2(ph.x, ph.x)));
                 }
-                // B row r = (s_j, t2 t4): T^l_{t2 t4} = sum_l2 w_{l l2} rho'^{l2}_{t2 t4} at K = kb * 6 + l (the weights
-                // of a missing row or momentum are zero)
-                {
+            }
+            // the MMAs that read this stage (tensor-memory A, shared-memory B) two stages ago must be complete before
+            // it is overwritten
+            int ok = 1;
+            if (n >= 2 && lane == 0)
+                ok = tc::mbar_wait_or_abort(tc::smem_u32(&empty[buf]), ((n >> 1) - 1) & 1, &abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                // raise the flag and keep the producers in step: all of them leave at the next stage's check
+                if (lane == 0) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(a.err, 1);
+                }
+            } else {
+                tc::fence_after();
+                // A: this warp's 32 lanes (rows) of the stage's tensor-memory columns, every lane (also padding)
+                put6_tmem(tmem + ((unsigned)((warp & 3) * 32) << 16) + A_COL0 + buf * A_STAGE_COLS, kb, va);
+                if (r < ROWS) {
+                    // B row r = (s_j, t2 t4): T^l_{t2 t4} = sum_l2 w_{l l2} rho'^{l2}_{t2 t4} at K = kb * 6 + l (the
+                    // weights of a missing row or momentum are zero)
                     const int j = r / NS2, cd = r % NS2, t2 = cd / NS, t4 = cd % NS, pp = KB + j * KB + kb;
-                    float2 x[NS], y[NS];
+                    float2 x[NS], y[NS], vb[NS];
                     ld6(rU + pp * NS2 + t2 * NS, x);
                     ld6(rU + pp * NS2 + t4 * NS, y);
                     float2 rho[NS];
@@ -326,25 +375,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
                         for (int l2 = 1; l2 < NS; l2++) t = __ffma2_rn(make_float2(wl[l2], wl[l2]), rho[l2], t);
                         vb[l1] = t;
                     }
-                }
-            }
-            // the MMAs that read this stage buffer two stages ago must be complete before it is overwritten
-            int ok = 1;
-            if (n >= 2 && lane == 0)
-                ok = tc::mbar_wait_or_abort(tc::smem_u32(&empty[buf]), ((n >> 1) - 1) & 1, &abort_flag) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                // raise the flag and keep the producers in step: all of them leave at the next stage's check
-                if (lane == 0) {
-                    atomicExch(&abort_flag, 1);
-                    atomicExch(a.err, 1);
-                }
-            } else {
-                if (r < ROWS) {
-                    put6(pa, A_PLANE / 4, r, kb, TM, va);
                     put6(pb, B_PLANE / 4, r, kb, TN, vb);
                 }
+                tc::tmem_wait_st();
                 tc::fence_smem_async();
+                tc::fence_before();
                 tc::mbar_arrive(tc::smem_u32(&full[buf]));
             }
             if (++st == spc) {
@@ -360,34 +395,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
             bool ok = true;
             int n = 0;
             for (int col = 0; col < my_items && ok; col++) {
-                const int cb = col & 1;
-                if (col >= 2 && !tc::mbar_wait_or_abort(tc::smem_u32(&acce[cb]), ((col >> 1) - 1) & 1, &abort_flag)) {
+                // the accumulator must have been read by the epilogue of the previous column
+                if (col >= 1 && !tc::mbar_wait_or_abort(tc::smem_u32(&acce[0]), (col - 1) & 1, &abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc::fence_after();
-                const unsigned tr = tmem + 256u * cb, ti = tr + 128u;
+                const unsigned tr = tmem, ti = tmem + ACC_IM;
                 for (int st = 0; st < a.spc; st++, n++) {
                     const int b = n & 1;
                     if (!tc::mbar_wait_or_abort(tc::smem_u32(&full[b]), (n >> 1) & 1, &abort_flag)) { ok = false; break; }
                     tc::fence_after();
-                    const unsigned sa = tc::smem_u32(stage(b)), sb = sa + 4 * A_PLANE;
+                    const unsigned sb = tc::smem_u32(stage(b)), ta = tmem + A_COL0 + b * A_STAGE_COLS;
 #pragma unroll
                     for (int kk = 0; kk < KST / 8; kk++) {
-                        const unsigned ao = kk * 2 * (TM / 8) * 128, bo = kk * 2 * (TN / 8) * 128;
-                        const unsigned long long arh = tc::smem_desc(sa + 0 * A_PLANE + ao, TM), arl = tc::smem_desc(sa + 1 * A_PLANE + ao, TM);
-                        const unsigned long long aih = tc::smem_desc(sa + 2 * A_PLANE + ao, TM), ail = tc::smem_desc(sa + 3 * A_PLANE + ao, TM);
+                        const unsigned bo = kk * 2 * (TN / 8) * 128;
+                        // A planes in tensor memory: K-step kk = 8 columns of each plane
+                        const unsigned arh = ta + 0 * A_PLANE_COLS + 8 * kk, arl = ta + 1 * A_PLANE_COLS + 8 * kk;
+                        const unsigned aih = ta + 2 * A_PLANE_COLS + 8 * kk, ail = ta + 3 * A_PLANE_COLS + 8 * kk;
                         const unsigned long long brh = tc::smem_desc(sb + 0 * B_PLANE + bo, TN), brl = tc::smem_desc(sb + 1 * B_PLANE + bo, TN);
                         const unsigned long long bih = tc::smem_desc(sb + 2 * B_PLANE + bo, TN), bil = tc::smem_desc(sb + 3 * B_PLANE + bo, TN);
                         const unsigned first = (st == 0 && kk == 0) ? 0u : 1u;
-                        tc::mma_tf32(tr, arh, brh, id, first);  tc::mma_tf32(tr, arh, brl, id, 1u);  tc::mma_tf32(tr, arl, brh, id, 1u);
-                        tc::mma_tf32(tr, aih, bih, idn, 1u);    tc::mma_tf32(tr, aih, bil, idn, 1u); tc::mma_tf32(tr, ail, bih, idn, 1u);
-                        tc::mma_tf32(ti, arh, bih, id, first);  tc::mma_tf32(ti, arh, bil, id, 1u);  tc::mma_tf32(ti, arl, bih, id, 1u);
-                        tc::mma_tf32(ti, aih, brh, id, 1u);     tc::mma_tf32(ti, aih, brl, id, 1u);  tc::mma_tf32(ti, ail, brh, id, 1u);
+                        tc::mma_tf32_ta(tr, arh, brh, id, first);  tc::mma_tf32_ta(tr, arh, brl, id, 1u);  tc::mma_tf32_ta(tr, arl, brh, id, 1u);
+                        tc::mma_tf32_ta(tr, aih, bih, idn, 1u);    tc::mma_tf32_ta(tr, aih, bil, idn, 1u); tc::mma_tf32_ta(tr, ail, bih, idn, 1u);
+                        tc::mma_tf32_ta(ti, arh, bih, id, first);  tc::mma_tf32_ta(ti, arh, bil, id, 1u);  tc::mma_tf32_ta(ti, arl, bih, id, 1u);
+                        tc::mma_tf32_ta(ti, aih, brh, id, 1u);     tc::mma_tf32_ta(ti, aih, brl, id, 1u);  tc::mma_tf32_ta(ti, ail, brh, id, 1u);
                     }
                     tc::commit(tc::smem_u32(&empty[b]));
                 }
-                if (ok) tc::commit(tc::smem_u32(&accf[cb]));
+                if (ok) tc::commit(tc::smem_u32(&accf[0]));
             }
             if (!ok) {
                 atomicExch(&abort_flag, 1);
@@ -401,9 +437,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
         const int qw = warp & 3, row = qw * 32 + lane;
         const unsigned lane_off = (unsigned)(qw * 32) << 16;
         for (int col = 0; col < my_items; col++) {
-            const int cb = col & 1;
             int ok = 1;
-            if (lane == 0) ok = tc::mbar_wait_or_abort(tc::smem_u32(&accf[cb]), (col >> 1) & 1, &abort_flag) ? 1 : 0;
+            if (lane == 0) ok = tc::mbar_wait_or_abort(tc::smem_u32(&accf[0]), col & 1, &abort_flag) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) {
@@ -417,8 +452,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
             float2 *Wc = a.W + ((size_t)g * Lf + kx) * COLS * ROWS;
             for (int c0 = 0; c0 < TN; c0 += 8) {
                 unsigned vr[8], vi[8];
-                tc::tmem_ld8(tmem + lane_off + 256u * cb + (unsigned)c0, vr);
-                tc::tmem_ld8(tmem + lane_off + 256u * cb + 128u + (unsigned)c0, vi);
+                tc::tmem_ld8(tmem + lane_off + (unsigned)c0, vr);
+                tc::tmem_ld8(tmem + lane_off + ACC_IM + (unsigned)c0, vi);
                 tc::tmem_wait_ld();
                 if (row < ROWS) {
 #pragma unroll
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) loops_tc_kernel(LtArgs a)
                 }
             }
             tc::fence_before();
-            tc::mbar_arrive(tc::smem_u32(&acce[cb]));
+            tc::mbar_arrive(tc::smem_u32(&acce[0]));
         }
     }
     __syncthreads();

@@ -84,6 +84,29 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem, unsigned long long da, u
                  "r"(acc) : "memory");
 }
 
+// D[tmem] (+)= A[tmem] B[desc], kind::tf32, one CTA: A in tensor memory (lane = row, one column per K element)
+__device__ __forceinline__ void mma_tf32_ta(unsigned tmem_d, unsigned tmem_a, unsigned long long db, unsigned idesc,
+                                            unsigned acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d), "r"(tmem_a), "l"(db),
+                 "r"(idesc), "r"(acc) : "memory");
+}
+
+// four / two consecutive 32-bit columns of this warp's lanes (lane i of the warp writes row 32 (warp % 4) + i); addr
+// holds the warp's lane base and the first column; warp-collective
+__device__ __forceinline__ void tmem_st4(unsigned addr, float v0, float v1, float v2, float v3)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(__float_as_uint(v0)),
+                 "r"(__float_as_uint(v1)), "r"(__float_as_uint(v2)), "r"(__float_as_uint(v3)) : "memory");
+}
+__device__ __forceinline__ void tmem_st2(unsigned addr, float v0, float v1)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(__float_as_uint(v0)),
+                 "r"(__float_as_uint(v1)) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // the mbarrier at bar receives one arrival once every tcgen05 operation this thread issued so far is complete
 __device__ __forceinline__ void commit(unsigned bar)
 {
