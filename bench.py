@@ -738,6 +738,22 @@ def main():
                 "unit_work": f"(N_s^4 + N_s^5 + {ndy_half} N_s^4) = {unit_cfma} complex FMA per (q, k) pair",
                 "units_per_launch": f"{m32.n_loop_q} directly summed q x {spec.Nk} k",
                 "avg_launch_ms": loop_ms_avg}
+    if m32.loops_backend == "tc":
+        # the tensor-core loop kernel: its bound is the TF32 tensor pipe; the method's FP32 count stays beside it
+        ex, us = loops_tc_tensor_flop(m32.n_loop_q, spec.Lf, spec.Nk, ndy_half)
+        tf32 = tf32_peak_tflops(peaks)
+        roofline = {"bound": "tensor", "kernel": "loops_tc_kernel (tcgen05 3xTF32 loop k-sum, N_s = 6)",
+                    "achieved": ex / (loop_ms_avg * 1e-3) / 1e12, "peak": tf32, "unit": "TFLOP/s",
+                    "frac": ex / (loop_ms_avg * 1e-3) / 1e12 / tf32, "traffic": None,
+                    "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
+                    "algorithmic_flops_per_launch": ex,
+                    "unit_work": "36 MMAs of 128 x 112 x 8 (TF32) per stage of 4 fine-mesh rows, per column and "
+                                 "group of 3 momenta",
+                    "units_per_launch": f"{m32.n_loop_q} directly summed q x {spec.Nk} k",
+                    "useful_frac": us / (loop_ms_avg * 1e-3) / 1e12 / tf32,
+                    "method_fp32": {"achieved": achieved, "peak": fp32_peak_tflops, "frac": achieved / fp32_peak_tflops,
+                                    "unit_work": f"(N_s^4 + N_s^5 + {ndy_half} N_s^4) = {unit_cfma} complex FMA per (q, k)"},
+                    "avg_launch_ms": loop_ms_avg}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
