@@ -281,7 +281,7 @@ def run_config_t2g(stream, peaks, fp32_peak, seed=0, k=10):
     prod = None
     if m.products == "tc":
         fl = products_tf32_flop(spec.M, n_products)
-        prod = {"bound": "tensor", "kernel": "tc_cgemm_kernel + operand packing (tcgen05, 3xTF32)", "phase_ms": ph["vlv"],
+        prod = {"bound": "tensor", "kernel": "vlv_tc_kernel (tcgen05, 3xTF32, operands split in the kernel)", "phase_ms": ph["vlv"],
                 "tf32_3pass_tflops": fl / (ph["vlv"] * 1e-3) / 1e12, "frac_tf32_3pass": fl / (ph["vlv"] * 1e-3) / 1e12 / tf32,
                 "method_complex_fp32_tflops": fl / 3 / (ph["vlv"] * 1e-3) / 1e12,
                 "frac_method_of_tf32_peak": fl / 3 / (ph["vlv"] * 1e-3) / 1e12 / tf32,
@@ -487,6 +487,8 @@ def main():
     ap.add_argument("--profile-precision", choices=["split", "fp64"], default="split")
     ap.add_argument("--profile-symmetric-states", action="store_true",
                     help="with --profile-rhs: force the orbit-representative projections and products")
+    ap.add_argument("--profile-general", action="store_true",
+                    help="with --profile-rhs: the general path (projections and products at every momentum)")
     ap.add_argument("--profile-model", choices=["rashba", "t2g_q8", "t2g_q16"], default="rashba",
                     help="with --profile-rhs: the benchmark workload, or t2g + SOC at 8x8 q / 6x6 k (a small case "
                          "of the multi-orbital kernels for full profiler captures), or t2g + SOC at 16x16 q / 12x12 k "
@@ -532,7 +534,8 @@ def main():
                   symmetry=SYMMETRY_STATES if args.profile_symmetric_states else SYMMETRY_AUTO)
         st = torch.from_numpy(inputs.random_state(spec, seed=1, scale=0.2)).cuda()
         for _ in range(args.profile_rhs):
-            m.rhs(T_BENCH, st, symmetric=True)   # the timed loop's path (the values do not change the launches)
+            # the timed loop's path (the values do not change the launches), or the general one
+            m.rhs(T_BENCH, st, symmetric=not args.profile_general)
         torch.cuda.synchronize()
         print(json.dumps({"profile_rhs": args.profile_rhs, "workload": WORKLOAD}))
         return
@@ -797,7 +800,7 @@ def main():
                     "d2h_bytes_per_step": state_bytes, "api": "tufrg_rhs_host_batch (copies of neighbouring steps "
                     "overlapped with the evaluations)", "one_call_per_step": e2e_single},
             "roofline": roofline,
-            "roofline_products": ({"bound": "tensor", "kernel": "tc_cgemm_kernel + operand packing (tcgen05, 3xTF32)",
+            "roofline_products": ({"bound": "tensor", "kernel": "vlv_tc_kernel (tcgen05, 3xTF32, operands split in the kernel)",
                                    "achieved": products_tf32_flop(spec.M, n_products) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12,
                                    "peak": tf32_peak_tflops(peaks), "unit": "TFLOP/s",
                                    "frac": products_tf32_flop(spec.M, n_products) / (phase_ms["vlv"] / args.steps * 1e-3) / 1e12

@@ -443,7 +443,8 @@ tufrg_status tufrg_set_device_error(tufrg_model *m, int value);
  * stream, stops recording and returns:
  *   h_ms[i], i < n_ms: summed device milliseconds per phase, in the order
  *     0 Fermi tables, 1 loop k-sum kernels, 2 loop partial reduction,
- *     3 Fourier transform, 4 projections, 5 V.L.V products, 6 Runge-Kutta kernels;
+ *     3 Fourier transform, 4 projections, 5 V.L.V products, 6 Runge-Kutta kernels, 7 the copy of the
+ *     orbit representatives' products to the other momenta of their orbits (symmetric states, large M);
  *   *h_launches: kernels this library launched while recording;
  *   *h_loop_launches: launches of the loop k-sum kernel (phase 1) alone. */
 tufrg_status tufrg_timing_begin(tufrg_model *m);

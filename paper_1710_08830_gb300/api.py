@@ -251,7 +251,7 @@ class Model:
                                                    int(mask), _ptr(out)))
         return out
 
-    PHASES = ("fermi", "loops", "loop_reduce", "dft", "project", "vlv", "rk")
+    PHASES = ("fermi", "loops", "loop_reduce", "dft", "project", "vlv", "rk", "sym_scatter")
 
     def timing_begin(self):
         self._check(self._L.tufrg_timing_begin(self._h))

@@ -492,8 +492,7 @@ void release(tufrg_model *m)
                     m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
-                    m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_tc_left[0], m->d_tc_left[1], m->d_tc_right,
-                    m->d_tc_gidx, m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
+                    m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
                     m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32, m->d_ffW};
     for (void *p : ptrs)
@@ -1025,23 +1024,10 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
             CK(cudaMalloc(reinterpret_cast<void **>(&m->d_loop_w), loops_tc_w_bytes(m)), "cudaMalloc loop column sums");
     }
     m->products = split ? (d.products == TUFRG_PRODUCTS_AUTO ? TUFRG_PRODUCTS_TC : d.products) : TUFRG_PRODUCTS_SIMT;
-    if (split && d.products != TUFRG_PRODUCTS_SIMT) {
-        // tensor-core products: packed operands and the loop-matrix gather index
-        size_t lb = 0, rb = 0;
-        tc_pack_bytes(m, &lb, &rb);
-        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_tc_left[0]), lb), "cudaMalloc packed operands");
-        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_tc_left[1]), lb), "cudaMalloc packed operands");
-        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_tc_right), rb), "cudaMalloc packed operands");
-        std::vector<int> gidx((size_t)m->M * m->M);
-        const int nsq = ns * ns;
-        for (int k = 0; k < m->M; k++)
-            for (int n = 0; n < m->M; n++)
-                gidx[(size_t)k * m->M + n] = (m->dij[(k / nsq) * m->nff + n / nsq] * nsq + k % nsq) * nsq + n % nsq;
-        CK(upload(&m->d_tc_gidx, gidx, m->stream), "upload gather index");
-    }
+    // product scratch: the large-M CUDA-core GEMMs' intermediate, or the tensor-core products' first product of both
+    // channels (FP32 complex, the same bytes)
     if (m->M > 64 || split)
-        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_T), (size_t)m->Nq * M2 * (split ? sizeof(float2) : sizeof(double2))),
-           "cudaMalloc product scratch");
+        CK(cudaMalloc(reinterpret_cast<void **>(&m->d_T), (size_t)m->Nq * M2 * sizeof(double2)), "cudaMalloc product scratch");
     CK(dalloc(&m->d_err, 1), "cudaMalloc error flag");
     CK(dalloc(&m->d_scal, 2), "cudaMalloc scalars");
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "zero error flag");

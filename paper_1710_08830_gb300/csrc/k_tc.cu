@@ -1,352 +1,443 @@
 // Tensor-core V.L.V products for the split path: dX/dT(q) = c_X A(q) L(q) A(q) (Eq. RGE_spin and the
 // orbital form of Eq. rge_Dmat) on 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// Complex GEMM C = A B as four real MMA streams into two TMEM accumulators:
+// Two persistent launches per right-hand side, each over the work list (channel, momentum, 128-row tile, NB-column
+// tile) of every requested channel and momentum:
+//   first:   T = A L    with L[k][n] gathered from the compact loops through the bond-pair table, FP32 scratch;
+//   second:  dX = c T A in FP64.
+// Complex GEMM as four real MMA streams into two tensor-memory accumulators:
 //   Cr += Ar Br - Ai Bi,   Ci += Ar Bi + Ai Br     (the minus by the descriptor's negate-A bit).
-// Precision: 3xTF32 - every FP32 operand x is split into hi = tf32(x) and lo = x - hi, and each real
-// product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory, which keeps FP32-level
-// accuracy on the TF32 datapath.
+// Precision: 3xTF32 - every FP32 operand x is split into hi = x with the 13 low mantissa bits cleared and lo = x - hi
+// (exact), and each real product is hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory.
 //
-// Operands are packed once per product by small kernels into the K-major, no-swizzle core-matrix
-// layout of the MMA (8 rows x 16 bytes per core matrix), as four planes (Re hi, Re lo, Im hi, Im lo)
-// per (row tile, 16-wide K stage), so that one pipeline stage of one operand is a single contiguous
-// block.  The GEMM kernel (one CTA = 128 output rows x NB complex columns of one transfer momentum)
-// runs a two-stage pipeline: thread 0 issues one bulk copy per operand and stage (cp.async.bulk with
-// mbarrier transaction counts), thread 32 issues the 24 MMAs of a stage (2 K-steps x 4 products x 3)
-// and commits them to the stage's "empty" barrier, so copies of stage s + 1 overlap the MMAs of s.
-// The first product writes T = A L directly in the packed left-operand layout of the second; the
-// second writes c T A in FP64.  Every wait is bounded: on time-out the kernel records an error code,
-// waits (bounded) for its own MMAs and for the bulk copies it issued, frees its TMEM and returns.
+// The operands are read in FP32 straight from the matrices and split inside the kernel (no packing launches).  Warp
+// roles of the 672-thread CTA (one per SM):
+//   warps 0-15  producers, thread (K group kg = tid / 128, row r = tid % 128): per K stage of 16 columns each thread
+//               loads 4 complex values of left-operand row r and 4 of right-operand row r for the next stage into
+//               registers while it splits the current one; the left operand's four TF32 planes (Re hi, Re lo,
+//               Im hi, Im lo) go to tensor memory (tcgen05.st, lane = row: warp w writes lanes 32 (w % 4) ..), the
+//               right operand's to shared memory in the K-major core-matrix layout;
+//   warp 16     tensor-memory allocation and the MMA issuer (one thread): 24 MMAs per stage (2 K-steps x 4 real
+//               products x 3 TF32 passes), the left operand read from tensor memory;
+//   warps 17-20 epilogue: tensor memory -> T (FP32) or c dX (FP64) in global memory.
+// Four stage buffers (mbarriers full / empty); one accumulator (mbarriers acc_full / acc_empty).  Every wait is
+// bounded; on time-out the kernel raises the error flag, every role stops, the MMAs in flight are waited for
+// (bounded) and the tensor memory is freed.
 #include "tc_common.cuh"
 #include "tufrg_internal.cuh"
 
 namespace tufrg {
 namespace {
 
-constexpr int TC_M = 128;        // MMA M (rows per CTA)
-constexpr int KS = 16;           // K per pipeline stage (two MMA K-steps of 8)
-constexpr int TC_THREADS = 128;
-constexpr int TMEM_COLS = 512;   // Cr at [0, NB), Ci at [256, 256 + NB)
-using tc::core_off;
-using tc::mbar_wait;
-using tc::smem_desc;
-using tc::smem_u32;
-using tc::tf32_hi;
+constexpr int TM = 128;             // MMA M: rows per tile
+constexpr int KS = 16;              // K per stage (two MMA K-steps of 8)
+constexpr int NSTAGE = 4;           // stage buffers
+constexpr int NPROD = 512;          // producer threads (warps 0-15)
+constexpr int MMA_WARP = 16;        // warps 17-20: epilogue
+constexpr int NTHREADS = 21 * 32;
+constexpr int NB_MAX = 128;         // columns per tile (complex), a multiple of 16
+// tensor memory: accumulator Re at [0, NB), Im at [128, 128 + NB); left operand of stage b at 256 + 64 b, plane p at
+// + 16 p (K = 16 columns)
+constexpr unsigned ACC_IM = 128, A_COL0 = 256, A_STAGE_COLS = 64, A_PLANE_COLS = 16;
+constexpr unsigned TMEM_COLS = 512;
+static_assert(A_COL0 + NSTAGE * A_STAGE_COLS <= TMEM_COLS, "tensor memory budget");
 
-__device__ __forceinline__ unsigned idesc_tf32(int nb, bool neg_a) { return tc::idesc_tf32(TC_M, nb, neg_a); }
-__device__ __forceinline__ void mma(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc, unsigned acc)
-{
-    tc::mma_tf32(tmem, da, db, idesc, acc);
-}
-
-struct PackDims {
-    int M;          // complex matrix order
-    int nks;        // K stages (16 wide) covering M
-    int nb;         // complex columns per N tile (multiple of 16, <= 256)
+struct Dims {
+    int M;          // complex matrix order (a multiple of 4)
+    int nks;        // K stages covering M
+    int nb;         // complex columns per tile (multiple of 16, <= 128)
     int m_tiles;    // 128-row tiles covering M
-    int n_tiles;    // NB-column tiles covering M
+    int n_tiles;    // nb-column tiles covering M
 };
 
-// left operand: rows m of X[q] (M x M, row-major), K = columns; planes (Re hi, Re lo, Im hi, Im lo)
-// block (q, row tile, K stage) = 4 planes of 128 x 16 floats.  Grid (m_tiles, nks, Nq), 512 threads.
-__global__ void __launch_bounds__(512) pack_left_kernel(const float2 *X, PackDims pd, const int *qlist, float *out)
+Dims dims_of(int M)
 {
-    const int rt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;   // q: packed slot
-    const int qs = qlist ? qlist[q] : q;                          // transfer momentum read
-    const int r = threadIdx.x & 127, kg = threadIdx.x >> 7;
-    const int m = rt * TC_M + r, k0 = ks * KS + kg * 4;
-    float re[4], im[4];
-    const float2 *src = X + ((size_t)qs * pd.M + m) * pd.M;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const float2 v = (m < pd.M && k0 + j < pd.M) ? src[k0 + j] : make_float2(0.f, 0.f);
-        re[j] = v.x;
-        im[j] = v.y;
-    }
-    float *blk = out + (((size_t)q * pd.m_tiles + rt) * pd.nks + ks) * 4 * (TC_M * KS);
-    const int o = core_off(r, kg * 4, TC_M);
-    float4 h, l;
-    h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
-    l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
-    *reinterpret_cast<float4 *>(blk + 0 * TC_M * KS + o) = h;
-    *reinterpret_cast<float4 *>(blk + 1 * TC_M * KS + o) = l;
-    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
-    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
-    *reinterpret_cast<float4 *>(blk + 2 * TC_M * KS + o) = h;
-    *reinterpret_cast<float4 *>(blk + 3 * TC_M * KS + o) = l;
+    Dims d{};
+    d.M = M;
+    d.nks = (M + KS - 1) / KS;
+    d.m_tiles = (M + TM - 1) / TM;
+    d.n_tiles = (M + NB_MAX - 1) / NB_MAX;
+    d.nb = ((M + d.n_tiles - 1) / d.n_tiles + 15) / 16 * 16;
+    return d;
 }
 
-// right operand B[k][n] of one transfer momentum as rows n, K = k: B = Y[q] (row-major) or, when gidx is
-// given, the loop matrix gathered from the compact loops, B[k][n] = Lc[q][gidx[k][n]].
-// Grid (n_tiles, nks, Nq), block (nb, 4).
-__global__ void pack_right_kernel(const float2 *Y, const float2 *Lc, const int *gidx, int lper, PackDims pd,
-                                  const int *qlist, float *out)
-{
-    const int nt = blockIdx.x, ks = blockIdx.y, q = blockIdx.z;   // q: packed slot
-    const int qs = qlist ? qlist[q] : q;                          // transfer momentum read
-    const int nl = threadIdx.x, kg = threadIdx.y;
-    const int n = nt * pd.nb + nl, k0 = ks * KS + kg * 4;
-    float re[4], im[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const int k = k0 + j;
-        float2 v = make_float2(0.f, 0.f);
-        if (n < pd.M && k < pd.M)
-            v = gidx ? Lc[(size_t)qs * lper + gidx[(size_t)k * pd.M + n]] : Y[((size_t)qs * pd.M + k) * pd.M + n];
-        re[j] = v.x;
-        im[j] = v.y;
-    }
-    const int R = pd.nb;
-    float *blk = out + (((size_t)q * pd.n_tiles + nt) * pd.nks + ks) * 4 * ((size_t)R * KS);
-    const int o = core_off(nl, kg * 4, R);
-    float4 h, l;
-    h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
-    l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
-    *reinterpret_cast<float4 *>(blk + 0 * R * KS + o) = h;
-    *reinterpret_cast<float4 *>(blk + 1 * R * KS + o) = l;
-    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
-    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
-    *reinterpret_cast<float4 *>(blk + 2 * R * KS + o) = h;
-    *reinterpret_cast<float4 *>(blk + 3 * R * KS + o) = l;
-}
-
-struct GemmArgs {
-    const float *left;      // packed left operand [Nq][m_tiles][nks][4][128 x 16]
-    const float *right;     // packed right operand [Nq][n_tiles][nks][4][nb x 16]
-    float *out_left;        // first product: C written as the packed left operand of the second (or null)
-    double2 *out64;         // second product: scale * C, [Nq][M][M] FP64 (or null)
+struct VlvArgs {
+    const float2 *A;        // [2][Nq][M][M] projections (FP32, row-major)
+    const float2 *Lc;       // [2][Nq][lper] compact loops (first product)
+    const int *dij;         // [nff][nff] bond pair -> bond-difference index of the compact loops
+    float2 *T;              // [2][nz][M][M] first product (written by the first launch, read by the second)
+    double2 *out;           // [2][Nq][M][M] second product
+    const int *qlist;       // slot z -> transfer momentum (null: the slot is the momentum)
+    const double *scal;     // scal[1]: the flow-scale factor of the right-hand side
     int *err;
-    PackDims pd;
-    double scale;
-    const double *scal;     // optional device scale factor (scal[1])
-    const int *qlist;       // optional: packed slot z holds transfer momentum qlist[z] (out64 index)
+    Dims d;
+    int nff, lper, Nq, nz;
+    int ch0, nch;           // channels ch0 .. ch0 + nch - 1
+    int n_items;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(GemmArgs a)
-{
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int NB = a.pd.nb, nks = a.pd.nks;
-    const unsigned a_bytes = 4u * TC_M * KS * 4u, b_bytes = 4u * (unsigned)NB * KS * 4u;
-    // stage s: [A planes | B planes]; both sizes are multiples of 1024 bytes
-    unsigned char *stage[2] = {smem_raw, smem_raw + a_bytes + b_bytes};
-    __shared__ __align__(8) unsigned long long full[2], empty[2], done;
-    __shared__ unsigned tmem_base_sh;
-    __shared__ int failed;
-    __shared__ int last_issued[2];   // last stage whose copies went to buffer b (-1: none)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = blockIdx.x, rt = blockIdx.y, q = blockIdx.z;
+// the stage's values of one producer thread: left-operand row r at K = k0 .. k0 + 3 and right-operand row r (an
+// output column) at the same K
+struct Vals {
+    float2 a[4], b[4];
+};
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+// one producer thread's sources for one item: the left operand's row (A in the first product, T in the second) and
+// the right operand's column (the compact loops of the momentum, or A), null when the row / column is padding
+struct Src {
+    const float2 *a;    // row m of the left operand
+    const float2 *b;    // first product: the momentum's compact loops + (n % NS2); second: column n of A
+    int nj;             // first product: n / NS2 (the column's bond index)
+};
+
+template <int PH, int NS2>
+__device__ __forceinline__ Src item_src(const VlvArgs &p, int ch, int z, int mt, int nt, int r)
+{
+    const int M = p.d.M, m = mt * TM + r, n = nt * p.d.nb + r;
+    const size_t M2 = (size_t)M * M;
+    const int qs = p.qlist ? p.qlist[z] : z;
+    Src s{nullptr, nullptr, 0};
+    if (m < M) s.a = (PH == 0 ? p.A + ((size_t)ch * p.Nq + qs) * M2 : p.T + ((size_t)ch * p.nz + z) * M2) + (size_t)m * M;
+    if (r < p.d.nb && n < M) {
+        if (PH == 0) {
+            s.b = p.Lc + ((size_t)ch * p.Nq + qs) * p.lper + n % NS2;
+            s.nj = n / NS2;
+        } else {
+            s.b = p.A + ((size_t)ch * p.Nq + qs) * M2 + n;
+        }
+    }
+    return s;
+}
+
+// K = k0 .. k0 + 3 of both operands (k0 a multiple of 4; M and NS2 are multiples of 4, so the four K values lie in
+// one bond block)
+template <int PH, int NS2>
+__device__ __forceinline__ void load_stage(const Src &src, const int *sdij, int nff, int M, int k0, Vals &v)
+{
+    const bool in = k0 < M;
+    if (src.a && in) {
+        const float4 *q = reinterpret_cast<const float4 *>(src.a + k0);
+        const float4 u0 = __ldg(q), u1 = __ldg(q + 1);
+        v.a[0] = make_float2(u0.x, u0.y);
+        v.a[1] = make_float2(u0.z, u0.w);
+        v.a[2] = make_float2(u1.x, u1.y);
+        v.a[3] = make_float2(u1.z, u1.w);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) v.a[j] = make_float2(0.f, 0.f);
+    }
+    if (src.b && in) {
+        if (PH == 0) {
+            // L[k][n] = Lc[(d(k / NS2, n / NS2) NS2 + k % NS2) NS2 + n % NS2]
+            const float2 *b = src.b + ((size_t)sdij[(k0 / NS2) * nff + src.nj] * NS2 + k0 % NS2) * NS2;
+#pragma unroll
+            for (int j = 0; j < 4; j++) v.b[j] = __ldg(b + j * NS2);
+        } else {
+            const float2 *b = src.b + (size_t)k0 * M;
+#pragma unroll
+            for (int j = 0; j < 4; j++) v.b[j] = __ldg(b + (size_t)j * M);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) v.b[j] = make_float2(0.f, 0.f);
+    }
+}
+
+// exact FP32 -> FP64 by the two formats' bit layouts (integer operations only: the FP64 pipe of this GPU is narrow);
+// FP32 subnormals become signed zeros
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x), e = (u >> 23) & 0xffu, sign = u & 0x80000000u;
+    const unsigned e64 = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = e == 0 ? sign : sign | (e64 << 20) | ((u & 0x7fffffu) >> 3);
+    const unsigned lo = e == 0 ? 0u : u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+template <int PH, int NS2>
+__global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];   // NSTAGE right-operand stages, then the bond table
+    const int NB = p.d.nb, nks = p.d.nks;
+    const unsigned b_plane = (unsigned)NB * KS * 4, b_stage = 4 * b_plane;   // bytes
+    int *sdij = reinterpret_cast<int *>(smem + NSTAGE * (size_t)b_stage);
+    __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], accf, acce, done;
+    __shared__ unsigned tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_base)),
                      "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; b++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
+        for (int b = 0; b < NSTAGE; b++) {
+            tc::mbar_init(tc::smem_u32(&full[b]), NPROD);
+            tc::mbar_init(tc::smem_u32(&empty[b]), 1);
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+        tc::mbar_init(tc::smem_u32(&accf), 1);
+        tc::mbar_init(tc::smem_u32(&acce), 128);
+        tc::mbar_init(tc::smem_u32(&done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        failed = 0;
-        last_issued[0] = last_issued[1] = -1;
+        abort_flag = 0;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (PH == 0)
+        for (int i = tid; i < p.nff * p.nff; i += NTHREADS) sdij[i] = p.dij[i];
+    tc::fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const unsigned tmem = tmem_base_sh;
+    tc::fence_after();
+    const unsigned tmem = tmem_base;
+    const int G = (int)gridDim.x;
+    const int my_items = p.n_items > (int)blockIdx.x ? (p.n_items - 1 - (int)blockIdx.x) / G + 1 : 0;
+    // item -> (channel, slot, row tile, column tile); column tiles fastest so that neighbouring CTAs share rows
+    auto decode = [&](int item, int &ch, int &z, int &mt, int &nt) {
+        nt = item % p.d.n_tiles;
+        int t = item / p.d.n_tiles;
+        mt = t % p.d.m_tiles;
+        t /= p.d.m_tiles;
+        z = t % p.nz;
+        ch = p.ch0 + t / p.nz;
+    };
 
-    const float *lsrc = a.left + (((size_t)q * a.pd.m_tiles + rt) * nks) * (a_bytes / 4);
-    const float *rsrc = a.right + (((size_t)q * a.pd.n_tiles + nt) * nks) * (b_bytes / 4);
-    if (tid == 0) {
-        // producer: one bulk copy per operand and stage
-        for (int s = 0; s < nks; s++) {
-            const int b = s & 1;
-            if (s >= 2 && !mbar_wait(smem_u32(&empty[b]), ((s >> 1) - 1) & 1)) { failed = 1; break; }
-            unsigned long long st;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                         : "=l"(st) : "r"(smem_u32(&full[b])), "r"(a_bytes + b_bytes) : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(stage[b])), "l"(lsrc + (size_t)s * (a_bytes / 4)), "r"(a_bytes),
-                         "r"(smem_u32(&full[b])) : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(stage[b] + a_bytes)), "l"(rsrc + (size_t)s * (b_bytes / 4)), "r"(b_bytes),
-                         "r"(smem_u32(&full[b])) : "memory");
-            last_issued[b] = s;
-        }
-    } else if (tid == 32) {
-        // MMA issuer: per stage, 2 K-steps x (Ar Br, -Ai Bi, Ar Bi, Ai Br) x (hi hi, hi lo, lo hi)
-        const unsigned id = idesc_tf32(NB, false), idn = idesc_tf32(NB, true);
-        const unsigned tr = tmem, ti = tmem + 256;
-        bool ok = true;
-        for (int s = 0; s < nks && ok; s++) {
-            const int b = s & 1;
-            if (!mbar_wait(smem_u32(&full[b]), (s >> 1) & 1)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned sa = smem_u32(stage[b]), sb = sa + a_bytes;
-            const unsigned pa = TC_M * KS * 4, pb = (unsigned)NB * KS * 4;   // plane strides (bytes)
-#pragma unroll
-            for (int kk = 0; kk < 2; kk++) {
-                const unsigned ao = kk * 2 * (TC_M / 8) * 128, bo = kk * 2 * (NB / 8) * 128;
-                const unsigned long long arh = smem_desc(sa + 0 * pa + ao, TC_M), arl = smem_desc(sa + 1 * pa + ao, TC_M);
-                const unsigned long long aih = smem_desc(sa + 2 * pa + ao, TC_M), ail = smem_desc(sa + 3 * pa + ao, TC_M);
-                const unsigned long long brh = smem_desc(sb + 0 * pb + bo, NB), brl = smem_desc(sb + 1 * pb + bo, NB);
-                const unsigned long long bih = smem_desc(sb + 2 * pb + bo, NB), bil = smem_desc(sb + 3 * pb + bo, NB);
-                const unsigned first = (s == 0 && kk == 0) ? 0u : 1u;
-                mma(tr, arh, brh, id, first);  mma(tr, arh, brl, id, 1u);  mma(tr, arl, brh, id, 1u);
-                mma(tr, aih, bih, idn, 1u);    mma(tr, aih, bil, idn, 1u); mma(tr, ail, bih, idn, 1u);
-                mma(ti, arh, bih, id, first);  mma(ti, arh, bil, id, 1u);  mma(ti, arl, bih, id, 1u);
-                mma(ti, aih, brh, id, 1u);     mma(ti, aih, brl, id, 1u);  mma(ti, ail, brh, id, 1u);
+    if (warp < MMA_WARP) {
+        // ------------------------------------------------------------------ producers
+        const int r = tid & 127, kg = tid >> 7;
+        const unsigned lane_base = (unsigned)((warp & 3) * 32) << 16;   // this warp's tensor-memory lanes
+        const int n_stages = my_items * nks;
+        const int M = p.d.M, nff = p.nff;
+        int li = 0, k0 = 4 * kg;   // item (local index) and first K of this thread in the stage of the loads in flight
+        int ch, z, mt, nt;
+        decode((int)blockIdx.x, ch, z, mt, nt);
+        Src src = item_src<PH, NS2>(p, ch, z, mt, nt, r);
+        Vals cur, nxt;
+        if (n_stages > 0) load_stage<PH, NS2>(src, sdij, nff, M, k0, nxt);
+        for (int n = 0; n < n_stages; n++) {
+            cur = nxt;
+            // issue the loads of stage n + 1 (they land while this stage is split and stored)
+            k0 += KS;
+            if (k0 >= nks * KS) {
+                k0 = 4 * kg;
+                if (++li < my_items) {
+                    decode((int)blockIdx.x + li * G, ch, z, mt, nt);
+                    src = item_src<PH, NS2>(p, ch, z, mt, nt, r);
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[b]))
-                         : "memory");
+            if (n + 1 < n_stages) load_stage<PH, NS2>(src, sdij, nff, M, k0, nxt);
+            const int b = n % NSTAGE;
+            // the MMAs that read this stage buffer NSTAGE stages ago must be complete
+            int ok = 1;
+            if (lane == 0) {
+                if (*(volatile int *)&abort_flag) ok = 0;
+                else if (n >= NSTAGE) ok = tc::mbar_wait_or_abort(tc::smem_u32(&empty[b]), ((n / NSTAGE) - 1) & 1, &abort_flag) ? 1 : 0;
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(p.err, 1);
+                }
+                break;   // the whole warp leaves (the MMA thread's waits then run out or see the flag)
+            }
+            tc::fence_after();
+            // left operand: four planes x 4 columns of this lane's row into tensor memory
+            const unsigned ca = tmem + lane_base + A_COL0 + b * A_STAGE_COLS + 4 * kg;
+            float h[4], l[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                h[j] = tf32_trunc(cur.a[j].x);
+                l[j] = cur.a[j].x - h[j];
+            }
+            tc::tmem_st4(ca + 0 * A_PLANE_COLS, h[0], h[1], h[2], h[3]);
+            tc::tmem_st4(ca + 1 * A_PLANE_COLS, l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                h[j] = tf32_trunc(cur.a[j].y);
+                l[j] = cur.a[j].y - h[j];
+            }
+            tc::tmem_st4(ca + 2 * A_PLANE_COLS, h[0], h[1], h[2], h[3]);
+            tc::tmem_st4(ca + 3 * A_PLANE_COLS, l[0], l[1], l[2], l[3]);
+            // right operand: row r of the stage's four planes in shared memory
+            if (r < NB) {
+                float *pb = reinterpret_cast<float *>(smem + (size_t)b * b_stage);
+                const int o = tc::core_off(r, 4 * kg, NB);
+                float4 hv, lv;
+                hv = make_float4(tf32_trunc(cur.b[0].x), tf32_trunc(cur.b[1].x), tf32_trunc(cur.b[2].x), tf32_trunc(cur.b[3].x));
+                lv = make_float4(cur.b[0].x - hv.x, cur.b[1].x - hv.y, cur.b[2].x - hv.z, cur.b[3].x - hv.w);
+                *reinterpret_cast<float4 *>(pb + 0 * (b_plane / 4) + o) = hv;
+                *reinterpret_cast<float4 *>(pb + 1 * (b_plane / 4) + o) = lv;
+                hv = make_float4(tf32_trunc(cur.b[0].y), tf32_trunc(cur.b[1].y), tf32_trunc(cur.b[2].y), tf32_trunc(cur.b[3].y));
+                lv = make_float4(cur.b[0].y - hv.x, cur.b[1].y - hv.y, cur.b[2].y - hv.z, cur.b[3].y - hv.w);
+                *reinterpret_cast<float4 *>(pb + 2 * (b_plane / 4) + o) = hv;
+                *reinterpret_cast<float4 *>(pb + 3 * (b_plane / 4) + o) = lv;
+            }
+            tc::tmem_wait_st();
+            tc::fence_smem_async();
+            tc::fence_before();
+            tc::mbar_arrive(tc::smem_u32(&full[b]));
         }
-        if (!ok) failed = 1;
-        // completion of every MMA issued above
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
-                     : "memory");
-    }
-    __syncwarp();
-    const bool fin = mbar_wait(smem_u32(&done), 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!fin || failed) {
-        if (tid == 0) {
-            atomicExch(a.err, 1);
-            // bulk copies issued into this CTA's shared memory may still be in flight (the MMA thread gave up
-            // before consuming them): wait, bounded, until the last one of each buffer has landed
-            for (int b = 0; b < 2; b++)
-                if (last_issued[b] >= 0) (void)mbar_wait(smem_u32(&full[b]), (last_issued[b] >> 1) & 1);
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const unsigned id = tc::idesc_tf32(TM, NB, false), idn = tc::idesc_tf32(TM, NB, true);
+            const unsigned tr = tmem, ti = tmem + ACC_IM;
+            bool ok = true;
+            int n = 0;
+            for (int it = 0; it < my_items && ok; it++) {
+                // the accumulator must have been read by the epilogue of the previous item
+                if (it >= 1 && !tc::mbar_wait_or_abort(tc::smem_u32(&acce), (it - 1) & 1, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                for (int s = 0; s < nks; s++, n++) {
+                    const int b = n % NSTAGE;
+                    if (!tc::mbar_wait_or_abort(tc::smem_u32(&full[b]), (n / NSTAGE) & 1, &abort_flag)) { ok = false; break; }
+                    tc::fence_after();
+                    const unsigned sb = tc::smem_u32(smem + (size_t)b * b_stage), ta = tmem + A_COL0 + b * A_STAGE_COLS;
+#pragma unroll
+                    for (int kk = 0; kk < KS / 8; kk++) {
+                        const unsigned bo = kk * 2 * (NB / 8) * 128;
+                        const unsigned arh = ta + 0 * A_PLANE_COLS + 8 * kk, arl = ta + 1 * A_PLANE_COLS + 8 * kk;
+                        const unsigned aih = ta + 2 * A_PLANE_COLS + 8 * kk, ail = ta + 3 * A_PLANE_COLS + 8 * kk;
+                        const unsigned long long brh = tc::smem_desc(sb + 0 * b_plane + bo, NB), brl = tc::smem_desc(sb + 1 * b_plane + bo, NB);
+                        const unsigned long long bih = tc::smem_desc(sb + 2 * b_plane + bo, NB), bil = tc::smem_desc(sb + 3 * b_plane + bo, NB);
+                        const unsigned first = (s == 0 && kk == 0) ? 0u : 1u;
+                        tc::mma_tf32_ta(tr, arh, brh, id, first);  tc::mma_tf32_ta(tr, arh, brl, id, 1u);  tc::mma_tf32_ta(tr, arl, brh, id, 1u);
+                        tc::mma_tf32_ta(tr, aih, bih, idn, 1u);    tc::mma_tf32_ta(tr, aih, bil, idn, 1u); tc::mma_tf32_ta(tr, ail, bih, idn, 1u);
+                        tc::mma_tf32_ta(ti, arh, bih, id, first);  tc::mma_tf32_ta(ti, arh, bil, id, 1u);  tc::mma_tf32_ta(ti, arl, bih, id, 1u);
+                        tc::mma_tf32_ta(ti, aih, brh, id, 1u);     tc::mma_tf32_ta(ti, aih, brl, id, 1u);  tc::mma_tf32_ta(ti, ail, brh, id, 1u);
+                    }
+                    tc::commit(tc::smem_u32(&empty[b]));
+                }
+                if (ok) tc::commit(tc::smem_u32(&accf));
+            }
+            if (!ok) {
+                atomicExch(&abort_flag, 1);
+                atomicExch(p.err, 1);
+            }
+            tc::commit(tc::smem_u32(&done));   // completion of every MMA issued above
         }
+        __syncwarp();
     } else {
-        // epilogue: lane = output row; 8 TMEM columns (8 complex outputs) per load from each accumulator
-        const int r = warp * 32 + lane, row = rt * TC_M + r, M = a.pd.M;
-        const double scale = a.scal ? a.scale * a.scal[1] : a.scale;
-        for (int c0 = 0; c0 < NB; c0 += 8) {
-            unsigned vr[8], vi[8];
-            const unsigned lane_off = (unsigned)(warp * 32) << 16;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7])
-                         : "r"(tmem + lane_off + (unsigned)c0));
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7])
-                         : "r"(tmem + lane_off + 256u + (unsigned)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int n0 = nt * NB + c0;   // first complex output column of this group
-            if (a.out64) {
-                if (row < M) {
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int n = n0 + j;
-                        if (n >= M) break;
-                        a.out64[((size_t)(a.qlist ? a.qlist[q] : q) * M + row) * M + n] =
-                            make_double2(scale * (double)__uint_as_float(vr[j]), scale * (double)__uint_as_float(vi[j]));
-                    }
+        // ------------------------------------------------------------------ epilogue: tensor memory -> global
+        const int qw = warp & 3, row = qw * 32 + lane, M = p.d.M;
+        const unsigned lane_off = (unsigned)(qw * 32) << 16;
+        const size_t M2 = (size_t)M * M;
+        for (int it = 0; it < my_items; it++) {
+            int ok = 1;
+            if (lane == 0) ok = tc::mbar_wait_or_abort(tc::smem_u32(&accf), it & 1, &abort_flag) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(&abort_flag, 1);
+                    atomicExch(p.err, 1);
                 }
-            } else {
-                // packed left operand of the next product: row tile rt, K = n (padding columns are zero here)
+                break;
+            }
+            tc::fence_after();
+            int ch, z, mt, nt;
+            decode((int)blockIdx.x + it * G, ch, z, mt, nt);
+            const int m = mt * TM + row;
+            const int qs = p.qlist ? p.qlist[z] : z;
+            // c_X times the flow-scale factor, applied in FP32 (the products carry FP32 accuracy)
+            const float c = PH == 1 ? (float)((ch == 0 ? 1.0 : 2.0) * (p.scal ? p.scal[1] : 1.0)) : 1.f;
+            for (int c0 = 0; c0 < NB; c0 += 8) {
+                unsigned vr[8], vi[8];
+                tc::tmem_ld8(tmem + lane_off + (unsigned)c0, vr);
+                tc::tmem_ld8(tmem + lane_off + ACC_IM + (unsigned)c0, vi);
+                tc::tmem_wait_ld();
+                const int n0 = nt * NB + c0;
+                if (m >= M || n0 >= M) continue;
+                if (PH == 0) {
+                    float2 *dst = p.T + ((size_t)ch * p.nz + z) * M2 + (size_t)m * M + n0;
+                    if (n0 + 8 <= M) {
 #pragma unroll
-                for (int g = 0; g < 2; g++) {
-                    const int k = n0 + 4 * g;
-                    if (k >= a.pd.nks * KS) break;
-                    float *blk = a.out_left + (((size_t)q * a.pd.m_tiles + rt) * a.pd.nks + k / KS) * 4 * (TC_M * KS);
-                    const int o = core_off(r, k % KS, TC_M);
-                    float re[4], im[4];
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        re[j] = __uint_as_float(vr[4 * g + j]);
-                        im[j] = __uint_as_float(vi[4 * g + j]);
+                        for (int j = 0; j < 8; j += 2)
+                            *reinterpret_cast<float4 *>(dst + j) = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
+                                                                               __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
+                    } else {
+                        for (int j = 0; j < 8 && n0 + j < M; j++) dst[j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
                     }
-                    float4 h = make_float4(tf32_hi(re[0]), tf32_hi(re[1]), tf32_hi(re[2]), tf32_hi(re[3]));
-                    float4 l = make_float4(re[0] - h.x, re[1] - h.y, re[2] - h.z, re[3] - h.w);
-                    *reinterpret_cast<float4 *>(blk + 0 * TC_M * KS + o) = h;
-                    *reinterpret_cast<float4 *>(blk + 1 * TC_M * KS + o) = l;
-                    h = make_float4(tf32_hi(im[0]), tf32_hi(im[1]), tf32_hi(im[2]), tf32_hi(im[3]));
-                    l = make_float4(im[0] - h.x, im[1] - h.y, im[2] - h.z, im[3] - h.w);
-                    *reinterpret_cast<float4 *>(blk + 2 * TC_M * KS + o) = h;
-                    *reinterpret_cast<float4 *>(blk + 3 * TC_M * KS + o) = l;
+                } else {
+                    double2 *dst = p.out + ((size_t)ch * p.Nq + qs) * M2 + (size_t)m * M + n0;
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (n0 + j < M)
+                            dst[j] = make_double2(f32_to_f64(c * __uint_as_float(vr[j])), f32_to_f64(c * __uint_as_float(vi[j])));
                 }
             }
+            tc::fence_before();
+            tc::mbar_arrive(tc::smem_u32(&acce));
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == MMA_WARP * 32) (void)tc::mbar_wait(tc::smem_u32(&done), 0);   // bounded; the MMAs read shared memory
+    tc::fence_before();
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        tc::fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
-PackDims pack_dims(const tufrg_model *m)
+template <int PH>
+cudaError_t launch_phase(tufrg_model *m, const VlvArgs &a)
 {
-    PackDims pd{};
-    pd.M = m->M;
-    pd.nks = (m->M + KS - 1) / KS;
-    pd.n_tiles = (m->M + 255) / 256;
-    pd.nb = ((m->M + pd.n_tiles - 1) / pd.n_tiles + 15) / 16 * 16;
-    pd.m_tiles = (m->M + TC_M - 1) / TC_M;
-    return pd;
+    const size_t smem = NSTAGE * 4 * (size_t)a.d.nb * KS * 4 + sizeof(int) * (size_t)a.nff * a.nff;
+    void (*k)(VlvArgs) = nullptr;
+    switch (m->ns * m->ns) {
+    case 4: k = vlv_tc_kernel<PH, 4>; break;
+    case 16: k = vlv_tc_kernel<PH, 16>; break;
+    case 36: k = vlv_tc_kernel<PH, 36>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<std::min(a.n_items, m->sm_count), NTHREADS, smem, m->stream>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-bool tc_supported(const tufrg_model *m) { return m->precision == TUFRG_SPLIT32 && m->products == TUFRG_PRODUCTS_TC; }
-
-// bytes of the packed left and right operands of all transfer momenta
-void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right)
+bool tc_supported(const tufrg_model *m)
 {
-    const PackDims pd = pack_dims(m);
-    *left = sizeof(float) * (size_t)m->Nq * pd.m_tiles * pd.nks * 4 * TC_M * KS;
-    *right = sizeof(float) * (size_t)m->Nq * pd.n_tiles * pd.nks * 4 * (size_t)pd.nb * KS;
+    const int ns2 = m->ns * m->ns;
+    return m->precision == TUFRG_SPLIT32 && m->products == TUFRG_PRODUCTS_TC && (ns2 == 4 || ns2 == 16 || ns2 == 36) &&
+           m->M % 4 == 0;
 }
 
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist)
 {
-    if (!m->d_tc_left[0] || !m->d_tc_right || !m->d_tc_gidx) return cudaErrorNotReady;
-    const PackDims pd = pack_dims(m);
+    if (!m->d_T) return cudaErrorNotReady;
     const int M = m->M, ns2 = m->ns * m->ns;
-    const size_t M2 = (size_t)M * M, lper = (size_t)m->nd * ns2 * ns2;
-    const size_t smem = 2 * (4 * (size_t)TC_M * KS * 4 + 4 * (size_t)pd.nb * KS * 4);
-    TUFRG_CUDA_TRY(cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int nz = qlist ? nlist : m->Nq;
-    const dim3 ggrid(pd.n_tiles, pd.m_tiles, nz);
-    const dim3 lgrid(pd.m_tiles, pd.nks, nz), rgrid(pd.n_tiles, pd.nks, nz), rblock(pd.nb, 4);
-    PhaseScope ps(m, PH_VLV, 8);
-    for (int ch = 0; ch < 2; ch++) {
-        double2 *o = d_out + (size_t)ch * m->Nq * M2;
-        if (!((channel_mask >> ch) & 1)) {
-            TUFRG_CUDA_TRY(cudaMemsetAsync(o, 0, sizeof(double2) * m->Nq * M2, m->stream));
-            continue;
-        }
-        const float2 *A = m->d_A32 + (size_t)ch * m->Nq * M2;
-        // T = A L
-        pack_left_kernel<<<lgrid, 512, 0, m->stream>>>(A, pd, qlist, m->d_tc_left[0]);
-        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(nullptr, m->d_Lc32 + ch * m->Nq * lper, m->d_tc_gidx, (int)lper,
-                                                           pd, qlist, m->d_tc_right);
-        GemmArgs g{};
-        g.left = m->d_tc_left[0];
-        g.right = m->d_tc_right;
-        g.out_left = m->d_tc_left[1];
-        g.out64 = nullptr;
-        g.err = m->d_err;
-        g.pd = pd;
-        g.scale = 1.0;
-        g.scal = nullptr;
-        g.qlist = qlist;
-        tc_cgemm_kernel<<<ggrid, TC_THREADS, smem, m->stream>>>(g);
-        TUFRG_CUDA_TRY(cudaGetLastError());
-        // dX = c T A
-        pack_right_kernel<<<rgrid, rblock, 0, m->stream>>>(A, nullptr, nullptr, 0, pd, qlist, m->d_tc_right);
-        GemmArgs h = g;
-        h.left = m->d_tc_left[1];
-        h.out_left = nullptr;
-        h.out64 = o;
-        h.scale = ch == 0 ? 1.0 : 2.0;
-        h.scal = m->d_scal;
-        tc_cgemm_kernel<<<ggrid, TC_THREADS, smem, m->stream>>>(h);
-        TUFRG_CUDA_TRY(cudaGetLastError());
-    }
-    return cudaSuccess;
+    const size_t M2 = (size_t)M * M;
+    PhaseScope ps(m, PH_VLV, 2);
+    for (int ch = 0; ch < 2; ch++)
+        if (!((channel_mask >> ch) & 1))
+            TUFRG_CUDA_TRY(cudaMemsetAsync(d_out + (size_t)ch * m->Nq * M2, 0, sizeof(double2) * m->Nq * M2, m->stream));
+    if (!(channel_mask & 3)) return cudaSuccess;
+    VlvArgs a{};
+    a.A = m->d_A32;
+    a.Lc = m->d_Lc32;
+    a.dij = m->d_dij;
+    a.T = reinterpret_cast<float2 *>(m->d_T);
+    a.out = d_out;
+    a.qlist = qlist;
+    a.scal = m->d_scal;
+    a.err = m->d_err;
+    a.d = dims_of(M);
+    a.nff = m->nff;
+    a.lper = m->nd * ns2 * ns2;
+    a.Nq = m->Nq;
+    a.nz = qlist ? nlist : m->Nq;
+    a.ch0 = (channel_mask & 1) ? 0 : 1;
+    a.nch = (channel_mask & 3) == 3 ? 2 : 1;
+    a.n_items = a.nch * a.nz * a.d.m_tiles * a.d.n_tiles;
+    if (a.n_items == 0) return cudaSuccess;
+    TUFRG_CUDA_TRY(launch_phase<0>(m, a));
+    return launch_phase<1>(m, a);
 }
 
 }  // namespace tufrg

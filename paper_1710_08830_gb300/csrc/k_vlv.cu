@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) sym_scatter_kernel(double2 *out, int Nq, 
 
 cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
 {
-    PhaseScope ps(m, PH_VLV);
+    PhaseScope ps(m, PH_SCATTER);
     const int threads = 256;
     sym_scatter_kernel<<<dim3(m->Nq, 2), threads, 2 * sizeof(int) * m->M, m->stream>>>(
         d_out, m->Nq, m->M, threads / m->M, threads % m->M, m->d_qmap, m->d_loop_list, m->d_sym_elem, m->d_sym_srow,

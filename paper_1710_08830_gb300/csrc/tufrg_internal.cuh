@@ -256,9 +256,6 @@ struct tufrg_model {
                                                //  high bit = minus sign; phase-table column)
     double2 *d_v0d[2] = {nullptr, nullptr};    // [M*M] bare vertex V0 at the onsite bond pair, 0 elsewhere
     float2 *d_X32 = nullptr;        // [2][Nq][M][M] FP32 copy of the state being evaluated (split path)
-    float *d_tc_left[2] = {nullptr, nullptr};   // tensor-core products: packed left operands (A, then T)
-    float *d_tc_right = nullptr;    // packed right operand (L, then A)
-    int *d_tc_gidx = nullptr;       // [M][M] index of L[k][n] in one momentum's compact loops
     float2 *d_lph32 = nullptr;      // [Lf] e^{-2 pi i n / Lf} for the split loop kernel
     float2 *d_clsph32 = nullptr;    // [Nq][ncls] e^{i u.R''} (split-path Fourier transform)
     float2 *d_v0d32[2] = {nullptr, nullptr};   // FP32 copies of d_v0d (split path)
@@ -272,7 +269,7 @@ struct tufrg_model {
     double2 *d_Xr = nullptr;        // [2][ncls][M][M] Fourier transforms
     double2 *d_A = nullptr;         // [2][Nq][M][M] projected vertex
     float2 *d_A32 = nullptr;        // [2][Nq][M][M] (split path)
-    double2 *d_T = nullptr;         // [Nq][M][M] GEMM intermediate (large M)
+    double2 *d_T = nullptr;         // [Nq][M][M] GEMM intermediate (large M); split: [2][Nq][M][M] FP32 complex
     float4 *d_rec = nullptr;        // [Nk][4] split-path loop records (projectors + Fermi data)
     float2 *d_Xr32 = nullptr;       // [2][ncls][M][M] Fourier transforms (split path)
     float2 *d_ph32 = nullptr;       // [Nq][nph] phase table (split path)
@@ -411,7 +408,6 @@ cudaError_t launch_band_basis(tufrg_model *m, const double2 *d_state, double2 *d
 bool orbit_products_supported(const tufrg_model *m);
 int orbit_max_size();   // largest orbit the fused orbit kernel takes   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
-void tc_pack_bytes(const tufrg_model *m, size_t *left, size_t *right);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);
 cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
 cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu
@@ -429,7 +425,7 @@ cudaError_t mlp_gemm_tc(cudaStream_t s, const TA *A, int lda, int ta, const stru
 cudaError_t surrogate_rearm(tufrg_model *m);
 void mlp_dims(const tufrg_mlp *n, int *n_in, int *n_out);
 
-enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_N = 7 };
+enum Phase { PH_FERMI = 0, PH_LOOPS = 1, PH_LOOPRED = 2, PH_DFT = 3, PH_PROJ = 4, PH_VLV = 5, PH_RK = 6, PH_SCATTER = 7, PH_N = 8 };
 
 // Brackets one kernel phase with events when timing is on; counts launches always.
 struct PhaseScope {
