@@ -19,8 +19,9 @@
 //               right operand's to shared memory in the K-major core-matrix layout;
 //   warp 16     tensor-memory allocation and the MMA issuer (one thread): 24 MMAs per stage (2 K-steps x 4 real
 //               products x 3 TF32 passes), the left operand read from tensor memory;
-//   warps 17-20 epilogue: tensor memory -> T (FP32) or c dX (FP64) in global memory.
-// Four stage buffers (mbarriers full / empty); one accumulator (mbarriers acc_full / acc_empty).  Every wait is
+//   warps 17-20 epilogue: tensor memory -> a shared-memory tile (then the accumulator is released to the next
+//               item's MMAs) -> T (FP32) or c dX (FP64) in global memory, consecutive lanes on consecutive columns.
+// Three stage buffers (mbarriers full / empty); one accumulator (mbarriers acc_full / acc_empty).  Every wait is
 // bounded; on time-out the kernel raises the error flag, every role stops, the MMAs in flight are waited for
 // (bounded) and the tensor memory is freed.
 #include "tc_common.cuh"
@@ -31,11 +32,11 @@ namespace {
 
 constexpr int TM = 128;             // MMA M: rows per tile
 constexpr int KS = 16;              // K per stage (two MMA K-steps of 8)
-constexpr int NSTAGE = 4;           // stage buffers
+constexpr int NSTAGE = 3;           // stage buffers
 constexpr int NPROD = 512;          // producer threads (warps 0-15)
 constexpr int MMA_WARP = 16;        // warps 17-20: epilogue
 constexpr int NTHREADS = 21 * 32;
-constexpr int NB_MAX = 128;         // columns per tile (complex), a multiple of 16
+constexpr int NB_MAX = 112;         // columns per tile (complex), a multiple of 16
 // tensor memory: accumulator Re at [0, NB), Im at [128, 128 + NB); left operand of stage b at 256 + 64 b, plane p at
 // + 16 p (K = 16 columns)
 constexpr unsigned ACC_IM = 128, A_COL0 = 256, A_STAGE_COLS = 64, A_PLANE_COLS = 16;
@@ -45,7 +46,7 @@ static_assert(A_COL0 + NSTAGE * A_STAGE_COLS <= TMEM_COLS, "tensor memory budget
 struct Dims {
     int M;          // complex matrix order (a multiple of 4)
     int nks;        // K stages covering M
-    int nb;         // complex columns per tile (multiple of 16, <= 128)
+    int nb;         // complex columns per tile (multiple of 16, <= 112)
     int m_tiles;    // 128-row tiles covering M
     int n_tiles;    // nb-column tiles covering M
 };
@@ -159,10 +160,13 @@ __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__
 template <int PH, int NS2>
 __global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];   // NSTAGE right-operand stages, then the bond table
+    // dynamic shared memory: NSTAGE right-operand stages, the epilogue's FP32 tile [128][NB + 2], the bond table
+    extern __shared__ __align__(1024) unsigned char smem[];
     const int NB = p.d.nb, nks = p.d.nks;
     const unsigned b_plane = (unsigned)NB * KS * 4, b_stage = 4 * b_plane;   // bytes
-    int *sdij = reinterpret_cast<int *>(smem + NSTAGE * (size_t)b_stage);
+    const int estr = NB + 2;                                                  // tile row stride (complex)
+    float2 *etile = reinterpret_cast<float2 *>(smem + NSTAGE * (size_t)b_stage);
+    int *sdij = reinterpret_cast<int *>(etile + (size_t)TM * estr);
     __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], accf, acce, done;
     __shared__ unsigned tmem_base;
     __shared__ int abort_flag;
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
         __syncwarp();
     } else {
         // ------------------------------------------------------------------ epilogue: tensor memory -> global
-        const int qw = warp & 3, row = qw * 32 + lane, M = p.d.M;
+        const int qw = warp & 3, M = p.d.M;
         const unsigned lane_off = (unsigned)(qw * 32) << 16;
         const size_t M2 = (size_t)M * M;
         for (int it = 0; it < my_items; it++) {
@@ -338,39 +342,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
                 break;
             }
             tc::fence_after();
-            int ch, z, mt, nt;
-            decode((int)blockIdx.x + it * G, ch, z, mt, nt);
-            const int m = mt * TM + row;
-            const int qs = p.qlist ? p.qlist[z] : z;
-            // c_X times the flow-scale factor, applied in FP32 (the products carry FP32 accuracy)
-            const float c = PH == 1 ? (float)((ch == 0 ? 1.0 : 2.0) * (p.scal ? p.scal[1] : 1.0)) : 1.f;
+            // the accumulator into this warp's rows of the shared-memory tile (lane = row, two columns per 16-byte
+            // store; the row stride of NB + 2 columns keeps them free of bank conflicts), then release it to the
+            // next item's MMAs
+            float2 *et = etile + (size_t)(qw * 32) * estr;
             for (int c0 = 0; c0 < NB; c0 += 8) {
                 unsigned vr[8], vi[8];
                 tc::tmem_ld8(tmem + lane_off + (unsigned)c0, vr);
                 tc::tmem_ld8(tmem + lane_off + ACC_IM + (unsigned)c0, vi);
                 tc::tmem_wait_ld();
-                const int n0 = nt * NB + c0;
-                if (m >= M || n0 >= M) continue;
-                if (PH == 0) {
-                    float2 *dst = p.T + ((size_t)ch * p.nz + z) * M2 + (size_t)m * M + n0;
-                    if (n0 + 8 <= M) {
 #pragma unroll
-                        for (int j = 0; j < 8; j += 2)
-                            *reinterpret_cast<float4 *>(dst + j) = make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]),
-                                                                               __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
-                    } else {
-                        for (int j = 0; j < 8 && n0 + j < M; j++) dst[j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
-                    }
-                } else {
-                    double2 *dst = p.out + ((size_t)ch * p.Nq + qs) * M2 + (size_t)m * M + n0;
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (n0 + j < M)
-                            dst[j] = make_double2(f32_to_f64(c * __uint_as_float(vr[j])), f32_to_f64(c * __uint_as_float(vi[j])));
-                }
+                for (int j = 0; j < 8; j += 2)
+                    *reinterpret_cast<float4 *>(et + (size_t)lane * estr + c0 + j) =
+                        make_float4(__uint_as_float(vr[j]), __uint_as_float(vi[j]), __uint_as_float(vr[j + 1]), __uint_as_float(vi[j + 1]));
             }
             tc::fence_before();
             tc::mbar_arrive(tc::smem_u32(&acce));
+            __syncwarp();
+            // coalesced rows: for each of the warp's 32 rows, consecutive lanes write consecutive columns
+            int ch, z, mt, nt;
+            decode((int)blockIdx.x + it * G, ch, z, mt, nt);
+            const int qs = p.qlist ? p.qlist[z] : z;
+            const int n0 = nt * NB, ncol = min(NB, M - n0), m0 = mt * TM + qw * 32, nrow = min(32, M - m0);
+            // c_X times the flow-scale factor, applied in FP32 (the products carry FP32 accuracy)
+            const float c = PH == 1 ? (float)((ch == 0 ? 1.0 : 2.0) * (p.scal ? p.scal[1] : 1.0)) : 1.f;
+            // two columns per lane and store (ncol and n0 are even, rows start 16-byte aligned)
+            const int npair = ncol / 2;
+#pragma unroll 4
+            for (int rr = 0; rr < nrow; rr++) {
+                const float4 *src = reinterpret_cast<const float4 *>(et + (size_t)rr * estr);
+                if (PH == 0) {
+                    float4 *dst = reinterpret_cast<float4 *>(p.T + ((size_t)ch * p.nz + z) * M2 + (size_t)(m0 + rr) * M + n0);
+                    for (int cp = lane; cp < npair; cp += 32) dst[cp] = src[cp];
+                } else {
+                    double2 *dst = p.out + ((size_t)ch * p.Nq + qs) * M2 + (size_t)(m0 + rr) * M + n0;
+                    for (int cp = lane; cp < npair; cp += 32) {
+                        const float4 v = src[cp];
+                        dst[2 * cp] = make_double2(f32_to_f64(c * v.x), f32_to_f64(c * v.y));
+                        dst[2 * cp + 1] = make_double2(f32_to_f64(c * v.z), f32_to_f64(c * v.w));
+                    }
+                }
+            }
+            __syncwarp();   // the tile rows are read before the next item's accumulator overwrites them
         }
     }
     __syncthreads();
@@ -386,7 +399,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
 template <int PH>
 cudaError_t launch_phase(tufrg_model *m, const VlvArgs &a)
 {
-    const size_t smem = NSTAGE * 4 * (size_t)a.d.nb * KS * 4 + sizeof(int) * (size_t)a.nff * a.nff;
+    const size_t smem = NSTAGE * 4 * (size_t)a.d.nb * KS * 4 + sizeof(float2) * (size_t)TM * (a.d.nb + 2) +
+                        sizeof(int) * (size_t)a.nff * a.nff;
     void (*k)(VlvArgs) = nullptr;
     switch (m->ns * m->ns) {
     case 4: k = vlv_tc_kernel<PH, 4>; break;
