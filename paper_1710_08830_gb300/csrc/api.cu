@@ -492,7 +492,7 @@ void release(tufrg_model *m)
                     m->d_ph32, m->d_dftpart, m->d_dpartner, m->d_err, m->d_scal, m->d_flow, m->d_eofs[0],
                     m->d_eofs[1], m->d_eterms[0], m->d_eterms[1], m->d_v0d[0], m->d_v0d[1], m->d_X32,
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
-                    m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_sym_srow, m->d_sym_qrow, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
+                    m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_sym_srow, m->d_sym_qrow, m->d_sym_sinv, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
                     m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32, m->d_ffW};
     for (void *p : ptrs)
@@ -844,16 +844,31 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                 m->sym_state = true;
                 CK(upload(&m->d_sym_srow, srow, m->stream), "upload symmetry tables");
                 CK(upload(&m->d_sym_qrow, qrow, m->stream), "upload symmetry tables");
+                // the inverse maps (every srow is a permutation when the bond set and the orbital pairs are closed
+                // under the elements; otherwise the copy runs per target momentum)
+                std::vector<int> sinv(srow.size(), -1);
+                bool perm = true;
+                for (size_t o = 0; o < srow.size() && perm; o++) {
+                    const size_t base = o / m->M * m->M;
+                    int &t = sinv[base + srow[o]];
+                    perm = t < 0;
+                    t = (int)(o - base);
+                }
+                if (perm) CK(upload(&m->d_sym_sinv, sinv, m->stream), "upload symmetry tables");
                 std::vector<int> ofs(m->n_loop_q + 1, 0), oq(m->Nq);
                 for (int q = 0; q < m->Nq; q++) ofs[ls.qmap[q].x + 1]++;
                 int max_orbit = 0;
                 for (int p = 0; p < m->n_loop_q; p++) max_orbit = std::max(max_orbit, ofs[p + 1]);
                 for (int p = 0; p < m->n_loop_q; p++) ofs[p + 1] += ofs[p];
+                // the momenta of every orbit, orbit after orbit (the copy of the representatives' products to the
+                // other members runs in this order, so that a representative's matrix stays in L2 for its orbit)
+                std::vector<int> fill(ofs.begin(), ofs.end() - 1);
+                for (int q = 0; q < m->Nq; q++) oq[fill[ls.qmap[q].x]++] = q;
+                CK(upload(&m->d_orb_ofs, ofs, m->stream), "upload symmetry tables");
+                CK(upload(&m->d_orb_q, oq, m->stream), "upload symmetry tables");
                 if (orbit_products_supported(m) && max_orbit <= orbit_max_size()) {
-                    // fused orbit products: the momenta of every orbit and, per element and channel, the
-                    // source entry, quarter turns and conjugation of every target entry
-                    std::vector<int> fill(ofs.begin(), ofs.end() - 1);
-                    for (int q = 0; q < m->Nq; q++) oq[fill[ls.qmap[q].x]++] = q;
+                    // fused orbit products: per element and channel, the source entry, quarter turns and
+                    // conjugation of every target entry
                     const int M = m->M;
                     std::vector<int> emap((size_t)ls.elem.size() * 2 * M * M);
                     for (size_t e = 0; e < ls.elem.size(); e++)
@@ -871,8 +886,6 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
                         for (int c = 0; c < M; c++)
                             lexp[(size_t)r * M + c] = (m->dij[(r >> 2) * m->nff + (c >> 2)] * 4 + (r & 3)) * 4 + (c & 3);
                     CK(upload(&m->d_orb_lexp, lexp, m->stream), "upload symmetry tables");
-                    CK(upload(&m->d_orb_ofs, ofs, m->stream), "upload symmetry tables");
-                    CK(upload(&m->d_orb_q, oq, m->stream), "upload symmetry tables");
                     CK(upload(&m->d_sym_emap, emap, m->stream), "upload symmetry tables");
                 }
             }

@@ -351,12 +351,29 @@ __global__ void vlv_small_kernel(const typename cpx<R>::t *A, const typename cpx
 // r' to source row srow[r'] with i^qrow[r'], conjugated for time-reversed elements).  One CTA per
 // (q', channel) walks the M^2 entries; the element's row tables sit in shared memory and the entry
 // indices advance incrementally (blockDim = dr M + dc).
+// (re, im) of a complex FP64 value times i^k, with the signs flipped on the bit patterns (integer operations)
+__device__ __forceinline__ double2 times_i_pow(double2 v, int k)
+{
+    const long long sg = (long long)0x8000000000000000ull;
+    const long long re = __double_as_longlong(v.x), im = __double_as_longlong(v.y);
+    switch (k & 3) {
+    case 0: return v;
+    case 1: return make_double2(__longlong_as_double(im ^ sg), v.x);
+    case 2: return make_double2(__longlong_as_double(re ^ sg), __longlong_as_double(im ^ sg));
+    default: return make_double2(v.y, __longlong_as_double(re ^ sg));
+    }
+}
+
+// dX/dT of the non-representative momenta from their representative's result: target entry (r, c) of momentum q2
+// = i^(qt[r] - qt[c]) (conjugated for antiunitary elements) times source entry (srow[r], srow[c]).  One CTA per
+// (momentum, channel); the momenta run orbit after orbit (order[]), so each representative's matrix is read from
+// DRAM once and then from L2 for the rest of its orbit.
 __global__ void __launch_bounds__(256) sym_scatter_kernel(double2 *out, int Nq, int M, int dr, int dc, const int2 *qmap,
-                                                          const int *list, const SymElem *elem, const int *srow,
-                                                          const int *qrow)
+                                                          const int *list, const int *order, const SymElem *elem,
+                                                          const int *srow, const int *qrow)
 {
     extern __shared__ int s_tab[];   // [M] source rows, [M] quarter turns
-    const int q2 = blockIdx.x, ch = blockIdx.y;
+    const int q2 = order[blockIdx.x], ch = blockIdx.y;
     const int2 ie = qmap[q2];
     const int q = list[ie.x];
     if (q == q2) return;             // representatives hold their own result
@@ -373,18 +390,48 @@ __global__ void __launch_bounds__(256) sym_scatter_kernel(double2 *out, int Nq, 
     int r = threadIdx.x / M, c = threadIdx.x - r * M;
     for (int t = threadIdx.x; t < M2; t += blockDim.x) {
         double2 v = src[(size_t)s_tab[r] * M + s_tab[c]];
-        if (conj) v.y = -v.y;
-        double2 w;
-        switch ((s_tab[M + r] - s_tab[M + c]) & 3) {
-        case 0: w = v; break;
-        case 1: w = make_double2(-v.y, v.x); break;
-        case 2: w = make_double2(-v.x, -v.y); break;
-        default: w = make_double2(v.y, -v.x); break;
-        }
-        dst[t] = w;
+        if (conj) v.y = __longlong_as_double(__double_as_longlong(v.y) ^ (long long)0x8000000000000000ull);
+        dst[t] = times_i_pow(v, s_tab[M + r] - s_tab[M + c]);
         r += dr;
         c += dc;
         if (c >= M) { c -= M; r++; }
+    }
+}
+
+// The same copy, orbit by orbit: one CTA per (representative, block of RB source rows, channel) reads its rows once
+// into shared memory and writes the target rows of every other member of the orbit, row r = sinv[i] of member q2
+// taking source row i: entry (r, c) = i^(qt[r] - qt[c]) (conjugated for antiunitary elements) times row i's entry
+// srow[c].  DRAM then sees each representative's matrix read once and every member's matrix written once, coalesced.
+constexpr int ORB_RB = 8;
+__global__ void __launch_bounds__(256) sym_orbit_copy_kernel(double2 *out, int Nq, int M, const int2 *qmap, const int *list,
+                                                             const int *orb_ofs, const int *orb_q, const SymElem *elem,
+                                                             const int *srow, const int *sinv, const int *qrow)
+{
+    extern __shared__ double2 s_rows[];   // [ORB_RB][M]
+    const int p = blockIdx.x, i0 = blockIdx.y * ORB_RB, ch = blockIdx.z;
+    const int q = list[p], nr = min(ORB_RB, M - i0);
+    const size_t M2 = (size_t)M * M;
+    const double2 *src = out + ((size_t)ch * Nq + q) * M2 + (size_t)i0 * M;
+    for (int t = threadIdx.x; t < nr * M; t += blockDim.x) s_rows[t] = src[t];
+    __syncthreads();
+    const long long sg = (long long)0x8000000000000000ull;
+    for (int mi = orb_ofs[p]; mi < orb_ofs[p + 1]; mi++) {
+        const int q2 = orb_q[mi];
+        if (q2 == q) continue;
+        const int e = qmap[q2].y;
+        const bool conj = elem[e].conj;
+        const int *sr = srow + ((size_t)e * 2 + ch) * M, *si = sinv + ((size_t)e * 2 + ch) * M, *qr = qrow + ((size_t)e * 2 + ch) * M;
+        double2 *dst = out + ((size_t)ch * Nq + q2) * M2;
+        for (int ii = 0; ii < nr; ii++) {
+            const int r = si[i0 + ii], qrr = qr[r];
+            const double2 *row = s_rows + (size_t)ii * M;
+            double2 *d = dst + (size_t)r * M;
+            for (int c = threadIdx.x; c < M; c += blockDim.x) {
+                double2 v = row[sr[c]];
+                if (conj) v.y = __longlong_as_double(__double_as_longlong(v.y) ^ sg);
+                d[c] = times_i_pow(v, qrr - qr[c]);
+            }
+        }
     }
 }
 
@@ -392,9 +439,18 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
 {
     PhaseScope ps(m, PH_SCATTER);
     const int threads = 256;
+    if (m->d_sym_sinv && m->d_orb_ofs) {
+        const size_t smem = sizeof(double2) * ORB_RB * m->M;
+        if (smem > 48 * 1024)
+            TUFRG_CUDA_TRY(cudaFuncSetAttribute(sym_orbit_copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sym_orbit_copy_kernel<<<dim3(m->n_loop_q, (m->M + ORB_RB - 1) / ORB_RB, 2), threads, smem, m->stream>>>(
+            d_out, m->Nq, m->M, m->d_qmap, m->d_loop_list, m->d_orb_ofs, m->d_orb_q, m->d_sym_elem, m->d_sym_srow,
+            m->d_sym_sinv, m->d_sym_qrow);
+        return cudaGetLastError();
+    }
     sym_scatter_kernel<<<dim3(m->Nq, 2), threads, 2 * sizeof(int) * m->M, m->stream>>>(
-        d_out, m->Nq, m->M, threads / m->M, threads % m->M, m->d_qmap, m->d_loop_list, m->d_sym_elem, m->d_sym_srow,
-        m->d_sym_qrow);
+        d_out, m->Nq, m->M, threads / m->M, threads % m->M, m->d_qmap, m->d_loop_list, m->d_orb_q, m->d_sym_elem,
+        m->d_sym_srow, m->d_sym_qrow);
     return cudaGetLastError();
 }
 

@@ -246,6 +246,7 @@ struct tufrg_model {
     double sym_tune_ms[2] = {-1.0, -1.0};   // projections + products at every momentum / representatives + gather
     int *d_sym_srow = nullptr;      // [n_sym_elem][2][M] source index of every target row / column
     int *d_sym_qrow = nullptr;      // [n_sym_elem][2][M] quarter turns of every target row / column
+    int *d_sym_sinv = nullptr;      // [n_sym_elem][2][M] target index of every source row (srow inverted), or null
     int *d_orb_ofs = nullptr;       // [n_loop_q + 1] orbit of each representative: momenta orb_q[ofs[p] .. ofs[p+1])
     int *d_orb_q = nullptr;         // [Nq]
     int *d_sym_emap = nullptr;      // [n_sym_elem][2][M^2] source entry << 3 | quarter turns << 1 | conj (small M)
