@@ -641,6 +641,26 @@ def test_flow_batch_matches_single_flows():
             assert r1["Tc"] == r2["Tc"]
 
 
+def test_flow_batch_mixed_spin_orbitals():
+    """A batch that mixes two-band (N_s = 2) and bilayer (N_s = 4) instances, with different meshes and bond sets,
+    gives exactly the flows tufrg_flow gives one at a time, in both precisions."""
+    api = _api()
+    specs = [inputs.rashba_bilayer(tp=-0.2, alpha=0.3, t_perp=0.4, U=3.0, mu=-0.9, Lq=6, nc=3, n_ff=5),
+             inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=3.2, mu=-0.8, Lq=8, nc=3, n_ff=9),
+             inputs.rashba_bilayer(tp=-0.1, alpha=0.2, t_perp=0.3, U=2.8, mu=-0.7, Lq=4, nc=4, n_ff=9),
+             inputs.hubbard_square(U=3.0, Lq=6, nc=4, n_ff=5, filling=0.9, T_mu=0.02)]
+    assert sorted({sp.n_s for sp in specs}) == [2, 4]
+    for prec in (api.FP64, api.SPLIT32):
+        single = [api.Model(sp, prec).flow(stop=6.0)[1] for sp in specs]
+        streams = [torch.cuda.Stream() for _ in specs]
+        models = [api.Model(sp, prec, stream=s) for sp, s in zip(specs, streams)]
+        batch = api.flow_batch(models, stop=6.0)
+        for r1, r2 in zip(single, batch):
+            assert r1["n_steps"] == r2["n_steps"] and r1["n_reject"] == r2["n_reject"]
+            assert r1["crossed"] == r2["crossed"]
+            assert r1["Tc"] == r2["Tc"]
+
+
 def test_flow_critical_at_start():
     """max|A| of the bare vertex already above the stop value: the flow is critical at T0 (Lambda_c = T0, no
     step, one evaluation), alone and inside a batch next to a flow that runs; the oracle agrees."""
