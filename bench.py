@@ -782,6 +782,7 @@ def main():
                        "precision": "split (FP32 loop sums, FP64 state)",
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "loop_momenta_summed": m32.n_loop_q, "symmetric_state": True,
+                       "loop_tiles": {"ky_chunks": m32.loop_ky_chunks, "tuning_ms": m32.loop_tiles_tuning_ms},
                        "symmetric_state_path": m32.symmetric_state_path,
                        "symmetric_state_tuning_ms": m32.symmetric_state_tuning_ms,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},

@@ -202,6 +202,15 @@ tufrg_status tufrg_loop_momenta(const tufrg_model *m, int *n_direct);
  * Errors: TUFRG_EINVAL for NULL arguments. */
 tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend);
 
+/* Launch shape of the loop k-sum: *ky_chunks = the number of k_y ranges each fine-mesh column is split into (the
+ * grid's depth; every range ends with a flush of its partial sums), and, for the two-band split path, which times
+ * every candidate from 1 to 16 ranges (each range at least 8 rows) at model set-up and keeps the fastest:
+ * *n_candidates = their number and h_ms[i] (i < min(n_ms, *n_candidates)) = the measured milliseconds per launch
+ * of candidate i, which has i + 1 ranges.  Other paths report their heuristic choice and *n_candidates = 0.
+ * The choice is cached per process and model shape, so models of the same shape sum in the same order.
+ * Errors: TUFRG_EINVAL for NULL arguments or n_ms < 0 (h_ms may be NULL when n_ms is 0). */
+tufrg_status tufrg_loop_tiles(const tufrg_model *m, int *ky_chunks, int *n_candidates, double *h_ms, int n_ms);
+
 /* Exchange propagators of a state in the band basis of the model's eigenvectors (Sec. 3.4, Eqs. trafo_P,
  * mat_trafo_P, mat_trafo_D): with f_R(k) = e^{-ik.R}, N the fine mesh's k-points and U the eigenvectors of
  * tufrg_bands,

@@ -76,6 +76,12 @@ class Model:
         lb = C.c_int()
         self._check(self._L.tufrg_loops_info(self._h, C.byref(lb)))
         self.loops_backend = {LOOPS_TC: "tc", LOOPS_SIMT: "simt"}.get(lb.value, "?")
+        kyc, ncand = C.c_int(), C.c_int()
+        cand_ms = np.zeros(16)
+        self._check(self._L.tufrg_loop_tiles(self._h, C.byref(kyc), C.byref(ncand), cand_ms.ctypes.data, len(cand_ms)))
+        # the loop k-sum's ky ranges per column, and the timed candidates {ranges: ms per launch} when tuned
+        self.loop_ky_chunks = kyc.value
+        self.loop_tiles_tuning_ms = {c + 1: float(cand_ms[c]) for c in range(min(ncand.value, len(cand_ms)))}
         su, t_gen, t_rep = C.c_int(), C.c_double(), C.c_double()
         self._check(self._L.tufrg_symmetry_info(self._h, C.byref(su), C.byref(t_gen), C.byref(t_rep)))
         self.symmetric_state_path = bool(su.value)   # rhs(symmetric=True) works at the representatives only

@@ -442,6 +442,7 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
 struct TuneResult {
     double ms[2];
     int choice;
+    std::vector<double> cand_ms;   // the loop kernel's launch shapes: one time per candidate
 };
 std::mutex g_tune_mutex;
 std::map<std::vector<int>, TuneResult> g_tune_cache;
@@ -892,6 +893,11 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         }
     }
     m->plan = plan_loops(m);
+    // the two-band split loop kernel's launch shapes are timed at the end of the set-up (the partial sums are
+    // sized for the largest)
+    if (loops2_supported(m)) m->plan_cand = loop_plan_candidates(m);
+    int max_partials = m->plan.n_partials;
+    for (const LoopPlan &p : m->plan_cand) max_partials = std::max(max_partials, p.n_partials);
 
     // ---- device memory
     const size_t Nk = m->Nk, ns2 = (size_t)ns * ns, ns4 = ns2 * ns2, M2 = (size_t)m->M * m->M;
@@ -1025,7 +1031,7 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     int ndyh = 0;
     for (int v : m->dys) ndyh += v >= 0;
     // partial sums of both channels (the split two-band path sums P and C before one reduction)
-    m->part_bytes = 2 * (size_t)m->Nq * m->plan.n_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
+    m->part_bytes = 2 * (size_t)m->Nq * max_partials * m->dxs.size() * ndyh * ns4 * (split ? sizeof(float2) : sizeof(double2));
     if (ns != 2) {
         if (!loops_gen_supported(m)) return fail(m, TUFRG_ENOTSUP, "bond set too large for the multi-orbital loop kernel");
         m->loops_tc = d.loops != TUFRG_LOOPS_SIMT && loops_tc_supported(m);
@@ -1083,6 +1089,45 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     }
     CK(cudaStreamSynchronize(m->stream), "init sync");
     TuneResult cached{};
+    if (m->plan_cand.size() > 1 && tune_lookup(m, 3, &cached)) {
+        m->plan = m->plan_cand[cached.choice];
+        m->plan_ms = cached.cand_ms;
+    } else if (m->plan_cand.size() > 1) {
+        // autotune the loop k-sum's launch shape (ky ranges per column: grid depth against the per-column flush) on
+        // this model's mesh; the P channel at T = 1 (the cost does not depend on the values)
+        CK(launch_set_scalars(m, 1.0, 1.0), "set scalars");
+        CK(launch_fermi(m), "loop records");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        m->plan_ms.assign(m->plan_cand.size(), 0.0);
+        int best = 0;
+        for (size_t c = 0; c < m->plan_cand.size(); c++) {
+            m->plan = m->plan_cand[c];
+            CK(launch_loops2(m, 0), "loop autotune warm-up");
+            CK(cudaEventRecord(e0, m->stream), "event");
+            const int reps = 3;
+            for (int r = 0; r < reps; r++) CK(launch_loops2(m, 0), "loop autotune");
+            CK(cudaEventRecord(e1, m->stream), "event");
+            CK(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+            m->plan_ms[c] = ms / reps;
+            if (m->plan_ms[c] < m->plan_ms[best]) best = (int)c;
+        }
+        m->plan = m->plan_cand[best];
+        TuneResult r{};
+        r.choice = best;
+        r.cand_ms = m->plan_ms;
+        tune_store(m, 3, r);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        m->launches = 0;
+        m->loop_launches = 0;
+        int dev_err = 0;
+        CK(cudaMemcpy(&dev_err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "copy error flag");
+        if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
+    }
     if (split && d.products == TUFRG_PRODUCTS_AUTO && tune_lookup(m, 0, &cached)) {
         m->products = cached.choice;
         m->tune_ms[0] = cached.ms[0];
@@ -1200,6 +1245,15 @@ tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend)
 {
     if (!m || !backend) return TUFRG_EINVAL;
     *backend = m->loops_tc ? TUFRG_LOOPS_TC : TUFRG_LOOPS_SIMT;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_loop_tiles(const tufrg_model *m, int *ky_chunks, int *n_candidates, double *h_ms, int n_ms)
+{
+    if (!m || !ky_chunks || !n_candidates || (n_ms > 0 && !h_ms) || n_ms < 0) return TUFRG_EINVAL;
+    *ky_chunks = m->plan.ky_chunks;
+    *n_candidates = (int)m->plan_ms.size();
+    for (int i = 0; i < n_ms && i < (int)m->plan_ms.size(); i++) h_ms[i] = m->plan_ms[i];
     return TUFRG_OK;
 }
 

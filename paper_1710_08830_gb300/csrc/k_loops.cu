@@ -389,6 +389,22 @@ LoopPlan plan_loops(const tufrg_model *m)
     return p;
 }
 
+std::vector<LoopPlan> loop_plan_candidates(const tufrg_model *m)
+{
+    // every number of ky ranges per column from 1 to 16 whose ranges keep at least 8 rows
+    std::vector<LoopPlan> v;
+    const int kx_per_cta = 32 * WARPS, ctas_x = (m->Lf + kx_per_cta - 1) / kx_per_cta;
+    for (int c = 1; c <= 16; c++) {
+        if ((m->Lf + c - 1) / c < 8) break;
+        LoopPlan p{};
+        p.kx_per_cta = kx_per_cta;
+        p.ky_chunks = c;
+        p.n_partials = ctas_x * WARPS * c;
+        v.push_back(p);
+    }
+    return v;
+}
+
 // launch shape of the reductions: one row of CTAs per momentum, threads over (d, ab)
 static void reduce_shape(const tufrg_model *m, int n_s, dim3 &grid, int &thr)
 {

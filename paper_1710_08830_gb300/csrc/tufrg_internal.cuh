@@ -304,6 +304,8 @@ struct tufrg_model {
     int step_graph_mask = 0;
 
     tufrg::LoopPlan plan{};
+    std::vector<tufrg::LoopPlan> plan_cand;   // timed launch shapes of the loop k-sum (two-band split path)
+    std::vector<double> plan_ms;              // their measured times (ms per launch), same order
     int gen_chunks = 1;             // multi-orbital loop kernel: kx ranges (CTAs, accumulator slots) per momentum
     int basis = TUFRG_BASIS_ORBITAL;   // single-particle basis of the flow
     std::vector<double> ffW;        // [nff][nff] irrep form factors over the bonds (empty: set not C4v-closed)
@@ -373,6 +375,8 @@ cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, co
                                const double2 *k6, size_t n);
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
+// the launch shapes the two-band split loop kernel's autotuner times (ky ranges per column)
+std::vector<LoopPlan> loop_plan_candidates(const tufrg_model *m);
 int plan_gen_chunks(const tufrg_model *m);   // kx ranges per momentum of the multi-orbital loop kernel
 size_t gen_red_offset(const tufrg_model *m);   // byte offset of the representatives' range sums in d_part
 size_t gen_part_bytes(const tufrg_model *m);   // loop scratch of the multi-orbital kernel

@@ -67,6 +67,7 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
         "tufrg_surrogate_stats": (None, ctypes.byref(ll), ctypes.byref(ll), ctypes.byref(ll)),
         "tufrg_timing_begin": (None,), "tufrg_timing_end": (None, None, 0, None, None),
         "tufrg_set_device_error": (None, 1), "tufrg_loops_info": (None, ctypes.byref(i)),
+        "tufrg_loop_tiles": (None, ctypes.byref(i), ctypes.byref(i), None, 0),
         "tufrg_shard_classes": (None, ctypes.byref(i), None), "tufrg_form_factors": (None, None, None),
         "tufrg_irrep_basis": (None, None, 0, None), "tufrg_rhs_shard_transform": (None, None, 1, None, 3, None),
         "tufrg_rhs_shard_finish": (None, 0.1, None, 1, None, None, 3, None),

@@ -641,6 +641,27 @@ def test_flow_batch_matches_single_flows():
             assert r1["Tc"] == r2["Tc"]
 
 
+def test_loop_tile_autotune():
+    """The two-band split loop kernel's launch shape (ky ranges per column) is timed at set-up over every candidate
+    and the fastest kept; a second model of the same shape reuses the choice (the same summation order), and the
+    loops at the chosen shape match the oracle."""
+    api = _api()
+    spec = CASES["rashba_ff9_Lf25"]()
+    m = api.Model(spec, api.SPLIT32)
+    t = m.loop_tiles_tuning_ms
+    assert len(t) >= 2 and all(v > 0 for v in t.values())
+    assert m.loop_ky_chunks == min(t, key=t.get)
+    assert all((spec.Lq * spec.nc + c - 1) // c >= 8 for c in t)
+    m2 = api.Model(spec, api.SPLIT32)
+    assert m2.loop_ky_chunks == m.loop_ky_chunks and m2.loop_tiles_tuning_ms == t
+    o = oracle.Oracle(spec)
+    L = m.loops(0.07).cpu().numpy()
+    for ch in (0, 1):
+        assert rel(L[ch], o.loops(0.07, ch)) < 2e-5
+    # the FP64 path keeps its heuristic shape
+    assert api.Model(spec, api.FP64).loop_tiles_tuning_ms == {}
+
+
 def test_flow_batch_mixed_spin_orbitals():
     """A batch that mixes two-band (N_s = 2) and bilayer (N_s = 4) instances, with different meshes and bond sets,
     gives exactly the flows tufrg_flow gives one at a time, in both precisions."""
