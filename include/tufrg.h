@@ -398,6 +398,46 @@ tufrg_status tufrg_loops_noalloc(int Lq, int nc, const double *d_E, const double
  * is the wall time of the whole batch.  Returns the first error status (all results are filled). */
 tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *opts, tufrg_flow_result *results);
 
+/* The flow of tufrg_flow driven step by step from the host, with checkpoints (the integration of Sec. 3.1 in the
+ * flow variable ln T; the steps, the controller and the results are those of tufrg_flow).
+ *
+ * tufrg_flow_start: zeroes the state, evaluates k1 = f(y0) and captures one Dormand-Prince attempt, as tufrg_flow
+ *   does before its first attempt; no attempt runs.  The model's work then runs on its private flow stream, ordered
+ *   after the caller's stream, until tufrg_flow_end orders the caller's stream after it.  tufrg_flow and
+ *   tufrg_flow_batch refuse a model with an open stepwise flow.
+ * tufrg_flow_step: replays one attempt (nothing once the flow has stopped) and fills *info with the controller
+ *   after it: T = exp(x) of the current accepted state, the next step h in ln T, the attempt's error norm, max |A|
+ *   of the current state, the accepted-step and rejection counts, accepted (1 if this attempt was accepted) and
+ *   status (0 running, 1 max |A| crossed the stop value, 2 reached T_end, 3 step limit, 4 non-finite, 5 step
+ *   underflow).
+ * tufrg_flow_amax_channels: h_amax[0], h_amax[1] = max |A_P|, max |A_C| over the projections of the last
+ *   evaluated stage (after an accepted attempt: of the accepted state).
+ * tufrg_flow_end: the tufrg_flow_result of what has run (wall_s from tufrg_flow_start or tufrg_flow_resume), the
+ *   state to d_state_out (device, [2][Nq][M][M] complex FP64, may be NULL); closes the stepwise flow.  Returns the
+ *   status tufrg_flow would return.
+ * tufrg_flow_checkpoint_bytes: size of a checkpoint of this model (0 for NULL).
+ * tufrg_flow_save: writes the open flow's checkpoint to the host buffer h_buf (caller-owned, at least
+ *   tufrg_flow_checkpoint_bytes): a header (library version, model shape, channel mask, the products backend and
+ *   loop launch shape in use), the device controller, the state y and k1 = f(y), FP64.
+ * tufrg_flow_resume: opens a stepwise flow from a checkpoint of a model of the same shape and channel mask,
+ *   restoring the controller, y and k1, and the checkpointed run's products backend and loop launch shape (they
+ *   fix the summation order): the steps that follow are bit for bit those of the uninterrupted run.  opts gives
+ *   the channel mask (the controller's scale range, tolerances and stop value come from the checkpoint).
+ * Errors: TUFRG_EINVAL (NULL arguments, bad options, a second open flow, no open flow, a short buffer, a
+ * checkpoint of another model, mask or library version), TUFRG_ENOTSUP (checkpoints of a model with a loop
+ * surrogate), TUFRG_ETIMEOUT (a bounded device wait gave up), TUFRG_ECUDA, and tufrg_flow_end's flow statuses. */
+typedef struct {
+    double T, h, err, amax;
+    int n_steps, n_reject, accepted, status;
+} tufrg_flow_step_info;
+tufrg_status tufrg_flow_start(tufrg_model *m, const tufrg_flow_opts *opts);
+tufrg_status tufrg_flow_step(tufrg_model *m, tufrg_flow_step_info *info);
+tufrg_status tufrg_flow_amax_channels(tufrg_model *m, double *h_amax);
+tufrg_status tufrg_flow_end(tufrg_model *m, void *d_state_out, tufrg_flow_result *result);
+size_t tufrg_flow_checkpoint_bytes(const tufrg_model *m);
+tufrg_status tufrg_flow_save(tufrg_model *m, void *h_buf, size_t bytes);
+tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *opts, const void *h_buf, size_t bytes);
+
 /* ------------------------------------------------------------------------------------------
  * Learned loop surrogate (an addition with no counterpart in the paper).
  * A multilayer perceptron n_in -> [width, GELU] x depth -> n_out with BF16 weights, FP32

@@ -46,6 +46,11 @@ class FlowResult(C.Structure):
                 ("lead_q", C.c_int), ("wall_s", C.c_double)]
 
 
+class FlowStepInfo(C.Structure):
+    _fields_ = [("T", C.c_double), ("h", C.c_double), ("err", C.c_double), ("amax", C.c_double),
+                ("n_steps", C.c_int), ("n_reject", C.c_int), ("accepted", C.c_int), ("status", C.c_int)]
+
+
 class TufrgError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -111,6 +116,17 @@ def lib():
             L.tufrg_loops_noalloc.restype = C.c_int
             L.tufrg_flow_batch.argtypes = [vp, i, C.POINTER(FlowOpts), vp]
             L.tufrg_flow_batch.restype = C.c_int
+            L.tufrg_flow_start.argtypes = [vp, C.POINTER(FlowOpts)]
+            L.tufrg_flow_step.argtypes = [vp, C.POINTER(FlowStepInfo)]
+            L.tufrg_flow_amax_channels.argtypes = [vp, vp]
+            L.tufrg_flow_end.argtypes = [vp, vp, C.POINTER(FlowResult)]
+            L.tufrg_flow_checkpoint_bytes.argtypes = [vp]
+            L.tufrg_flow_checkpoint_bytes.restype = C.c_size_t
+            L.tufrg_flow_save.argtypes = [vp, vp, C.c_size_t]
+            L.tufrg_flow_resume.argtypes = [vp, C.POINTER(FlowOpts), vp, C.c_size_t]
+            for fn in ("tufrg_flow_start", "tufrg_flow_step", "tufrg_flow_amax_channels", "tufrg_flow_end",
+                       "tufrg_flow_save", "tufrg_flow_resume"):
+                getattr(L, fn).restype = C.c_int
             L.tufrg_mlp_create.argtypes = [i, i, i, i, C.c_ulonglong, vp, C.POINTER(vp)]
             L.tufrg_mlp_free.argtypes = [vp]
             L.tufrg_mlp_free.restype = None
@@ -152,4 +168,5 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info", "tufrg_loop_tiles",
            "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish", "tufrg_form_factors",
-           "tufrg_irrep_basis")
+           "tufrg_irrep_basis", "tufrg_flow_start", "tufrg_flow_step", "tufrg_flow_amax_channels", "tufrg_flow_end",
+           "tufrg_flow_checkpoint_bytes", "tufrg_flow_save", "tufrg_flow_resume")

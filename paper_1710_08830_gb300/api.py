@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import (BASIS_BAND, BASIS_ORBITAL, CH_C, CH_P, FP64, LOOPS_AUTO, LOOPS_SIMT, LOOPS_TC, PRODUCTS_AUTO, PRODUCTS_SIMT, PRODUCTS_TC, SPLIT32, SYMMETRIC_STATE, SYMMETRY_AUTO,
                    SYMMETRY_OFF, SYMMETRY_STATES,
-                   FlowOpts, FlowResult, ModelDesc, TufrgError)
+                   FlowOpts, FlowResult, FlowStepInfo, ModelDesc, TufrgError)
 from .inputs import FLOW_ATOL, FLOW_RTOL, FLOW_STOP, FLOW_T0, FLOW_T_END, ModelSpec
 
 __all__ = ["Model", "flow_batch", "FP64", "SPLIT32", "PRODUCTS_AUTO", "PRODUCTS_TC", "PRODUCTS_SIMT", "SYMMETRY_AUTO",
@@ -270,13 +270,56 @@ class Model:
 
     def flow(self, T0: float = FLOW_T0, T_end: float = FLOW_T_END, rtol: float = FLOW_RTOL, atol: float = FLOW_ATOL,
              h0: float = -0.05, stop: float = FLOW_STOP, mask: int = CH_P | CH_C, max_steps: int = 100000,
-             want_state: bool = True):
+             want_state: bool = True, metrics_path: Optional[str] = None, checkpoint_path: Optional[str] = None,
+             checkpoint_every: int = 0, resume_from: Optional[str] = None, stop_after: int = 0):
+        """The adaptive flow (tufrg_flow).  With metrics_path, checkpoint_path or resume_from it runs step by step
+        (tufrg_flow_start / tufrg_flow_resume, tufrg_flow_step, tufrg_flow_end): one JSON line per accepted step
+        to metrics_path (T, h, err, max|A| per channel, counts), the checkpoint written to checkpoint_path every
+        checkpoint_every accepted steps (replacing the previous one), the flow continued from the checkpoint file
+        resume_from.  stop_after > 0 ends the run after that many accepted steps of this call (the result is then
+        that of an unfinished flow; resume from its checkpoint to continue)."""
         o = FlowOpts(T0, T_end, rtol, atol, h0, stop, int(mask), int(max_steps))
         r = FlowResult()
         st_out = self.zeros_state() if want_state else None
-        self._check(self._L.tufrg_flow(self._h, C.byref(o), _ptr(st_out) if want_state else None, C.byref(r)))
-        res = {f: getattr(r, f) for f, _ in FlowResult._fields_}
-        return st_out, res
+        if not (metrics_path or checkpoint_path or resume_from):
+            self._check(self._L.tufrg_flow(self._h, C.byref(o), _ptr(st_out) if want_state else None, C.byref(r)))
+            return st_out, {f: getattr(r, f) for f, _ in FlowResult._fields_}
+        import json
+        import os
+        nbytes = self._L.tufrg_flow_checkpoint_bytes(self._h)
+        buf = np.empty(nbytes, np.uint8)
+        if resume_from:
+            data = np.fromfile(resume_from, np.uint8)
+            self._check(self._L.tufrg_flow_resume(self._h, C.byref(o), data.ctypes.data, data.size))
+        else:
+            self._check(self._L.tufrg_flow_start(self._h, C.byref(o)))
+        info, amax2 = FlowStepInfo(), np.zeros(2)
+        metrics = open(metrics_path, "a") if metrics_path else None
+        try:
+            done = 0
+            while True:
+                self._check(self._L.tufrg_flow_step(self._h, C.byref(info)))
+                if info.accepted:
+                    done += 1
+                    if metrics:
+                        self._check(self._L.tufrg_flow_amax_channels(self._h, amax2.ctypes.data))
+                        metrics.write(json.dumps({"step": info.n_steps, "T": info.T, "h": info.h, "err": info.err,
+                                                  "amax": info.amax, "amax_P": float(amax2[0]),
+                                                  "amax_C": float(amax2[1]), "n_reject": info.n_reject,
+                                                  "status": info.status}) + "\n")
+                    if checkpoint_path and checkpoint_every > 0 and info.n_steps % checkpoint_every == 0:
+                        self._check(self._L.tufrg_flow_save(self._h, buf.ctypes.data, nbytes))
+                        tmp = checkpoint_path + ".tmp"
+                        buf.tofile(tmp)
+                        os.replace(tmp, checkpoint_path)
+                if info.status != 0 or (stop_after > 0 and done >= stop_after):
+                    break
+        finally:
+            if metrics:
+                metrics.close()
+            st = self._L.tufrg_flow_end(self._h, _ptr(st_out) if want_state else None, C.byref(r))
+        self._check(st)
+        return st_out, {f: getattr(r, f) for f, _ in FlowResult._fields_}
 
 
 def flow_batch(models, T0: float = FLOW_T0, T_end: float = FLOW_T_END, rtol: float = FLOW_RTOL,

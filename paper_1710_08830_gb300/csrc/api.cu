@@ -495,7 +495,7 @@ void release(tufrg_model *m)
                     m->d_loop_list, m->d_qmap, m->d_sym_elem, m->d_sym_dinv, m->d_lph32,
                     m->d_clsph32, m->d_v0d32[0], m->d_v0d32[1], m->d_sym_srow, m->d_sym_qrow, m->d_sym_sinv, m->d_orb_ofs, m->d_orb_q, m->d_sym_emap, m->d_orb_lexp, m->d_band_tc,
                     m->d_dft_tabs, m->d_dft_phy, m->d_dft_phx, m->d_dft_phy32, m->d_dft_phx32, m->d_loop_w,
-                    m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32, m->d_ffW};
+                    m->d_shard_q, m->d_shard_out, m->d_v0q, m->d_v0q32, m->d_ffW, m->d_amax_ch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &p : m->d_k)
@@ -586,8 +586,8 @@ tufrg_status enqueue_attempt(tufrg_model *m, int mask)
     return TUFRG_OK;
 }
 
-// Allocate the flow buffers, zero the state, evaluate k1 = f(y0) and capture one attempt as a graph.
-tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
+// The flow's buffers: state, candidate, stage derivatives, device controller and its pinned host mirror.
+tufrg_status flow_alloc(tufrg_model *m)
 {
     const size_t n = state_elems(m);
     if (!m->d_y) {
@@ -598,6 +598,46 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
         CK(dalloc(&m->d_flow, 1), "cudaMalloc flow state");
         CK(cudaMallocHost(reinterpret_cast<void **>(&m->h_flow), sizeof(FlowDev)), "cudaMallocHost flow state");
     }
+    return TUFRG_OK;
+}
+
+// Capture one Dormand-Prince attempt of the given channel mask as the model's step graph (kept while the mask and
+// the launch shapes stay the same).
+tufrg_status flow_capture(tufrg_model *m, int mask)
+{
+    if (m->step_graph && m->step_graph_mask == mask) return TUFRG_OK;
+    if (m->step_graph) {
+        cudaGraphExecDestroy(m->step_graph);
+        m->step_graph = nullptr;
+    }
+    const bool timing = m->timing;
+    m->timing = false;   // no event records inside the captured graph
+    const long long l0 = m->launches, ll0 = m->loop_launches;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    tufrg_status st = enqueue_attempt(m, mask);
+    cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+    m->timing = timing;
+    m->launches = l0;
+    m->loop_launches = ll0;
+    if (st != TUFRG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return cuda_fail(m, ce, "end capture");
+    ce = cudaGraphInstantiate(&m->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(m, ce, "graph instantiate");
+    m->step_graph_mask = mask;
+    return TUFRG_OK;
+}
+
+// Allocate the flow buffers, zero the state, evaluate k1 = f(y0) and capture one attempt as a graph.
+tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
+{
+    const size_t n = state_elems(m);
+    tufrg_status st = flow_alloc(m);
+    if (st != TUFRG_OK) return st;
     FlowDev f{};
     f.x = std::log(o->T0);
     f.xend = std::log(o->T_end);
@@ -615,34 +655,10 @@ tufrg_status flow_prepare(tufrg_model *m, const tufrg_flow_opts *o)
     CK(surrogate_rearm(m), "re-arm surrogate");
     // k1 = f(x0, y0) and max|A| of the initial state
     CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
-    tufrg_status st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0], nullptr, true);
+    st = rhs_device(m, m->d_y, o->channel_mask, m->d_k[0], nullptr, true);
     if (st != TUFRG_OK) return st;
     CK(launch_flow_init(m, m->d_flow), "flow init");
-    if (!m->step_graph || m->step_graph_mask != o->channel_mask) {
-        if (m->step_graph) {
-            cudaGraphExecDestroy(m->step_graph);
-            m->step_graph = nullptr;
-        }
-        const bool timing = m->timing;
-        m->timing = false;   // no event records inside the captured graph
-        const long long l0 = m->launches, ll0 = m->loop_launches;
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        st = enqueue_attempt(m, o->channel_mask);
-        cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
-        m->timing = timing;
-        m->launches = l0;
-        m->loop_launches = ll0;
-        if (st != TUFRG_OK) {
-            if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (ce != cudaSuccess) return cuda_fail(m, ce, "end capture");
-        ce = cudaGraphInstantiate(&m->step_graph, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) return cuda_fail(m, ce, "graph instantiate");
-        m->step_graph_mask = o->channel_mask;
-    }
+    if ((st = flow_capture(m, o->channel_mask)) != TUFRG_OK) return st;
     // the controller state after the initial evaluation: a flow whose initial max|A| already exceeds the stop
     // value is critical at T0 and runs no attempt
     CK(cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream), "copy flow state");
@@ -713,6 +729,46 @@ tufrg_status flow_finish(tufrg_model *m, void *d_state_out, tufrg_flow_result *r
     case 5: return fail(m, TUFRG_ENOTCONV, "step size underflow");
     default: return TUFRG_OK;
     }
+}
+
+// Checkpoint layout: this header, the device controller (FlowDev), the state y and its derivative k1 = f(y) (the
+// first stage of the next attempt), both [2][Nq][M][M] complex FP64.
+struct CkptHeader {
+    char magic[8];          // "TUFRGCK1"
+    int version, flowdev_bytes;
+    int precision, ns, nff, Lq, nc, M, channel_mask, basis, regulator, loops_tc;
+    int products, ky_chunks;   // launch shapes in use (they fix the summation order)
+    long long n_elems;
+};
+
+CkptHeader ckpt_header(const tufrg_model *m, int mask)
+{
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "TUFRGCK1", 8);
+    h.version = 1;
+    h.flowdev_bytes = (int)sizeof(FlowDev);
+    h.precision = m->precision;
+    h.ns = m->ns;
+    h.nff = m->nff;
+    h.Lq = m->Lq;
+    h.nc = m->nc;
+    h.M = m->M;
+    h.channel_mask = mask;
+    h.basis = m->basis;
+    h.regulator = m->regulator;
+    h.loops_tc = m->loops_tc ? 1 : 0;
+    h.products = m->products;
+    h.ky_chunks = m->plan.ky_chunks;
+    h.n_elems = (long long)state_elems(m);
+    return h;
+}
+
+double bits_to_double(unsigned long long b)
+{
+    double d;
+    std::memcpy(&d, &b, sizeof(d));
+    return d;
 }
 
 tufrg_status read_device_error(tufrg_model *m)
@@ -1548,6 +1604,7 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_
 {
     tufrg_status st = flow_check_args(m, o, res);
     if (st != TUFRG_OK) return st;
+    if (m->flow_open) return fail(m, TUFRG_EINVAL, "a stepwise flow is open on this model");
     const auto t_start = std::chrono::steady_clock::now();
     std::memset(res, 0, sizeof(*res));
     cudaStream_t user;
@@ -1568,6 +1625,171 @@ tufrg_status tufrg_flow(tufrg_model *m, const tufrg_flow_opts *o, void *d_state_
     return st != TUFRG_OK ? st : st2;
 }
 
+// ---- the flow step by step, with checkpoints
+
+tufrg_status tufrg_flow_start(tufrg_model *m, const tufrg_flow_opts *o)
+{
+    tufrg_flow_result unused{};
+    tufrg_status st = flow_check_args(m, o, &unused);
+    if (st != TUFRG_OK) return st;
+    if (m->flow_open) return fail(m, TUFRG_EINVAL, "a stepwise flow is already open on this model");
+    cudaStream_t user;
+    if ((st = flow_enter(m, &user)) != TUFRG_OK) return st;
+    st = flow_prepare(m, o);
+    if (st != TUFRG_OK) {
+        flow_leave(m, user);
+        return st;
+    }
+    m->flow_open = true;
+    m->flow_user = user;
+    m->flow_mask = o->channel_mask;
+    m->flow_t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_flow_step(tufrg_model *m, tufrg_flow_step_info *s)
+{
+    if (!m || !s) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!m->flow_open) return fail(m, TUFRG_EINVAL, "no stepwise flow is open on this model");
+    if (m->h_flow->status == 0) {
+        cudaError_t e = cudaGraphLaunch(m->step_graph, m->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_flow, m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(m, e, "flow graph");
+    }
+    const FlowDev &f = *m->h_flow;
+    s->T = std::exp(f.x);
+    s->h = f.h;
+    s->err = f.err;
+    s->amax = f.amax;
+    s->n_steps = f.n_steps;
+    s->n_reject = f.n_reject;
+    s->accepted = f.accepted;
+    s->status = f.status;
+    return read_device_error(m);
+}
+
+tufrg_status tufrg_flow_amax_channels(tufrg_model *m, double *h_amax)
+{
+    if (!m || !h_amax) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!m->d_amax_ch) CK(cudaMalloc(reinterpret_cast<void **>(&m->d_amax_ch), 2 * sizeof(unsigned long long)), "cudaMalloc");
+    CK(launch_amax_channels(m, m->sym_state), "max |A| per channel");
+    unsigned long long b[2];
+    CK(cudaMemcpyAsync(b, m->d_amax_ch, sizeof(b), cudaMemcpyDeviceToHost, m->stream), "copy maxima");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    for (int c = 0; c < 2; c++) h_amax[c] = bits_to_double(b[c]);
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_flow_end(tufrg_model *m, void *d_state_out, tufrg_flow_result *res)
+{
+    if (!m || !res) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!m->flow_open) return fail(m, TUFRG_EINVAL, "no stepwise flow is open on this model");
+    std::memset(res, 0, sizeof(*res));
+    tufrg_status st = read_device_error(m);
+    if (st == TUFRG_OK) st = flow_finish(m, d_state_out, res);
+    const tufrg_status st2 = flow_leave(m, m->flow_user);
+    m->flow_open = false;
+    res->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - m->flow_t0;
+    return st != TUFRG_OK ? st : st2;
+}
+
+size_t tufrg_flow_checkpoint_bytes(const tufrg_model *m)
+{
+    if (!m) return 0;
+    return sizeof(CkptHeader) + sizeof(FlowDev) + 2 * sizeof(double2) * state_elems(m);
+}
+
+tufrg_status tufrg_flow_save(tufrg_model *m, void *h_buf, size_t bytes)
+{
+    if (!m || !h_buf) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (!m->flow_open) return fail(m, TUFRG_EINVAL, "no stepwise flow is open on this model");
+    if (m->sur) return fail(m, TUFRG_ENOTSUP, "checkpoints of flows with a loop surrogate are not supported");
+    if (bytes < tufrg_flow_checkpoint_bytes(m)) return fail(m, TUFRG_EINVAL, "checkpoint buffer too small");
+    const size_t n = state_elems(m);
+    CkptHeader h = ckpt_header(m, m->flow_mask);
+    unsigned char *p = static_cast<unsigned char *>(h_buf);
+    std::memcpy(p, &h, sizeof(h));
+    CK(cudaMemcpyAsync(p + sizeof(h), m->d_flow, sizeof(FlowDev), cudaMemcpyDeviceToHost, m->stream), "copy controller");
+    CK(cudaMemcpyAsync(p + sizeof(h) + sizeof(FlowDev), m->d_y, sizeof(double2) * n, cudaMemcpyDeviceToHost, m->stream),
+       "copy state");
+    CK(cudaMemcpyAsync(p + sizeof(h) + sizeof(FlowDev) + sizeof(double2) * n, m->d_k[0], sizeof(double2) * n,
+                       cudaMemcpyDeviceToHost, m->stream), "copy derivative");
+    CK(cudaStreamSynchronize(m->stream), "sync");
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *o, const void *h_buf, size_t bytes)
+{
+    tufrg_flow_result unused{};
+    tufrg_status st = flow_check_args(m, o, &unused);
+    if (st != TUFRG_OK) return st;
+    if (!h_buf) return fail(m, TUFRG_EINVAL, "NULL argument");
+    if (m->flow_open) return fail(m, TUFRG_EINVAL, "a stepwise flow is already open on this model");
+    if (m->sur) return fail(m, TUFRG_ENOTSUP, "checkpoints of flows with a loop surrogate are not supported");
+    if (bytes < tufrg_flow_checkpoint_bytes(m)) return fail(m, TUFRG_EINVAL, "checkpoint buffer too small");
+    CkptHeader h;
+    std::memcpy(&h, h_buf, sizeof(h));
+    const CkptHeader want = ckpt_header(m, o->channel_mask);
+    if (std::memcmp(h.magic, want.magic, sizeof(h.magic)) != 0 || h.version != want.version ||
+        h.flowdev_bytes != want.flowdev_bytes)
+        return fail(m, TUFRG_EINVAL, "not a checkpoint of this library version");
+    if (h.precision != want.precision || h.ns != want.ns || h.nff != want.nff || h.Lq != want.Lq || h.nc != want.nc ||
+        h.M != want.M || h.n_elems != want.n_elems || h.channel_mask != want.channel_mask || h.basis != want.basis ||
+        h.regulator != want.regulator || h.loops_tc != want.loops_tc)
+        return fail(m, TUFRG_EINVAL, "the checkpoint belongs to another model or channel mask");
+    // the launch shapes the checkpointed run used (they fix the summation order), then a fresh capture if needed
+    bool reshaped = false;
+    if (h.products != m->products) {
+        if (m->precision == TUFRG_FP64 || (h.products != TUFRG_PRODUCTS_TC && h.products != TUFRG_PRODUCTS_SIMT))
+            return fail(m, TUFRG_EINVAL, "the checkpoint's products backend does not apply to this model");
+        m->products = h.products;
+        reshaped = true;
+    }
+    if (h.ky_chunks != m->plan.ky_chunks) {
+        if (h.ky_chunks < 1 || h.ky_chunks > (int)m->plan_cand.size())
+            return fail(m, TUFRG_EINVAL, "the checkpoint's loop launch shape does not apply to this model");
+        m->plan = m->plan_cand[h.ky_chunks - 1];
+        reshaped = true;
+    }
+    if (reshaped && m->step_graph) {
+        cudaGraphExecDestroy(m->step_graph);
+        m->step_graph = nullptr;
+    }
+    const size_t n = state_elems(m);
+    const unsigned char *p = static_cast<const unsigned char *>(h_buf);
+    cudaStream_t user;
+    if ((st = flow_enter(m, &user)) != TUFRG_OK) return st;
+    auto run = [&]() -> tufrg_status {
+        tufrg_status s2 = flow_alloc(m);
+        if (s2 != TUFRG_OK) return s2;
+        std::memcpy(m->h_flow, p + sizeof(h), sizeof(FlowDev));
+        CK(cudaMemcpyAsync(m->d_flow, m->h_flow, sizeof(FlowDev), cudaMemcpyHostToDevice, m->stream), "copy controller");
+        CK(cudaMemcpyAsync(m->d_y, p + sizeof(h) + sizeof(FlowDev), sizeof(double2) * n, cudaMemcpyHostToDevice, m->stream),
+           "copy state");
+        // the projections of the restored state (the final report locates max |A| in them); the derivative goes to
+        // a stage buffer that the next attempt overwrites, k1 itself comes from the checkpoint
+        CK(launch_stage_scalars(m, m->d_flow, 0.0), "stage temperature");
+        s2 = rhs_device(m, m->d_y, o->channel_mask, m->d_k[1], nullptr, true);
+        if (s2 != TUFRG_OK) return s2;
+        CK(cudaMemcpyAsync(m->d_k[0], p + sizeof(h) + sizeof(FlowDev) + sizeof(double2) * n, sizeof(double2) * n,
+                           cudaMemcpyHostToDevice, m->stream), "copy derivative");
+        if ((s2 = flow_capture(m, o->channel_mask)) != TUFRG_OK) return s2;
+        CK(cudaStreamSynchronize(m->stream), "sync");
+        return TUFRG_OK;
+    };
+    st = run();
+    if (st != TUFRG_OK) {
+        flow_leave(m, user);
+        return st;
+    }
+    m->flow_open = true;
+    m->flow_user = user;
+    m->flow_mask = o->channel_mask;
+    m->flow_t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    return TUFRG_OK;
+}
+
 tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *o, tufrg_flow_result *res)
 {
     if (!models || n < 1 || !o || !res) return TUFRG_EINVAL;
@@ -1577,6 +1799,7 @@ tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flo
             if (models[j] == models[i]) return fail(models[i], TUFRG_EINVAL, "a model appears twice in the batch");
         tufrg_status st = flow_check_args(models[i], o, &res[i]);
         if (st != TUFRG_OK) return st;
+        if (models[i]->flow_open) return fail(models[i], TUFRG_EINVAL, "a stepwise flow is open on this model");
     }
     const auto t_start = std::chrono::steady_clock::now();
     std::vector<char> active(n, 1);

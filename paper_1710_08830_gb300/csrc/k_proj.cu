@@ -338,6 +338,35 @@ __global__ void amax_locate_kernel(const C2 *A, size_t n, const unsigned long lo
     if ((unsigned long long)__double_as_longlong(mag_of(abs2(A[i]))) == *amax) atomicMin(where, (unsigned long long)i);
 }
 
+// max |A| per channel (out[0] = P, out[1] = C, bit patterns of the non-negative magnitudes, atomicMax), the
+// magnitude formed as in the projection; grid-stride, one atomic per warp and channel run
+template <typename C2>
+__global__ void __launch_bounds__(256) amax_channels_kernel(const C2 *A, size_t n, unsigned long long *out,
+                                                            const int2 *qmap, const int *list, size_t M2, int Nq)
+{
+    const size_t per_ch = M2 * (size_t)Nq;
+    unsigned long long best[2] = {0ull, 0ull};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (qmap) {
+            const int q = (int)((i / M2) % (size_t)Nq);
+            if (list[qmap[q].x] != q) continue;
+        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(mag_of(abs2(A[i])));
+        const int ch = i < per_ch ? 0 : 1;
+        best[ch] = b > best[ch] ? b : best[ch];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 2; ch++) {
+        unsigned long long v = best[ch];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(out + ch, v);
+    }
+}
+
 template <typename R, typename XT, int CPT>
 cudaError_t dft_run(tufrg_model *m, const XT *d_state, const XT *clsph, int ch_lo, int nch, typename cpx<R>::t *part,
                     typename cpx<R>::t *Xr)
@@ -494,6 +523,20 @@ cudaError_t launch_project_local(tufrg_model *m, const double2 *d_state_local, c
                                                qlist, nlist, d_A, nullptr, 1, m->d_v0q);
     return project_run<float, float2, 2>(m, d_state32_local, m->d_Xr32, m->d_v0d32[0], m->d_v0d32[1], m->d_ph32,
                                          channel_mask, qlist, nlist, d_A, m->d_A32, 1, m->d_v0q32);
+}
+
+cudaError_t launch_amax_channels(tufrg_model *m, bool reps_only)
+{
+    TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax_ch, 0, 2 * sizeof(unsigned long long), m->stream));
+    m->launches++;
+    const size_t n = 2 * (size_t)m->Nq * m->M * m->M, M2 = (size_t)m->M * m->M;
+    const int2 *qm = reps_only ? m->d_qmap : nullptr;
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)m->sm_count * 8);
+    if (m->precision == TUFRG_FP64)
+        amax_channels_kernel<<<grid, 256, 0, m->stream>>>(m->d_A, n, m->d_amax_ch, qm, m->d_loop_list, M2, m->Nq);
+    else
+        amax_channels_kernel<<<grid, 256, 0, m->stream>>>(m->d_A32, n, m->d_amax_ch, qm, m->d_loop_list, M2, m->Nq);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only)

@@ -301,6 +301,12 @@ struct tufrg_model {
     cudaGraphExec_t step_graph = nullptr;    // one captured Dormand-Prince attempt
     cudaStream_t flow_stream = nullptr;      // private capturable stream of the flow (joined to `stream` by events)
     cudaEvent_t flow_ev = nullptr;
+    // a flow driven step by step from the host (tufrg_flow_start .. tufrg_flow_end)
+    bool flow_open = false;
+    cudaStream_t flow_user = nullptr;        // the caller's stream, rejoined at the end
+    int flow_mask = 0;
+    double flow_t0 = 0.0;                    // host clock at the start (seconds)
+    unsigned long long *d_amax_ch = nullptr; // [2] max |A| per channel (bit patterns of non-negative doubles)
     int step_graph_mask = 0;
 
     tufrg::LoopPlan plan{};
@@ -373,6 +379,7 @@ cudaError_t launch_flow_init(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_decide(tufrg_model *m, FlowDev *fs);
 cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, const double2 *yn, double2 *k0,
                                const double2 *k6, size_t n);
+cudaError_t launch_amax_channels(tufrg_model *m, bool reps_only);
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
 // the launch shapes the two-band split loop kernel's autotuner times (ky ranges per column)

@@ -68,6 +68,9 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
         "tufrg_timing_begin": (None,), "tufrg_timing_end": (None, None, 0, None, None),
         "tufrg_set_device_error": (None, 1), "tufrg_loops_info": (None, ctypes.byref(i)),
         "tufrg_loop_tiles": (None, ctypes.byref(i), ctypes.byref(i), None, 0),
+        "tufrg_flow_start": (None, None), "tufrg_flow_step": (None, None), "tufrg_flow_amax_channels": (None, None),
+        "tufrg_flow_end": (None, None, None), "tufrg_flow_save": (None, None, 0),
+        "tufrg_flow_resume": (None, None, None, 0),
         "tufrg_shard_classes": (None, ctypes.byref(i), None), "tufrg_form_factors": (None, None, None),
         "tufrg_irrep_basis": (None, None, 0, None), "tufrg_rhs_shard_transform": (None, None, 1, None, 3, None),
         "tufrg_rhs_shard_finish": (None, 0.1, None, 1, None, None, 3, None),
@@ -79,6 +82,7 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     }
     for name, args in calls.items():
         assert getattr(L, name)(*args) == 1, name                # TUFRG_EINVAL
+    assert L.tufrg_flow_checkpoint_bytes(None) == 0
     assert L.tufrg_mlp_num_params(None) == -1
     assert L.tufrg_mlp_last_error(None) == b"network handle is NULL"
     L.tufrg_free(None)
