@@ -291,6 +291,12 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
  * every state of a flow from X = 0 has them when the bare vertex does), and projections and products then
  * run for the orbit representatives only, the other momenta being written from them.  For a state without
  * those symmetries the result is wrong; the flag is ignored when the model has no usable symmetry.
+ * The second call for a given (d_state, d_dstate, channel_mask) captures the evaluation's launches (after the
+ * temperature, which they read from device memory) in a CUDA graph that later calls with the same three replay;
+ * the four most recently used triples are kept.  Results are those of direct launches, bit for bit.  On the legacy
+ * default stream (not capturable) the graph runs on a private stream ordered after it and before its next work by
+ * events.  Calls launch directly while the caller captures the model's stream, while the phases are being timed
+ * (tufrg_timing_begin) and with a loop surrogate.
  * Errors: TUFRG_EINVAL (NULL argument, T not positive and finite, bad channel_mask), TUFRG_ECUDA. */
 enum { TUFRG_SYMMETRIC_STATE = 4 };
 tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate);

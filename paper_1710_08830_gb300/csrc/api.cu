@@ -484,6 +484,18 @@ std::vector<double2> phase_table(int Lq, const std::vector<int> &vecs)
     return t;
 }
 
+}  // namespace
+namespace tufrg {
+// the captured right-hand-side graphs are dropped whenever the launches they hold would change
+void drop_rhs_graphs(tufrg_model *m)
+{
+    for (auto &r : m->rhs_graphs)
+        if (r.exec) cudaGraphExecDestroy(r.exec);
+    m->rhs_graphs.clear();
+}
+}  // namespace tufrg
+namespace {
+
 void release(tufrg_model *m)
 {
     void *ptrs[] = {m->d_E, m->d_U, m->d_U32, m->d_ft, m->d_ft32, m->d_dslot, m->d_deltas, m->d_hopR, m->d_hopt,
@@ -505,6 +517,10 @@ void release(tufrg_model *m)
     tufrg_set_surrogate(m, nullptr, nullptr, nullptr, nullptr, 0.0, 0, nullptr);
     if (m->h_flow) cudaFreeHost(m->h_flow);
     if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
+    drop_rhs_graphs(m);
+    for (auto &e : m->rhs_ev)
+        if (e) cudaEventDestroy(e);
+    if (m->rhs_stream) cudaStreamDestroy(m->rhs_stream);
     if (m->flow_ev) cudaEventDestroy(m->flow_ev);
     if (m->flow_stream) cudaStreamDestroy(m->flow_stream);
     for (int b = 0; b < 2; b++) {
@@ -1435,8 +1451,86 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
         return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C, optionally with TUFRG_SYMMETRIC_STATE");
     CK(launch_set_scalars(m, T, 1.0), "set temperature");
     CK(surrogate_rearm(m), "re-arm surrogate");
-    return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask & 3, reinterpret_cast<double2 *>(d_dstate),
-                      nullptr, (channel_mask & TUFRG_SYMMETRIC_STATE) != 0);
+    auto direct = [&]() {
+        return rhs_device(m, reinterpret_cast<const double2 *>(d_state), channel_mask & 3,
+                          reinterpret_cast<double2 *>(d_dstate), nullptr, (channel_mask & TUFRG_SYMMETRIC_STATE) != 0);
+    };
+    // The launches after the temperature (which they read from device memory) are replayed from a captured graph:
+    // the same kernels in the same order without the gaps between launches.  Direct launches instead while the
+    // phases are being timed, with a loop surrogate, or when the caller is capturing the stream itself.  The legacy
+    // default stream cannot be captured: there the graph runs on a private stream joined to it by events.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (m->timing || m->sur || m->rhs_graph_off ||
+        (m->stream != nullptr && (cudaStreamIsCapturing(m->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)))
+        return direct();
+    tufrg_model::RhsGraph *g = nullptr;
+    for (auto &r : m->rhs_graphs)
+        if (r.in == d_state && r.out == d_dstate && r.mask == channel_mask) g = &r;
+    auto make_room = [&]() {   // the least recently used entry makes room (at most 4 kept)
+        if (m->rhs_graphs.size() < 4) return;
+        auto lru = m->rhs_graphs.begin();
+        for (auto it = m->rhs_graphs.begin(); it != m->rhs_graphs.end(); ++it)
+            if (it->used < lru->used) lru = it;
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        m->rhs_graphs.erase(lru);
+    };
+    if (!g) {
+        // first use of these buffers: launch directly and remember them (a one-off call costs no capture)
+        make_room();
+        m->rhs_graphs.push_back(tufrg_model::RhsGraph{d_state, d_dstate, channel_mask, nullptr, 0, 0, ++m->rhs_graph_clock});
+        return direct();
+    }
+    // on the legacy default stream: the private stream, ordered after it here and before it at the end
+    const cudaStream_t user = m->stream;
+    if (user == nullptr) {
+        if (!m->rhs_stream) {
+            CK(cudaStreamCreateWithFlags(&m->rhs_stream, cudaStreamNonBlocking), "create stream");
+            CK(cudaEventCreateWithFlags(&m->rhs_ev[0], cudaEventDisableTiming), "create event");
+            CK(cudaEventCreateWithFlags(&m->rhs_ev[1], cudaEventDisableTiming), "create event");
+        }
+        CK(cudaEventRecord(m->rhs_ev[0], user), "record");
+        CK(cudaStreamWaitEvent(m->rhs_stream, m->rhs_ev[0], 0), "wait");
+        m->stream = m->rhs_stream;
+    }
+    struct Rejoin {   // back to the caller's stream on every return
+        tufrg_model *m;
+        cudaStream_t user;
+        ~Rejoin()
+        {
+            if (user != nullptr || m->stream == nullptr) return;
+            cudaEventRecord(m->rhs_ev[1], m->stream);
+            cudaStreamWaitEvent(user, m->rhs_ev[1], 0);
+            m->stream = user;
+        }
+    } rejoin{m, user};
+    if (!g->exec) {
+        const long long l0 = m->launches, ll0 = m->loop_launches;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const tufrg_status st = direct();
+        const cudaError_t ce = cudaStreamEndCapture(m->stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = (st == TUFRG_OK && ce == cudaSuccess) ? cudaGraphInstantiate(&exec, graph, 0) : cudaErrorUnknown;
+        if (graph) cudaGraphDestroy(graph);
+        const long long dl = m->launches - l0, dll = m->loop_launches - ll0;
+        m->launches = l0;
+        m->loop_launches = ll0;
+        if (st != TUFRG_OK) return st;
+        if (ce != cudaSuccess || ie != cudaSuccess) {
+            // not capturable here: launch directly from now on
+            (void)cudaGetLastError();
+            m->rhs_graph_off = true;
+            return direct();
+        }
+        g->exec = exec;
+        g->launches = dl;
+        g->loop_launches = dll;
+    }
+    g->used = ++m->rhs_graph_clock;
+    CK(cudaGraphLaunch(g->exec, m->stream), "right-hand side graph");
+    m->launches += g->launches;
+    m->loop_launches += g->loop_launches;
+    return TUFRG_OK;
 }
 
 // ------------------------------------------------------------------ right-hand side over shards of momenta
@@ -1756,6 +1850,7 @@ tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *o, const v
         cudaGraphExecDestroy(m->step_graph);
         m->step_graph = nullptr;
     }
+    if (reshaped) drop_rhs_graphs(m);
     const size_t n = state_elems(m);
     const unsigned char *p = static_cast<const unsigned char *>(h_buf);
     cudaStream_t user;

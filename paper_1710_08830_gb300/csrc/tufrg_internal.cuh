@@ -301,6 +301,21 @@ struct tufrg_model {
     cudaGraphExec_t step_graph = nullptr;    // one captured Dormand-Prince attempt
     cudaStream_t flow_stream = nullptr;      // private capturable stream of the flow (joined to `stream` by events)
     cudaEvent_t flow_ev = nullptr;
+    // tufrg_rhs replays captured graphs of its launches, one per (input, output, mask) used more than once (the
+    // four most recently used triples kept; exec is null after the first use)
+    struct RhsGraph {
+        const void *in;
+        void *out;
+        int mask;
+        cudaGraphExec_t exec;
+        long long launches, loop_launches;   // kernels the graph holds (the launch counters advance by these)
+        unsigned long long used;
+    };
+    std::vector<RhsGraph> rhs_graphs;
+    unsigned long long rhs_graph_clock = 0;
+    bool rhs_graph_off = false;              // a capture failed once: launch directly from then on
+    cudaStream_t rhs_stream = nullptr;       // private stream of the graphs when the model's stream is the legacy one
+    cudaEvent_t rhs_ev[2] = {nullptr, nullptr};
     // a flow driven step by step from the host (tufrg_flow_start .. tufrg_flow_end)
     bool flow_open = false;
     cudaStream_t flow_user = nullptr;        // the caller's stream, rejoined at the end
@@ -382,6 +397,7 @@ cudaError_t launch_flow_commit(tufrg_model *m, const FlowDev *fs, double2 *y, co
 cudaError_t launch_amax_channels(tufrg_model *m, bool reps_only);
 cudaError_t launch_amax_locate(tufrg_model *m, size_t n, bool reps_only);   // on the last projection (d_A or d_A32)
 LoopPlan plan_loops(const tufrg_model *m);
+void drop_rhs_graphs(tufrg_model *m);
 // the launch shapes the two-band split loop kernel's autotuner times (ky ranges per column)
 std::vector<LoopPlan> loop_plan_candidates(const tufrg_model *m);
 int plan_gen_chunks(const tufrg_model *m);   // kx ranges per momentum of the multi-orbital loop kernel

@@ -8,6 +8,8 @@ Sizes span several CTAs and a ragged tail of the fine mesh (Lf = 24, 25, 30, 120
 degenerate bands of the SU(2) model, the complete 4x4 bond set and the full-size
 24x24 / 8x8 Rashba workload.
 """
+import contextlib
+
 import numpy as np
 import pytest
 
@@ -639,6 +641,35 @@ def test_flow_batch_matches_single_flows():
             assert r1["n_steps"] == r2["n_steps"] and r1["n_reject"] == r2["n_reject"]
             assert r1["crossed"] == r2["crossed"]
             assert r1["Tc"] == r2["Tc"]
+
+
+def test_rhs_graph_replay_matches_direct_launches():
+    """tufrg_rhs replays a captured graph per (input, output, mask); the results equal the direct launches (taken
+    while the phases are timed) bit for bit, for both precisions, both state flags, new buffers and more buffer
+    pairs than the graph cache holds, on the legacy default stream (graphs on a private stream) and on a stream of
+    the caller's."""
+    api = _api()
+    spec = CASES["rashba_ff9_Lf25"]()
+    for prec, stream in ((api.SPLIT32, None), (api.FP64, None), (api.SPLIT32, torch.cuda.Stream())):
+        with (torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()):
+            m = api.Model(spec, prec, stream=stream)
+            X1 = 0.05 * m.rhs(0.5, m.zeros_state())
+            for sym in (False, True):
+                for T in (0.4, 0.13):
+                    m.timing_begin()
+                    want = m.rhs(T, X1, symmetric=sym).clone()
+                    m.timing_end()
+                    outs = [m.zeros_state() for _ in range(6)]
+                    for rep in range(2):
+                        for o in outs:
+                            m.rhs(T, X1, out=o, symmetric=sym)
+                            assert torch.equal(o, want)
+            one = m.rhs(0.2, X1, mask=api.CH_P)
+            m.timing_begin()
+            ref = m.rhs(0.2, X1, mask=api.CH_P)
+            m.timing_end()
+            assert torch.equal(one, ref) and not torch.any(one[1])
+        torch.cuda.synchronize()
 
 
 def test_loop_tile_autotune():
