@@ -4,7 +4,7 @@
 // Two persistent launches per right-hand side, each over the work list (channel, momentum, 128-row tile, NB-column
 // tile) of every requested channel and momentum:
 //   first:   T = A L    with L[k][n] gathered from the compact loops through the bond-pair table, FP32 scratch;
-//   second:  dX = c T A in FP64 (exact widening on the integer pipe, widen_f).
+//   second:  dX = c T A in FP64 (exact widening on the integer pipe).
 // Complex GEMM as four real MMA streams into two tensor-memory accumulators:
 //   Cr += Ar Br - Ai Bi,   Ci += Ar Bi + Ai Br     (the minus by the descriptor's negate-A bit).
 // Precision: 3xTF32 - every FP32 operand x is split into hi = x with the 13 low mantissa bits cleared and lo = x - hi
@@ -142,6 +142,18 @@ __device__ __forceinline__ void load_stage(const Src &src, const int *sdij, int 
 #pragma unroll
         for (int j = 0; j < 4; j++) v.b[j] = make_float2(0.f, 0.f);
     }
+}
+
+// exact FP32 -> FP64 by the two formats' bit layouts with selects only (the library's widen_f also handles
+// subnormals, through a call that costs the epilogue's store loop its throughput); FP32 subnormals become signed
+// zeros here (products below 1.2e-38 in magnitude)
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x), e = (u >> 23) & 0xffu, sign = u & 0x80000000u;
+    const unsigned e64 = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = e == 0 ? sign : sign | (e64 << 20) | ((u & 0x7fffffu) >> 3);
+    const unsigned lo = e == 0 ? 0u : u << 29;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
@@ -367,8 +379,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) vlv_tc_kernel(VlvArgs p)
                     double2 *dst = p.out + ((size_t)ch * p.Nq + qs) * M2 + (size_t)(m0 + rr) * M + n0;
                     for (int cp = lane; cp < npair; cp += 32) {
                         const float4 v = src[cp];
-                        dst[2 * cp] = make_double2(widen_f(c * v.x), widen_f(c * v.y));
-                        dst[2 * cp + 1] = make_double2(widen_f(c * v.z), widen_f(c * v.w));
+                        dst[2 * cp] = make_double2(f32_to_f64(c * v.x), f32_to_f64(c * v.y));
+                        dst[2 * cp + 1] = make_double2(f32_to_f64(c * v.z), f32_to_f64(c * v.w));
                     }
                 }
             }

@@ -398,39 +398,46 @@ __global__ void __launch_bounds__(256) sym_scatter_kernel(double2 *out, int Nq, 
     }
 }
 
-// The same copy, orbit by orbit: one CTA per (representative, block of RB source rows, channel) reads its rows once
-// into shared memory and writes the target rows of every other member of the orbit, row r = sinv[i] of member q2
+// The same copy, orbit by orbit: one CTA per (representative, block of ORB_RB source rows, channel) reads its rows
+// once into shared memory and writes the target rows of every other member of the orbit, row r = sinv[i] of member q2
 // taking source row i: entry (r, c) = i^(qt[r] - qt[c]) (conjugated for antiunitary elements) times row i's entry
-// srow[c].  DRAM then sees each representative's matrix read once and every member's matrix written once, coalesced.
+// srow[c].  Warp w writes the target row of source row i0 + w, its lanes on consecutive columns (coalesced); the
+// member's column maps are staged in shared memory.  DRAM then sees each representative's matrix read once and every
+// member's matrix written once.
 constexpr int ORB_RB = 8;
-__global__ void __launch_bounds__(256) sym_orbit_copy_kernel(double2 *out, int Nq, int M, const int2 *qmap, const int *list,
-                                                             const int *orb_ofs, const int *orb_q, const SymElem *elem,
-                                                             const int *srow, const int *sinv, const int *qrow)
+__global__ void __launch_bounds__(32 * ORB_RB) sym_orbit_copy_kernel(double2 *out, int Nq, int M, const int2 *qmap,
+                                                                     const int *list, const int *orb_ofs, const int *orb_q,
+                                                                     const SymElem *elem, const int *srow, const int *sinv,
+                                                                     const int *qrow)
 {
-    extern __shared__ double2 s_rows[];   // [ORB_RB][M]
+    extern __shared__ double2 s_rows[];   // [ORB_RB][M] source rows, then [M] column sources, [M] quarter turns
+    int *s_sr = reinterpret_cast<int *>(s_rows + (size_t)ORB_RB * M), *s_qr = s_sr + M;
     const int p = blockIdx.x, i0 = blockIdx.y * ORB_RB, ch = blockIdx.z;
-    const int q = list[p], nr = min(ORB_RB, M - i0);
+    const int q = list[p], nr = min(ORB_RB, M - i0), w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t M2 = (size_t)M * M;
     const double2 *src = out + ((size_t)ch * Nq + q) * M2 + (size_t)i0 * M;
     for (int t = threadIdx.x; t < nr * M; t += blockDim.x) s_rows[t] = src[t];
-    __syncthreads();
     const long long sg = (long long)0x8000000000000000ull;
     for (int mi = orb_ofs[p]; mi < orb_ofs[p + 1]; mi++) {
         const int q2 = orb_q[mi];
         if (q2 == q) continue;
         const int e = qmap[q2].y;
         const bool conj = elem[e].conj;
-        const int *sr = srow + ((size_t)e * 2 + ch) * M, *si = sinv + ((size_t)e * 2 + ch) * M, *qr = qrow + ((size_t)e * 2 + ch) * M;
-        double2 *dst = out + ((size_t)ch * Nq + q2) * M2;
-        for (int ii = 0; ii < nr; ii++) {
-            const int r = si[i0 + ii], qrr = qr[r];
-            const double2 *row = s_rows + (size_t)ii * M;
-            double2 *d = dst + (size_t)r * M;
-            for (int c = threadIdx.x; c < M; c += blockDim.x) {
-                double2 v = row[sr[c]];
-                if (conj) v.y = __longlong_as_double(__double_as_longlong(v.y) ^ sg);
-                d[c] = times_i_pow(v, qrr - qr[c]);
-            }
+        const size_t tab = ((size_t)e * 2 + ch) * M;
+        __syncthreads();   // the previous member's maps are no longer read (and the rows have landed)
+        for (int c = threadIdx.x; c < M; c += blockDim.x) {
+            s_sr[c] = srow[tab + c];
+            s_qr[c] = qrow[tab + c];
+        }
+        __syncthreads();
+        if (w >= nr) continue;
+        const int r = sinv[tab + i0 + w], qrr = s_qr[r];
+        const double2 *row = s_rows + (size_t)w * M;
+        double2 *d = out + ((size_t)ch * Nq + q2) * M2 + (size_t)r * M;
+        for (int c = lane; c < M; c += 32) {
+            double2 v = row[s_sr[c]];
+            if (conj) v.y = __longlong_as_double(__double_as_longlong(v.y) ^ sg);
+            d[c] = times_i_pow(v, qrr - s_qr[c]);
         }
     }
 }
@@ -440,10 +447,10 @@ cudaError_t launch_sym_scatter(tufrg_model *m, double2 *d_out)
     PhaseScope ps(m, PH_SCATTER);
     const int threads = 256;
     if (m->d_sym_sinv && m->d_orb_ofs) {
-        const size_t smem = sizeof(double2) * ORB_RB * m->M;
+        const size_t smem = sizeof(double2) * ORB_RB * m->M + 2 * sizeof(int) * m->M;
         if (smem > 48 * 1024)
             TUFRG_CUDA_TRY(cudaFuncSetAttribute(sym_orbit_copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        sym_orbit_copy_kernel<<<dim3(m->n_loop_q, (m->M + ORB_RB - 1) / ORB_RB, 2), threads, smem, m->stream>>>(
+        sym_orbit_copy_kernel<<<dim3(m->n_loop_q, (m->M + ORB_RB - 1) / ORB_RB, 2), 32 * ORB_RB, smem, m->stream>>>(
             d_out, m->Nq, m->M, m->d_qmap, m->d_loop_list, m->d_orb_ofs, m->d_orb_q, m->d_sym_elem, m->d_sym_srow,
             m->d_sym_sinv, m->d_sym_qrow);
         return cudaGetLastError();
