@@ -246,6 +246,12 @@ tufrg_status tufrg_irrep_basis(tufrg_model *m, const void *d_state, int inverse,
  * TUFRG_ECUDA for a failed launch. */
 tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda_stream);
 
+/* Widen n FP32 values at d_in to FP64 at d_out (device buffers, no overlap), exactly (subnormals, signed zeros,
+ * infinities and NaN payloads included): the widening the split path applies to its FP32 results.  Stream ordered
+ * on cuda_stream (NULL = legacy default stream).  Errors: TUFRG_EINVAL for NULL buffers with n > 0, TUFRG_ECUDA
+ * for a failed launch. */
+tufrg_status tufrg_widen_f64(const void *d_in, void *d_out, size_t n, void *cuda_stream);
+
 /* Symmetric-state path (TUFRG_SYMMETRIC_STATE): *in_use = 1 when calls that set the flag project and
  * multiply at the orbit representatives only, 0 when they take the general path (the state symmetries
  * do not hold for this model).  *ms_general and *ms_reps are the init-time timings of projections +

@@ -100,6 +100,8 @@ def lib():
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_symmetry_info.restype = C.c_int
             L.tufrg_round_f32.argtypes = [vp, vp, C.c_size_t, vp]
+            L.tufrg_widen_f64.argtypes = [vp, vp, C.c_size_t, vp]
+            L.tufrg_widen_f64.restype = C.c_int
             L.tufrg_band_basis.argtypes = [vp, vp, vp]
             L.tufrg_band_basis.restype = C.c_int
             L.tufrg_round_f32.restype = C.c_int
@@ -169,4 +171,4 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info", "tufrg_loop_tiles",
            "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish", "tufrg_form_factors",
            "tufrg_irrep_basis", "tufrg_flow_start", "tufrg_flow_step", "tufrg_flow_amax_channels", "tufrg_flow_end",
-           "tufrg_flow_checkpoint_bytes", "tufrg_flow_save", "tufrg_flow_resume")
+           "tufrg_flow_checkpoint_bytes", "tufrg_flow_save", "tufrg_flow_resume", "tufrg_widen_f64")

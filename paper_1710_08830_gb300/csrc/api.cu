@@ -1347,6 +1347,14 @@ tufrg_status tufrg_round_f32(const void *d_in, void *d_out, size_t n, void *cuda
     return e == cudaSuccess ? TUFRG_OK : TUFRG_ECUDA;
 }
 
+tufrg_status tufrg_widen_f64(const void *d_in, void *d_out, size_t n, void *cuda_stream)
+{
+    if (n > 0 && (!d_in || !d_out)) return TUFRG_EINVAL;
+    const cudaError_t e = launch_widen_f64(static_cast<const float *>(d_in), static_cast<double *>(d_out), n,
+                                           static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? TUFRG_OK : TUFRG_ECUDA;
+}
+
 tufrg_status tufrg_symmetry_info(const tufrg_model *m, int *in_use, double *ms_general, double *ms_reps)
 {
     if (!m || !in_use || !ms_general || !ms_reps) return TUFRG_EINVAL;

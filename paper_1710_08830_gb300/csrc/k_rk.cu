@@ -169,6 +169,20 @@ cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const
     return cudaGetLastError();
 }
 
+__global__ void widen_f64_kernel(const float *in, double *out, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = widen_f(in[i]);
+}
+
+cudaError_t launch_widen_f64(const float *d_in, double *d_out, size_t n, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 8192);
+    widen_f64_kernel<<<(unsigned)blocks, 256, 0, stream>>>(d_in, d_out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_round_f32(const double *d_in, float *d_out, size_t n, cudaStream_t stream)
 {
     if (n == 0) return cudaSuccess;

@@ -381,6 +381,7 @@ cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_s
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
                            double2 *d_A, const int *qlist = nullptr, int nlist = 0);
 cudaError_t launch_to_f32(tufrg_model *m, const double2 *d_state, float2 *d_out, size_t n);
+cudaError_t launch_widen_f64(const float *d_in, double *d_out, size_t n, cudaStream_t stream);
 cudaError_t launch_round_f32(const double *d_in, float *d_out, size_t n, cudaStream_t stream);
 // qlist (nlist entries): only these transfer momenta
 cudaError_t launch_vlv(tufrg_model *m, const double2 *d_A, int channel_mask, double2 *d_out, const int *qlist = nullptr,

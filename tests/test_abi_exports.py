@@ -77,7 +77,7 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
         "tufrg_mlp_create": (4, 8, 1, 2, 0, None, None), "tufrg_mlp_get_params": (None, None),
         "tufrg_mlp_set_params": (None, None), "tufrg_mlp_forward": (None, None, 1, None),
         "tufrg_mlp_gradients": (None, None, None, 1, None, None), "tufrg_mlp_train_step": (None, None, None, 1, 1e-3, None),
-        "tufrg_round_f32": (None, None, 5, None),
+        "tufrg_round_f32": (None, None, 5, None), "tufrg_widen_f64": (None, None, 5, None),
         "tufrg_loops_noalloc": (4, 2, None, None, 0.0, 0.1, 5, None, 3, None, None),
     }
     for name, args in calls.items():

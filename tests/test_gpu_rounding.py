@@ -53,3 +53,37 @@ def test_round_f32_matches_ieee_and_cuda():
     assert L.tufrg_round_f32(nan.data_ptr(), o2.data_ptr(), 2, None) == 0
     assert torch.isnan(o2).all()
     assert L.tufrg_round_f32(None, None, 0, None) == 0
+
+
+@pytest.mark.gpu
+def test_widen_f64_is_exact():
+    """FP32 -> FP64 on the integer pipe: bit for bit numpy's (IEEE) widening over normal values, every subnormal
+    exponent, signed zeros and infinities, and NaNs with their payloads kept."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_08830_gb300 import _lib, build
+    build.build()
+    L = _lib.lib()
+    rng = np.random.default_rng(11)
+    bits = np.concatenate([
+        rng.integers(0, 2 ** 32, 200000, dtype=np.uint64).astype(np.uint32),            # every class, random
+        (rng.integers(1, 2 ** 23, 20000, dtype=np.uint64) | (rng.integers(0, 2, 20000, dtype=np.uint64) << 31)
+         ).astype(np.uint32),                                                          # subnormals of both signs
+        np.array([0, 1 << 31, 1, (1 << 31) | 1, 0x7fffff, 0x800000, 0x7f800000, 0xff800000, 0x7fc00000,
+                  0x7f800001, 0xffbfffff, 0x7f7fffff], dtype=np.uint32)])
+    x = bits.view(np.float32)
+    xd = torch.from_numpy(x.copy()).cuda()
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    assert L.tufrg_widen_f64(xd.data_ptr(), out.data_ptr(), x.size, None) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    fin = ~np.isnan(x)
+    want = x[fin].astype(np.float64)
+    assert np.array_equal(got[fin].view(np.uint64), want.view(np.uint64))
+    # NaN: sign and the 22 payload bits below the quiet bit kept in the top of the FP64 significand
+    nb = got[~fin].view(np.uint64)
+    src = bits[~fin].astype(np.uint64)
+    assert np.all(np.isnan(got[~fin]))
+    assert np.array_equal(nb >> np.uint64(63), src >> np.uint64(31))
+    assert np.array_equal((nb >> np.uint64(29)) & np.uint64(0x7fffff), src & np.uint64(0x7fffff))
+    assert L.tufrg_widen_f64(None, None, 0, None) == 0
