@@ -520,6 +520,9 @@ void release(tufrg_model *m)
     drop_rhs_graphs(m);
     for (auto &e : m->rhs_ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : m->aux_ev)
+        if (e) cudaEventDestroy(e);
+    if (m->aux_stream) cudaStreamDestroy(m->aux_stream);
     if (m->rhs_stream) cudaStreamDestroy(m->rhs_stream);
     if (m->flow_ev) cudaEventDestroy(m->flow_ev);
     if (m->flow_stream) cudaStreamDestroy(m->flow_stream);
@@ -548,19 +551,42 @@ tufrg_status rhs_device(tufrg_model *m, const double2 *d_state, int mask, double
     const bool sym = symmetric_state && m->sym_state;
     const int *ql = sym ? m->d_loop_list : nullptr;
     const int nl = sym ? m->n_loop_q : 0;
-    // without an FP32 copy the separable transform writes one as it reads the FP64 state (the sliced
-    // direct transform reads a converted copy)
-    if (split && !d_state32 && m->dft_warps == 0) {
-        CK(launch_to_f32(m, d_state, m->d_X32, state_elems(m)), "state conversion");
-        d_state32 = m->d_X32;
+    // The state's branch (Fourier transform, projections) and the loops' branch (Fermi data, loop k-sum and its
+    // reduction) share no buffer: on a second stream they overlap, joined before the products.  Serial while the
+    // phases are timed (their events stay on one stream).
+    const bool fork = !m->timing && m->aux_stream;
+    auto state_branch = [&]() -> tufrg_status {
+        // without an FP32 copy the separable transform writes one as it reads the FP64 state (the sliced
+        // direct transform reads a converted copy)
+        if (split && !d_state32 && m->dft_warps == 0) {
+            CK(launch_to_f32(m, d_state, m->d_X32, state_elems(m)), "state conversion");
+            d_state32 = m->d_X32;
+        }
+        CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
+        if (split && !d_state32) d_state32 = m->d_X32;
+        // the split path's products read the FP32 copy only
+        CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A, ql, nl), "projections");
+        return TUFRG_OK;
+    };
+    if (fork) {
+        CK(cudaEventRecord(m->aux_ev[0], m->stream), "fork");
+        CK(cudaStreamWaitEvent(m->aux_stream, m->aux_ev[0], 0), "fork");
+        const cudaStream_t main = m->stream;
+        m->stream = m->aux_stream;
+        const tufrg_status st = state_branch();
+        m->stream = main;
+        if (st != TUFRG_OK) return st;
+        CK(cudaEventRecord(m->aux_ev[1], m->aux_stream), "join");
     }
     CK(launch_fermi(m), "fermi tables");
     // a symmetric state's products read the loops of the orbit representatives only
     CK(launch_loops(m, mask, sym), "loop k-sum");
-    CK(launch_dft(m, d_state, d_state32, mask), "Fourier transform");
-    if (split && !d_state32) d_state32 = m->d_X32;
-    // the split path's products read the FP32 copy only
-    CK(launch_project(m, d_state, d_state32, mask, split ? nullptr : m->d_A, ql, nl), "projections");
+    if (fork) {
+        CK(cudaStreamWaitEvent(m->stream, m->aux_ev[1], 0), "join");
+    } else {
+        const tufrg_status st = state_branch();
+        if (st != TUFRG_OK) return st;
+    }
     if (sym) CK(launch_products_sym(m, mask, d_out), "V.L.V products (orbit representatives)");
     else CK(launch_vlv(m, m->d_A, mask, d_out), "V.L.V products");
     return TUFRG_OK;
@@ -833,6 +859,9 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
     m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    CK(cudaStreamCreateWithFlags(&m->aux_stream, cudaStreamNonBlocking), "create stream");
+    CK(cudaEventCreateWithFlags(&m->aux_ev[0], cudaEventDisableTiming), "create event");
+    CK(cudaEventCreateWithFlags(&m->aux_ev[1], cudaEventDisableTiming), "create event");
     m->hopR.assign(d.hop_R, d.hop_R + 2 * d.n_hop);
     m->hopt.assign(d.hop_t, d.hop_t + (size_t)2 * d.n_hop * d.n_s * d.n_s);
     m->V0.assign(d.V0, d.V0 + 2 * (size_t)d.n_s * d.n_s * d.n_s * d.n_s);

@@ -300,6 +300,10 @@ struct tufrg_model {
     tufrg::FlowDev *h_flow = nullptr;        // pinned host mirror
     cudaGraphExec_t step_graph = nullptr;    // one captured Dormand-Prince attempt
     cudaStream_t flow_stream = nullptr;      // private capturable stream of the flow (joined to `stream` by events)
+    // second stream of a right-hand side: the Fourier transform and projections (they read the state only) run
+    // there while the loop k-sum (it reads the temperature only) runs on `stream`; joined before the products
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t aux_ev[2] = {nullptr, nullptr};
     cudaEvent_t flow_ev = nullptr;
     // tufrg_rhs replays captured graphs of its launches, one per (input, output, mask) used more than once (the
     // four most recently used triples kept; exec is null after the first use)
