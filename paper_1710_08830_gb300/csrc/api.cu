@@ -859,9 +859,6 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     m->ns = d.n_s; m->nhop = d.n_hop; m->nff = d.n_ff; m->Lq = d.Lq; m->nc = d.nc; m->precision = d.precision;
     m->Lf = d.Lq * d.nc; m->Nq = d.Lq * d.Lq; m->Nk = m->Lf * m->Lf; m->M = d.n_ff * d.n_s * d.n_s;
     m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-    CK(cudaStreamCreateWithFlags(&m->aux_stream, cudaStreamNonBlocking), "create stream");
-    CK(cudaEventCreateWithFlags(&m->aux_ev[0], cudaEventDisableTiming), "create event");
-    CK(cudaEventCreateWithFlags(&m->aux_ev[1], cudaEventDisableTiming), "create event");
     m->hopR.assign(d.hop_R, d.hop_R + 2 * d.n_hop);
     m->hopt.assign(d.hop_t, d.hop_t + (size_t)2 * d.n_hop * d.n_s * d.n_s);
     m->V0.assign(d.V0, d.V0 + 2 * (size_t)d.n_s * d.n_s * d.n_s * d.n_s);
@@ -1000,7 +997,10 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     int max_partials = m->plan.n_partials;
     for (const LoopPlan &p : m->plan_cand) max_partials = std::max(max_partials, p.n_partials);
 
-    // ---- device memory
+    // ---- device memory (and the right-hand side's second stream)
+    CK(cudaStreamCreateWithFlags(&m->aux_stream, cudaStreamNonBlocking), "create stream");
+    CK(cudaEventCreateWithFlags(&m->aux_ev[0], cudaEventDisableTiming), "create event");
+    CK(cudaEventCreateWithFlags(&m->aux_ev[1], cudaEventDisableTiming), "create event");
     const size_t Nk = m->Nk, ns2 = (size_t)ns * ns, ns4 = ns2 * ns2, M2 = (size_t)m->M * m->M;
     const bool split = m->precision != TUFRG_FP64;
     std::vector<double2> hopt2((size_t)m->nhop * ns2), V02(ns4);
