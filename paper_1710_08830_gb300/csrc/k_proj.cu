@@ -30,7 +30,9 @@ namespace {
 
 template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const double2 &v);
 template <> __device__ __forceinline__ double2 ld_as<double>(const double2 &v) { return v; }
-template <> __device__ __forceinline__ float2 ld_as<float>(const double2 &v) { return make_float2(narrow_f(v.x), narrow_f(v.y)); }
+// FP64 -> FP32 of a complex value: the real part by the hardware conversion (the FP64 pipe), the imaginary part on
+// the integer pipe (narrow_f, the same rounding bit for bit), so that the two pipes share the work
+template <> __device__ __forceinline__ float2 ld_as<float>(const double2 &v) { return make_float2(__double2float_rn(v.x), narrow_f(v.y)); }
 template <typename R> __device__ __forceinline__ typename cpx<R>::t ld_as(const float2 &v);
 template <> __device__ __forceinline__ float2 ld_as<float>(const float2 &v) { return v; }
 
