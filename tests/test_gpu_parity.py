@@ -565,6 +565,29 @@ def test_t2g_rhs(case, prec):
     assert rel(d, ref) < (TOL64 if prec == "FP64" else TOL32)
 
 
+@pytest.mark.parametrize("shape", ["t2g_ff13", "bilayer_ff5", "rashba_ff5"])
+def test_tc_products_tile_shapes(shape):
+    """The tensor-core products at the tile shapes their work list takes: M = 468 (N_s = 6, 4 row tiles x 5 column
+    tiles of 96), M = 80 (N_s = 4, one row tile, 80-column tile), M = 20 (N_s = 2, a 32-column tile), against the
+    oracle's right-hand side, on both the general and the symmetric-state path."""
+    api = _api()
+    spec = {"t2g_ff13": lambda: inputs.t2g_soc(seed=4, Lq=5, nc=2, n_ff=13, filling=4.0, T_mu=0.05),
+            "bilayer_ff5": lambda: inputs.rashba_bilayer(Lq=5, nc=2, n_ff=5),
+            "rashba_ff5": lambda: inputs.rashba_hubbard(tp=-0.1, alpha=0.2, U=2.5, mu=-0.8, Lq=6, nc=4, n_ff=5)}[shape]()
+    m = api.Model(spec, api.SPLIT32, products=api.PRODUCTS_TC)
+    assert m.products == "tc"
+    o = oracle.Oracle(spec)
+    st = inputs.random_state(spec, seed=21, scale=0.15)
+    d = m.rhs(0.2, st).cpu().numpy()
+    ref, _ = o.rhs(0.2, st, 3)
+    assert rel(d, ref) < TOL32
+    # a symmetric state through the representatives' products (the orbit copy writes the other momenta)
+    X1 = 0.05 * m.rhs(0.5, m.zeros_state())
+    sym = m.rhs(0.3, X1, symmetric=True).cpu().numpy()
+    ref1, _ = o.rhs(0.3, X1.cpu().numpy(), 3)
+    assert rel(sym, ref1) < TOL32
+
+
 BILAYER = {   # N_s = 4: two Rashba layers with opposite couplings, interlayer hopping, onsite U per layer
     "bilayer_ff5_Lf10": lambda: inputs.rashba_bilayer(Lq=5, nc=2, n_ff=5),                            # M = 80
     "bilayer_ff9_Lf8": lambda: inputs.rashba_bilayer(Lq=4, nc=2, n_ff=9, alpha=0.25, t_perp=0.3),    # M = 144
