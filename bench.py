@@ -298,6 +298,7 @@ def run_config_t2g(stream, peaks, fp32_peak, seed=0, k=10):
             "rhs_per_s": 1e3 / ms, "ms_per_rhs": ms, "init_s": init_s, "T": T_BENCH,
             "phase_ms_per_rhs": ph, "roofline_loops": loops, "roofline_products": prod,
             "split_vs_fp64_maxrel": err, "products": m.products, "loops_backend": m.loops_backend,
+            "products_tiles": {"width": m.products_tile_width, "tuning_ms": m.products_tiles_tuning_ms},
             "flow_to_T_steps": rf["n_steps"], "note": "state: the split flow from T0 = 10 down to T = 0.1"}
 
 
@@ -783,6 +784,7 @@ def main():
                        "products": m32.products, "products_tuning_ms": m32.products_tuning_ms,
                        "loop_momenta_summed": m32.n_loop_q, "symmetric_state": True,
                        "loop_tiles": {"ky_chunks": m32.loop_ky_chunks, "tuning_ms": m32.loop_tiles_tuning_ms},
+                       "products_tiles": {"width": m32.products_tile_width, "tuning_ms": m32.products_tiles_tuning_ms},
                        "symmetric_state_path": m32.symmetric_state_path,
                        "symmetric_state_tuning_ms": m32.symmetric_state_tuning_ms,
                        "l2": "flushed (256 MB write) between timed steps", "instances": f"{world} (seed = rank)"},

@@ -211,6 +211,14 @@ tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend);
  * Errors: TUFRG_EINVAL for NULL arguments or n_ms < 0 (h_ms may be NULL when n_ms is 0). */
 tufrg_status tufrg_loop_tiles(const tufrg_model *m, int *ky_chunks, int *n_candidates, double *h_ms, int n_ms);
 
+/* Tile shape of the tensor-core products (split path): *tile_width = the complex columns per output tile (128-row
+ * tiles of NB columns; 0 for FP64 models), and, when the products backend was autotuned (TUFRG_PRODUCTS_AUTO), the
+ * timings of the column-tile candidates the autotuner compared: *n_candidates = their number and h_ms[i]
+ * (i < min(n_ms, *n_candidates)) the milliseconds of candidate i (i = 0: the widest tiles, at most 112 columns;
+ * i = 1: one tile more per matrix).  The tiling does not change any output element's summation order.
+ * Errors: TUFRG_EINVAL for NULL arguments or n_ms < 0. */
+tufrg_status tufrg_products_tiles(const tufrg_model *m, int *tile_width, int *n_candidates, double *h_ms, int n_ms);
+
 /* Exchange propagators of a state in the band basis of the model's eigenvectors (Sec. 3.4, Eqs. trafo_P,
  * mat_trafo_P, mat_trafo_D): with f_R(k) = e^{-ik.R}, N the fine mesh's k-points and U the eigenvectors of
  * tufrg_bands,

@@ -97,6 +97,8 @@ def lib():
             L.tufrg_loops_info.restype = C.c_int
             L.tufrg_loop_tiles.argtypes = [vp, ip, ip, vp, i]
             L.tufrg_loop_tiles.restype = C.c_int
+            L.tufrg_products_tiles.argtypes = [vp, ip, ip, vp, i]
+            L.tufrg_products_tiles.restype = C.c_int
             L.tufrg_symmetry_info.argtypes = [vp, ip, C.POINTER(d), C.POINTER(d)]
             L.tufrg_symmetry_info.restype = C.c_int
             L.tufrg_round_f32.argtypes = [vp, vp, C.c_size_t, vp]
@@ -168,7 +170,7 @@ EXPORTS = ("tufrg_init_model", "tufrg_free", "tufrg_last_error", "tufrg_dims", "
            "tufrg_band_basis",
            "tufrg_flow_batch", "tufrg_mlp_create", "tufrg_mlp_free", "tufrg_mlp_last_error", "tufrg_mlp_num_params",
            "tufrg_mlp_get_params", "tufrg_mlp_set_params", "tufrg_mlp_forward", "tufrg_mlp_gradients",
-           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info", "tufrg_loop_tiles",
+           "tufrg_mlp_train_step", "tufrg_set_surrogate", "tufrg_surrogate_stats", "tufrg_set_device_error", "tufrg_loops_info", "tufrg_loop_tiles", "tufrg_products_tiles",
            "tufrg_shard_classes", "tufrg_rhs_shard_transform", "tufrg_rhs_shard_finish", "tufrg_form_factors",
            "tufrg_irrep_basis", "tufrg_flow_start", "tufrg_flow_step", "tufrg_flow_amax_channels", "tufrg_flow_end",
            "tufrg_flow_checkpoint_bytes", "tufrg_flow_save", "tufrg_flow_resume", "tufrg_widen_f64")

@@ -82,6 +82,12 @@ class Model:
         # the loop k-sum's ky ranges per column, and the timed candidates {ranges: ms per launch} when tuned
         self.loop_ky_chunks = kyc.value
         self.loop_tiles_tuning_ms = {c + 1: float(cand_ms[c]) for c in range(min(ncand.value, len(cand_ms)))}
+        tw, ntc = C.c_int(), C.c_int()
+        tc_ms = np.zeros(4)
+        self._check(self._L.tufrg_products_tiles(self._h, C.byref(tw), C.byref(ntc), tc_ms.ctypes.data, len(tc_ms)))
+        # the tensor-core products' tile width (complex columns) and the autotuner's timings of its candidates
+        self.products_tile_width = tw.value
+        self.products_tiles_tuning_ms = [float(tc_ms[c]) for c in range(min(ntc.value, len(tc_ms)))]
         su, t_gen, t_rep = C.c_int(), C.c_double(), C.c_double()
         self._check(self._L.tufrg_symmetry_info(self._h, C.byref(su), C.byref(t_gen), C.byref(t_rep)))
         self.symmetric_state_path = bool(su.value)   # rhs(symmetric=True) works at the representatives only

@@ -442,7 +442,8 @@ void build_loop_symmetry(const tufrg_model *m, LoopSymmetry &ls)
 struct TuneResult {
     double ms[2];
     int choice;
-    std::vector<double> cand_ms;   // the loop kernel's launch shapes: one time per candidate
+    std::vector<double> cand_ms;   // launch-shape candidates: one time per candidate
+    int aux = 0;                   // products: the chosen column-tile count
 };
 std::mutex g_tune_mutex;
 std::map<std::vector<int>, TuneResult> g_tune_cache;
@@ -1233,6 +1234,8 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         m->products = cached.choice;
         m->tune_ms[0] = cached.ms[0];
         m->tune_ms[1] = cached.ms[1];
+        m->tc_tile_ms = cached.cand_ms;
+        m->tc_ntiles = cached.aux;
     } else if (split && d.products == TUFRG_PRODUCTS_AUTO) {
         // autotune the products backend on this model's sizes (the cost does not depend on the values)
         const size_t nA = 2 * (size_t)m->Nq * M2;
@@ -1245,20 +1248,39 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         CK(cudaEventCreate(&e1), "event");
         const int cand[2] = {TUFRG_PRODUCTS_TC, TUFRG_PRODUCTS_SIMT};
         CK(launch_set_scalars(m, 1.0, 1.0), "set scalars");
+        // the tensor cores at each column-tile count (tile width), then the CUDA cores
+        const std::vector<int> tiles = tc_tile_candidates(m);
+        m->tc_tile_ms.assign(tiles.size(), 0.0);
+        int best_tiles = tiles[0];
         for (int c = 0; c < 2; c++) {
             m->products = cand[c];
-            CK(launch_vlv(m, m->d_A, 3, tmp), "autotune warm-up");
-            CK(cudaEventRecord(e0, m->stream), "event");
-            const int reps = 3;
-            for (int r = 0; r < reps; r++) CK(launch_vlv(m, m->d_A, 3, tmp), "autotune");
-            CK(cudaEventRecord(e1, m->stream), "event");
-            CK(cudaEventSynchronize(e1), "event");
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1), "event");
-            m->tune_ms[c] = ms / reps;
+            for (size_t t = 0; t < (c == 0 ? tiles.size() : 1); t++) {
+                if (c == 0) m->tc_ntiles = tiles[t];
+                CK(launch_vlv(m, m->d_A, 3, tmp), "autotune warm-up");
+                CK(cudaEventRecord(e0, m->stream), "event");
+                const int reps = 3;
+                for (int r = 0; r < reps; r++) CK(launch_vlv(m, m->d_A, 3, tmp), "autotune");
+                CK(cudaEventRecord(e1, m->stream), "event");
+                CK(cudaEventSynchronize(e1), "event");
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (c == 0) {
+                    m->tc_tile_ms[t] = ms / reps;
+                    if (t == 0 || m->tc_tile_ms[t] < m->tune_ms[0]) {
+                        m->tune_ms[0] = m->tc_tile_ms[t];
+                        best_tiles = tiles[t];
+                    }
+                } else {
+                    m->tune_ms[1] = ms / reps;
+                }
+            }
         }
+        m->tc_ntiles = best_tiles;
         m->products = m->tune_ms[0] <= m->tune_ms[1] ? TUFRG_PRODUCTS_TC : TUFRG_PRODUCTS_SIMT;
-        tune_store(m, 0, TuneResult{{m->tune_ms[0], m->tune_ms[1]}, m->products});
+        TuneResult r{{m->tune_ms[0], m->tune_ms[1]}, m->products};
+        r.cand_ms = m->tc_tile_ms;
+        r.aux = m->tc_ntiles;
+        tune_store(m, 0, r);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaFree(tmp);
@@ -1346,6 +1368,15 @@ tufrg_status tufrg_loops_info(const tufrg_model *m, int *backend)
 {
     if (!m || !backend) return TUFRG_EINVAL;
     *backend = m->loops_tc ? TUFRG_LOOPS_TC : TUFRG_LOOPS_SIMT;
+    return TUFRG_OK;
+}
+
+tufrg_status tufrg_products_tiles(const tufrg_model *m, int *tile_width, int *n_candidates, double *h_ms, int n_ms)
+{
+    if (!m || !tile_width || !n_candidates || (n_ms > 0 && !h_ms) || n_ms < 0) return TUFRG_EINVAL;
+    *tile_width = (m->precision != TUFRG_FP64) ? tc_tile_width(m) : 0;
+    *n_candidates = (int)m->tc_tile_ms.size();
+    for (int i = 0; i < n_ms && i < (int)m->tc_tile_ms.size(); i++) h_ms[i] = m->tc_tile_ms[i];
     return TUFRG_OK;
 }
 

@@ -51,13 +51,14 @@ struct Dims {
     int n_tiles;    // nb-column tiles covering M
 };
 
-Dims dims_of(int M)
+// n_tiles column tiles (0: the fewest that keep NB <= 112), NB the smallest multiple of 16 covering M with them
+Dims dims_of(int M, int n_tiles)
 {
     Dims d{};
     d.M = M;
     d.nks = (M + KS - 1) / KS;
     d.m_tiles = (M + TM - 1) / TM;
-    d.n_tiles = (M + NB_MAX - 1) / NB_MAX;
+    d.n_tiles = std::max(n_tiles, (M + NB_MAX - 1) / NB_MAX);
     d.nb = ((M + d.n_tiles - 1) / d.n_tiles + 15) / 16 * 16;
     return d;
 }
@@ -416,6 +417,18 @@ cudaError_t launch_phase(tufrg_model *m, const VlvArgs &a)
 
 }  // namespace
 
+// the column-tile counts the products autotuner times: the fewest (widest tiles) and one more; the second only when it
+// changes the tile width and keeps it at least 16
+std::vector<int> tc_tile_candidates(const tufrg_model *m)
+{
+    const Dims a = dims_of(m->M, 0), b = dims_of(m->M, a.n_tiles + 1);
+    std::vector<int> v{a.n_tiles};
+    if (b.nb != a.nb && b.nb >= 16) v.push_back(b.n_tiles);
+    return v;
+}
+
+int tc_tile_width(const tufrg_model *m) { return dims_of(m->M, m->tc_ntiles).nb; }
+
 bool tc_supported(const tufrg_model *m)
 {
     const int ns2 = m->ns * m->ns;
@@ -442,7 +455,7 @@ cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, cons
     a.qlist = qlist;
     a.scal = m->d_scal;
     a.err = m->d_err;
-    a.d = dims_of(M);
+    a.d = dims_of(M, m->tc_ntiles);
     a.nff = m->nff;
     a.lper = m->nd * ns2 * ns2;
     a.Nq = m->Nq;

@@ -287,6 +287,8 @@ struct tufrg_model {
     int *d_err = nullptr;           // device-side error flag (bounded waits)
     int products = TUFRG_PRODUCTS_SIMT;     // backend of the split-path products
     double tune_ms[2] = {-1.0, -1.0};       // autotuner timings (tensor cores, CUDA cores)
+    int tc_ntiles = 0;                       // tensor-core products: column tiles per matrix (0: the fewest)
+    std::vector<double> tc_tile_ms;         // the products autotuner's timings of the column-tile candidates
     double *d_red = nullptr;        // density reduction scratch
     // flow work buffers
     double2 *d_y = nullptr, *d_yt = nullptr, *d_yn = nullptr, *d_k[7] = {};
@@ -441,6 +443,8 @@ cudaError_t launch_band_basis(tufrg_model *m, const double2 *d_state, double2 *d
 bool orbit_products_supported(const tufrg_model *m);
 int orbit_max_size();   // largest orbit the fused orbit kernel takes   // symmetric states: non-representative momenta
 bool tc_supported(const tufrg_model *m);
+std::vector<int> tc_tile_candidates(const tufrg_model *m);
+int tc_tile_width(const tufrg_model *m);
 cudaError_t launch_vlv_tc(tufrg_model *m, int channel_mask, double2 *d_out, const int *qlist, int nlist);
 cudaError_t launch_loop_records(tufrg_model *m);          // per evaluation: Fermi data at d_scal[0]
 cudaError_t launch_loop_records_static(tufrg_model *m);   // once per model: projectors and e = E - mu

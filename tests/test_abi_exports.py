@@ -68,6 +68,7 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
         "tufrg_timing_begin": (None,), "tufrg_timing_end": (None, None, 0, None, None),
         "tufrg_set_device_error": (None, 1), "tufrg_loops_info": (None, ctypes.byref(i)),
         "tufrg_loop_tiles": (None, ctypes.byref(i), ctypes.byref(i), None, 0),
+        "tufrg_products_tiles": (None, ctypes.byref(i), ctypes.byref(i), None, 0),
         "tufrg_flow_start": (None, None), "tufrg_flow_step": (None, None), "tufrg_flow_amax_channels": (None, None),
         "tufrg_flow_end": (None, None, None), "tufrg_flow_save": (None, None, 0),
         "tufrg_flow_resume": (None, None, None, 0),

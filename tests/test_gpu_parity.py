@@ -588,6 +588,24 @@ def test_tc_products_tile_shapes(shape):
     assert rel(sym, ref1) < TOL32
 
 
+def test_tc_products_tile_autotune():
+    """With the products backend on AUTO the tensor cores are timed at two column-tile widths (M = 180: 96 and 64
+    columns) and the faster kept; the tiling changes no output element's summation order, so the products equal
+    those at the default width bit for bit."""
+    api = _api()
+    spec = T2G["t2g_ff5_Lf8"]()
+    m = api.Model(spec, api.SPLIT32)
+    t = m.products_tiles_tuning_ms
+    assert len(t) == 2 and all(v > 0 for v in t)
+    assert m.products_tile_width == (96 if t[0] <= t[1] else 64)
+    ref = api.Model(spec, api.SPLIT32, products=api.PRODUCTS_TC)
+    assert ref.products_tile_width == 96 and ref.products_tiles_tuning_ms == []
+    st = inputs.random_state(spec, seed=5, scale=0.15)
+    if m.products == "tc":
+        assert torch.equal(m.rhs(0.2, st), ref.rhs(0.2, st))
+    assert api.Model(spec, api.FP64).products_tile_width == 0
+
+
 BILAYER = {   # N_s = 4: two Rashba layers with opposite couplings, interlayer hopping, onsite U per layer
     "bilayer_ff5_Lf10": lambda: inputs.rashba_bilayer(Lq=5, nc=2, n_ff=5),                            # M = 80
     "bilayer_ff9_Lf8": lambda: inputs.rashba_bilayer(Lq=4, nc=2, n_ff=9, alpha=0.25, t_perp=0.3),    # M = 144
