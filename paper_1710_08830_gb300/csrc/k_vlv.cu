@@ -475,7 +475,7 @@ cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out
         return launch_sym_scatter(m, d_out);
     }
     const int M = m->M, nt = M / 2;
-    const int threads = (nt * nt + 31) / 32 * 32;
+    const int threads = 1024;   // (M/2)^2 <= 1024 threads form the product; all of them write the orbit
     const size_t smem = 2 * sizeof(float2) * M * M;
     if (smem > 48 * 1024)
         TUFRG_CUDA_TRY(cudaFuncSetAttribute(vlv_orbit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
