@@ -1,4 +1,5 @@
-// Dormand-Prince 5(4) stage combinations and the error norm, FP64, on the device.
+// Dormand-Prince 5(4) stage combinations (FP64) and the error norm (FP64; FP32 arithmetic on the split path), on the
+// device.
 // The flow state is HBM resident; these kernels stream it once per stage.
 #include <algorithm>
 
@@ -63,6 +64,39 @@ __global__ void rk_error_kernel(const double2 *y, const double2 *yn, const FlowD
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// The same norm on the split path in FP32 arithmetic (this GPU's FP64 pipe, which the square roots and divisions
+// above run on, is narrow): the stage derivatives there are FP32 results widened exactly, so their FP32 values are
+// read back without rounding (narrow_f on the integer pipe); the weighted sums, magnitudes and the ratio are FP32,
+// which is ample for a step-size control norm.  The maximum is published as the double of the FP32 value.
+__global__ void rk_error_f32_kernel(const double2 *y, const double2 *yn, const FlowDev *fs, StageArgs s, size_t n,
+                                    unsigned long long *out)
+{
+    const float h = fabsf((float)fs->h), atol = (float)fs->atol, rtol = (float)fs->rtol;
+    float e[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) e[j] = j < s.nk ? (float)s.a[j] : 0.f;
+    float mx = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float er = 0.f, ei = 0.f;
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            if (j >= s.nk) break;
+            const double2 kv = reinterpret_cast<const double2 *>(s.k[j])[i];
+            er = fmaf(e[j], narrow_f(kv.x), er);
+            ei = fmaf(e[j], narrow_f(kv.y), ei);
+        }
+        const float ea = h * sqrtf(fmaf(er, er, ei * ei));
+        const double2 a = y[i], b = yn[i];
+        const float ax = narrow_f(a.x), ay = narrow_f(a.y), bx = narrow_f(b.x), by = narrow_f(b.y);
+        const float ya = sqrtf(fmaf(ax, ax, ay * ay)), yb = sqrtf(fmaf(bx, bx, by * by));
+        float r = ea / (atol + rtol * fmaxf(ya, yb));
+        if (!isfinite(r)) r = INFINITY;
+        mx = fmaxf(mx, r);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(out, (unsigned long long)__double_as_longlong((double)mx));
 }
 
 // temperature of stage j: T = exp(x + c_j h); the products are scaled by T (f = T dX/dT)
@@ -212,7 +246,10 @@ cudaError_t launch_rk_error(tufrg_model *m, const double2 *y, const double2 *yn,
     }
     TUFRG_CUDA_TRY(cudaMemsetAsync(m->d_amax + 2, 0, sizeof(unsigned long long), m->stream));
     PhaseScope ps(m, PH_RK);
-    rk_error_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(y, yn, fs, s, n, m->d_amax + 2);
+    if (m->precision == TUFRG_FP64)
+        rk_error_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(y, yn, fs, s, n, m->d_amax + 2);
+    else
+        rk_error_f32_kernel<<<grid_for(m, n), 256, 0, m->stream>>>(y, yn, fs, s, n, m->d_amax + 2);
     return cudaGetLastError();
 }
 
