@@ -1,5 +1,5 @@
-// Dormand-Prince 5(4) stage combinations (FP64) and the error norm (FP64; FP32 arithmetic on the split path), on the
-// device.
+// Dormand-Prince 5(4) stage combinations and the error norm on the device: FP64, or on the split path FP32 sums of the
+// (exactly FP32) stage derivatives with the FP64 state update.
 // The flow state is HBM resident; these kernels stream it once per stage.
 #include <algorithm>
 
@@ -23,6 +23,28 @@ __global__ void rk_combine_kernel(double *out, float *out32, const double *y, co
         double acc = 0.0;
         for (int j = 0; j < s.nk; j++) acc = fma(s.a[j], s.k[j][i], acc);
         const double v = fma(h, acc, y[i]);
+        if (out) out[i] = v;
+        if (out32) out32[i] = narrow_f(v);
+    }
+}
+
+// The same on the split path: the stage derivatives are exact FP32 values, so the weighted sum runs in FP32 (read back
+// without rounding by narrow_f) and only the step y + h sum is FP64 (one fused operation per element: the state keeps
+// its FP64 accumulation, the increment carries the FP32 accuracy of the derivatives)
+__global__ void rk_combine_f32_kernel(double *out, float *out32, const double *y, const FlowDev *fs, StageArgs s, size_t n)
+{
+    const double h = fs->h;
+    float a[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) a[j] = j < s.nk ? (float)s.a[j] : 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            if (j >= s.nk) break;
+            acc = fmaf(a[j], narrow_f(s.k[j][i]), acc);
+        }
+        const double v = fma(h, widen_f(acc), y[i]);
         if (out) out[i] = v;
         if (out32) out32[i] = narrow_f(v);
     }
@@ -197,9 +219,14 @@ cudaError_t launch_rk_combine(tufrg_model *m, double2 *out, float2 *out32, const
     }
     const size_t nd = 2 * n;
     PhaseScope ps(m, PH_RK);
-    rk_combine_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
-                                                              reinterpret_cast<float *>(out32),
-                                                              reinterpret_cast<const double *>(y), fs, s, nd);
+    if (m->precision == TUFRG_FP64)
+        rk_combine_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
+                                                                  reinterpret_cast<float *>(out32),
+                                                                  reinterpret_cast<const double *>(y), fs, s, nd);
+    else
+        rk_combine_f32_kernel<<<grid_for(m, nd), 256, 0, m->stream>>>(reinterpret_cast<double *>(out),
+                                                                      reinterpret_cast<float *>(out32),
+                                                                      reinterpret_cast<const double *>(y), fs, s, nd);
     return cudaGetLastError();
 }
 
