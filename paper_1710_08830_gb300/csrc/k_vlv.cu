@@ -474,7 +474,7 @@ cudaError_t launch_products_sym(tufrg_model *m, int channel_mask, double2 *d_out
         TUFRG_CUDA_TRY(launch_vlv(m, m->d_A, channel_mask, d_out, m->d_loop_list, m->n_loop_q));
         return launch_sym_scatter(m, d_out);
     }
-    const int M = m->M, nt = M / 2;
+    const int M = m->M;
     const int threads = 1024;   // (M/2)^2 <= 1024 threads form the product; all of them write the orbit
     const size_t smem = 2 * sizeof(float2) * M * M;
     if (smem > 48 * 1024)
