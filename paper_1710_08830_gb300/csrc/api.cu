@@ -1,5 +1,6 @@
 // C ABI of libtufrg: model set-up (tables, memory), the right-hand side and the flow.
 // Every entry point returns a tufrg_status and never throws across the boundary.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <climits>
 #include <array>
@@ -2029,8 +2030,13 @@ tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flo
 
 namespace tufrg {
 
+// NVTX ranges named after the phases (host-side markers for profilers; no cost without an attached tool)
+static const char *const kPhaseNames[PH_N] = {"tufrg fermi", "tufrg loops", "tufrg loop_reduce", "tufrg dft",
+                                              "tufrg project", "tufrg vlv", "tufrg rk", "tufrg sym_scatter"};
+
 PhaseScope::PhaseScope(tufrg_model *mm, int phase, int n_launch) : m(mm)
 {
+    nvtxRangePushA(kPhaseNames[phase]);
     m->launches += n_launch;
     if (phase == PH_LOOPS) m->loop_launches += n_launch;
     if (!m->timing) return;
@@ -2049,6 +2055,7 @@ PhaseScope::PhaseScope(tufrg_model *mm, int phase, int n_launch) : m(mm)
 PhaseScope::~PhaseScope()
 {
     if (idx >= 0) cudaEventRecord(m->trec[idx].b, m->stream);
+    nvtxRangePop();
 }
 
 }  // namespace tufrg
