@@ -41,7 +41,10 @@
  *   so the M x M loop matrix is L[(R1,a),(R2,b)] = Lc[q][d(R1-R2)][a][b].
  * - Every call is stream-ordered on the stream given to tufrg_init_model and
  *   returns a status; no call throws, aborts or exits.  On error the outputs
- *   are unspecified and tufrg_last_error() describes the cause.
+ *   are unspecified and tufrg_last_error() describes the cause.  A call that
+ *   fails on a CUDA runtime call consumes that error (cudaGetLastError), so
+ *   it is not left pending for the caller's next launch check; tufrg_init_model
+ *   also discards an error left pending by the caller's earlier runtime calls.
  * - Device pointers (prefix d_) must be device memory of the current device
  *   with the documented size, owned by the caller; host pointers (h_) are
  *   host memory owned by the caller.  Descriptors are copied at init.
@@ -169,7 +172,8 @@ typedef struct {
  * and projection gather tables (Sec. 3.3) and allocates all work memory.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: TUFRG_EINVAL (bad descriptor, non-Hermitian H, bonds not distinct modulo Lq), TUFRG_ENOTSUP (n_s other
- * than 2, 4, 6), TUFRG_ETOOBIG (projection tables beyond 2^31 entries), TUFRG_ENOMEM, TUFRG_ECUDA,
+ * than 2, 4, 6), TUFRG_ETOOBIG (projection tables beyond 2^31 entries), TUFRG_ENOMEM (a device allocation, or a
+ * host allocation for the tables, failed; every entry point maps a device allocation failure to it), TUFRG_ECUDA,
  * TUFRG_ETIMEOUT (a bounded device-side wait gave up while the products backends were timed).  Ownership: on success and on every failure after the model object was
  * allocated, *out holds it (on failure with the message for tufrg_last_error and whatever device memory was already
  * allocated); the caller releases it with tufrg_free in both cases.  *out is NULL only when out or desc is NULL
@@ -445,7 +449,9 @@ tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flo
  *   the channel mask (the controller's scale range, tolerances and stop value come from the checkpoint).
  * Errors: TUFRG_EINVAL (NULL arguments, bad options, a second open flow, no open flow, a short buffer, a
  * checkpoint of another model, mask or library version), TUFRG_ENOTSUP (checkpoints of a model with a loop
- * surrogate), TUFRG_ETIMEOUT (a bounded device wait gave up), TUFRG_ECUDA, and tufrg_flow_end's flow statuses. */
+ * surrogate), TUFRG_ENONFINITE (tufrg_flow_resume: a non-finite value in the checkpoint's state or derivative; the
+ * model is left as it was), TUFRG_ETIMEOUT (a bounded device wait gave up), TUFRG_ECUDA, and tufrg_flow_end's flow
+ * statuses. */
 typedef struct {
     double T, h, err, amax;
     int n_steps, n_reject, accepted, status;

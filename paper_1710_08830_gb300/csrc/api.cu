@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <new>
@@ -35,6 +36,10 @@ tufrg_status fail(tufrg_model *m, tufrg_status st, const std::string &msg)
 tufrg_status cuda_fail(tufrg_model *m, cudaError_t e, const char *where)
 {
     if (m) m->err = std::string(where) + ": " + cudaGetErrorString(e);
+    // consume the error: a failed allocation or launch must not stay pending for the caller's next launch check
+    // (nor for the next one of this library); a sticky error stays in the context regardless
+    (void)cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return TUFRG_ENOMEM;
     return e == cudaErrorNotSupported ? TUFRG_ENOTSUP : TUFRG_ECUDA;
 }
 
@@ -827,14 +832,19 @@ tufrg_status read_device_error(tufrg_model *m)
 
 extern "C" {
 
+// The host tables of init grow with the meshes and the bond set: a failed host allocation there (std::bad_alloc, or
+// std::length_error for a size beyond what a container holds) becomes TUFRG_ENOMEM instead of crossing the boundary.
 tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, tufrg_model **out)
-{
+try {
     if (!out) return TUFRG_EINVAL;
     *out = nullptr;
     if (!desc) return TUFRG_EINVAL;
     tufrg_model *m = new (std::nothrow) tufrg_model();
     if (!m) return TUFRG_ENOMEM;
     *out = m;   // so that tufrg_last_error works even when set-up fails
+    // an error that an earlier runtime call of this thread left pending (a failed allocation of the caller's) would
+    // be taken for the failure of the first launch below; it is not this model's
+    (void)cudaGetLastError();
     const tufrg_model_desc &d = *desc;
     if (d.n_s < 1 || d.n_s > 8) return fail(m, TUFRG_EINVAL, "n_s must be in [1, 8]");
     if (d.n_s != 2 && d.n_s != 4 && d.n_s != 6) return fail(m, TUFRG_ENOTSUP, "the library supports n_s = 2, 4, 6");
@@ -1155,7 +1165,10 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
     CK(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream), "zero error flag");
     CK(cudaMalloc(&m->d_part, m->part_bytes), "cudaMalloc loop partials");
     CK(dalloc(&m->d_Xr, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
-    CK(cudaMalloc(&m->d_dftpart, (size_t)m->dft_nsplit * 2 * m->ncls * M2 * (split ? sizeof(float2) : sizeof(double2))),
+    // partial sums of the sliced direct transform, or Z(u_x, R_y) of the separable one ([2][Lq][n_Ry][M^2])
+    const size_t dft_scratch = m->dft_warps > 0 ? 2 * (size_t)m->Lq * m->dft_nry * M2
+                                                : (size_t)m->dft_nsplit * 2 * m->ncls * M2;
+    CK(cudaMalloc(&m->d_dftpart, dft_scratch * (split ? sizeof(float2) : sizeof(double2))),
        "cudaMalloc Fourier partials");
     if (split) CK(dalloc(&m->d_Xr32, 2 * (size_t)m->ncls * M2), "cudaMalloc Fourier transforms");
     if (loops2_supported(m)) CK(dalloc(&m->d_rec, Nk * 3), "cudaMalloc loop records");
@@ -1347,6 +1360,16 @@ tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, t
         if (dev_err) return fail(m, TUFRG_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
     }
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    tufrg_model *m = out ? *out : nullptr;
+    if (m) {
+        try {
+            m->err = std::string("host allocation failed: ") + ex.what();
+        } catch (...) {
+            m->err.clear();
+        }
+    }
+    return TUFRG_ENOMEM;
 }
 
 tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt)
@@ -1901,17 +1924,28 @@ tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *o, const v
         h.M != want.M || h.n_elems != want.n_elems || h.channel_mask != want.channel_mask || h.basis != want.basis ||
         h.regulator != want.regulator || h.loops_tc != want.loops_tc)
         return fail(m, TUFRG_EINVAL, "the checkpoint belongs to another model or channel mask");
+    const size_t n = state_elems(m);
+    const unsigned char *p = static_cast<const unsigned char *>(h_buf);
+    // a state or derivative that is not finite would only surface as a failed step later, or not at all where it
+    // sits outside the rows the symmetric path reads: refuse it here
+    for (size_t i = 0; i < 4 * n; i++) {
+        double v;
+        std::memcpy(&v, p + sizeof(h) + sizeof(FlowDev) + i * sizeof(double), sizeof(v));
+        if (!std::isfinite(v)) return fail(m, TUFRG_ENONFINITE, "the checkpoint holds a non-finite state or derivative");
+    }
     // the launch shapes the checkpointed run used (they fix the summation order), then a fresh capture if needed
+    // (both checked before either is changed, so that a refused checkpoint leaves the model as it was)
+    if (h.products != m->products &&
+        (m->precision == TUFRG_FP64 || (h.products != TUFRG_PRODUCTS_TC && h.products != TUFRG_PRODUCTS_SIMT)))
+        return fail(m, TUFRG_EINVAL, "the checkpoint's products backend does not apply to this model");
+    if (h.ky_chunks != m->plan.ky_chunks && (h.ky_chunks < 1 || h.ky_chunks > (int)m->plan_cand.size()))
+        return fail(m, TUFRG_EINVAL, "the checkpoint's loop launch shape does not apply to this model");
     bool reshaped = false;
     if (h.products != m->products) {
-        if (m->precision == TUFRG_FP64 || (h.products != TUFRG_PRODUCTS_TC && h.products != TUFRG_PRODUCTS_SIMT))
-            return fail(m, TUFRG_EINVAL, "the checkpoint's products backend does not apply to this model");
         m->products = h.products;
         reshaped = true;
     }
     if (h.ky_chunks != m->plan.ky_chunks) {
-        if (h.ky_chunks < 1 || h.ky_chunks > (int)m->plan_cand.size())
-            return fail(m, TUFRG_EINVAL, "the checkpoint's loop launch shape does not apply to this model");
         m->plan = m->plan_cand[h.ky_chunks - 1];
         reshaped = true;
     }
@@ -1920,8 +1954,6 @@ tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *o, const v
         m->step_graph = nullptr;
     }
     if (reshaped) drop_rhs_graphs(m);
-    const size_t n = state_elems(m);
-    const unsigned char *p = static_cast<const unsigned char *>(h_buf);
     cudaStream_t user;
     if ((st = flow_enter(m, &user)) != TUFRG_OK) return st;
     auto run = [&]() -> tufrg_status {

@@ -132,13 +132,16 @@ int gsz(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
 tufrg_status mfail(tufrg_mlp *n, tufrg_status st, const std::string &msg)
 {
     if (n) n->err = msg;
+    (void)cudaGetLastError();   // leave no failed call's error pending for the caller's next launch check
     return st;
 }
 
-#define MK(expr, where)                                                                      \
-    do {                                                                                     \
-        cudaError_t _e = (expr);                                                             \
-        if (_e != cudaSuccess) return mfail(n, TUFRG_ECUDA, std::string(where) + ": " + cudaGetErrorString(_e)); \
+#define MK(expr, where)                                                                           \
+    do {                                                                                          \
+        cudaError_t _e = (expr);                                                                  \
+        if (_e != cudaSuccess)                                                                    \
+            return mfail(n, _e == cudaErrorMemoryAllocation ? TUFRG_ENOMEM : TUFRG_ECUDA,         \
+                         std::string(where) + ": " + cudaGetErrorString(_e));                     \
     } while (0)
 
 // C = op(A) op(B) (+ bias) on the tensor cores with the network's operand scratch

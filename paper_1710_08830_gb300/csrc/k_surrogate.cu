@@ -200,8 +200,13 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
             m->err = "tufrg_set_surrogate: check momentum out of range";
             return TUFRG_EINVAL;
         }
+    cudaError_t failed = cudaSuccess;
     auto ck = [&](cudaError_t e, const char *w) {
-        if (e != cudaSuccess) m->err = std::string(w) + ": " + cudaGetErrorString(e);
+        if (e != cudaSuccess) {
+            m->err = std::string(w) + ": " + cudaGetErrorString(e);
+            failed = e;
+            (void)cudaGetLastError();
+        }
         return e == cudaSuccess;
     };
     const size_t chk_part = (size_t)n_check * m->plan.n_partials * m->dxs.size() * 5 * 16;
@@ -221,7 +226,7 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
               ck(cudaMemset(m->d_sur_count, 0, 3 * sizeof(unsigned long long)), "memset");
     if (!ok) {
         drop();
-        return TUFRG_ECUDA;
+        return failed == cudaErrorMemoryAllocation ? TUFRG_ENOMEM : TUFRG_ECUDA;
     }
     int nin = 0, nout = 0;
     mlp_dims(net, &nin, &nout);
@@ -250,8 +255,10 @@ tufrg_status tufrg_surrogate_stats(tufrg_model *m, long long *accepted, long lon
     unsigned long long c[3] = {0, 0, 0};
     if (m->d_sur_count) {
         if (cudaMemcpyAsync(c, m->d_sur_count, sizeof(c), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-            cudaStreamSynchronize(m->stream) != cudaSuccess)
+            cudaStreamSynchronize(m->stream) != cudaSuccess) {
+            (void)cudaGetLastError();
             return TUFRG_ECUDA;
+        }
     }
     if (accepted) *accepted = (long long)c[0];
     if (rejected) *rejected = (long long)c[1];
