@@ -1069,7 +1069,7 @@ try {
         }
         m->dft_nry = (int)ry.size();
         m->dft_nrx = (int)rx.size();
-        dft_sep_plan(m, &m->dft_warps, &m->dft_epw_log2);
+        dft_sep_plan(m, &m->dft_warps);
         if (m->dft_warps > 0) {
             std::vector<int> tabs(2 * m->ncls + m->dft_nry + 1, 0);
             int pos = 0;

@@ -89,102 +89,124 @@ __global__ void __launch_bounds__(128) dft_kernel(const XT *__restrict__ X, int 
 
 // Separable form of the same transform, u = (u_x, u_y), R'' = (R_x, R_y):
 //   Z(u_x, R_y) = sum_{u_y} e^{i u_y R_y} X(u_x, u_y),   X(R'') = (1/Nq) sum_{u_x} e^{i u_x R_x} Z(u_x, R_y),
-// Lq (n_Ry + n_cls / Lq) complex FMAs per entry and class instead of Nq.  One CTA owns EPW = 2^epw_log2
-// consecutive matrix entries of one channel; lane = (sub, el) of a warp takes entry el of the block and
-// the rows u_x = w G + sub, + W G, ... (G = 32 / EPW rows side by side), forms Z for the distinct R_y
-// of the classes (in registers) and adds e^{i u_x R_x} Z into its own shared-memory column; the W G
-// columns of an entry are summed in a fixed order at the end (deterministic, one pass over the state, no
-// partials in HBM).  Classes are visited grouped by R_y: sorted position c has class id cid[c], R_x
-// index rxi[c], and the group of the r-th R_y is [ryo[r], ryo[r+1]).  Reading the FP64 state on the split
-// path, the kernel also writes its FP32 rounding to x32 (the copy the projections read).
+// Lq (n_Ry + n_cls / Lq) complex FMAs per entry and class instead of Nq, in two passes:
+//   dft_rows_kernel: one thread per (channel, u_x, matrix entry) reads its Lq values of the state, UB loads in
+//     flight at a time (the only pass over the state, coalesced across entries), keeps Z
+//     for the n_Ry distinct R_y of the classes in registers and writes them to a scratch [ch][u_x][R_y][M^2]
+//     small enough to stay in L2; reading the FP64 state on the split path it also writes the FP32 rounding (the
+//     copy the projections read);
+//   dft_cols_kernel: a CTA per (channel, R_y, 32 consecutive entries) stages Z(u_x, R_y) of its entries in shared
+//     memory, DFT_UXC values of u_x at a time; warp w adds e^{i u_x R_x} Z(u_x, R_y) over u_x for the w-th class
+//     with that R_y, one entry per lane.
+// Both sums run in a fixed order (deterministic).  Neither kernel holds partial sums of the classes in shared
+// memory, so their CTAs are small and share the SMs with the loop k-sum that runs beside the state's branch.
 constexpr int DFT_MAXRY = 9;
-constexpr int DFT_MAXW = 24;      // FP32 accumulators
-constexpr int DFT_MAXW64 = 12;    // FP64 accumulators (twice the registers and shared memory per warp)
+constexpr int DFT_MAXG = 32;     // classes of one R_y (warps of a dft_cols_kernel CTA)
+constexpr int DFT_UXC = 32;      // u_x staged per round in dft_cols_kernel
+constexpr int DFT_THREADS = 128;
+constexpr size_t DFT_TABLE_CAP = 32 * 1024;   // phases (and class tables) staged in shared memory
 
 __device__ __forceinline__ void put32(float2 *p, float2 v) { *p = v; }
 __device__ __forceinline__ void put32(float2 *, double2) {}
 
 template <typename R, typename XT>
-__global__ void __launch_bounds__(32 * (sizeof(R) == 8 ? DFT_MAXW64 : DFT_MAXW)) dft_sep_kernel(
-    const XT *__restrict__ X, int Lq, int M2, int ncls, int nry, int nrx, int epw_log2, const int *__restrict__ tabs,
-    const typename cpx<R>::t *__restrict__ phy, const typename cpx<R>::t *__restrict__ phx, int ch_lo, double inv_nq,
-    typename cpx<R>::t *__restrict__ Xr, float2 *__restrict__ x32)
+__global__ void __launch_bounds__(DFT_THREADS) dft_rows_kernel(const XT *__restrict__ X, int Lq, int M2, int nry,
+                                                               const typename cpx<R>::t *__restrict__ phy, int ch_lo,
+                                                               typename cpx<R>::t *__restrict__ Z,
+                                                               float2 *__restrict__ x32)
 {
     using C2 = typename cpx<R>::t;
-    constexpr int UB = 8;   // loads in flight per thread
+    constexpr int UB = 8;   // loads in flight per thread (more registers than this leave too few warps per SM)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int EPW = 1 << epw_log2, G = 32 >> epw_log2, sub = lane >> epw_log2, el = lane & (EPW - 1);
-    C2 *part = reinterpret_cast<C2 *>(smem_raw);            // [W][ncls][32]
-    C2 *sphy = part + (size_t)W * ncls * 32;               // [Lq][nry]  e^{i u_y R_y}
-    C2 *sphx = sphy + Lq * nry;                             // [Lq][nrx]  e^{i u_x R_x}
-    int *stab = reinterpret_cast<int *>(sphx + Lq * nrx);   // cid [ncls], rxi [ncls], ryo [nry + 1]
+    C2 *sphy = reinterpret_cast<C2 *>(smem_raw);   // [Lq][nry]  e^{i u_y R_y}
     for (int i = threadIdx.x; i < Lq * nry; i += blockDim.x) sphy[i] = phy[i];
-    for (int i = threadIdx.x; i < Lq * nrx; i += blockDim.x) sphx[i] = phx[i];
-    for (int i = threadIdx.x; i < 2 * ncls + nry + 1; i += blockDim.x) stab[i] = tabs[i];
-    C2 *mine = part + (size_t)w * ncls * 32;
-    for (int c = 0; c < ncls; c++) mine[c * 32 + lane] = mk(R(0), R(0));
     __syncthreads();
-    const int *cid = stab, *rxi = stab + ncls, *ryo = stab + 2 * ncls;
-    const int ch = ch_lo + blockIdx.y, e = blockIdx.x * EPW + el;
-    const bool valid = e < M2;
-    const size_t Nq = (size_t)Lq * Lq;
-    for (int ux = w * G + sub; ux < Lq; ux += W * G) {
-        C2 z[DFT_MAXRY];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, ux = blockIdx.y, ch = ch_lo + blockIdx.z;
+    if (e >= M2) return;
+    const size_t row = ((size_t)ch * Lq * Lq + (size_t)ux * Lq) * M2 + e;
+    C2 z[DFT_MAXRY];
 #pragma unroll
-        for (int r = 0; r < DFT_MAXRY; r++) z[r] = mk(R(0), R(0));
-        const size_t row = ((size_t)ch * Nq + (size_t)ux * Lq) * M2 + (valid ? e : 0);
-        for (int uy0 = 0; uy0 < Lq; uy0 += UB) {
-            // all loads of the batch first, then the roundings (and the FP32 copy)
-            XT raw[UB];
+    for (int r = 0; r < DFT_MAXRY; r++) z[r] = mk(R(0), R(0));
+    for (int uy0 = 0; uy0 < Lq; uy0 += UB) {
+        // all loads of the batch first, then the roundings (and the FP32 copy)
+        XT raw[UB];
 #pragma unroll
-            for (int j = 0; j < UB; j++) {
-                raw[j].x = 0;
-                raw[j].y = 0;
-                if (valid && uy0 + j < Lq) raw[j] = X[row + (size_t)(uy0 + j) * M2];
-            }
-            C2 x[UB];
+        for (int j = 0; j < UB; j++) {
+            raw[j].x = 0;
+            raw[j].y = 0;
+            if (uy0 + j < Lq) raw[j] = X[row + (size_t)(uy0 + j) * M2];
+        }
+        C2 x[UB];
 #pragma unroll
-            for (int j = 0; j < UB; j++) {
-                x[j] = ld_as<R>(raw[j]);
-                if (x32 && valid && uy0 + j < Lq) put32(x32 + row + (size_t)(uy0 + j) * M2, x[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < UB; j++) {
-                if (uy0 + j >= Lq) break;
-                const C2 *p = sphy + (uy0 + j) * nry;
-#pragma unroll
-                for (int r = 0; r < DFT_MAXRY; r++) {
-                    if (r >= nry) break;
-                    const C2 ph = p[r];
-                    z[r].x = fma(ph.x, x[j].x, fma(-ph.y, x[j].y, z[r].x));
-                    z[r].y = fma(ph.x, x[j].y, fma(ph.y, x[j].x, z[r].y));
-                }
-            }
+        for (int j = 0; j < UB; j++) {
+            x[j] = ld_as<R>(raw[j]);
+            if (x32 && uy0 + j < Lq) put32(x32 + row + (size_t)(uy0 + j) * M2, x[j]);
         }
 #pragma unroll
-        for (int r = 0; r < DFT_MAXRY; r++) {
-            if (r >= nry) break;
-            for (int c = ryo[r]; c < ryo[r + 1]; c++) {
-                const C2 ph = sphx[ux * nrx + rxi[c]];
-                C2 &o = mine[c * 32 + lane];
-                o.x = fma(ph.x, z[r].x, fma(-ph.y, z[r].y, o.x));
-                o.y = fma(ph.x, z[r].y, fma(ph.y, z[r].x, o.y));
+        for (int j = 0; j < UB; j++) {
+            if (uy0 + j >= Lq) break;
+            const C2 *p = sphy + (uy0 + j) * nry;
+#pragma unroll
+            for (int r = 0; r < DFT_MAXRY; r++) {
+                if (r >= nry) break;
+                const C2 ph = p[r];
+                z[r].x = fma(ph.x, x[j].x, fma(-ph.y, x[j].y, z[r].x));
+                z[r].y = fma(ph.x, x[j].y, fma(ph.y, x[j].x, z[r].y));
             }
         }
     }
+    C2 *zo = Z + ((size_t)ch * Lq + ux) * nry * M2 + e;
+#pragma unroll
+    for (int r = 0; r < DFT_MAXRY; r++)
+        if (r < nry) zo[(size_t)r * M2] = z[r];
+}
+
+// Classes are visited grouped by R_y: sorted position c has class id cid[c] and R_x index rxi[c], and the group of
+// the r-th R_y is [ryo[r], ryo[r+1]).
+template <typename R>
+__global__ void __launch_bounds__(32 * DFT_MAXG) dft_cols_kernel(const typename cpx<R>::t *__restrict__ Z, int Lq,
+                                                                 int M2, int ncls, int nry, int nrx,
+                                                                 const int *__restrict__ tabs,
+                                                                 const typename cpx<R>::t *__restrict__ phx, int ch_lo,
+                                                                 double inv_nq, typename cpx<R>::t *__restrict__ Xr)
+{
+    using C2 = typename cpx<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *sz = reinterpret_cast<C2 *>(smem_raw);              // [DFT_UXC][32]  Z(u_x, R_y) of the CTA's entries
+    C2 *sphx = sz + DFT_UXC * 32;                           // [Lq][nrx]  e^{i u_x R_x}
+    int *stab = reinterpret_cast<int *>(sphx + Lq * nrx);   // cid [ncls], rxi [ncls], ryo [nry + 1]
+    for (int i = threadIdx.x; i < Lq * nrx; i += blockDim.x) sphx[i] = phx[i];
+    for (int i = threadIdx.x; i < 2 * ncls + nry + 1; i += blockDim.x) stab[i] = tabs[i];
     __syncthreads();
-    const R scale = R(inv_nq);
-    for (int o = threadIdx.x; o < (ncls << epw_log2); o += blockDim.x) {
-        const int c = o >> epw_log2, l = o & (EPW - 1), e2 = blockIdx.x * EPW + l;
-        R sx = 0, sy = 0;
-        for (int k = 0; k < W; k++)
-            for (int g = 0; g < G; g++) {
-                const C2 v = part[((size_t)k * ncls + c) * 32 + (g << epw_log2) + l];
-                sx += v.x;
-                sy += v.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e0 = blockIdx.x * 32, r = blockIdx.y, ch = ch_lo + blockIdx.z;
+    const int *cid = stab, *rxi = stab + ncls, *ryo = stab + 2 * ncls;
+    const int c = ryo[r] + w;
+    const bool mine = c < ryo[r + 1];   // this warp's class (warps past the group only help stage Z)
+    const int rx = mine ? rxi[c] : 0;
+    const C2 *zc = Z + ((size_t)ch * Lq * nry + r) * M2 + e0;   // Z(u_x, R_y) of entry e0 + l at zc[u_x nry M^2 + l]
+    const size_t zs = (size_t)nry * M2;
+    const int ne = min(32, M2 - e0);
+    C2 acc = mk(R(0), R(0));
+    for (int u0 = 0; u0 < Lq; u0 += DFT_UXC) {
+        const int nu = min(DFT_UXC, Lq - u0);
+        __syncthreads();   // the previous round's reads are done
+        for (int i = threadIdx.x; i < nu * 32; i += blockDim.x) {
+            const int ul = i >> 5, l = i & 31;
+            sz[i] = l < ne ? zc[(size_t)(u0 + ul) * zs + l] : mk(R(0), R(0));
+        }
+        __syncthreads();
+        if (mine)
+            for (int ul = 0; ul < nu; ul++) {
+                const C2 v = sz[ul * 32 + lane];
+                const C2 ph = sphx[(u0 + ul) * nrx + rx];
+                acc.x = fma(ph.x, v.x, fma(-ph.y, v.y, acc.x));
+                acc.y = fma(ph.x, v.y, fma(ph.y, v.x, acc.y));
             }
-        if (e2 < M2) Xr[((size_t)ch * ncls + cid[c]) * M2 + e2] = mk(sx * scale, sy * scale);
+    }
+    if (mine && lane < ne) {
+        const R scale = R(inv_nq);
+        Xr[((size_t)ch * ncls + cid[c]) * M2 + e0 + lane] = mk(acc.x * scale, acc.y * scale);
     }
 }
 
@@ -414,24 +436,24 @@ int dft_plan_nsplit(const tufrg_model *m)
     return (int)ns;
 }
 
-// launch shape of the separable transform: entries per warp (2^epw_log2, small enough that the grid
-// covers the GPU twice) and warps per CTA (0: not applicable, the sliced direct sum runs instead)
-void dft_sep_plan(const tufrg_model *m, int *warps, int *epw_log2)
+// whether the separable transform applies (*warps = warps of a dft_cols_kernel CTA = the largest number of classes
+// with one R_y, 0: the sliced direct sum runs instead): at most DFT_MAXRY distinct R_y, at most DFT_MAXG classes per
+// R_y, and the phase and class tables of each kernel within DFT_TABLE_CAP
+void dft_sep_plan(const tufrg_model *m, int *warps)
 {
     *warps = 0;
-    *epw_log2 = 5;
     if (m->dft_nry < 1 || m->dft_nry > DFT_MAXRY) return;
-    const int M2 = m->M * m->M;
-    while (*epw_log2 > 3 && 2L * ((M2 + (1 << *epw_log2) - 1) >> *epw_log2) < 2L * m->sm_count) (*epw_log2)--;
-    const int G = 32 >> *epw_log2;                          // rows side by side in a warp
     const size_t c2 = m->precision == TUFRG_FP64 ? sizeof(double2) : sizeof(float2);
-    const size_t fixed = c2 * m->Lq * (m->dft_nry + m->dft_nrx) + sizeof(int) * (2 * m->ncls + m->dft_nry + 1);
-    const size_t per_warp = c2 * m->ncls * 32, cap = 200 * 1024;
-    if (fixed + per_warp > cap) return;
-    const int wmax = (int)std::min<size_t>(m->precision == TUFRG_FP64 ? DFT_MAXW64 : DFT_MAXW, (cap - fixed) / per_warp);
-    const int need = (m->Lq + G - 1) / G;                  // warps for one row each
-    const int rows = (need + wmax - 1) / wmax;             // row groups per warp
-    *warps = (need + rows - 1) / rows;
+    if (c2 * m->Lq * m->dft_nry > DFT_TABLE_CAP) return;
+    if (c2 * (m->Lq * m->dft_nrx + DFT_UXC * 32) + sizeof(int) * (2 * m->ncls + m->dft_nry + 1) > DFT_TABLE_CAP) return;
+    int gmax = 0;
+    for (int c = 0; c < m->ncls; c++) {
+        int g = 0;
+        for (int c2 = 0; c2 < m->ncls; c2++) g += m->cls[2 * c2 + 1] == m->cls[2 * c + 1];
+        gmax = std::max(gmax, g);
+    }
+    if (gmax < 1 || gmax > DFT_MAXG) return;
+    *warps = gmax;
 }
 
 template <typename R, typename XT>
@@ -439,15 +461,17 @@ cudaError_t dft_sep_run(tufrg_model *m, const XT *d_state, const typename cpx<R>
                         int ch_lo, int nch, typename cpx<R>::t *Xr, float2 *x32)
 {
     using C2 = typename cpx<R>::t;
-    const int W = m->dft_warps, M2 = m->M * m->M, EPW = 1 << m->dft_epw_log2;
-    const size_t smem = sizeof(C2) * ((size_t)W * m->ncls * 32 + (size_t)m->Lq * (m->dft_nry + m->dft_nrx)) +
-                        sizeof(int) * (2 * m->ncls + m->dft_nry + 1);
-    auto k = dft_sep_kernel<R, XT>;
-    if (smem > 48 * 1024) TUFRG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PhaseScope ps(m, PH_DFT);
-    k<<<dim3((M2 + EPW - 1) / EPW, nch), 32 * W, smem, m->stream>>>(d_state, m->Lq, M2, m->ncls, m->dft_nry, m->dft_nrx,
-                                                                   m->dft_epw_log2, m->d_dft_tabs, phy, phx, ch_lo,
-                                                                   1.0 / m->Nq, Xr, x32);
+    const int M2 = m->M * m->M, xb = (M2 + DFT_THREADS - 1) / DFT_THREADS;
+    C2 *Z = static_cast<C2 *>(m->d_dftpart);
+    const size_t smem_rows = sizeof(C2) * (size_t)m->Lq * m->dft_nry;
+    const size_t smem_cols = sizeof(C2) * ((size_t)m->Lq * m->dft_nrx + DFT_UXC * 32) +
+                             sizeof(int) * (2 * m->ncls + m->dft_nry + 1);
+    PhaseScope ps(m, PH_DFT, 2);
+    dft_rows_kernel<R, XT><<<dim3(xb, m->Lq, nch), DFT_THREADS, smem_rows, m->stream>>>(d_state, m->Lq, M2, m->dft_nry, phy, ch_lo, Z,
+                                                                      x32);
+    TUFRG_CUDA_TRY(cudaGetLastError());
+    dft_cols_kernel<R><<<dim3((M2 + 31) / 32, m->dft_nry, nch), 32 * m->dft_warps, smem_cols, m->stream>>>(
+        Z, m->Lq, M2, m->ncls, m->dft_nry, m->dft_nrx, m->d_dft_tabs, phx, ch_lo, 1.0 / m->Nq, Xr);
     return cudaGetLastError();
 }
 

@@ -274,11 +274,12 @@ struct tufrg_model {
     float4 *d_rec = nullptr;        // [Nk][4] split-path loop records (projectors + Fermi data)
     float2 *d_Xr32 = nullptr;       // [2][ncls][M][M] Fourier transforms (split path)
     float2 *d_ph32 = nullptr;       // [Nq][nph] phase table (split path)
-    void *d_dftpart = nullptr;      // Fourier-transform partial sums (scratch)
+    void *d_dftpart = nullptr;      // Fourier-transform scratch: partial sums, or Z(u_x, R_y) of the separable form
     int dft_nsplit = 1;             // transfer-mesh slices of the Fourier transform
-    // separable Fourier transform: distinct R_y / R_x of the classes, warps per CTA (0 = not used),
-    // int tables (class id by R_y group, R_x index, R_y group offsets) and phases [Lq][n_Ry], [Lq][n_Rx]
-    int dft_nry = 0, dft_nrx = 0, dft_warps = 0, dft_epw_log2 = 5;
+    // separable Fourier transform: distinct R_y / R_x of the classes, warps per CTA of its column pass (the most
+    // classes with one R_y; 0 = not used), int tables (class id by R_y group, R_x index, R_y group offsets) and
+    // phases [Lq][n_Ry], [Lq][n_Rx]; its row pass keeps Z(u_x, R_y) in d_dftpart
+    int dft_nry = 0, dft_nrx = 0, dft_warps = 0;
     int *d_dft_tabs = nullptr;
     double2 *d_dft_phy = nullptr, *d_dft_phx = nullptr;
     float2 *d_dft_phy32 = nullptr, *d_dft_phx32 = nullptr;
@@ -380,8 +381,8 @@ cudaError_t launch_set_scalars(tufrg_model *m, double T, double scale);
 // momenta, and no FP64 copy on the split path (what the symmetric-state products read)
 cudaError_t launch_loops(tufrg_model *m, int channel_mask, bool reps_only = false);
 // The split path reads the FP32 copy of the state (d_state32), the plain path the FP64 state.
-// launch shape of the separable transform (warps per CTA, 0 if it does not apply; entries per warp)
-void dft_sep_plan(const tufrg_model *m, int *warps, int *epw_log2);
+// whether the separable transform applies: *warps = warps per CTA of its column pass, 0 if it does not
+void dft_sep_plan(const tufrg_model *m, int *warps);
 cudaError_t launch_dft(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask);
 // qlist (nlist entries): only these transfer momenta (the orbit representatives of a symmetric state)
 cudaError_t launch_project(tufrg_model *m, const double2 *d_state, const float2 *d_state32, int channel_mask,
