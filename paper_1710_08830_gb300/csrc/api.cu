@@ -43,6 +43,20 @@ tufrg_status cuda_fail(tufrg_model *m, cudaError_t e, const char *where)
     return e == cudaErrorNotSupported ? TUFRG_ENOTSUP : TUFRG_ECUDA;
 }
 
+// A host allocation that failed inside an entry point (std::bad_alloc, or std::length_error for a size beyond what
+// a container holds) is reported as TUFRG_ENOMEM instead of crossing the C boundary.
+tufrg_status host_alloc_fail(tufrg_model *m, const std::exception &ex) noexcept
+{
+    if (m) {
+        try {
+            m->err = std::string("host allocation failed: ") + ex.what();
+        } catch (...) {
+            m->err.clear();
+        }
+    }
+    return TUFRG_ENOMEM;
+}
+
 #define CK(expr, where)                                        \
     do {                                                       \
         cudaError_t _e = (expr);                               \
@@ -832,8 +846,7 @@ tufrg_status read_device_error(tufrg_model *m)
 
 extern "C" {
 
-// The host tables of init grow with the meshes and the bond set: a failed host allocation there (std::bad_alloc, or
-// std::length_error for a size beyond what a container holds) becomes TUFRG_ENOMEM instead of crossing the boundary.
+// The host tables of init grow with the meshes and the bond set (host_alloc_fail).
 tufrg_status tufrg_init_model(const tufrg_model_desc *desc, void *cuda_stream, tufrg_model **out)
 try {
     if (!out) return TUFRG_EINVAL;
@@ -1361,15 +1374,7 @@ try {
     }
     return TUFRG_OK;
 } catch (const std::exception &ex) {
-    tufrg_model *m = out ? *out : nullptr;
-    if (m) {
-        try {
-            m->err = std::string("host allocation failed: ") + ex.what();
-        } catch (...) {
-            m->err.clear();
-        }
-    }
-    return TUFRG_ENOMEM;
+    return host_alloc_fail(out ? *out : nullptr, ex);
 }
 
 tufrg_status tufrg_model_info(const tufrg_model *m, int *products, double *ms_tc, double *ms_simt)
@@ -1536,7 +1541,7 @@ tufrg_status tufrg_project(tufrg_model *m, const void *d_state, int channel_mask
 }
 
 tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channel_mask, void *d_dstate)
-{
+try {
     if (!m || !d_state || !d_dstate) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~(3 | TUFRG_SYMMETRIC_STATE))
@@ -1623,6 +1628,8 @@ tufrg_status tufrg_rhs(tufrg_model *m, double T, const void *d_state, int channe
     m->launches += g->launches;
     m->loop_launches += g->loop_launches;
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    return host_alloc_fail(m, ex);
 }
 
 // ------------------------------------------------------------------ right-hand side over shards of momenta
@@ -1674,7 +1681,7 @@ tufrg_status tufrg_shard_classes(const tufrg_model *m, int *ncls, int *h_cls)
 
 tufrg_status tufrg_rhs_shard_transform(tufrg_model *m, const void *d_state_local, int n_q, const int *h_q_list,
                                        int channel_mask, void *d_xr)
-{
+try {
     if (!m || !d_state_local || !d_xr) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
     tufrg_status st = upload_shard(m, n_q, h_q_list);
@@ -1682,11 +1689,13 @@ tufrg_status tufrg_rhs_shard_transform(tufrg_model *m, const void *d_state_local
     CK(launch_shard_dft(m, reinterpret_cast<const double2 *>(d_state_local), n_q, m->d_shard_q, channel_mask,
                         reinterpret_cast<double2 *>(d_xr)), "shard Fourier transform");
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    return host_alloc_fail(m, ex);
 }
 
 tufrg_status tufrg_rhs_shard_finish(tufrg_model *m, double T, const void *d_state_local, int n_q, const int *h_q_list,
                                     const void *d_xr, int channel_mask, void *d_dstate_local)
-{
+try {
     if (!m || !d_state_local || !d_xr || !d_dstate_local) return fail(m, TUFRG_EINVAL, "NULL argument");
     if (!(T > 0) || !std::isfinite(T)) return fail(m, TUFRG_EINVAL, "T must be positive and finite");
     if (channel_mask & ~3) return fail(m, TUFRG_EINVAL, "channel_mask must be a subset of P|C");
@@ -1711,6 +1720,8 @@ tufrg_status tufrg_rhs_shard_finish(tufrg_model *m, double T, const void *d_stat
     CK(launch_shard_gather(m, m->d_shard_out, n_q, m->d_shard_q, reinterpret_cast<double2 *>(d_dstate_local)),
        "gather of the shard's rows");
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    return host_alloc_fail(m, ex);
 }
 
 tufrg_status tufrg_rhs_host(tufrg_model *m, double T, const void *h_state, int channel_mask, void *h_dstate)
@@ -1987,7 +1998,7 @@ tufrg_status tufrg_flow_resume(tufrg_model *m, const tufrg_flow_opts *o, const v
 }
 
 tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flow_opts *o, tufrg_flow_result *res)
-{
+try {
     if (!models || n < 1 || !o || !res) return TUFRG_EINVAL;
     for (int i = 0; i < n; i++) {
         if (!models[i]) return TUFRG_EINVAL;
@@ -2056,6 +2067,8 @@ tufrg_status tufrg_flow_batch(tufrg_model *const *models, int n, const tufrg_flo
     const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     for (int i = 0; i < n; i++) res[i].wall_s = wall;
     return first;
+} catch (const std::exception &ex) {
+    return host_alloc_fail(nullptr, ex);
 }
 
 }  // extern "C"

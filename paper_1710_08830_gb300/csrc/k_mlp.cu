@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <random>
 #include <string>
@@ -134,6 +135,19 @@ tufrg_status mfail(tufrg_mlp *n, tufrg_status st, const std::string &msg)
     if (n) n->err = msg;
     (void)cudaGetLastError();   // leave no failed call's error pending for the caller's next launch check
     return st;
+}
+
+// a host allocation that failed inside an entry point becomes TUFRG_ENOMEM instead of crossing the C boundary
+tufrg_status mlp_host_alloc_fail(tufrg_mlp *n, const std::exception &ex) noexcept
+{
+    if (n) {
+        try {
+            n->err = std::string("host allocation failed: ") + ex.what();
+        } catch (...) {
+            n->err.clear();
+        }
+    }
+    return TUFRG_ENOMEM;
 }
 
 #define MK(expr, where)                                                                           \
@@ -272,7 +286,7 @@ extern "C" {
 
 tufrg_status tufrg_mlp_create(int n_in, int width, int depth, int n_out, unsigned long long seed, void *cuda_stream,
                               tufrg_mlp **out)
-{
+try {
     if (!out) return TUFRG_EINVAL;
     *out = nullptr;
     if (n_in < 1 || width < 1 || depth < 1 || n_out < 1 || n_in > 4096 || width > 4096 || n_out > 65536) return TUFRG_EINVAL;
@@ -317,6 +331,8 @@ tufrg_status tufrg_mlp_create(int n_in, int width, int depth, int n_out, unsigne
     MK(cudaGetLastError(), "convert parameters");
     MK(cudaStreamSynchronize(n->stream), "sync");
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    return mlp_host_alloc_fail(out ? *out : nullptr, ex);
 }
 
 void tufrg_mlp_free(tufrg_mlp *n)

@@ -17,6 +17,8 @@
 // and skipped evaluations are counted on the device.
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <string>
 #include <vector>
 
 #include "tufrg_internal.cuh"
@@ -163,7 +165,7 @@ extern "C" {
 
 tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_mean, const float *h_std,
                                  const double *h_feature_params, double resid_tol, int n_check, const int *h_check_q)
-{
+try {
     if (!m) return TUFRG_EINVAL;
     auto drop = [&]() {
         void *ptrs[] = {m->d_check_q, m->d_sur_X, m->d_sur_Y, m->d_sur_mean, m->d_sur_std, m->d_chk_part, m->d_chk,
@@ -247,6 +249,16 @@ tufrg_status tufrg_set_surrogate(tufrg_model *m, tufrg_mlp *net, const float *h_
     }
     cudaDeviceSynchronize();
     return TUFRG_OK;
+} catch (const std::exception &ex) {
+    // a host allocation that failed (the error message) becomes TUFRG_ENOMEM instead of crossing the C boundary
+    if (m) {
+        try {
+            m->err = std::string("host allocation failed: ") + ex.what();
+        } catch (...) {
+            m->err.clear();
+        }
+    }
+    return TUFRG_ENOMEM;
 }
 
 tufrg_status tufrg_surrogate_stats(tufrg_model *m, long long *accepted, long long *rejected, long long *skipped)

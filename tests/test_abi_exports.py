@@ -4,6 +4,7 @@ import glob
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -88,6 +89,31 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.tufrg_mlp_last_error(None) == b"network handle is NULL"
     L.tufrg_free(None)
     L.tufrg_mlp_free(None)
+
+
+def test_host_allocation_failure_is_a_status_not_an_exception(libpath):
+    """A host allocation that fails inside an entry point returns TUFRG_ENOMEM instead of throwing across the C
+    boundary (which would end the caller's process).  tufrg_mlp_create's initial weights (64 layers of width 4096,
+    4.2 GB) are allocated on the host before any CUDA call, here in a child process whose address space is limited
+    to 1 GB more than it already maps; no device is touched."""
+    code = r"""
+import ctypes, resource, sys
+L = ctypes.CDLL(sys.argv[1])
+L.tufrg_mlp_last_error.restype = ctypes.c_char_p
+vm = 0
+for line in open("/proc/self/status"):
+    if line.startswith("VmSize:"):
+        vm = int(line.split()[1]) * 1024
+resource.setrlimit(resource.RLIMIT_AS, (vm + (1 << 30), resource.getrlimit(resource.RLIMIT_AS)[1]))
+out = ctypes.c_void_p()
+st = L.tufrg_mlp_create(16, 4096, 64, 16, ctypes.c_ulonglong(0), None, ctypes.byref(out))
+msg = L.tufrg_mlp_last_error(out) if out.value else b""
+print(st, msg.decode())
+"""
+    r = subprocess.run([sys.executable, "-c", code, libpath], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    st, msg = r.stdout.strip().split(" ", 1)
+    assert int(st) == 2 and msg.startswith("host allocation failed"), r.stdout
 
 
 def test_bad_descriptors_are_rejected_before_device_use(libpath):
