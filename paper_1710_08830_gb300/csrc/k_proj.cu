@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(128) dft_kernel(const XT *__restrict__ X, int 
 // Lq (n_Ry + n_cls / Lq) complex FMAs per entry and class instead of Nq, in two passes:
 //   dft_rows_kernel: one thread per (channel, u_x, matrix entry) reads its Lq values of the state, UB loads in
 //     flight at a time (the only pass over the state, coalesced across entries), keeps Z for the n_Ry distinct
-//     R_y of the classes in registers and writes them to a scratch [ch][u_x][R_y][M^2] small enough to stay in
-//     L2; reading the FP64 state on the split path it also writes the FP32 rounding (the copy the projections
-//     read);
+//     R_y of the classes in registers and writes them to a scratch [ch][u_x][R_y][M^2] (n_Ry / Lq of the state's
+//     size: 2.5 MB at the 24x24 two-band workload, held in L2); reading the FP64 state on the split path it also
+//     writes the FP32 rounding (the copy the projections read);
 //   dft_cols_kernel: a CTA per (channel, R_y, 32 consecutive entries) stages Z(u_x, R_y) of its entries in shared
 //     memory, DFT_UXC values of u_x at a time; warp w adds e^{i u_x R_x} Z(u_x, R_y) over u_x for the w-th class
 //     with that R_y, one entry per lane.
